@@ -1,0 +1,282 @@
+"""Python access to the FP64 CPU oracle (``oracle/hs3d_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use this module; the product library never does.
+The C source is compiled with gcc (``-O2 -fopenmp``, plain IEEE arithmetic, no
+fast-math) into ``oracle/_build/liboracle.so`` on first use.
+
+Array layouts (numpy, float64, C order):
+  u, dudt      [E, 5, n, n, n]   (last axis is i, the xi direction)
+  X            [E, 3, n, n, n]
+  Ja           [E, 3(d), 3(c), n, n, n]   Ja[e, d, c] = J d xi_d / d x_c
+  J            [E, n, n, n]
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hs3d_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PHYSICS = {"euler": 0, "ns": 1}
+SURFACE = {"lf": 0, "roe": 1, "ec": 2}
+VOLUME = {"standard": 0, "ec": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library; returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c11", "-D_GNU_SOURCE", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Box(C.Structure):
+    _fields_ = [("ex", C.c_int), ("ey", C.c_int), ("ez", C.c_int), ("N", C.c_int),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("amp", C.c_double)]
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("physics", C.c_int), ("surface_flux", C.c_int), ("volume_form", C.c_int),
+                ("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double), ("cfl", C.c_double)]
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_lgl.argtypes = [C.c_int, _dp, _dp]
+            L.orc_dmatrix.argtypes = [C.c_int, _dp, _dp]
+            L.orc_mesh_create.argtypes = [C.POINTER(_Box), C.c_void_p]
+            L.orc_mesh_create.restype = C.c_void_p
+            L.orc_mesh_destroy.argtypes = [C.c_void_p]
+            L.orc_mesh_E.argtypes = [C.c_void_p]
+            L.orc_mesh_arrays.argtypes = [C.c_void_p] + [C.c_void_p] * 6
+            L.orc_neighbour.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+            L.orc_metrics.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+            for name in ("orc_flux_lf", "orc_flux_roe", "orc_flux_ec"):
+                getattr(L, name).argtypes = [_dp, _dp, _dp, C.c_double, _dp]
+            L.orc_flux_roe_signed.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_int]
+            L.orc_flux_euler.argtypes = [_dp, _dp, C.c_double, _dp]
+            L.orc_flux_visc.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp, _dp]
+            L.orc_entropy_vars.argtypes = [_dp, C.c_double, _dp]
+            L.orc_logmean.argtypes = [C.c_double, C.c_double]
+            L.orc_logmean.restype = C.c_double
+            L.orc_residual.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
+            L.orc_gradients.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
+            L.orc_dt.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp]
+            L.orc_dt.restype = C.c_double
+            L.orc_rk3_step.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp, C.c_double, C.POINTER(C.c_double)]
+            L.orc_rk3_coefficients.argtypes = [_dp, _dp, _dp]
+            L.orc_lsrk3_stage.argtypes = [C.c_longlong, C.c_int, C.c_double, _dp, _dp, _dp]
+            L.orc_ic_vortex.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, _dp]
+            L.orc_ic_tgv.argtypes = [C.c_void_p, C.c_double, C.c_double, _dp]
+            L.orc_integrals.argtypes = [C.c_void_p, C.c_double, _dp, C.c_void_p, _dp]
+            _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------- 1-D operators
+
+def lgl(N: int):
+    """Gauss-Lobatto nodes and weights on [-1, 1] (ascending)."""
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    if lib().orc_lgl(N, x, w) != 0:
+        raise ValueError("N must be >= 1")
+    return x, w
+
+
+def dmatrix(N: int, x=None):
+    """Nodal derivative matrix D[i, j] = l_j'(x_i) on the Gauss-Lobatto nodes (or given x)."""
+    if x is None:
+        x, _ = lgl(N)
+    D = np.zeros((N + 1, N + 1))
+    lib().orc_dmatrix(N, np.ascontiguousarray(x, dtype=np.float64), D)
+    return D
+
+
+# --------------------------------------------------------------------------- configuration
+
+class Cfg:
+    def __init__(self, physics="euler", surface="lf", volume="standard", gamma=1.4, Re=1600.0, Pr=0.72, cfl=0.5):
+        self.physics, self.surface, self.volume = physics, surface, volume
+        self.gamma, self.Re, self.Pr, self.cfl = gamma, Re, Pr, cfl
+
+    def c(self):
+        return _Cfg(PHYSICS[self.physics], SURFACE[self.surface], VOLUME[self.volume],
+                    self.gamma, self.Re, self.Pr, self.cfl)
+
+
+class Mesh:
+    """Oracle mesh of an ex*ey*ez periodic box with Gauss-Lobatto nodes of degree N."""
+
+    def __init__(self, ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, X=None):
+        self.ex, self.ey, self.ez, self.N = ex, ey, ez, N
+        self.n = N + 1
+        self.E = ex * ey * ez
+        self.lo, self.hi, self.amp = tuple(lo), tuple(hi), amp
+        box = _Box(ex, ey, ez, N, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), amp)
+        Xp = None
+        if X is not None:
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            assert X.shape == (self.E, 3, self.n, self.n, self.n)
+            Xp = X.ctypes.data
+        self._h = lib().orc_mesh_create(C.byref(box), Xp)
+        if not self._h:
+            raise ValueError("bad mesh description")
+        n = self.n
+        self.xi = np.zeros(n)
+        self.w = np.zeros(n)
+        self.D = np.zeros((n, n))
+        self.X = np.zeros((self.E, 3, n, n, n))
+        self.Ja = np.zeros((self.E, 3, 3, n, n, n))
+        self.J = np.zeros((self.E, n, n, n))
+        lib().orc_mesh_arrays(self._h, *(a.ctypes.data for a in (self.xi, self.w, self.D, self.X, self.Ja, self.J)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_mesh_destroy(h)
+            self._h = None
+
+    @property
+    def shape(self):
+        return (self.E, 5, self.n, self.n, self.n)
+
+    def neighbour(self, e, d, side):
+        return lib().orc_neighbour(self._h, e, d, side)
+
+    # ---- initial conditions
+    def ic_vortex(self, gamma=1.4, Ma=0.5, beta=5.0, xc=None, yc=None, t=0.0):
+        if xc is None:
+            xc = 0.5 * (self.lo[0] + self.hi[0])
+        if yc is None:
+            yc = 0.5 * (self.lo[1] + self.hi[1])
+        u = np.zeros(self.shape)
+        lib().orc_ic_vortex(self._h, gamma, Ma, beta, xc, yc, t, u)
+        return u
+
+    def ic_tgv(self, gamma=1.4, Ma=0.1):
+        u = np.zeros(self.shape)
+        lib().orc_ic_tgv(self._h, gamma, Ma, u)
+        return u
+
+    # ---- operators
+    def residual(self, cfg: Cfg, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(self.shape)
+        lib().orc_residual(self._h, C.byref(cfg.c()), u, out)
+        return out
+
+    def gradients(self, cfg: Cfg, u):
+        """BR1 gradients [E, 4(v1,v2,v3,T), 3(x,y,z), n, n, n]."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros((self.E, 4, 3, self.n, self.n, self.n))
+        lib().orc_gradients(self._h, C.byref(cfg.c()), u, out)
+        return out
+
+    def dt(self, cfg: Cfg, u):
+        return lib().orc_dt(self._h, C.byref(cfg.c()), np.ascontiguousarray(u, dtype=np.float64))
+
+    def rk3_step(self, cfg: Cfg, u, g=None, dt=0.0):
+        """One Williamson RK3 step in place on u (and g); returns the dt used."""
+        if g is None:
+            g = np.zeros_like(u)
+        used = C.c_double(0.0)
+        lib().orc_rk3_step(self._h, C.byref(cfg.c()), u, g, dt, C.byref(used))
+        return used.value
+
+    def integrals(self, gamma, u, dudt=None):
+        """[sum J w u_v (or dudt_v) for v in 0..4, entropy rate, entropy-rate magnitude scale]."""
+        out = np.zeros(7)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        dp = None
+        if dudt is not None:
+            dudt = np.ascontiguousarray(dudt, dtype=np.float64)
+            dp = dudt.ctypes.data
+        lib().orc_integrals(self._h, gamma, u, dp, out)
+        return out
+
+
+# --------------------------------------------------------------------------- point functions
+
+def _v(a, k=5):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.shape == (k,)
+    return a
+
+
+def flux_euler(u, a, gamma=1.4):
+    f = np.zeros(5)
+    lib().orc_flux_euler(_v(u), _v(a, 3), gamma, f)
+    return f
+
+
+def flux_lf(uL, uR, nh, gamma=1.4):
+    f = np.zeros(5)
+    lib().orc_flux_lf(_v(uL), _v(uR), _v(nh, 3), gamma, f)
+    return f
+
+
+def flux_roe(uL, uR, nh, gamma=1.4):
+    f = np.zeros(5)
+    lib().orc_flux_roe(_v(uL), _v(uR), _v(nh, 3), gamma, f)
+    return f
+
+
+def roe_wave_sum(uL, uR, nh, gamma=1.4):
+    """sum_k lambda_k alpha_k r_k with signed eigenvalues."""
+    f = np.zeros(5)
+    lib().orc_flux_roe_signed(_v(uL), _v(uR), _v(nh, 3), gamma, f, 1)
+    return f
+
+
+def flux_ec(uL, uR, a, gamma=1.4):
+    f = np.zeros(5)
+    lib().orc_flux_ec(_v(uL), _v(uR), _v(a, 3), gamma, f)
+    return f
+
+
+def flux_visc(q, G, mu, kappa, a):
+    f = np.zeros(5)
+    lib().orc_flux_visc(_v(q, 4), np.ascontiguousarray(G, dtype=np.float64).reshape(12), mu, kappa, _v(a, 3), f)
+    return f
+
+
+def entropy_vars(u, gamma=1.4):
+    w = np.zeros(5)
+    lib().orc_entropy_vars(_v(u), gamma, w)
+    return w
+
+
+def logmean(a, b):
+    return lib().orc_logmean(a, b)
+
+
+def rk3_coefficients():
+    A, B, Cc = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib().orc_rk3_coefficients(A, B, Cc)
+    return A, B, Cc
+
+
+def lsrk3_stage(k, dt, u, g, R):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lib().orc_lsrk3_stage(u.size, k, dt, u, g, np.ascontiguousarray(R, dtype=np.float64))

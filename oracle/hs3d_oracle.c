@@ -1,0 +1,890 @@
+/*
+ * hs3d oracle -- a plain, slow FP64 CPU implementation of the DGSEM residual
+ * and the Williamson low-storage RK3 step for the compressible Euler and
+ * Navier-Stokes equations on periodic curvilinear hexahedral boxes.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * only the tests, __graft_entry__.smoke() and the CPU-baseline leg of bench.py
+ * load it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Everything is computed in the order the method states it, with one loop per
+ * formula.  Sources (HORSES3D paper, arXiv 2206.09733):
+ *   - conservative variables, Euler flux F_e, viscous flux F_v  (Sec. 3.2,
+ *     Eq. compressibleNScompact and Eq. viscousfluxes)
+ *   - mapped equations J u_t + div_xi F~ = 0 with contravariant fluxes
+ *     (Sec. 3.3, Eq. compressibleNScompact_transformed)
+ *   - weak form with a numerical flux at element faces, Gauss-Lobatto
+ *     quadrature (Sec. 3.3, Eqs. NS2-NS5)
+ *   - Lax-Friedrichs, Roe and central surface fluxes, BR1 viscous scheme
+ *     (Sec. 3.3, list of convective and viscous fluxes)
+ *   - Chandrashekar entropy-conservative split form (Sec. 3.5)
+ *   - entropy S = -rho s, s = ln p - gamma ln rho, w = dS/du (Sec. 4.4,
+ *     Eq. shock:entropy)
+ *   - Williamson low-storage RK3 (Sec. 3.7)
+ * The paper prints no formula for the fluxes, the split form, the RK
+ * coefficients, the metric terms, the time-step rule or BR1; those are the
+ * published methods it cites, restated here (each function says which).
+ *
+ * Layout (shared with callers, not with the CUDA code): polynomial degree N
+ * (the paper's P), n = N+1 Gauss-Lobatto nodes per direction, node
+ * (i,j,k) -> i + n*(j + n*k).  State u[e][v][node] with v = rho, rho v1,
+ * rho v2, rho v3, rho e.  Node coordinates X[e][c][node].  Metric terms
+ * Ja[e][d][c][node] = J * d xi_d / d x_c, Jacobian J[e][node].
+ * Elements of an ex*ey*ez box: e = a + ex*(b + ey*c), all faces periodic.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NVAR 5
+#define NGRAD 4 /* gradient variables q = (v1, v2, v3, T) */
+
+void orc_flux_roe_signed(const double *uL, const double *uR, const double *nh, double g, double *f, int sign_mode);
+
+/* ------------------------------------------------------------------------ */
+/* 1-D Gauss-Lobatto operators (Sec. 3.3: GL quadrature)                    */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre polynomial L_N(x) and its derivative by the three-term recurrence. */
+static void legendre_and_derivative(int N, double x, double *L, double *dL)
+{
+    double Lm1 = 1.0, L0 = x;          /* L_0, L_1 */
+    double dLm1 = 0.0, dL0 = 1.0;
+    if (N == 0) { *L = 1.0; *dL = 0.0; return; }
+    for (int k = 2; k <= N; ++k) {
+        double Lk = ((2.0 * k - 1.0) * x * L0 - (k - 1.0) * Lm1) / k;
+        double dLk = dLm1 + (2.0 * k - 1.0) * L0;   /* L_k' = L_{k-2}' + (2k-1) L_{k-1} */
+        Lm1 = L0; L0 = Lk;
+        dLm1 = dL0; dL0 = dLk;
+    }
+    *L = L0; *dL = dL0;
+}
+
+/* Gauss-Lobatto nodes: -1, +1 and the roots of L_N'.  Newton on L_N' with the
+ * second derivative taken from Legendre's equation
+ *   (1-x^2) L'' - 2x L' + N(N+1) L = 0.
+ * Weights w_i = 2 / (N(N+1) L_N(x_i)^2).  Nodes in ascending order. */
+int orc_lgl(int N, double *x, double *w)
+{
+    if (N < 1) return -1;
+    int n = N + 1;
+    for (int j = 0; j < n; ++j) {
+        double xj;
+        if (j == 0) xj = -1.0;
+        else if (j == N) xj = 1.0;
+        else {
+            xj = -cos(M_PI * j / N);     /* Chebyshev-Gauss-Lobatto start */
+            for (int it = 0; it < 100; ++it) {
+                double L, dL;
+                legendre_and_derivative(N, xj, &L, &dL);
+                double d2L = (2.0 * xj * dL - N * (N + 1.0) * L) / (1.0 - xj * xj);
+                double dx = dL / d2L;
+                xj -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+        }
+        double L, dL;
+        legendre_and_derivative(N, xj, &L, &dL);
+        x[j] = xj;
+        w[j] = 2.0 / (N * (N + 1.0) * L * L);
+    }
+    return 0;
+}
+
+/* Nodal derivative matrix D_ij = l_j'(x_i) from barycentric weights
+ * lambda_j = 1 / prod_{k != j} (x_j - x_k):
+ *   D_ij = (lambda_j / lambda_i) / (x_i - x_j),   i != j
+ *   D_ii = - sum_{j != i} D_ij.
+ * D is stored row-major: D[i*n + j]. */
+int orc_dmatrix(int N, const double *x, double *D)
+{
+    int n = N + 1;
+    double lam[16];
+    if (n > 16) return -1;
+    for (int j = 0; j < n; ++j) {
+        double p = 1.0;
+        for (int k = 0; k < n; ++k) if (k != j) p *= (x[j] - x[k]);
+        lam[j] = 1.0 / p;
+    }
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+            s += D[i * n + j];
+        }
+        D[i * n + i] = -s;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh: periodic box of ex*ey*ez hexahedra, optional smooth perturbation    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int ex, ey, ez, N;
+    double lo[3], hi[3];
+    double amp;   /* x_c += amp*(L_c/2pi)*sin(t_x)sin(t_y)sin(t_z), t = box mapped to [-pi,pi] */
+} orc_box;
+
+typedef struct {
+    orc_box box;
+    int n, n3, E;
+    double xi[16], w[16], D[256];
+    double *X;    /* [E][3][n3] */
+    double *Ja;   /* [E][3][3][n3] */
+    double *J;    /* [E][n3] */
+} orc_mesh;
+
+static int node_index(int n, int i, int j, int k) { return i + n * (j + n * k); }
+
+/* Element neighbour across face (d, side), side = +1 or -1, periodic wrap. */
+static int neighbour(const orc_box *b, int e, int d, int side)
+{
+    int ab[3];
+    int E3[3] = {b->ex, b->ey, b->ez};
+    ab[0] = e % b->ex;
+    ab[1] = (e / b->ex) % b->ey;
+    ab[2] = e / (b->ex * b->ey);
+    ab[d] = (ab[d] + side + E3[d]) % E3[d];
+    return ab[0] + b->ex * (ab[1] + b->ey * ab[2]);
+}
+
+int orc_neighbour(const orc_mesh *m, int e, int d, int side)
+{
+    return neighbour(&m->box, e, d, side);
+}
+
+/* Gauss-Lobatto node coordinates of every element:
+ *   x_c = lo_c + h_c*(index_c + (xi+1)/2)
+ * then the smooth displacement (same scalar for every coordinate, scaled by the
+ * box length so that [-pi,pi]^3 gets exactly amp*sin(x)sin(y)sin(z)), evaluated
+ * at the unperturbed position. */
+static void box_nodes(const orc_box *b, const double *xi, double *X)
+{
+    int n = b->N + 1, n3 = n * n * n;
+    int E3[3] = {b->ex, b->ey, b->ez};
+    int E = b->ex * b->ey * b->ez;
+    for (int e = 0; e < E; ++e) {
+        int ab[3] = {e % b->ex, (e / b->ex) % b->ey, e / (b->ex * b->ey)};
+        for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            int ijk[3] = {i, j, k};
+            double x0[3], th[3];
+            for (int c = 0; c < 3; ++c) {
+                double L = b->hi[c] - b->lo[c];
+                double h = L / E3[c];
+                x0[c] = b->lo[c] + h * (ab[c] + 0.5 * (xi[ijk[c]] + 1.0));
+                th[c] = -M_PI + 2.0 * M_PI * (x0[c] - b->lo[c]) / L;
+            }
+            double s = sin(th[0]) * sin(th[1]) * sin(th[2]);
+            for (int c = 0; c < 3; ++c) {
+                double L = b->hi[c] - b->lo[c];
+                X[(e * 3 + c) * n3 + node_index(n, i, j, k)] = x0[c] + b->amp * (L / (2.0 * M_PI)) * s;
+            }
+        }
+    }
+}
+
+/* Derivative along reference direction d of a nodal field f (one element):
+ * (D_d f)_ijk = sum_m D[ind_d][m] f(node with ind_d -> m). */
+static double dir_derivative(int n, const double *D, const double *f, int d, int i, int j, int k)
+{
+    double s = 0.0;
+    for (int m = 0; m < n; ++m) {
+        int idx;
+        if (d == 0) idx = node_index(n, m, j, k);
+        else if (d == 1) idx = node_index(n, i, m, k);
+        else idx = node_index(n, i, j, m);
+        int row = (d == 0) ? i : (d == 1) ? j : k;
+        s += D[row * n + m] * f[idx];
+    }
+    return s;
+}
+
+/* Metric terms in the conservative curl form (Kopriva 2006, the
+ * free-stream-preserving form for curved DGSEM; Sec. 3.3 "contravariant
+ * fluxes"): for reference direction i and physical component c with
+ * (c, m, l) cyclic,
+ *   Ja^i_c = d/dxi_{i+2} ( X_l dX_m/dxi_{i+1} ) - d/dxi_{i+1} ( X_l dX_m/dxi_{i+2} ),
+ * indices mod 3, the products taken pointwise at the nodes (interpolation onto
+ * degree N).  J = det(dX/dxi) with the derivatives from D. */
+int orc_metrics(int E, int N, const double *D, const double *X, double *Ja, double *J)
+{
+    int n = N + 1, n3 = n * n * n;
+    double *tmp = (double *)malloc(sizeof(double) * n3 * 2);
+    double *dX = (double *)malloc(sizeof(double) * n3 * 9);   /* dX[c][d][node] */
+    if (!tmp || !dX) { free(tmp); free(dX); return -1; }
+    for (int e = 0; e < E; ++e) {
+        const double *Xe = X + (size_t)e * 3 * n3;
+        /* dX_c / dxi_d at every node */
+        for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i)
+            dX[(c * 3 + d) * n3 + node_index(n, i, j, k)] =
+                dir_derivative(n, D, Xe + c * n3, d, i, j, k);
+        /* J = a1 . (a2 x a3), a_d = dX/dxi_d */
+        for (int p = 0; p < n3; ++p) {
+            double a[3][3];
+            for (int d = 0; d < 3; ++d) for (int c = 0; c < 3; ++c) a[d][c] = dX[(c * 3 + d) * n3 + p];
+            double cx = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+            double cy = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+            double cz = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+            J[(size_t)e * n3 + p] = a[0][0] * cx + a[0][1] * cy + a[0][2] * cz;
+        }
+        for (int i = 0; i < 3; ++i) {
+            int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+            for (int c = 0; c < 3; ++c) {
+                int m = (c + 1) % 3, l = (c + 2) % 3;
+                /* tmp0 = X_l dX_m/dxi_{i1},  tmp1 = X_l dX_m/dxi_{i2} */
+                for (int p = 0; p < n3; ++p) {
+                    tmp[p] = Xe[l * n3 + p] * dX[(m * 3 + i1) * n3 + p];
+                    tmp[n3 + p] = Xe[l * n3 + p] * dX[(m * 3 + i2) * n3 + p];
+                }
+                for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int ii = 0; ii < n; ++ii) {
+                    int p = node_index(n, ii, j, k);
+                    double v = dir_derivative(n, D, tmp, i2, ii, j, k)
+                             - dir_derivative(n, D, tmp + n3, i1, ii, j, k);
+                    Ja[(((size_t)e * 3 + i) * 3 + c) * n3 + p] = v;
+                }
+            }
+        }
+    }
+    free(tmp); free(dX);
+    return 0;
+}
+
+/* Build a mesh.  If X_in is given ([E][3][n3]) it replaces the box generator. */
+orc_mesh *orc_mesh_create(const orc_box *b, const double *X_in)
+{
+    if (b->N < 1 || b->N > 15 || b->ex < 1 || b->ey < 1 || b->ez < 1) return NULL;
+    orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
+    if (!m) return NULL;
+    m->box = *b;
+    m->n = b->N + 1;
+    m->n3 = m->n * m->n * m->n;
+    m->E = b->ex * b->ey * b->ez;
+    orc_lgl(b->N, m->xi, m->w);
+    orc_dmatrix(b->N, m->xi, m->D);
+    size_t en = (size_t)m->E * m->n3;
+    m->X = (double *)malloc(sizeof(double) * en * 3);
+    m->Ja = (double *)malloc(sizeof(double) * en * 9);
+    m->J = (double *)malloc(sizeof(double) * en);
+    if (!m->X || !m->Ja || !m->J) { free(m->X); free(m->Ja); free(m->J); free(m); return NULL; }
+    if (X_in) memcpy(m->X, X_in, sizeof(double) * en * 3);
+    else box_nodes(b, m->xi, m->X);
+    orc_metrics(m->E, b->N, m->D, m->X, m->Ja, m->J);
+    return m;
+}
+
+void orc_mesh_destroy(orc_mesh *m)
+{
+    if (!m) return;
+    free(m->X); free(m->Ja); free(m->J); free(m);
+}
+
+int orc_mesh_E(const orc_mesh *m) { return m->E; }
+void orc_mesh_arrays(const orc_mesh *m, double *xi, double *w, double *D, double *X, double *Ja, double *J)
+{
+    size_t en = (size_t)m->E * m->n3;
+    if (xi) memcpy(xi, m->xi, sizeof(double) * m->n);
+    if (w) memcpy(w, m->w, sizeof(double) * m->n);
+    if (D) memcpy(D, m->D, sizeof(double) * m->n * m->n);
+    if (X) memcpy(X, m->X, sizeof(double) * en * 3);
+    if (Ja) memcpy(Ja, m->Ja, sizeof(double) * en * 9);
+    if (J) memcpy(J, m->J, sizeof(double) * en);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Physics (Sec. 3.2)                                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int physics;       /* 0 Euler, 1 Navier-Stokes */
+    int surface_flux;  /* 0 Lax-Friedrichs, 1 Roe, 2 entropy-conservative (central) */
+    int volume_form;   /* 0 standard, 1 Chandrashekar split form */
+    double gamma, Re, Pr, cfl;
+} orc_cfg;
+
+/* rho, v, p from u; p = (gamma-1)(rho e - rho |v|^2 / 2). */
+static void primitives(const double *u, double g, double *rho, double v[3], double *p)
+{
+    *rho = u[0];
+    v[0] = u[1] / u[0];
+    v[1] = u[2] / u[0];
+    v[2] = u[3] / u[0];
+    *p = (g - 1.0) * (u[4] - 0.5 * u[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+}
+
+/* F_e . a for any vector a (the columns of the paper's F_e matrix, combined):
+ * [rho v.a, rho v1 v.a + p a1, rho v2 v.a + p a2, rho v3 v.a + p a3, rho H v.a],
+ * H = (rho e + p)/rho. */
+void orc_flux_euler(const double *u, const double *a, double g, double *f)
+{
+    double rho, v[3], p;
+    primitives(u, g, &rho, v, &p);
+    double va = v[0] * a[0] + v[1] * a[1] + v[2] * a[2];
+    f[0] = rho * va;
+    f[1] = u[1] * va + p * a[0];
+    f[2] = u[2] * va + p * a[1];
+    f[3] = u[3] * va + p * a[2];
+    f[4] = (u[4] + p) * va;
+}
+
+/* Lax-Friedrichs flux with unit normal nh:
+ *   F* = (F_L + F_R).nh / 2 - lambda (u_R - u_L) / 2,
+ *   lambda = max(|v_L.nh| + c_L, |v_R.nh| + c_R),  c = sqrt(gamma p / rho). */
+void orc_flux_lf(const double *uL, const double *uR, const double *nh, double g, double *f)
+{
+    double FL[NVAR], FR[NVAR], rL, vL[3], pL, rR, vR[3], pR;
+    orc_flux_euler(uL, nh, g, FL);
+    orc_flux_euler(uR, nh, g, FR);
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double sL = fabs(vL[0] * nh[0] + vL[1] * nh[1] + vL[2] * nh[2]) + sqrt(g * pL / rL);
+    double sR = fabs(vR[0] * nh[0] + vR[1] * nh[1] + vR[2] * nh[2]) + sqrt(g * pR / rR);
+    double lam = sL > sR ? sL : sR;
+    for (int v = 0; v < NVAR; ++v) f[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+/* Roe flux with unit normal nh (Roe 1981; no entropy fix):
+ *   F* = (F_L + F_R).nh / 2 - (1/2) sum_k |lambda_k| alpha_k r_k
+ * with sqrt(rho)-weighted averages v~, H~, c~^2 = (gamma-1)(H~ - |v~|^2/2),
+ * rho~ = sqrt(rho_L rho_R), eigenvalues v~.n - c~, v~.n (x3), v~.n + c~, and
+ * wave strengths from the jumps of rho, v, p:
+ *   alpha_1 = (dp - rho~ c~ dvn)/(2 c~^2)       r_1 = [1, v~ - c~ n, H~ - c~ v~n]
+ *   alpha_2 = drho - dp/c~^2                    r_2 = [1, v~, |v~|^2/2]
+ *   shear   = rho~ (dv - dvn n)                 r_s = [0, shear, v~.shear]
+ *   alpha_5 = (dp + rho~ c~ dvn)/(2 c~^2)       r_5 = [1, v~ + c~ n, H~ + c~ v~n]. */
+void orc_flux_roe(const double *uL, const double *uR, const double *nh, double g, double *f)
+{
+    orc_flux_roe_signed(uL, uR, nh, g, f, 0);
+}
+
+/* sign_mode = 0: the Roe flux above.  sign_mode = 1: f receives the wave sum
+ * sum_k lambda_k alpha_k r_k with SIGNED eigenvalues (used by the tests to
+ * check Roe's property that it equals F_R.n - F_L.n). */
+void orc_flux_roe_signed(const double *uL, const double *uR, const double *nh, double g, double *f, int sign_mode)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double HL = (uL[4] + pL) / rL, HR = (uR[4] + pR) / rR;
+    double sL = sqrt(rL), sR = sqrt(rR);
+    double vt[3];
+    for (int c = 0; c < 3; ++c) vt[c] = (sL * vL[c] + sR * vR[c]) / (sL + sR);
+    double Ht = (sL * HL + sR * HR) / (sL + sR);
+    double q2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+    double ct = sqrt((g - 1.0) * (Ht - 0.5 * q2));
+    double rt = sL * sR;
+    double vnt = vt[0] * nh[0] + vt[1] * nh[1] + vt[2] * nh[2];
+    double drho = rR - rL, dp = pR - pL;
+    double dv[3] = {vR[0] - vL[0], vR[1] - vL[1], vR[2] - vL[2]};
+    double dvn = dv[0] * nh[0] + dv[1] * nh[1] + dv[2] * nh[2];
+    double a1 = (dp - rt * ct * dvn) / (2.0 * ct * ct);
+    double a5 = (dp + rt * ct * dvn) / (2.0 * ct * ct);
+    double a2 = drho - dp / (ct * ct);
+    double sh[3];
+    for (int c = 0; c < 3; ++c) sh[c] = rt * (dv[c] - dvn * nh[c]);
+    double l1 = vnt - ct, l2 = vnt, l5 = vnt + ct;
+    if (!sign_mode) { l1 = fabs(l1); l2 = fabs(l2); l5 = fabs(l5); }
+    double W[NVAR];
+    W[0] = l1 * a1 + l2 * a2 + l5 * a5;
+    for (int c = 0; c < 3; ++c)
+        W[1 + c] = l1 * a1 * (vt[c] - ct * nh[c]) + l2 * (a2 * vt[c] + sh[c]) + l5 * a5 * (vt[c] + ct * nh[c]);
+    W[4] = l1 * a1 * (Ht - ct * vnt) + l2 * (a2 * 0.5 * q2 + vt[0] * sh[0] + vt[1] * sh[1] + vt[2] * sh[2])
+         + l5 * a5 * (Ht + ct * vnt);
+    if (sign_mode) { for (int v = 0; v < NVAR; ++v) f[v] = W[v]; return; }
+    double FL[NVAR], FR[NVAR];
+    orc_flux_euler(uL, nh, g, FL);
+    orc_flux_euler(uR, nh, g, FR);
+    for (int v = 0; v < NVAR; ++v) f[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * W[v];
+}
+
+/* Logarithmic mean (a-b)/(ln a - ln b) in the Ismail-Roe form:
+ * zeta = a/b, f = (zeta-1)/(zeta+1), u = f^2,
+ * F = 1 + u/3 + u^2/5 + u^3/7 for u < 1e-4, else ln(zeta)/(2f);
+ * result (a+b)/(2F). */
+double orc_logmean(double a, double b)
+{
+    double zeta = a / b;
+    double f = (zeta - 1.0) / (zeta + 1.0);
+    double u = f * f;
+    double F;
+    if (u < 1e-4) F = 1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0;
+    else F = log(zeta) / (2.0 * f);
+    return (a + b) / (2.0 * F);
+}
+
+/* Chandrashekar's entropy-conservative, kinetic-energy-preserving two-point
+ * flux (Sec. 3.5 lists it; formula from Chandrashekar 2013), dotted with an
+ * arbitrary vector a:
+ *   beta = rho/(2p); rho^ = ln-mean(rho), beta^ = ln-mean(beta);
+ *   {.} arithmetic mean; p~ = {rho}/(2{beta});
+ *   f_rho = rho^ {v}.a;  f_m = f_rho {v} + p~ a;
+ *   f_E = f_rho [ 1/(2(gamma-1) beta^) - {|v|^2}/2 ] + {v}.f_m. */
+void orc_flux_ec(const double *uL, const double *uR, const double *a, double g, double *f)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
+    double rho_ln = orc_logmean(rL, rR);
+    double beta_ln = orc_logmean(bL, bR);
+    double rho_av = 0.5 * (rL + rR), beta_av = 0.5 * (bL + bR);
+    double vav[3] = {0.5 * (vL[0] + vR[0]), 0.5 * (vL[1] + vR[1]), 0.5 * (vL[2] + vR[2])};
+    double v2av = 0.5 * ((vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]) + (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]));
+    double pt = rho_av / (2.0 * beta_av);
+    double van = vav[0] * a[0] + vav[1] * a[1] + vav[2] * a[2];
+    f[0] = rho_ln * van;
+    for (int c = 0; c < 3; ++c) f[1 + c] = f[0] * vav[c] + pt * a[c];
+    f[4] = f[0] * (1.0 / (2.0 * (g - 1.0) * beta_ln) - 0.5 * v2av)
+         + vav[0] * f[1] + vav[1] * f[2] + vav[2] * f[3];
+}
+
+/* Entropy variables w = dS/du for S = -rho s, s = ln p - gamma ln rho
+ * (Sec. 4.4, Eq. shock:entropy):
+ *   w = [gamma - s - (gamma-1) rho |v|^2/(2p), (gamma-1) rho v/p, -(gamma-1) rho/p]. */
+void orc_entropy_vars(const double *u, double g, double *w)
+{
+    double rho, v[3], p;
+    primitives(u, g, &rho, v, &p);
+    double s = log(p) - g * log(rho);
+    double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    w[0] = g - s - (g - 1.0) * rho * v2 / (2.0 * p);
+    w[1] = (g - 1.0) * rho * v[0] / p;
+    w[2] = (g - 1.0) * rho * v[1] / p;
+    w[3] = (g - 1.0) * rho * v[2] / p;
+    w[4] = -(g - 1.0) * rho / p;
+}
+
+/* Gradient variables q = (v1, v2, v3, T), T = p/rho (gas constant 1). */
+static void grad_vars(const double *u, double g, double *q)
+{
+    double rho, v[3], p;
+    primitives(u, g, &rho, v, &p);
+    q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = p / rho;
+}
+
+/* Viscous flux F_v . a (Sec. 3.2, Eq. viscousfluxes) from q = (v, T) and
+ * G[v][c] = d q_v / d x_c:
+ *   tau = mu (grad v + grad v^T) - (2/3) mu I div v,
+ *   row 5 = sum_j v_j tau_{cj} + kappa dT/dx_c. */
+void orc_flux_visc(const double *q, const double *G, double mu, double kappa, const double *a, double *f)
+{
+    double div = G[0 * 3 + 0] + G[1 * 3 + 1] + G[2 * 3 + 2];
+    double tau[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            tau[i][j] = mu * (G[i * 3 + j] + G[j * 3 + i]) - (i == j ? (2.0 / 3.0) * mu * div : 0.0);
+    f[0] = 0.0;
+    for (int i = 0; i < 3; ++i) f[1 + i] = tau[i][0] * a[0] + tau[i][1] * a[1] + tau[i][2] * a[2];
+    double fe = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double col = q[0] * tau[0][c] + q[1] * tau[1][c] + q[2] * tau[2][c] + kappa * G[3 * 3 + c];
+        fe += col * a[c];
+    }
+    f[4] = fe;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Residual (Sec. 3.3, Eq. NS4/NS5 in strong form on GL nodes)              */
+/* ------------------------------------------------------------------------ */
+
+static double visc_mu(const orc_cfg *cfg) { return 1.0 / cfg->Re; }
+static double visc_kappa(const orc_cfg *cfg)
+{
+    /* kappa = mu c_p / Pr with c_p = gamma/(gamma-1) for gas constant 1 */
+    return visc_mu(cfg) * cfg->gamma / ((cfg->gamma - 1.0) * cfg->Pr);
+}
+
+/* Index of the node of an element with index m along direction d and the
+ * other two indices taken from (i,j,k). */
+static int node_along(int n, int d, int m, int i, int j, int k)
+{
+    if (d == 0) return node_index(n, m, j, k);
+    if (d == 1) return node_index(n, i, m, k);
+    return node_index(n, i, j, m);
+}
+
+/* The node of the neighbour that coincides with face node p of element e on
+ * face (d, side): same tangential indices, index along d at the opposite end. */
+static int matching_node(int n, int d, int side, int i, int j, int k)
+{
+    int m = (side > 0) ? 0 : n - 1;
+    return node_along(n, d, m, i, j, k);
+}
+
+/* BR1 gradients of q = (v, T) (Bassi & Rebay 1997; Sec. 3.3 lists BR1):
+ *   J grad q_c = sum_d D_d (Ja^d_c q) + sum_faces (1/w_end) (q* - q_in) (s n)_c,
+ *   q* = (q_in + q_out)/2, (s n) = outward scaled normal = +-Ja^d at the node.
+ * grad[e][v][c][node]. */
+static void br1_gradients(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *grad)
+{
+    int n = m->n, n3 = m->n3, E = m->E, N = n - 1;
+    double g = cfg->gamma;
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < E; ++e) {
+        double *q = (double *)malloc(sizeof(double) * NGRAD * n3);
+        double *f = (double *)malloc(sizeof(double) * 3 * n3);   /* Ja^d_c q_v for d = 0..2 */
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], qp[NGRAD];
+            for (int v = 0; v < NVAR; ++v) up[v] = u[((size_t)e * NVAR + v) * n3 + p];
+            grad_vars(up, g, qp);
+            for (int v = 0; v < NGRAD; ++v) q[v * n3 + p] = qp[v];
+        }
+        for (int v = 0; v < NGRAD; ++v)
+        for (int c = 0; c < 3; ++c) {
+            for (int d = 0; d < 3; ++d)
+                for (int p = 0; p < n3; ++p)
+                    f[d * n3 + p] = m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p] * q[v * n3 + p];
+            for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+                int p = node_index(n, i, j, k);
+                double acc = 0.0;
+                for (int d = 0; d < 3; ++d) acc += dir_derivative(n, m->D, f + d * n3, d, i, j, k);
+                grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p] = acc;
+            }
+        }
+        /* surface lifting */
+        int ijk[3];
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            ijk[0] = i; ijk[1] = j; ijk[2] = k;
+            int p = node_index(n, i, j, k);
+            for (int d = 0; d < 3; ++d)
+            for (int side = -1; side <= 1; side += 2) {
+                int at = (side > 0) ? N : 0;
+                if (ijk[d] != at) continue;
+                int nb = neighbour(&m->box, e, d, side);
+                int pn = matching_node(n, d, side, i, j, k);
+                double un[NVAR], qn[NGRAD];
+                for (int v = 0; v < NVAR; ++v) un[v] = u[((size_t)nb * NVAR + v) * n3 + pn];
+                grad_vars(un, g, qn);
+                for (int v = 0; v < NGRAD; ++v) {
+                    double jump = 0.5 * (qn[v] + q[v * n3 + p]) - q[v * n3 + p];
+                    for (int c = 0; c < 3; ++c) {
+                        double sn = side * m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p];
+                        grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p] += jump * sn / m->w[at];
+                    }
+                }
+            }
+        }
+        for (int v = 0; v < NGRAD; ++v)
+            for (int c = 0; c < 3; ++c)
+                for (int p = 0; p < n3; ++p)
+                    grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p] /= m->J[(size_t)e * n3 + p];
+        free(q); free(f);
+    }
+}
+
+/* Inviscid numerical flux times the face scale: s F*(u_in, u_out; n^) with
+ * Sn = s n^ the outward scaled normal. */
+static void surface_flux(int kind, const double *uin, const double *uout, const double *Sn, double g, double *f)
+{
+    if (kind == 2) { orc_flux_ec(uin, uout, Sn, g, f); return; }
+    double s = sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
+    double nh[3] = {Sn[0] / s, Sn[1] / s, Sn[2] / s};
+    if (kind == 0) orc_flux_lf(uin, uout, nh, g, f);
+    else orc_flux_roe(uin, uout, nh, g, f);
+    for (int v = 0; v < NVAR; ++v) f[v] *= s;
+}
+
+/* du/dt = -(V + S)/J per element, with
+ *   standard form  V = sum_d D_d F~^d,  F~^d = sum_c Ja^d_c (F_e - F_v)_c
+ *   split form     V = sum_d [ 2 sum_m D_im F#(u_i, u_m).(Ja^d_i + Ja^d_m)/2 ] - sum_d D_d F~_v^d
+ *   surface        S = (1/w_end) [ F^*(in,out; Sn) - F_v^*.Sn - (F_e - F_v)(in).Sn ]
+ * on each face node, F_v^* = (F_v(in) + F_v(out))/2 (BR1). */
+int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *dudt)
+{
+    int n = m->n, n3 = m->n3, E = m->E, N = n - 1;
+    double g = cfg->gamma;
+    int ns = (cfg->physics == 1);
+    double mu = ns ? visc_mu(cfg) : 0.0, kappa = ns ? visc_kappa(cfg) : 0.0;
+    double *grad = NULL;
+    if (ns) {
+        grad = (double *)malloc(sizeof(double) * (size_t)E * NGRAD * 3 * n3);
+        if (!grad) return -1;
+        br1_gradients(m, cfg, u, grad);
+    }
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < E; ++e) {
+        double *Ft = (double *)malloc(sizeof(double) * 3 * NVAR * n3);   /* total contravariant flux */
+        double *Fv = (double *)malloc(sizeof(double) * 3 * NVAR * n3);   /* viscous contravariant flux */
+        double *R = (double *)calloc(NVAR * n3, sizeof(double));
+        /* contravariant fluxes at every node */
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], qp[NGRAD], G[12];
+            for (int v = 0; v < NVAR; ++v) up[v] = u[((size_t)e * NVAR + v) * n3 + p];
+            if (ns) {
+                grad_vars(up, g, qp);
+                for (int v = 0; v < NGRAD; ++v)
+                    for (int c = 0; c < 3; ++c) G[v * 3 + c] = grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p];
+            }
+            for (int d = 0; d < 3; ++d) {
+                double a[3], fe[NVAR], fv[NVAR] = {0, 0, 0, 0, 0};
+                for (int c = 0; c < 3; ++c) a[c] = m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p];
+                orc_flux_euler(up, a, g, fe);
+                if (ns) orc_flux_visc(qp, G, mu, kappa, a, fv);
+                for (int v = 0; v < NVAR; ++v) {
+                    Ft[(d * NVAR + v) * n3 + p] = fe[v] - fv[v];
+                    Fv[(d * NVAR + v) * n3 + p] = fv[v];
+                }
+            }
+        }
+        /* volume term */
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            int p = node_index(n, i, j, k);
+            int ijk[3] = {i, j, k};
+            for (int d = 0; d < 3; ++d) {
+                if (cfg->volume_form == 0) {
+                    for (int v = 0; v < NVAR; ++v)
+                        R[v * n3 + p] += dir_derivative(n, m->D, Ft + (d * NVAR + v) * n3, d, i, j, k);
+                } else {
+                    double ui[NVAR];
+                    for (int v = 0; v < NVAR; ++v) ui[v] = u[((size_t)e * NVAR + v) * n3 + p];
+                    for (int mm = 0; mm < n; ++mm) {
+                        int pm = node_along(n, d, mm, i, j, k);
+                        double um[NVAR], a[3], fs[NVAR];
+                        for (int v = 0; v < NVAR; ++v) um[v] = u[((size_t)e * NVAR + v) * n3 + pm];
+                        for (int c = 0; c < 3; ++c)
+                            a[c] = 0.5 * (m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p]
+                                        + m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + pm]);
+                        orc_flux_ec(ui, um, a, g, fs);
+                        double Dim = m->D[ijk[d] * n + mm];
+                        for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += 2.0 * Dim * fs[v];
+                    }
+                    if (ns)
+                        for (int v = 0; v < NVAR; ++v)
+                            R[v * n3 + p] -= dir_derivative(n, m->D, Fv + (d * NVAR + v) * n3, d, i, j, k);
+                }
+            }
+        }
+        /* surface term */
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            int p = node_index(n, i, j, k);
+            int ijk[3] = {i, j, k};
+            for (int d = 0; d < 3; ++d)
+            for (int side = -1; side <= 1; side += 2) {
+                int at = (side > 0) ? N : 0;
+                if (ijk[d] != at) continue;
+                int nb = neighbour(&m->box, e, d, side);
+                int pn = matching_node(n, d, side, i, j, k);
+                double uin[NVAR], uout[NVAR], Sn[3], fstar[NVAR];
+                for (int v = 0; v < NVAR; ++v) {
+                    uin[v] = u[((size_t)e * NVAR + v) * n3 + p];
+                    uout[v] = u[((size_t)nb * NVAR + v) * n3 + pn];
+                }
+                for (int c = 0; c < 3; ++c) Sn[c] = side * m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p];
+                surface_flux(cfg->surface_flux, uin, uout, Sn, g, fstar);
+                if (ns) {
+                    double qi[NGRAD], qo[NGRAD], Gi[12], Go[12], fvi[NVAR], fvo[NVAR];
+                    grad_vars(uin, g, qi);
+                    grad_vars(uout, g, qo);
+                    for (int v = 0; v < NGRAD; ++v)
+                        for (int c = 0; c < 3; ++c) {
+                            Gi[v * 3 + c] = grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p];
+                            Go[v * 3 + c] = grad[(((size_t)nb * NGRAD + v) * 3 + c) * n3 + pn];
+                        }
+                    orc_flux_visc(qi, Gi, mu, kappa, Sn, fvi);
+                    orc_flux_visc(qo, Go, mu, kappa, Sn, fvo);
+                    for (int v = 0; v < NVAR; ++v) fstar[v] -= 0.5 * (fvi[v] + fvo[v]);
+                }
+                for (int v = 0; v < NVAR; ++v) {
+                    /* own flux (F_e - F_v)(in).Sn = side * F~^d(in) */
+                    double own = side * Ft[(d * NVAR + v) * n3 + p];
+                    R[v * n3 + p] += (fstar[v] - own) / m->w[at];
+                }
+            }
+        }
+        for (int v = 0; v < NVAR; ++v)
+            for (int p = 0; p < n3; ++p)
+                dudt[((size_t)e * NVAR + v) * n3 + p] = -R[v * n3 + p] / m->J[(size_t)e * n3 + p];
+        free(Ft); free(Fv); free(R);
+    }
+    free(grad);
+    return 0;
+}
+
+/* BR1 gradients exposed for tests: grad[e][v][c][node]. */
+int orc_gradients(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *grad)
+{
+    br1_gradients(m, cfg, u, grad);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time step and low-storage RK3 (Sec. 3.7)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Williamson (1980) 3-stage low-storage RK coefficients. */
+static const double RK3_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+static const double RK3_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+static const double RK3_C[3] = {0.0, 1.0 / 3.0, 3.0 / 4.0};
+
+void orc_rk3_coefficients(double *A, double *B, double *C)
+{
+    for (int k = 0; k < 3; ++k) { A[k] = RK3_A[k]; B[k] = RK3_B[k]; C[k] = RK3_C[k]; }
+}
+
+/* One low-storage stage on a flat array: g <- A_k g + dt R; u <- u + B_k g.
+ * Stage 0 (A_0 = 0) does not read g. */
+void orc_lsrk3_stage(long long count, int k, double dt, double *u, double *g, const double *R)
+{
+    for (long long i = 0; i < count; ++i) {
+        double gi = (k == 0) ? dt * R[i] : RK3_A[k] * g[i] + dt * R[i];
+        g[i] = gi;
+        u[i] = u[i] + RK3_B[k] * gi;
+    }
+}
+
+/* Time step (no formula in the paper; the reading used by this library):
+ *   convective  dt_c = cfl * 2 / (n * max_nodes sum_d (|Ja^d.v| + c |Ja^d|)/J)
+ *   viscous     dt_v = 12 / (n^4 * max_nodes (mu/rho) sum_d (|Ja^d|/J)^2)
+ *               (= h^2/(nu n^4) on a straight box; Navier-Stokes only)
+ *   dt = min(dt_c, dt_v). */
+double orc_dt(const orc_mesh *m, const orc_cfg *cfg, const double *u)
+{
+    int n = m->n, n3 = m->n3, E = m->E;
+    double g = cfg->gamma;
+    double lam_c = 0.0, lam_v = 0.0;
+    double mu = (cfg->physics == 1) ? visc_mu(cfg) : 0.0;
+    for (int e = 0; e < E; ++e)
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], rho, v[3], pr;
+            for (int vv = 0; vv < NVAR; ++vv) up[vv] = u[((size_t)e * NVAR + vv) * n3 + p];
+            primitives(up, g, &rho, v, &pr);
+            double c = sqrt(g * pr / rho);
+            double Jp = m->J[(size_t)e * n3 + p];
+            double sc = 0.0, sv = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double *a0 = m->Ja + (((size_t)e * 3 + d) * 3) * n3 + p;
+                double a[3] = {a0[0], a0[n3], a0[2 * n3]};
+                double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                sc += (fabs(a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) + c * an) / Jp;
+                sv += (an / Jp) * (an / Jp);
+            }
+            if (sc > lam_c) lam_c = sc;
+            if (mu * sv / rho > lam_v) lam_v = mu * sv / rho;
+        }
+    double dt = cfg->cfl * 2.0 / (n * lam_c);
+    if (lam_v > 0.0) {
+        double dtv = 12.0 / ((double)n * n * n * n * lam_v);
+        if (dtv < dt) dt = dtv;
+    }
+    return dt;
+}
+
+/* One Williamson RK3 step.  dt_in > 0 is used as given; dt_in <= 0 computes dt
+ * from the state at the start of the step.  Returns the dt used through *dt_used. */
+int orc_rk3_step(const orc_mesh *m, const orc_cfg *cfg, double *u, double *g, double dt_in, double *dt_used)
+{
+    long long count = (long long)m->E * NVAR * m->n3;
+    double dt = dt_in > 0.0 ? dt_in : orc_dt(m, cfg, u);
+    double *R = (double *)malloc(sizeof(double) * count);
+    if (!R) return -1;
+    for (int k = 0; k < 3; ++k) {
+        orc_residual(m, cfg, u, R);
+        orc_lsrk3_stage(count, k, dt, u, g, R);
+    }
+    free(R);
+    if (dt_used) *dt_used = dt;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial conditions                                                        */
+/* ------------------------------------------------------------------------ */
+
+static void conservative(double rho, const double v[3], double p, double g, double *u)
+{
+    u[0] = rho;
+    u[1] = rho * v[0];
+    u[2] = rho * v[1];
+    u[3] = rho * v[2];
+    u[4] = p / (g - 1.0) + 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+/* Isentropic vortex (Shu's form) in the x-y plane, advected at u_inf = Ma sqrt(gamma)
+ * along x, free stream rho = p = 1:
+ *   r^2 = dx^2 + dy^2 (nearest periodic image of the centre moved to xc + u_inf t),
+ *   du = -beta/(2pi) e^{(1-r^2)/2} dy,  dv = beta/(2pi) e^{(1-r^2)/2} dx,
+ *   T = 1 - (gamma-1) beta^2/(8 gamma pi^2) e^{1-r^2},  rho = T^{1/(gamma-1)},  p = rho^gamma.
+ * An exact solution of the Euler equations; at time t it is the state at t=0
+ * translated by u_inf t. */
+void orc_ic_vortex(const orc_mesh *m, double g, double Ma, double beta, double xc, double yc, double t, double *u)
+{
+    int n3 = m->n3, E = m->E;
+    double uinf = Ma * sqrt(g);
+    double Lx = m->box.hi[0] - m->box.lo[0], Ly = m->box.hi[1] - m->box.lo[1];
+    double cx = xc + uinf * t;
+    for (int e = 0; e < E; ++e)
+        for (int p = 0; p < n3; ++p) {
+            double x = m->X[((size_t)e * 3 + 0) * n3 + p];
+            double y = m->X[((size_t)e * 3 + 1) * n3 + p];
+            double dx = x - cx, dy = y - yc;
+            dx -= Lx * floor(dx / Lx + 0.5);
+            dy -= Ly * floor(dy / Ly + 0.5);
+            double r2 = dx * dx + dy * dy;
+            double ex = exp(0.5 * (1.0 - r2));
+            double v[3] = {uinf - beta / (2.0 * M_PI) * ex * dy, beta / (2.0 * M_PI) * ex * dx, 0.0};
+            double T = 1.0 - (g - 1.0) * beta * beta / (8.0 * g * M_PI * M_PI) * ex * ex;
+            double rho = pow(T, 1.0 / (g - 1.0));
+            double pr = pow(rho, g);
+            double up[NVAR];
+            conservative(rho, v, pr, g, up);
+            for (int vv = 0; vv < NVAR; ++vv) u[((size_t)e * NVAR + vv) * n3 + p] = up[vv];
+        }
+}
+
+/* Taylor-Green vortex, rho0 = V0 = L = 1, p0 = 1/(gamma Ma^2):
+ *   v1 = sin x cos y cos z,  v2 = -cos x sin y cos z,  v3 = 0,
+ *   p = p0 + (cos 2x + cos 2y)(cos 2z + 2)/16,  rho = p/p0. */
+void orc_ic_tgv(const orc_mesh *m, double g, double Ma, double *u)
+{
+    int n3 = m->n3, E = m->E;
+    double p0 = 1.0 / (g * Ma * Ma);
+    for (int e = 0; e < E; ++e)
+        for (int p = 0; p < n3; ++p) {
+            double x = m->X[((size_t)e * 3 + 0) * n3 + p];
+            double y = m->X[((size_t)e * 3 + 1) * n3 + p];
+            double z = m->X[((size_t)e * 3 + 2) * n3 + p];
+            double v[3] = {sin(x) * cos(y) * cos(z), -cos(x) * sin(y) * cos(z), 0.0};
+            double pr = p0 + (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0) / 16.0;
+            double rho = pr / p0;
+            double up[NVAR];
+            conservative(rho, v, pr, g, up);
+            for (int vv = 0; vv < NVAR; ++vv) u[((size_t)e * NVAR + vv) * n3 + p] = up[vv];
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Quadrature integrals sum_e sum_ijk J w_i w_j w_k f_v, f = u or du/dt (5 values),
+ * plus the entropy rate sum J w w w (w(u) . dudt) in out[5] when dudt is given,
+ * and sum |J w w w w_v dudt_v| in out[6] (the scale for relative checks).
+ * Sequential, fixed order. */
+void orc_integrals(const orc_mesh *m, double g, const double *u, const double *dudt, double *out)
+{
+    int n = m->n, n3 = m->n3, E = m->E;
+    for (int v = 0; v < 7; ++v) out[v] = 0.0;
+    for (int e = 0; e < E; ++e)
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            int p = node_index(n, i, j, k);
+            double wq = m->J[(size_t)e * n3 + p] * m->w[i] * m->w[j] * m->w[k];
+            const double *f = dudt ? dudt : u;
+            for (int v = 0; v < NVAR; ++v) out[v] += wq * f[((size_t)e * NVAR + v) * n3 + p];
+            if (dudt) {
+                double up[NVAR], wv[NVAR];
+                for (int v = 0; v < NVAR; ++v) up[v] = u[((size_t)e * NVAR + v) * n3 + p];
+                orc_entropy_vars(up, g, wv);
+                for (int v = 0; v < NVAR; ++v) {
+                    double t = wq * wv[v] * dudt[((size_t)e * NVAR + v) * n3 + p];
+                    out[5] += t;
+                    out[6] += fabs(t);
+                }
+            }
+        }
+}

@@ -1,0 +1,615 @@
+"""Pins of the FP64 CPU oracle against what the mathematics fixes.
+
+Each oracle function is checked against something other than itself: closed
+forms, exact results of the discretisation (polynomial exactness, summation by
+parts, discrete metric identities, Roe's property, Tadmor's entropy condition),
+conservation and entropy invariants of the semi-discrete scheme, and
+convergence to exact solutions of the PDE.  Sections cited are those of the
+HORSES3D paper (arXiv 2206.09733).
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+G = 1.4
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def _random_state(rng, shape_tail=(), gamma=G, vmax=0.8, rho=(0.5, 2.0), p=(0.5, 2.0)):
+    r = rng.uniform(*rho, size=shape_tail)
+    v = rng.uniform(-vmax, vmax, size=(3,) + shape_tail)
+    pr = rng.uniform(*p, size=shape_tail)
+    u = np.stack([r, r * v[0], r * v[1], r * v[2], pr / (gamma - 1) + 0.5 * r * (v ** 2).sum(0)])
+    return u
+
+
+# --------------------------------------------------------------------------- 1-D operators (Sec. 3.3)
+
+def _golden_lgl():
+    rows = {}
+    with open(os.path.join(GOLD, "lgl_closed_forms.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            N, xs, ws = (s.strip() for s in line.split("|"))
+            ev = lambda s: float(eval(s, {"sqrt": np.sqrt}))  # noqa: E731  (closed-form expressions)
+            rows[int(N)] = ([ev(t) for t in xs.split(",")], [ev(t) for t in ws.split(",")])
+    return rows
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_lgl_closed_forms(N):
+    xs, ws = _golden_lgl()[N]
+    x, w = O.lgl(N)
+    assert np.allclose(x, xs, atol=1e-15, rtol=0)
+    assert np.allclose(w, ws, atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_lgl_quadrature_exactness(N):
+    x, w = O.lgl(N)
+    assert abs(w.sum() - 2.0) < 1e-14
+    assert np.allclose(x, -x[::-1], atol=1e-15)
+    for deg in range(0, 2 * N):          # GL is exact through degree 2N-1
+        exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
+        assert abs(np.dot(w, x ** deg) - exact) < 2e-14
+    # and not exact at degree 2N (so the rule really is Lobatto, not Gauss)
+    assert abs(np.dot(w, x ** (2 * N)) - 2.0 / (2 * N + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_dmatrix_exact_and_sbp(N):
+    x, w = O.lgl(N)
+    D = O.dmatrix(N)
+    for m in range(0, N + 1):
+        exact = m * x ** (m - 1) if m else np.zeros_like(x)
+        assert np.abs(D @ x ** m - exact).max() < 1e-12 * max(1, N ** 2)
+    assert np.abs(D.sum(1)).max() < 1e-12
+    M = np.diag(w)
+    B = np.zeros((N + 1, N + 1))
+    B[0, 0], B[-1, -1] = -1.0, 1.0
+    assert np.abs(M @ D + (M @ D).T - B).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- mesh and metric terms (Sec. 3.3)
+
+def test_straight_box_geometry_closed_form():
+    m = O.Mesh(3, 2, 4, 3, lo=(0.0, -1.0, 2.0), hi=(6.0, 1.0, 10.0))
+    h = np.array([2.0, 1.0, 2.0])
+    n = 4
+    for e in range(m.E):
+        for d in range(3):
+            for c in range(3):
+                expect = np.prod(h[[k for k in range(3) if k != d]] / 2) if c == d else 0.0
+                assert np.abs(m.Ja[e, d, c] - expect).max() < 1e-14 * 10 * np.abs(m.X).max()
+    assert np.abs(m.J - np.prod(h / 2)).max() < 1e-13
+    # node coordinates: element (a,b,c) spans [lo + a h, lo + (a+1) h]
+    xi = m.xi
+    for e in (0, 5, m.E - 1):
+        a, b, c = e % 3, (e // 3) % 2, e // 6
+        assert np.allclose(m.X[e, 0, 0, 0, :], 0.0 + h[0] * (a + (xi + 1) / 2))
+        assert np.allclose(m.X[e, 1, 0, :, 0], -1.0 + h[1] * (b + (xi + 1) / 2))
+        assert np.allclose(m.X[e, 2, :, 0, 0], 2.0 + h[2] * (c + (xi + 1) / 2))
+    assert n == m.n
+
+
+def _face_nodes(m, arr, e, d, side):
+    idx = [slice(None)] * 3
+    idx[2 - d] = -1 if side > 0 else 0    # arrays are [k, j, i]
+    return arr[e][(Ellipsis,) + tuple(idx)]
+
+
+def test_curved_mesh_watertight_and_boundary_fixed():
+    L = 2 * np.pi
+    m = O.Mesh(3, 3, 3, 4, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=0.1)
+    for e in range(m.E):
+        for d in range(3):
+            nb = m.neighbour(e, d, +1)
+            a = _face_nodes(m, m.X, e, d, +1)
+            b = _face_nodes(m, m.X, nb, d, -1).copy()
+            wrap = (e // [1, 3, 9][d]) % 3 == 2
+            if wrap:
+                b[d] += L
+            assert np.abs(a - b).max() < 1e-12
+    # displacement vanishes on the box boundary (sin(+-pi) = 0)
+    assert np.abs(m.X[:, 0].min() + np.pi) < 1e-14 and np.abs(m.X[:, 0].max() - np.pi) < 1e-14
+    assert m.J.min() > 0
+
+
+@pytest.mark.parametrize("N", [3, 4, 6])
+def test_metric_identity_and_face_normals(N):
+    m = O.Mesh(2, 3, 2, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=0.1)
+    D = m.D
+    scale = np.abs(m.Ja).max()
+    for e in range(m.E):
+        for c in range(3):
+            s = (np.einsum("im,kjm->kji", D, m.Ja[e, 0, c]) + np.einsum("jm,kmi->kji", D, m.Ja[e, 1, c])
+                 + np.einsum("km,mji->kji", D, m.Ja[e, 2, c]))
+            assert np.abs(s).max() < 1e-13 * scale * N ** 2
+        # the scaled normal Ja^d on a shared face is the same from both elements
+        for d in range(3):
+            nb = m.neighbour(e, d, +1)
+            a = _face_nodes(m, m.Ja[:, d], e, d, +1)
+            b = _face_nodes(m, m.Ja[:, d], nb, d, -1)
+            assert np.abs(a - b).max() < 1e-12 * scale
+
+
+def test_metrics_match_analytic_cofactors_for_polynomial_map():
+    """A quadratic map is represented exactly at N >= 3, and so are the
+    products X_l dX_m of the curl form; the discrete Ja must then equal the
+    analytic cofactor matrix J dxi/dx and J the analytic determinant."""
+    N = 4
+    n = N + 1
+    xi, _ = O.lgl(N)
+    k, j, i = np.meshgrid(xi, xi, xi, indexing="ij")
+    r, s, t = i, j, k
+
+    def Xmap(r, s, t):
+        return np.stack([r + 0.10 * s * s + 0.05 * r * t,
+                         s + 0.08 * t * r - 0.03 * r * r,
+                         t + 0.06 * r * s + 0.04 * s * s])
+
+    def jac(r, s, t):   # dX_c / dxi_d as A[c][d]
+        return np.array([[1 + 0.05 * t, 0.20 * s, 0.05 * r],
+                         [0.08 * t - 0.06 * r, np.ones_like(r), 0.08 * r],
+                         [0.06 * s, 0.06 * r + 0.08 * s, np.ones_like(r)]])
+
+    X = Xmap(r, s, t)[None]
+    m = O.Mesh(1, 1, 1, N, X=X)
+    A = jac(r, s, t)
+    A = np.moveaxis(A, (0, 1), (-2, -1))            # [k,j,i,c,d]
+    detA = np.linalg.det(A)
+    cof = np.linalg.inv(A) * detA[..., None, None]  # [k,j,i,d,c] = J dxi_d/dx_c
+    assert np.abs(m.J[0] - detA).max() < 1e-13
+    for d in range(3):
+        for c in range(3):
+            assert np.abs(m.Ja[0, d, c] - cof[..., d, c]).max() < 1e-13
+    assert n == m.n
+
+
+# --------------------------------------------------------------------------- point fluxes (Secs. 3.2, 3.3, 3.5)
+
+def _fd_jacobian(f, u, eps=1e-7):
+    J = np.zeros((5, 5))
+    for k in range(5):
+        du = np.zeros(5)
+        du[k] = eps * max(1.0, abs(u[k]))
+        J[:, k] = (f(u + du) - f(u - du)) / (2 * du[k])
+    return J
+
+
+def test_euler_flux_eigenstructure():
+    """The flux Jacobian dF.n/du has eigenvalues v.n - c, v.n (x3), v.n + c."""
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        u = _random_state(rng)
+        nh = rng.standard_normal(3)
+        nh /= np.linalg.norm(nh)
+        A = _fd_jacobian(lambda q: O.flux_euler(q, nh), u)
+        ev = np.sort(np.linalg.eigvals(A).real)
+        rho, v = u[0], u[1:4] / u[0]
+        p = (G - 1) * (u[4] - 0.5 * rho * v @ v)
+        c = np.sqrt(G * p / rho)
+        vn = v @ nh
+        assert np.allclose(ev, np.sort([vn - c, vn, vn, vn, vn + c]), atol=1e-6)
+
+
+def test_euler_flux_rotation_and_homogeneity():
+    rng = np.random.default_rng(2)
+    u = _random_state(rng)
+    a = rng.standard_normal(3)
+    # homogeneous of degree one in u and linear in a
+    assert np.allclose(O.flux_euler(2.5 * u, a), 2.5 * O.flux_euler(u, a), rtol=1e-14)
+    b = rng.standard_normal(3)
+    assert np.allclose(O.flux_euler(u, a + b), O.flux_euler(u, a) + O.flux_euler(u, b), rtol=1e-13)
+    # rotational invariance: F(u).n = T^-1 F(T u).(R n)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    T = np.eye(5)
+    T[1:4, 1:4] = Q
+    lhs = O.flux_euler(u, a)
+    rhs = np.linalg.solve(T, O.flux_euler(T @ u, Q @ a))
+    assert np.allclose(lhs, rhs, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["lf", "roe", "ec"])
+def test_surface_flux_consistency_and_symmetry(kind):
+    rng = np.random.default_rng(3)
+    f = {"lf": O.flux_lf, "roe": O.flux_roe, "ec": O.flux_ec}[kind]
+    for _ in range(20):
+        uL, uR = _random_state(rng), _random_state(rng)
+        nh = rng.standard_normal(3)
+        nh /= np.linalg.norm(nh)
+        assert np.allclose(f(uL, uL, nh), O.flux_euler(uL, nh), rtol=1e-13, atol=1e-13)
+        assert np.allclose(f(uL, uR, nh), -f(uR, uL, -nh), rtol=1e-13, atol=1e-13)
+
+
+def _psi(u, a):
+    """Entropy-flux potential for S = -rho s: psi = (gamma - 1) rho v.a."""
+    return (G - 1) * u[1:4] @ a
+
+
+def test_ec_flux_tadmor_identity():
+    """Tadmor's condition [[w]].F# = [[psi]]; the survey's scratch check found
+    that only the {|v|^2}/2 kinetic term satisfies it, to round-off."""
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        uL, uR = _random_state(rng), _random_state(rng)
+        a = rng.standard_normal(3)
+        dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+        lhs = dw @ O.flux_ec(uL, uR, a)
+        rhs = _psi(uR, a) - _psi(uL, a)
+        assert abs(lhs - rhs) < 1e-12 * (1 + abs(rhs))
+    # near-equal states exercise the series branch of the logarithmic mean
+    uL = _random_state(rng)
+    uR = uL * (1 + 1e-5 * rng.standard_normal(5))
+    dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+    a = np.array([0.3, -0.2, 0.9])
+    assert abs(dw @ O.flux_ec(uL, uR, a) - (_psi(uR, a) - _psi(uL, a))) < 1e-15
+
+
+def test_entropy_variables_are_gradient_of_entropy():
+    rng = np.random.default_rng(5)
+    u = _random_state(rng)
+
+    def S(q):
+        rho, v = q[0], q[1:4] / q[0]
+        p = (G - 1) * (q[4] - 0.5 * rho * v @ v)
+        return -rho * (np.log(p) - G * np.log(rho))
+
+    grad = np.array([(S(u + e) - S(u - e)) / 2e-6 for e in np.eye(5) * 1e-6])
+    assert np.allclose(O.entropy_vars(u), grad, rtol=1e-7, atol=1e-8)
+
+
+@pytest.mark.parametrize("kind", ["lf", "roe"])
+def test_dissipative_fluxes_produce_entropy(kind):
+    """[[w]].F* <= [[psi]] (entropy stable) for LF always; for Roe on these
+    subsonic, expansion-free random pairs it holds too (no entropy fix)."""
+    rng = np.random.default_rng(6)
+    f = {"lf": O.flux_lf, "roe": O.flux_roe}[kind]
+    worst = -np.inf
+    for _ in range(200):
+        uL = _random_state(rng)
+        uR = uL * (1 + 0.05 * rng.standard_normal(5))
+        nh = rng.standard_normal(3)
+        nh /= np.linalg.norm(nh)
+        dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+        worst = max(worst, dw @ f(uL, uR, nh) - (_psi(uR, nh) - _psi(uL, nh)))
+    assert worst <= 1e-14
+
+
+def test_roe_property_and_supersonic_upwinding():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        uL, uR = _random_state(rng), _random_state(rng)
+        nh = rng.standard_normal(3)
+        nh /= np.linalg.norm(nh)
+        # Roe's property: sum_k lambda_k alpha_k r_k = F(u_R).n - F(u_L).n
+        W = O.roe_wave_sum(uL, uR, nh)
+        assert np.allclose(W, O.flux_euler(uR, nh) - O.flux_euler(uL, nh), rtol=1e-12, atol=1e-12)
+    # all waves moving in +n (v.n > c on both sides): the Roe flux is F(u_L).n
+    nh = np.array([0.6, 0.0, 0.8])
+    for sgn in (+1, -1):
+        def sup(rho, p, vt):
+            c = np.sqrt(G * p / rho)
+            v = sgn * 3.0 * c * nh + vt
+            return np.array([rho, rho * v[0], rho * v[1], rho * v[2], p / (G - 1) + 0.5 * rho * v @ v])
+        uL = sup(1.0, 1.0, np.array([0.0, 0.3, 0.0]))
+        uR = sup(1.3, 0.7, np.array([0.4, -0.2, -0.3]))
+        expect = O.flux_euler(uL if sgn > 0 else uR, nh)
+        assert np.allclose(O.flux_roe(uL, uR, nh), expect, rtol=1e-13, atol=1e-13)
+
+
+def test_lf_uses_two_sided_max_wave_speed():
+    """For a pure density jump at rest the LF flux is -lambda [[rho]]/2 with
+    lambda = max(c_L, c_R)."""
+    uL = np.array([1.0, 0, 0, 0, 1.0 / (G - 1)])
+    uR = np.array([0.5, 0, 0, 0, 1.0 / (G - 1)])
+    nh = np.array([1.0, 0, 0])
+    f = O.flux_lf(uL, uR, nh)
+    lam = max(np.sqrt(G / 1.0), np.sqrt(G / 0.5))
+    assert abs(f[0] - (-0.5 * lam * (0.5 - 1.0))) < 1e-15
+    assert abs(f[1] - 1.0) < 1e-15
+
+
+def test_logmean():
+    for a, b in [(1.0, 2.0), (3.0, 0.1), (1.0, 1.0 + 1e-3), (2.0, 2.0)]:
+        ref = a if a == b else (a - b) / (np.log(a) - np.log(b))
+        assert abs(O.logmean(a, b) - ref) < 1e-14 * ref * (1 if abs(a - b) > 0.1 else 1e3)
+    # continuous across the branch switch u = 1e-4
+    for b in np.linspace(1.0195, 1.0215, 41):
+        ref = (1.0 - b) / (np.log(1.0) - np.log(b))
+        assert abs(O.logmean(1.0, b) - ref) < 1e-12
+
+
+def test_viscous_flux_special_flows():
+    mu, kappa = 0.3, 0.7
+    q = np.array([0.2, -0.1, 0.4, 1.3])
+    a = np.array([0.3, -1.1, 0.5])
+    # rigid rotation (antisymmetric velocity gradient) and uniform dilatation
+    # (Stokes' hypothesis) carry no viscous stress
+    W = np.array([[0, 0.4, -0.2], [-0.4, 0, 0.7], [0.2, -0.7, 0]])
+    for Gv in (W, 0.8 * np.eye(3)):
+        Gm = np.zeros((4, 3))
+        Gm[:3] = Gv
+        assert np.abs(O.flux_visc(q, Gm, mu, kappa, a)).max() < 1e-15
+    # simple shear u = s y: tau_xy = tau_yx = mu s
+    s = 1.7
+    Gm = np.zeros((4, 3))
+    Gm[0, 1] = s
+    f = O.flux_visc(q, Gm, mu, kappa, np.array([0, 1.0, 0]))
+    assert np.allclose(f[:4], [0, mu * s, 0, 0], atol=1e-15)
+    assert abs(f[4] - q[0] * mu * s) < 1e-15
+    # pure heat flux
+    Gm = np.zeros((4, 3))
+    Gm[3] = [0.5, -0.25, 2.0]
+    assert abs(O.flux_visc(q, Gm, mu, kappa, a)[4] - kappa * Gm[3] @ a) < 1e-15
+
+
+# --------------------------------------------------------------------------- semi-discrete invariants (Secs. 3.3, 3.5)
+
+COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec") for v in ("standard", "ec")]
+
+
+@pytest.fixture(scope="module")
+def curved():
+    return O.Mesh(3, 2, 3, 3, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=0.1)
+
+
+@pytest.mark.parametrize("combo", COMBOS)
+def test_free_stream_preservation(curved, combo):
+    m = curved
+    u = np.zeros(m.shape)
+    st = np.array([1.2, 0.36, -0.24, 0.12, 2.6])
+    u[:] = st[None, :, None, None, None]
+    r = m.residual(O.Cfg(*combo, Re=50.0), u)
+    assert np.abs(r).max() < 1e-13 * np.abs(st).max() * 10
+
+
+@pytest.mark.parametrize("combo", COMBOS)
+def test_discrete_conservation(curved, combo):
+    m = curved
+    rng = np.random.default_rng(8)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    r = m.residual(O.Cfg(*combo, Re=50.0), u)
+    tot = m.integrals(G, u, r)[:5]
+    mag = m.integrals(G, u, np.abs(r))[:5]
+    assert np.abs(tot / mag).max() < 1e-13
+
+
+def test_entropy_conservation_of_split_form(curved):
+    m = curved
+    rng = np.random.default_rng(9)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    ec = m.integrals(G, u, m.residual(O.Cfg("euler", "ec", "ec"), u))
+    assert abs(ec[5]) < 1e-13 * ec[6]
+    # with a dissipative surface flux entropy decreases (S = -rho s is the
+    # mathematical entropy), and the standard form is not entropy-conservative
+    roe = m.integrals(G, u, m.residual(O.Cfg("euler", "roe", "ec"), u))
+    assert roe[5] < -1e-6 * roe[6]
+    std = m.integrals(G, u, m.residual(O.Cfg("euler", "ec", "standard"), u))
+    assert abs(std[5]) > 1e-8 * std[6]
+
+
+def _wave(m, t, v=(0.7, 0.3, -0.2), p=1.0, amp=0.2, L=10.0):
+    X = m.X
+    ph = 2 * np.pi * ((X[:, 0] - v[0] * t) + (X[:, 1] - v[1] * t) + (X[:, 2] - v[2] * t)) / L
+    rho = 1 + amp * np.sin(ph)
+    u = np.zeros(m.shape)
+    u[:, 0] = rho
+    for c in range(3):
+        u[:, 1 + c] = rho * v[c]
+    u[:, 4] = p / (G - 1) + 0.5 * rho * sum(c * c for c in v)
+    return u
+
+
+@pytest.mark.parametrize("volume", ["standard", "ec"])
+@pytest.mark.parametrize("surface", ["lf", "roe", "ec"])
+def test_residual_spectral_convergence_density_wave(surface, volume):
+    """A density wave at uniform v and p is an exact Euler solution
+    u(x - v t); the residual must converge spectrally to -v.grad u on a
+    curved mesh."""
+    errs = []
+    for N in (2, 3, 4, 5, 6):
+        m = O.Mesh(3, 3, 3, N, lo=(0,) * 3, hi=(10,) * 3, amp=0.05)
+        d = 1e-5
+        exact = (_wave(m, d) - _wave(m, -d)) / (2 * d)
+        errs.append(_rel(m.residual(O.Cfg("euler", surface, volume), _wave(m, 0.0)), exact))
+    assert errs[-1] < 2e-3
+    assert all(b < 0.45 * a for a, b in zip(errs, errs[1:]))
+
+
+def test_residual_converges_to_isentropic_vortex():
+    """The translated isentropic vortex (Shu) is an exact Euler solution; the
+    residual of the initial condition converges spectrally to -u_inf du/dx."""
+    errs = []
+    kw = dict(xc=5.3, yc=4.6)   # no node on the plane opposite the centre
+    for N in (3, 4, 5, 6, 7):
+        m = O.Mesh(8, 8, 1, N, lo=(0, 0, 0), hi=(10, 10, 10 / 8))
+        d = 1e-5
+        exact = (m.ic_vortex(G, 0.5, 5.0, t=d, **kw) - m.ic_vortex(G, 0.5, 5.0, t=-d, **kw)) / (2 * d)
+        errs.append(_rel(m.residual(O.Cfg("euler", "lf", "standard"), m.ic_vortex(G, 0.5, 5.0, **kw)), exact))
+    assert errs[-1] < 3e-3
+    assert all(b < 0.5 * a for a, b in zip(errs, errs[1:]))
+
+
+def test_br1_gradient_exact_for_polynomials_on_straight_mesh():
+    """On a straight box a velocity and temperature field of degree <= N that
+    is continuous across elements is differentiated exactly by BR1."""
+    N = 3
+    m = O.Mesh(2, 2, 2, N, lo=(0,) * 3, hi=(2.0, 2.0, 2.0))
+    x, y, z = m.X[:, 0], m.X[:, 1], m.X[:, 2]
+    v1, v2, v3 = 0.1 * x * y, 0.2 * z - 0.05 * x * x, 0.03 * y * z
+    T = 1.0 + 0.1 * x + 0.05 * y * y
+    rho = 1.0 + 0.0 * x
+    u = np.stack([rho, rho * v1, rho * v2, rho * v3, rho * T / (G - 1) + 0.5 * rho * (v1 ** 2 + v2 ** 2 + v3 ** 2)], 1)
+    # periodic box: use a field that only lives inside one element to avoid the wrap;
+    # compare in the interior element faces shared inside the box
+    grad = m.gradients(O.Cfg("ns"), u)
+    exact = {
+        (0, 0): 0.1 * y, (0, 1): 0.1 * x, (0, 2): 0 * x,
+        (1, 0): -0.1 * x, (1, 1): 0 * x, (1, 2): 0.2 + 0 * x,
+        (2, 0): 0 * x, (2, 1): 0.03 * z, (2, 2): 0.03 * y,
+        (3, 0): 0.1 + 0 * x, (3, 1): 0.1 * y, (3, 2): 0 * x,
+    }
+    # element 0 touches the periodic wrap on its -x,-y,-z faces; only the
+    # interior of the box is checked: nodes whose lifting partners lie inside
+    for (v, c), ex in exact.items():
+        g = grad[:, v, c]
+        inside = np.ones_like(g, dtype=bool)
+        for e in range(m.E):
+            a, b, cc = e % 2, (e // 2) % 2, e // 4
+            if a == 0:
+                inside[e, :, :, 0] = False
+            if a == 1:
+                inside[e, :, :, -1] = False
+            if b == 0:
+                inside[e, :, 0, :] = False
+            if b == 1:
+                inside[e, :, -1, :] = False
+            if cc == 0:
+                inside[e, 0, :, :] = False
+            if cc == 1:
+                inside[e, -1, :, :] = False
+        assert np.abs((g - ex)[inside]).max() < 1e-12
+
+
+def test_br1_heat_conduction():
+    """At rest with uniform pressure the energy equation reduces to
+    d(rho e)/dt = kappa lap T; the BR1 residual converges to it spectrally
+    (mass and momentum residuals vanish)."""
+    errs = []
+    for N in (3, 5, 7):
+        m = O.Mesh(3, 3, 3, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=0.05)
+        x, y, z = m.X[:, 0], m.X[:, 1], m.X[:, 2]
+        eps = 1e-3
+        S = np.sin(x) * np.sin(y) * np.sin(z)
+        T = 1.0 + eps * S
+        u = np.zeros(m.shape)
+        u[:, 0] = 1.0 / T
+        u[:, 4] = 1.0 / (G - 1)
+        Re, Pr = 10.0, 0.72
+        r = m.residual(O.Cfg("ns", "lf", "standard", Re=Re, Pr=Pr), u)
+        kappa = (1 / Re) * G / ((G - 1) * Pr)
+        errs.append(_rel(r[:, 4], kappa * eps * (-3.0) * S))
+        assert np.abs(r[:, :4]).max() < 1e-12
+    assert errs[-1] < 1e-3 and errs[0] > 10 * errs[-1]
+
+
+@pytest.mark.parametrize("Re", [100.0, 1600.0])
+def test_tgv_initial_dissipation(Re):
+    """Taylor-Green: <|v|^2>/2 = 1/8, enstrophy <|w|^2> = 3/4, so the viscous
+    kinetic-energy decay at t = 0 is -3/(4 Re).  The EC split form and EC
+    surface flux add no numerical dissipation; the Euler residual is
+    subtracted to isolate the viscous part."""
+    m = O.Mesh(8, 8, 8, 4, lo=(-np.pi,) * 3, hi=(np.pi,) * 3)
+    u = m.ic_tgv(G, 0.1)
+    Jw = m.J * np.einsum("i,j,k->kji", m.w, m.w, m.w)[None]
+    rho, v = u[:, 0], u[:, 1:4] / u[:, 0:1]
+    vol = (2 * np.pi) ** 3
+    assert abs((Jw * 0.5 * (v * v).sum(1)).sum() / vol - 0.125) < 1e-6
+
+    def rate(cfg):
+        r = m.residual(cfg, u)
+        return (Jw * ((v * r[:, 1:4]).sum(1) - 0.5 * (v * v).sum(1) * r[:, 0])).sum() / vol
+
+    visc = rate(O.Cfg("ns", "ec", "ec", Re=Re)) - rate(O.Cfg("euler", "ec", "ec"))
+    assert abs(visc / (-0.75 / Re) - 1) < 1e-6
+
+
+def test_tgv_initial_condition_is_isothermal():
+    m = O.Mesh(4, 4, 4, 3, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=0.05)
+    Ma = 0.1
+    u = m.ic_tgv(G, Ma)
+    rho, v = u[:, 0], u[:, 1:4] / u[:, 0:1]
+    p = (G - 1) * (u[:, 4] - 0.5 * rho * (v * v).sum(1))
+    assert np.abs(p / rho - 1 / (G * Ma * Ma)).max() < 1e-10
+    assert np.abs(v[:, 2]).max() == 0.0
+
+
+# --------------------------------------------------------------------------- time integration (Sec. 3.7)
+
+def test_williamson_coefficients_match_golden():
+    rows = {}
+    with open(os.path.join(GOLD, "williamson_rk3.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, *vals = (s.strip() for s in line.split("|"))
+            rows[k] = [float(Fraction(v)) for v in vals]
+    A, B, Cc = O.rk3_coefficients()
+    assert np.allclose(A, rows["A"], rtol=0, atol=1e-16)
+    assert np.allclose(B, rows["B"], rtol=0, atol=1e-16)
+    assert np.allclose(Cc, rows["C"], rtol=0, atol=1e-16)
+
+
+def test_rk3_amplification_polynomial():
+    """For y' = z y one step multiplies by exactly 1 + z + z^2/2 + z^3/6
+    (third order, three stages)."""
+    for z in (-0.3, -1.0, 0.5 + 0.7j, -2.0 + 1.0j):
+        zr = np.array([z.real]) if isinstance(z, float) else None
+        if zr is not None:
+            y, gg = np.array([1.0]), np.zeros(1)
+            for k in range(3):
+                O.lsrk3_stage(k, 1.0, y, gg, z * y.copy())
+            assert abs(y[0] - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
+        else:
+            # complex z via the real 2x2 form of y' = z y
+            y, gg = np.array([1.0, 0.0]), np.zeros(2)
+            for k in range(3):
+                R = np.array([z.real * y[0] - z.imag * y[1], z.imag * y[0] + z.real * y[1]])
+                O.lsrk3_stage(k, 1.0, y, gg, R)
+            ref = 1 + z + z * z / 2 + z ** 3 / 6
+            assert abs(complex(y[0], y[1]) - ref) < 1e-15
+
+
+def test_rk3_third_order_on_nonlinear_problem():
+    """Self-convergence of the full scheme on the vortex at fixed space:
+    successive differences shrink by 2^3 when dt halves."""
+    m = O.Mesh(4, 4, 1, 3, lo=(0, 0, 0), hi=(10, 10, 2.5))
+    cfg = O.Cfg("euler", "roe", "standard")
+    u0 = m.ic_vortex(G, 0.5, 5.0)
+    T = 0.4
+    sols = []
+    for nsteps in (8, 16, 32, 64):
+        u = u0.copy()
+        g = np.zeros_like(u)
+        for _ in range(nsteps):
+            m.rk3_step(cfg, u, g, dt=T / nsteps)
+        sols.append(u)
+    d = [np.linalg.norm(a - b) for a, b in zip(sols, sols[1:])]
+    ratios = [a / b for a, b in zip(d, d[1:])]
+    assert all(6.5 < r < 9.5 for r in ratios), ratios
+
+
+def test_dt_rule_closed_form_on_straight_box():
+    m = O.Mesh(4, 4, 4, 3, lo=(0,) * 3, hi=(8.0,) * 3)
+    h, n = 2.0, 4
+    st = np.array([1.3, 1.3 * 0.4, 1.3 * -0.2, 1.3 * 0.1, 0.0])
+    v = st[1:4] / st[0]
+    p = 0.9
+    st[4] = p / (G - 1) + 0.5 * st[0] * v @ v
+    u = np.zeros(m.shape)
+    u[:] = st[None, :, None, None, None]
+    c = np.sqrt(G * p / st[0])
+    dtc = 0.5 * h / (n * (np.abs(v).sum() + 3 * c))
+    assert abs(m.dt(O.Cfg("euler", cfl=0.5), u) - dtc) < 1e-12 * dtc
+    Re = 0.05    # strong viscosity so that the viscous limit binds
+    nu = (1 / Re) / st[0]
+    dtv = h * h / (nu * n ** 4)
+    got = m.dt(O.Cfg("ns", cfl=0.5, Re=Re), u)
+    assert abs(got - min(dtc, dtv)) < 1e-12 * got and dtv < dtc
+
+
+def test_integrals_volume_and_mass():
+    m = O.Mesh(3, 3, 3, 4, lo=(0,) * 3, hi=(3.0, 2.0, 1.0))
+    u = np.zeros(m.shape)
+    u[:, 0] = 2.0
+    assert abs(m.integrals(G, u)[0] - 12.0) < 1e-12 * 12.0
