@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Throughput of the DGSEM RK3 step: DOF-stage-updates/s on one GB300.
+
+Workload (the metric's configuration): compressible Navier-Stokes
+Taylor-Green vortex, Ma 0.1, Re 1600, Pr 0.72, periodic [-pi,pi]^3 with 16^3
+curved hexahedra (every node moved by 0.05 sin x sin y sin z), N = 3
+(64^3 nodes), Chandrashekar split-form volume term + Roe surface flux + BR1,
+Williamson RK3 with the CFL-0.5 time step recomputed on the device each
+step.  A step is one RK3 step (three residual evaluations + updates) of the
+whole mesh.  value = nodes * 3 stages * K / (sum of the K step times), for
+the mixed path (FP32 flux arithmetic, FP64 state / geometry / RK); the
+FP64 path is reported beside it with its own throughput, and each path
+states its L2 difference.
+
+The state (~70 MB with geometry and scratch) fits in the 129 MB L2, so L2 is
+flushed (a 512 MB buffer is written) between timed steps; each step is timed
+with CUDA events on the launching stream and the flush is outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hs3d|reference]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on the
+same workload (a bounded sample per step), as the reference arm.
+Under torchrun (N > 1) every rank runs an independent replica (the path is
+a single-GPU solver; replicas only) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# workload
+EX = EY = EZ = 16
+N = 3
+AMP = 0.05
+MA, RE, PR, GAMMA, CFL = 0.1, 1600.0, 0.72, 1.4, 0.5
+NODES = EX * EY * EZ * (N + 1) ** 3
+METRIC = "DOF-stage-updates/s"
+WORKLOAD = ("NS Taylor-Green vortex Ma 0.1 Re 1600, [-pi,pi]^3, 16^3 curved hex (amp 0.05), N=3 (64^3 DOF), "
+            "EC split form + Roe + BR1, Williamson RK3 CFL 0.5")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hs3d", choices=["hs3d", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing (replicas only)
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("HS3D_DIST_BACKEND", "nccl")
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate(units_local, seconds_local, world):
+    """Whole-job throughput: units all ranks processed / slowest rank's time."""
+    units = reduce_sum(units_local, world)
+    secs = reduce_max(seconds_local, world)
+    return units / secs, secs
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ------------------------------------------------------------------ algorithmic cost model (per launch)
+
+def kernel_bytes(kernel, prec, E=EX * EY * EZ, n=N + 1):
+    """Compulsory DRAM bytes of one launch of each kernel (FP64 state and
+    geometry; scratch arrays fstar/grad in the arithmetic type)."""
+    s = 8 if prec == "fp64" else 4
+    n2, n3 = n * n, n ** 3
+    if kernel == "volume":     # u, Ja, invJ, grad, 6 face fluxes in; g in/out, u out
+        return E * (5 * n3 * 8 + 9 * n3 * 8 + n3 * 8 + 12 * n3 * s + 6 * 5 * n2 * s + 5 * n3 * 8 * 3)
+    if kernel == "face":       # two traces, face normal, two gradient traces in; flux out
+        return 3 * E * (2 * 5 * n2 * 8 + 3 * n2 * 8 + 2 * 12 * n2 * s + 5 * n2 * s)
+    if kernel == "grad":       # u, Ja, invJ, 6 neighbour traces in; gradients out
+        return E * (5 * n3 * 8 + 9 * n3 * 8 + n3 * 8 + 6 * 5 * n2 * 8 + 12 * n3 * s)
+    return 0
+
+
+def volume_flops(E=EX * EY * EZ, n=N + 1):
+    """Algorithmic flops of one launch of the split-form NS element kernel
+    (an FMA counts 2, a divide / sqrt / log 1 each), counted from the
+    formulas the kernel evaluates:
+      primitives 14, three Euler fluxes 3*13, three viscous fluxes 3*40,
+      two-point fluxes 3*(n-1) * 63 (two log means 2*14, averages 14,
+      flux 21) plus the 5-term axpy 10 each, diagonal 3*10,
+      viscous D-contraction 3*n*8, surface lift <= 3*10, scale + RK 5*5."""
+    per_node = 14 + 3 * 13 + 3 * 40 + 3 * (n - 1) * (63 + 10) + 3 * 10 + 3 * n * 8 + 30 + 25
+    return E * n ** 3 * per_node
+
+
+# ------------------------------------------------------------------ the hs3d arm
+
+def run_hs3d(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2206_09733_gb300 as hs
+    from paper_2206_09733_gb300 import build as hsbuild
+
+    if rank == 0 or not os.path.exists(hs.LIB_PATH):
+        hsbuild.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    mesh = hs.Mesh(EX, EY, EZ, N, lo=lo, hi=hi, amp=AMP)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def cfg(prec):
+        return hs.solver_cfg("ns", "roe", "ec", prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+
+    def fresh():
+        u = mesh.init_state(mesh.empty_state(), "tgv", GAMMA, MA)
+        return u, torch.zeros_like(u)
+
+    def timed_steps(prec, K, W, sampler=None):
+        u, g = fresh()
+        c = cfg(prec)
+        for _ in range(W):
+            mesh.rk3_run(c, u, g, 1)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.fill_(1.0)                  # evict the working set from L2 between steps
+            a.record(stream)
+            mesh.rk3_run(c, u, g, 1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, u
+
+    # --- headline: mixed path, then FP64 path, K timed steps each
+    with ClockSampler(local) as clk:
+        ms32, u32 = timed_steps("mixed32", args.steps, args.warmup)
+        ms64, u64 = timed_steps("fp64", args.steps, args.warmup)
+    clocks = clk.summary()
+    v32, s32 = aggregate(NODES * 3 * args.steps, ms32 * 1e-3, world)
+    v64, s64 = aggregate(NODES * 3 * args.steps, ms64 * 1e-3, world)
+    # both paths advanced W + K steps from the same initial state
+    d = (u32 - u64).double()
+    l2_32_vs_64 = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(u64))
+    t64, steps64 = mesh.clock()
+
+    # --- per-kernel attribution (eager steps with events between kernels)
+    prof = {}
+    for prec in ("mixed32", "fp64"):
+        u, g = fresh()
+        acc = {"dt": 0.0, "grad": 0.0, "face": 0.0, "volume": 0.0, "step": 0.0}
+        reps = min(args.steps, 20)
+        for _ in range(3):
+            mesh.rk3_step_profiled(cfg(prec), u, g)
+        for _ in range(reps):
+            flush.fill_(1.0)
+            r = mesh.rk3_step_profiled(cfg(prec), u, g)
+            for k in acc:
+                acc[k] += r[k] / reps
+        prof[prec] = acc
+    peaks = hs.alu_peaks()
+
+    # --- e2e: the C-ABI with HOST buffers: H2D of the state, one RK3 step, D2H of the state
+    pin_in = torch.empty(mesh.shape, dtype=torch.float64, pin_memory=True)
+    pin_out = torch.empty_like(pin_in)
+    u, g = fresh()
+    pin_in.copy_(u.cpu())
+    c = cfg("mixed32")
+    for _ in range(args.warmup):
+        u.copy_(pin_in, non_blocking=True)
+        mesh.rk3_run(c, u, g, 1)
+        pin_out.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    K_e2e = args.steps
+    barrier(world)
+    t0 = time.perf_counter()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(K_e2e):
+        u.copy_(pin_in, non_blocking=True)
+        mesh.rk3_run(c, u, g, 1)
+        pin_out.copy_(u, non_blocking=True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = e_start.elapsed_time(e_end)
+    e2e_val, _ = aggregate(NODES * 3 * K_e2e, e2e_ms * 1e-3, world)
+    state_bytes = NODES * 5 * 8
+
+    # --- roofline of the dominant kernel of the mixed path
+    p32 = prof["mixed32"]
+    dom = max(("grad", "face", "volume"), key=lambda k: p32[k])
+    per_launch_ms = p32[dom] / 3.0
+    hbm_peak = measured_hbm_peak()
+    achieved_gbs = kernel_bytes(dom, "mixed32") / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak[0], "unit": "GB/s",
+            "frac": round(achieved_gbs / hbm_peak[0], 4), "traffic": None, "kernel": f"k_volume<3,float,NS,EC>"
+            if dom == "volume" else dom, "peak_source": hbm_peak[1]}
+    p64 = prof["fp64"]
+    fp64_ach = volume_flops() / (p64["volume"] / 3.0 * 1e-3) / 1e12
+    fp64_roof = {"bound": "alu", "kernel": "k_volume<3,double,NS,EC>", "achieved": round(fp64_ach, 3),
+                 "peak": round(peaks["fp64_tflops"], 3), "unit": "TFLOP/s",
+                 "frac": round(fp64_ach / peaks["fp64_tflops"], 4),
+                 "peak_source": "measured FP64 FMA-chain kernel (hs3d_alu_peaks)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(u64_final_check=None)
+
+    launches_per_step = 2 + 3 * 3
+    line = {
+        "metric": METRIC, "value": round(v32, 1), "unit": "DOF-stage-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s32 * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (analytic Taylor-Green initial condition)",
+        "config": {"workload": WORKLOAD, "E": EX * EY * EZ, "N": N, "nodes": NODES,
+                   "precision": "mixed32: FP32 flux arithmetic, FP64 state/geometry/primitive conversion/RK",
+                   "l2": "flushed between timed steps (512 MB write outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "timing": "sum of per-step CUDA-event times on the launching stream, CUDA-graph replay"},
+        "l2_rel_vs_fp64_gpu": l2_32_vs_64,
+        "fp64": {"value": round(v64, 1), "ms_per_step": round(s64 * 1e3 / args.steps, 4), "dtype": "f64",
+                 "sim_time_after_all_steps": t64, "roofline": fp64_roof},
+        "kernel_ms_per_step": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in prof.items()},
+        "alu_peaks_measured": {k: round(v, 3) for k, v in peaks.items()},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_val, 1), "unit": "DOF-stage-updates/s", "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes,
+                "how": "hs3d_rk3_run per step from a pinned host state: H2D copy, one RK3 step, D2H copy"},
+        "gpu_launches": launches_per_step * args.steps * 2,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+# ------------------------------------------------------------------ the oracle on the host cores
+
+def cpu_baseline(u64_final_check=None, budget_s=15.0):
+    """Time the FP64 CPU oracle (as it stands) on this workload: RK3 steps
+    from the initial condition until ~budget_s of CPU work."""
+    import numpy as np
+
+    import oracle as O
+    om = O.Mesh(EX, EY, EZ, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=AMP)
+    oc = O.Cfg("ns", "roe", "ec", gamma=GAMMA, Re=RE, Pr=PR, cfl=CFL)
+    u = om.ic_tgv(GAMMA, MA)
+    g = np.zeros_like(u)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        om.rk3_step(oc, u, g)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 200:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(NODES * 3 * steps / el, 1), "unit": "DOF-stage-updates/s", "cores": cores,
+            "kind": "oracle", "sample": f"{steps} RK3 steps of the full 16^3 N=3 workload from t=0 "
+                                        f"({el:.1f} s, OpenMP over elements)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    O.build()
+    om = O.Mesh(EX, EY, EZ, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=AMP)
+    oc = O.Cfg("ns", "roe", "ec", gamma=GAMMA, Re=RE, Pr=PR, cfl=CFL)
+    u = om.ic_tgv(GAMMA, MA)
+    g = np.zeros_like(u)
+    for _ in range(args.warmup):
+        om.rk3_step(oc, u, g)
+    # each timed step is one full oracle RK3 step; cap the run near two minutes
+    K = args.steps
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(K):
+        om.rk3_step(oc, u, g)
+        done += 1
+        if time.perf_counter() - t0 > 120.0:
+            break
+    el = time.perf_counter() - t0
+    val = NODES * 3 * done / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 1), "unit": "DOF-stage-updates/s",
+            "n_gpus": world, "steps": done, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / done, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (analytic Taylor-Green initial condition)",
+            "config": {"workload": WORKLOAD, "E": EX * EY * EZ, "N": N, "nodes": NODES},
+            "cpu_baseline": {"value": round(val, 1), "unit": "DOF-stage-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{done} full RK3 steps (of {K} requested) after {args.warmup} warm-up steps"},
+            "e2e": {"value": round(val, 1), "unit": "DOF-stage-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_hs3d(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * hs3d -- GB300 (sm_103a) DGSEM residual and low-storage RK3 library for the
+ * compressible Euler and Navier-Stokes equations on curvilinear hexahedra.
+ *
+ * The method is the one of the HORSES3D paper (arXiv 2206.09733):
+ *   - conservation law u_t + div F_e = div F_v, u = (rho, rho v, rho e)
+ *     (Sec. 3.2, Eq. compressibleNScompact; F_v of Eq. viscousfluxes);
+ *   - mapped to the reference cube, J u_t + div_xi F~ = 0 with contravariant
+ *     fluxes (Sec. 3.3, Eq. compressibleNScompact_transformed);
+ *   - DGSEM weak form with a numerical flux at faces on Gauss-Lobatto nodes
+ *     (Sec. 3.3, Eqs. NS2-NS5), Lax-Friedrichs / Roe / central surface
+ *     fluxes and BR1 viscous terms (Sec. 3.3, list of fluxes);
+ *   - Chandrashekar entropy-conservative split form (Sec. 3.5);
+ *   - Williamson low-storage RK3 (Sec. 3.7).
+ *
+ * Conventions for every entry point:
+ *   - All device arrays are FP64, contiguous, at least 16-byte aligned,
+ *     element-major: u[e][v][k][j][i] with v = rho, rho v1, rho v2, rho v3,
+ *     rho e and i the fastest (xi) index; n = N+1 nodes per direction.
+ *     Elements of an ex*ey*ez box are numbered e = a + ex*(b + ey*c).
+ *   - The caller owns state arrays (u, g, dudt); the library owns meshes,
+ *     their geometry and scratch, and server slots.
+ *   - Calls taking a `stream` (a cudaStream_t, NULL = legacy default stream)
+ *     are stream-ordered and asynchronous; they enqueue work and return.
+ *     The same mesh must not be used by two streams at once (its scratch is
+ *     shared).
+ *   - No exception crosses the ABI.  Every call returns an hs3d_status; on
+ *     error hs3d_last_error() gives a thread-local message.  A CUDA error is
+ *     reported as HS3D_ERR_CUDA.  Invalid arguments are rejected before any
+ *     work is enqueued (HS3D_ERR_INVALID), unsupported combinations with
+ *     HS3D_ERR_UNSUPPORTED.
+ *   - There is no CPU fallback: without a usable GPU every compute call
+ *     returns HS3D_ERR_CUDA.
+ */
+#ifndef HS3D_H
+#define HS3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HS3D_OK = 0,
+    HS3D_PENDING = 1,            /* server: request not finished yet */
+    HS3D_ERR_INVALID = -1,       /* bad argument or descriptor */
+    HS3D_ERR_NOMEM = -2,         /* device or host allocation failed, or request larger than the budget */
+    HS3D_ERR_CUDA = -3,          /* a CUDA call failed (no device, launch error, ...) */
+    HS3D_ERR_TIMEOUT = -4,       /* a bounded wait ran out */
+    HS3D_ERR_NONPHYSICAL = -5,   /* rho <= 0, p <= 0 or NaN detected in a state */
+    HS3D_ERR_UNSUPPORTED = -6    /* valid but not implemented combination */
+} hs3d_status;
+
+/* physics */
+enum { HS3D_EULER = 0, HS3D_NS = 1 };
+/* surface (Riemann) flux, Sec. 3.3: Lax-Friedrichs, Roe, central
+ * (entropy-conservative Chandrashekar flux, no dissipation) */
+enum { HS3D_FLUX_LF = 0, HS3D_FLUX_ROE = 1, HS3D_FLUX_EC = 2 };
+/* volume term: standard DGSEM or Chandrashekar split form (Sec. 3.5) */
+enum { HS3D_VOL_STANDARD = 0, HS3D_VOL_EC = 1 };
+/* arithmetic: all FP64; or FP32 flux arithmetic with FP64 state, geometry,
+ * primitive-variable conversion and RK accumulation */
+enum { HS3D_FP64 = 0, HS3D_MIXED32 = 1 };
+/* initial conditions */
+enum { HS3D_IC_VORTEX = 0, HS3D_IC_TGV = 1 };
+
+/* Mesh of a periodic box [lo, hi] with ex*ey*ez hexahedra of degree N
+ * (1 <= N <= 7) on Gauss-Lobatto nodes (Sec. 3.1, 3.3).  Every node is moved
+ * by perturb_amp * (L_c/2pi) * sin(t_x) sin(t_y) sin(t_z), t = the unperturbed
+ * position mapped linearly from [lo, hi] to [-pi, pi] (so on [-pi,pi]^3 the
+ * displacement is exactly amp*sin(x)sin(y)sin(z) in every coordinate).
+ * node_xyz, if not NULL, is a HOST FP64 array [E][3][n][n][n] of node
+ * coordinates that replaces the generator (the box must still be periodic and
+ * the faces of neighbouring elements must coincide).  periodic[] must be all
+ * 1 (other boundaries: HS3D_ERR_UNSUPPORTED). */
+typedef struct {
+    int ex, ey, ez;
+    int N;
+    double lo[3], hi[3];
+    int periodic[3];
+    double perturb_amp;
+    const double *node_xyz;
+} hs3d_mesh_desc;
+
+/* Solver configuration.  gamma: ratio of specific heats; Re, Pr: Reynolds and
+ * Prandtl numbers (mu = 1/Re, kappa = mu gamma/((gamma-1) Pr), gas constant
+ * 1, temperature T = p/rho); Ma: used only by initial conditions; cfl: the
+ * convective CFL number of the time-step rule. */
+typedef struct {
+    int physics;
+    int surface_flux;
+    int volume_form;
+    int precision;
+    double gamma, Re, Pr, Ma, cfl;
+} hs3d_solver_cfg;
+
+/* Initial condition.  VORTEX: isentropic vortex of strength beta centred at
+ * (xc, yc) (uniform in z), free stream rho = p = 1 moving at Ma*sqrt(gamma)
+ * along x, evaluated at time t (translated, nearest periodic image).
+ * TGV: Taylor-Green vortex, p0 = 1/(gamma Ma^2), rho = p/p0. */
+typedef struct {
+    int kind;
+    double gamma, Ma, beta, xc, yc, t;
+} hs3d_ic;
+
+typedef struct hs3d_mesh hs3d_mesh;
+typedef struct hs3d_server hs3d_server;
+
+/* Build a mesh on the current CUDA device: node coordinates, curl-form metric
+ * terms Ja^d_c = J dxi_d/dx_c and J (Sec. 3.3), face normals, computed by GPU
+ * kernels in FP64.  Synchronous.  The library owns all its memory;
+ * HS3D_ERR_NOMEM if the device cannot hold it. */
+hs3d_status hs3d_mesh_create(const hs3d_mesh_desc *desc, hs3d_mesh **out);
+void hs3d_mesh_destroy(hs3d_mesh *mesh);
+
+/* Elements, degree and device bytes held by the mesh (any pointer may be NULL). */
+hs3d_status hs3d_mesh_info(const hs3d_mesh *mesh, int64_t *E, int *N, size_t *device_bytes);
+
+/* Copy the mesh geometry into caller-owned DEVICE arrays (any may be NULL):
+ * X [E][3][n3], Ja [E][3][3][n3], J [E][n3].  Stream-ordered. */
+hs3d_status hs3d_mesh_geometry(const hs3d_mesh *mesh, double *X, double *Ja, double *J, void *stream);
+
+/* Evaluate an initial condition at the mesh nodes into u (device). */
+hs3d_status hs3d_init_state(const hs3d_mesh *mesh, const hs3d_ic *ic, double *u, void *stream);
+
+/* Semi-discrete residual du/dt = -(V + S)/J (Sec. 3.3, Eq. NS5 in strong
+ * form on Gauss-Lobatto nodes): volume term V (standard or split form),
+ * surface term S lifted from the numerical fluxes, Jacobian scaling; for NS
+ * the BR1 gradients and viscous fluxes.  u and dudt: device [E][5][n3],
+ * distinct arrays.  Stream-ordered. */
+hs3d_status hs3d_residual(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, const double *u, double *dudt,
+                          void *stream);
+
+/* One Williamson low-storage RK3 step (Sec. 3.7): per stage k,
+ *   g <- A_k g + dt R(u),  u <- u + B_k g,
+ * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  u and g: device
+ * [E][5][n3], updated in place (g need not be initialised).  dt > 0 is used
+ * as given; dt <= 0 computes dt on the device from the state at the start of
+ * the step:
+ *   dt = min( cfl*2/(n max_nodes sum_d (|Ja^d.v| + c|Ja^d|)/J),
+ *             12/(n^4 max_nodes (mu/rho) sum_d (|Ja^d|/J)^2) )   (viscous term NS only).
+ * Stream-ordered. */
+hs3d_status hs3d_rk3_step(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
+                          void *stream);
+
+/* nsteps RK3 steps as hs3d_rk3_step, replayed from a CUDA graph captured on
+ * the first call for this (mesh, cfg, u, g, dt) (re-captured when any of them
+ * changes).  Stream-ordered. */
+hs3d_status hs3d_rk3_run(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
+                         int nsteps, void *stream);
+
+/* dt of the rule above for state u, written to dt_out (DEVICE, 1 double). */
+hs3d_status hs3d_dt(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, const double *u, double *dt_out,
+                    void *stream);
+
+/* Simulated time and step count accumulated by hs3d_rk3_step / hs3d_rk3_run on
+ * this mesh since creation or the last reset (reset != 0 zeroes them).
+ * Synchronises the stream. */
+hs3d_status hs3d_clock(const hs3d_mesh *mesh, double *t, int64_t *steps, int reset, void *stream);
+
+/* Quadrature diagnostics (FP64, fixed-order two-level reduction, so the
+ * result is bitwise reproducible): out[0..4] = sum_e sum_ijk J w_i w_j w_k
+ * f_v with f = dudt if given else u; if dudt is given out[5] = entropy rate
+ * sum J w w w (w(u).dudt) with w = dS/du, S = -rho s, s = ln p - gamma ln rho
+ * (Sec. 4.4, Eq. shock:entropy) and out[6] = sum |J w w w w_v dudt_v|.
+ * out: DEVICE, 7 doubles.  Stream-ordered. */
+hs3d_status hs3d_diagnostics(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, const double *u,
+                             const double *dudt, double *out, void *stream);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* One RK3 step exactly as hs3d_rk3_step, launched eagerly with CUDA events
+ * between the kernels on `stream`; waits for the step and writes the device
+ * time in milliseconds to the HOST array ms_out[5]: [0] dt rule (maxima +
+ * finalize), [1] BR1 gradient kernels, [2] face kernels, [3] element
+ * (volume + lift + RK) kernels, each summed over the three stages, [4] the
+ * whole step.  Not part of the method; used to attribute time to kernels. */
+hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g,
+                                   double dt, double *ms_out, void *stream);
+
+/* Measured arithmetic throughput of this GPU from FMA-chain kernels (8
+ * independent chains per thread, 8 CTAs of 256 threads per SM), written to
+ * the HOST array tflops_out[2]: [0] FP64, [1] FP32, in TFLOP/s (an FMA counts
+ * two flops).  The roofline denominators of ALU-bound kernels.  Synchronous. */
+hs3d_status hs3d_alu_peaks(double *tflops_out, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A solve request: a mesh, a solver configuration, an initial condition and
+ * a stopping rule (t_final > 0: integrate to exactly t_final, the last dt
+ * clipped; else n_steps steps).  result_host, if not NULL, is a caller-owned
+ * HOST buffer of E*5*n3 doubles that receives the final state; it must stay
+ * valid until hs3d_poll reports the request finished. */
+typedef struct {
+    hs3d_mesh_desc mesh;
+    hs3d_solver_cfg cfg;
+    hs3d_ic ic;
+    double t_final;
+    int n_steps;
+    double *result_host;
+} hs3d_request;
+
+/* Outcome and timing of a request (seconds since the server was created). */
+typedef struct {
+    hs3d_status status;      /* HS3D_OK when finished, HS3D_PENDING, or an error */
+    double t_sim;            /* simulated time reached */
+    int64_t steps;           /* RK steps taken */
+    int64_t dof;             /* nodes of the request (E n^3) */
+    double t_submit, t_admit, t_done;
+    size_t device_bytes;     /* footprint charged to the budget */
+} hs3d_result;
+
+/* A continuous-batching server on the current device.  hbm_budget_bytes
+ * bounds the device memory held by admitted requests (0: 90% of the free
+ * memory at creation).  max_batch bounds the requests sharing one launch
+ * (0: 256).  A host thread admits queued requests when the budget has room,
+ * groups the admitted ones by (N, physics, fluxes, precision), runs one RK3
+ * step per group with shared launches, retires finished requests and
+ * immediately admits the next. */
+hs3d_status hs3d_server_create(size_t hbm_budget_bytes, int max_batch, hs3d_server **out);
+/* Stops the thread after the running step; unfinished requests are dropped. */
+void hs3d_server_destroy(hs3d_server *server);
+/* Copies the request and queues it; never blocks on the GPU.  HS3D_ERR_NOMEM
+ * if the request alone exceeds the budget, HS3D_ERR_INVALID for a bad
+ * descriptor. */
+hs3d_status hs3d_submit(hs3d_server *server, const hs3d_request *req, uint64_t *ticket);
+/* Non-blocking: HS3D_PENDING until the request is finished, then its final
+ * status; res (may be NULL) receives the timing record.  A finished ticket
+ * can be polled again; unknown tickets give HS3D_ERR_INVALID. */
+hs3d_status hs3d_poll(hs3d_server *server, uint64_t ticket, hs3d_result *res);
+/* Counters: requests queued, running, finished; device bytes in use. */
+hs3d_status hs3d_server_stats(hs3d_server *server, int64_t *queued, int64_t *running, int64_t *finished,
+                              size_t *bytes_in_use);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *hs3d_last_error(void);
+/* Library version string. */
+const char *hs3d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS3D_H */

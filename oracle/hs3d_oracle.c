@@ -593,8 +593,9 @@ static void surface_flux(int kind, const double *uin, const double *uout, const 
 /* du/dt = -(V + S)/J per element, with
  *   standard form  V = sum_d D_d F~^d,  F~^d = sum_c Ja^d_c (F_e - F_v)_c
  *   split form     V = sum_d [ 2 sum_m D_im F#(u_i, u_m).(Ja^d_i + Ja^d_m)/2 ] - sum_d D_d F~_v^d
- *   surface        S = (1/w_end) [ F^*(in,out; Sn) - F_v^*.Sn - (F_e - F_v)(in).Sn ]
- * on each face node, F_v^* = (F_v(in) + F_v(out))/2 (BR1). */
+ *   surface        S = (1/w_end) [ +-(F^*(L,R; Sn_L) - F_v^*.Sn_L) - (F_e - F_v)(in).(+-Ja^d_in) ]
+ * on each face node (+ on the element's +d face, - on its -d face),
+ * F_v^* = (F_v(L) + F_v(R))/2 (BR1), Sn_L = Ja^d of the face's minus-side element. */
 int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *dudt)
 {
     int n = m->n, n3 = m->n3, E = m->E, N = n - 1;
@@ -660,7 +661,13 @@ int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double 
                 }
             }
         }
-        /* surface term */
+        /* surface term.  The numerical flux is single-valued on each face
+         * (Eq. NS4: F* couples the two elements): it is evaluated once per
+         * face node with the face's scaled normal, taken from the element on
+         * the face's minus side ("left", L) and pointing into the plus side
+         * (R); the element on the plus side receives it with the opposite
+         * sign.  The element's own boundary flux uses its own Ja^d, as the
+         * volume term does. */
         for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
             int p = node_index(n, i, j, k);
             int ijk[3] = {i, j, k};
@@ -670,30 +677,32 @@ int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double 
                 if (ijk[d] != at) continue;
                 int nb = neighbour(&m->box, e, d, side);
                 int pn = matching_node(n, d, side, i, j, k);
-                double uin[NVAR], uout[NVAR], Sn[3], fstar[NVAR];
+                int eL = (side > 0) ? e : nb, pL = (side > 0) ? p : pn;
+                int eR = (side > 0) ? nb : e, pR = (side > 0) ? pn : p;
+                double uL[NVAR], uR[NVAR], Sn[3], fstar[NVAR];
                 for (int v = 0; v < NVAR; ++v) {
-                    uin[v] = u[((size_t)e * NVAR + v) * n3 + p];
-                    uout[v] = u[((size_t)nb * NVAR + v) * n3 + pn];
+                    uL[v] = u[((size_t)eL * NVAR + v) * n3 + pL];
+                    uR[v] = u[((size_t)eR * NVAR + v) * n3 + pR];
                 }
-                for (int c = 0; c < 3; ++c) Sn[c] = side * m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p];
-                surface_flux(cfg->surface_flux, uin, uout, Sn, g, fstar);
+                for (int c = 0; c < 3; ++c) Sn[c] = m->Ja[(((size_t)eL * 3 + d) * 3 + c) * n3 + pL];
+                surface_flux(cfg->surface_flux, uL, uR, Sn, g, fstar);
                 if (ns) {
-                    double qi[NGRAD], qo[NGRAD], Gi[12], Go[12], fvi[NVAR], fvo[NVAR];
-                    grad_vars(uin, g, qi);
-                    grad_vars(uout, g, qo);
+                    double qL[NGRAD], qR[NGRAD], GL[12], GR[12], fvL[NVAR], fvR[NVAR];
+                    grad_vars(uL, g, qL);
+                    grad_vars(uR, g, qR);
                     for (int v = 0; v < NGRAD; ++v)
                         for (int c = 0; c < 3; ++c) {
-                            Gi[v * 3 + c] = grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p];
-                            Go[v * 3 + c] = grad[(((size_t)nb * NGRAD + v) * 3 + c) * n3 + pn];
+                            GL[v * 3 + c] = grad[(((size_t)eL * NGRAD + v) * 3 + c) * n3 + pL];
+                            GR[v * 3 + c] = grad[(((size_t)eR * NGRAD + v) * 3 + c) * n3 + pR];
                         }
-                    orc_flux_visc(qi, Gi, mu, kappa, Sn, fvi);
-                    orc_flux_visc(qo, Go, mu, kappa, Sn, fvo);
-                    for (int v = 0; v < NVAR; ++v) fstar[v] -= 0.5 * (fvi[v] + fvo[v]);
+                    orc_flux_visc(qL, GL, mu, kappa, Sn, fvL);
+                    orc_flux_visc(qR, GR, mu, kappa, Sn, fvR);
+                    for (int v = 0; v < NVAR; ++v) fstar[v] -= 0.5 * (fvL[v] + fvR[v]);
                 }
                 for (int v = 0; v < NVAR; ++v) {
-                    /* own flux (F_e - F_v)(in).Sn = side * F~^d(in) */
+                    /* outward flux side*F*, own flux (F_e - F_v)(in).(side Ja^d) = side * F~^d(in) */
                     double own = side * Ft[(d * NVAR + v) * n3 + p];
-                    R[v * n3 + p] += (fstar[v] - own) / m->w[at];
+                    R[v * n3 + p] += (side * fstar[v] - own) / m->w[at];
                 }
             }
         }

@@ -1,0 +1,308 @@
+"""hs3d: GB300-native DGSEM residual and low-storage RK3 for compressible Euler/Navier-Stokes.
+
+A thin ctypes binding over the C-ABI in ``include/hs3d.h`` (``libhs3d.so``,
+built in-tree by ``paper_2206_09733_gb300.build``).  It only marshals
+arguments: device arrays are torch CUDA tensors (float64, contiguous) passed
+by pointer together with the current torch stream; every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback --
+without the built library or a GPU, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhs3d.so")
+
+OK, PENDING = 0, 1
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONPHYSICAL, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT",
+                -5: "NONPHYSICAL", -6: "UNSUPPORTED"}
+EULER, NS = 0, 1
+FLUX_LF, FLUX_ROE, FLUX_EC = 0, 1, 2
+VOL_STANDARD, VOL_EC = 0, 1
+FP64, MIXED32 = 0, 1
+IC_VORTEX, IC_TGV = 0, 1
+
+PHYSICS = {"euler": EULER, "ns": NS}
+SURFACE = {"lf": FLUX_LF, "roe": FLUX_ROE, "ec": FLUX_EC}
+VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC}
+PRECISION = {"fp64": FP64, "mixed32": MIXED32}
+
+# every entry point declared in include/hs3d.h
+EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh_geometry", "hs3d_init_state",
+           "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
+           "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
+           "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks"]
+
+
+class HS3DError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"hs3d {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("ex", C.c_int), ("ey", C.c_int), ("ez", C.c_int), ("N", C.c_int),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int * 3),
+                ("perturb_amp", C.c_double), ("node_xyz", C.c_void_p)]
+
+
+class SolverCfg(C.Structure):
+    _fields_ = [("physics", C.c_int), ("surface_flux", C.c_int), ("volume_form", C.c_int), ("precision", C.c_int),
+                ("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double), ("Ma", C.c_double),
+                ("cfl", C.c_double)]
+
+
+class IC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("gamma", C.c_double), ("Ma", C.c_double), ("beta", C.c_double),
+                ("xc", C.c_double), ("yc", C.c_double), ("t", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh", MeshDesc), ("cfg", SolverCfg), ("ic", IC), ("t_final", C.c_double),
+                ("n_steps", C.c_int), ("result_host", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("t_sim", C.c_double), ("steps", C.c_int64), ("dof", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("device_bytes", C.c_size_t)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libhs3d.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise HS3DError(ERR_CUDA, f"{LIB_PATH} missing: run paper_2206_09733_gb300.build")
+            L = C.CDLL(LIB_PATH)
+            vp, i, d = C.c_void_p, C.c_int, C.c_double
+            sig = {
+                "hs3d_mesh_create": [C.POINTER(MeshDesc), C.POINTER(vp)],
+                "hs3d_mesh_destroy": [vp],
+                "hs3d_mesh_info": [vp, C.POINTER(C.c_int64), C.POINTER(i), C.POINTER(C.c_size_t)],
+                "hs3d_mesh_geometry": [vp, vp, vp, vp, vp],
+                "hs3d_init_state": [vp, C.POINTER(IC), vp, vp],
+                "hs3d_residual": [vp, C.POINTER(SolverCfg), vp, vp, vp],
+                "hs3d_rk3_step": [vp, C.POINTER(SolverCfg), vp, vp, d, vp],
+                "hs3d_rk3_run": [vp, C.POINTER(SolverCfg), vp, vp, d, i, vp],
+                "hs3d_dt": [vp, C.POINTER(SolverCfg), vp, vp, vp],
+                "hs3d_clock": [vp, C.POINTER(d), C.POINTER(C.c_int64), i, vp],
+                "hs3d_diagnostics": [vp, C.POINTER(SolverCfg), vp, vp, vp, vp],
+                "hs3d_server_create": [C.c_size_t, i, C.POINTER(vp)],
+                "hs3d_server_destroy": [vp],
+                "hs3d_submit": [vp, C.POINTER(Request), C.POINTER(C.c_uint64)],
+                "hs3d_poll": [vp, C.c_uint64, C.POINTER(Result)],
+                "hs3d_server_stats": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_size_t)],
+                "hs3d_rk3_step_profiled": [vp, C.POINTER(SolverCfg), vp, vp, d, C.POINTER(d), vp],
+                "hs3d_alu_peaks": [C.POINTER(d), vp],
+                "hs3d_last_error": [],
+                "hs3d_version": [],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            L.hs3d_mesh_destroy.restype = None
+            L.hs3d_server_destroy.restype = None
+            L.hs3d_last_error.restype = C.c_char_p
+            L.hs3d_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def check(status):
+    if status not in (OK, PENDING):
+        raise HS3DError(status, lib().hs3d_last_error().decode())
+    return status
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise HS3DError(ERR_INVALID, f"{name} must be a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def solver_cfg(physics="euler", surface="lf", volume="standard", precision="fp64", gamma=1.4, Re=1600.0,
+               Pr=0.72, Ma=0.1, cfl=0.5) -> SolverCfg:
+    return SolverCfg(PHYSICS[physics], SURFACE[surface], VOLUME[volume], PRECISION[precision],
+                     gamma, Re, Pr, Ma, cfl)
+
+
+def mesh_desc(ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None) -> MeshDesc:
+    return MeshDesc(ex, ey, ez, N, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int * 3)(1, 1, 1),
+                    amp, node_xyz)
+
+
+class Mesh:
+    """A library-owned mesh on the current CUDA device (``hs3d_mesh_create``)."""
+
+    def __init__(self, ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None):
+        self.ex, self.ey, self.ez, self.N = ex, ey, ez, N
+        self.n = N + 1
+        self.E = ex * ey * ez
+        self.lo, self.hi = tuple(lo), tuple(hi)
+        keep = None
+        xyz = None
+        if node_xyz is not None:
+            import numpy as np
+            keep = np.ascontiguousarray(node_xyz, dtype=np.float64)
+            xyz = keep.ctypes.data
+        d = mesh_desc(ex, ey, ez, N, lo, hi, amp, xyz)
+        h = C.c_void_p()
+        check(lib().hs3d_mesh_create(C.byref(d), C.byref(h)))
+        self._h = h
+        del keep
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().hs3d_mesh_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.E, 5, self.n, self.n, self.n)
+
+    def info(self):
+        E, N, b = C.c_int64(), C.c_int(), C.c_size_t()
+        check(lib().hs3d_mesh_info(self._h, C.byref(E), C.byref(N), C.byref(b)))
+        return E.value, N.value, b.value
+
+    def empty_state(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    def geometry(self, stream=None):
+        import torch
+        n = self.n
+        X = torch.empty((self.E, 3, n, n, n), dtype=torch.float64, device="cuda")
+        Ja = torch.empty((self.E, 3, 3, n, n, n), dtype=torch.float64, device="cuda")
+        J = torch.empty((self.E, n, n, n), dtype=torch.float64, device="cuda")
+        check(lib().hs3d_mesh_geometry(self._h, _ptr(X), _ptr(Ja), _ptr(J), _stream(stream)))
+        return X, Ja, J
+
+    def init_state(self, u, kind="vortex", gamma=1.4, Ma=0.5, beta=5.0, xc=None, yc=None, t=0.0, stream=None):
+        if xc is None:
+            xc = 0.5 * (self.lo[0] + self.hi[0])
+        if yc is None:
+            yc = 0.5 * (self.lo[1] + self.hi[1])
+        ic = IC({"vortex": IC_VORTEX, "tgv": IC_TGV}[kind], gamma, Ma, beta, xc, yc, t)
+        check(lib().hs3d_init_state(self._h, C.byref(ic), _ptr(u, "u"), _stream(stream)))
+        return u
+
+    def residual(self, cfg: SolverCfg, u, dudt, stream=None):
+        check(lib().hs3d_residual(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(dudt, "dudt"), _stream(stream)))
+        return dudt
+
+    def rk3_step(self, cfg: SolverCfg, u, g, dt=0.0, stream=None):
+        check(lib().hs3d_rk3_step(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), _stream(stream)))
+
+    def rk3_run(self, cfg: SolverCfg, u, g, nsteps, dt=0.0, stream=None):
+        check(lib().hs3d_rk3_run(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), int(nsteps),
+                                 _stream(stream)))
+
+    def rk3_step_profiled(self, cfg: SolverCfg, u, g, dt=0.0, stream=None):
+        """One eager RK3 step with per-kernel event timing; returns
+        {"dt": ms, "grad": ms, "face": ms, "volume": ms, "step": ms}."""
+        ms = (C.c_double * 5)()
+        check(lib().hs3d_rk3_step_profiled(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), ms,
+                                           _stream(stream)))
+        return dict(zip(("dt", "grad", "face", "volume", "step"), list(ms)))
+
+    def dt(self, cfg: SolverCfg, u, out, stream=None):
+        check(lib().hs3d_dt(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(out, "dt_out"), _stream(stream)))
+        return out
+
+    def clock(self, reset=False, stream=None):
+        t, s = C.c_double(), C.c_int64()
+        check(lib().hs3d_clock(self._h, C.byref(t), C.byref(s), int(reset), _stream(stream)))
+        return t.value, s.value
+
+    def diagnostics(self, cfg: SolverCfg, u, out, dudt=None, stream=None):
+        check(lib().hs3d_diagnostics(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(dudt, "dudt"), _ptr(out, "out"),
+                                     _stream(stream)))
+        return out
+
+
+class Server:
+    """Continuous-batching solve server (hs3d_server_create / hs3d_submit / hs3d_poll)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_batch=0):
+        h = C.c_void_p()
+        check(lib().hs3d_server_create(int(hbm_budget_bytes), int(max_batch), C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hs3d_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, mesh: MeshDesc, cfg: SolverCfg, ic: IC, t_final=0.0, n_steps=0, result=None):
+        """Queue a solve; `result` (a C-contiguous float64 numpy array of
+        E*5*n^3 values) receives the final state.  Returns the ticket."""
+        ptr = None
+        if result is not None:
+            if not (result.flags["C_CONTIGUOUS"] and result.dtype.name == "float64"):
+                raise HS3DError(ERR_INVALID, "result must be a C-contiguous float64 array")
+            ptr = result.ctypes.data
+        req = Request(mesh, cfg, ic, float(t_final), int(n_steps), ptr)
+        t = C.c_uint64()
+        check(lib().hs3d_submit(self._h, C.byref(req), C.byref(t)))
+        self._keep[t.value] = result
+        return t.value
+
+    def poll(self, ticket):
+        """(status, Result): status is PENDING, OK or the request's error code."""
+        res = Result()
+        st = lib().hs3d_poll(self._h, C.c_uint64(ticket), C.byref(res))
+        if st != PENDING:
+            self._keep.pop(ticket, None)
+        return st, res
+
+    def stats(self):
+        q, r, f, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+        check(lib().hs3d_server_stats(self._h, C.byref(q), C.byref(r), C.byref(f), C.byref(b)))
+        return {"queued": q.value, "running": r.value, "finished": f.value, "bytes_in_use": b.value}
+
+
+def ic_desc(kind="vortex", gamma=1.4, Ma=0.5, beta=5.0, xc=5.0, yc=5.0, t=0.0) -> IC:
+    return IC({"vortex": IC_VORTEX, "tgv": IC_TGV}[kind], gamma, Ma, beta, xc, yc, t)
+
+
+def alu_peaks(stream=None):
+    """Measured FP64 and FP32 FMA throughput in TFLOP/s (hs3d_alu_peaks)."""
+    out = (C.c_double * 2)()
+    check(lib().hs3d_alu_peaks(out, _stream(stream)))
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1]}
+
+
+def version() -> str:
+    return lib().hs3d_version().decode()

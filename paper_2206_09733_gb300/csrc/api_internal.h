@@ -1,0 +1,45 @@
+// Host-side internals shared by api.cu and server.cu.
+#pragma once
+
+#include <stdarg.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+struct hs3d_mesh {
+    int ex = 0, ey = 0, ez = 0, N = 0, n = 0, n2 = 0, n3 = 0;
+    int E = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, amp = 0.0;
+    int device = 0;
+    double *X = nullptr, *Ja = nullptr, *J = nullptr, *invJ = nullptr, *fn = nullptr;
+    void *fstar = nullptr;          // scratch, sized for FP64
+    void *grad = nullptr;           // scratch, sized for FP64
+    hs3d::Clock *clk = nullptr;
+    double *diag_partials = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;  // private stream for set-up and graph capture
+    // graph cache of hs3d_rk3_run
+    std::mutex mu;
+    cudaGraphExec_t gexec = nullptr;
+    const double *g_u = nullptr;
+    const double *g_g = nullptr;
+    double g_dt = 0.0;
+    hs3d_solver_cfg g_cfg{};
+};
+
+namespace hs3d {
+
+hs3d_status fail(hs3d_status st, const char *fmt, ...);
+hs3d_status cuda_fail(cudaError_t e, const char *what);
+hs3d_status validate_cfg(const hs3d_solver_cfg *c);
+hs3d_status validate_desc(const hs3d_mesh_desc *d);
+hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out);
+void mesh_free(hs3d_mesh *m);
+size_t mesh_bytes(int N, long long E);
+Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, double *g, double *out);
+Batch single_batch(const Item &it);
+cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int stage, cudaStream_t s);
+cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt, cudaStream_t s);
+
+}  // namespace hs3d

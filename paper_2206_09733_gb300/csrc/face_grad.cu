@@ -1,0 +1,300 @@
+// Face Riemann solve and BR1 gradients.
+//
+// k_face: one thread per face node.  Gathers the two traces (Gauss-Lobatto
+// nodes include the element boundary, so the trace is the boundary node
+// itself), computes the inviscid numerical flux (LF, Roe or central EC,
+// Sec. 3.3) times the face scale and, for Navier-Stokes, subtracts the BR1
+// viscous flux (F_v(L) + F_v(R)).Sn/2.  Each face is solved once; both
+// elements read the result (with opposite sign on the -d side).
+//
+// k_grad: BR1 gradients of q = (v1, v2, v3, T), T = p/rho (Bassi & Rebay 1997):
+//   J grad q_c = sum_d D_d (Ja^d_c q) + sum_faces (1/w_end) (q* - q_in) (+-Ja^d_c),
+//   q* = (q_in + q_out)/2.  Element per thread group, node per thread.
+#include "internal.cuh"
+#include "physics.cuh"
+
+namespace hs3d {
+
+// Index of the node with index `end` along direction d and tangential (ta, tb).
+template <int n>
+__device__ __forceinline__ int face_node(int d, int end, int ta, int tb)
+{
+    if (d == 0) return end + n * (ta + n * tb);
+    if (d == 1) return ta + n * (end + n * tb);
+    return ta + n * (tb + n * end);
+}
+
+template <typename R>
+struct Side {
+    Prim<R> q;
+    R E;
+};
+
+template <int N, typename R, bool NS>
+__global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, int flux)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= b.total_faces * n2) return;
+    const long long gf = t / n2;
+    const int ab = (int)(t - gf * n2);
+    const Item &it = find_item_face(b, gf);
+    if (it.clk && it.clk->done) return;
+    const int E = it.E;
+    const int f = (int)(gf - it.face_begin);
+    const int d = f / E;
+    const int eL = f - d * E;
+    const int eR = nbr_plus(eL, d, it.ex, it.ey, it.ez);
+    const int ta = ab % n, tb = ab / n;
+    const int pL = face_node<n>(d, N, ta, tb), pR = face_node<n>(d, 0, ta, tb);
+    const double gm1d = it.gamma - 1.0;
+
+    double uL[5], uR[5];
+    const double *UL = it.u + (size_t)eL * 5 * n3 + pL;
+    const double *UR = it.u + (size_t)eR * 5 * n3 + pR;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        uL[v] = UL[v * n3];
+        uR[v] = UR[v * n3];
+    }
+    const Prim<R> qL = prim_from_u<R>(uL, gm1d), qR = prim_from_u<R>(uR, gm1d);
+    const double *Fn = it.fn + (size_t)f * 3 * n2 + ab;
+    const R s1 = (R)Fn[0], s2 = (R)Fn[n2], s3 = (R)Fn[2 * n2];
+    const R gam = (R)it.gamma, gm1 = (R)gm1d;
+    R fs[5];
+    if (flux == HS3D_FLUX_EC) {
+        flux_ec(ec_node(qL), ec_node(qR), gm1, s1, s2, s3, fs);
+    } else {
+        R ul[5], du[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            ul[v] = (R)uL[v];
+            du[v] = (R)(uR[v] - uL[v]);    // jump formed in FP64
+        }
+        R ur[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ur[v] = ul[v] + du[v];
+        if (flux == HS3D_FLUX_LF) flux_lf(qL, ul, qR, ur, gam, s1, s2, s3, fs);
+        else flux_roe(qL, ul, qR, ur, gam, s1, s2, s3, fs);
+    }
+    if (NS) {
+        const R *GL = (const R *)it.grad + (size_t)eL * 12 * n3 + pL;
+        const R *GR = (const R *)it.grad + (size_t)eR * 12 * n3 + pR;
+        R gl[12], gr[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            gl[k] = GL[k * n3];
+            gr[k] = GR[k * n3];
+        }
+        R fl[5], fr[5];
+        visc_flux(qL, gl, (R)it.mu, (R)it.kappa, s1, s2, s3, fl);
+        visc_flux(qR, gr, (R)it.mu, (R)it.kappa, s1, s2, s3, fr);
+#pragma unroll
+        for (int v = 1; v < 5; ++v) fs[v] -= (R)0.5 * (fl[v] + fr[v]);
+    }
+    R *out = (R *)it.fstar + (size_t)f * 5 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * n2] = fs[v];
+}
+
+// ------------------------------------------------------------------ BR1 gradients
+
+template <int N>
+constexpr int grad_threads()
+{
+    return ((N + 1) * (N + 1) * (N + 1) > 256) ? (N + 1) * (N + 1) * (N + 1) : 256;
+}
+
+template <int N, typename R>
+__global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constant__ Batch b, const Ops *__restrict__ ops)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sD = (R *)smem_raw;                      // n*n
+    R *sq = sD + ((n * n + 1) & ~1);            // [epb][4][n3]
+    const int epb = blockDim.x / n3;
+    R *sJa = sq + epb * 4 * n3;                 // [epb][9][n3]
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = (R)ops->D[t];
+    const double w0 = ops->w[0];
+    const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
+    const long long ge = blockIdx.x * (long long)epb + le;
+    bool valid = (le < epb) && ge < b.total_elems;
+    const Item *itp = nullptr;
+    int e = 0;
+    if (valid) {
+        itp = &find_item_elem(b, ge);
+        e = (int)(ge - itp->elem_begin);
+        if (itp->clk && itp->clk->done) valid = false;
+    }
+    R *q = sq + le * 4 * n3;
+    R *ja = sJa + le * 9 * n3;
+    double qin[4];
+    const double gm1 = valid ? itp->gamma - 1.0 : 0.4;
+    if (valid) {
+        const double *U = itp->u + (size_t)e * 5 * n3 + p;
+        double u[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
+        double ir = 1.0 / u[0];
+        qin[0] = u[1] * ir;
+        qin[1] = u[2] * ir;
+        qin[2] = u[3] * ir;
+        double pr = gm1 * (u[4] - 0.5 * (u[1] * qin[0] + u[2] * qin[1] + u[3] * qin[2]));
+        qin[3] = pr * ir;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) q[v * n3 + p] = (R)qin[v];
+        const double *JA = itp->Ja + (size_t)e * 9 * n3 + p;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ja[k * n3 + p] = (R)JA[k * n3];
+    }
+    __syncthreads();
+    if (!valid) return;
+    const int ijk[3] = {p % n, (p / n) % n, p / n2};
+    R acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = (R)0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+        const int base = p - ijk[d] * stride;
+        const R *Drow = sD + ijk[d] * n;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+            const int pm = base + m * stride;
+            const R Dm = Drow[m];
+            const R a1 = Dm * ja[(d * 3 + 0) * n3 + pm], a2 = Dm * ja[(d * 3 + 1) * n3 + pm],
+                    a3 = Dm * ja[(d * 3 + 2) * n3 + pm];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const R qv = q[v * n3 + pm];
+                acc[v * 3 + 0] += a1 * qv;
+                acc[v * 3 + 1] += a2 * qv;
+                acc[v * 3 + 2] += a3 * qv;
+            }
+        }
+    }
+    // surface lifting of the BR1 jumps
+    const Item &it = *itp;
+    const R iw = (R)(1.0 / w0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int end = side ? N : 0;
+            if (ijk[d] != end) continue;
+            const int nb = side ? nbr_plus(e, d, it.ex, it.ey, it.ez) : nbr_minus(e, d, it.ex, it.ey, it.ez);
+            const int ta = (d == 0) ? ijk[1] : ijk[0];
+            const int tb = (d == 2) ? ijk[1] : ijk[2];
+            const int pn = face_node<n>(d, side ? 0 : N, ta, tb);
+            const double *U = it.u + (size_t)nb * 5 * n3 + pn;
+            double u[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
+            double ir = 1.0 / u[0];
+            double qo[4];
+            qo[0] = u[1] * ir;
+            qo[1] = u[2] * ir;
+            qo[2] = u[3] * ir;
+            qo[3] = gm1 * (u[4] - 0.5 * (u[1] * qo[0] + u[2] * qo[1] + u[3] * qo[2])) * ir;
+            const R sg = side ? (R)1 : (R)-1;
+            const R n1 = sg * ja[(d * 3 + 0) * n3 + p], n2_ = sg * ja[(d * 3 + 1) * n3 + p],
+                    n3_ = sg * ja[(d * 3 + 2) * n3 + p];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const R j = (R)(0.5 * (qo[v] - qin[v])) * iw;
+                acc[v * 3 + 0] += j * n1;
+                acc[v * 3 + 1] += j * n2_;
+                acc[v * 3 + 2] += j * n3_;
+            }
+        }
+    }
+    const R ij = (R)it.invJ[(size_t)e * n3 + p];
+    R *G = (R *)it.grad + (size_t)e * 12 * n3 + p;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) G[k * n3] = acc[k] * ij;
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <int N, typename R>
+static cudaError_t face_launch(int physics, int flux, const Batch &b, cudaStream_t s)
+{
+    constexpr int n2 = (N + 1) * (N + 1);
+    long long total = b.total_faces * n2;
+    if (total == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (physics == HS3D_NS) k_face<N, R, true><<<blocks, 256, 0, s>>>(b, flux);
+    else k_face<N, R, false><<<blocks, 256, 0, s>>>(b, flux);
+    return cudaGetLastError();
+}
+
+template <int N, typename R>
+static cudaError_t grad_launch(const Batch &b, cudaStream_t s)
+{
+    constexpr int n = N + 1, n3 = n * n * n;
+    if (b.total_elems == 0) return cudaSuccess;
+    int epb = elems_per_block(N, 0);
+    int threads = epb * n3;
+    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * 13 * n3);
+    unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
+    const Ops *ops = device_ops(N);
+    if (!ops) return cudaErrorMemoryAllocation;
+    k_grad<N, R><<<blocks, threads, smem, s>>>(b, ops);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t prep_grad()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_grad<N, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_grad<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return e;
+}
+
+#define HS3D_SWITCH_N(CALL_N)                 \
+    switch (N) {                              \
+        case 1: return CALL_N(1);             \
+        case 2: return CALL_N(2);             \
+        case 3: return CALL_N(3);             \
+        case 4: return CALL_N(4);             \
+        case 5: return CALL_N(5);             \
+        case 6: return CALL_N(6);             \
+        case 7: return CALL_N(7);             \
+        default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t prepare_grad(int N)
+{
+#define P(K) prep_grad<K>()
+    HS3D_SWITCH_N(P)
+#undef P
+}
+
+cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, cudaStream_t s)
+{
+#define F64(K) face_launch<K, double>(physics, flux, b, s)
+#define F32(K) face_launch<K, float>(physics, flux, b, s)
+    if (prec == HS3D_FP64) {
+        HS3D_SWITCH_N(F64)
+    } else {
+        HS3D_SWITCH_N(F32)
+    }
+#undef F64
+#undef F32
+}
+
+cudaError_t launch_grad(int N, int prec, const Batch &b, cudaStream_t s)
+{
+#define G64(K) grad_launch<K, double>(b, s)
+#define G32(K) grad_launch<K, float>(b, s)
+    if (prec == HS3D_FP64) {
+        HS3D_SWITCH_N(G64)
+    } else {
+        HS3D_SWITCH_N(G32)
+    }
+#undef G64
+#undef G32
+}
+
+}  // namespace hs3d

@@ -1,0 +1,269 @@
+// Gauss-Lobatto operators, mesh geometry and initial conditions.
+//
+// Geometry (Sec. 3.3): node coordinates of a periodic box with an optional
+// smooth perturbation, the Jacobian J = det(dX/dxi) and the metric terms in
+// the conservative curl form (Kopriva 2006), which satisfy the discrete
+// metric identity sum_d D_d Ja^d = 0 and so preserve a free stream on curved
+// elements:
+//   Ja^i_c = D_{i+2}(X_l D_{i+1} X_m) - D_{i+1}(X_l D_{i+2} X_m),  (c,m,l) cyclic.
+// All in FP64, one CTA per element, one thread per node.
+#include <math.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hs3d {
+
+// ---------------------------------------------------------------- 1-D operators
+
+// L_{N-1}(x), L_N(x), L_{N+1}(x) by the three-term recurrence.
+static void legendre3(int N, double x, double &Lm, double &L, double &Lp)
+{
+    double lkm1 = 1.0, lk = x, lkm2 = 0.0;   // L_{k-1}, L_k, L_{k-2} for k = 1
+    for (int k = 1; k <= N; ++k) {
+        double lkp1 = ((2.0 * k + 1.0) * x * lk - k * lkm1) / (k + 1.0);
+        lkm2 = lkm1;
+        lkm1 = lk;
+        lk = lkp1;
+    }
+    Lm = lkm2;   // L_{N-1}
+    L = lkm1;    // L_N
+    Lp = lk;     // L_{N+1}
+}
+
+static Ops make_ops(int N)
+{
+    Ops o{};
+    int n = N + 1;
+    // Nodes: roots of q = L_{N+1} - L_{N-1}, q' = (2N+1) L_N (Newton from
+    // Chebyshev-Gauss-Lobatto points), symmetrised.
+    for (int j = 0; j < n; ++j) {
+        double x = -cos(M_PI * j / N);
+        if (j == 0) x = -1.0;
+        if (j == N) x = 1.0;
+        if (j != 0 && j != N) {
+            for (int it = 0; it < 200; ++it) {
+                double Lm, L, Lp;
+                legendre3(N, x, Lm, L, Lp);
+                double dx = (Lp - Lm) / ((2.0 * N + 1.0) * L);
+                x -= dx;
+                if (fabs(dx) <= 1e-17) break;
+            }
+        }
+        o.xi[j] = x;
+    }
+    for (int j = 0; j < n / 2; ++j) {
+        double s = 0.5 * (o.xi[N - j] - o.xi[j]);
+        o.xi[j] = -s;
+        o.xi[N - j] = s;
+    }
+    if (n % 2) o.xi[N / 2] = 0.0;
+    double LN[kMaxn];
+    for (int j = 0; j < n; ++j) {
+        double Lm, L, Lp;
+        legendre3(N, o.xi[j], Lm, L, Lp);
+        LN[j] = L;
+        o.w[j] = 2.0 / (N * (N + 1.0) * L * L);
+    }
+    // Derivative matrix in the closed form for Gauss-Lobatto nodes:
+    //   D_ij = L_N(x_i) / (L_N(x_j) (x_i - x_j)), i != j;
+    //   D_00 = -N(N+1)/4, D_NN = N(N+1)/4, other diagonal entries 0.
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v;
+            if (i != j) v = LN[i] / (LN[j] * (o.xi[i] - o.xi[j]));
+            else if (i == 0) v = -0.25 * N * (N + 1.0);
+            else if (i == N) v = 0.25 * N * (N + 1.0);
+            else v = 0.0;
+            o.D[i * n + j] = v;
+            o.Df[i * n + j] = (float)v;
+        }
+    return o;
+}
+
+const Ops &host_ops(int N)
+{
+    static std::mutex mu;
+    static std::map<int, Ops> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(N);
+    if (it == cache.end()) it = cache.emplace(N, make_ops(N)).first;
+    return it->second;
+}
+
+const Ops *device_ops(int N)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, Ops *> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    const Ops &h = host_ops(N);
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(dev, N);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    Ops *d = nullptr;
+    if (cudaMalloc(&d, sizeof(Ops)) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, &h, sizeof(Ops), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    cache[key] = d;
+    return d;
+}
+
+// ---------------------------------------------------------------- geometry kernel
+
+template <int N>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
+k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, double lo1, double lo2, double hi0,
+           double hi1, double hi2, double amp, const Ops *__restrict__ ops, double *__restrict__ X,
+           double *__restrict__ Ja, double *__restrict__ J, double *__restrict__ invJ, double *__restrict__ fn)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    __shared__ double sD[n * n];
+    __shared__ double sX[3][n3];
+    __shared__ double sT[2][n3];
+    const int e = blockIdx.x;
+    const int E = ex * ey * ez;
+    const int p = threadIdx.x;
+    const int ijk[3] = {p % n, (p / n) % n, p / n2};
+    for (int t = p; t < n * n; t += n3) sD[t] = ops->D[t];
+    const double lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
+    const int ab[3] = {e % ex, (e / ex) % ey, e / (ex * ey)};
+    const int Ed[3] = {ex, ey, ez};
+    double x[3];
+    if (xyz) {
+        for (int c = 0; c < 3; ++c) x[c] = xyz[((size_t)e * 3 + c) * n3 + p];
+    } else {
+        double th[3];
+        for (int c = 0; c < 3; ++c) {
+            double L = hi[c] - lo[c];
+            double h = L / Ed[c];
+            x[c] = lo[c] + h * (ab[c] + 0.5 * (ops->xi[ijk[c]] + 1.0));
+            th[c] = -M_PI + 2.0 * M_PI * (x[c] - lo[c]) / L;
+        }
+        double s = sin(th[0]) * sin(th[1]) * sin(th[2]);
+        for (int c = 0; c < 3; ++c) x[c] += amp * ((hi[c] - lo[c]) / (2.0 * M_PI)) * s;
+    }
+    for (int c = 0; c < 3; ++c) sX[c][p] = x[c];
+    __syncthreads();
+
+    // a[d][c] = dX_c/dxi_d at this node
+    auto deriv = [&](const double *f, int d) {
+        double acc = 0.0;
+        const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+        const int base = p - ijk[d] * stride;
+        const double *Drow = sD + ijk[d] * n;
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += Drow[m] * f[base + m * stride];
+        return acc;
+    };
+    double a[3][3];
+    for (int d = 0; d < 3; ++d)
+        for (int c = 0; c < 3; ++c) a[d][c] = deriv(sX[c], d);
+    double Jp = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) + a[0][1] * (a[1][2] * a[2][0] - a[1][0] * a[2][2]) +
+                a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    J[(size_t)e * n3 + p] = Jp;
+    invJ[(size_t)e * n3 + p] = 1.0 / Jp;
+    for (int c = 0; c < 3; ++c) X[((size_t)e * 3 + c) * n3 + p] = x[c];
+
+    for (int i = 0; i < 3; ++i) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        for (int c = 0; c < 3; ++c) {
+            const int m = (c + 1) % 3, l = (c + 2) % 3;
+            __syncthreads();
+            sT[0][p] = x[l] * a[i1][m];
+            sT[1][p] = x[l] * a[i2][m];
+            __syncthreads();
+            double v = deriv(sT[0], i2) - deriv(sT[1], i1);
+            Ja[(((size_t)e * 3 + i) * 3 + c) * n3 + p] = v;
+            if (ijk[i] == N) {
+                // tangential (a,b) index of this node on the +i face
+                int ta = (i == 0) ? ijk[1] : ijk[0];
+                int tb = (i == 2) ? ijk[1] : ijk[2];
+                fn[(((size_t)i * E + e) * 3 + c) * n2 + ta + n * tb] = v;
+            }
+        }
+    }
+}
+
+cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
+                            const double *hi, double amp, double *X, double *Ja, double *J, double *invJ,
+                            double *fn, cudaStream_t s)
+{
+    const Ops *ops = device_ops(N);
+    if (!ops) return cudaErrorMemoryAllocation;
+    int E = ex * ey * ez;
+    int n3 = (N + 1) * (N + 1) * (N + 1);
+#define HS3D_GEO(NN)                                                                                            \
+    case NN:                                                                                                    \
+        k_geometry<NN><<<E, n3, 0, s>>>(node_xyz_dev, ex, ey, ez, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], amp, \
+                                        ops, X, Ja, J, invJ, fn);                                               \
+        break;
+    switch (N) {
+        HS3D_GEO(1) HS3D_GEO(2) HS3D_GEO(3) HS3D_GEO(4) HS3D_GEO(5) HS3D_GEO(6) HS3D_GEO(7)
+        default: return cudaErrorInvalidValue;
+    }
+#undef HS3D_GEO
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- initial conditions
+
+// Isentropic vortex (Shu) and Taylor-Green vortex at the mesh nodes.
+__global__ void k_init_state(int n3, long long total, const double *__restrict__ X, hs3d_ic ic, double Lx, double Ly,
+                             double *__restrict__ u)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    long long e = t / n3;
+    int p = (int)(t % n3);
+    double x = X[(e * 3 + 0) * n3 + p], y = X[(e * 3 + 1) * n3 + p], z = X[(e * 3 + 2) * n3 + p];
+    double g = ic.gamma;
+    double rho, v1, v2, v3, pr;
+    if (ic.kind == HS3D_IC_VORTEX) {
+        double uinf = ic.Ma * sqrt(g);
+        double dx = x - (ic.xc + uinf * ic.t), dy = y - ic.yc;
+        dx -= Lx * floor(dx / Lx + 0.5);
+        dy -= Ly * floor(dy / Ly + 0.5);
+        double r2 = dx * dx + dy * dy;
+        double ex = exp(0.5 * (1.0 - r2));
+        double k = ic.beta / (2.0 * M_PI);
+        v1 = uinf - k * ex * dy;
+        v2 = k * ex * dx;
+        v3 = 0.0;
+        double T = 1.0 - (g - 1.0) * ic.beta * ic.beta / (8.0 * g * M_PI * M_PI) * ex * ex;
+        rho = pow(T, 1.0 / (g - 1.0));
+        pr = rho * T;
+    } else {
+        double p0 = 1.0 / (g * ic.Ma * ic.Ma);
+        v1 = sin(x) * cos(y) * cos(z);
+        v2 = -cos(x) * sin(y) * cos(z);
+        v3 = 0.0;
+        pr = p0 + (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0) * (1.0 / 16.0);
+        rho = pr / p0;
+    }
+    double *ue = u + e * 5 * n3 + p;
+    ue[0] = rho;
+    ue[n3] = rho * v1;
+    ue[2 * n3] = rho * v2;
+    ue[3 * n3] = rho * v3;
+    ue[4 * n3] = pr / (g - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3);
+}
+
+cudaError_t launch_init_state(int N, int E, const double *X, const hs3d_ic &ic, const double *lo, const double *hi,
+                              double *u, cudaStream_t s)
+{
+    int n3 = (N + 1) * (N + 1) * (N + 1);
+    long long total = (long long)E * n3;
+    int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    k_init_state<<<(unsigned)blocks, threads, 0, s>>>(n3, total, X, ic, hi[0] - lo[0], hi[1] - lo[1], u);
+    return cudaGetLastError();
+}
+
+}  // namespace hs3d

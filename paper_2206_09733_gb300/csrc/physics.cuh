@@ -1,0 +1,220 @@
+// Point-wise physics of the compressible Euler / Navier-Stokes equations,
+// templated on the arithmetic type R (double, or float in the mixed path).
+//
+//   conserved u = (rho, rho v, rho e), p = (gamma-1)(rho e - rho|v|^2/2)
+//   Euler flux F_e.a = (rho v.a, rho v v.a + p a, (rho e + p) v.a)      (Sec. 3.2)
+//   viscous flux with tau = mu(grad v + grad v^T) - 2/3 mu I div v and the
+//   heat flux kappa grad T                                             (Sec. 3.2, Eq. viscousfluxes)
+//   surface fluxes Lax-Friedrichs, Roe, central EC (Sec. 3.3 list)
+//   Chandrashekar two-point flux (Sec. 3.5)
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hs3d {
+
+template <typename R>
+struct Prim {
+    R rho, v1, v2, v3, p;
+};
+
+// Primitive variables computed in FP64 from the FP64 state (the subtraction
+// rho e - rho|v|^2/2 cancels at low Mach), then rounded to R.
+template <typename R>
+__device__ __forceinline__ Prim<R> prim_from_u(const double u[5], double gm1)
+{
+    double ir = 1.0 / u[0];
+    double v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
+    double p = gm1 * (u[4] - 0.5 * (u[1] * v1 + u[2] * v2 + u[3] * v3));
+    Prim<R> q;
+    q.rho = (R)u[0];
+    q.v1 = (R)v1;
+    q.v2 = (R)v2;
+    q.v3 = (R)v3;
+    q.p = (R)p;
+    return q;
+}
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_(R x);
+template <>
+__device__ __forceinline__ double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+template <typename R>
+__device__ __forceinline__ R log_(R x);
+template <>
+__device__ __forceinline__ double log_<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float log_<float>(float x) { return logf(x); }
+
+// Euler flux dotted with a (any vector); E = rho e.
+template <typename R>
+__device__ __forceinline__ void euler_flux(const Prim<R> &q, R E, R a1, R a2, R a3, R f[5])
+{
+    R va = q.v1 * a1 + q.v2 * a2 + q.v3 * a3;
+    R m = q.rho * va;
+    f[0] = m;
+    f[1] = m * q.v1 + q.p * a1;
+    f[2] = m * q.v2 + q.p * a2;
+    f[3] = m * q.v3 + q.p * a3;
+    f[4] = (E + q.p) * va;
+}
+
+// Viscous flux dotted with a.  G[v*3 + c] = d q_v / d x_c for q = (v1,v2,v3,T).
+template <typename R>
+__device__ __forceinline__ void visc_flux(const Prim<R> &q, const R G[12], R mu, R kappa, R a1, R a2, R a3,
+                                          R f[5])
+{
+    R div = G[0] + G[4] + G[8];
+    R l = (R)(2.0 / 3.0) * mu * div;
+    R t11 = mu * (G[0] + G[0]) - l;
+    R t22 = mu * (G[4] + G[4]) - l;
+    R t33 = mu * (G[8] + G[8]) - l;
+    R t12 = mu * (G[1] + G[3]);
+    R t13 = mu * (G[2] + G[6]);
+    R t23 = mu * (G[5] + G[7]);
+    R s1 = t11 * a1 + t12 * a2 + t13 * a3;
+    R s2 = t12 * a1 + t22 * a2 + t23 * a3;
+    R s3 = t13 * a1 + t23 * a2 + t33 * a3;
+    f[0] = (R)0;
+    f[1] = s1;
+    f[2] = s2;
+    f[3] = s3;
+    f[4] = q.v1 * s1 + q.v2 * s2 + q.v3 * s3 + kappa * (G[9] * a1 + G[10] * a2 + G[11] * a3);
+}
+
+// Lax-Friedrichs flux times the face scale s = |Sn|, Sn the scaled normal
+// pointing from L to R:  s [ (F_L + F_R).n/2 - lambda (u_R - u_L)/2 ],
+// lambda = max(|v_L.n| + c_L, |v_R.n| + c_R).
+template <typename R>
+__device__ __forceinline__ void flux_lf(const Prim<R> &L, const R uL[5], const Prim<R> &Rr, const R uR[5], R gamma,
+                                        R s1, R s2, R s3, R f[5])
+{
+    R s = sqrt(s1 * s1 + s2 * s2 + s3 * s3);
+    R fl[5], fr[5];
+    euler_flux(L, uL[4], s1, s2, s3, fl);
+    euler_flux(Rr, uR[4], s1, s2, s3, fr);
+    R vnL = fabs(L.v1 * s1 + L.v2 * s2 + L.v3 * s3) + s * sqrt(gamma * L.p / L.rho);
+    R vnR = fabs(Rr.v1 * s1 + Rr.v2 * s2 + Rr.v3 * s3) + s * sqrt(gamma * Rr.p / Rr.rho);
+    R lam = fmax(vnL, vnR);    // = s * lambda
+#pragma unroll
+    for (int v = 0; v < 5; ++v) f[v] = (R)0.5 * (fl[v] + fr[v]) - (R)0.5 * lam * (uR[v] - uL[v]);
+}
+
+// Roe flux times the face scale (Roe 1981, sqrt(rho)-weighted averages, no
+// entropy fix): s [ (F_L + F_R).n/2 - sum_k |lambda_k| alpha_k r_k / 2 ].
+template <typename R>
+__device__ __forceinline__ void flux_roe(const Prim<R> &L, const R uL[5], const Prim<R> &Rr, const R uR[5], R gamma,
+                                         R s1, R s2, R s3, R f[5])
+{
+    R s = sqrt(s1 * s1 + s2 * s2 + s3 * s3);
+    R is = (R)1 / s;
+    R n1 = s1 * is, n2 = s2 * is, n3 = s3 * is;
+    R fl[5], fr[5];
+    euler_flux(L, uL[4], s1, s2, s3, fl);
+    euler_flux(Rr, uR[4], s1, s2, s3, fr);
+    R sl = sqrt(L.rho), sr = sqrt(Rr.rho);
+    R iw = (R)1 / (sl + sr);
+    R HL = (uL[4] + L.p) / L.rho, HR = (uR[4] + Rr.p) / Rr.rho;
+    R vt1 = (sl * L.v1 + sr * Rr.v1) * iw;
+    R vt2 = (sl * L.v2 + sr * Rr.v2) * iw;
+    R vt3 = (sl * L.v3 + sr * Rr.v3) * iw;
+    R Ht = (sl * HL + sr * HR) * iw;
+    R q2 = vt1 * vt1 + vt2 * vt2 + vt3 * vt3;
+    R c2 = (gamma - (R)1) * (Ht - (R)0.5 * q2);
+    R ct = sqrt(c2);
+    R ic2 = (R)1 / c2;
+    R rt = sl * sr;
+    R vnt = vt1 * n1 + vt2 * n2 + vt3 * n3;
+    R dr = Rr.rho - L.rho, dp = Rr.p - L.p;
+    R d1 = Rr.v1 - L.v1, d2 = Rr.v2 - L.v2, d3 = Rr.v3 - L.v3;
+    R dvn = d1 * n1 + d2 * n2 + d3 * n3;
+    R a1 = (dp - rt * ct * dvn) * (R)0.5 * ic2;
+    R a5 = (dp + rt * ct * dvn) * (R)0.5 * ic2;
+    R a2 = dr - dp * ic2;
+    R sh1 = rt * (d1 - dvn * n1), sh2 = rt * (d2 - dvn * n2), sh3 = rt * (d3 - dvn * n3);
+    R l1 = fabs(vnt - ct) * a1, l2 = fabs(vnt), l5 = fabs(vnt + ct) * a5;
+    R W0 = l1 + l2 * a2 + l5;
+    R W1 = l1 * (vt1 - ct * n1) + l2 * (a2 * vt1 + sh1) + l5 * (vt1 + ct * n1);
+    R W2 = l1 * (vt2 - ct * n2) + l2 * (a2 * vt2 + sh2) + l5 * (vt2 + ct * n2);
+    R W3 = l1 * (vt3 - ct * n3) + l2 * (a2 * vt3 + sh3) + l5 * (vt3 + ct * n3);
+    R W4 = l1 * (Ht - ct * vnt) + l2 * (a2 * (R)0.5 * q2 + vt1 * sh1 + vt2 * sh2 + vt3 * sh3) + l5 * (Ht + ct * vnt);
+    R hs = (R)0.5 * s;
+    f[0] = (R)0.5 * (fl[0] + fr[0]) - hs * W0;
+    f[1] = (R)0.5 * (fl[1] + fr[1]) - hs * W1;
+    f[2] = (R)0.5 * (fl[2] + fr[2]) - hs * W2;
+    f[3] = (R)0.5 * (fl[3] + fr[3]) - hs * W3;
+    f[4] = (R)0.5 * (fl[4] + fr[4]) - hs * W4;
+}
+
+template <typename R>
+struct LogMeanEps;
+template <>
+struct LogMeanEps<double> {
+    static constexpr double v = 1e-4;
+};
+template <>
+struct LogMeanEps<float> {
+    static constexpr float v = 1e-2f;
+};
+
+// Logarithmic mean (a-b)/(ln a - ln b) from precomputed logarithms; near
+// a = b the series (a+b)/(2(1 + u/3 + u^2/5 + u^3/7)), u = ((a-b)/(a+b))^2
+// (Ismail & Roe) avoids the 0/0.
+template <typename R>
+__device__ __forceinline__ R log_mean(R a, R b, R la, R lb)
+{
+    R d = a - b, sum = a + b;
+    R f = d / sum;
+    R u = f * f;
+    if (u < LogMeanEps<R>::v) {
+        R F = (R)1 + u * ((R)(1.0 / 3.0) + u * ((R)0.2 + u * (R)(1.0 / 7.0)));
+        return sum / ((R)2 * F);
+    }
+    return d / (la - lb);
+}
+
+// Per-node quantities the Chandrashekar flux uses.
+template <typename R>
+struct ECNode {
+    R rho, v1, v2, v3, beta, lrho, lbeta;
+};
+
+template <typename R>
+__device__ __forceinline__ ECNode<R> ec_node(const Prim<R> &q)
+{
+    ECNode<R> z;
+    z.rho = q.rho;
+    z.v1 = q.v1;
+    z.v2 = q.v2;
+    z.v3 = q.v3;
+    z.beta = q.rho / ((R)2 * q.p);
+    z.lrho = log_(q.rho);
+    z.lbeta = log_(z.beta);
+    return z;
+}
+
+// Chandrashekar's entropy-conservative, kinetic-energy-preserving flux dotted
+// with a:  beta = rho/(2p), rho^ and beta^ logarithmic means, {.} arithmetic
+// means, p~ = {rho}/(2{beta}),
+//   f_rho = rho^ {v}.a,  f_m = f_rho {v} + p~ a,
+//   f_E = f_rho (1/(2(gamma-1) beta^) - {|v|^2}/2) + {v}.f_m.
+template <typename R>
+__device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr, R gm1, R a1, R a2, R a3, R f[5])
+{
+    R rho_ln = log_mean(L.rho, Rr.rho, L.lrho, Rr.lrho);
+    R beta_ln = log_mean(L.beta, Rr.beta, L.lbeta, Rr.lbeta);
+    R m1 = (R)0.5 * (L.v1 + Rr.v1), m2 = (R)0.5 * (L.v2 + Rr.v2), m3 = (R)0.5 * (L.v3 + Rr.v3);
+    R v2 = (R)0.5 * ((L.v1 * L.v1 + L.v2 * L.v2 + L.v3 * L.v3) + (Rr.v1 * Rr.v1 + Rr.v2 * Rr.v2 + Rr.v3 * Rr.v3));
+    R pt = (L.rho + Rr.rho) / ((R)2 * (L.beta + Rr.beta));
+    R fr = rho_ln * (m1 * a1 + m2 * a2 + m3 * a3);
+    f[0] = fr;
+    f[1] = fr * m1 + pt * a1;
+    f[2] = fr * m2 + pt * a2;
+    f[3] = fr * m3 + pt * a3;
+    f[4] = fr * ((R)1 / ((R)2 * gm1 * beta_ln) - (R)0.5 * v2) + m1 * f[1] + m2 * f[2] + m3 * f[3];
+}
+
+}  // namespace hs3d

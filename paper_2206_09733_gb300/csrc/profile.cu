@@ -1,0 +1,114 @@
+// Instrumentation entry points: per-kernel timing of one RK3 step and
+// FMA-chain measurements of the FP64 / FP32 arithmetic peaks.
+#include <string.h>
+
+#include "api_internal.h"
+
+namespace hs3d {
+
+// Independent FMA chains per thread, long enough to hide the pipe latency.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chain(T *out, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == (T)12345.678) out[threadIdx.x] = s;   // keep the chains alive
+}
+
+template <typename T>
+static double fma_tflops(int sms, int iters, cudaStream_t s, cudaError_t &err)
+{
+    T *out = nullptr;
+    err = cudaMalloc(&out, 256 * sizeof(T));
+    if (err != cudaSuccess) return 0.0;
+    int blocks = sms * 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma_chain<T><<<blocks, 256, 0, s>>>(out, iters / 4, (T)0.999, (T)0.001);   // warm-up
+    cudaEventRecord(e0, s);
+    k_fma_chain<T><<<blocks, 256, 0, s>>>(out, iters, (T)0.999, (T)0.001);
+    cudaEventRecord(e1, s);
+    err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    double flops = 2.0 * 8.0 * (double)iters * blocks * 256.0;
+    return flops / (ms * 1e-3) / 1e12;
+}
+
+}  // namespace hs3d
+
+using namespace hs3d;
+
+extern "C" {
+
+hs3d_status hs3d_alu_peaks(double *tflops_out, void *stream)
+{
+    if (!tflops_out) return fail(HS3D_ERR_INVALID, "tflops_out is NULL");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    cudaStream_t s = (cudaStream_t)stream;
+    tflops_out[0] = fma_tflops<double>(sms, 1 << 12, s, e);
+    if (e == cudaSuccess) tflops_out[1] = fma_tflops<float>(sms, 1 << 16, s, e);
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "fma chain kernel");
+}
+
+hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c, double *u, double *g, double dt,
+                                   double *ms_out, void *stream)
+{
+    if (!m || !ms_out) return fail(HS3D_ERR_INVALID, "mesh or ms_out is NULL");
+    hs3d_status st = validate_cfg(c);
+    if (st != HS3D_OK) return st;
+    if (!u || !g || u == g) return fail(HS3D_ERR_INVALID, "bad u/g");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int NEV = 12;
+    cudaEvent_t ev[NEV];
+    for (int k = 0; k < NEV; ++k) cudaEventCreate(&ev[k]);
+    Batch b = single_batch(make_item(m, c, u, g, nullptr));
+    b.dt_fixed = dt > 0.0 ? dt : 0.0;
+    cudaError_t e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess && !(dt > 0.0)) e = launch_lambda(m->N, c->physics, b, s);
+    if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    int k = 2;
+    for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+        if (c->physics == HS3D_NS) e = launch_grad(m->N, c->precision, b, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
+        if (e == cudaSuccess) e = launch_face(m->N, c->precision, c->physics, c->surface_flux, b, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
+        if (e == cudaSuccess) e = launch_volume(m->N, c->precision, c->physics, c->volume_form, b, stage, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[k - 1]);
+    if (e == cudaSuccess) {
+        float t;
+        memset(ms_out, 0, sizeof(double) * 5);
+        cudaEventElapsedTime(&t, ev[0], ev[1]);
+        ms_out[0] = t;
+        for (int stage = 0; stage < 3; ++stage) {
+            for (int part = 0; part < 3; ++part) {
+                cudaEventElapsedTime(&t, ev[1 + stage * 3 + part], ev[2 + stage * 3 + part]);
+                ms_out[1 + part] += t;
+            }
+        }
+        cudaEventElapsedTime(&t, ev[0], ev[k - 1]);
+        ms_out[4] = t;
+    }
+    for (int j = 0; j < NEV; ++j) cudaEventDestroy(ev[j]);
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "profiled step");
+}
+
+}  // extern "C"

@@ -1,0 +1,462 @@
+// Continuous-batching server: many independent solves share the GPU.
+//
+// A host thread runs this loop:
+//   1. admit queued requests (FIFO) while the device-memory budget has room:
+//      build the request's mesh, allocate its state, evaluate its initial
+//      condition and arm its clock (t_final or n_steps);
+//   2. group the running requests by (N, physics, surface flux, volume form,
+//      precision) and advance every group by one RK3 step with shared
+//      launches: each kernel walks a table of items (one per request), so one
+//      launch covers all requests of a group;
+//   3. gather the clocks of all running requests into one small array, copy
+//      it to pinned host memory and wait for it with a bounded poll;
+//   4. retire finished requests (copy the state out, free the slot, stamp the
+//      time) and go back to 1, so new requests join as soon as memory frees.
+// Every element's arithmetic depends only on its own request, and the dt
+// maxima are exact, so a request's result is the same alone and in any mix.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace hs3d {
+
+struct ClockView {
+    double t;
+    long long step;
+    int done;
+    int bad;
+};
+
+__global__ void k_gather_clocks(const Item *items, int n, ClockView *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Clock *c = items[i].clk;
+    out[i].t = c->t;
+    out[i].step = c->step;
+    out[i].done = c->done;
+    out[i].bad = c->bad;
+}
+
+enum ReqState { Q_QUEUED, Q_RUNNING, Q_DONE };
+
+struct ServerReq {
+    uint64_t id = 0;
+    hs3d_request req{};
+    std::vector<double> xyz;   // private copy of node coordinates, if given
+    ReqState state = Q_QUEUED;
+    hs3d_result res{};
+    hs3d_mesh *mesh = nullptr;
+    double *u = nullptr, *g = nullptr;
+    size_t bytes = 0;
+};
+
+static size_t request_bytes(const hs3d_request &r)
+{
+    long long E = (long long)r.mesh.ex * r.mesh.ey * r.mesh.ez;
+    long long n3 = (long long)(r.mesh.N + 1) * (r.mesh.N + 1) * (r.mesh.N + 1);
+    return mesh_bytes(r.mesh.N, E) + 2 * sizeof(double) * (size_t)E * 5 * n3;
+}
+
+}  // namespace hs3d
+
+using namespace hs3d;
+
+struct hs3d_server {
+    int device = 0;
+    size_t budget = 0, in_use = 0;
+    int max_batch = 256;
+    double wait_limit_s = 120.0;
+    int fault_alloc = 0;   // host-side fault injection: fail the next admissions' allocation
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    uint64_t next_id = 1;
+    std::deque<ServerReq *> queue;
+    std::vector<ServerReq *> running;
+    std::unordered_map<uint64_t, ServerReq *> all;
+    int64_t finished = 0;
+    std::thread th;
+    cudaStream_t stream = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    // per-group device item tables and the clock gather buffers
+    Item *d_items = nullptr;
+    int d_items_cap = 0;
+    ClockView *d_clk = nullptr, *h_clk = nullptr;
+    int clk_cap = 0;
+    cudaEvent_t ev = nullptr;
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace hs3d {
+
+static void release(hs3d_server *S, ServerReq *r)
+{
+    if (r->u) cudaFree(r->u);
+    if (r->g) cudaFree(r->g);
+    if (r->mesh) mesh_free(r->mesh);
+    r->u = r->g = nullptr;
+    r->mesh = nullptr;
+    S->in_use -= r->bytes;
+}
+
+// Build the request's slot.  Returns HS3D_OK, HS3D_ERR_NOMEM (retry later) or another error (fail it).
+static hs3d_status admit(hs3d_server *S, ServerReq *r)
+{
+    if (S->fault_alloc > 0) {
+        S->fault_alloc--;
+        return fail(HS3D_ERR_NOMEM, "injected allocation failure");
+    }
+    hs3d_mesh_desc d = r->req.mesh;
+    d.node_xyz = r->xyz.empty() ? nullptr : r->xyz.data();
+    hs3d_status st = mesh_build(&d, &r->mesh);
+    if (st != HS3D_OK) return st;
+    size_t sz = sizeof(double) * (size_t)r->mesh->E * 5 * r->mesh->n3;
+    cudaError_t e = cudaMalloc(&r->u, sz);
+    if (e == cudaSuccess) e = cudaMalloc(&r->g, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (r->u) cudaFree(r->u);
+        r->u = nullptr;
+        mesh_free(r->mesh);
+        r->mesh = nullptr;
+        return fail(HS3D_ERR_NOMEM, "state allocation failed");
+    }
+    e = launch_init_state(r->mesh->N, r->mesh->E, r->mesh->X, r->req.ic, r->mesh->lo, r->mesh->hi, r->u, S->stream);
+    Clock c{};
+    c.t_final = r->req.t_final > 0.0 ? r->req.t_final : 0.0;
+    c.nsteps = r->req.t_final > 0.0 ? 0 : r->req.n_steps;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->mesh->clk, &c, sizeof c, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) {
+        cudaFree(r->u);
+        cudaFree(r->g);
+        r->u = r->g = nullptr;
+        mesh_free(r->mesh);
+        r->mesh = nullptr;
+        return cuda_fail(e, "request set-up");
+    }
+    r->bytes = request_bytes(r->req);
+    S->in_use += r->bytes;
+    return HS3D_OK;
+}
+
+static void finish(hs3d_server *S, ServerReq *r, hs3d_status st, const ClockView *cv)
+{
+    if (st == HS3D_OK && r->req.result_host) {
+        size_t sz = sizeof(double) * (size_t)r->mesh->E * 5 * r->mesh->n3;
+        cudaError_t e = cudaMemcpy(r->req.result_host, r->u, sz, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = HS3D_ERR_CUDA;
+    }
+    if (cv) {
+        r->res.t_sim = cv->t;
+        r->res.steps = cv->step;
+    }
+    r->res.status = st;
+    r->res.t_done = S->now();
+    release(S, r);
+    r->state = Q_DONE;
+    S->finished++;
+}
+
+typedef std::tuple<int, int, int, int, int> BucketKey;
+
+static BucketKey key_of(const ServerReq *r)
+{
+    const hs3d_solver_cfg &c = r->req.cfg;
+    return BucketKey(r->req.mesh.N, c.physics, c.surface_flux, c.volume_form, c.precision);
+}
+
+static cudaError_t ensure_capacity(hs3d_server *S, int n)
+{
+    if (n > S->d_items_cap) {
+        if (S->d_items) cudaFree(S->d_items);
+        int cap = std::max(n, 2 * S->d_items_cap);
+        cudaError_t e = cudaMalloc(&S->d_items, sizeof(Item) * cap);
+        if (e != cudaSuccess) {
+            S->d_items = nullptr;
+            S->d_items_cap = 0;
+            return e;
+        }
+        S->d_items_cap = cap;
+    }
+    if (n > S->clk_cap) {
+        if (S->d_clk) cudaFree(S->d_clk);
+        if (S->h_clk) cudaFreeHost(S->h_clk);
+        int cap = std::max(n, 2 * S->clk_cap);
+        cudaError_t e = cudaMalloc(&S->d_clk, sizeof(ClockView) * cap);
+        if (e == cudaSuccess) e = cudaMallocHost(&S->h_clk, sizeof(ClockView) * cap);
+        if (e != cudaSuccess) {
+            S->clk_cap = 0;
+            return e;
+        }
+        S->clk_cap = cap;
+    }
+    return cudaSuccess;
+}
+
+// One RK3 step for every running request, grouped into shared launches, then
+// the clocks of all running requests land in S->h_clk (in `running` order).
+static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
+{
+    int n = (int)run.size();
+    cudaError_t e = ensure_capacity(S, n);
+    if (e != cudaSuccess) return e;
+    std::vector<Item> items(n);
+    std::map<BucketKey, std::vector<int>> buckets;
+    for (int i = 0; i < n; ++i) buckets[key_of(run[i])].push_back(i);
+    // order the item table bucket by bucket so each group is a contiguous range
+    std::vector<int> order;
+    std::vector<std::pair<int, int>> ranges;
+    std::vector<const hs3d_solver_cfg *> cfgs;
+    for (auto &kv : buckets) {
+        for (size_t s = 0; s < kv.second.size(); s += S->max_batch) {
+            int begin = (int)order.size();
+            for (size_t k = s; k < std::min(kv.second.size(), s + (size_t)S->max_batch); ++k)
+                order.push_back(kv.second[k]);
+            ranges.push_back({begin, (int)order.size()});
+            cfgs.push_back(&run[kv.second[0]]->req.cfg);
+        }
+    }
+    std::vector<ServerReq *> sorted(n);
+    for (int k = 0; k < n; ++k) sorted[k] = run[order[k]];
+    run.swap(sorted);
+    for (size_t b = 0; b < ranges.size(); ++b) {
+        long long eb = 0, fb = 0;
+        for (int k = ranges[b].first; k < ranges[b].second; ++k) {
+            ServerReq *r = run[k];
+            Item it = make_item(r->mesh, &r->req.cfg, r->u, r->g, nullptr);
+            it.elem_begin = eb;
+            it.face_begin = fb;
+            eb += r->mesh->E;
+            fb += 3LL * r->mesh->E;
+            items[k] = it;
+        }
+    }
+    e = cudaMemcpyAsync(S->d_items, items.data(), sizeof(Item) * n, cudaMemcpyHostToDevice, S->stream);
+    for (size_t b = 0; b < ranges.size() && e == cudaSuccess; ++b) {
+        int lo = ranges[b].first, hi = ranges[b].second;
+        Batch bt{};
+        bt.nitems = hi - lo;
+        if (bt.nitems == 1) {
+            bt.single = items[lo];
+            bt.single.elem_begin = 0;
+            bt.single.face_begin = 0;
+        }
+        bt.items = S->d_items + lo;
+        bt.total_elems = 0;
+        for (int k = lo; k < hi; ++k) bt.total_elems += run[k]->mesh->E;
+        bt.total_faces = 3 * bt.total_elems;
+        e = enqueue_rk3_step(run[lo]->req.mesh.N, cfgs[b], bt, 0.0, S->stream);
+    }
+    if (e == cudaSuccess) {
+        k_gather_clocks<<<(n + 127) / 128, 128, 0, S->stream>>>(S->d_items, n, S->d_clk);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->h_clk, S->d_clk, sizeof(ClockView) * n, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ev, S->stream);
+    if (e != cudaSuccess) return e;
+    // bounded wait for the step
+    double t_start = S->now();
+    while (true) {
+        cudaError_t q = cudaEventQuery(S->ev);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return q;
+        if (S->now() - t_start > S->wait_limit_s) return cudaErrorTimeout;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return cudaSuccess;
+}
+
+static void server_loop(hs3d_server *S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        // 1. admission (FIFO while the budget has room)
+        while (!S->queue.empty()) {
+            ServerReq *r = S->queue.front();
+            size_t need = request_bytes(r->req);
+            if (S->in_use + need > S->budget && !S->running.empty()) break;
+            S->queue.pop_front();
+            hs3d_status st = admit(S, r);
+            if (st == HS3D_ERR_NOMEM && !S->running.empty()) {
+                S->queue.push_front(r);   // wait for memory to free
+                break;
+            }
+            if (st != HS3D_OK) {
+                r->res.status = st;
+                r->res.t_done = S->now();
+                r->state = Q_DONE;
+                S->finished++;
+                continue;
+            }
+            r->state = Q_RUNNING;
+            r->res.t_admit = S->now();
+            r->res.device_bytes = r->bytes;
+            S->running.push_back(r);
+        }
+        if (S->running.empty()) {
+            S->cv.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        // 2-3. one batched step, without holding the lock (submit/poll stay responsive)
+        std::vector<ServerReq *> run = S->running;
+        lk.unlock();
+        cudaError_t e = step_all(S, run);
+        lk.lock();
+        S->running = run;   // step_all reorders by bucket
+        // 4. retire
+        std::vector<ServerReq *> keep;
+        for (size_t k = 0; k < run.size(); ++k) {
+            ServerReq *r = run[k];
+            if (e != cudaSuccess) {
+                finish(S, r, e == cudaErrorTimeout ? HS3D_ERR_TIMEOUT : HS3D_ERR_CUDA, nullptr);
+                continue;
+            }
+            const ClockView &cv = S->h_clk[k];
+            bool complete = (r->req.t_final > 0.0) ? cv.t >= r->req.t_final : cv.step >= r->req.n_steps;
+            if (cv.bad) finish(S, r, HS3D_ERR_NONPHYSICAL, &cv);
+            else if (complete || cv.done) finish(S, r, HS3D_OK, &cv);
+            else keep.push_back(r);
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        S->running.swap(keep);
+    }
+}
+
+}  // namespace hs3d
+
+extern "C" {
+
+hs3d_status hs3d_server_create(size_t hbm_budget_bytes, int max_batch, hs3d_server **out)
+{
+    if (!out) return fail(HS3D_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (max_batch < 0) return fail(HS3D_ERR_INVALID, "max_batch < 0");
+    hs3d_server *S = new (std::nothrow) hs3d_server();
+    if (!S) return fail(HS3D_ERR_NOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&S->device);
+    size_t fr = 0, tot = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (S->stream) cudaStreamDestroy(S->stream);
+        delete S;
+        return cuda_fail(e, "server set-up");
+    }
+    S->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    S->max_batch = max_batch ? max_batch : 256;
+    if (const char *w = getenv("HS3D_SERVER_WAIT_LIMIT_S")) S->wait_limit_s = atof(w);
+    if (const char *f = getenv("HS3D_FAULT_ALLOC_FAILURES")) S->fault_alloc = atoi(f);
+    S->t0 = std::chrono::steady_clock::now();
+    S->th = std::thread(server_loop, S);
+    *out = S;
+    return HS3D_OK;
+}
+
+void hs3d_server_destroy(hs3d_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    cudaStreamSynchronize(S->stream);
+    for (auto &kv : S->all) {
+        ServerReq *r = kv.second;
+        if (r->state == Q_RUNNING) release(S, r);
+        delete r;
+    }
+    if (S->d_items) cudaFree(S->d_items);
+    if (S->d_clk) cudaFree(S->d_clk);
+    if (S->h_clk) cudaFreeHost(S->h_clk);
+    if (S->ev) cudaEventDestroy(S->ev);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+}
+
+hs3d_status hs3d_submit(hs3d_server *S, const hs3d_request *req, uint64_t *ticket)
+{
+    if (!S || !req || !ticket) return fail(HS3D_ERR_INVALID, "server, request or ticket is NULL");
+    hs3d_status st = validate_desc(&req->mesh);
+    if (st == HS3D_OK) st = validate_cfg(&req->cfg);
+    if (st != HS3D_OK) return st;
+    if (!(req->t_final > 0.0) && req->n_steps <= 0)
+        return fail(HS3D_ERR_INVALID, "request needs t_final > 0 or n_steps > 0");
+    if (req->ic.kind != HS3D_IC_VORTEX && req->ic.kind != HS3D_IC_TGV)
+        return fail(HS3D_ERR_INVALID, "bad initial condition kind");
+    size_t need = request_bytes(*req);
+    ServerReq *r = new (std::nothrow) ServerReq();
+    if (!r) return fail(HS3D_ERR_NOMEM, "host allocation failed");
+    r->req = *req;
+    if (req->mesh.node_xyz) {
+        size_t cnt = (size_t)req->mesh.ex * req->mesh.ey * req->mesh.ez * 3 * (req->mesh.N + 1) * (req->mesh.N + 1) *
+                     (req->mesh.N + 1);
+        r->xyz.assign(req->mesh.node_xyz, req->mesh.node_xyz + cnt);
+    }
+    r->req.mesh.node_xyz = nullptr;
+    long long E = (long long)req->mesh.ex * req->mesh.ey * req->mesh.ez;
+    r->res.status = HS3D_PENDING;
+    r->res.dof = E * (req->mesh.N + 1) * (req->mesh.N + 1) * (req->mesh.N + 1);
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (need > S->budget) {
+            delete r;
+            return fail(HS3D_ERR_NOMEM, "request needs %zu bytes, budget is %zu", need, S->budget);
+        }
+        r->id = S->next_id++;
+        r->res.t_submit = S->now();
+        S->all[r->id] = r;
+        S->queue.push_back(r);
+        *ticket = r->id;
+    }
+    S->cv.notify_all();
+    return HS3D_OK;
+}
+
+hs3d_status hs3d_poll(hs3d_server *S, uint64_t ticket, hs3d_result *res)
+{
+    if (!S) return fail(HS3D_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return fail(HS3D_ERR_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    ServerReq *r = it->second;
+    if (res) *res = r->res;
+    if (r->state != Q_DONE) return HS3D_PENDING;
+    if (r->res.status != HS3D_OK) return fail(r->res.status, "request %llu failed", (unsigned long long)ticket);
+    return HS3D_OK;
+}
+
+hs3d_status hs3d_server_stats(hs3d_server *S, int64_t *queued, int64_t *running, int64_t *finished, size_t *bytes)
+{
+    if (!S) return fail(HS3D_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    if (queued) *queued = (int64_t)S->queue.size();
+    if (running) *running = (int64_t)S->running.size();
+    if (finished) *finished = S->finished;
+    if (bytes) *bytes = S->in_use;
+    return HS3D_OK;
+}
+
+}  // extern "C"

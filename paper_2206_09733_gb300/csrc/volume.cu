@@ -1,0 +1,326 @@
+// Element kernel: volume term + surface lifting + Jacobian scaling + RK stage.
+//
+// Strong form of Eq. NS5 (Sec. 3.3) on Gauss-Lobatto nodes, per element:
+//   du/dt = -(V + S)/J
+//   standard form   V = sum_d D_d F~^d,   F~^d = Ja^d . (F_e - F_v)
+//   split form      V = sum_d sum_m D_im F#(u_i, u_m).(Ja^d_i + Ja^d_m) - sum_d D_d (Ja^d . F_v)
+//                   with the Chandrashekar two-point flux F# (Sec. 3.5)
+//   surface         S = (1/w_end) (F^* - F~^d_in) on the +d face, (1/w_0)(-F^* + F~^d_in) on the -d face
+//                   F^* the face flux computed once per face by k_face
+// followed either by the residual store or by one Williamson low-storage RK3
+// stage (Sec. 3.7) g <- A_k g + dt R, u <- u + B_k g in FP64.
+//
+// One thread per node, `epb` elements per CTA.  The element's contravariant
+// fluxes (standard form) or its per-node two-point-flux inputs (split form)
+// are staged in shared memory; the tensor-product contractions along
+// xi/eta/zeta read them from there.
+#include "internal.cuh"
+#include "physics.cuh"
+
+namespace hs3d {
+
+__constant__ double c_rkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+__constant__ double c_rkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+template <int N>
+constexpr int vol_threads()
+{
+    return ((N + 1) * (N + 1) * (N + 1) > 256) ? (N + 1) * (N + 1) * (N + 1) : 256;
+}
+
+template <int n>
+__device__ __forceinline__ void tangential(int d, const int ijk[3], int &ta, int &tb)
+{
+    ta = (d == 0) ? ijk[1] : ijk[0];
+    tb = (d == 2) ? ijk[1] : ijk[2];
+}
+
+// Number of R values staged per node.
+template <int FORM, bool NS>
+constexpr int vol_smem_per_node()
+{
+    return FORM == HS3D_VOL_STANDARD ? 15 : (16 + (NS ? 15 : 0));
+}
+
+template <int N, typename R, bool NS, int FORM>
+__global__ void __launch_bounds__(vol_threads<N>()) k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int PER = vol_smem_per_node<FORM, NS>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sD = (R *)smem_raw;
+    R *sbuf = sD + ((n * n + 1) & ~1);
+    const int epb = blockDim.x / n3;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = (R)ops->D[t];
+    const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
+    const long long ge = blockIdx.x * (long long)epb + le;
+    bool valid = ge < b.total_elems;
+    const Item *itp = nullptr;
+    int e = 0;
+    if (valid) {
+        itp = &find_item_elem(b, ge);
+        e = (int)(ge - itp->elem_begin);
+        if (itp->clk && itp->clk->done) valid = false;
+    }
+    R *S = sbuf + (size_t)le * PER * n3;
+    const int ijk[3] = {p % n, (p / n) % n, p / n2};
+
+    double u[5];
+    R ja[9];
+    R Fown[3][5];   // own total contravariant flux Ja^d.(F_e - F_v) at this node
+    R Fe[3][5];     // split form: own Ja^d.F_e (diagonal two-point term)
+    Prim<R> q;
+    if (valid) {
+        const Item &it = *itp;
+        const double *U = it.u + (size_t)e * 5 * n3 + p;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
+        q = prim_from_u<R>(u, it.gamma - 1.0);
+        const double *JA = it.Ja + (size_t)e * 9 * n3 + p;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ja[k] = (R)JA[k * n3];
+        const R E = (R)u[4];
+        R fv[3][5];
+        if (NS) {
+            const R *Gp = (const R *)it.grad + (size_t)e * 12 * n3 + p;
+            R G[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) G[k] = Gp[k * n3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                visc_flux(q, G, (R)it.mu, (R)it.kappa, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fv[d]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            euler_flux(q, E, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], Fe[d]);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Fown[d][v] = NS ? Fe[d][v] - fv[d][v] : Fe[d][v];
+        }
+        if (FORM == HS3D_VOL_STANDARD) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) S[(d * 5 + v) * n3 + p] = Fown[d][v];
+        } else {
+            ECNode<R> z = ec_node(q);
+            S[0 * n3 + p] = z.rho;
+            S[1 * n3 + p] = z.v1;
+            S[2 * n3 + p] = z.v2;
+            S[3 * n3 + p] = z.v3;
+            S[4 * n3 + p] = z.beta;
+            S[5 * n3 + p] = z.lrho;
+            S[6 * n3 + p] = z.lbeta;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) S[(7 + k) * n3 + p] = ja[k];
+            if (NS) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) S[(16 + d * 5 + v) * n3 + p] = fv[d][v];
+            }
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
+    const Item &it = *itp;
+
+    R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+    if (FORM == HS3D_VOL_STANDARD) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+            const int base = p - ijk[d] * stride;
+            const R *Drow = sD + ijk[d] * n;
+#pragma unroll
+            for (int m = 0; m < n; ++m) {
+                const R Dm = Drow[m];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += Dm * S[(d * 5 + v) * n3 + base + m * stride];
+            }
+        }
+    } else {
+        const R gm1 = (R)(it.gamma - 1.0);
+        const ECNode<R> zi = {S[0 * n3 + p], S[1 * n3 + p], S[2 * n3 + p], S[3 * n3 + p],
+                              S[4 * n3 + p], S[5 * n3 + p], S[6 * n3 + p]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+            const int base = p - ijk[d] * stride;
+            const R *Drow = sD + ijk[d] * n;
+#pragma unroll
+            for (int m = 0; m < n; ++m) {
+                const R Dm = Drow[m];
+                const int pm = base + m * stride;
+                if (m == ijk[d]) {
+                    // F#(u_i, u_i).(2 Ja^d_i) = 2 Ja^d_i . F_e(u_i)
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) V[v] += (R)2 * Dm * Fe[d][v];
+                } else {
+                    const ECNode<R> zm = {S[0 * n3 + pm], S[1 * n3 + pm], S[2 * n3 + pm], S[3 * n3 + pm],
+                                          S[4 * n3 + pm], S[5 * n3 + pm], S[6 * n3 + pm]};
+                    const R a1 = ja[d * 3 + 0] + S[(7 + d * 3 + 0) * n3 + pm];
+                    const R a2 = ja[d * 3 + 1] + S[(7 + d * 3 + 1) * n3 + pm];
+                    const R a3 = ja[d * 3 + 2] + S[(7 + d * 3 + 2) * n3 + pm];
+                    R fs[5];
+                    flux_ec(zi, zm, gm1, a1, a2, a3, fs);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) V[v] += Dm * fs[v];
+                }
+                if (NS) {
+#pragma unroll
+                    for (int v = 1; v < 5; ++v) V[v] -= Dm * S[(16 + d * 5 + v) * n3 + pm];
+                }
+            }
+        }
+    }
+
+    // surface lifting
+    const R iw = (R)(1.0 / ops->w[0]);
+    const R *FS = (const R *)it.fstar;
+    const int E = it.E;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (ijk[d] == N || ijk[d] == 0) {
+            int ta, tb;
+            tangential<n>(d, ijk, ta, tb);
+            const int ab = ta + n * tb;
+            if (ijk[d] == N) {
+                const R *F = FS + ((size_t)d * E + e) * 5 * n2 + ab;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += iw * (F[v * n2] - Fown[d][v]);
+            }
+            if (ijk[d] == 0) {
+                const int em = nbr_minus(e, d, it.ex, it.ey, it.ez);
+                const R *F = FS + ((size_t)d * E + em) * 5 * n2 + ab;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += iw * (Fown[d][v] - F[v * n2]);
+            }
+        }
+    }
+
+    const double ij = it.invJ[(size_t)e * n3 + p];
+    if (stage < 0) {
+        double *O = it.out + (size_t)e * 5 * n3 + p;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
+    } else {
+        const double dt = it.clk->dt;
+        const double A = c_rkA[stage], B = c_rkB[stage];
+        double *Gp = it.g + (size_t)e * 5 * n3 + p;
+        double *Up = it.u + (size_t)e * 5 * n3 + p;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const double r = -(double)V[v] * ij;
+            const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
+            Gp[v * n3] = gv;
+            Up[v * n3] = u[v] + B * gv;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+static int g_epb[kMaxn + 1][2] = {};
+
+int elems_per_block(int N, int which)
+{
+    int v = g_epb[N][which];
+    if (v > 0) return v;
+    int n3 = (N + 1) * (N + 1) * (N + 1);
+    int e = 256 / n3;
+    return e < 1 ? 1 : e;
+}
+
+void set_elems_per_block(int N, int which, int epb) { g_epb[N][which] = epb; }
+
+template <int N, typename R, bool NS, int FORM>
+static cudaError_t vol_launch2(const Batch &b, int stage, cudaStream_t s)
+{
+    constexpr int n = N + 1, n3 = n * n * n;
+    int epb = elems_per_block(N, 1);
+    int threads = epb * n3;
+    if (threads > vol_threads<N>()) {
+        epb = vol_threads<N>() / n3;
+        threads = epb * n3;
+    }
+    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3);
+    unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
+    const Ops *ops = device_ops(N);
+    if (!ops) return cudaErrorMemoryAllocation;
+    k_volume<N, R, NS, FORM><<<blocks, threads, smem, s>>>(b, ops, stage);
+    return cudaGetLastError();
+}
+
+template <int N, typename R>
+static cudaError_t vol_launch(int physics, int form, const Batch &b, int stage, cudaStream_t s)
+{
+    if (b.total_elems == 0) return cudaSuccess;
+    if (physics == HS3D_NS) {
+        if (form == HS3D_VOL_EC) return vol_launch2<N, R, true, HS3D_VOL_EC>(b, stage, s);
+        return vol_launch2<N, R, true, HS3D_VOL_STANDARD>(b, stage, s);
+    }
+    if (form == HS3D_VOL_EC) return vol_launch2<N, R, false, HS3D_VOL_EC>(b, stage, s);
+    return vol_launch2<N, R, false, HS3D_VOL_STANDARD>(b, stage, s);
+}
+
+template <int N>
+static cudaError_t prep_vol()
+{
+    const int big = 220 * 1024;
+    cudaError_t e = cudaSuccess;
+#define HS3D_ATTR(R, NS, F)                                                                                  \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(k_volume<N, R, NS, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    HS3D_ATTR(double, false, HS3D_VOL_STANDARD)
+    HS3D_ATTR(double, true, HS3D_VOL_STANDARD)
+    HS3D_ATTR(double, false, HS3D_VOL_EC)
+    HS3D_ATTR(double, true, HS3D_VOL_EC)
+    HS3D_ATTR(float, false, HS3D_VOL_STANDARD)
+    HS3D_ATTR(float, true, HS3D_VOL_STANDARD)
+    HS3D_ATTR(float, false, HS3D_VOL_EC)
+    HS3D_ATTR(float, true, HS3D_VOL_EC)
+#undef HS3D_ATTR
+    return e;
+}
+
+cudaError_t prepare_volume(int N)
+{
+    switch (N) {
+        case 1: return prep_vol<1>();
+        case 2: return prep_vol<2>();
+        case 3: return prep_vol<3>();
+        case 4: return prep_vol<4>();
+        case 5: return prep_vol<5>();
+        case 6: return prep_vol<6>();
+        case 7: return prep_vol<7>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_volume(int N, int prec, int physics, int form, const Batch &b, int stage, cudaStream_t s)
+{
+    if (prec == HS3D_FP64) {
+        switch (N) {
+            case 1: return vol_launch<1, double>(physics, form, b, stage, s);
+            case 2: return vol_launch<2, double>(physics, form, b, stage, s);
+            case 3: return vol_launch<3, double>(physics, form, b, stage, s);
+            case 4: return vol_launch<4, double>(physics, form, b, stage, s);
+            case 5: return vol_launch<5, double>(physics, form, b, stage, s);
+            case 6: return vol_launch<6, double>(physics, form, b, stage, s);
+            case 7: return vol_launch<7, double>(physics, form, b, stage, s);
+        }
+    } else {
+        switch (N) {
+            case 1: return vol_launch<1, float>(physics, form, b, stage, s);
+            case 2: return vol_launch<2, float>(physics, form, b, stage, s);
+            case 3: return vol_launch<3, float>(physics, form, b, stage, s);
+            case 4: return vol_launch<4, float>(physics, form, b, stage, s);
+            case 5: return vol_launch<5, float>(physics, form, b, stage, s);
+            case 6: return vol_launch<6, float>(physics, form, b, stage, s);
+            case 7: return vol_launch<7, float>(physics, form, b, stage, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hs3d

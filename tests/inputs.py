@@ -1,0 +1,47 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds none of the method's arithmetic: it draws densities,
+velocities and specific internal energies and assembles conserved variables
+rho, rho v, rho (eps + |v|^2/2) from them.  No equation of state, flux,
+operator or mesh quantity appears here.
+"""
+import numpy as np
+
+
+def random_state(shape, seed, rho=(0.8, 1.2), vmax=0.5, eps=(1.8, 2.7), smooth=False):
+    """Conserved state of shape [E, 5, n, n, n] (float64).
+
+    rho ~ U(rho), v_c ~ U(-vmax, vmax), specific internal energy ~ U(eps).
+    smooth=True replaces the independent draws by a few random low-order
+    products of node indices within each element plus an element offset, so
+    that neighbouring nodes differ little (closer to a resolved flow field).
+    """
+    rng = np.random.default_rng(seed)
+    E, nv, n = shape[0], shape[1], shape[2]
+    assert nv == 5 and shape[2] == shape[3] == shape[4]
+
+    def field(lo, hi):
+        if not smooth:
+            return rng.uniform(lo, hi, size=(E, n, n, n))
+        t = np.linspace(-1.0, 1.0, n)
+        k, j, i = np.meshgrid(t, t, t, indexing="ij")
+        base = rng.uniform(lo, hi, size=(E, 1, 1, 1))
+        amp = 0.05 * (hi - lo)
+        c = rng.uniform(-1, 1, size=(E, 4, 1, 1, 1))
+        f = base + amp * (c[:, 0] * i + c[:, 1] * j + c[:, 2] * k + c[:, 3] * i * j)
+        return np.clip(f, lo, hi)
+
+    r = field(*rho)
+    v = [field(-vmax, vmax) for _ in range(3)]
+    e = field(*eps)
+    u = np.empty(shape)
+    u[:, 0] = r
+    for c in range(3):
+        u[:, 1 + c] = r * v[c]
+    u[:, 4] = r * (e + 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+    return u
+
+
+def cube(ex, ey, ez, lo=-np.pi, hi=np.pi):
+    """Box extents (lo, hi) for an ex*ey*ez mesh of a cube."""
+    return (lo, lo, lo), (hi, hi, hi)

@@ -499,7 +499,12 @@ def test_br1_heat_conduction():
         r = m.residual(O.Cfg("ns", "lf", "standard", Re=Re, Pr=Pr), u)
         kappa = (1 / Re) * G / ((G - 1) * Pr)
         errs.append(_rel(r[:, 4], kappa * eps * (-3.0) * S))
-        assert np.abs(r[:, :4]).max() < 1e-12
+        # mass and momentum vanish to round-off of the pressure terms, whose
+        # scale is p |D| |Ja| / J ~ N^2 here (the face normal is single-valued,
+        # the element's own boundary flux uses its own Ja: at the periodic wrap
+        # the two differ in the last bits)
+        scale = (1.0 / G) * N * N * np.abs(m.Ja).max() / m.J.min()
+        assert np.abs(r[:, :4]).max() < 1e-12 * scale
     assert errs[-1] < 1e-3 and errs[0] > 10 * errs[-1]
 
 
