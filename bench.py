@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hs3d", choices=["hs3d", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=128, help="requests in the batched-serving sample (0: skip)")
     return ap.parse_args()
 
 
@@ -305,6 +306,10 @@ def run_hs3d(args, world, rank, local):
                  "frac": round(fp64_ach / peaks["fp64_tflops"], 4),
                  "peak_source": "measured FP64 FMA-chain kernel (hs3d_alu_peaks)"}
 
+    serving = None
+    if args.serving > 0:
+        serving = run_serving(args.serving, max(4, args.serving // 16))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(u64_final_check=None)
@@ -332,6 +337,8 @@ def run_hs3d(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps * 2,
         "clocks": clocks,
     }
+    if serving is not None:
+        line["serving"] = serving
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -345,6 +352,101 @@ def measured_hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback 6.8 TB/s"
+
+
+# ------------------------------------------------------------------ serving (continuous batching)
+
+def serving_requests(count, seed=0):
+    """The batched-serving request stream: periodic cubes [0,10]^3 with E^3
+    elements, E ~ U{4..24}, N ~ U{2..7}, isentropic vortex with centre ~
+    U(box), strength ~ U[1,5], Mach ~ U[0.1,0.8], integrated to t = 1.0 at
+    CFL 0.5; Poisson arrivals at 200 requests/s."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for _ in range(count):
+        E = int(rng.integers(4, 25))
+        N = int(rng.integers(2, 8))
+        xc, yc = rng.uniform(0, 10, size=2)
+        beta = float(rng.uniform(1, 5))
+        Ma = float(rng.uniform(0.1, 0.8))
+        t += float(rng.exponential(1 / 200.0))
+        reqs.append(dict(E=E, N=N, xc=float(xc), yc=float(yc), beta=beta, Ma=Ma, arrival=t))
+    return reqs
+
+
+def run_serving(count, seq_count, rate_scale=1.0):
+    """Submit `count` requests at their arrival times to the batched server
+    (mixed FP32 residual, FP64 state), poll to completion; then run the first
+    `seq_count` requests one at a time through the single-solve FP64 API.
+    Returns solves/s, p50/p99 latency and the sequential comparison."""
+    import numpy as np
+    import torch
+
+    import paper_2206_09733_gb300 as hs
+    reqs = serving_requests(count)
+
+    def descs(r, prec):
+        mesh = hs.mesh_desc(r["E"], r["E"], r["E"], r["N"], lo=(0, 0, 0), hi=(10, 10, 10))
+        cfg = hs.solver_cfg("euler", "lf", "ec", prec, gamma=GAMMA, cfl=CFL)
+        ic = hs.ic_desc("vortex", GAMMA, r["Ma"], r["beta"], r["xc"], r["yc"])
+        return mesh, cfg, ic
+
+    srv = hs.Server()
+    # warm-up: one small request through the server
+    m, c, i = descs(reqs[0], "mixed32")
+    t = srv.submit(m, c, i, t_final=0.05)
+    while srv.poll(t)[0] == hs.PENDING:
+        time.sleep(0.001)
+    tickets = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        target = r["arrival"] * rate_scale
+        while time.perf_counter() - t0 < target:
+            time.sleep(0.0002)
+        m, c, i = descs(r, "mixed32")
+        tickets.append(srv.submit(m, c, i, t_final=1.0))
+    done = {}
+    while len(done) < len(tickets):
+        for tk in tickets:
+            if tk not in done:
+                st, res = srv.poll(tk)
+                if st != hs.PENDING:
+                    done[tk] = (st, res.t_done - res.t_submit, res.t_done, res.t_submit, res.dof * res.steps * 3)
+        time.sleep(0.0005)
+    ok = [v for v in done.values() if v[0] == hs.OK]
+    lat = np.array([v[1] for v in ok])
+    span = max(v[2] for v in ok) - min(v[3] for v in ok)
+    dof_stage = sum(v[4] for v in ok)
+    srv.close()
+    # sequential FP64 per-solve through the single-mesh API
+    seq_t = 0.0
+    for r in reqs[:seq_count]:
+        mesh = hs.Mesh(r["E"], r["E"], r["E"], r["N"], lo=(0, 0, 0), hi=(10, 10, 10))
+        u = mesh.init_state(mesh.empty_state(), "vortex", GAMMA, r["Ma"], r["beta"], r["xc"], r["yc"])
+        g = torch.zeros_like(u)
+        cfg = hs.solver_cfg("euler", "lf", "ec", "fp64", gamma=GAMMA, cfl=CFL)
+        dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        tsim = 0.0
+        while tsim < 1.0 - 1e-12:
+            mesh.dt(cfg, u, dt_dev)
+            dt = min(float(dt_dev.item()), 1.0 - tsim)
+            mesh.rk3_step(cfg, u, g, dt=dt)
+            tsim += dt
+        torch.cuda.synchronize()
+        seq_t += time.perf_counter() - a
+        del mesh
+    return {"requests": count, "completed": len(ok), "solves_per_s": round(len(ok) / span, 2),
+            "dof_stage_per_s": round(dof_stage / span, 1),
+            "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
+            "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
+            "arrivals": f"Poisson 200 req/s x {1 / rate_scale:g}",
+            "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5",
+            "sequential_fp64_solves_per_s": round(seq_count / seq_t, 2),
+            "sequential_sample": f"first {seq_count} requests, one at a time, FP64, hs3d_rk3_step + host dt read"}
 
 
 # ------------------------------------------------------------------ the oracle on the host cores
