@@ -169,6 +169,28 @@ hs3d_status hs3d_clock(const hs3d_mesh *mesh, double *t, int64_t *steps, int res
 hs3d_status hs3d_diagnostics(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, const double *u,
                              const double *dudt, double *out, void *stream);
 
+/* The quadrature diagnostics of hs3d_diagnostics, for callers that cannot
+ * allocate device memory: code running while a CUDA stream capture is
+ * active (cudaMalloc is not allowed there), code inside a framework whose
+ * memory pool owns all device memory, or real-time loops that must not
+ * allocate or synchronise.  The paper has no counterpart; this is a library
+ * convenience.  Allocates nothing: the caller passes every input (N, E,
+ * gamma, the Jacobian J [E][n3] e.g. copied out by hs3d_mesh_geometry, the
+ * state u and optionally dudt, all DEVICE FP64) and the DEVICE output out[7]
+ * (same meaning as hs3d_diagnostics; the two give the same result).  The
+ * per-block partial sums live in one fixed device array of 4096 slots, each
+ * covering 2048 nodes, so E*(N+1)^3 may not exceed 8,388,608 nodes
+ * (HS3D_ERR_INVALID beyond).  The array is compiled into the library: every
+ * GPU that loads it holds the array (256 KB) until the process exits.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array and leaves its partial sums in it; each
+ * call writes every slot it later reads, so nothing needs clearing, but two
+ * calls that overlap on the GPU (other streams, other threads) race on the
+ * array and give wrong results.  Stream-ordered. */
+hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, const double *J, const double *u,
+                                     const double *dudt, double *out, void *stream);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* One RK3 step exactly as hs3d_rk3_step, launched eagerly with CUDA events

@@ -35,7 +35,8 @@ PRECISION = {"fp64": FP64, "mixed32": MIXED32}
 EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh_geometry", "hs3d_init_state",
            "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
            "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
-           "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks"]
+           "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
+           "hs3d_diagnostics_noalloc"]
 
 
 class HS3DError(RuntimeError):
@@ -105,6 +106,7 @@ def lib():
                                       C.POINTER(C.c_size_t)],
                 "hs3d_rk3_step_profiled": [vp, C.POINTER(SolverCfg), vp, vp, d, C.POINTER(d), vp],
                 "hs3d_alu_peaks": [C.POINTER(d), vp],
+                "hs3d_diagnostics_noalloc": [i, C.c_int64, d, vp, vp, vp, vp, vp],
                 "hs3d_last_error": [],
                 "hs3d_version": [],
             }
@@ -291,6 +293,14 @@ class Server:
         q, r, f, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
         check(lib().hs3d_server_stats(self._h, C.byref(q), C.byref(r), C.byref(f), C.byref(b)))
         return {"queued": q.value, "running": r.value, "finished": f.value, "bytes_in_use": b.value}
+
+
+def diagnostics_noalloc(N, E, gamma, J, u, out, dudt=None, stream=None):
+    """hs3d_diagnostics_noalloc: the quadrature diagnostics with no device
+    allocation (for callers that cannot allocate; see include/hs3d.h)."""
+    check(lib().hs3d_diagnostics_noalloc(int(N), int(E), float(gamma), _ptr(J, "J"), _ptr(u, "u"),
+                                         _ptr(dudt, "dudt"), _ptr(out, "out"), _stream(stream)))
+    return out
 
 
 def ic_desc(kind="vortex", gamma=1.4, Ma=0.5, beta=5.0, xc=5.0, yc=5.0, t=0.0) -> IC:
