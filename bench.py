@@ -57,7 +57,15 @@ def parse():
     ap.add_argument("--impl", default="hs3d", choices=["hs3d", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=128, help="requests in the batched-serving sample (0: skip)")
-    return ap.parse_args()
+    ap.add_argument("--mesh", type=int, default=16,
+                    help="elements per direction (16 = the metric's workload; larger sizes for profiling only)")
+    ap.add_argument("--only", choices=["mixed32", "fp64"], default=None,
+                    help="time one precision only (profiling runs)")
+    args = ap.parse_args()
+    global EX, EY, EZ, NODES
+    EX = EY = EZ = args.mesh
+    NODES = EX * EY * EZ * (N + 1) ** 3
+    return args
 
 
 # ------------------------------------------------------------------ distributed plumbing (replicas only)
@@ -164,21 +172,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ algorithmic cost model (per launch)
 
-def kernel_bytes(kernel, prec, E=EX * EY * EZ, n=N + 1):
-    """Compulsory DRAM bytes of one launch of each kernel (FP64 state and
-    geometry; scratch arrays fstar/grad in the arithmetic type)."""
+def kernel_bytes(kernel, prec, E=None, n=N + 1):
+    """Compulsory DRAM bytes of one launch of each kernel (FP64 state; metric
+    terms in the arithmetic type, 1/J in FP64; scratch arrays fstar/grad in
+    the arithmetic type)."""
+    E = EX * EY * EZ if E is None else E
     s = 8 if prec == "fp64" else 4
     n2, n3 = n * n, n ** 3
     if kernel == "volume":     # u, Ja, invJ, grad, 6 face fluxes in; g in/out, u out
-        return E * (5 * n3 * 8 + 9 * n3 * 8 + n3 * 8 + 12 * n3 * s + 6 * 5 * n2 * s + 5 * n3 * 8 * 3)
+        return E * (5 * n3 * 8 + 9 * n3 * s + n3 * 8 + 12 * n3 * s + 6 * 5 * n2 * s + 5 * n3 * 8 * 3)
     if kernel == "face":       # two traces, face normal, two gradient traces in; flux out
         return 3 * E * (2 * 5 * n2 * 8 + 3 * n2 * 8 + 2 * 12 * n2 * s + 5 * n2 * s)
     if kernel == "grad":       # u, Ja, invJ, 6 neighbour traces in; gradients out
-        return E * (5 * n3 * 8 + 9 * n3 * 8 + n3 * 8 + 6 * 5 * n2 * 8 + 12 * n3 * s)
+        return E * (5 * n3 * 8 + 9 * n3 * s + n3 * 8 + 6 * 5 * n2 * 8 + 12 * n3 * s)
     return 0
 
 
-def volume_flops(E=EX * EY * EZ, n=N + 1):
+def volume_flops(E=None, n=N + 1):
     """Algorithmic flops of one launch of the split-form NS element kernel
     (an FMA counts 2, a divide / sqrt / log 1 each), counted from the
     formulas the kernel evaluates:
@@ -186,6 +196,7 @@ def volume_flops(E=EX * EY * EZ, n=N + 1):
       two-point fluxes 3*(n-1) * 63 (two log means 2*14, averages 14,
       flux 21) plus the 5-term axpy 10 each, diagonal 3*10,
       viscous D-contraction 3*n*8, surface lift <= 3*10, scale + RK 5*5."""
+    E = EX * EY * EZ if E is None else E
     per_node = 14 + 3 * 13 + 3 * 40 + 3 * (n - 1) * (63 + 10) + 3 * 10 + 3 * n * 8 + 30 + 25
     return E * n ** 3 * per_node
 
@@ -236,6 +247,13 @@ def run_hs3d(args, world, rank, local):
         return ms, u
 
     # --- headline: mixed path, then FP64 path, K timed steps each
+    if args.only:
+        # profiling run: one precision, no extras
+        ms, _ = timed_steps(args.only, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"profiling_run": True, "precision": args.only, "mesh": EX, "steps": args.steps,
+                              "ms_per_step": round(ms / args.steps, 4)}), flush=True)
+        return
     with ClockSampler(local) as clk:
         ms32, u32 = timed_steps("mixed32", args.steps, args.warmup)
         ms64, u64 = timed_steps("fp64", args.steps, args.warmup)
@@ -314,7 +332,7 @@ def run_hs3d(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(u64_final_check=None)
 
-    launches_per_step = 2 + 3 * 3
+    launches_per_step = 2 + 3 * 3   # priming dt pass, dt finalize, 3 x (grad, face, element)
     line = {
         "metric": METRIC, "value": round(v32, 1), "unit": "DOF-stage-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s32 * 1e3 / args.steps, 4),
@@ -416,6 +434,10 @@ def run_serving(count, seq_count, rate_scale=1.0):
                     done[tk] = (st, res.t_done - res.t_submit, res.t_done, res.t_submit, res.dof * res.steps * 3)
         time.sleep(0.0005)
     ok = [v for v in done.values() if v[0] == hs.OK]
+    failed = {}
+    for v in done.values():
+        if v[0] != hs.OK:
+            failed[hs.STATUS_NAMES.get(v[0], str(v[0]))] = failed.get(hs.STATUS_NAMES.get(v[0], str(v[0])), 0) + 1
     lat = np.array([v[1] for v in ok])
     span = max(v[2] for v in ok) - min(v[3] for v in ok)
     dof_stage = sum(v[4] for v in ok)
@@ -439,7 +461,7 @@ def run_serving(count, seq_count, rate_scale=1.0):
         torch.cuda.synchronize()
         seq_t += time.perf_counter() - a
         del mesh
-    return {"requests": count, "completed": len(ok), "solves_per_s": round(len(ok) / span, 2),
+    return {"requests": count, "completed": len(ok), "failed": failed, "solves_per_s": round(len(ok) / span, 2),
             "dof_stage_per_s": round(dof_stage / span, 1),
             "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
             "latency_p99_s": round(float(np.percentile(lat, 99)), 4),

@@ -139,7 +139,7 @@ hs3d_status hs3d_residual(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, con
  * [E][5][n3], updated in place (g need not be initialised).  dt > 0 is used
  * as given; dt <= 0 computes dt on the device from the state at the start of
  * the step:
- *   dt = min( cfl*2/(n max_nodes sum_d (|Ja^d.v| + c|Ja^d|)/J),
+ *   dt = min( cfl*8/(n^2 max_nodes sum_d (|Ja^d.v| + c|Ja^d|)/J),
  *             12/(n^4 max_nodes (mu/rho) sum_d (|Ja^d|/J)^2) )   (viscous term NS only).
  * Stream-ordered. */
 hs3d_status hs3d_rk3_step(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
@@ -190,6 +190,16 @@ hs3d_status hs3d_diagnostics(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, 
  * array and give wrong results.  Stream-ordered. */
 hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, const double *J, const double *u,
                                      const double *dudt, double *out, void *stream);
+
+/* Autotuner: times every admissible launch shape (elements per CTA) of the
+ * BR1-gradient and element kernels for this mesh and configuration on a
+ * scratch state, keeps the fastest for (N, precision, kernel) for the rest of
+ * the process, and writes the choices to the JSON file named by the
+ * environment variable HS3D_TUNE_CACHE if set (read back at the next mesh
+ * creation).  choice_out (HOST, 2 ints, may be NULL) receives [gradient,
+ * element] elements per CTA.  Synchronous; allocates two scratch states.
+ * Call it outside any stream capture. */
+hs3d_status hs3d_autotune(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, int *choice_out, void *stream);
 
 /* ---------------------------------------------------------------- instrumentation */
 

@@ -748,7 +748,9 @@ void orc_lsrk3_stage(long long count, int k, double dt, double *u, double *g, co
 }
 
 /* Time step (no formula in the paper; the reading used by this library):
- *   convective  dt_c = cfl * 2 / (n * max_nodes sum_d (|Ja^d.v| + c |Ja^d|)/J)
+ *   convective  dt_c = cfl * 8 / (n^2 * max_nodes sum_d (|Ja^d.v| + c |Ja^d|)/J)
+ *               (the RK3 stability limit of the DGSEM operator shrinks like 1/n^2;
+ *               at n = 4 this equals cfl * 2 / (n * ...))
  *   viscous     dt_v = 12 / (n^4 * max_nodes (mu/rho) sum_d (|Ja^d|/J)^2)
  *               (= h^2/(nu n^4) on a straight box; Navier-Stokes only)
  *   dt = min(dt_c, dt_v). */
@@ -776,7 +778,7 @@ double orc_dt(const orc_mesh *m, const orc_cfg *cfg, const double *u)
             if (sc > lam_c) lam_c = sc;
             if (mu * sv / rho > lam_v) lam_v = mu * sv / rho;
         }
-    double dt = cfg->cfl * 2.0 / (n * lam_c);
+    double dt = cfg->cfl * 8.0 / ((double)n * n * lam_c);
     if (lam_v > 0.0) {
         double dtv = 12.0 / ((double)n * n * n * n * lam_v);
         if (dtv < dt) dt = dtv;

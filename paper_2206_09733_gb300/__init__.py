@@ -36,7 +36,7 @@ EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh
            "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
            "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
            "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
-           "hs3d_diagnostics_noalloc"]
+           "hs3d_diagnostics_noalloc", "hs3d_autotune"]
 
 
 class HS3DError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
                 "hs3d_rk3_step_profiled": [vp, C.POINTER(SolverCfg), vp, vp, d, C.POINTER(d), vp],
                 "hs3d_alu_peaks": [C.POINTER(d), vp],
                 "hs3d_diagnostics_noalloc": [i, C.c_int64, d, vp, vp, vp, vp, vp],
+                "hs3d_autotune": [vp, C.POINTER(SolverCfg), C.POINTER(i), vp],
                 "hs3d_last_error": [],
                 "hs3d_version": [],
             }
@@ -239,10 +240,23 @@ class Mesh:
         check(lib().hs3d_dt(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(out, "dt_out"), _stream(stream)))
         return out
 
-    def clock(self, reset=False, stream=None):
+    def clock(self, reset=False, stream=None, check_state=True):
+        """(simulated time, steps) of this mesh's clock; raises on a
+        non-physical state unless check_state=False, which returns
+        (time, steps, status) instead."""
         t, s = C.c_double(), C.c_int64()
-        check(lib().hs3d_clock(self._h, C.byref(t), C.byref(s), int(reset), _stream(stream)))
+        st = lib().hs3d_clock(self._h, C.byref(t), C.byref(s), int(reset), _stream(stream))
+        if not check_state:
+            return t.value, s.value, st
+        check(st)
         return t.value, s.value
+
+    def autotune(self, cfg: SolverCfg, stream=None):
+        """Pick the fastest elements-per-CTA of the gradient and element
+        kernels for this mesh and cfg; returns (gradient, element)."""
+        ch = (C.c_int * 2)()
+        check(lib().hs3d_autotune(self._h, C.byref(cfg), ch, _stream(stream)))
+        return ch[0], ch[1]
 
     def diagnostics(self, cfg: SolverCfg, u, out, dudt=None, stream=None):
         check(lib().hs3d_diagnostics(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(dudt, "dudt"), _ptr(out, "out"),

@@ -31,6 +31,7 @@ hs3d_status cuda_fail(cudaError_t e, const char *what)
 
 cudaError_t prepare_kernels(int N)
 {
+    tune_cache_load();
     if (!device_ops(N)) return cudaErrorMemoryAllocation;
     cudaError_t e = prepare_volume(N);
     if (e == cudaSuccess) e = prepare_grad(N);
@@ -73,7 +74,8 @@ hs3d_status validate_desc(const hs3d_mesh_desc *d)
 size_t mesh_bytes(int N, long long E)
 {
     long long n = N + 1, n2 = n * n, n3 = n2 * n;
-    size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) + sizeof(double) * 3 * (size_t)E * 3 * n2;
+    size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) + sizeof(float) * (size_t)E * n3 * 9 +
+                 sizeof(double) * 3 * (size_t)E * 3 * n2;
     size_t scratch = sizeof(double) * (3 * (size_t)E * 5 * n2 + (size_t)E * 12 * n3);
     return geo + scratch + sizeof(Clock) + 4096 * 7 * sizeof(double);
 }
@@ -87,6 +89,7 @@ static hs3d_status mesh_alloc(hs3d_mesh *m)
     } allocs[] = {
         {(void **)&m->X, sizeof(double) * E * 3 * n3},
         {(void **)&m->Ja, sizeof(double) * E * 9 * n3},
+        {(void **)&m->Jaf, sizeof(float) * E * 9 * n3},
         {(void **)&m->J, sizeof(double) * E * n3},
         {(void **)&m->invJ, sizeof(double) * E * n3},
         {(void **)&m->fn, sizeof(double) * 3 * E * 3 * n2},
@@ -110,7 +113,7 @@ void mesh_free(hs3d_mesh *m)
 {
     if (!m) return;
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    void *ptrs[] = {m->X, m->Ja, m->J, m->invJ, m->fn, m->fstar, m->grad, m->clk, m->diag_partials};
+    void *ptrs[] = {m->X, m->Ja, m->Jaf, m->J, m->invJ, m->fn, m->fstar, m->grad, m->clk, m->diag_partials};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->stream) cudaStreamDestroy(m->stream);
@@ -167,8 +170,8 @@ hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out)
             return cuda_fail(e, "uploading node_xyz");
         }
     }
-    e = launch_geometry(m->N, xyz_dev, m->ex, m->ey, m->ez, m->lo, m->hi, m->amp, m->X, m->Ja, m->J, m->invJ, m->fn,
-                        m->stream);
+    e = launch_geometry(m->N, xyz_dev, m->ex, m->ey, m->ez, m->lo, m->hi, m->amp, m->X, m->Ja, m->Jaf, m->J, m->invJ,
+                        m->fn, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->clk, 0, sizeof(Clock), m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (xyz_dev) cudaFree(xyz_dev);
@@ -184,6 +187,7 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
 {
     Item it{};
     it.Ja = m->Ja;
+    it.Jaf = m->Jaf;
     it.invJ = m->invJ;
     it.fn = m->fn;
     it.J = m->J;
@@ -219,22 +223,37 @@ Batch single_batch(const Item &it)
 }
 
 // Residual of a batch: [BR1 gradients] -> faces -> volume/lift/scale (+ RK stage).
-cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int stage, cudaStream_t s)
+cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int stage, int lam_slot, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
     if (c->physics == HS3D_NS) e = launch_grad(N, c->precision, b, s);
     if (e == cudaSuccess) e = launch_face(N, c->precision, c->physics, c->surface_flux, b, s);
-    if (e == cudaSuccess) e = launch_volume(N, c->precision, c->physics, c->volume_form, b, stage, s);
+    if (e == cudaSuccess) e = launch_volume(N, c->precision, c->physics, c->volume_form, b, stage, lam_slot, s);
     return e;
 }
 
-cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt, cudaStream_t s)
+// One RK3 step of a batch.  The dt maxima come from clock slot 0 filled by a
+// fresh k_lambda pass (fresh_lambda != 0, a single step on a state the caller
+// may have changed), or from slot 1, filled by the previous step's last
+// stage (or by prime_lambda before the first step of a run).  The last stage
+// always refills slot 1 for the next step.
+cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt, int fresh_lambda, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
     b.dt_fixed = dt > 0.0 ? dt : 0.0;
-    if (!(dt > 0.0)) e = launch_lambda(N, c->physics, b, s);
-    if (e == cudaSuccess) e = launch_dt_finalize(N, b, 0, s);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = enqueue_stage(N, c, b, k, s);
+    int slot = fresh_lambda ? 0 : 1;
+    if (fresh_lambda && !(dt > 0.0)) e = launch_lambda(N, c->precision, c->physics, b, 0, s);
+    if (e == cudaSuccess) e = launch_dt_finalize(N, b, 0, slot, s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = enqueue_stage(N, c, b, k, k == 2 ? 1 : -1, s);
+    return e;
+}
+
+// Fill clock slot 1 from the current state (before the first step of a run).
+cudaError_t prime_lambda(int N, const hs3d_solver_cfg *c, const Batch &b, Clock *clk, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (clk) e = cudaMemsetAsync(&clk->lam[1][0], 0, sizeof(clk->lam[1]), s);
+    if (e == cudaSuccess) e = launch_lambda(N, c->precision, c->physics, b, 1, s);
     return e;
 }
 
@@ -307,7 +326,7 @@ hs3d_status hs3d_residual(const hs3d_mesh *m, const hs3d_solver_cfg *c, const do
     if ((const void *)u == (const void *)dudt) return fail(HS3D_ERR_INVALID, "u and dudt must differ");
     Item it = make_item(m, c, u, nullptr, dudt);
     it.clk = nullptr;
-    cudaError_t e = enqueue_stage(m->N, c, single_batch(it), -1, (cudaStream_t)stream);
+    cudaError_t e = enqueue_stage(m->N, c, single_batch(it), -1, -1, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
 }
 
@@ -320,7 +339,7 @@ hs3d_status hs3d_rk3_step(const hs3d_mesh *m, const hs3d_solver_cfg *c, double *
     if (st != HS3D_OK) return st;
     if (u == g) return fail(HS3D_ERR_INVALID, "u and g must differ");
     Item it = make_item(m, c, u, g, nullptr);
-    cudaError_t e = enqueue_rk3_step(m->N, c, single_batch(it), dt, (cudaStream_t)stream);
+    cudaError_t e = enqueue_rk3_step(m->N, c, single_batch(it), dt, 1, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "rk3 step launch");
 }
 
@@ -348,7 +367,7 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = enqueue_rk3_step(m->N, c, single_batch(it), dt, m->stream);
+            cudaError_t e2 = enqueue_rk3_step(m->N, c, single_batch(it), dt, 0, m->stream);
             e = cudaStreamEndCapture(m->stream, &graph);
             if (e2 != cudaSuccess) e = e2;
         }
@@ -364,6 +383,10 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
         m->g_dt = dt;
         m->g_cfg = *c;
     }
+    if (!(dt > 0.0)) {
+        Item it = make_item(m, c, u, g, nullptr);
+        e = prime_lambda(m->N, c, single_batch(it), m->clk, (cudaStream_t)stream);
+    }
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(m->gexec, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");
 }
@@ -377,8 +400,8 @@ hs3d_status hs3d_dt(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *
     if (st != HS3D_OK) return st;
     Item it = make_item(m, c, u, nullptr, dt_out);
     Batch b = single_batch(it);
-    cudaError_t e = launch_lambda(m->N, c->physics, b, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 2, (cudaStream_t)stream);
+    cudaError_t e = launch_lambda(m->N, c->precision, c->physics, b, 0, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 2, 0, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "dt launch");
 }
 

@@ -13,6 +13,7 @@ struct hs3d_mesh {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, amp = 0.0;
     int device = 0;
     double *X = nullptr, *Ja = nullptr, *J = nullptr, *invJ = nullptr, *fn = nullptr;
+    float *Jaf = nullptr;
     void *fstar = nullptr;          // scratch, sized for FP64
     void *grad = nullptr;           // scratch, sized for FP64
     hs3d::Clock *clk = nullptr;
@@ -39,7 +40,8 @@ void mesh_free(hs3d_mesh *m);
 size_t mesh_bytes(int N, long long E);
 Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, double *g, double *out);
 Batch single_batch(const Item &it);
-cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int stage, cudaStream_t s);
-cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt, cudaStream_t s);
+cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int stage, int lam_slot, cudaStream_t s);
+cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt, int fresh_lambda, cudaStream_t s);
+cudaError_t prime_lambda(int N, const hs3d_solver_cfg *c, const Batch &b, Clock *clk, cudaStream_t s);
 
 }  // namespace hs3d

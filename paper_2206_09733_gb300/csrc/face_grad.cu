@@ -24,12 +24,6 @@ __device__ __forceinline__ int face_node(int d, int end, int ta, int tb)
     return ta + n * (tb + n * end);
 }
 
-template <typename R>
-struct Side {
-    Prim<R> q;
-    R E;
-};
-
 template <int N, typename R, bool NS>
 __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, int flux)
 {
@@ -63,7 +57,7 @@ __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, i
     const R gam = (R)it.gamma, gm1 = (R)gm1d;
     R fs[5];
     if (flux == HS3D_FLUX_EC) {
-        flux_ec(ec_node(qL), ec_node(qR), gm1, s1, s2, s3, fs);
+        flux_ec(ec_node(qL), ec_node(qR), (R)(0.5 / gm1d), s1, s2, s3, fs);
     } else {
         R ul[5], du[5];
 #pragma unroll
@@ -105,20 +99,40 @@ constexpr int grad_threads()
     return ((N + 1) * (N + 1) * (N + 1) > 256) ? (N + 1) * (N + 1) * (N + 1) : 256;
 }
 
+template <typename R>
+__device__ __forceinline__ void grad_vars(const Prim<R> &q, R out[4])
+{
+    out[0] = q.v1;
+    out[1] = q.v2;
+    out[2] = q.v3;
+    out[3] = q.p / q.rho;
+}
+
+template <typename R>
+__device__ __forceinline__ const R *grad_metric(const Item &it);
+template <>
+__device__ __forceinline__ const double *grad_metric<double>(const Item &it) { return it.Ja; }
+template <>
+__device__ __forceinline__ const float *grad_metric<float>(const Item &it) { return it.Jaf; }
+
+// Shared memory per element: q [4][n3], Ja [9][n3], neighbour traces of q
+// [6 faces][4][n2] (slot 2d: the -d face, slot 2d+1: the +d face).  The
+// neighbour traces are gathered by all threads of the element before the
+// barrier, so the lifting reads no global memory.
 template <int N, typename R>
 __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constant__ Batch b, const Ops *__restrict__ ops)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int PER_ELEM = 13 * n3 + 24 * n2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sD = (R *)smem_raw;                      // n*n
-    R *sq = sD + ((n * n + 1) & ~1);            // [epb][4][n3]
+    R *sE = sD + ((n * n + 1) & ~1);            // [epb][PER_ELEM]
     const int epb = blockDim.x / n3;
-    R *sJa = sq + epb * 4 * n3;                 // [epb][9][n3]
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = (R)ops->D[t];
     const double w0 = ops->w[0];
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
     const long long ge = blockIdx.x * (long long)epb + le;
-    bool valid = (le < epb) && ge < b.total_elems;
+    bool valid = ge < b.total_elems;
     const Item *itp = nullptr;
     int e = 0;
     if (valid) {
@@ -126,26 +140,37 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
         e = (int)(ge - itp->elem_begin);
         if (itp->clk && itp->clk->done) valid = false;
     }
-    R *q = sq + le * 4 * n3;
-    R *ja = sJa + le * 9 * n3;
-    double qin[4];
-    const double gm1 = valid ? itp->gamma - 1.0 : 0.4;
+    R *q = sE + (size_t)le * PER_ELEM;
+    R *ja = q + 4 * n3;
+    R *qn = ja + 9 * n3;
+    R qin[4];
     if (valid) {
-        const double *U = itp->u + (size_t)e * 5 * n3 + p;
+        const Item &it = *itp;
+        const double gm1 = it.gamma - 1.0;
+        for (int t = p; t < 6 * n2; t += n3) {
+            const int slot = t / n2, ab = t - slot * n2;
+            const int d = slot >> 1, plus = slot & 1;
+            const int nb = plus ? nbr_plus(e, d, it.ex, it.ey, it.ez) : nbr_minus(e, d, it.ex, it.ey, it.ez);
+            const int pn = face_node<n>(d, plus ? 0 : N, ab % n, ab / n);
+            const double *U = it.u + (size_t)nb * 5 * n3 + pn;
+            double u[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
+            R g4[4];
+            grad_vars(prim_from_u<R>(u, gm1), g4);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) qn[(slot * 4 + v) * n2 + ab] = g4[v];
+        }
+        const double *U = it.u + (size_t)e * 5 * n3 + p;
         double u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
-        double ir = 1.0 / u[0];
-        qin[0] = u[1] * ir;
-        qin[1] = u[2] * ir;
-        qin[2] = u[3] * ir;
-        double pr = gm1 * (u[4] - 0.5 * (u[1] * qin[0] + u[2] * qin[1] + u[3] * qin[2]));
-        qin[3] = pr * ir;
+        grad_vars(prim_from_u<R>(u, gm1), qin);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) q[v * n3 + p] = (R)qin[v];
-        const double *JA = itp->Ja + (size_t)e * 9 * n3 + p;
+        for (int v = 0; v < 4; ++v) q[v * n3 + p] = qin[v];
+        const R *JA = grad_metric<R>(it) + (size_t)e * 9 * n3 + p;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) ja[k * n3 + p] = (R)JA[k * n3];
+        for (int k = 0; k < 9; ++k) ja[k * n3 + p] = JA[k * n3];
     }
     __syncthreads();
     if (!valid) return;
@@ -173,35 +198,24 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
             }
         }
     }
-    // surface lifting of the BR1 jumps
+    // surface lifting of the BR1 jumps (q* - q_in) = (q_out - q_in)/2
     const Item &it = *itp;
     const R iw = (R)(1.0 / w0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+        const int ta = (d == 0) ? ijk[1] : ijk[0];
+        const int tb = (d == 2) ? ijk[1] : ijk[2];
+        const int ab = ta + n * tb;
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int end = side ? N : 0;
-            if (ijk[d] != end) continue;
-            const int nb = side ? nbr_plus(e, d, it.ex, it.ey, it.ez) : nbr_minus(e, d, it.ex, it.ey, it.ez);
-            const int ta = (d == 0) ? ijk[1] : ijk[0];
-            const int tb = (d == 2) ? ijk[1] : ijk[2];
-            const int pn = face_node<n>(d, side ? 0 : N, ta, tb);
-            const double *U = it.u + (size_t)nb * 5 * n3 + pn;
-            double u[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
-            double ir = 1.0 / u[0];
-            double qo[4];
-            qo[0] = u[1] * ir;
-            qo[1] = u[2] * ir;
-            qo[2] = u[3] * ir;
-            qo[3] = gm1 * (u[4] - 0.5 * (u[1] * qo[0] + u[2] * qo[1] + u[3] * qo[2])) * ir;
-            const R sg = side ? (R)1 : (R)-1;
+        for (int plus = 0; plus < 2; ++plus) {
+            if (ijk[d] != (plus ? N : 0)) continue;
+            const R sg = plus ? (R)1 : (R)-1;
             const R n1 = sg * ja[(d * 3 + 0) * n3 + p], n2_ = sg * ja[(d * 3 + 1) * n3 + p],
                     n3_ = sg * ja[(d * 3 + 2) * n3 + p];
+            const int slot = 2 * d + plus;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const R j = (R)(0.5 * (qo[v] - qin[v])) * iw;
+                const R j = (R)0.5 * (qn[(slot * 4 + v) * n2 + ab] - qin[v]) * iw;
                 acc[v * 3 + 0] += j * n1;
                 acc[v * 3 + 1] += j * n2_;
                 acc[v * 3 + 2] += j * n3_;
@@ -233,9 +247,10 @@ static cudaError_t grad_launch(const Batch &b, cudaStream_t s)
 {
     constexpr int n = N + 1, n3 = n * n * n;
     if (b.total_elems == 0) return cudaSuccess;
-    int epb = elems_per_block(N, 0);
+    int epb = elems_per_block_p(N, sizeof(R) == 4 ? HS3D_MIXED32 : HS3D_FP64, 0);
+    if (epb * n3 > grad_threads<N>()) epb = grad_threads<N>() / n3;
     int threads = epb * n3;
-    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * 13 * n3);
+    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * (13 * n3 + 24 * (N + 1) * (N + 1)));
     unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;

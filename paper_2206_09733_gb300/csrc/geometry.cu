@@ -121,7 +121,8 @@ template <int N>
 __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
 k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, double lo1, double lo2, double hi0,
            double hi1, double hi2, double amp, const Ops *__restrict__ ops, double *__restrict__ X,
-           double *__restrict__ Ja, double *__restrict__ J, double *__restrict__ invJ, double *__restrict__ fn)
+           double *__restrict__ Ja, float *__restrict__ Jaf, double *__restrict__ J, double *__restrict__ invJ,
+           double *__restrict__ fn)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     __shared__ double sD[n * n];
@@ -181,6 +182,7 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
             __syncthreads();
             double v = deriv(sT[0], i2) - deriv(sT[1], i1);
             Ja[(((size_t)e * 3 + i) * 3 + c) * n3 + p] = v;
+            Jaf[(((size_t)e * 3 + i) * 3 + c) * n3 + p] = (float)v;
             if (ijk[i] == N) {
                 // tangential (a,b) index of this node on the +i face
                 int ta = (i == 0) ? ijk[1] : ijk[0];
@@ -192,7 +194,7 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
 }
 
 cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
-                            const double *hi, double amp, double *X, double *Ja, double *J, double *invJ,
+                            const double *hi, double amp, double *X, double *Ja, float *Jaf, double *J, double *invJ,
                             double *fn, cudaStream_t s)
 {
     const Ops *ops = device_ops(N);
@@ -202,7 +204,7 @@ cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, i
 #define HS3D_GEO(NN)                                                                                            \
     case NN:                                                                                                    \
         k_geometry<NN><<<E, n3, 0, s>>>(node_xyz_dev, ex, ey, ez, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], amp, \
-                                        ops, X, Ja, J, invJ, fn);                                               \
+                                        ops, X, Ja, Jaf, J, invJ, fn);                                          \
         break;
     switch (N) {
         HS3D_GEO(1) HS3D_GEO(2) HS3D_GEO(3) HS3D_GEO(4) HS3D_GEO(5) HS3D_GEO(6) HS3D_GEO(7)

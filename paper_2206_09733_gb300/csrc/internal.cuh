@@ -4,6 +4,7 @@
 // block and every warp load of a node-indexed field is coalesced):
 //   u, g, dudt  double [E][5][n3]             conserved variables
 //   Ja          double [E][3(d)][3(c)][n3]     Ja^d_c = J dxi_d/dx_c (curl form)
+//   Jaf         float  [E][3(d)][3(c)][n3]     the same, rounded once for the FP32 flux arithmetic
 //   invJ        double [E][n3]                 1/J
 //   fn          double [3(d)][E][3(c)][n2]     scaled normal Ja^d of face (d, e) taken
 //                                              from element e on its +d face
@@ -25,8 +26,10 @@ constexpr int kMaxn = kMaxN + 1;
 
 // Per-solve device clock: dt rule inputs and the simulated time.
 struct Clock {
-    unsigned long long lam_c;   // bits of max convective rate (non-negative double)
-    unsigned long long lam_v;   // bits of max viscous rate
+    // Bits of the max convective / viscous rates (non-negative doubles), two
+    // slots: [0] filled by k_lambda before a single step, [1] filled by the
+    // last RK stage of the previous step (or by k_lambda before a run).
+    unsigned long long lam[2][2];
     double dt;                  // dt of the current step
     double t;                   // simulated time after the current step
     double t_final;             // > 0: clip dt so that t reaches t_final exactly
@@ -40,6 +43,7 @@ struct Clock {
 // One solve (mesh + state) inside a launch.
 struct Item {
     const double *Ja;
+    const float *Jaf;       // FP32 copy of Ja (the mixed path rounds Ja to FP32 anyway)
     const double *invJ;
     const double *fn;
     const double *J;       // for diagnostics
@@ -100,6 +104,34 @@ __device__ __forceinline__ const Item &find_item_face(const Batch &b, long long 
     return b.items[lo];
 }
 
+// Max-reduce non-negative rates over the lanes of a warp that share the same
+// clock (threads map to consecutive nodes and an item's elements are
+// consecutive, so each group is a contiguous run of lanes) and add them to
+// that clock slot with one atomic per group.  All 32 lanes must call this.
+__device__ __forceinline__ void warp_max_to_clock(unsigned long long *dst_c, unsigned long long *dst_v, double lc,
+                                                  double lv, bool active)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned long long key = active ? (unsigned long long)dst_c : 0ull;
+    unsigned peers = __match_any_sync(full, key);
+    const int first = __ffs(peers) - 1;
+    const int last = 31 - __clz(peers);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        double oc = __shfl_down_sync(full, lc, off);
+        double ov = __shfl_down_sync(full, lv, off);
+        if (lane + off <= last) {
+            lc = fmax(lc, oc);
+            lv = fmax(lv, ov);
+        }
+    }
+    if (active && lane == first) {
+        atomicMax(dst_c, (unsigned long long)__double_as_longlong(lc));
+        if (dst_v) atomicMax(dst_v, (unsigned long long)__double_as_longlong(lv));
+    }
+}
+
 // Element neighbour across direction d (+1 side), periodic.
 __device__ __forceinline__ int nbr_plus(int e, int d, int ex, int ey, int ez)
 {
@@ -121,15 +153,19 @@ __device__ __forceinline__ int nbr_minus(int e, int d, int ex, int ey, int ez)
 
 // Launch helpers implemented in the .cu files (return cudaError_t of the launch).
 cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
-                            const double *hi, double amp, double *X, double *Ja, double *J, double *invJ,
+                            const double *hi, double amp, double *X, double *Ja, float *Jaf, double *J, double *invJ,
                             double *fn, cudaStream_t s);
 cudaError_t launch_init_state(int N, int E, const double *X, const hs3d_ic &ic, const double *lo, const double *hi,
                               double *u, cudaStream_t s);
-cudaError_t launch_lambda(int N, int physics, const Batch &b, cudaStream_t s);
-cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, cudaStream_t s);
+cudaError_t launch_lambda(int N, int prec, int physics, const Batch &b, int slot, cudaStream_t s);
+// mode 0: advance every item's clock using lambda slot `slot`; mode 2: dt value of b.single into b.single.out
+cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, int slot, cudaStream_t s);
 cudaError_t launch_grad(int N, int prec, const Batch &b, cudaStream_t s);
 cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, cudaStream_t s);
-cudaError_t launch_volume(int N, int prec, int physics, int form, const Batch &b, int stage, cudaStream_t s);
+// stage -1: residual into out; 0..2: RK stage; lam_slot >= 0 (stage 2 only): also accumulate the
+// dt maxima of the updated state into that clock slot
+cudaError_t launch_volume(int N, int prec, int physics, int form, const Batch &b, int stage, int lam_slot,
+                          cudaStream_t s);
 cudaError_t launch_diagnostics(int N, const Item &it, const double *dudt, double *partials, int nblocks, double *out,
                                cudaStream_t s);
 int diagnostics_blocks(int N, int E);
@@ -140,9 +176,12 @@ cudaError_t prepare_kernels(int N);
 cudaError_t prepare_volume(int N);
 cudaError_t prepare_grad(int N);
 
-// Elements per block for the element kernels (threads = epb * n^3);
-// which = 0: BR1 gradient kernel, 1: volume kernel.
-int elems_per_block(int N, int which);
-void set_elems_per_block(int N, int which, int epb);
+// Elements per block for the element kernels (threads = epb * n^3), per
+// (N, precision 0 = FP64 / 1 = mixed, kernel: 0 = BR1 gradient, 1 = volume);
+// the autotuner's choice if one was made, else 256 threads' worth.
+int elems_per_block_p(int N, int prec, int which);
+int tuned_elems_per_block(int N, int prec, int which);   // 0 if untuned
+void set_elems_per_block_p(int N, int prec, int which, int epb);
+void tune_cache_load();
 
 }  // namespace hs3d

@@ -18,20 +18,38 @@ struct Prim {
     R rho, v1, v2, v3, p;
 };
 
-// Primitive variables computed in FP64 from the FP64 state (the subtraction
-// rho e - rho|v|^2/2 cancels at low Mach), then rounded to R.
+// Primitive variables from the FP64 conserved state.  FP64 path: in FP64.
+// Mixed path: the state is rounded to FP32 once and the primitives computed
+// in FP32 (at Mach 0.1, rho e / p ~ 2.5, so the subtraction loses no more than
+// rounding p itself to FP32 would).
 template <typename R>
-__device__ __forceinline__ Prim<R> prim_from_u(const double u[5], double gm1)
+__device__ __forceinline__ Prim<R> prim_from_u(const double u[5], double gm1);
+
+template <>
+__device__ __forceinline__ Prim<double> prim_from_u<double>(const double u[5], double gm1)
 {
     double ir = 1.0 / u[0];
     double v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
-    double p = gm1 * (u[4] - 0.5 * (u[1] * v1 + u[2] * v2 + u[3] * v3));
-    Prim<R> q;
-    q.rho = (R)u[0];
-    q.v1 = (R)v1;
-    q.v2 = (R)v2;
-    q.v3 = (R)v3;
-    q.p = (R)p;
+    Prim<double> q;
+    q.rho = u[0];
+    q.v1 = v1;
+    q.v2 = v2;
+    q.v3 = v3;
+    q.p = gm1 * (u[4] - 0.5 * (u[1] * v1 + u[2] * v2 + u[3] * v3));
+    return q;
+}
+
+template <>
+__device__ __forceinline__ Prim<float> prim_from_u<float>(const double u[5], double gm1)
+{
+    const float r = (float)u[0], m1 = (float)u[1], m2 = (float)u[2], m3 = (float)u[3], E = (float)u[4];
+    const float ir = __frcp_rn(r);
+    Prim<float> q;
+    q.rho = r;
+    q.v1 = m1 * ir;
+    q.v2 = m2 * ir;
+    q.v3 = m3 * ir;
+    q.p = (float)gm1 * (E - 0.5f * (m1 * q.v1 + m2 * q.v2 + m3 * q.v3));
     return q;
 }
 
@@ -160,21 +178,12 @@ struct LogMeanEps<float> {
     static constexpr float v = 1e-2f;
 };
 
-// Logarithmic mean (a-b)/(ln a - ln b) from precomputed logarithms; near
-// a = b the series (a+b)/(2(1 + u/3 + u^2/5 + u^3/7)), u = ((a-b)/(a+b))^2
-// (Ismail & Roe) avoids the 0/0.
 template <typename R>
-__device__ __forceinline__ R log_mean(R a, R b, R la, R lb)
-{
-    R d = a - b, sum = a + b;
-    R f = d / sum;
-    R u = f * f;
-    if (u < LogMeanEps<R>::v) {
-        R F = (R)1 + u * ((R)(1.0 / 3.0) + u * ((R)0.2 + u * (R)(1.0 / 7.0)));
-        return sum / ((R)2 * F);
-    }
-    return d / (la - lb);
-}
+__device__ __forceinline__ R rcp_(R x);
+template <>
+__device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
+template <>
+__device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
 
 // Per-node quantities the Chandrashekar flux uses.
 template <typename R>
@@ -201,20 +210,42 @@ __device__ __forceinline__ ECNode<R> ec_node(const Prim<R> &q)
 // means, p~ = {rho}/(2{beta}),
 //   f_rho = rho^ {v}.a,  f_m = f_rho {v} + p~ a,
 //   f_E = f_rho (1/(2(gamma-1) beta^) - {|v|^2}/2) + {v}.f_m.
+// Logarithmic mean L(a,b) = (a-b)/(ln a - ln b) with the logarithms taken per
+// node; near a = b (u = ((a-b)/(a+b))^2 below LogMeanEps) the Ismail-Roe
+// series L = (a+b)/(2F), F = 1 + u/3 + u^2/5 + u^3/7, is used: for rho^ as
+// (a+b)/2 times the series of 1/F to the same order (1 - u/3 - 4u^2/45 -
+// 44u^3/945), for 1/beta^ directly as 2F/(a+b).  Only the two reciprocals
+// 1/(rho_L+rho_R) and 1/(beta_L+beta_R) are needed on that branch;
+// hg = 1/(2(gamma-1)).
 template <typename R>
-__device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr, R gm1, R a1, R a2, R a3, R f[5])
+__device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr, R hg, R a1, R a2, R a3, R f[5])
 {
-    R rho_ln = log_mean(L.rho, Rr.rho, L.lrho, Rr.lrho);
-    R beta_ln = log_mean(L.beta, Rr.beta, L.lbeta, Rr.lbeta);
-    R m1 = (R)0.5 * (L.v1 + Rr.v1), m2 = (R)0.5 * (L.v2 + Rr.v2), m3 = (R)0.5 * (L.v3 + Rr.v3);
-    R v2 = (R)0.5 * ((L.v1 * L.v1 + L.v2 * L.v2 + L.v3 * L.v3) + (Rr.v1 * Rr.v1 + Rr.v2 * Rr.v2 + Rr.v3 * Rr.v3));
-    R pt = (L.rho + Rr.rho) / ((R)2 * (L.beta + Rr.beta));
-    R fr = rho_ln * (m1 * a1 + m2 * a2 + m3 * a3);
-    f[0] = fr;
-    f[1] = fr * m1 + pt * a1;
-    f[2] = fr * m2 + pt * a2;
-    f[3] = fr * m3 + pt * a3;
-    f[4] = fr * ((R)1 / ((R)2 * gm1 * beta_ln) - (R)0.5 * v2) + m1 * f[1] + m2 * f[2] + m3 * f[3];
+    const R srho = L.rho + Rr.rho, sbeta = L.beta + Rr.beta;
+    const R irho = rcp_(srho), ibeta = rcp_(sbeta);
+    const R dr = L.rho - Rr.rho;
+    const R fr = dr * irho, ur = fr * fr;
+    R rho_ln;
+    if (ur < LogMeanEps<R>::v)
+        rho_ln = (R)0.5 * srho * ((R)1 - ur * ((R)(1.0 / 3.0) + ur * ((R)(4.0 / 45.0) + ur * (R)(44.0 / 945.0))));
+    else
+        rho_ln = dr / (L.lrho - Rr.lrho);
+    const R db = L.beta - Rr.beta;
+    const R fb = db * ibeta, ub = fb * fb;
+    R ibeta_ln;
+    if (ub < LogMeanEps<R>::v)
+        ibeta_ln = (R)2 * ibeta * ((R)1 + ub * ((R)(1.0 / 3.0) + ub * ((R)0.2 + ub * (R)(1.0 / 7.0))));
+    else
+        ibeta_ln = (L.lbeta - Rr.lbeta) / db;
+    const R m1 = (R)0.5 * (L.v1 + Rr.v1), m2 = (R)0.5 * (L.v2 + Rr.v2), m3 = (R)0.5 * (L.v3 + Rr.v3);
+    const R v2 =
+        (R)0.5 * ((L.v1 * L.v1 + L.v2 * L.v2 + L.v3 * L.v3) + (Rr.v1 * Rr.v1 + Rr.v2 * Rr.v2 + Rr.v3 * Rr.v3));
+    const R pt = (R)0.5 * srho * ibeta;
+    const R fm = rho_ln * (m1 * a1 + m2 * a2 + m3 * a3);
+    f[0] = fm;
+    f[1] = fm * m1 + pt * a1;
+    f[2] = fm * m2 + pt * a2;
+    f[3] = fm * m3 + pt * a3;
+    f[4] = fm * (hg * ibeta_ln - (R)0.5 * v2) + m1 * f[1] + m2 * f[2] + m3 * f[3];
 }
 
 }  // namespace hs3d

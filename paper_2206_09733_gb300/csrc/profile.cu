@@ -80,8 +80,8 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
     Batch b = single_batch(make_item(m, c, u, g, nullptr));
     b.dt_fixed = dt > 0.0 ? dt : 0.0;
     cudaError_t e = cudaEventRecord(ev[0], s);
-    if (e == cudaSuccess && !(dt > 0.0)) e = launch_lambda(m->N, c->physics, b, s);
-    if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 0, s);
+    if (e == cudaSuccess && !(dt > 0.0)) e = launch_lambda(m->N, c->precision, c->physics, b, 0, s);
+    if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 0, 0, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     int k = 2;
     for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
@@ -89,7 +89,8 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
         if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
         if (e == cudaSuccess) e = launch_face(m->N, c->precision, c->physics, c->surface_flux, b, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
-        if (e == cudaSuccess) e = launch_volume(m->N, c->precision, c->physics, c->volume_form, b, stage, s);
+        if (e == cudaSuccess)
+            e = launch_volume(m->N, c->precision, c->physics, c->volume_form, b, stage, stage == 2 ? 1 : -1, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[k - 1]);

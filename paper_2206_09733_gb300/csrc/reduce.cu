@@ -2,7 +2,8 @@
 //
 // Time step (the paper names explicit RK3 with a CFL condition, Sec. 3.7, but
 // gives no formula; this library uses)
-//   dt_c = cfl * 2 / (n * max_nodes sum_d (|Ja^d.v| + c |Ja^d|)/J)
+//   dt_c = cfl * 8 / (n^2 * max_nodes sum_d (|Ja^d.v| + c |Ja^d|)/J)
+//          (the RK3 stability limit of the DGSEM operator shrinks like 1/n^2)
 //   dt_v = 12 / (n^4 * max_nodes (mu/rho) sum_d (|Ja^d|/J)^2)      (Navier-Stokes)
 //   dt   = min(dt_c, dt_v), clipped to reach t_final exactly.
 // The maxima are taken with atomicMax on the bit patterns of non-negative
@@ -14,17 +15,24 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "physics.cuh"
 
 namespace hs3d {
 
-template <int N>
-__global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b, int ns)
+template <typename R>
+__device__ __forceinline__ const R *lambda_metric(const Item &it);
+template <>
+__device__ __forceinline__ const double *lambda_metric<double>(const Item &it) { return it.Ja; }
+template <>
+__device__ __forceinline__ const float *lambda_metric<float>(const Item &it) { return it.Jaf; }
+
+template <int N, typename R>
+__global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b, int ns, int slot)
 {
     constexpr int n = N + 1, n3 = n * n * n;
-    __shared__ double s_lc[256], s_lv[256];
-    __shared__ const Item *s_it[256];
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double lc = 0.0, lv = 0.0;
+    bool active = false;
     const Item *itp = nullptr;
     if (t < b.total_elems * n3) {
         const long long ge = t / n3;
@@ -33,54 +41,48 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b,
         const Item &it = *itp;
         const int e = (int)(ge - it.elem_begin);
         const double *U = it.u + (size_t)e * 5 * n3 + p;
-        double rho = U[0], ir = 1.0 / rho;
-        double v1 = U[n3] * ir, v2 = U[2 * n3] * ir, v3 = U[3 * n3] * ir;
-        double pr = (it.gamma - 1.0) * (U[4 * n3] - 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3));
-        if (!(rho > 0.0) || !(pr > 0.0)) {
+        double u[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
+        const Prim<R> q = prim_from_u<R>(u, it.gamma - 1.0);
+        if (!(q.rho > (R)0) || !(q.p > (R)0)) {
             it.clk->bad = 1;
         } else {
-            double c = sqrt(it.gamma * pr * ir);
-            const double *JA = it.Ja + (size_t)e * 9 * n3 + p;
-            double iJ = it.invJ[(size_t)e * n3 + p];
-            double sv = 0.0;
+            const R c = sqrt((R)it.gamma * q.p / q.rho);
+            const R *JA = lambda_metric<R>(it) + (size_t)e * 9 * n3 + p;
+            const R iJ = (R)it.invJ[(size_t)e * n3 + p];
+            R sc = (R)0, sv = (R)0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double a1 = JA[(d * 3) * n3], a2 = JA[(d * 3 + 1) * n3], a3 = JA[(d * 3 + 2) * n3];
-                double an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
-                lc += (fabs(a1 * v1 + a2 * v2 + a3 * v3) + c * an) * iJ;
+                const R a1 = JA[(d * 3) * n3], a2 = JA[(d * 3 + 1) * n3], a3 = JA[(d * 3 + 2) * n3];
+                const R an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
+                sc += (fabs(a1 * q.v1 + a2 * q.v2 + a3 * q.v3) + c * an) * iJ;
                 sv += (an * iJ) * (an * iJ);
             }
-            if (ns) lv = it.mu * sv * ir;
+            lc = (double)sc;
+            if (ns) lv = (double)((R)it.mu * sv / q.rho);
+            active = true;
         }
     }
-    s_lc[threadIdx.x] = lc;
-    s_lv[threadIdx.x] = lv;
-    s_it[threadIdx.x] = itp;
-    __syncthreads();
-    // runs of equal items: the first thread of each run reduces it
-    if (itp && (threadIdx.x == 0 || s_it[threadIdx.x - 1] != itp)) {
-        double mc = lc, mv = lv;
-        for (int k = threadIdx.x + 1; k < blockDim.x && s_it[k] == itp; ++k) {
-            mc = fmax(mc, s_lc[k]);
-            mv = fmax(mv, s_lv[k]);
-        }
-        atomicMax(&itp->clk->lam_c, (unsigned long long)__double_as_longlong(mc));
-        if (ns) atomicMax(&itp->clk->lam_v, (unsigned long long)__double_as_longlong(mv));
+    unsigned long long *dc = nullptr, *dv = nullptr;
+    if (active) {
+        dc = &itp->clk->lam[slot][0];
+        dv = ns ? &itp->clk->lam[slot][1] : nullptr;
     }
+    warp_max_to_clock(dc, dv, lc, lv, active);
 }
 
-// One thread per item: dt from the maxima (mode 0) or the fixed dt (mode 1),
-// clipped at t_final; advances the clock and resets the maxima.
-__global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int mode)
+// One thread per item: dt from the maxima in clock slot `slot` (or the fixed
+// dt), clipped at t_final; advances the clock and resets both maxima slots.
+__global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int slot)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.nitems) return;
     const Item &it = (b.nitems == 1) ? b.single : b.items[i];
     Clock *c = it.clk;
-    double lc = __longlong_as_double((long long)c->lam_c);
-    double lv = __longlong_as_double((long long)c->lam_v);
-    c->lam_c = 0ull;
-    c->lam_v = 0ull;
+    double lc = __longlong_as_double((long long)c->lam[slot][0]);
+    double lv = __longlong_as_double((long long)c->lam[slot][1]);
+    c->lam[0][0] = c->lam[0][1] = c->lam[1][0] = c->lam[1][1] = 0ull;
     // a solve that has reached its stopping rule takes no further step
     if (c->done || (c->t_final > 0.0 && c->t >= c->t_final) || (c->nsteps > 0 && c->step >= c->nsteps)) {
         c->done = 1;
@@ -93,7 +95,7 @@ __global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int mode)
     } else if (c->dt_fixed > 0.0) {
         dt = c->dt_fixed;
     } else {
-        dt = it.cfl * 2.0 / (n * lc);
+        dt = it.cfl * 8.0 / ((double)n * n * lc);
         if (lv > 0.0) {
             double n4 = (double)n * n * n * n;
             double dtv = 12.0 / (n4 * lv);
@@ -119,43 +121,43 @@ __global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int mode)
 // dt only (no clock update): writes the rule's dt to out and resets the maxima.
 __global__ void k_dt_value(Clock *c, int n, double cfl, double *out)
 {
-    double lc = __longlong_as_double((long long)c->lam_c);
-    double lv = __longlong_as_double((long long)c->lam_v);
-    c->lam_c = 0ull;
-    c->lam_v = 0ull;
-    double dt = cfl * 2.0 / (n * lc);
+    double lc = __longlong_as_double((long long)c->lam[0][0]);
+    double lv = __longlong_as_double((long long)c->lam[0][1]);
+    c->lam[0][0] = 0ull;
+    c->lam[0][1] = 0ull;
+    double dt = cfl * 8.0 / ((double)n * n * lc);
     if (lv > 0.0) dt = fmin(dt, 12.0 / ((double)n * n * n * n * lv));
     *out = dt;
 }
 
-cudaError_t launch_lambda(int N, int physics, const Batch &b, cudaStream_t s)
+cudaError_t launch_lambda(int N, int prec, int physics, const Batch &b, int slot, cudaStream_t s)
 {
     int n3 = (N + 1) * (N + 1) * (N + 1);
     long long total = b.total_elems * n3;
     if (total == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((total + 255) / 256);
     int ns = physics == HS3D_NS;
+#define HS3D_LAM(K)                                                                                 \
+    case K:                                                                                         \
+        if (prec == HS3D_FP64) k_lambda<K, double><<<blocks, 256, 0, s>>>(b, ns, slot);             \
+        else k_lambda<K, float><<<blocks, 256, 0, s>>>(b, ns, slot);                                \
+        break;
     switch (N) {
-        case 1: k_lambda<1><<<blocks, 256, 0, s>>>(b, ns); break;
-        case 2: k_lambda<2><<<blocks, 256, 0, s>>>(b, ns); break;
-        case 3: k_lambda<3><<<blocks, 256, 0, s>>>(b, ns); break;
-        case 4: k_lambda<4><<<blocks, 256, 0, s>>>(b, ns); break;
-        case 5: k_lambda<5><<<blocks, 256, 0, s>>>(b, ns); break;
-        case 6: k_lambda<6><<<blocks, 256, 0, s>>>(b, ns); break;
-        case 7: k_lambda<7><<<blocks, 256, 0, s>>>(b, ns); break;
+        HS3D_LAM(1) HS3D_LAM(2) HS3D_LAM(3) HS3D_LAM(4) HS3D_LAM(5) HS3D_LAM(6) HS3D_LAM(7)
         default: return cudaErrorInvalidValue;
     }
+#undef HS3D_LAM
     return cudaGetLastError();
 }
 
-cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, cudaStream_t s)
+cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, int slot, cudaStream_t s)
 {
     if (mode == 2) {   // dt value of a single item into b.single.out
         k_dt_value<<<1, 1, 0, s>>>(b.single.clk, N + 1, b.single.cfl, b.single.out);
         return cudaGetLastError();
     }
     unsigned blocks = (unsigned)((b.nitems + 127) / 128);
-    k_dt_finalize<<<blocks, 128, 0, s>>>(b, N + 1, mode);
+    k_dt_finalize<<<blocks, 128, 0, s>>>(b, N + 1, slot);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,11 @@ static hs3d_status admit(hs3d_server *S, ServerReq *r)
     c.t_final = r->req.t_final > 0.0 ? r->req.t_final : 0.0;
     c.nsteps = r->req.t_final > 0.0 ? 0 : r->req.n_steps;
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->mesh->clk, &c, sizeof c, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) {
+        // dt maxima of the initial state, for the first batched step
+        Item it = make_item(r->mesh, &r->req.cfg, r->u, r->g, nullptr);
+        e = prime_lambda(r->mesh->N, &r->req.cfg, single_batch(it), nullptr, S->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     if (e != cudaSuccess) {
         cudaFree(r->u);
@@ -263,7 +268,7 @@ static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
         bt.total_elems = 0;
         for (int k = lo; k < hi; ++k) bt.total_elems += run[k]->mesh->E;
         bt.total_faces = 3 * bt.total_elems;
-        e = enqueue_rk3_step(run[lo]->req.mesh.N, cfgs[b], bt, 0.0, S->stream);
+        e = enqueue_rk3_step(run[lo]->req.mesh.N, cfgs[b], bt, 0.0, 0, S->stream);
     }
     if (e == cudaSuccess) {
         k_gather_clocks<<<(n + 127) / 128, 128, 0, S->stream>>>(S->d_items, n, S->d_clk);

@@ -8,12 +8,17 @@
 //   surface         S = (1/w_end) (F^* - F~^d_in) on the +d face, (1/w_0)(-F^* + F~^d_in) on the -d face
 //                   F^* the face flux computed once per face by k_face
 // followed either by the residual store or by one Williamson low-storage RK3
-// stage (Sec. 3.7) g <- A_k g + dt R, u <- u + B_k g in FP64.
+// stage (Sec. 3.7) g <- A_k g + dt R, u <- u + B_k g in FP64.  After the last
+// stage the kernel also reduces the dt maxima of the updated state (the time
+// step rule's input for the next step) so that no separate pass over the
+// state is needed between steps.
 //
 // One thread per node, `epb` elements per CTA.  The element's contravariant
 // fluxes (standard form) or its per-node two-point-flux inputs (split form)
-// are staged in shared memory; the tensor-product contractions along
-// xi/eta/zeta read them from there.
+// are staged in shared memory; the six face-flux blocks of the element are
+// loaded into shared memory by all of its threads at the start (contiguous
+// 5n^2 chunks), so the surface term reads no global memory after the
+// contraction.
 #include "internal.cuh"
 #include "physics.cuh"
 
@@ -28,13 +33,6 @@ constexpr int vol_threads()
     return ((N + 1) * (N + 1) * (N + 1) > 256) ? (N + 1) * (N + 1) * (N + 1) : 256;
 }
 
-template <int n>
-__device__ __forceinline__ void tangential(int d, const int ijk[3], int &ta, int &tb)
-{
-    ta = (d == 0) ? ijk[1] : ijk[0];
-    tb = (d == 2) ? ijk[1] : ijk[2];
-}
-
 // Number of R values staged per node.
 template <int FORM, bool NS>
 constexpr int vol_smem_per_node()
@@ -42,15 +40,25 @@ constexpr int vol_smem_per_node()
     return FORM == HS3D_VOL_STANDARD ? 15 : (16 + (NS ? 15 : 0));
 }
 
+template <typename R>
+__device__ __forceinline__ const R *metric_ptr(const Item &it);
+template <>
+__device__ __forceinline__ const double *metric_ptr<double>(const Item &it) { return it.Ja; }
+template <>
+__device__ __forceinline__ const float *metric_ptr<float>(const Item &it) { return it.Jaf; }
+
 template <int N, typename R, bool NS, int FORM>
-__global__ void __launch_bounds__(vol_threads<N>()) k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage)
+__global__ void __launch_bounds__(vol_threads<N>())
+k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, int lam_slot)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr int PER = vol_smem_per_node<FORM, NS>();
+    constexpr int FACEVALS = 6 * 5 * n2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sD = (R *)smem_raw;
-    R *sbuf = sD + ((n * n + 1) & ~1);
     const int epb = blockDim.x / n3;
+    R *sbuf = sD + ((n * n + 1) & ~1);
+    R *sface = sbuf + (size_t)epb * PER * n3;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = (R)ops->D[t];
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
     const long long ge = blockIdx.x * (long long)epb + le;
@@ -63,6 +71,7 @@ __global__ void __launch_bounds__(vol_threads<N>()) k_volume(const __grid_consta
         if (itp->clk && itp->clk->done) valid = false;
     }
     R *S = sbuf + (size_t)le * PER * n3;
+    R *F6 = sface + (size_t)le * FACEVALS;
     const int ijk[3] = {p % n, (p / n) % n, p / n2};
 
     double u[5];
@@ -72,13 +81,25 @@ __global__ void __launch_bounds__(vol_threads<N>()) k_volume(const __grid_consta
     Prim<R> q;
     if (valid) {
         const Item &it = *itp;
+        // the six face-flux blocks of this element: slot 2d+1 the +d face (own
+        // index), slot 2d the -d face (owned by the -d neighbour)
+        {
+            const R *FS = (const R *)it.fstar;
+            const int E = it.E;
+            for (int t = p; t < FACEVALS; t += n3) {
+                const int slot = t / (5 * n2), off = t - slot * 5 * n2;
+                const int d = slot >> 1;
+                const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
+                F6[t] = FS[((size_t)d * E + owner) * 5 * n2 + off];
+            }
+        }
         const double *U = it.u + (size_t)e * 5 * n3 + p;
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
         q = prim_from_u<R>(u, it.gamma - 1.0);
-        const double *JA = it.Ja + (size_t)e * 9 * n3 + p;
+        const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) ja[k] = (R)JA[k * n3];
+        for (int k = 0; k < 9; ++k) ja[k] = JA[k * n3];
         const R E = (R)u[4];
         R fv[3][5];
         if (NS) {
@@ -121,146 +142,177 @@ __global__ void __launch_bounds__(vol_threads<N>()) k_volume(const __grid_consta
         }
     }
     __syncthreads();
-    if (!valid) return;
-    const Item &it = *itp;
 
-    R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
-    if (FORM == HS3D_VOL_STANDARD) {
+    double lc = 0.0, lv = 0.0;
+    bool lam_active = false;
+    if (valid) {
+        const Item &it = *itp;
+        R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+        if (FORM == HS3D_VOL_STANDARD) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
-            const int base = p - ijk[d] * stride;
-            const R *Drow = sD + ijk[d] * n;
+            for (int d = 0; d < 3; ++d) {
+                const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+                const int base = p - ijk[d] * stride;
+                const R *Drow = sD + ijk[d] * n;
 #pragma unroll
-            for (int m = 0; m < n; ++m) {
-                const R Dm = Drow[m];
+                for (int m = 0; m < n; ++m) {
+                    const R Dm = Drow[m];
 #pragma unroll
-                for (int v = 0; v < 5; ++v) V[v] += Dm * S[(d * 5 + v) * n3 + base + m * stride];
-            }
-        }
-    } else {
-        const R gm1 = (R)(it.gamma - 1.0);
-        const ECNode<R> zi = {S[0 * n3 + p], S[1 * n3 + p], S[2 * n3 + p], S[3 * n3 + p],
-                              S[4 * n3 + p], S[5 * n3 + p], S[6 * n3 + p]};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
-            const int base = p - ijk[d] * stride;
-            const R *Drow = sD + ijk[d] * n;
-#pragma unroll
-            for (int m = 0; m < n; ++m) {
-                const R Dm = Drow[m];
-                const int pm = base + m * stride;
-                if (m == ijk[d]) {
-                    // F#(u_i, u_i).(2 Ja^d_i) = 2 Ja^d_i . F_e(u_i)
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) V[v] += (R)2 * Dm * Fe[d][v];
-                } else {
-                    const ECNode<R> zm = {S[0 * n3 + pm], S[1 * n3 + pm], S[2 * n3 + pm], S[3 * n3 + pm],
-                                          S[4 * n3 + pm], S[5 * n3 + pm], S[6 * n3 + pm]};
-                    const R a1 = ja[d * 3 + 0] + S[(7 + d * 3 + 0) * n3 + pm];
-                    const R a2 = ja[d * 3 + 1] + S[(7 + d * 3 + 1) * n3 + pm];
-                    const R a3 = ja[d * 3 + 2] + S[(7 + d * 3 + 2) * n3 + pm];
-                    R fs[5];
-                    flux_ec(zi, zm, gm1, a1, a2, a3, fs);
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) V[v] += Dm * fs[v];
-                }
-                if (NS) {
-#pragma unroll
-                    for (int v = 1; v < 5; ++v) V[v] -= Dm * S[(16 + d * 5 + v) * n3 + pm];
+                    for (int v = 0; v < 5; ++v) V[v] += Dm * S[(d * 5 + v) * n3 + base + m * stride];
                 }
             }
-        }
-    }
-
-    // surface lifting
-    const R iw = (R)(1.0 / ops->w[0]);
-    const R *FS = (const R *)it.fstar;
-    const int E = it.E;
+        } else {
+            const R hg = (R)(0.5 / (it.gamma - 1.0));
+            const ECNode<R> zi = {S[0 * n3 + p], S[1 * n3 + p], S[2 * n3 + p], S[3 * n3 + p],
+                                  S[4 * n3 + p], S[5 * n3 + p], S[6 * n3 + p]};
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (ijk[d] == N || ijk[d] == 0) {
-            int ta, tb;
-            tangential<n>(d, ijk, ta, tb);
+            for (int d = 0; d < 3; ++d) {
+                const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+                const int base = p - ijk[d] * stride;
+                const R *Drow = sD + ijk[d] * n;
+#pragma unroll
+                for (int m = 0; m < n; ++m) {
+                    const R Dm = Drow[m];
+                    const int pm = base + m * stride;
+                    if (m == ijk[d]) {
+                        // F#(u_i, u_i).(2 Ja^d_i) = 2 Ja^d_i . F_e(u_i)
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) V[v] += (R)2 * Dm * Fe[d][v];
+                    } else {
+                        const ECNode<R> zm = {S[0 * n3 + pm], S[1 * n3 + pm], S[2 * n3 + pm], S[3 * n3 + pm],
+                                              S[4 * n3 + pm], S[5 * n3 + pm], S[6 * n3 + pm]};
+                        const R a1 = ja[d * 3 + 0] + S[(7 + d * 3 + 0) * n3 + pm];
+                        const R a2 = ja[d * 3 + 1] + S[(7 + d * 3 + 1) * n3 + pm];
+                        const R a3 = ja[d * 3 + 2] + S[(7 + d * 3 + 2) * n3 + pm];
+                        R fs[5];
+                        flux_ec(zi, zm, hg, a1, a2, a3, fs);
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) V[v] += Dm * fs[v];
+                    }
+                    if (NS) {
+#pragma unroll
+                        for (int v = 1; v < 5; ++v) V[v] -= Dm * S[(16 + d * 5 + v) * n3 + pm];
+                    }
+                }
+            }
+        }
+
+        // surface lifting from the staged face fluxes
+        const R iw = (R)(1.0 / ops->w[0]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int ta = (d == 0) ? ijk[1] : ijk[0];
+            const int tb = (d == 2) ? ijk[1] : ijk[2];
             const int ab = ta + n * tb;
             if (ijk[d] == N) {
-                const R *F = FS + ((size_t)d * E + e) * 5 * n2 + ab;
+                const R *F = F6 + (2 * d + 1) * 5 * n2 + ab;
 #pragma unroll
                 for (int v = 0; v < 5; ++v) V[v] += iw * (F[v * n2] - Fown[d][v]);
             }
             if (ijk[d] == 0) {
-                const int em = nbr_minus(e, d, it.ex, it.ey, it.ez);
-                const R *F = FS + ((size_t)d * E + em) * 5 * n2 + ab;
+                const R *F = F6 + (2 * d) * 5 * n2 + ab;
 #pragma unroll
                 for (int v = 0; v < 5; ++v) V[v] += iw * (Fown[d][v] - F[v * n2]);
             }
         }
-    }
 
-    const double ij = it.invJ[(size_t)e * n3 + p];
-    if (stage < 0) {
-        double *O = it.out + (size_t)e * 5 * n3 + p;
+        const double ij = it.invJ[(size_t)e * n3 + p];
+        if (stage < 0) {
+            double *O = it.out + (size_t)e * 5 * n3 + p;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
-    } else {
-        const double dt = it.clk->dt;
-        const double A = c_rkA[stage], B = c_rkB[stage];
-        double *Gp = it.g + (size_t)e * 5 * n3 + p;
-        double *Up = it.u + (size_t)e * 5 * n3 + p;
+            for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
+        } else {
+            const double dt = it.clk->dt;
+            const double A = c_rkA[stage], B = c_rkB[stage];
+            double *Gp = it.g + (size_t)e * 5 * n3 + p;
+            double *Up = it.u + (size_t)e * 5 * n3 + p;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            const double r = -(double)V[v] * ij;
-            const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
-            Gp[v * n3] = gv;
-            Up[v * n3] = u[v] + B * gv;
+            for (int v = 0; v < 5; ++v) {
+                const double r = -(double)V[v] * ij;
+                const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
+                Gp[v * n3] = gv;
+                u[v] = u[v] + B * gv;
+                Up[v * n3] = u[v];
+            }
+            if (lam_slot >= 0) {
+                // dt maxima of the updated state (same rule as k_lambda, in R)
+                const Prim<R> qn = prim_from_u<R>(u, it.gamma - 1.0);
+                if (!(qn.rho > (R)0) || !(qn.p > (R)0)) {
+                    it.clk->bad = 1;
+                } else {
+                    const R c = sqrt((R)it.gamma * qn.p / qn.rho);
+                    const R iJ = (R)ij;
+                    R sc = (R)0, sv = (R)0;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const R a1 = ja[d * 3], a2 = ja[d * 3 + 1], a3 = ja[d * 3 + 2];
+                        const R an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
+                        sc += (fabs(a1 * qn.v1 + a2 * qn.v2 + a3 * qn.v3) + c * an) * iJ;
+                        sv += (an * iJ) * (an * iJ);
+                    }
+                    lc = (double)sc;
+                    lv = NS ? (double)((R)it.mu * sv / qn.rho) : 0.0;
+                    lam_active = true;
+                }
+            }
         }
+    }
+    if (lam_slot >= 0 && stage == 2) {
+        unsigned long long *dc = nullptr, *dv = nullptr;
+        if (lam_active) {
+            dc = &itp->clk->lam[lam_slot][0];
+            dv = NS ? &itp->clk->lam[lam_slot][1] : nullptr;
+        }
+        warp_max_to_clock(dc, dv, lc, lv, lam_active);
     }
 }
 
 // ------------------------------------------------------------------ launch
 
-static int g_epb[kMaxn + 1][2] = {};
+static int g_epb[kMaxn + 1][2][2] = {};
 
-int elems_per_block(int N, int which)
+int tuned_elems_per_block(int N, int prec, int which) { return g_epb[N][prec ? 1 : 0][which]; }
+
+int elems_per_block_p(int N, int prec, int which)
 {
-    int v = g_epb[N][which];
+    int v = g_epb[N][prec ? 1 : 0][which];
     if (v > 0) return v;
     int n3 = (N + 1) * (N + 1) * (N + 1);
     int e = 256 / n3;
     return e < 1 ? 1 : e;
 }
 
-void set_elems_per_block(int N, int which, int epb) { g_epb[N][which] = epb; }
+void set_elems_per_block_p(int N, int prec, int which, int epb) { g_epb[N][prec ? 1 : 0][which] = epb; }
 
 template <int N, typename R, bool NS, int FORM>
-static cudaError_t vol_launch2(const Batch &b, int stage, cudaStream_t s)
+static cudaError_t vol_launch2(const Batch &b, int stage, int lam_slot, cudaStream_t s)
 {
-    constexpr int n = N + 1, n3 = n * n * n;
-    int epb = elems_per_block(N, 1);
+    constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;
+    int epb = elems_per_block_p(N, sizeof(R) == 4 ? HS3D_MIXED32 : HS3D_FP64, 1);
     int threads = epb * n3;
     if (threads > vol_threads<N>()) {
         epb = vol_threads<N>() / n3;
         threads = epb * n3;
     }
-    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3);
+    size_t smem =
+        sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 + (size_t)epb * 30 * n2);
     unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    k_volume<N, R, NS, FORM><<<blocks, threads, smem, s>>>(b, ops, stage);
+    k_volume<N, R, NS, FORM><<<blocks, threads, smem, s>>>(b, ops, stage, stage == 2 ? lam_slot : -1);
     return cudaGetLastError();
 }
 
 template <int N, typename R>
-static cudaError_t vol_launch(int physics, int form, const Batch &b, int stage, cudaStream_t s)
+static cudaError_t vol_launch(int physics, int form, const Batch &b, int stage, int lam_slot, cudaStream_t s)
 {
     if (b.total_elems == 0) return cudaSuccess;
     if (physics == HS3D_NS) {
-        if (form == HS3D_VOL_EC) return vol_launch2<N, R, true, HS3D_VOL_EC>(b, stage, s);
-        return vol_launch2<N, R, true, HS3D_VOL_STANDARD>(b, stage, s);
+        if (form == HS3D_VOL_EC) return vol_launch2<N, R, true, HS3D_VOL_EC>(b, stage, lam_slot, s);
+        return vol_launch2<N, R, true, HS3D_VOL_STANDARD>(b, stage, lam_slot, s);
     }
-    if (form == HS3D_VOL_EC) return vol_launch2<N, R, false, HS3D_VOL_EC>(b, stage, s);
-    return vol_launch2<N, R, false, HS3D_VOL_STANDARD>(b, stage, s);
+    if (form == HS3D_VOL_EC) return vol_launch2<N, R, false, HS3D_VOL_EC>(b, stage, lam_slot, s);
+    return vol_launch2<N, R, false, HS3D_VOL_STANDARD>(b, stage, lam_slot, s);
 }
 
 template <int N>
@@ -297,29 +349,17 @@ cudaError_t prepare_volume(int N)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_volume(int N, int prec, int physics, int form, const Batch &b, int stage, cudaStream_t s)
+cudaError_t launch_volume(int N, int prec, int physics, int form, const Batch &b, int stage, int lam_slot,
+                          cudaStream_t s)
 {
-    if (prec == HS3D_FP64) {
-        switch (N) {
-            case 1: return vol_launch<1, double>(physics, form, b, stage, s);
-            case 2: return vol_launch<2, double>(physics, form, b, stage, s);
-            case 3: return vol_launch<3, double>(physics, form, b, stage, s);
-            case 4: return vol_launch<4, double>(physics, form, b, stage, s);
-            case 5: return vol_launch<5, double>(physics, form, b, stage, s);
-            case 6: return vol_launch<6, double>(physics, form, b, stage, s);
-            case 7: return vol_launch<7, double>(physics, form, b, stage, s);
-        }
-    } else {
-        switch (N) {
-            case 1: return vol_launch<1, float>(physics, form, b, stage, s);
-            case 2: return vol_launch<2, float>(physics, form, b, stage, s);
-            case 3: return vol_launch<3, float>(physics, form, b, stage, s);
-            case 4: return vol_launch<4, float>(physics, form, b, stage, s);
-            case 5: return vol_launch<5, float>(physics, form, b, stage, s);
-            case 6: return vol_launch<6, float>(physics, form, b, stage, s);
-            case 7: return vol_launch<7, float>(physics, form, b, stage, s);
-        }
+#define HS3D_VOLN(K)                                                                           \
+    case K:                                                                                    \
+        return prec == HS3D_FP64 ? vol_launch<K, double>(physics, form, b, stage, lam_slot, s) \
+                                 : vol_launch<K, float>(physics, form, b, stage, lam_slot, s);
+    switch (N) {
+        HS3D_VOLN(1) HS3D_VOLN(2) HS3D_VOLN(3) HS3D_VOLN(4) HS3D_VOLN(5) HS3D_VOLN(6) HS3D_VOLN(7)
     }
+#undef HS3D_VOLN
     return cudaErrorInvalidValue;
 }
 

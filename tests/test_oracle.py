@@ -604,13 +604,48 @@ def test_dt_rule_closed_form_on_straight_box():
     u = np.zeros(m.shape)
     u[:] = st[None, :, None, None, None]
     c = np.sqrt(G * p / st[0])
-    dtc = 0.5 * h / (n * (np.abs(v).sum() + 3 * c))
+    dtc = 0.5 * 4 * h / (n * n * (np.abs(v).sum() + 3 * c))
     assert abs(m.dt(O.Cfg("euler", cfl=0.5), u) - dtc) < 1e-12 * dtc
     Re = 0.05    # strong viscosity so that the viscous limit binds
     nu = (1 / Re) / st[0]
     dtv = h * h / (nu * n ** 4)
     got = m.dt(O.Cfg("ns", cfl=0.5, Re=Re), u)
     assert abs(got - min(dtc, dtv)) < 1e-12 * got and dtv < dtc
+
+
+def _dgsem_advection_1d(N, K=6, h=1.0):
+    """1-D strong-form DGSEM operator of u_t + u_x = 0 (upwind flux) on K
+    periodic elements, assembled from the oracle's D and w."""
+    _, w = O.lgl(N)
+    D = O.dmatrix(N)
+    n = N + 1
+    L = np.zeros((K * n, K * n))
+    for k in range(K):
+        s = slice(k * n, (k + 1) * n)
+        L[s, s] -= (2 / h) * D
+        L[k * n, k * n] -= (2 / h) / w[0]
+        L[k * n, ((k - 1) % K) * n + N] += (2 / h) / w[0]
+    return L
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_dt_rule_is_inside_rk3_stability_region(N):
+    """The convective rule cfl*8/(n^2 lambda) at cfl = 0.5, applied to the
+    1-D operator (lambda = 2a/h), keeps every dt*mu inside the Williamson RK3
+    stability region |1 + z + z^2/2 + z^3/6| <= 1 with a factor-of-two
+    margin for every N (a rule scaling like 1/n instead reaches the limit at
+    N = 7)."""
+    mu = np.linalg.eigvals(_dgsem_advection_1d(N))
+    n = N + 1
+    dt = 0.5 * 8 / (n * n * 2.0)          # h = a = 1
+
+    def amp(z):
+        return abs(1 + z + z * z / 2 + z ** 3 / 6)
+
+    assert max(amp(2 * dt * m) for m in mu) <= 1 + 1e-9
+    # and the 1/n scaling at the same CFL leaves almost no margin at N = 7
+    if N == 7:
+        assert max(amp(1.2 * (0.5 * 2 / (n * 2.0)) * m) for m in mu) > 1
 
 
 def test_integrals_volume_and_mass():
