@@ -36,7 +36,7 @@ EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh
            "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
            "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
            "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
-           "hs3d_diagnostics_noalloc", "hs3d_autotune"]
+           "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding"]
 
 
 class HS3DError(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
                 "hs3d_alu_peaks": [C.POINTER(d), vp],
                 "hs3d_diagnostics_noalloc": [i, C.c_int64, d, vp, vp, vp, vp, vp],
                 "hs3d_autotune": [vp, C.POINTER(SolverCfg), C.POINTER(i), vp],
+                "hs3d_check_rounding": [vp, C.c_int64, vp, vp],
                 "hs3d_last_error": [],
                 "hs3d_version": [],
             }
@@ -315,6 +316,16 @@ def diagnostics_noalloc(N, E, gamma, J, u, out, dudt=None, stream=None):
     check(lib().hs3d_diagnostics_noalloc(int(N), int(E), float(gamma), _ptr(J, "J"), _ptr(u, "u"),
                                          _ptr(dudt, "dudt"), _ptr(out, "out"), _stream(stream)))
     return out
+
+
+def check_rounding(x, stream=None):
+    """Counts from hs3d_check_rounding for a float64 CUDA tensor x:
+    (d2f mismatches, widening mismatches, inputs below the FP32 normal range)."""
+    import torch
+    counts = torch.zeros(3, dtype=torch.int64, device=x.device)
+    check(lib().hs3d_check_rounding(_ptr(x, "x"), x.numel(), C.c_void_p(counts.data_ptr()), _stream(stream)))
+    torch.cuda.synchronize()
+    return tuple(int(v) for v in counts.cpu())
 
 
 def ic_desc(kind="vortex", gamma=1.4, Ma=0.5, beta=5.0, xc=5.0, yc=5.0, t=0.0) -> IC:

@@ -74,8 +74,8 @@ hs3d_status validate_desc(const hs3d_mesh_desc *d)
 size_t mesh_bytes(int N, long long E)
 {
     long long n = N + 1, n2 = n * n, n3 = n2 * n;
-    size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) + sizeof(float) * (size_t)E * n3 * 9 +
-                 sizeof(double) * 3 * (size_t)E * 3 * n2;
+    size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) + sizeof(float) * (size_t)E * n3 * 15 +
+                 (sizeof(double) + sizeof(float)) * 3 * (size_t)E * 3 * n2;
     size_t scratch = sizeof(double) * (3 * (size_t)E * 5 * n2 + (size_t)E * 12 * n3);
     return geo + scratch + sizeof(Clock) + 4096 * 7 * sizeof(double);
 }
@@ -92,7 +92,10 @@ static hs3d_status mesh_alloc(hs3d_mesh *m)
         {(void **)&m->Jaf, sizeof(float) * E * 9 * n3},
         {(void **)&m->J, sizeof(double) * E * n3},
         {(void **)&m->invJ, sizeof(double) * E * n3},
+        {(void **)&m->invJf, sizeof(float) * E * n3},
+        {(void **)&m->uf, sizeof(float) * E * 5 * n3},
         {(void **)&m->fn, sizeof(double) * 3 * E * 3 * n2},
+        {(void **)&m->fnf, sizeof(float) * 3 * E * 3 * n2},
         {(void **)&m->fstar, sizeof(double) * 3 * E * 5 * n2},
         {(void **)&m->grad, sizeof(double) * E * 12 * n3},
         {(void **)&m->clk, sizeof(Clock)},
@@ -113,7 +116,8 @@ void mesh_free(hs3d_mesh *m)
 {
     if (!m) return;
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    void *ptrs[] = {m->X, m->Ja, m->Jaf, m->J, m->invJ, m->fn, m->fstar, m->grad, m->clk, m->diag_partials};
+    void *ptrs[] = {m->X,    m->Ja,   m->Jaf, m->J,   m->invJ,          m->invJf,
+                    m->uf,   m->fn,   m->fnf, m->fstar, m->grad, m->clk, m->diag_partials};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->stream) cudaStreamDestroy(m->stream);
@@ -171,7 +175,7 @@ hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out)
         }
     }
     e = launch_geometry(m->N, xyz_dev, m->ex, m->ey, m->ez, m->lo, m->hi, m->amp, m->X, m->Ja, m->Jaf, m->J, m->invJ,
-                        m->fn, m->stream);
+                        m->invJf, m->fn, m->fnf, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->clk, 0, sizeof(Clock), m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (xyz_dev) cudaFree(xyz_dev);
@@ -189,9 +193,12 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
     it.Ja = m->Ja;
     it.Jaf = m->Jaf;
     it.invJ = m->invJ;
+    it.invJf = m->invJf;
     it.fn = m->fn;
+    it.fnf = m->fnf;
     it.J = m->J;
     it.u = const_cast<double *>(u);
+    it.uf = m->uf;
     it.g = g;
     it.out = out;
     it.fstar = m->fstar;
@@ -207,6 +214,13 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
     it.mu = (c && c->physics == HS3D_NS) ? 1.0 / c->Re : 0.0;
     it.kappa = (c && c->physics == HS3D_NS) ? it.mu * c->gamma / ((c->gamma - 1.0) * c->Pr) : 0.0;
     it.cfl = c ? c->cfl : 0.5;
+    it.gm1 = it.gamma - 1.0;
+    it.hg = 0.5 / it.gm1;
+    it.gammaf = (float)it.gamma;
+    it.gm1f = (float)it.gm1;
+    it.hgf = (float)it.hg;
+    it.muf = (float)it.mu;
+    it.kappaf = (float)it.kappa;
     return it;
 }
 
@@ -243,6 +257,7 @@ cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt
     b.dt_fixed = dt > 0.0 ? dt : 0.0;
     int slot = fresh_lambda ? 0 : 1;
     if (fresh_lambda && !(dt > 0.0)) e = launch_lambda(N, c->precision, c->physics, b, 0, s);
+    else if (fresh_lambda && c->precision == HS3D_MIXED32) e = launch_shadow(N, b, s);
     if (e == cudaSuccess) e = launch_dt_finalize(N, b, 0, slot, s);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = enqueue_stage(N, c, b, k, k == 2 ? 1 : -1, s);
     return e;
@@ -326,7 +341,9 @@ hs3d_status hs3d_residual(const hs3d_mesh *m, const hs3d_solver_cfg *c, const do
     if ((const void *)u == (const void *)dudt) return fail(HS3D_ERR_INVALID, "u and dudt must differ");
     Item it = make_item(m, c, u, nullptr, dudt);
     it.clk = nullptr;
-    cudaError_t e = enqueue_stage(m->N, c, single_batch(it), -1, -1, (cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    if (c->precision == HS3D_MIXED32) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = enqueue_stage(m->N, c, single_batch(it), -1, -1, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
 }
 
@@ -383,9 +400,10 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
         m->g_dt = dt;
         m->g_cfg = *c;
     }
-    if (!(dt > 0.0)) {
+    {
         Item it = make_item(m, c, u, g, nullptr);
-        e = prime_lambda(m->N, c, single_batch(it), m->clk, (cudaStream_t)stream);
+        if (!(dt > 0.0)) e = prime_lambda(m->N, c, single_batch(it), m->clk, (cudaStream_t)stream);
+        else if (c->precision == HS3D_MIXED32) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
     }
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(m->gexec, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");

@@ -13,7 +13,9 @@ struct hs3d_mesh {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, amp = 0.0;
     int device = 0;
     double *X = nullptr, *Ja = nullptr, *J = nullptr, *invJ = nullptr, *fn = nullptr;
-    float *Jaf = nullptr;
+    float *Jaf = nullptr, *invJf = nullptr;
+    float *uf = nullptr;            // FP32 shadow of the state being stepped (mixed path)
+    float *fnf = nullptr;
     void *fstar = nullptr;          // scratch, sized for FP64
     void *grad = nullptr;           // scratch, sized for FP64
     hs3d::Clock *clk = nullptr;

@@ -24,6 +24,27 @@ __device__ __forceinline__ int face_node(int d, int end, int ta, int tb)
     return ta + n * (tb + n * end);
 }
 
+// Primitive variables of node `idx` (element base + node) of an item: FP64
+// path from u, mixed path from the FP32 shadow uf.
+template <typename R>
+__device__ __forceinline__ Prim<R> load_prim(const Item &it, size_t idx, int n3, R gm1);
+template <>
+__device__ __forceinline__ Prim<double> load_prim<double>(const Item &it, size_t idx, int n3, double gm1)
+{
+    double u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = it.u[idx + (size_t)v * n3];
+    return prim_from_u<double>(u, gm1);
+}
+template <>
+__device__ __forceinline__ Prim<float> load_prim<float>(const Item &it, size_t idx, int n3, float gm1)
+{
+    float u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = it.uf[idx + (size_t)v * n3];
+    return prim_from_f(u, gm1);
+}
+
 template <int N, typename R, bool NS>
 __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, int flux)
 {
@@ -41,35 +62,42 @@ __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, i
     const int eR = nbr_plus(eL, d, it.ex, it.ey, it.ez);
     const int ta = ab % n, tb = ab / n;
     const int pL = face_node<n>(d, N, ta, tb), pR = face_node<n>(d, 0, ta, tb);
-    const double gm1d = it.gamma - 1.0;
-
-    double uL[5], uR[5];
-    const double *UL = it.u + (size_t)eL * 5 * n3 + pL;
-    const double *UR = it.u + (size_t)eR * 5 * n3 + pR;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        uL[v] = UL[v * n3];
-        uR[v] = UR[v * n3];
+    
+    const Phys<R> P = phys_of<R>(it);
+    const size_t iL = (size_t)eL * 5 * n3 + pL, iR = (size_t)eR * 5 * n3 + pR;
+    const Prim<R> qL = load_prim<R>(it, iL, n3, P.gm1), qR = load_prim<R>(it, iR, n3, P.gm1);
+    R s1, s2, s3;
+    if constexpr (sizeof(R) == 8) {
+        const double *Fn = it.fn + (size_t)f * 3 * n2 + ab;
+        s1 = Fn[0];
+        s2 = Fn[n2];
+        s3 = Fn[2 * n2];
+    } else {
+        const float *Fn = it.fnf + (size_t)f * 3 * n2 + ab;
+        s1 = Fn[0];
+        s2 = Fn[n2];
+        s3 = Fn[2 * n2];
     }
-    const Prim<R> qL = prim_from_u<R>(uL, gm1d), qR = prim_from_u<R>(uR, gm1d);
-    const double *Fn = it.fn + (size_t)f * 3 * n2 + ab;
-    const R s1 = (R)Fn[0], s2 = (R)Fn[n2], s3 = (R)Fn[2 * n2];
-    const R gam = (R)it.gamma, gm1 = (R)gm1d;
     R fs[5];
     if (flux == HS3D_FLUX_EC) {
-        flux_ec(ec_node(qL), ec_node(qR), (R)(0.5 / gm1d), s1, s2, s3, fs);
-    } else {
-        R ul[5], du[5];
+        flux_ec(ec_node(qL), ec_node(qR), P.hg, s1, s2, s3, fs);
+    } else if (flux == HS3D_FLUX_LF) {
+        // the LF dissipation uses the conserved jump, formed in FP64 before rounding
+        double uL[5], uR[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-            ul[v] = (R)uL[v];
-            du[v] = (R)(uR[v] - uL[v]);    // jump formed in FP64
+            uL[v] = it.u[iL + (size_t)v * n3];
+            uR[v] = it.u[iR + (size_t)v * n3];
         }
+        R ul[5] = {qL.rho, narrow<R>(uL[1]), narrow<R>(uL[2]), narrow<R>(uL[3]), qL.E};
         R ur[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) ur[v] = ul[v] + du[v];
-        if (flux == HS3D_FLUX_LF) flux_lf(qL, ul, qR, ur, gam, s1, s2, s3, fs);
-        else flux_roe(qL, ul, qR, ur, gam, s1, s2, s3, fs);
+        for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
+        flux_lf(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+    } else {
+        const R ul[5] = {qL.rho, (R)0, (R)0, (R)0, qL.E};
+        const R ur[5] = {qR.rho, (R)0, (R)0, (R)0, qR.E};
+        flux_roe(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
     }
     if (NS) {
         const R *GL = (const R *)it.grad + (size_t)eL * 12 * n3 + pL;
@@ -81,8 +109,8 @@ __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, i
             gr[k] = GR[k * n3];
         }
         R fl[5], fr[5];
-        visc_flux(qL, gl, (R)it.mu, (R)it.kappa, s1, s2, s3, fl);
-        visc_flux(qR, gr, (R)it.mu, (R)it.kappa, s1, s2, s3, fr);
+        visc_flux(qL, gl, P.mu, P.kappa, s1, s2, s3, fl);
+        visc_flux(qR, gr, P.mu, P.kappa, s1, s2, s3, fr);
 #pragma unroll
         for (int v = 1; v < 5; ++v) fs[v] -= (R)0.5 * (fl[v] + fr[v]);
     }
@@ -128,8 +156,7 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
     R *sD = (R *)smem_raw;                      // n*n
     R *sE = sD + ((n * n + 1) & ~1);            // [epb][PER_ELEM]
     const int epb = blockDim.x / n3;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = (R)ops->D[t];
-    const double w0 = ops->w[0];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
     const long long ge = blockIdx.x * (long long)epb + le;
     bool valid = ge < b.total_elems;
@@ -146,26 +173,18 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
     R qin[4];
     if (valid) {
         const Item &it = *itp;
-        const double gm1 = it.gamma - 1.0;
+        const R gm1 = phys_of<R>(it).gm1;
         for (int t = p; t < 6 * n2; t += n3) {
             const int slot = t / n2, ab = t - slot * n2;
             const int d = slot >> 1, plus = slot & 1;
             const int nb = plus ? nbr_plus(e, d, it.ex, it.ey, it.ez) : nbr_minus(e, d, it.ex, it.ey, it.ez);
             const int pn = face_node<n>(d, plus ? 0 : N, ab % n, ab / n);
-            const double *U = it.u + (size_t)nb * 5 * n3 + pn;
-            double u[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
             R g4[4];
-            grad_vars(prim_from_u<R>(u, gm1), g4);
+            grad_vars(load_prim<R>(it, (size_t)nb * 5 * n3 + pn, n3, gm1), g4);
 #pragma unroll
             for (int v = 0; v < 4; ++v) qn[(slot * 4 + v) * n2 + ab] = g4[v];
         }
-        const double *U = it.u + (size_t)e * 5 * n3 + p;
-        double u[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
-        grad_vars(prim_from_u<R>(u, gm1), qin);
+        grad_vars(load_prim<R>(it, (size_t)e * 5 * n3 + p, n3, gm1), qin);
 #pragma unroll
         for (int v = 0; v < 4; ++v) q[v * n3 + p] = qin[v];
         const R *JA = grad_metric<R>(it) + (size_t)e * 9 * n3 + p;
@@ -200,7 +219,7 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
     }
     // surface lifting of the BR1 jumps (q* - q_in) = (q_out - q_in)/2
     const Item &it = *itp;
-    const R iw = (R)(1.0 / w0);
+    const R iw = ops_iw0<R>(ops);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const int ta = (d == 0) ? ijk[1] : ijk[0];
@@ -222,7 +241,9 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
             }
         }
     }
-    const R ij = (R)it.invJ[(size_t)e * n3 + p];
+    R ij;
+    if constexpr (sizeof(R) == 8) ij = it.invJ[(size_t)e * n3 + p];
+    else ij = it.invJf[(size_t)e * n3 + p];
     R *G = (R *)it.grad + (size_t)e * 12 * n3 + p;
 #pragma unroll
     for (int k = 0; k < 12; ++k) G[k * n3] = acc[k] * ij;

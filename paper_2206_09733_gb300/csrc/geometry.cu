@@ -81,6 +81,8 @@ static Ops make_ops(int N)
             o.D[i * n + j] = v;
             o.Df[i * n + j] = (float)v;
         }
+    o.iw0 = 1.0 / o.w[0];
+    o.iw0f = (float)o.iw0;
     return o;
 }
 
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
 k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, double lo1, double lo2, double hi0,
            double hi1, double hi2, double amp, const Ops *__restrict__ ops, double *__restrict__ X,
            double *__restrict__ Ja, float *__restrict__ Jaf, double *__restrict__ J, double *__restrict__ invJ,
-           double *__restrict__ fn)
+           float *__restrict__ invJf, double *__restrict__ fn, float *__restrict__ fnf)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     __shared__ double sD[n * n];
@@ -170,6 +172,7 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
                 a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
     J[(size_t)e * n3 + p] = Jp;
     invJ[(size_t)e * n3 + p] = 1.0 / Jp;
+    invJf[(size_t)e * n3 + p] = (float)(1.0 / Jp);
     for (int c = 0; c < 3; ++c) X[((size_t)e * 3 + c) * n3 + p] = x[c];
 
     for (int i = 0; i < 3; ++i) {
@@ -188,6 +191,7 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
                 int ta = (i == 0) ? ijk[1] : ijk[0];
                 int tb = (i == 2) ? ijk[1] : ijk[2];
                 fn[(((size_t)i * E + e) * 3 + c) * n2 + ta + n * tb] = v;
+                fnf[(((size_t)i * E + e) * 3 + c) * n2 + ta + n * tb] = (float)v;
             }
         }
     }
@@ -195,7 +199,7 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
 
 cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
                             const double *hi, double amp, double *X, double *Ja, float *Jaf, double *J, double *invJ,
-                            double *fn, cudaStream_t s)
+                            float *invJf, double *fn, float *fnf, cudaStream_t s)
 {
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
@@ -204,7 +208,7 @@ cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, i
 #define HS3D_GEO(NN)                                                                                            \
     case NN:                                                                                                    \
         k_geometry<NN><<<E, n3, 0, s>>>(node_xyz_dev, ex, ey, ez, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], amp, \
-                                        ops, X, Ja, Jaf, J, invJ, fn);                                          \
+                                        ops, X, Ja, Jaf, J, invJ, invJf, fn, fnf);                              \
         break;
     switch (N) {
         HS3D_GEO(1) HS3D_GEO(2) HS3D_GEO(3) HS3D_GEO(4) HS3D_GEO(5) HS3D_GEO(6) HS3D_GEO(7)

@@ -3,9 +3,10 @@
 // Data layout in HBM (all element-major so that one element is one contiguous
 // block and every warp load of a node-indexed field is coalesced):
 //   u, g, dudt  double [E][5][n3]             conserved variables
+//   uf          float  [E][5][n3]              FP32 shadow of u (mixed path): d2f_rn of u
 //   Ja          double [E][3(d)][3(c)][n3]     Ja^d_c = J dxi_d/dx_c (curl form)
 //   Jaf         float  [E][3(d)][3(c)][n3]     the same, rounded once for the FP32 flux arithmetic
-//   invJ        double [E][n3]                 1/J
+//   invJ        double [E][n3]                 1/J (and an FP32 copy invJf)
 //   fn          double [3(d)][E][3(c)][n2]     scaled normal Ja^d of face (d, e) taken
 //                                              from element e on its +d face
 //   fstar       R      [3(d)][E][5][n2]        numerical flux minus viscous flux, times
@@ -45,9 +46,13 @@ struct Item {
     const double *Ja;
     const float *Jaf;       // FP32 copy of Ja (the mixed path rounds Ja to FP32 anyway)
     const double *invJ;
+    const float *invJf;     // FP32 copy of 1/J
     const double *fn;
+    const float *fnf;       // FP32 copy of fn
     const double *J;       // for diagnostics
     double *u;
+    float *uf;              // FP32 shadow of u (the mixed path's kernels read it; written by the
+                            // kernel that writes u, or by a shadow/priming pass)
     double *g;
     double *out;            // residual output (residual mode)
     void *fstar;            // R [3][E][5][n2]
@@ -58,7 +63,28 @@ struct Item {
     long long elem_begin;   // first element of this item in the launch
     long long face_begin;   // first face of this item in the launch (3E faces per item)
     double gamma, mu, kappa, cfl;
+    double gm1, hg;                          // gamma - 1, 1/(2(gamma - 1))
+    float gammaf, gm1f, hgf, muf, kappaf;    // the same constants rounded once for the FP32 path
 };
+
+// Physical constants of an item in the arithmetic type R (no per-thread
+// FP64 arithmetic or conversion in the FP32 path).
+template <typename R>
+struct Phys {
+    R gamma, gm1, hg, mu, kappa;
+};
+template <typename R>
+__device__ __forceinline__ Phys<R> phys_of(const Item &it);
+template <>
+__device__ __forceinline__ Phys<double> phys_of<double>(const Item &it)
+{
+    return Phys<double>{it.gamma, it.gm1, it.hg, it.mu, it.kappa};
+}
+template <>
+__device__ __forceinline__ Phys<float> phys_of<float>(const Item &it)
+{
+    return Phys<float>{it.gammaf, it.gm1f, it.hgf, it.muf, it.kappaf};
+}
 
 struct Batch {
     Item single;            // used when nitems == 1
@@ -75,7 +101,22 @@ struct Ops {
     double w[kMaxn];
     double xi[kMaxn];
     float Df[kMaxn * kMaxn];
+    double iw0;                // 1/w_0 = 1/w_N (surface lifting factor)
+    float iw0f;
 };
+
+template <typename R>
+__device__ __forceinline__ R ops_D(const Ops *o, int k);
+template <>
+__device__ __forceinline__ double ops_D<double>(const Ops *o, int k) { return o->D[k]; }
+template <>
+__device__ __forceinline__ float ops_D<float>(const Ops *o, int k) { return o->Df[k]; }
+template <typename R>
+__device__ __forceinline__ R ops_iw0(const Ops *o);
+template <>
+__device__ __forceinline__ double ops_iw0<double>(const Ops *o) { return o->iw0; }
+template <>
+__device__ __forceinline__ float ops_iw0<float>(const Ops *o) { return o->iw0f; }
 
 // Host side.
 const Ops &host_ops(int N);        // computed once per N
@@ -154,10 +195,12 @@ __device__ __forceinline__ int nbr_minus(int e, int d, int ex, int ey, int ez)
 // Launch helpers implemented in the .cu files (return cudaError_t of the launch).
 cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
                             const double *hi, double amp, double *X, double *Ja, float *Jaf, double *J, double *invJ,
-                            double *fn, cudaStream_t s);
+                            float *invJf, double *fn, float *fnf, cudaStream_t s);
 cudaError_t launch_init_state(int N, int E, const double *X, const hs3d_ic &ic, const double *lo, const double *hi,
                               double *u, cudaStream_t s);
 cudaError_t launch_lambda(int N, int prec, int physics, const Batch &b, int slot, cudaStream_t s);
+// Write the FP32 shadow uf of every item's state (mixed path, when no dt pass does it).
+cudaError_t launch_shadow(int N, const Batch &b, cudaStream_t s);
 // mode 0: advance every item's clock using lambda slot `slot`; mode 2: dt value of b.single into b.single.out
 cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, int slot, cudaStream_t s);
 cudaError_t launch_grad(int N, int prec, const Batch &b, cudaStream_t s);

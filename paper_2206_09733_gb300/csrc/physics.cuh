@@ -15,15 +15,70 @@ namespace hs3d {
 
 template <typename R>
 struct Prim {
-    R rho, v1, v2, v3, p;
+    R rho, v1, v2, v3, p, E;   // E = rho e, the conserved total energy
 };
 
-// Primitive variables from the FP64 conserved state.  FP64 path: in FP64.
-// Mixed path: the state is rounded to FP32 once and the primitives computed
-// in FP32 (at Mach 0.1, rho e / p ~ 2.5, so the subtraction loses no more than
-// rounding p itself to FP32 would).
+// FP64 -> FP32 with round-to-nearest-even, on the integer pipe.  On this GPU
+// every FP64-pipe instruction (conversions included) costs as much issue
+// bandwidth as ~64 FP32 ones, so the mixed path rounds its FP64 inputs with
+// bit operations on the IEEE-754 encodings instead: sign kept; the 52-bit
+// significand cut to 23 bits, rounding on the 29 dropped bits (ties to even,
+// a carry may step into the exponent); exponent rebased from 1023 to 127.
+// Results below the smallest normal FP32 are flushed to signed zero (the
+// state never holds such values), above the largest become infinity, NaN
+// stays NaN.
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    const int ef = e - 1023 + 127;
+    if (e == 0x7ff) return __int_as_float((int)(sign | 0x7f800000u | ((m | rest) ? 0x400000u : 0u)));
+    if (ef <= 0) return __int_as_float((int)sign);
+    if (ef >= 255) return __int_as_float((int)(sign | 0x7f800000u));
+    unsigned r = ((unsigned)ef << 23) | m;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) r += 1u;
+    return __int_as_float((int)(sign | r));
+}
+
+// FP32 -> FP64 (exact) on the integer pipe; FP32 subnormals become zero.
+__device__ __forceinline__ double f2d_exact(float x);
 template <typename R>
-__device__ __forceinline__ Prim<R> prim_from_u(const double u[5], double gm1);
+__device__ __forceinline__ double widen(R x);
+template <>
+__device__ __forceinline__ double widen<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ double widen<float>(float x) { return f2d_exact(x); }
+template <typename R>
+__device__ __forceinline__ R narrow(double x);
+template <>
+__device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float narrow<float>(double x) { return d2f_rn(x); }
+
+__device__ __forceinline__ double f2d_exact(float x)
+{
+    const unsigned b = (unsigned)__float_as_int(x);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned m = b & 0x7fffffu;
+    unsigned hi;
+    if (e == 0) hi = sign;
+    else if (e == 0xff) hi = sign | 0x7ff00000u | (m >> 3);
+    else hi = sign | ((e - 127u + 1023u) << 20) | (m >> 3);
+    const unsigned lo = (e == 0) ? 0u : (m << 29);
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// Primitive variables from the FP64 conserved state.  FP64 path: in FP64.
+// Mixed path: the state is rounded to FP32 once (d2f_rn) and the primitives
+// computed in FP32 (at Mach 0.1, rho e / p ~ 2.5, so the subtraction loses no
+// more than rounding p itself to FP32 would).
+template <typename R>
+__device__ __forceinline__ Prim<R> prim_from_u(const double u[5], R gm1);
 
 template <>
 __device__ __forceinline__ Prim<double> prim_from_u<double>(const double u[5], double gm1)
@@ -36,21 +91,30 @@ __device__ __forceinline__ Prim<double> prim_from_u<double>(const double u[5], d
     q.v2 = v2;
     q.v3 = v3;
     q.p = gm1 * (u[4] - 0.5 * (u[1] * v1 + u[2] * v2 + u[3] * v3));
+    q.E = u[4];
     return q;
 }
 
-template <>
-__device__ __forceinline__ Prim<float> prim_from_u<float>(const double u[5], double gm1)
+// Primitive variables from a state already rounded to FP32.
+__device__ __forceinline__ Prim<float> prim_from_f(const float uf[5], float gm1)
 {
-    const float r = (float)u[0], m1 = (float)u[1], m2 = (float)u[2], m3 = (float)u[3], E = (float)u[4];
+    const float r = uf[0], m1 = uf[1], m2 = uf[2], m3 = uf[3], E = uf[4];
     const float ir = __frcp_rn(r);
     Prim<float> q;
     q.rho = r;
     q.v1 = m1 * ir;
     q.v2 = m2 * ir;
     q.v3 = m3 * ir;
-    q.p = (float)gm1 * (E - 0.5f * (m1 * q.v1 + m2 * q.v2 + m3 * q.v3));
+    q.p = gm1 * (E - 0.5f * (m1 * q.v1 + m2 * q.v2 + m3 * q.v3));
+    q.E = E;
     return q;
+}
+
+template <>
+__device__ __forceinline__ Prim<float> prim_from_u<float>(const double u[5], float gm1)
+{
+    const float uf[5] = {d2f_rn(u[0]), d2f_rn(u[1]), d2f_rn(u[2]), d2f_rn(u[3]), d2f_rn(u[4])};
+    return prim_from_f(uf, gm1);
 }
 
 template <typename R>

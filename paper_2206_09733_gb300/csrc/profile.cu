@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include "api_internal.h"
+#include "physics.cuh"
 
 namespace hs3d {
 
@@ -47,9 +48,46 @@ static double fma_tflops(int sms, int iters, cudaStream_t s, cudaError_t &err)
     return flops / (ms * 1e-3) / 1e12;
 }
 
+// Compare the integer-pipe conversions with the hardware ones on n inputs:
+// counts[0] = d2f_rn(x) differs bitwise from __double2float_rn(x) for x in
+// the normal FP32 range or NaN/infinite, counts[1] = f2d_exact(f) differs from
+// (double)f for f = __double2float_rn(x), counts[2] = inputs below the FP32
+// normal range (flushed to zero by d2f_rn by design).
+__global__ void k_check_rounding(const double *in, long long n, unsigned long long *counts)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = in[i];
+    const float hw = __double2float_rn(x);
+    const float sw = d2f_rn(x);
+    const bool tiny = fabs(x) < 1.1754943508222875e-38 && x != 0.0;
+    if (tiny) {
+        atomicAdd(&counts[2], 1ull);
+    } else {
+        const bool both_nan = (hw != hw) && (sw != sw);
+        if (!both_nan && __float_as_int(hw) != __float_as_int(sw)) atomicAdd(&counts[0], 1ull);
+    }
+    if (hw == hw && fabsf(hw) >= 1.17549435e-38f) {
+        const double a = f2d_exact(hw), b = (double)hw;
+        if (__double_as_longlong(a) != __double_as_longlong(b)) atomicAdd(&counts[1], 1ull);
+    }
+}
+
 }  // namespace hs3d
 
 using namespace hs3d;
+
+extern "C" hs3d_status hs3d_check_rounding(const double *in, int64_t n, unsigned long long *counts, void *stream)
+{
+    if (!in || !counts || n < 0) return fail(HS3D_ERR_INVALID, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && n > 0) {
+        k_check_rounding<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, counts);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "rounding check");
+}
 
 extern "C" {
 
@@ -81,6 +119,7 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
     b.dt_fixed = dt > 0.0 ? dt : 0.0;
     cudaError_t e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess && !(dt > 0.0)) e = launch_lambda(m->N, c->precision, c->physics, b, 0, s);
+    else if (e == cudaSuccess && c->precision == HS3D_MIXED32) e = launch_shadow(m->N, b, s);
     if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 0, 0, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     int k = 2;

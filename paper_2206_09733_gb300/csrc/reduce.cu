@@ -44,13 +44,29 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b,
         double u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
-        const Prim<R> q = prim_from_u<R>(u, it.gamma - 1.0);
+        const Phys<R> P = phys_of<R>(it);
+        Prim<R> q;
+        if constexpr (sizeof(R) == 8) {
+            q = prim_from_u<R>(u, P.gm1);
+        } else {
+            // the mixed path's dt pass also writes the FP32 shadow of the state
+            float us[5];
+            float *S = it.uf + (size_t)e * 5 * n3 + p;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                us[v] = d2f_rn(u[v]);
+                S[v * n3] = us[v];
+            }
+            q = prim_from_f(us, P.gm1);
+        }
         if (!(q.rho > (R)0) || !(q.p > (R)0)) {
             it.clk->bad = 1;
         } else {
-            const R c = sqrt((R)it.gamma * q.p / q.rho);
+            const R c = sqrt(P.gamma * q.p / q.rho);
             const R *JA = lambda_metric<R>(it) + (size_t)e * 9 * n3 + p;
-            const R iJ = (R)it.invJ[(size_t)e * n3 + p];
+            R iJ;
+            if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
+            else iJ = it.invJf[(size_t)e * n3 + p];
             R sc = (R)0, sv = (R)0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -59,8 +75,8 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b,
                 sc += (fabs(a1 * q.v1 + a2 * q.v2 + a3 * q.v3) + c * an) * iJ;
                 sv += (an * iJ) * (an * iJ);
             }
-            lc = (double)sc;
-            if (ns) lv = (double)((R)it.mu * sv / q.rho);
+            lc = widen<R>(sc);
+            if (ns) lv = widen<R>(P.mu * sv / q.rho);
             active = true;
         }
     }
@@ -147,6 +163,28 @@ cudaError_t launch_lambda(int N, int prec, int physics, const Batch &b, int slot
         default: return cudaErrorInvalidValue;
     }
 #undef HS3D_LAM
+    return cudaGetLastError();
+}
+
+// FP32 shadow of every item's state, one thread per node.
+__global__ void __launch_bounds__(256) k_shadow(const __grid_constant__ Batch b, int n3)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= b.total_elems * n3) return;
+    const long long ge = t / n3;
+    const int p = (int)(t - ge * n3);
+    const Item &it = find_item_elem(b, ge);
+    const size_t idx = (size_t)(ge - it.elem_begin) * 5 * n3 + p;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) it.uf[idx + (size_t)v * n3] = d2f_rn(it.u[idx + (size_t)v * n3]);
+}
+
+cudaError_t launch_shadow(int N, const Batch &b, cudaStream_t s)
+{
+    const int n3 = (N + 1) * (N + 1) * (N + 1);
+    const long long total = b.total_elems * n3;
+    if (total == 0) return cudaSuccess;
+    k_shadow<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(b, n3);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,15 @@ constexpr int vol_smem_per_node()
     return FORM == HS3D_VOL_STANDARD ? 15 : (16 + (NS ? 15 : 0));
 }
 
+// Node with index `idx` along direction d on the line with tangential indices (ta, tb).
+template <int n>
+__device__ __forceinline__ int line_node(int d, int idx, int ta, int tb)
+{
+    if (d == 0) return idx + n * (ta + n * tb);
+    if (d == 1) return ta + n * (idx + n * tb);
+    return ta + n * (tb + n * idx);
+}
+
 template <typename R>
 __device__ __forceinline__ const R *metric_ptr(const Item &it);
 template <>
@@ -59,7 +68,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     const int epb = blockDim.x / n3;
     R *sbuf = sD + ((n * n + 1) & ~1);
     R *sface = sbuf + (size_t)epb * PER * n3;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = (R)ops->D[t];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
     const long long ge = blockIdx.x * (long long)epb + le;
     bool valid = ge < b.total_elems;
@@ -83,6 +92,28 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         const Item &it = *itp;
         // the six face-flux blocks of this element: slot 2d+1 the +d face (own
         // index), slot 2d the -d face (owned by the -d neighbour)
+        // this node's inputs first, so their latencies overlap the gather below
+        const size_t node = (size_t)e * 5 * n3 + p;
+        const Phys<R> P = phys_of<R>(it);
+        const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ja[k] = JA[k * n3];
+        if constexpr (sizeof(R) == 8) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = it.u[node + v * n3];
+            q = prim_from_u<R>(u, P.gm1);
+        } else {
+            // the FP32 shadow carries exactly the rounded state the fluxes use;
+            // the FP64 state is needed only for the RK accumulation
+            float us[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) us[v] = it.uf[node + v * n3];
+            if (stage >= 0) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) u[v] = it.u[node + v * n3];
+            }
+            q = prim_from_f(us, P.gm1);
+        }
         {
             const R *FS = (const R *)it.fstar;
             const int E = it.E;
@@ -93,14 +124,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 F6[t] = FS[((size_t)d * E + owner) * 5 * n2 + off];
             }
         }
-        const double *U = it.u + (size_t)e * 5 * n3 + p;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = U[v * n3];
-        q = prim_from_u<R>(u, it.gamma - 1.0);
-        const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ja[k] = JA[k * n3];
-        const R E = (R)u[4];
+        const R E = q.E;
         R fv[3][5];
         if (NS) {
             const R *Gp = (const R *)it.grad + (size_t)e * 12 * n3 + p;
@@ -109,7 +133,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
             for (int k = 0; k < 12; ++k) G[k] = Gp[k * n3];
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-                visc_flux(q, G, (R)it.mu, (R)it.kappa, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fv[d]);
+                visc_flux(q, G, P.mu, P.kappa, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fv[d]);
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -145,10 +169,9 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
 
     double lc = 0.0, lv = 0.0;
     bool lam_active = false;
-    if (valid) {
-        const Item &it = *itp;
-        R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
-        if (FORM == HS3D_VOL_STANDARD) {
+    R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+    if (FORM == HS3D_VOL_STANDARD) {
+        if (valid) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
@@ -161,44 +184,79 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                     for (int v = 0; v < 5; ++v) V[v] += Dm * S[(d * 5 + v) * n3 + base + m * stride];
                 }
             }
-        } else {
-            const R hg = (R)(0.5 / (it.gamma - 1.0));
-            const ECNode<R> zi = {S[0 * n3 + p], S[1 * n3 + p], S[2 * n3 + p], S[3 * n3 + p],
-                                  S[4 * n3 + p], S[5 * n3 + p], S[6 * n3 + p]};
+        }
+    } else {
+        // Split form.  F#(u_i,u_m).(Ja_i + Ja_m) is symmetric in (i, m), so
+        // each pair of nodes on a line is evaluated once: per direction, the
+        // element's threads share the n^2 * n(n-1)/2 pair fluxes (written to
+        // shared memory), then every node sums D_im times the fluxes of its
+        // line in the original order m = 0..N.
+        constexpr int NP = n * (n - 1) / 2;
+        constexpr int W = n2 * NP;
+        R *PB = sface + (size_t)epb * FACEVALS + (size_t)le * 5 * W;
+        const R hg = valid ? phys_of<R>(*itp).hg : (R)0;
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            if (valid) {
+                for (int w = p; w < W; w += n3) {
+                    const int l = w / NP;
+                    int pp = w - l * NP, ia = 0;
+                    while (pp >= n - 1 - ia) {
+                        pp -= n - 1 - ia;
+                        ++ia;
+                    }
+                    const int im = ia + 1 + pp;
+                    const int ta = l % n, tb = l / n;
+                    const int a = line_node<n>(d, ia, ta, tb), c = line_node<n>(d, im, ta, tb);
+                    const ECNode<R> za = {S[0 * n3 + a], S[1 * n3 + a], S[2 * n3 + a], S[3 * n3 + a],
+                                          S[4 * n3 + a], S[5 * n3 + a], S[6 * n3 + a]};
+                    const ECNode<R> zc = {S[0 * n3 + c], S[1 * n3 + c], S[2 * n3 + c], S[3 * n3 + c],
+                                          S[4 * n3 + c], S[5 * n3 + c], S[6 * n3 + c]};
+                    const R a1 = S[(7 + d * 3 + 0) * n3 + a] + S[(7 + d * 3 + 0) * n3 + c];
+                    const R a2 = S[(7 + d * 3 + 1) * n3 + a] + S[(7 + d * 3 + 1) * n3 + c];
+                    const R a3 = S[(7 + d * 3 + 2) * n3 + a] + S[(7 + d * 3 + 2) * n3 + c];
+                    R fs[5];
+                    flux_ec(za, zc, hg, a1, a2, a3, fs);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
+                    for (int v = 0; v < 5; ++v) PB[v * W + w] = fs[v];
+                }
+            }
+            __syncthreads();
+            if (valid) {
+                const int i = ijk[d];
+                const int ta = (d == 0) ? ijk[1] : ijk[0];
+                const int tb = (d == 2) ? ijk[1] : ijk[2];
+                const int l = ta + n * tb;
                 const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
-                const int base = p - ijk[d] * stride;
-                const R *Drow = sD + ijk[d] * n;
+                const int base = p - i * stride;
+                const R *Drow = sD + i * n;
 #pragma unroll
                 for (int m = 0; m < n; ++m) {
                     const R Dm = Drow[m];
-                    const int pm = base + m * stride;
-                    if (m == ijk[d]) {
+                    if (m == i) {
                         // F#(u_i, u_i).(2 Ja^d_i) = 2 Ja^d_i . F_e(u_i)
 #pragma unroll
                         for (int v = 0; v < 5; ++v) V[v] += (R)2 * Dm * Fe[d][v];
                     } else {
-                        const ECNode<R> zm = {S[0 * n3 + pm], S[1 * n3 + pm], S[2 * n3 + pm], S[3 * n3 + pm],
-                                              S[4 * n3 + pm], S[5 * n3 + pm], S[6 * n3 + pm]};
-                        const R a1 = ja[d * 3 + 0] + S[(7 + d * 3 + 0) * n3 + pm];
-                        const R a2 = ja[d * 3 + 1] + S[(7 + d * 3 + 1) * n3 + pm];
-                        const R a3 = ja[d * 3 + 2] + S[(7 + d * 3 + 2) * n3 + pm];
-                        R fs[5];
-                        flux_ec(zi, zm, hg, a1, a2, a3, fs);
+                        const int lo = m < i ? m : i, hi = m < i ? i : m;
+                        const int w = l * NP + lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) V[v] += Dm * fs[v];
+                        for (int v = 0; v < 5; ++v) V[v] += Dm * PB[v * W + w];
                     }
                     if (NS) {
+                        const int pm = base + m * stride;
 #pragma unroll
                         for (int v = 1; v < 5; ++v) V[v] -= Dm * S[(16 + d * 5 + v) * n3 + pm];
                     }
                 }
             }
+            __syncthreads();
         }
-
+    }
+    if (valid) {
+        const Item &it = *itp;
         // surface lifting from the staged face fluxes
-        const R iw = (R)(1.0 / ops->w[0]);
+        const R iw = ops_iw0<R>(ops);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int ta = (d == 0) ? ijk[1] : ijk[0];
@@ -216,32 +274,68 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
             }
         }
 
-        const double ij = it.invJ[(size_t)e * n3 + p];
-        if (stage < 0) {
-            double *O = it.out + (size_t)e * 5 * n3 + p;
+        float nf[5];   // mixed path: FP32 shadow of the updated state
+        if constexpr (sizeof(R) == 8) {
+            const double ij = it.invJ[(size_t)e * n3 + p];
+            if (stage < 0) {
+                double *O = it.out + (size_t)e * 5 * n3 + p;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
-        } else {
-            const double dt = it.clk->dt;
-            const double A = c_rkA[stage], B = c_rkB[stage];
-            double *Gp = it.g + (size_t)e * 5 * n3 + p;
-            double *Up = it.u + (size_t)e * 5 * n3 + p;
+                for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
+            } else {
+                const double dt = it.clk->dt;
+                const double A = c_rkA[stage], B = c_rkB[stage];
+                double *Gp = it.g + (size_t)e * 5 * n3 + p;
+                double *Up = it.u + (size_t)e * 5 * n3 + p;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-                const double r = -(double)V[v] * ij;
-                const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
-                Gp[v * n3] = gv;
-                u[v] = u[v] + B * gv;
-                Up[v * n3] = u[v];
+                for (int v = 0; v < 5; ++v) {
+                    const double r = -(double)V[v] * ij;
+                    const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
+                    Gp[v * n3] = gv;
+                    u[v] = u[v] + B * gv;
+                    Up[v * n3] = u[v];
+                }
             }
+        } else {
+            // mixed path: the increment dt R = -dt V / J is formed in FP32 and
+            // widened exactly; the register and the state accumulate in FP64
+            // (two FP64 FMAs per variable).
+            const float ijf = it.invJf[(size_t)e * n3 + p];
+            if (stage < 0) {
+                double *O = it.out + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) O[v * n3] = f2d_exact(-(float)V[v] * ijf);
+            } else {
+                const float sdt = d2f_rn(it.clk->dt) * ijf;
+                const double A = c_rkA[stage], B = c_rkB[stage];
+                double *Gp = it.g + (size_t)e * 5 * n3 + p;
+                double *Up = it.u + (size_t)e * 5 * n3 + p;
+                float *Sp = it.uf + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    const double inc = f2d_exact(-(float)V[v] * sdt);
+                    const double gv = (stage == 0) ? inc : fma(A, Gp[v * n3], inc);
+                    Gp[v * n3] = gv;
+                    u[v] = fma(B, gv, u[v]);
+                    Up[v * n3] = u[v];
+                    nf[v] = d2f_rn(u[v]);
+                    Sp[v * n3] = nf[v];
+                }
+            }
+        }
+        if (stage >= 0) {
             if (lam_slot >= 0) {
                 // dt maxima of the updated state (same rule as k_lambda, in R)
-                const Prim<R> qn = prim_from_u<R>(u, it.gamma - 1.0);
+                const Phys<R> P = phys_of<R>(it);
+                Prim<R> qn;
+                if constexpr (sizeof(R) == 8) qn = prim_from_u<R>(u, P.gm1);
+                else qn = prim_from_f(nf, P.gm1);
                 if (!(qn.rho > (R)0) || !(qn.p > (R)0)) {
                     it.clk->bad = 1;
                 } else {
-                    const R c = sqrt((R)it.gamma * qn.p / qn.rho);
-                    const R iJ = (R)ij;
+                    const R c = sqrt(P.gamma * qn.p / qn.rho);
+                    R iJ;
+                    if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
+                    else iJ = it.invJf[(size_t)e * n3 + p];
                     R sc = (R)0, sv = (R)0;
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
@@ -250,8 +344,8 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                         sc += (fabs(a1 * qn.v1 + a2 * qn.v2 + a3 * qn.v3) + c * an) * iJ;
                         sv += (an * iJ) * (an * iJ);
                     }
-                    lc = (double)sc;
-                    lv = NS ? (double)((R)it.mu * sv / qn.rho) : 0.0;
+                    lc = widen<R>(sc);
+                    lv = NS ? widen<R>(P.mu * sv / qn.rho) : 0.0;
                     lam_active = true;
                 }
             }
@@ -294,8 +388,9 @@ static cudaError_t vol_launch2(const Batch &b, int stage, int lam_slot, cudaStre
         epb = vol_threads<N>() / n3;
         threads = epb * n3;
     }
-    size_t smem =
-        sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 + (size_t)epb * 30 * n2);
+    const size_t pairs = (FORM == HS3D_VOL_EC) ? (size_t)5 * n2 * (n * (n - 1) / 2) : 0;
+    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 +
+                               (size_t)epb * 30 * n2 + (size_t)epb * pairs);
     unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;

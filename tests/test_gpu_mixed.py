@@ -74,3 +74,22 @@ def test_mixed_tgv_residual_and_state():
     print(f"mixed TGV 16^3: residual rel-L2 {err_r:.3e}, state after 10 steps rel-L2 {err_u:.3e}")
     assert err_r < 1e-2
     assert err_u < 1e-5
+
+
+def test_integer_pipe_rounding_matches_hardware():
+    """The mixed path's FP64->FP32 rounding (bit operations) equals the
+    hardware round-to-nearest conversion on random and edge-case inputs;
+    the exact widening equals the hardware FP32->FP64 conversion."""
+    rng = np.random.default_rng(0)
+    parts = [rng.standard_normal(1 << 20) * 10.0 ** rng.uniform(-30, 30, 1 << 20),
+             rng.uniform(-1e3, 1e3, 1 << 20),
+             np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, 3.4028234663852886e38,
+                       3.4028235677973366e38, 1.1754943508222875e-38, 1e-40, -1e-45, 1e300, -1e-300])]
+    # halfway cases: float grid points plus exactly half an FP32 ulp
+    f = rng.uniform(1, 2, 1 << 16).astype(np.float32).astype(np.float64)
+    parts.append(f + 2.0 ** -24)
+    parts.append(f - 2.0 ** -24)
+    x = torch.from_numpy(np.concatenate(parts)).cuda()
+    bad, bad_widen, tiny = hs.check_rounding(x)
+    assert bad == 0 and bad_widen == 0
+    assert tiny >= 3
