@@ -33,6 +33,16 @@ constexpr int vol_threads()
     return ((N + 1) * (N + 1) * (N + 1) > 256) ? (N + 1) * (N + 1) * (N + 1) : 256;
 }
 
+// Minimum resident CTAs per SM asked of the compiler: the mixed path is
+// latency bound, so its register budget is capped (64 per thread with
+// 256- or 512-thread CTAs) to keep more warps resident; the FP64 path is
+// bound by the FP64 pipe and keeps its registers.
+template <int N, typename R>
+constexpr int vol_min_blocks()
+{
+    return sizeof(R) == 4 ? (((N + 1) * (N + 1) * (N + 1) <= 256) ? 4 : 2) : 1;
+}
+
 // Number of R values staged per node.
 template <int FORM, bool NS>
 constexpr int vol_smem_per_node()
@@ -57,7 +67,7 @@ template <>
 __device__ __forceinline__ const float *metric_ptr<float>(const Item &it) { return it.Jaf; }
 
 template <int N, typename R, bool NS, int FORM>
-__global__ void __launch_bounds__(vol_threads<N>())
+__global__ void __launch_bounds__(vol_threads<N>(), vol_min_blocks<N, R>())
 k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, int lam_slot)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -84,17 +94,15 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     const int ijk[3] = {p % n, (p / n) % n, p / n2};
 
     double u[5];
-    R ja[9];
-    R Fown[3][5];   // own total contravariant flux Ja^d.(F_e - F_v) at this node
-    R Fe[3][5];     // split form: own Ja^d.F_e (diagonal two-point term)
-    Prim<R> q;
+    R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+    const R iw = ops_iw0<R>(ops);
+    Prim<R> q;   // kept across the barrier: the surface term recomputes the own flux from it
     if (valid) {
         const Item &it = *itp;
-        // the six face-flux blocks of this element: slot 2d+1 the +d face (own
-        // index), slot 2d the -d face (owned by the -d neighbour)
         // this node's inputs first, so their latencies overlap the gather below
         const size_t node = (size_t)e * 5 * n3 + p;
         const Phys<R> P = phys_of<R>(it);
+        R ja[9];
         const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
 #pragma unroll
         for (int k = 0; k < 9; ++k) ja[k] = JA[k * n3];
@@ -103,17 +111,20 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
             for (int v = 0; v < 5; ++v) u[v] = it.u[node + v * n3];
             q = prim_from_u<R>(u, P.gm1);
         } else {
-            // the FP32 shadow carries exactly the rounded state the fluxes use;
-            // the FP64 state is needed only for the RK accumulation
+            // the FP32 shadow carries exactly the rounded state the fluxes use
             float us[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) us[v] = it.uf[node + v * n3];
-            if (stage >= 0) {
-#pragma unroll
-                for (int v = 0; v < 5; ++v) u[v] = it.u[node + v * n3];
-            }
             q = prim_from_f(us, P.gm1);
         }
+        R G[12];
+        if (NS) {
+            const R *Gp = (const R *)it.grad + (size_t)e * 12 * n3 + p;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) G[k] = Gp[k * n3];
+        }
+        // the six face-flux blocks of this element: slot 2d+1 the +d face (own
+        // index), slot 2d the -d face (owned by the -d neighbour)
         {
             const R *FS = (const R *)it.fstar;
             const int E = it.E;
@@ -124,29 +135,31 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 F6[t] = FS[((size_t)d * E + owner) * 5 * n2 + off];
             }
         }
-        const R E = q.E;
-        R fv[3][5];
-        if (NS) {
-            const R *Gp = (const R *)it.grad + (size_t)e * 12 * n3 + p;
-            R G[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) G[k] = Gp[k * n3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                visc_flux(q, G, P.mu, P.kappa, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fv[d]);
-        }
+        // contravariant fluxes at this node; for the split form the diagonal
+        // two-point term F#(u_i,u_i).(2 Ja_i) = 2 Ja_i.F_e(u_i) goes straight
+        // into V so that no flux is held across the barrier
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            euler_flux(q, E, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], Fe[d]);
+            R fe[5], fv[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+            euler_flux(q, q.E, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fe);
+            if (NS) visc_flux(q, G, P.mu, P.kappa, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fv);
+            R own[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) Fown[d][v] = NS ? Fe[d][v] - fv[d][v] : Fe[d][v];
+            for (int v = 0; v < 5; ++v) own[v] = NS ? fe[v] - fv[v] : fe[v];
+            if (FORM == HS3D_VOL_STANDARD) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) S[(d * 5 + v) * n3 + p] = own[v];
+            } else {
+                const R dii = (R)2 * ops_D<R>(ops, ijk[d] * n + ijk[d]);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += dii * fe[v];
+                if (NS) {
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) S[(16 + d * 5 + v) * n3 + p] = fv[v];
+                }
+            }
         }
-        if (FORM == HS3D_VOL_STANDARD) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-                for (int v = 0; v < 5; ++v) S[(d * 5 + v) * n3 + p] = Fown[d][v];
-        } else {
+        if (FORM != HS3D_VOL_STANDARD) {
             ECNode<R> z = ec_node(q);
             S[0 * n3 + p] = z.rho;
             S[1 * n3 + p] = z.v1;
@@ -157,19 +170,12 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
             S[6 * n3 + p] = z.lbeta;
 #pragma unroll
             for (int k = 0; k < 9; ++k) S[(7 + k) * n3 + p] = ja[k];
-            if (NS) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) S[(16 + d * 5 + v) * n3 + p] = fv[d][v];
-            }
         }
     }
     __syncthreads();
 
     double lc = 0.0, lv = 0.0;
     bool lam_active = false;
-    R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
     if (FORM == HS3D_VOL_STANDARD) {
         if (valid) {
 #pragma unroll
@@ -190,7 +196,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         // each pair of nodes on a line is evaluated once: per direction, the
         // element's threads share the n^2 * n(n-1)/2 pair fluxes (written to
         // shared memory), then every node sums D_im times the fluxes of its
-        // line in the original order m = 0..N.
+        // line.
         constexpr int NP = n * (n - 1) / 2;
         constexpr int W = n2 * NP;
         R *PB = sface + (size_t)epb * FACEVALS + (size_t)le * 5 * W;
@@ -233,11 +239,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
 #pragma unroll
                 for (int m = 0; m < n; ++m) {
                     const R Dm = Drow[m];
-                    if (m == i) {
-                        // F#(u_i, u_i).(2 Ja^d_i) = 2 Ja^d_i . F_e(u_i)
-#pragma unroll
-                        for (int v = 0; v < 5; ++v) V[v] += (R)2 * Dm * Fe[d][v];
-                    } else {
+                    if (m != i) {
                         const int lo = m < i ? m : i, hi = m < i ? i : m;
                         const int w = l * NP + lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
 #pragma unroll
@@ -255,22 +257,42 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     }
     if (valid) {
         const Item &it = *itp;
-        // surface lifting from the staged face fluxes
-        const R iw = ops_iw0<R>(ops);
+        // surface term (1/w)(F* - own) on the +d face, (1/w)(own - F*) on the
+        // -d face: the difference is formed first (it is small where the large
+        // fluxes nearly cancel), with the own flux Ja^d.(F_e - F_v) re-read
+        // (standard form) or recomputed from the node's state (split form)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
+            if (ijk[d] != N && ijk[d] != 0) continue;
             const int ta = (d == 0) ? ijk[1] : ijk[0];
             const int tb = (d == 2) ? ijk[1] : ijk[2];
             const int ab = ta + n * tb;
+            R own[5];
+            if (FORM == HS3D_VOL_STANDARD) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) own[v] = S[(d * 5 + v) * n3 + p];
+            } else {
+                euler_flux(q, q.E, S[(7 + d * 3) * n3 + p], S[(8 + d * 3) * n3 + p], S[(9 + d * 3) * n3 + p], own);
+                if (NS) {
+#pragma unroll
+                    for (int v = 1; v < 5; ++v) own[v] -= S[(16 + d * 5 + v) * n3 + p];
+                }
+            }
             if (ijk[d] == N) {
                 const R *F = F6 + (2 * d + 1) * 5 * n2 + ab;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) V[v] += iw * (F[v * n2] - Fown[d][v]);
-            }
-            if (ijk[d] == 0) {
+                for (int v = 0; v < 5; ++v) V[v] += iw * (F[v * n2] - own[v]);
+            } else {
                 const R *F = F6 + (2 * d) * 5 * n2 + ab;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) V[v] += iw * (Fown[d][v] - F[v * n2]);
+                for (int v = 0; v < 5; ++v) V[v] += iw * (own[v] - F[v * n2]);
+            }
+        }
+        if constexpr (sizeof(R) == 4) {
+            // the FP64 state is needed only for the RK accumulation
+            if (stage >= 0) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) u[v] = it.u[(size_t)e * 5 * n3 + p + v * n3];
             }
         }
 
@@ -337,9 +359,10 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                     if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
                     else iJ = it.invJf[(size_t)e * n3 + p];
                     R sc = (R)0, sv = (R)0;
+                    const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        const R a1 = ja[d * 3], a2 = ja[d * 3 + 1], a3 = ja[d * 3 + 2];
+                        const R a1 = JA[(d * 3) * n3], a2 = JA[(d * 3 + 1) * n3], a3 = JA[(d * 3 + 2) * n3];
                         const R an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
                         sc += (fabs(a1 * qn.v1 + a2 * qn.v2 + a3 * qn.v3) + c * an) * iJ;
                         sv += (an * iJ) * (an * iJ);
@@ -417,7 +440,10 @@ static cudaError_t prep_vol()
     cudaError_t e = cudaSuccess;
 #define HS3D_ATTR(R, NS, F)                                                                                  \
     if (e == cudaSuccess)                                                                                    \
-        e = cudaFuncSetAttribute(k_volume<N, R, NS, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        e = cudaFuncSetAttribute(k_volume<N, R, NS, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);    \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(k_volume<N, R, NS, F>, cudaFuncAttributePreferredSharedMemoryCarveout,       \
+                                 cudaSharedmemCarveoutMaxShared);
     HS3D_ATTR(double, false, HS3D_VOL_STANDARD)
     HS3D_ATTR(double, true, HS3D_VOL_STANDARD)
     HS3D_ATTR(double, false, HS3D_VOL_EC)
