@@ -29,7 +29,8 @@ _lib = None
 
 PHYSICS = {"euler": 0, "ns": 1}
 SURFACE = {"lf": 0, "roe": 1, "ec": 2}
-VOLUME = {"standard": 0, "ec": 1}
+VOLUME = {"standard": 0, "ec": 1, "kg": 2, "pirozzoli": 3, "ducros": 4}
+TIME = {"rk3": 0, "rk4": 1}
 
 
 def build(force: bool = False) -> str:
@@ -50,7 +51,8 @@ class _Box(C.Structure):
 
 class _Cfg(C.Structure):
     _fields_ = [("physics", C.c_int), ("surface_flux", C.c_int), ("volume_form", C.c_int),
-                ("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double), ("cfl", C.c_double)]
+                ("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double), ("cfl", C.c_double),
+                ("time_scheme", C.c_int)]
 
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -84,6 +86,9 @@ def lib():
             L.orc_dt.restype = C.c_double
             L.orc_rk3_step.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp, C.c_double, C.POINTER(C.c_double)]
             L.orc_rk3_coefficients.argtypes = [_dp, _dp, _dp]
+            L.orc_rk4_coefficients.argtypes = [_dp, _dp, _dp]
+            L.orc_lsrk_stage.argtypes = [C.c_int, C.c_longlong, C.c_int, C.c_double, _dp, _dp, _dp]
+            L.orc_flux_split.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, _dp]
             L.orc_lsrk3_stage.argtypes = [C.c_longlong, C.c_int, C.c_double, _dp, _dp, _dp]
             L.orc_ic_vortex.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_double, _dp]
@@ -116,13 +121,14 @@ def dmatrix(N: int, x=None):
 # --------------------------------------------------------------------------- configuration
 
 class Cfg:
-    def __init__(self, physics="euler", surface="lf", volume="standard", gamma=1.4, Re=1600.0, Pr=0.72, cfl=0.5):
+    def __init__(self, physics="euler", surface="lf", volume="standard", gamma=1.4, Re=1600.0, Pr=0.72, cfl=0.5,
+                 time="rk3"):
         self.physics, self.surface, self.volume = physics, surface, volume
-        self.gamma, self.Re, self.Pr, self.cfl = gamma, Re, Pr, cfl
+        self.gamma, self.Re, self.Pr, self.cfl, self.time = gamma, Re, Pr, cfl, time
 
     def c(self):
         return _Cfg(PHYSICS[self.physics], SURFACE[self.surface], VOLUME[self.volume],
-                    self.gamma, self.Re, self.Pr, self.cfl)
+                    self.gamma, self.Re, self.Pr, self.cfl, TIME[self.time])
 
 
 class Mesh:
@@ -269,6 +275,24 @@ def entropy_vars(u, gamma=1.4):
 
 def logmean(a, b):
     return lib().orc_logmean(a, b)
+
+
+def flux_split(kind, uL, uR, a, gamma=1.4):
+    """Two-point split-form flux: kind "kg", "pirozzoli" or "ducros"."""
+    f = np.zeros(5)
+    lib().orc_flux_split(VOLUME[kind], _v(uL), _v(uR), _v(a, 3), gamma, f)
+    return f
+
+
+def rk4_coefficients():
+    A, B, Cc = np.zeros(5), np.zeros(5), np.zeros(5)
+    lib().orc_rk4_coefficients(A, B, Cc)
+    return A, B, Cc
+
+
+def lsrk_stage(scheme, k, dt, u, g, R):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lib().orc_lsrk_stage(TIME[scheme], u.size, k, dt, u, g, np.ascontiguousarray(R, dtype=np.float64))
 
 
 def rk3_coefficients():

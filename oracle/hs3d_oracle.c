@@ -304,8 +304,9 @@ void orc_mesh_arrays(const orc_mesh *m, double *xi, double *w, double *D, double
 typedef struct {
     int physics;       /* 0 Euler, 1 Navier-Stokes */
     int surface_flux;  /* 0 Lax-Friedrichs, 1 Roe, 2 entropy-conservative (central) */
-    int volume_form;   /* 0 standard, 1 Chandrashekar split form */
+    int volume_form;   /* 0 standard; split forms: 1 Chandrashekar, 2 Kennedy-Gruber, 3 Pirozzoli, 4 Ducros */
     double gamma, Re, Pr, cfl;
+    int time_scheme;   /* 0 Williamson RK3, 1 Carpenter-Kennedy RK4(5) */
 } orc_cfg;
 
 /* rho, v, p from u; p = (gamma-1)(rho e - rho |v|^2 / 2). */
@@ -442,6 +443,50 @@ void orc_flux_ec(const double *uL, const double *uR, const double *a, double g, 
     for (int c = 0; c < 3; ++c) f[1 + c] = f[0] * vav[c] + pt * a[c];
     f[4] = f[0] * (1.0 / (2.0 * (g - 1.0) * beta_ln) - 0.5 * v2av)
          + vav[0] * f[1] + vav[1] * f[2] + vav[2] * f[3];
+}
+
+/* Further split forms of Sec. 3.5, each a symmetric two-point flux dotted
+ * with a ({.} arithmetic mean of the two states, v_a = v.a, e = rho e / rho,
+ * h = (rho e + p)/rho):
+ *   Kennedy-Gruber (2008):  f_rho = {rho}{v_a},  f_m = {rho}{v_a}{v} + {p} a,
+ *                           f_E = {rho}{v_a}{e} + {p}{v_a}
+ *   Pirozzoli (2010):       f_rho = {rho}{v_a},  f_m = {rho}{v_a}{v} + {p} a,
+ *                           f_E = {rho}{v_a}{h}
+ *   Ducros et al. (2000):   f_rho = {rho}{v_a},  f_m = {rho v}{v_a} + {p} a,
+ *                           f_E = {rho e + p}{v_a}
+ * kind: 2 Kennedy-Gruber, 3 Pirozzoli, 4 Ducros. */
+void orc_flux_split(int kind, const double *uL, const double *uR, const double *a, double g, double *f)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double rho_av = 0.5 * (rL + rR), p_av = 0.5 * (pL + pR);
+    double vaL = vL[0] * a[0] + vL[1] * a[1] + vL[2] * a[2];
+    double vaR = vR[0] * a[0] + vR[1] * a[1] + vR[2] * a[2];
+    double va_av = 0.5 * (vaL + vaR);
+    if (kind == 4) {
+        f[0] = rho_av * va_av;
+        for (int c = 0; c < 3; ++c) f[1 + c] = 0.5 * (uL[1 + c] + uR[1 + c]) * va_av + p_av * a[c];
+        f[4] = 0.5 * ((uL[4] + pL) + (uR[4] + pR)) * va_av;
+        return;
+    }
+    double m = rho_av * va_av;
+    f[0] = m;
+    for (int c = 0; c < 3; ++c) f[1 + c] = m * 0.5 * (vL[c] + vR[c]) + p_av * a[c];
+    if (kind == 2) {
+        double e_av = 0.5 * (uL[4] / rL + uR[4] / rR);
+        f[4] = m * e_av + p_av * va_av;
+    } else {
+        double h_av = 0.5 * ((uL[4] + pL) / rL + (uR[4] + pR) / rR);
+        f[4] = m * h_av;
+    }
+}
+
+/* Two-point volume flux of split form `form` (1..4) dotted with a. */
+static void split_flux(int form, const double *ui, const double *um, const double *a, double g, double *f)
+{
+    if (form == 1) orc_flux_ec(ui, um, a, g, f);
+    else orc_flux_split(form, ui, um, a, g, f);
 }
 
 /* Entropy variables w = dS/du for S = -rho s, s = ln p - gamma ln rho
@@ -593,6 +638,7 @@ static void surface_flux(int kind, const double *uin, const double *uout, const 
 /* du/dt = -(V + S)/J per element, with
  *   standard form  V = sum_d D_d F~^d,  F~^d = sum_c Ja^d_c (F_e - F_v)_c
  *   split form     V = sum_d [ 2 sum_m D_im F#(u_i, u_m).(Ja^d_i + Ja^d_m)/2 ] - sum_d D_d F~_v^d
+ *                  (F# the Chandrashekar, Kennedy-Gruber, Pirozzoli or Ducros two-point flux)
  *   surface        S = (1/w_end) [ +-(F^*(L,R; Sn_L) - F_v^*.Sn_L) - (F_e - F_v)(in).(+-Ja^d_in) ]
  * on each face node (+ on the element's +d face, - on its -d face),
  * F_v^* = (F_v(L) + F_v(R))/2 (BR1), Sn_L = Ja^d of the face's minus-side element. */
@@ -651,7 +697,7 @@ int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double 
                         for (int c = 0; c < 3; ++c)
                             a[c] = 0.5 * (m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p]
                                         + m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + pm]);
-                        orc_flux_ec(ui, um, a, g, fs);
+                        split_flux(cfg->volume_form, ui, um, a, g, fs);
                         double Dim = m->D[ijk[d] * n + mm];
                         for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += 2.0 * Dim * fs[v];
                     }
@@ -731,20 +777,46 @@ static const double RK3_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
 static const double RK3_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 static const double RK3_C[3] = {0.0, 1.0 / 3.0, 3.0 / 4.0};
 
+/* Carpenter & Kennedy (1994) 5-stage, fourth-order 2N-storage RK
+ * coefficients (their fourth-order five-stage solution; the paper's
+ * "explicit Runge-Kutta 4th order" option, Sec. 3.7). */
+static const double RK4_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double RK4_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                2277821191437.0 / 14882151754819.0};
+static const double RK4_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                                2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+static int lsrk_stages(int scheme) { return scheme == 1 ? 5 : 3; }
+static const double *lsrk_A(int scheme) { return scheme == 1 ? RK4_A : RK3_A; }
+static const double *lsrk_B(int scheme) { return scheme == 1 ? RK4_B : RK3_B; }
+
 void orc_rk3_coefficients(double *A, double *B, double *C)
 {
     for (int k = 0; k < 3; ++k) { A[k] = RK3_A[k]; B[k] = RK3_B[k]; C[k] = RK3_C[k]; }
 }
 
+void orc_rk4_coefficients(double *A, double *B, double *C)
+{
+    for (int k = 0; k < 5; ++k) { A[k] = RK4_A[k]; B[k] = RK4_B[k]; C[k] = RK4_C[k]; }
+}
+
 /* One low-storage stage on a flat array: g <- A_k g + dt R; u <- u + B_k g.
  * Stage 0 (A_0 = 0) does not read g. */
+void orc_lsrk_stage(int scheme, long long count, int k, double dt, double *u, double *g, const double *R)
+{
+    const double *A = lsrk_A(scheme), *B = lsrk_B(scheme);
+    for (long long i = 0; i < count; ++i) {
+        double gi = (k == 0) ? dt * R[i] : A[k] * g[i] + dt * R[i];
+        g[i] = gi;
+        u[i] = u[i] + B[k] * gi;
+    }
+}
+
 void orc_lsrk3_stage(long long count, int k, double dt, double *u, double *g, const double *R)
 {
-    for (long long i = 0; i < count; ++i) {
-        double gi = (k == 0) ? dt * R[i] : RK3_A[k] * g[i] + dt * R[i];
-        g[i] = gi;
-        u[i] = u[i] + RK3_B[k] * gi;
-    }
+    orc_lsrk_stage(0, count, k, dt, u, g, R);
 }
 
 /* Time step (no formula in the paper; the reading used by this library):
@@ -786,7 +858,8 @@ double orc_dt(const orc_mesh *m, const orc_cfg *cfg, const double *u)
     return dt;
 }
 
-/* One Williamson RK3 step.  dt_in > 0 is used as given; dt_in <= 0 computes dt
+/* One low-storage RK step of the configured scheme (Williamson RK3 or
+ * Carpenter-Kennedy RK4).  dt_in > 0 is used as given; dt_in <= 0 computes dt
  * from the state at the start of the step.  Returns the dt used through *dt_used. */
 int orc_rk3_step(const orc_mesh *m, const orc_cfg *cfg, double *u, double *g, double dt_in, double *dt_used)
 {
@@ -794,9 +867,9 @@ int orc_rk3_step(const orc_mesh *m, const orc_cfg *cfg, double *u, double *g, do
     double dt = dt_in > 0.0 ? dt_in : orc_dt(m, cfg, u);
     double *R = (double *)malloc(sizeof(double) * count);
     if (!R) return -1;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < lsrk_stages(cfg->time_scheme); ++k) {
         orc_residual(m, cfg, u, R);
-        orc_lsrk3_stage(count, k, dt, u, g, R);
+        orc_lsrk_stage(cfg->time_scheme, count, k, dt, u, g, R);
     }
     free(R);
     if (dt_used) *dt_used = dt;

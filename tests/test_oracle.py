@@ -653,3 +653,167 @@ def test_integrals_volume_and_mass():
     u = np.zeros(m.shape)
     u[:, 0] = 2.0
     assert abs(m.integrals(G, u)[0] - 12.0) < 1e-12 * 12.0
+
+
+# --------------------------------------------------------------------------- further split forms (Sec. 3.5) and RK4 (Sec. 3.7)
+
+SPLITS = ["kg", "pirozzoli", "ducros"]
+
+
+@pytest.mark.parametrize("kind", SPLITS)
+def test_split_flux_consistency_and_symmetry(kind):
+    rng = np.random.default_rng(31)
+    for _ in range(20):
+        uL, uR = _random_state(rng), _random_state(rng)
+        a = rng.standard_normal(3)
+        assert np.allclose(O.flux_split(kind, uL, uL, a), O.flux_euler(uL, a), rtol=1e-13, atol=1e-13)
+        assert np.allclose(O.flux_split(kind, uL, uR, a), O.flux_split(kind, uR, uL, a), rtol=1e-14, atol=1e-14)
+        # linear in the direction vector
+        b = rng.standard_normal(3)
+        assert np.allclose(O.flux_split(kind, uL, uR, a + b),
+                           O.flux_split(kind, uL, uR, a) + O.flux_split(kind, uL, uR, b), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,kep", [("kg", True), ("pirozzoli", True), ("ducros", False), ("ec", True)])
+def test_split_flux_kinetic_energy_preservation(kind, kep):
+    """Jameson's condition for a kinetic-energy-preserving flux: the
+    momentum flux is {v} times the mass flux plus a pressure term along a."""
+    rng = np.random.default_rng(32)
+    worst = 0.0
+    for _ in range(20):
+        uL, uR = _random_state(rng), _random_state(rng)
+        a = rng.standard_normal(3)
+        f = O.flux_ec(uL, uR, a) if kind == "ec" else O.flux_split(kind, uL, uR, a)
+        vav = 0.5 * (uL[1:4] / uL[0] + uR[1:4] / uR[0])
+        r = f[1:4] - vav * f[0]
+        # the remainder must be parallel to a
+        worst = max(worst, np.linalg.norm(np.cross(r, a)) / (np.linalg.norm(r) * np.linalg.norm(a) + 1e-300))
+    if kep:
+        assert worst < 1e-12
+    else:
+        assert worst > 1e-3
+
+
+@pytest.mark.parametrize("volume", SPLITS)
+def test_split_forms_free_stream_and_conservation(curved, volume):
+    m = curved
+    st = np.array([1.2, 0.36, -0.24, 0.12, 2.6])
+    u = np.broadcast_to(st[None, :, None, None, None], m.shape).copy()
+    for physics in ("euler", "ns"):
+        r = m.residual(O.Cfg(physics, "roe", volume, Re=50.0), u)
+        assert np.abs(r).max() < 1e-12
+    rng = np.random.default_rng(33)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    r = m.residual(O.Cfg("ns", "lf", volume, Re=50.0), u)
+    tot = m.integrals(G, u, r)[:5]
+    mag = m.integrals(G, u, np.abs(r))[:5]
+    assert np.abs(tot / mag).max() < 1e-13
+
+
+@pytest.mark.parametrize("kind", SPLITS)
+def test_split_flux_differencing_equals_product_rule_form(kind):
+    """Flux differencing 2 sum_j D_ij f#(u_i, u_j) with an average-product
+    two-point flux reproduces the split derivative written with products
+    (Kennedy-Gruber's quarter form for triple products, the half form for
+    pairs).  This ties each flux to the split form it names, at arbitrary
+    nodal values, through the SBP matrix alone."""
+    N = 5
+    D = O.dmatrix(N)
+    rng = np.random.default_rng(34)
+    u = _random_state(rng, (N + 1,)).T            # (n, 5) nodal states
+    a = np.array([1.0, 0.0, 0.0])
+    lhs = np.array([2 * sum(D[i, j] * O.flux_split(kind, u[i], u[j], a) for j in range(N + 1))
+                    for i in range(N + 1)])
+    rho = u[:, 0]
+    v = u[:, 1:4] / rho[:, None]
+    E = u[:, 4]
+    p = (G - 1) * (E - 0.5 * rho * (v * v).sum(1))
+    vx = v[:, 0]
+
+    def d2(x, y):      # {x}{y} -> (D(xy) + x Dy + y Dx) / 2
+        return 0.5 * (D @ (x * y) + x * (D @ y) + y * (D @ x))
+
+    def d3(x, y, z):   # {x}{y}{z} -> quarter form
+        return 0.25 * (D @ (x * y * z) + x * (D @ (y * z)) + y * (D @ (x * z)) + z * (D @ (x * y))
+                       + x * y * (D @ z) + x * z * (D @ y) + y * z * (D @ x))
+
+    rhs = np.zeros_like(lhs)
+    if kind == "ducros":
+        rhs[:, 0] = d2(u[:, 0], vx)
+        for b in range(3):
+            rhs[:, 1 + b] = d2(u[:, 1 + b], vx)
+        rhs[:, 1] += D @ p
+        rhs[:, 4] = d2(E + p, vx)
+    else:
+        rhs[:, 0] = d2(rho, vx)
+        for b in range(3):
+            rhs[:, 1 + b] = d3(rho, vx, v[:, b])
+        rhs[:, 1] += D @ p
+        if kind == "kg":
+            rhs[:, 4] = d3(rho, vx, E / rho) + d2(p, vx)
+        else:
+            rhs[:, 4] = d3(rho, vx, (E + p) / rho)
+    assert np.abs(lhs - rhs).max() < 1e-11 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("volume", SPLITS)
+def test_split_forms_spectral_convergence(volume):
+    errs = []
+    for N in (2, 3, 4, 5, 6):
+        m = O.Mesh(3, 3, 3, N, lo=(0,) * 3, hi=(10,) * 3, amp=0.05)
+        d = 1e-5
+        exact = (_wave(m, d) - _wave(m, -d)) / (2 * d)
+        errs.append(_rel(m.residual(O.Cfg("euler", "roe", volume), _wave(m, 0.0)), exact))
+    # the triple-product forms carry larger error constants on a density
+    # wave (they do not keep pressure equilibrium) but converge spectrally
+    assert errs[-1] < 4e-3
+    assert all(b < 0.4 * a for a, b in zip(errs, errs[1:]))
+
+
+def test_carpenter_kennedy_coefficients_match_golden():
+    rows = {}
+    with open(os.path.join(GOLD, "carpenter_kennedy_rk4.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, *vals = (s.strip() for s in line.split("|"))
+            rows[k] = [float(Fraction(v)) for v in vals]
+    A, B, Cc = O.rk4_coefficients()
+    for got, key in ((A, "A"), (B, "B"), (Cc, "C")):
+        assert np.allclose(got, rows[key], rtol=0, atol=1e-16)
+
+
+def test_rk4_amplification_is_fourth_order():
+    """The 5-stage scheme's amplification for y' = z y is a degree-5
+    polynomial whose first five coefficients are 1, 1, 1/2, 1/6, 1/24."""
+    zs = np.linspace(-0.5, 0.5, 6)
+    amps = []
+    for z in zs:
+        y, gg = np.array([1.0]), np.zeros(1)
+        for k in range(5):
+            O.lsrk_stage("rk4", k, 1.0, y, gg, z * y.copy())
+        amps.append(y[0])
+    coef = np.linalg.solve(np.vander(zs, 6, increasing=True), np.array(amps))
+    assert np.allclose(coef[:5], [1, 1, 0.5, 1 / 6, 1 / 24], rtol=0, atol=1e-10)
+    assert abs(coef[5] - 1 / 120) > 1e-6    # not the fifth-order Taylor term
+
+
+def test_rk4_fourth_order_on_nonlinear_problem():
+    """Self-convergence with a smooth right-hand side: the entropy-
+    conservative surface and volume fluxes.  (Roe's |A| is only Lipschitz
+    where an eigenvalue changes sign, which caps the observed order of a
+    fourth-order integrator near two on this vortex.)"""
+    m = O.Mesh(4, 4, 1, 3, lo=(0, 0, 0), hi=(10, 10, 2.5))
+    cfg = O.Cfg("euler", "ec", "ec", time="rk4")
+    u0 = m.ic_vortex(G, 0.5, 5.0)
+    T = 0.4
+    sols = []
+    for nsteps in (4, 8, 16, 32):
+        u = u0.copy()
+        g = np.zeros_like(u)
+        for _ in range(nsteps):
+            m.rk3_step(cfg, u, g, dt=T / nsteps)
+        sols.append(u)
+    d = [np.linalg.norm(a - b) for a, b in zip(sols, sols[1:])]
+    ratios = [a / b for a, b in zip(d, d[1:])]
+    assert all(12.0 < r < 20.0 for r in ratios), ratios
