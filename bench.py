@@ -175,6 +175,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+# ------------------------------------------------------------------ measured DRAM traffic of the dominant kernel
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of k_volume<3,float,NS,EC> on this workload,
+# from one ncu capture (profiles/k_volume_mixed_ec_ns_N3_tgv16_traffic.md), and the digest of the
+# kernel's sources at the time of the capture: the figure is reported only while they are unchanged.
+VOLUME_TRAFFIC = {"bytes_per_launch": 49774165,
+                  "sources_sha256": "c82acdf802f110aa879ace94ea925a24832e77fbde546fb7b38734ffcbd64b4f"}
+VOLUME_SOURCES = ["volume_kernel.cuh", "volume_ec.cu", "physics.cuh", "internal.cuh"]
+
+
+def volume_sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in VOLUME_SOURCES:
+        with open(os.path.join(ROOT, "paper_2206_09733_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_volume_traffic():
+    t = VOLUME_TRAFFIC
+    if t["bytes_per_launch"] is None or t["sources_sha256"] != volume_sources_digest():
+        return None
+    return t["bytes_per_launch"]
+
+
 # ------------------------------------------------------------------ algorithmic cost model (per launch)
 
 def kernel_bytes(kernel, prec, E=None, n=N + 1):
@@ -330,8 +356,10 @@ def run_hs3d(args, world, rank, local):
     hbm_peak = measured_hbm_peak()
     achieved_gbs = kernel_bytes(dom, "mixed32") / (per_launch_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak[0], "unit": "GB/s",
-            "frac": round(achieved_gbs / hbm_peak[0], 4), "traffic": None, "kernel": f"k_volume<3,float,NS,EC>"
-            if dom == "volume" else dom, "peak_source": hbm_peak[1]}
+            "frac": round(achieved_gbs / hbm_peak[0], 4),
+            "traffic": measured_volume_traffic() if dom == "volume" else None,
+            "algorithmic_bytes_per_launch": kernel_bytes(dom, "mixed32"),
+            "kernel": "k_volume<3,float,NS,EC>" if dom == "volume" else dom, "peak_source": hbm_peak[1]}
     p64 = prof["fp64"]
     fp64_ach = volume_flops() / (p64["volume"] / 3.0 * 1e-3) / 1e12
     fp64_roof = {"bound": "alu", "kernel": "k_volume<3,double,NS,EC>", "achieved": round(fp64_ach, 3),
@@ -345,6 +373,9 @@ def run_hs3d(args, world, rank, local):
         extra["tgv_64cubed_N3_standard_lf_euler"] = run_workload("sweep", 64, 3, "euler", "lf", "standard", 5, 2)
         extra["tgv_52cubed_N4_standard_lf_euler"] = run_workload("sweep", 52, 4, "euler", "lf", "standard", 5, 2)
         extra["tgv_64cubed_N3_standard_roe_br1"] = run_workload("sweep", 64, 3, "ns", "roe", "standard", 5, 2)
+        for vol, tm in (("kg", "rk4"), ("pirozzoli", "rk3"), ("ducros", "rk3")):
+            extra[f"tgv_32cubed_N3_{vol}_roe_br1_{tm}"] = run_workload("split", 32, 3, "ns", "roe", vol, 5, 2,
+                                                                       time=tm)
 
     if args.stress > 0:
         extra["admission_stress"] = run_stress(args.stress, args.stress_budget_gb, args.stress_emax, "mixed32")
@@ -402,19 +433,20 @@ def measured_hbm_peak():
 
 # ------------------------------------------------------------------ further workloads (reported beside the line)
 
-def step_bytes(prec, physics, E, n):
-    """Compulsory DRAM bytes of one RK3 step: three stages of (BR1 gradients,)
-    face fluxes and the element kernel, plus the priming dt pass."""
+def step_bytes(prec, physics, E, n, stages=3):
+    """Compulsory DRAM bytes of one RK step: `stages` stages of (BR1
+    gradients,) face fluxes and the element kernel (the dt maxima are fused
+    into the last stage)."""
     per_stage = kernel_bytes("face", prec, E, n) + kernel_bytes("volume", prec, E, n)
     if physics == "ns":
         per_stage += kernel_bytes("grad", prec, E, n)
     else:   # no gradients are read by the face and element kernels
         s = 8 if prec == "fp64" else 4
         per_stage -= E * 12 * n ** 3 * s + 3 * E * 24 * n * n * s
-    return 3 * per_stage
+    return stages * per_stage
 
 
-def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisions=("mixed32", "fp64")):
+def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisions=("mixed32", "fp64"), time="rk3"):
     """DOF-stage-updates/s of one curved TGV configuration (Ma 0.1, Re 1600,
     amp 0.05, CFL 0.5), CUDA-event timed per step; the state exceeds L2 so no
     flush is needed.  Also the algorithmic HBM throughput of the step."""
@@ -425,10 +457,12 @@ def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisio
     mesh = hs.Mesh(Ed, Ed, Ed, Nd, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=AMP)
     n = Nd + 1
     nodes = Ed ** 3 * n ** 3
-    out = {"E": Ed ** 3, "N": Nd, "nodes": nodes, "scheme": f"{physics} {surface} surface, {volume} volume"}
+    stages = 5 if time == "rk4" else 3
+    out = {"E": Ed ** 3, "N": Nd, "nodes": nodes,
+           "scheme": f"{physics} {surface} surface, {volume} volume, {time} ({stages} stages)"}
     stream = torch.cuda.current_stream()
     for prec in precisions:
-        cfg = hs.solver_cfg(physics, surface, volume, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+        cfg = hs.solver_cfg(physics, surface, volume, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL, time=time)
         mesh.autotune(cfg)
         u = mesh.init_state(mesh.empty_state(), "tgv", GAMMA, MA)
         g = torch.zeros_like(u)
@@ -440,8 +474,8 @@ def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisio
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
-        gbs = step_bytes(prec, physics, Ed ** 3, n) / (ms * 1e-3) / 1e9
-        out[prec] = {"value": round(nodes * 3 / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
+        gbs = step_bytes(prec, physics, Ed ** 3, n, stages) / (ms * 1e-3) / 1e9
+        out[prec] = {"value": round(nodes * stages / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
                      "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac": round(gbs / measured_hbm_peak()[0], 4)}
         del u, g
     del mesh

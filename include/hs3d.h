@@ -58,8 +58,25 @@ enum { HS3D_EULER = 0, HS3D_NS = 1 };
 /* surface (Riemann) flux, Sec. 3.3: Lax-Friedrichs, Roe, central
  * (entropy-conservative Chandrashekar flux, no dissipation) */
 enum { HS3D_FLUX_LF = 0, HS3D_FLUX_ROE = 1, HS3D_FLUX_EC = 2 };
-/* volume term: standard DGSEM or Chandrashekar split form (Sec. 3.5) */
-enum { HS3D_VOL_STANDARD = 0, HS3D_VOL_EC = 1 };
+/* volume term (Sec. 3.5): standard DGSEM, or a split form written as flux
+ * differencing with a symmetric two-point flux F#(u_i, u_m).(Ja_i + Ja_m):
+ *   EC         Chandrashekar's entropy-conservative, kinetic-energy-preserving flux
+ *   KG         Kennedy-Gruber:  {rho}{v_a}, {rho}{v_a}{v} + {p}a, {rho}{v_a}{e} + {p}{v_a}
+ *   PIROZZOLI  Pirozzoli:       as KG for mass and momentum, energy {rho}{v_a}{h}
+ *   DUCROS     Ducros et al.:   {rho}{v_a}, {rho v}{v_a} + {p}a, {rho e + p}{v_a}
+ * ({.} arithmetic mean of the two nodes, v_a = v.a, e = (rho e)/rho,
+ * h = (rho e + p)/rho) */
+enum {
+    HS3D_VOL_STANDARD = 0,
+    HS3D_VOL_EC = 1,
+    HS3D_VOL_KG = 2,
+    HS3D_VOL_PIROZZOLI = 3,
+    HS3D_VOL_DUCROS = 4
+};
+/* explicit low-storage time integrator (Sec. 3.7): Williamson's three-stage
+ * third-order scheme, or Carpenter and Kennedy's five-stage fourth-order
+ * 2N-storage scheme (NASA TM 109112, 1994) */
+enum { HS3D_TIME_RK3 = 0, HS3D_TIME_RK4 = 1 };
 /* arithmetic: all FP64; or FP32 flux arithmetic with FP64 state, geometry,
  * primitive-variable conversion and RK accumulation */
 enum { HS3D_FP64 = 0, HS3D_MIXED32 = 1 };
@@ -87,13 +104,16 @@ typedef struct {
 /* Solver configuration.  gamma: ratio of specific heats; Re, Pr: Reynolds and
  * Prandtl numbers (mu = 1/Re, kappa = mu gamma/((gamma-1) Pr), gas constant
  * 1, temperature T = p/rho); Ma: used only by initial conditions; cfl: the
- * convective CFL number of the time-step rule. */
+ * convective CFL number of the time-step rule; time_scheme: HS3D_TIME_RK3
+ * or HS3D_TIME_RK4, the integrator of hs3d_rk3_step/hs3d_rk3_run and of the
+ * server (a zero-initialised struct selects RK3). */
 typedef struct {
     int physics;
     int surface_flux;
     int volume_form;
     int precision;
     double gamma, Re, Pr, Ma, cfl;
+    int time_scheme;
 } hs3d_solver_cfg;
 
 /* Initial condition.  VORTEX: isentropic vortex of strength beta centred at
@@ -133,9 +153,12 @@ hs3d_status hs3d_init_state(const hs3d_mesh *mesh, const hs3d_ic *ic, double *u,
 hs3d_status hs3d_residual(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, const double *u, double *dudt,
                           void *stream);
 
-/* One Williamson low-storage RK3 step (Sec. 3.7): per stage k,
+/* One low-storage Runge-Kutta step (Sec. 3.7) of the scheme cfg->time_scheme
+ * names: per stage k,
  *   g <- A_k g + dt R(u),  u <- u + B_k g,
- * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  u and g: device
+ * Williamson RK3: A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15);
+ * Carpenter-Kennedy RK4: five stages with their published A_k, B_k.
+ * (The name keeps "rk3" for the default scheme.)  u and g: device
  * [E][5][n3], updated in place (g need not be initialised).  dt > 0 is used
  * as given; dt <= 0 computes dt on the device from the state at the start of
  * the step:
@@ -145,7 +168,7 @@ hs3d_status hs3d_residual(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, con
 hs3d_status hs3d_rk3_step(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
                           void *stream);
 
-/* nsteps RK3 steps as hs3d_rk3_step, replayed from a CUDA graph captured on
+/* nsteps steps as hs3d_rk3_step, replayed from a CUDA graph captured on
  * the first call for this (mesh, cfg, u, g, dt) (re-captured when any of them
  * changes).  Stream-ordered. */
 hs3d_status hs3d_rk3_run(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
@@ -207,7 +230,7 @@ hs3d_status hs3d_autotune(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, int
  * between the kernels on `stream`; waits for the step and writes the device
  * time in milliseconds to the HOST array ms_out[5]: [0] dt rule (maxima +
  * finalize), [1] BR1 gradient kernels, [2] face kernels, [3] element
- * (volume + lift + RK) kernels, each summed over the three stages, [4] the
+ * (volume + lift + RK) kernels, each summed over the stages, [4] the
  * whole step.  Not part of the method; used to attribute time to kernels. */
 hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g,
                                    double dt, double *ms_out, void *stream);

@@ -22,13 +22,15 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -
                 -5: "NONPHYSICAL", -6: "UNSUPPORTED"}
 EULER, NS = 0, 1
 FLUX_LF, FLUX_ROE, FLUX_EC = 0, 1, 2
-VOL_STANDARD, VOL_EC = 0, 1
+VOL_STANDARD, VOL_EC, VOL_KG, VOL_PIROZZOLI, VOL_DUCROS = 0, 1, 2, 3, 4
+TIME_RK3, TIME_RK4 = 0, 1
 FP64, MIXED32 = 0, 1
 IC_VORTEX, IC_TGV = 0, 1
 
 PHYSICS = {"euler": EULER, "ns": NS}
 SURFACE = {"lf": FLUX_LF, "roe": FLUX_ROE, "ec": FLUX_EC}
-VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC}
+VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC, "kg": VOL_KG, "pirozzoli": VOL_PIROZZOLI, "ducros": VOL_DUCROS}
+TIME = {"rk3": TIME_RK3, "rk4": TIME_RK4}
 PRECISION = {"fp64": FP64, "mixed32": MIXED32}
 
 # every entry point declared in include/hs3d.h
@@ -54,7 +56,7 @@ class MeshDesc(C.Structure):
 class SolverCfg(C.Structure):
     _fields_ = [("physics", C.c_int), ("surface_flux", C.c_int), ("volume_form", C.c_int), ("precision", C.c_int),
                 ("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double), ("Ma", C.c_double),
-                ("cfl", C.c_double)]
+                ("cfl", C.c_double), ("time_scheme", C.c_int)]
 
 
 class IC(C.Structure):
@@ -147,9 +149,9 @@ def _ptr(t, name="tensor"):
 
 
 def solver_cfg(physics="euler", surface="lf", volume="standard", precision="fp64", gamma=1.4, Re=1600.0,
-               Pr=0.72, Ma=0.1, cfl=0.5) -> SolverCfg:
+               Pr=0.72, Ma=0.1, cfl=0.5, time="rk3") -> SolverCfg:
     return SolverCfg(PHYSICS[physics], SURFACE[surface], VOLUME[volume], PRECISION[precision],
-                     gamma, Re, Pr, Ma, cfl)
+                     gamma, Re, Pr, Ma, cfl, TIME[time])
 
 
 def mesh_desc(ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None) -> MeshDesc:

@@ -44,8 +44,10 @@ hs3d_status validate_cfg(const hs3d_solver_cfg *c)
     if (c->physics != HS3D_EULER && c->physics != HS3D_NS) return fail(HS3D_ERR_INVALID, "bad physics %d", c->physics);
     if (c->surface_flux < HS3D_FLUX_LF || c->surface_flux > HS3D_FLUX_EC)
         return fail(HS3D_ERR_INVALID, "bad surface_flux %d", c->surface_flux);
-    if (c->volume_form != HS3D_VOL_STANDARD && c->volume_form != HS3D_VOL_EC)
+    if (c->volume_form < HS3D_VOL_STANDARD || c->volume_form > HS3D_VOL_DUCROS)
         return fail(HS3D_ERR_INVALID, "bad volume_form %d", c->volume_form);
+    if (c->time_scheme != HS3D_TIME_RK3 && c->time_scheme != HS3D_TIME_RK4)
+        return fail(HS3D_ERR_INVALID, "bad time_scheme %d", c->time_scheme);
     if (c->precision != HS3D_FP64 && c->precision != HS3D_MIXED32)
         return fail(HS3D_ERR_UNSUPPORTED, "unsupported precision %d", c->precision);
     if (!(c->gamma > 1.0)) return fail(HS3D_ERR_INVALID, "gamma must be > 1");
@@ -242,11 +244,11 @@ cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int s
     cudaError_t e = cudaSuccess;
     if (c->physics == HS3D_NS) e = launch_grad(N, c->precision, b, s);
     if (e == cudaSuccess) e = launch_face(N, c->precision, c->physics, c->surface_flux, b, s);
-    if (e == cudaSuccess) e = launch_volume(N, c->precision, c->physics, c->volume_form, b, stage, lam_slot, s);
+    if (e == cudaSuccess) e = launch_volume(N, c->precision, c->physics, c->volume_form, c->time_scheme, b, stage, lam_slot, s);
     return e;
 }
 
-// One RK3 step of a batch.  The dt maxima come from clock slot 0 filled by a
+// One low-storage RK step (scheme c->time_scheme) of a batch.  The dt maxima come from clock slot 0 filled by a
 // fresh k_lambda pass (fresh_lambda != 0, a single step on a state the caller
 // may have changed), or from slot 1, filled by the previous step's last
 // stage (or by prime_lambda before the first step of a run).  The last stage
@@ -259,7 +261,8 @@ cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt
     if (fresh_lambda && !(dt > 0.0)) e = launch_lambda(N, c->precision, c->physics, b, 0, s);
     else if (fresh_lambda && c->precision == HS3D_MIXED32) e = launch_shadow(N, b, s);
     if (e == cudaSuccess) e = launch_dt_finalize(N, b, 0, slot, s);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = enqueue_stage(N, c, b, k, k == 2 ? 1 : -1, s);
+    const int ns = rk_stages(c->time_scheme);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) e = enqueue_stage(N, c, b, k, k == ns - 1 ? 1 : -1, s);
     return e;
 }
 
@@ -373,7 +376,11 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
     if (nsteps < 0) return fail(HS3D_ERR_INVALID, "nsteps < 0");
     if (nsteps == 0) return HS3D_OK;
     std::lock_guard<std::mutex> lock(m->mu);
-    bool same = m->gexec && m->g_u == u && m->g_g == g && m->g_dt == dt && memcmp(&m->g_cfg, c, sizeof *c) == 0;
+    const hs3d_solver_cfg &k = m->g_cfg;   // field-wise: the struct has padding
+    bool same = m->gexec && m->g_u == u && m->g_g == g && m->g_dt == dt && k.physics == c->physics &&
+                k.surface_flux == c->surface_flux && k.volume_form == c->volume_form &&
+                k.precision == c->precision && k.gamma == c->gamma && k.Re == c->Re && k.Pr == c->Pr &&
+                k.Ma == c->Ma && k.cfl == c->cfl && k.time_scheme == c->time_scheme;
     cudaError_t e = cudaSuccess;
     if (!same) {
         if (m->gexec) {

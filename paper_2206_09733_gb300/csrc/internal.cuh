@@ -173,6 +173,47 @@ __device__ __forceinline__ void warp_max_to_clock(unsigned long long *dst_c, uns
     }
 }
 
+// Asynchronous global->shared copies (cp.async, sm_80+): the copies are
+// issued without staging through registers and waited for once.
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Copy `count` contiguous values of type R from global to shared memory with
+// the widest cp.async both addresses allow (16 bytes when the byte count and
+// both addresses are multiples of 16), spread over `nthreads` threads.
+template <typename R>
+__device__ __forceinline__ void cp_async_block(R *dst, const R *src, int count, int tid, int nthreads)
+{
+    const int bytes = count * (int)sizeof(R);
+    if ((bytes & 15) == 0 && (((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+        const int chunks = bytes >> 4;
+        for (int c = tid; c < chunks; c += nthreads)
+            cp_async_16((char *)dst + 16 * c, (const char *)src + 16 * c);
+    } else {
+        for (int c = tid; c < count; c += nthreads) {
+            if (sizeof(R) == 8) cp_async_8(dst + c, src + c);
+            else cp_async_4(dst + c, src + c);
+        }
+    }
+}
+
 // Element neighbour across direction d (+1 side), periodic.
 __device__ __forceinline__ int nbr_plus(int e, int d, int ex, int ey, int ez)
 {
@@ -205,10 +246,13 @@ cudaError_t launch_shadow(int N, const Batch &b, cudaStream_t s);
 cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, int slot, cudaStream_t s);
 cudaError_t launch_grad(int N, int prec, const Batch &b, cudaStream_t s);
 cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, cudaStream_t s);
-// stage -1: residual into out; 0..2: RK stage; lam_slot >= 0 (stage 2 only): also accumulate the
-// dt maxima of the updated state into that clock slot
-cudaError_t launch_volume(int N, int prec, int physics, int form, const Batch &b, int stage, int lam_slot,
+// stage -1: residual into out; 0..rk_stages(scheme)-1: RK stage of `scheme`; lam_slot >= 0 (last
+// stage only): also accumulate the dt maxima of the updated state into that clock slot
+cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, const Batch &b, int stage, int lam_slot,
                           cudaStream_t s);
+// Low-storage RK schemes (HS3D_TIME_*): stage count and the stage's (A_k, B_k).
+int rk_stages(int scheme);
+void rk_coeffs(int scheme, int k, double *A, double *B);
 cudaError_t launch_diagnostics(int N, const Item &it, const double *dudt, double *partials, int nblocks, double *out,
                                cudaStream_t s);
 int diagnostics_blocks(int N, int E);

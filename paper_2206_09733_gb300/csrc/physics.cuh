@@ -6,10 +6,13 @@
 //   viscous flux with tau = mu(grad v + grad v^T) - 2/3 mu I div v and the
 //   heat flux kappa grad T                                             (Sec. 3.2, Eq. viscousfluxes)
 //   surface fluxes Lax-Friedrichs, Roe, central EC (Sec. 3.3 list)
-//   Chandrashekar two-point flux (Sec. 3.5)
+//   two-point fluxes of the split forms (Sec. 3.5): Chandrashekar,
+//   Kennedy-Gruber, Pirozzoli, Ducros
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "../../include/hs3d.h"
 
 namespace hs3d {
 
@@ -310,6 +313,79 @@ __device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr,
     f[2] = fm * m2 + pt * a2;
     f[3] = fm * m3 + pt * a3;
     f[4] = fm * (hg * ibeta_ln - (R)0.5 * v2) + m1 * f[1] + m2 * f[2] + m3 * f[3];
+}
+
+// ------------------------------------------------------------------ split forms
+//
+// Per-node inputs of the two-point fluxes, kSplitSlots values per node:
+//   EC         rho, v1, v2, v3, beta = rho/(2p), ln rho, ln beta
+//   KG         rho, v1, v2, v3, p, e = (rho e)/rho
+//   PIROZZOLI  rho, v1, v2, v3, p, h = (rho e + p)/rho
+//   DUCROS     rho, v1, v2, v3, p, rho e + p
+// (the average-product forms leave the seventh slot unused).
+constexpr int kSplitSlots = 7;
+
+template <int FORM, typename R>
+__device__ __forceinline__ void split_node(const Prim<R> &q, R z[kSplitSlots])
+{
+    z[0] = q.rho;
+    z[1] = q.v1;
+    z[2] = q.v2;
+    z[3] = q.v3;
+    if constexpr (FORM == HS3D_VOL_EC) {
+        const ECNode<R> c = ec_node(q);
+        z[4] = c.beta;
+        z[5] = c.lrho;
+        z[6] = c.lbeta;
+    } else {
+        z[4] = q.p;
+        if constexpr (FORM == HS3D_VOL_KG) z[5] = q.E / q.rho;
+        else if constexpr (FORM == HS3D_VOL_PIROZZOLI) z[5] = (q.E + q.p) / q.rho;
+        else z[5] = q.E + q.p;
+        z[6] = (R)0;
+    }
+}
+
+// Average-product two-point fluxes dotted with a = (a1, a2, a3), {x} = (x_L + x_R)/2,
+// v_a = v.a, m = {rho}{v_a}:
+//   KG         (m, m{v} + {p}a, m{e} + {p}{v_a})
+//   PIROZZOLI  (m, m{v} + {p}a, m{h})
+//   DUCROS     ({rho}{v_a}, {rho v}{v_a} + {p}a, {rho e + p}{v_a})
+template <int FORM, typename R>
+__device__ __forceinline__ void flux_avg_product(const R *L, const R *Rr, R a1, R a2, R a3, R f[5])
+{
+    const R h = (R)0.5;
+    const R vaL = L[1] * a1 + L[2] * a2 + L[3] * a3;
+    const R vaR = Rr[1] * a1 + Rr[2] * a2 + Rr[3] * a3;
+    const R va = h * (vaL + vaR);
+    const R rho = h * (L[0] + Rr[0]);
+    const R pav = h * (L[4] + Rr[4]);
+    const R m = rho * va;
+    f[0] = m;
+    if constexpr (FORM == HS3D_VOL_DUCROS) {
+        f[1] = h * (L[0] * L[1] + Rr[0] * Rr[1]) * va + pav * a1;
+        f[2] = h * (L[0] * L[2] + Rr[0] * Rr[2]) * va + pav * a2;
+        f[3] = h * (L[0] * L[3] + Rr[0] * Rr[3]) * va + pav * a3;
+        f[4] = h * (L[5] + Rr[5]) * va;
+    } else {
+        f[1] = m * (h * (L[1] + Rr[1])) + pav * a1;
+        f[2] = m * (h * (L[2] + Rr[2])) + pav * a2;
+        f[3] = m * (h * (L[3] + Rr[3])) + pav * a3;
+        if constexpr (FORM == HS3D_VOL_KG) f[4] = m * (h * (L[5] + Rr[5])) + pav * va;
+        else f[4] = m * (h * (L[5] + Rr[5]));
+    }
+}
+
+template <int FORM, typename R>
+__device__ __forceinline__ void split_pair(const R *L, const R *Rr, R hg, R a1, R a2, R a3, R f[5])
+{
+    if constexpr (FORM == HS3D_VOL_EC) {
+        const ECNode<R> zl = {L[0], L[1], L[2], L[3], L[4], L[5], L[6]};
+        const ECNode<R> zr = {Rr[0], Rr[1], Rr[2], Rr[3], Rr[4], Rr[5], Rr[6]};
+        flux_ec(zl, zr, hg, a1, a2, a3, f);
+    } else {
+        flux_avg_product<FORM>(L, Rr, a1, a2, a3, f);
+    }
 }
 
 }  // namespace hs3d

@@ -1,4 +1,4 @@
-// Instrumentation entry points: per-kernel timing of one RK3 step and
+// Instrumentation entry points: per-kernel timing of one RK step and
 // FMA-chain measurements of the FP64 / FP32 arithmetic peaks.
 #include <string.h>
 
@@ -112,7 +112,8 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
     if (st != HS3D_OK) return st;
     if (!u || !g || u == g) return fail(HS3D_ERR_INVALID, "bad u/g");
     cudaStream_t s = (cudaStream_t)stream;
-    const int NEV = 12;
+    const int ns = rk_stages(c->time_scheme);
+    const int NEV = 2 + 3 * 5;
     cudaEvent_t ev[NEV];
     for (int k = 0; k < NEV; ++k) cudaEventCreate(&ev[k]);
     Batch b = single_batch(make_item(m, c, u, g, nullptr));
@@ -123,13 +124,14 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
     if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 0, 0, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     int k = 2;
-    for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+    for (int stage = 0; stage < ns && e == cudaSuccess; ++stage) {
         if (c->physics == HS3D_NS) e = launch_grad(m->N, c->precision, b, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
         if (e == cudaSuccess) e = launch_face(m->N, c->precision, c->physics, c->surface_flux, b, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
         if (e == cudaSuccess)
-            e = launch_volume(m->N, c->precision, c->physics, c->volume_form, b, stage, stage == 2 ? 1 : -1, s);
+            e = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, stage,
+                              stage == ns - 1 ? 1 : -1, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[k++], s);
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[k - 1]);
@@ -138,7 +140,7 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
         memset(ms_out, 0, sizeof(double) * 5);
         cudaEventElapsedTime(&t, ev[0], ev[1]);
         ms_out[0] = t;
-        for (int stage = 0; stage < 3; ++stage) {
+        for (int stage = 0; stage < ns; ++stage) {
             for (int part = 0; part < 3; ++part) {
                 cudaEventElapsedTime(&t, ev[1 + stage * 3 + part], ev[2 + stage * 3 + part]);
                 ms_out[1 + part] += t;

@@ -5,7 +5,7 @@
 //      build the request's mesh, allocate its state, evaluate its initial
 //      condition and arm its clock (t_final or n_steps);
 //   2. group the running requests by (N, physics, surface flux, volume form,
-//      precision) and advance every group by one RK3 step with shared
+//      precision, time scheme) and advance every group by one RK step with shared
 //      launches: each kernel walks a table of items (one per request), so one
 //      launch covers all requests of a group;
 //   3. gather the clocks of all running requests into one small array, copy
@@ -180,12 +180,12 @@ static void finish(hs3d_server *S, ServerReq *r, hs3d_status st, const ClockView
     S->finished++;
 }
 
-typedef std::tuple<int, int, int, int, int> BucketKey;
+typedef std::tuple<int, int, int, int, int, int> BucketKey;
 
 static BucketKey key_of(const ServerReq *r)
 {
     const hs3d_solver_cfg &c = r->req.cfg;
-    return BucketKey(r->req.mesh.N, c.physics, c.surface_flux, c.volume_form, c.precision);
+    return BucketKey(r->req.mesh.N, c.physics, c.surface_flux, c.volume_form, c.precision, c.time_scheme);
 }
 
 static cudaError_t ensure_capacity(hs3d_server *S, int n)
@@ -216,7 +216,7 @@ static cudaError_t ensure_capacity(hs3d_server *S, int n)
     return cudaSuccess;
 }
 
-// One RK3 step for every running request, grouped into shared launches, then
+// One RK step for every running request, grouped into shared launches, then
 // the clocks of all running requests land in S->h_clk (in `running` order).
 static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
 {

@@ -89,11 +89,11 @@ static float time_kernels(hs3d_mesh *m, const hs3d_solver_cfg *c, const Batch &b
     err = cudaSuccess;
     // one untimed launch (also surfaces launch errors for this shape)
     if (which == 0) err = launch_grad(m->N, c->precision, b, s);
-    else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, b, -1, -1, s);
+    else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, -1, -1, s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int r = 0; r < reps && err == cudaSuccess; ++r) {
         if (which == 0) err = launch_grad(m->N, c->precision, b, s);
-        else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, b, -1, -1, s);
+        else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, -1, -1, s);
     }
     if (err == cudaSuccess) err = cudaEventRecord(e1, s);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);

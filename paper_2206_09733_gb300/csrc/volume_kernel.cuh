@@ -1,0 +1,477 @@
+// Element kernel: volume term + surface lifting + Jacobian scaling + RK stage.
+// (Template shared by the per-volume-form translation units volume_*.cu.)
+//
+// Strong form of Eq. NS5 (Sec. 3.3) on Gauss-Lobatto nodes, per element:
+//   du/dt = -(V + S)/J
+//   standard form   V = sum_d D_d F~^d,   F~^d = Ja^d . (F_e - F_v)
+//   split form      V = sum_d sum_m D_im F#(u_i, u_m).(Ja^d_i + Ja^d_m) - sum_d D_d (Ja^d . F_v)
+//                   with a symmetric two-point flux F# (Sec. 3.5): Chandrashekar,
+//                   Kennedy-Gruber, Pirozzoli or Ducros
+//   surface         S = (1/w_end) (F^* - F~^d_in) on the +d face, (1/w_0)(-F^* + F~^d_in) on the -d face
+//                   F^* the face flux computed once per face by k_face
+// followed either by the residual store or by one low-storage RK stage
+// (Sec. 3.7) g <- A_k g + dt R, u <- u + B_k g in FP64, with the stage's A_k,
+// B_k passed by the host (Williamson RK3 or Carpenter-Kennedy RK4).  After
+// the last stage the kernel also reduces the dt maxima of the updated state (the time
+// step rule's input for the next step) so that no separate pass over the
+// state is needed between steps.
+//
+// One thread per node, `epb` elements per CTA.  The element's contravariant
+// fluxes (standard form) or its per-node two-point-flux inputs (split form)
+// are staged in shared memory; the six face-flux blocks of the element are
+// loaded into shared memory by all of its threads at the start (contiguous
+// 5n^2 chunks), so the surface term reads no global memory after the
+// contraction.
+#pragma once
+
+#include "internal.cuh"
+#include "physics.cuh"
+
+namespace hs3d {
+
+template <int N>
+constexpr int vol_threads()
+{
+    return ((N + 1) * (N + 1) * (N + 1) > 256) ? (N + 1) * (N + 1) * (N + 1) : 256;
+}
+
+// Minimum resident CTAs per SM asked of the compiler: the mixed path is
+// latency bound, so its register budget is capped (64 per thread with
+// 256- or 512-thread CTAs) to keep more warps resident; the FP64 path is
+// bound by the FP64 pipe and keeps its registers.
+template <int N, typename R>
+constexpr int vol_min_blocks()
+{
+    return sizeof(R) == 4 ? (((N + 1) * (N + 1) * (N + 1) <= 256) ? 4 : 2) : 1;
+}
+
+// Number of R values staged per node.
+template <int FORM, bool NS>
+constexpr int vol_smem_per_node()
+{
+    return FORM == HS3D_VOL_STANDARD ? 15 : (16 + (NS ? 15 : 0));
+}
+
+// Node with index `idx` along direction d on the line with tangential indices (ta, tb).
+template <int n>
+__device__ __forceinline__ int line_node(int d, int idx, int ta, int tb)
+{
+    if (d == 0) return idx + n * (ta + n * tb);
+    if (d == 1) return ta + n * (idx + n * tb);
+    return ta + n * (tb + n * idx);
+}
+
+template <typename R>
+__device__ __forceinline__ const R *metric_ptr(const Item &it);
+template <>
+__device__ __forceinline__ const double *metric_ptr<double>(const Item &it) { return it.Ja; }
+template <>
+__device__ __forceinline__ const float *metric_ptr<float>(const Item &it) { return it.Jaf; }
+
+template <int N, typename R, bool NS, int FORM>
+__global__ void __launch_bounds__(vol_threads<N>(), vol_min_blocks<N, R>())
+k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB, int lam_slot)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr int PER = vol_smem_per_node<FORM, NS>();
+    constexpr int FACEVALS = 6 * 5 * n2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sD = (R *)smem_raw;
+    const int epb = blockDim.x / n3;
+    R *sbuf = sD + ((n * n + 1) & ~1);
+    R *sface = sbuf + (size_t)epb * PER * n3;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
+    const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
+    const long long ge = blockIdx.x * (long long)epb + le;
+    bool valid = ge < b.total_elems;
+    const Item *itp = nullptr;
+    int e = 0;
+    if (valid) {
+        itp = &find_item_elem(b, ge);
+        e = (int)(ge - itp->elem_begin);
+        if (itp->clk && itp->clk->done) valid = false;
+    }
+    R *S = sbuf + (size_t)le * PER * n3;
+    R *F6 = sface + (size_t)le * FACEVALS;
+    const int ijk[3] = {p % n, (p / n) % n, p / n2};
+
+    double u[5];
+    R V[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+    const R iw = ops_iw0<R>(ops);
+    Prim<R> q;   // kept across the barrier: the surface term recomputes the own flux from it
+    if (valid) {
+        const Item &it = *itp;
+        // the six face-flux blocks of this element (slot 2d+1: the +d face,
+        // own index; slot 2d: the -d face, owned by the -d neighbour) go to
+        // shared memory by asynchronous copies, waited for before the barrier
+        if constexpr (sizeof(R) == 4) {
+            const R *FS = (const R *)it.fstar;
+#pragma unroll
+            for (int slot = 0; slot < 6; ++slot) {
+                const int d = slot >> 1;
+                const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
+                cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
+            }
+        }
+        const size_t node = (size_t)e * 5 * n3 + p;
+        const Phys<R> P = phys_of<R>(it);
+        R ja[9];
+        const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ja[k] = JA[k * n3];
+        if constexpr (sizeof(R) == 8) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = it.u[node + v * n3];
+            q = prim_from_u<R>(u, P.gm1);
+        } else {
+            // the FP32 shadow carries exactly the rounded state the fluxes use
+            float us[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) us[v] = it.uf[node + v * n3];
+            q = prim_from_f(us, P.gm1);
+        }
+        R G[12];
+        if (NS) {
+            const R *Gp = (const R *)it.grad + (size_t)e * 12 * n3 + p;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) G[k] = Gp[k * n3];
+        }
+        if constexpr (sizeof(R) == 8) {   // (the mixed path issued its face copies above)
+            const R *FS = (const R *)it.fstar;
+#pragma unroll
+            for (int slot = 0; slot < 6; ++slot) {
+                const int d = slot >> 1;
+                const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
+                cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
+            }
+        }
+        // contravariant fluxes at this node; for the split form the diagonal
+        // two-point term F#(u_i,u_i).(2 Ja_i) = 2 Ja_i.F_e(u_i) goes straight
+        // into V so that no flux is held across the barrier
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            R fe[5], fv[5] = {(R)0, (R)0, (R)0, (R)0, (R)0};
+            euler_flux(q, q.E, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fe);
+            if (NS) visc_flux(q, G, P.mu, P.kappa, ja[d * 3], ja[d * 3 + 1], ja[d * 3 + 2], fv);
+            R own[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) own[v] = NS ? fe[v] - fv[v] : fe[v];
+            if (FORM == HS3D_VOL_STANDARD) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) S[(d * 5 + v) * n3 + p] = own[v];
+            } else {
+                const R dii = (R)2 * ops_D<R>(ops, ijk[d] * n + ijk[d]);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += dii * fe[v];
+                if (NS) {
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) S[(16 + d * 5 + v) * n3 + p] = fv[v];
+                }
+            }
+        }
+        if (FORM != HS3D_VOL_STANDARD) {
+            R z[kSplitSlots];
+            split_node<FORM>(q, z);
+#pragma unroll
+            for (int k = 0; k < kSplitSlots; ++k) S[k * n3 + p] = z[k];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) S[(7 + k) * n3 + p] = ja[k];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    double lc = 0.0, lv = 0.0;
+    bool lam_active = false;
+    if (FORM == HS3D_VOL_STANDARD) {
+        if (valid) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+                const int base = p - ijk[d] * stride;
+                const R *Drow = sD + ijk[d] * n;
+#pragma unroll
+                for (int m = 0; m < n; ++m) {
+                    const R Dm = Drow[m];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) V[v] += Dm * S[(d * 5 + v) * n3 + base + m * stride];
+                }
+            }
+        }
+    } else {
+        // Split form.  F#(u_i,u_m).(Ja_i + Ja_m) is symmetric in (i, m), so
+        // each pair of nodes on a line is evaluated once: per direction, the
+        // element's threads share the n^2 * n(n-1)/2 pair fluxes (written to
+        // shared memory), then every node sums D_im times the fluxes of its
+        // line.
+        constexpr int NP = n * (n - 1) / 2;
+        constexpr int W = n2 * NP;
+        R *PB = sface + (size_t)epb * FACEVALS + (size_t)le * 5 * W;
+        const R hg = valid ? phys_of<R>(*itp).hg : (R)0;
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            if (valid) {
+                for (int w = p; w < W; w += n3) {
+                    const int l = w / NP;
+                    int pp = w - l * NP, ia = 0;
+                    while (pp >= n - 1 - ia) {
+                        pp -= n - 1 - ia;
+                        ++ia;
+                    }
+                    const int im = ia + 1 + pp;
+                    const int ta = l % n, tb = l / n;
+                    const int a = line_node<n>(d, ia, ta, tb), c = line_node<n>(d, im, ta, tb);
+                    R za[kSplitSlots], zc[kSplitSlots];
+#pragma unroll
+                    for (int k = 0; k < kSplitSlots; ++k) {
+                        za[k] = S[k * n3 + a];
+                        zc[k] = S[k * n3 + c];
+                    }
+                    const R a1 = S[(7 + d * 3 + 0) * n3 + a] + S[(7 + d * 3 + 0) * n3 + c];
+                    const R a2 = S[(7 + d * 3 + 1) * n3 + a] + S[(7 + d * 3 + 1) * n3 + c];
+                    const R a3 = S[(7 + d * 3 + 2) * n3 + a] + S[(7 + d * 3 + 2) * n3 + c];
+                    R fs[5];
+                    split_pair<FORM>(za, zc, hg, a1, a2, a3, fs);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) PB[v * W + w] = fs[v];
+                }
+            }
+            __syncthreads();
+            if (valid) {
+                const int i = ijk[d];
+                const int ta = (d == 0) ? ijk[1] : ijk[0];
+                const int tb = (d == 2) ? ijk[1] : ijk[2];
+                const int l = ta + n * tb;
+                const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
+                const int base = p - i * stride;
+                const R *Drow = sD + i * n;
+#pragma unroll
+                for (int m = 0; m < n; ++m) {
+                    const R Dm = Drow[m];
+                    if (m != i) {
+                        const int lo = m < i ? m : i, hi = m < i ? i : m;
+                        const int w = l * NP + lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) V[v] += Dm * PB[v * W + w];
+                    }
+                    if (NS) {
+                        const int pm = base + m * stride;
+#pragma unroll
+                        for (int v = 1; v < 5; ++v) V[v] -= Dm * S[(16 + d * 5 + v) * n3 + pm];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (valid) {
+        const Item &it = *itp;
+        // surface term (1/w)(F* - own) on the +d face, (1/w)(own - F*) on the
+        // -d face: the difference is formed first (it is small where the large
+        // fluxes nearly cancel), with the own flux Ja^d.(F_e - F_v) re-read
+        // (standard form) or recomputed from the node's state (split form)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (ijk[d] != N && ijk[d] != 0) continue;
+            const int ta = (d == 0) ? ijk[1] : ijk[0];
+            const int tb = (d == 2) ? ijk[1] : ijk[2];
+            const int ab = ta + n * tb;
+            R own[5];
+            if (FORM == HS3D_VOL_STANDARD) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) own[v] = S[(d * 5 + v) * n3 + p];
+            } else {
+                euler_flux(q, q.E, S[(7 + d * 3) * n3 + p], S[(8 + d * 3) * n3 + p], S[(9 + d * 3) * n3 + p], own);
+                if (NS) {
+#pragma unroll
+                    for (int v = 1; v < 5; ++v) own[v] -= S[(16 + d * 5 + v) * n3 + p];
+                }
+            }
+            if (ijk[d] == N) {
+                const R *F = F6 + (2 * d + 1) * 5 * n2 + ab;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += iw * (F[v * n2] - own[v]);
+            } else {
+                const R *F = F6 + (2 * d) * 5 * n2 + ab;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) V[v] += iw * (own[v] - F[v * n2]);
+            }
+        }
+        if constexpr (sizeof(R) == 4) {
+            // the FP64 state is needed only for the RK accumulation
+            if (stage >= 0) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) u[v] = it.u[(size_t)e * 5 * n3 + p + v * n3];
+            }
+        }
+
+        float nf[5];   // mixed path: FP32 shadow of the updated state
+        if constexpr (sizeof(R) == 8) {
+            const double ij = it.invJ[(size_t)e * n3 + p];
+            if (stage < 0) {
+                double *O = it.out + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
+            } else {
+                const double dt = it.clk->dt;
+                const double A = rkA, B = rkB;
+                double *Gp = it.g + (size_t)e * 5 * n3 + p;
+                double *Up = it.u + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    const double r = -(double)V[v] * ij;
+                    const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
+                    Gp[v * n3] = gv;
+                    u[v] = u[v] + B * gv;
+                    Up[v * n3] = u[v];
+                }
+            }
+        } else {
+            // mixed path: the increment dt R = -dt V / J is formed in FP32 and
+            // widened exactly; the register and the state accumulate in FP64
+            // (two FP64 FMAs per variable).
+            const float ijf = it.invJf[(size_t)e * n3 + p];
+            if (stage < 0) {
+                double *O = it.out + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) O[v * n3] = f2d_exact(-(float)V[v] * ijf);
+            } else {
+                const float sdt = d2f_rn(it.clk->dt) * ijf;
+                const double A = rkA, B = rkB;
+                double *Gp = it.g + (size_t)e * 5 * n3 + p;
+                double *Up = it.u + (size_t)e * 5 * n3 + p;
+                float *Sp = it.uf + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    const double inc = f2d_exact(-(float)V[v] * sdt);
+                    const double gv = (stage == 0) ? inc : fma(A, Gp[v * n3], inc);
+                    Gp[v * n3] = gv;
+                    u[v] = fma(B, gv, u[v]);
+                    Up[v * n3] = u[v];
+                    nf[v] = d2f_rn(u[v]);
+                    Sp[v * n3] = nf[v];
+                }
+            }
+        }
+        if (stage >= 0) {
+            if (lam_slot >= 0) {
+                // dt maxima of the updated state (same rule as k_lambda, in R)
+                const Phys<R> P = phys_of<R>(it);
+                Prim<R> qn;
+                if constexpr (sizeof(R) == 8) qn = prim_from_u<R>(u, P.gm1);
+                else qn = prim_from_f(nf, P.gm1);
+                if (!(qn.rho > (R)0) || !(qn.p > (R)0)) {
+                    it.clk->bad = 1;
+                } else {
+                    const R c = sqrt(P.gamma * qn.p / qn.rho);
+                    R iJ;
+                    if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
+                    else iJ = it.invJf[(size_t)e * n3 + p];
+                    R sc = (R)0, sv = (R)0;
+                    const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const R a1 = JA[(d * 3) * n3], a2 = JA[(d * 3 + 1) * n3], a3 = JA[(d * 3 + 2) * n3];
+                        const R an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
+                        sc += (fabs(a1 * qn.v1 + a2 * qn.v2 + a3 * qn.v3) + c * an) * iJ;
+                        sv += (an * iJ) * (an * iJ);
+                    }
+                    lc = widen<R>(sc);
+                    lv = NS ? widen<R>(P.mu * sv / qn.rho) : 0.0;
+                    lam_active = true;
+                }
+            }
+        }
+    }
+    if (lam_slot >= 0 && stage >= 0) {
+        unsigned long long *dc = nullptr, *dv = nullptr;
+        if (lam_active) {
+            dc = &itp->clk->lam[lam_slot][0];
+            dv = NS ? &itp->clk->lam[lam_slot][1] : nullptr;
+        }
+        warp_max_to_clock(dc, dv, lc, lv, lam_active);
+    }
+}
+
+// ------------------------------------------------------------------ launch (one volume form)
+
+template <int N, typename R, bool NS, int FORM>
+static cudaError_t vol_launch2(const Batch &b, int stage, double rkA, double rkB, int lam_slot, cudaStream_t s)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;
+    int epb = elems_per_block_p(N, sizeof(R) == 4 ? HS3D_MIXED32 : HS3D_FP64, 1);
+    int threads = epb * n3;
+    if (threads > vol_threads<N>()) {
+        epb = vol_threads<N>() / n3;
+        threads = epb * n3;
+    }
+    const size_t pairs = (FORM != HS3D_VOL_STANDARD) ? (size_t)5 * n2 * (n * (n - 1) / 2) : 0;
+    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 +
+                               (size_t)epb * 30 * n2 + (size_t)epb * pairs);
+    unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
+    const Ops *ops = device_ops(N);
+    if (!ops) return cudaErrorMemoryAllocation;
+    k_volume<N, R, NS, FORM><<<blocks, threads, smem, s>>>(b, ops, stage, rkA, rkB, stage >= 0 ? lam_slot : -1);
+    return cudaGetLastError();
+}
+
+template <int FORM>
+cudaError_t launch_volume_form(int N, int prec, int physics, const Batch &b, int stage, double rkA, double rkB,
+                               int lam_slot, cudaStream_t s)
+{
+    if (b.total_elems == 0) return cudaSuccess;
+#define HS3D_VOLN(K)                                                                                          \
+    case K:                                                                                                   \
+        if (prec == HS3D_FP64)                                                                                \
+            return physics == HS3D_NS ? vol_launch2<K, double, true, FORM>(b, stage, rkA, rkB, lam_slot, s)   \
+                                      : vol_launch2<K, double, false, FORM>(b, stage, rkA, rkB, lam_slot, s); \
+        return physics == HS3D_NS ? vol_launch2<K, float, true, FORM>(b, stage, rkA, rkB, lam_slot, s)        \
+                                  : vol_launch2<K, float, false, FORM>(b, stage, rkA, rkB, lam_slot, s);
+    switch (N) {
+        HS3D_VOLN(1) HS3D_VOLN(2) HS3D_VOLN(3) HS3D_VOLN(4) HS3D_VOLN(5) HS3D_VOLN(6) HS3D_VOLN(7)
+    }
+#undef HS3D_VOLN
+    return cudaErrorInvalidValue;
+}
+
+template <int N, int FORM>
+static cudaError_t prep_vol_n()
+{
+    const int big = 220 * 1024;
+    cudaError_t e = cudaSuccess;
+#define HS3D_ATTR(R, NS)                                                                                      \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(k_volume<N, R, NS, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(k_volume<N, R, NS, FORM>, cudaFuncAttributePreferredSharedMemoryCarveout,    \
+                                 cudaSharedmemCarveoutMaxShared);
+    HS3D_ATTR(double, false)
+    HS3D_ATTR(double, true)
+    HS3D_ATTR(float, false)
+    HS3D_ATTR(float, true)
+#undef HS3D_ATTR
+    return e;
+}
+
+template <int FORM>
+cudaError_t prepare_volume_form(int N)
+{
+    switch (N) {
+        case 1: return prep_vol_n<1, FORM>();
+        case 2: return prep_vol_n<2, FORM>();
+        case 3: return prep_vol_n<3, FORM>();
+        case 4: return prep_vol_n<4, FORM>();
+        case 5: return prep_vol_n<5, FORM>();
+        case 6: return prep_vol_n<6, FORM>();
+        case 7: return prep_vol_n<7, FORM>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Each volume_<form>.cu instantiates the two entry points for its form.
+#define HS3D_VOLUME_FORM_TU(FORM)                                                                               \
+    template cudaError_t launch_volume_form<FORM>(int, int, int, const Batch &, int, double, double, int,        \
+                                                  cudaStream_t);                                                 \
+    template cudaError_t prepare_volume_form<FORM>(int);
+
+}  // namespace hs3d

@@ -6,6 +6,8 @@ validation paths that return before touching the device are exercised.
 import ctypes as C
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -71,8 +73,28 @@ def test_null_arguments_rejected(lib):
     assert lib.hs3d_poll(None, 1, None) in (hs.ERR_INVALID, hs.ERR_UNSUPPORTED)
 
 
-def test_structs_match_header_layout():
-    # sizes of the public structs as laid out by the C compiler on this ABI
-    assert C.sizeof(hs.MeshDesc) == 4 * 4 + 8 * 6 + 4 * 3 + 4 + 8 + 8
-    assert C.sizeof(hs.SolverCfg) == 4 * 4 + 8 * 5
-    assert C.sizeof(hs.IC) == 8 + 8 * 6
+def test_structs_match_header_layout(tmp_path):
+    """Size and field offsets of every public struct as the C compiler lays
+    them out from include/hs3d.h, against the ctypes mirror."""
+    structs = {"hs3d_mesh_desc": hs.MeshDesc, "hs3d_solver_cfg": hs.SolverCfg, "hs3d_ic": hs.IC,
+               "hs3d_request": hs.Request, "hs3d_result": hs.Result}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hs3d.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    gcc = shutil.which("gcc") or pytest.skip("no C compiler")
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = structs[cname]
+        got = C.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(val), (cname, field, got, val)
+        seen += 1
+    assert seen == sum(1 + len(py._fields_) for py in structs.values())

@@ -35,7 +35,8 @@ def _built():
     hs.lib()
 
 
-COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec") for v in ("standard", "ec")]
+COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec")
+          for v in ("standard", "ec", "kg", "pirozzoli", "ducros")]
 
 
 @pytest.mark.parametrize("combo", COMBOS)

@@ -47,9 +47,9 @@ def pair(ex, ey, ez, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=0.0):
     return O.Mesh(ex, ey, ez, N, lo=lo, hi=hi, amp=amp), hs.Mesh(ex, ey, ez, N, lo=lo, hi=hi, amp=amp)
 
 
-def cfgs(physics, surface, volume, precision="fp64", Re=400.0, cfl=0.5):
-    return (O.Cfg(physics, surface, volume, gamma=G, Re=Re, Pr=0.72, cfl=cfl),
-            hs.solver_cfg(physics, surface, volume, precision, gamma=G, Re=Re, Pr=0.72, cfl=cfl))
+def cfgs(physics, surface, volume, precision="fp64", Re=400.0, cfl=0.5, time="rk3"):
+    return (O.Cfg(physics, surface, volume, gamma=G, Re=Re, Pr=0.72, cfl=cfl, time=time),
+            hs.solver_cfg(physics, surface, volume, precision, gamma=G, Re=Re, Pr=0.72, cfl=cfl, time=time))
 
 
 # ------------------------------------------------------------------ geometry and initial conditions
@@ -87,7 +87,8 @@ def test_initial_conditions_match_oracle(kind):
 
 # ------------------------------------------------------------------ residual parity
 
-COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec") for v in ("standard", "ec")]
+VOLUMES = ("standard", "ec", "kg", "pirozzoli", "ducros")
+COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec") for v in VOLUMES]
 
 
 @pytest.mark.parametrize("combo", COMBOS)
@@ -107,7 +108,8 @@ def test_residual_parity_all_schemes(combo):
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
-@pytest.mark.parametrize("combo", [("ns", "roe", "ec"), ("euler", "lf", "standard"), ("ns", "roe", "standard")])
+@pytest.mark.parametrize("combo", [("ns", "roe", "ec"), ("euler", "lf", "standard"), ("ns", "roe", "standard"),
+                                   ("euler", "roe", "kg"), ("ns", "lf", "pirozzoli"), ("euler", "ec", "ducros")])
 def test_residual_parity_every_degree(N, combo):
     om, gm = pair(2, 3, 2, N, amp=0.08)
     u0 = random_state(om.shape, seed=100 + N, smooth=True)
@@ -246,6 +248,43 @@ def test_vortex_10_steps_parity_stable_variants(E, volume):
     assert rel(host(u), uo) < TOL64
 
 
+@pytest.mark.parametrize("volume", ["ec", "kg", "pirozzoli"])
+def test_vortex_rk4_steps_parity(volume):
+    """Carpenter-Kennedy RK4 (five stages) with the kinetic-energy-preserving
+    split forms on the 4^3 vortex: 10 steps, state parity 1e-12, and the
+    same number of steps and simulated time on the device clock."""
+    om, gm = pair(4, 4, 4, 3, lo=(0,) * 3, hi=(10,) * 3, amp=0.05)
+    oc, gc = cfgs("euler", "roe", volume, cfl=0.5, time="rk4")
+    uo = om.ic_vortex(G, 0.5, 5.0)
+    go = np.zeros_like(uo)
+    t = 0.0
+    for _ in range(10):
+        t += om.dt(oc, uo)
+        om.rk3_step(oc, uo, go)
+    u = gm.init_state(gm.empty_state(), "vortex", G, 0.5, 5.0)
+    g = torch.zeros_like(u)
+    gm.clock(reset=True)
+    gm.rk3_run(gc, u, g, 10)
+    assert rel(host(u), uo) < TOL64
+    ts, steps = gm.clock()
+    assert steps == 10 and abs(ts - t) < 1e-13 * t
+
+
+def test_rk4_differs_from_rk3_and_is_deterministic():
+    _, gm = pair(3, 3, 3, 2, amp=0.05)
+    u0 = gm.init_state(gm.empty_state(), "tgv", G, 0.1)
+    outs = []
+    for time in ("rk3", "rk4", "rk4"):
+        _, gc = cfgs("ns", "roe", "kg", time=time)
+        u = u0.clone()
+        g = torch.zeros_like(u)
+        for _ in range(3):
+            gm.rk3_step(gc, u, g, dt=1e-2)
+        outs.append(u)
+    assert torch.equal(outs[1], outs[2])
+    assert not torch.equal(outs[0], outs[1])
+
+
 def test_rk3_run_graph_equals_stepwise():
     _, gm = pair(4, 4, 4, 3, amp=0.05)
     _, gc = cfgs("ns", "roe", "ec")
@@ -258,9 +297,10 @@ def test_rk3_run_graph_equals_stepwise():
     assert torch.equal(u1, u2)
 
 
-def test_tgv_ns_steps_parity_16cubed():
+@pytest.mark.parametrize("volume,time", [("ec", "rk3"), ("kg", "rk4"), ("ducros", "rk3")])
+def test_tgv_ns_steps_parity_16cubed(volume, time):
     om, gm = pair(16, 16, 16, 3, amp=0.05)
-    oc, gc = cfgs("ns", "roe", "ec", Re=1600.0)
+    oc, gc = cfgs("ns", "roe", volume, Re=1600.0, time=time)
     uo = om.ic_tgv(G, 0.1)
     go = np.zeros_like(uo)
     for _ in range(5):

@@ -47,9 +47,9 @@ def wait_all(srv, tickets, limit_s=120.0):
     return out
 
 
-def vortex_request(E, N, xc, yc, beta, Ma, precision="mixed32", volume="ec"):
+def vortex_request(E, N, xc, yc, beta, Ma, precision="mixed32", volume="ec", time="rk3"):
     mesh = hs.mesh_desc(E, E, 1, N, lo=(0, 0, 0), hi=(10, 10, 10.0 / E))
-    cfg = hs.solver_cfg("euler", "lf", volume, precision, cfl=0.5)
+    cfg = hs.solver_cfg("euler", "lf", volume, precision, cfl=0.5, time=time)
     ic = hs.ic_desc("vortex", G, Ma, beta, xc, yc)
     return mesh, cfg, ic
 
@@ -91,6 +91,31 @@ def test_result_same_alone_and_in_mix_and_matches_oracle():
         for _ in range(n_steps):
             om.rk3_step(oc, u, g)
         assert np.linalg.norm(a - u) / np.linalg.norm(u) < 1e-12
+    srv.close()
+
+
+def test_mixed_schemes_share_the_server_and_match_the_oracle():
+    """Requests with different split forms and time integrators run side by
+    side (each group in its own launches) and each matches the oracle."""
+    specs = [("ec", "rk4"), ("kg", "rk3"), ("pirozzoli", "rk4"), ("ducros", "rk3"), ("kg", "rk4")]
+    E, N, n_steps = 4, 3, 5
+    srv = hs.Server()
+    tickets, outs = [], []
+    for volume, time_ in specs:
+        mesh, cfg, ic = vortex_request(E, N, 5.0, 5.0, 2.0, 0.4, precision="fp64", volume=volume, time=time_)
+        out = np.zeros((E * E, 5, N + 1, N + 1, N + 1))
+        tickets.append(srv.submit(mesh, cfg, ic, n_steps=n_steps, result=out))
+        outs.append(out)
+    res = wait_all(srv, tickets)
+    for (volume, time_), t, a in zip(specs, tickets, outs):
+        assert res[t][0] == hs.OK and res[t][1].steps == n_steps
+        om = O.Mesh(E, E, 1, N, lo=(0, 0, 0), hi=(10, 10, 10.0 / E))
+        oc = O.Cfg("euler", "lf", volume, cfl=0.5, time=time_)
+        u = om.ic_vortex(G, 0.4, 2.0, xc=5.0, yc=5.0)
+        g = np.zeros_like(u)
+        for _ in range(n_steps):
+            om.rk3_step(oc, u, g)
+        assert np.linalg.norm(a - u) / np.linalg.norm(u) < 1e-12, (volume, time_)
     srv.close()
 
 

@@ -817,3 +817,23 @@ def test_rk4_fourth_order_on_nonlinear_problem():
     d = [np.linalg.norm(a - b) for a, b in zip(sols, sols[1:])]
     ratios = [a / b for a, b in zip(d, d[1:])]
     assert all(12.0 < r < 20.0 for r in ratios), ratios
+
+
+def _lsrk_amplification(scheme, z, stages):
+    """|y_1| for y' = z y, y_0 = 1, one step of the oracle's low-storage
+    scheme (complex z through the real 2x2 form)."""
+    y, gg = np.array([1.0, 0.0]), np.zeros(2)
+    for k in range(stages):
+        R = np.array([z.real * y[0] - z.imag * y[1], z.imag * y[0] + z.real * y[1]])
+        O.lsrk_stage(scheme, k, 1.0, y, gg, R)
+    return abs(complex(y[0], y[1]))
+
+
+@pytest.mark.parametrize("N", [1, 3, 5, 7])
+def test_dt_rule_is_inside_rk4_stability_region(N):
+    """The same convective rule keeps twice every dt*mu of the 1-D DGSEM
+    operator inside the five-stage scheme's stability region too."""
+    mu = np.linalg.eigvals(_dgsem_advection_1d(N))
+    n = N + 1
+    dt = 0.5 * 8 / (n * n * 2.0)
+    assert max(_lsrk_amplification("rk4", 2 * dt * m, 5) for m in mu) <= 1 + 1e-9
