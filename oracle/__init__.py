@@ -28,8 +28,8 @@ _lock = threading.Lock()
 _lib = None
 
 PHYSICS = {"euler": 0, "ns": 1}
-SURFACE = {"lf": 0, "roe": 1, "ec": 2}
-VOLUME = {"standard": 0, "ec": 1, "kg": 2, "pirozzoli": 3, "ducros": 4}
+SURFACE = {"lf": 0, "roe": 1, "ec": 2, "rusanov": 3, "ldroe": 4, "matrix": 5}
+VOLUME = {"standard": 0, "ec": 1, "kg": 2, "pirozzoli": 3, "ducros": 4, "morinishi": 5, "ir": 6}
 TIME = {"rk3": 0, "rk4": 1}
 
 
@@ -72,7 +72,8 @@ def lib():
             L.orc_mesh_arrays.argtypes = [C.c_void_p] + [C.c_void_p] * 6
             L.orc_neighbour.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
             L.orc_metrics.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
-            for name in ("orc_flux_lf", "orc_flux_roe", "orc_flux_ec"):
+            for name in ("orc_flux_lf", "orc_flux_roe", "orc_flux_ec", "orc_flux_rusanov", "orc_flux_ldroe",
+                         "orc_flux_matrix", "orc_flux_morinishi", "orc_flux_ir"):
                 getattr(L, name).argtypes = [_dp, _dp, _dp, C.c_double, _dp]
             L.orc_flux_roe_signed.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_int]
             L.orc_flux_euler.argtypes = [_dp, _dp, C.c_double, _dp]
@@ -278,9 +279,23 @@ def logmean(a, b):
 
 
 def flux_split(kind, uL, uR, a, gamma=1.4):
-    """Two-point split-form flux: kind "kg", "pirozzoli" or "ducros"."""
+    """Two-point split-form flux: kind "kg", "pirozzoli", "ducros",
+    "morinishi", "ir" (Ismail-Roe) or "ec" (Chandrashekar)."""
     f = np.zeros(5)
-    lib().orc_flux_split(VOLUME[kind], _v(uL), _v(uR), _v(a, 3), gamma, f)
+    if kind == "ec":
+        lib().orc_flux_ec(_v(uL), _v(uR), _v(a, 3), gamma, f)
+    elif kind in ("morinishi", "ir"):
+        getattr(lib(), "orc_flux_" + kind)(_v(uL), _v(uR), _v(a, 3), gamma, f)
+    else:
+        lib().orc_flux_split(VOLUME[kind], _v(uL), _v(uR), _v(a, 3), gamma, f)
+    return f
+
+
+def flux_surface(kind, uL, uR, nh, gamma=1.4):
+    """Surface flux with unit normal nh: "lf", "roe", "rusanov", "ldroe",
+    "matrix" (entropy-stable matrix dissipation) or "ec"."""
+    f = np.zeros(5)
+    getattr(lib(), "orc_flux_" + kind)(_v(uL), _v(uR), _v(nh, 3), gamma, f)
     return f
 
 

@@ -15,9 +15,11 @@
  *     (Sec. 3.3, Eq. compressibleNScompact_transformed)
  *   - weak form with a numerical flux at element faces, Gauss-Lobatto
  *     quadrature (Sec. 3.3, Eqs. NS2-NS5)
- *   - Lax-Friedrichs, Roe and central surface fluxes, BR1 viscous scheme
- *     (Sec. 3.3, list of convective and viscous fluxes)
- *   - Chandrashekar entropy-conservative split form (Sec. 3.5)
+ *   - Lax-Friedrichs, Rusanov, Roe, low-dissipation Roe, matrix-dissipation
+ *     and central surface fluxes, BR1 viscous scheme (Sec. 3.3, list of
+ *     convective and viscous fluxes)
+ *   - split forms: Chandrashekar, Kennedy-Gruber, Pirozzoli, Ducros,
+ *     Morinishi, entropy conserving (Ismail-Roe) (Sec. 3.5)
  *   - entropy S = -rho s, s = ln p - gamma ln rho, w = dS/du (Sec. 4.4,
  *     Eq. shock:entropy)
  *   - Williamson low-storage RK3 (Sec. 3.7)
@@ -40,6 +42,8 @@
 #define NGRAD 4 /* gradient variables q = (v1, v2, v3, T) */
 
 void orc_flux_roe_signed(const double *uL, const double *uR, const double *nh, double g, double *f, int sign_mode);
+void orc_flux_ec(const double *uL, const double *uR, const double *a, double g, double *f);
+double orc_logmean(double a, double b);
 
 /* ------------------------------------------------------------------------ */
 /* 1-D Gauss-Lobatto operators (Sec. 3.3: GL quadrature)                    */
@@ -303,8 +307,10 @@ void orc_mesh_arrays(const orc_mesh *m, double *xi, double *w, double *D, double
 
 typedef struct {
     int physics;       /* 0 Euler, 1 Navier-Stokes */
-    int surface_flux;  /* 0 Lax-Friedrichs, 1 Roe, 2 entropy-conservative (central) */
-    int volume_form;   /* 0 standard; split forms: 1 Chandrashekar, 2 Kennedy-Gruber, 3 Pirozzoli, 4 Ducros */
+    int surface_flux;  /* 0 Lax-Friedrichs, 1 Roe, 2 entropy-conservative (central), 3 Rusanov,
+                          4 low-dissipation Roe, 5 entropy-stable matrix dissipation */
+    int volume_form;   /* 0 standard; split forms: 1 Chandrashekar, 2 Kennedy-Gruber, 3 Pirozzoli, 4 Ducros,
+                          5 Morinishi, 6 Ismail-Roe */
     double gamma, Re, Pr, cfl;
     int time_scheme;   /* 0 Williamson RK3, 1 Carpenter-Kennedy RK4(5) */
 } orc_cfg;
@@ -350,6 +356,94 @@ void orc_flux_lf(const double *uL, const double *uR, const double *nh, double g,
     for (int v = 0; v < NVAR; ++v) f[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (uR[v] - uL[v]);
 }
 
+/* Rusanov flux: as Lax-Friedrichs with the wave-speed bound
+ *   lambda = max(|v_L.nh|, |v_R.nh|) + max(c_L, c_R)
+ * (each side's largest convective and acoustic speeds combined). */
+void orc_flux_rusanov(const double *uL, const double *uR, const double *nh, double g, double *f)
+{
+    double FL[NVAR], FR[NVAR], rL, vL[3], pL, rR, vR[3], pR;
+    orc_flux_euler(uL, nh, g, FL);
+    orc_flux_euler(uR, nh, g, FR);
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double vnL = fabs(vL[0] * nh[0] + vL[1] * nh[1] + vL[2] * nh[2]);
+    double vnR = fabs(vR[0] * nh[0] + vR[1] * nh[1] + vR[2] * nh[2]);
+    double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    double lam = (vnL > vnR ? vnL : vnR) + (cL > cR ? cL : cR);
+    for (int v = 0; v < NVAR; ++v) f[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+/* Entropy variables in the usual normalisation, w = dS'/du for
+ * S' = -rho s / (gamma-1), s = ln p - gamma ln rho:
+ *   w = [(gamma - s)/(gamma-1) - rho|v|^2/(2p), rho v / p, -rho / p]
+ * (the paper's S = -rho s gives (gamma-1) times these). */
+static void entropy_vars_std(const double *u, double g, double *w)
+{
+    double rho, v[3], p;
+    primitives(u, g, &rho, v, &p);
+    double s = log(p) - g * log(rho);
+    w[0] = (g - s) / (g - 1.0) - rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / (2.0 * p);
+    for (int c = 0; c < 3; ++c) w[1 + c] = rho * v[c] / p;
+    w[4] = -rho / p;
+}
+
+/* Entropy-stable flux with matrix dissipation (Winters, Derigs, Gassner and
+ * Walch 2017): the Chandrashekar flux minus a dissipation built from the
+ * scaled eigenvectors of the flux Jacobian in direction nh, applied to the
+ * jump of the entropy variables,
+ *   F* = F_EC(u_L, u_R).nh - (1/2) sum_k |lambda_k| T_k r_k (r_k . [[w]]),
+ * evaluated at the averages
+ *   rho^ = ln-mean(rho), beta^ = ln-mean(beta), beta = rho/(2p),
+ *   p^ = {rho}/(2{beta}), v^ = {v}, v2^ = 2|{v}|^2 - {|v|^2},
+ *   a^ = sqrt(gamma p^/rho^), h^ = gamma/(2(gamma-1) beta^) + v2^/2:
+ *   k = 1, 5: lambda = v^.n -+ a^, r = [1, v^ -+ a^ n, h^ -+ a^ v^.n], T = rho^/(2 gamma)
+ *   k = 2:    lambda = v^.n,       r = [1, v^, v2^/2],                T = rho^ (gamma-1)/gamma
+ *   shear:    lambda = v^.n,       sum over two unit tangents t of r = [0, t, v^.t], T = p^
+ * (the shear pair is summed with the projector I - n n^T, so no tangent
+ * basis is chosen).  For equal states sum_k T_k r_k r_k^T = du/dw, so the
+ * dissipation is |A| du/dw [[w]] ~ |A| [[u]] for small jumps; it is positive
+ * semi-definite in [[w]] for any states, so the flux is entropy stable. */
+void orc_flux_matrix(const double *uL, const double *uR, const double *nh, double g, double *f)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
+    double rho_h = orc_logmean(rL, rR), beta_ln = orc_logmean(bL, bR);
+    double p_h = 0.5 * (rL + rR) / (bL + bR);
+    double v[3], v2av = 0.5 * ((vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]) +
+                               (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]));
+    for (int c = 0; c < 3; ++c) v[c] = 0.5 * (vL[c] + vR[c]);
+    double v2h = 2.0 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) - v2av;
+    double a_h = sqrt(g * p_h / rho_h);
+    double h_h = g / (2.0 * (g - 1.0) * beta_ln) + 0.5 * v2h;
+    double vn = v[0] * nh[0] + v[1] * nh[1] + v[2] * nh[2];
+    double wL[NVAR], wR[NVAR], dw[NVAR];
+    entropy_vars_std(uL, g, wL);
+    entropy_vars_std(uR, g, wR);
+    for (int k = 0; k < NVAR; ++k) dw[k] = wR[k] - wL[k];
+    double r1[NVAR] = {1.0, v[0] - a_h * nh[0], v[1] - a_h * nh[1], v[2] - a_h * nh[2], h_h - a_h * vn};
+    double r2[NVAR] = {1.0, v[0], v[1], v[2], 0.5 * v2h};
+    double r5[NVAR] = {1.0, v[0] + a_h * nh[0], v[1] + a_h * nh[1], v[2] + a_h * nh[2], h_h + a_h * vn};
+    double T15 = rho_h / (2.0 * g), T2 = rho_h * (g - 1.0) / g;
+    double l1 = fabs(vn - a_h), l2 = fabs(vn), l5 = fabs(vn + a_h);
+    double c1 = 0.0, c2 = 0.0, c5 = 0.0;
+    for (int k = 0; k < NVAR; ++k) { c1 += r1[k] * dw[k]; c2 += r2[k] * dw[k]; c5 += r5[k] * dw[k]; }
+    /* shear: q = [[w_m]] + v^ [[w_E]], projected on the face plane */
+    double q[3], qn = 0.0;
+    for (int c = 0; c < 3; ++c) q[c] = dw[1 + c] + v[c] * dw[4];
+    for (int c = 0; c < 3; ++c) qn += q[c] * nh[c];
+    double Pq[3];
+    for (int c = 0; c < 3; ++c) Pq[c] = q[c] - qn * nh[c];
+    double Dsh[NVAR] = {0.0, Pq[0], Pq[1], Pq[2], v[0] * Pq[0] + v[1] * Pq[1] + v[2] * Pq[2]};
+    double fec[NVAR];
+    orc_flux_ec(uL, uR, nh, g, fec);
+    for (int k = 0; k < NVAR; ++k) {
+        double D = l1 * T15 * c1 * r1[k] + l2 * T2 * c2 * r2[k] + l5 * T15 * c5 * r5[k] + l2 * p_h * Dsh[k];
+        f[k] = fec[k] - 0.5 * D;
+    }
+}
+
 /* Roe flux with unit normal nh (Roe 1981; no entropy fix):
  *   F* = (F_L + F_R).nh / 2 - (1/2) sum_k |lambda_k| alpha_k r_k
  * with sqrt(rho)-weighted averages v~, H~, c~^2 = (gamma-1)(H~ - |v~|^2/2),
@@ -359,15 +453,43 @@ void orc_flux_lf(const double *uL, const double *uR, const double *nh, double g,
  *   alpha_2 = drho - dp/c~^2                    r_2 = [1, v~, |v~|^2/2]
  *   shear   = rho~ (dv - dvn n)                 r_s = [0, shear, v~.shear]
  *   alpha_5 = (dp + rho~ c~ dvn)/(2 c~^2)       r_5 = [1, v~ + c~ n, H~ + c~ v~n]. */
+static void roe_flux(const double *uL, const double *uR, const double *nh, double g, double zvel, int sign_mode,
+                     double *f);
+
 void orc_flux_roe(const double *uL, const double *uR, const double *nh, double g, double *f)
 {
-    orc_flux_roe_signed(uL, uR, nh, g, f, 0);
+    roe_flux(uL, uR, nh, g, 1.0, 0, f);
 }
 
 /* sign_mode = 0: the Roe flux above.  sign_mode = 1: f receives the wave sum
  * sum_k lambda_k alpha_k r_k with SIGNED eigenvalues (used by the tests to
  * check Roe's property that it equals F_R.n - F_L.n). */
 void orc_flux_roe_signed(const double *uL, const double *uR, const double *nh, double g, double *f, int sign_mode)
+{
+    roe_flux(uL, uR, nh, g, 1.0, sign_mode, f);
+}
+
+/* Low-dissipation Roe flux (the L2Roe of Osswald et al. 2016): the Roe flux
+ * with the velocity jump in the dissipation (dvn and the shear jump) scaled by
+ *   z = min(1, max(M_L, M_R)),  M = |v| / c,
+ * so that at low Mach numbers the velocity dissipation falls like M while the
+ * density and pressure waves keep Roe's upwinding; identical to Roe for
+ * M >= 1. */
+void orc_flux_ldroe(const double *uL, const double *uR, const double *nh, double g, double *f)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double ML = sqrt(vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]) / sqrt(g * pL / rL);
+    double MR = sqrt(vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]) / sqrt(g * pR / rR);
+    double z = ML > MR ? ML : MR;
+    if (z > 1.0) z = 1.0;
+    roe_flux(uL, uR, nh, g, z, 0, f);
+}
+
+/* Roe flux whose dissipation sees the velocity jump times zvel (1: Roe). */
+static void roe_flux(const double *uL, const double *uR, const double *nh, double g, double zvel, int sign_mode,
+                     double *f)
 {
     double rL, vL[3], pL, rR, vR[3], pR;
     primitives(uL, g, &rL, vL, &pL);
@@ -382,7 +504,7 @@ void orc_flux_roe_signed(const double *uL, const double *uR, const double *nh, d
     double rt = sL * sR;
     double vnt = vt[0] * nh[0] + vt[1] * nh[1] + vt[2] * nh[2];
     double drho = rR - rL, dp = pR - pL;
-    double dv[3] = {vR[0] - vL[0], vR[1] - vL[1], vR[2] - vL[2]};
+    double dv[3] = {zvel * (vR[0] - vL[0]), zvel * (vR[1] - vL[1]), zvel * (vR[2] - vL[2])};
     double dvn = dv[0] * nh[0] + dv[1] * nh[1] + dv[2] * nh[2];
     double a1 = (dp - rt * ct * dvn) / (2.0 * ct * ct);
     double a5 = (dp + rt * ct * dvn) / (2.0 * ct * ct);
@@ -482,10 +604,63 @@ void orc_flux_split(int kind, const double *uL, const double *uR, const double *
     }
 }
 
-/* Two-point volume flux of split form `form` (1..4) dotted with a. */
+/* Morinishi's split form (Morinishi 2010, skew-symmetric convective terms
+ * with the mass flux rho v kept whole), as a two-point flux dotted with a:
+ *   f_rho = {rho v_a},  f_m = {rho v_a}{v} + {p} a,
+ *   f_E   = {rho v_a}{|v|^2/2} + gamma/(gamma-1) {p v_a}
+ * (kinetic energy carried in the same skew-symmetric way as momentum,
+ * enthalpy of the internal energy in divergence form). */
+void orc_flux_morinishi(const double *uL, const double *uR, const double *a, double g, double *f)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double vaL = vL[0] * a[0] + vL[1] * a[1] + vL[2] * a[2];
+    double vaR = vR[0] * a[0] + vR[1] * a[1] + vR[2] * a[2];
+    double m = 0.5 * (rL * vaL + rR * vaR);
+    double p_av = 0.5 * (pL + pR);
+    double kL = 0.5 * (vL[0] * vL[0] + vL[1] * vL[1] + vL[2] * vL[2]);
+    double kR = 0.5 * (vR[0] * vR[0] + vR[1] * vR[1] + vR[2] * vR[2]);
+    f[0] = m;
+    for (int c = 0; c < 3; ++c) f[1 + c] = m * 0.5 * (vL[c] + vR[c]) + p_av * a[c];
+    f[4] = m * 0.5 * (kL + kR) + g / (g - 1.0) * 0.5 * (pL * vaL + pR * vaR);
+}
+
+/* Ismail and Roe's entropy-conservative flux (Ismail & Roe 2009), dotted
+ * with a: parameter vector z = sqrt(rho/p) (1, v, p), so z1 = sqrt(rho/p),
+ * z_v = z1 v, z5 = sqrt(rho p); with {.} arithmetic and (.)^ln logarithmic
+ * means:
+ *   rho^ = {z1} z5^ln,  v^ = {z_v}/{z1},  p1^ = {z5}/{z1},
+ *   p2^ = (gamma+1)/(2 gamma) z5^ln/z1^ln + (gamma-1)/(2 gamma) {z5}/{z1},
+ *   h^ = gamma p2^ / ((gamma-1) rho^) + |v^|^2/2,
+ *   f = (rho^ v^.a, rho^ v^.a v^ + p1^ a, rho^ v^.a h^). */
+void orc_flux_ir(const double *uL, const double *uR, const double *a, double g, double *f)
+{
+    double rL, vL[3], pL, rR, vR[3], pR;
+    primitives(uL, g, &rL, vL, &pL);
+    primitives(uR, g, &rR, vR, &pR);
+    double z1L = sqrt(rL / pL), z1R = sqrt(rR / pR);
+    double z5L = sqrt(rL * pL), z5R = sqrt(rR * pR);
+    double z1a = 0.5 * (z1L + z1R), z5a = 0.5 * (z5L + z5R);
+    double z1ln = orc_logmean(z1L, z1R), z5ln = orc_logmean(z5L, z5R);
+    double rho = z1a * z5ln;
+    double v[3];
+    for (int c = 0; c < 3; ++c) v[c] = 0.5 * (z1L * vL[c] + z1R * vR[c]) / z1a;
+    double p1 = z5a / z1a;
+    double p2 = (g + 1.0) / (2.0 * g) * z5ln / z1ln + (g - 1.0) / (2.0 * g) * z5a / z1a;
+    double h = g * p2 / ((g - 1.0) * rho) + 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double va = v[0] * a[0] + v[1] * a[1] + v[2] * a[2];
+    f[0] = rho * va;
+    for (int c = 0; c < 3; ++c) f[1 + c] = rho * va * v[c] + p1 * a[c];
+    f[4] = rho * va * h;
+}
+
+/* Two-point volume flux of split form `form` (1..6) dotted with a. */
 static void split_flux(int form, const double *ui, const double *um, const double *a, double g, double *f)
 {
     if (form == 1) orc_flux_ec(ui, um, a, g, f);
+    else if (form == 5) orc_flux_morinishi(ui, um, a, g, f);
+    else if (form == 6) orc_flux_ir(ui, um, a, g, f);
     else orc_flux_split(form, ui, um, a, g, f);
 }
 
@@ -631,7 +806,10 @@ static void surface_flux(int kind, const double *uin, const double *uout, const 
     double s = sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
     double nh[3] = {Sn[0] / s, Sn[1] / s, Sn[2] / s};
     if (kind == 0) orc_flux_lf(uin, uout, nh, g, f);
-    else orc_flux_roe(uin, uout, nh, g, f);
+    else if (kind == 1) orc_flux_roe(uin, uout, nh, g, f);
+    else if (kind == 3) orc_flux_rusanov(uin, uout, nh, g, f);
+    else if (kind == 4) orc_flux_ldroe(uin, uout, nh, g, f);
+    else orc_flux_matrix(uin, uout, nh, g, f);
     for (int v = 0; v < NVAR; ++v) f[v] *= s;
 }
 

@@ -837,3 +837,217 @@ def test_dt_rule_is_inside_rk4_stability_region(N):
     n = N + 1
     dt = 0.5 * 8 / (n * n * 2.0)
     assert max(_lsrk_amplification("rk4", 2 * dt * m, 5) for m in mu) <= 1 + 1e-9
+
+
+# --------------------------------------------------------------------------- further surface fluxes (Sec. 3.3) and
+#                                                                              split forms (Sec. 3.5)
+
+NEW_SURFACE = ["rusanov", "ldroe", "matrix"]
+
+
+def _unit(rng):
+    nh = rng.standard_normal(3)
+    return nh / np.linalg.norm(nh)
+
+
+@pytest.mark.parametrize("kind", NEW_SURFACE)
+def test_new_surface_flux_consistency_and_conservation(kind):
+    rng = np.random.default_rng(41)
+    for _ in range(30):
+        uL, uR = _random_state(rng), _random_state(rng)
+        nh = _unit(rng)
+        assert np.allclose(O.flux_surface(kind, uL, uL, nh), O.flux_euler(uL, nh), rtol=1e-13, atol=1e-13)
+        assert np.allclose(O.flux_surface(kind, uL, uR, nh), -O.flux_surface(kind, uR, uL, -nh),
+                           rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["rusanov", "matrix"])
+def test_new_surface_flux_entropy_stability(kind):
+    """[[w]].F* <= [[psi]]: Rusanov (dissipation lambda [[u]] with lambda at
+    least LF's) and the matrix dissipation (positive semi-definite in [[w]])
+    for arbitrary pairs, large jumps included."""
+    rng = np.random.default_rng(42)
+    worst = -np.inf
+    for _ in range(300):
+        uL = _random_state(rng)
+        uR = _random_state(rng) if rng.random() < 0.5 else uL * (1 + 0.05 * rng.standard_normal(5))
+        nh = _unit(rng)
+        dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+        worst = max(worst, dw @ O.flux_surface(kind, uL, uR, nh) - (_psi(uR, nh) - _psi(uL, nh)))
+    assert worst <= 1e-13
+
+
+def test_rusanov_dissipates_at_least_as_much_as_lf():
+    """Both are (F_L+F_R)/2 - lambda [[u]]/2; the Rusanov speed bound is never
+    below LF's, so its entropy production [[w]].(F_rus - F_lf) <= 0, and it is
+    strictly larger when one side has the larger |v.n| and the other the
+    larger sound speed."""
+    rng = np.random.default_rng(43)
+    for _ in range(100):
+        uL, uR = _random_state(rng), _random_state(rng)
+        nh = _unit(rng)
+        dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+        assert dw @ (O.flux_surface("rusanov", uL, uR, nh) - O.flux_lf(uL, uR, nh)) <= 1e-13
+    # fast cold left state, slow hot right state
+    nh = np.array([1.0, 0.0, 0.0])
+    uL = np.array([1.0, 0.5, 0.0, 0.0, 0.5 / (G - 1) + 0.125])
+    uR = np.array([1.0, 0.0, 0.0, 0.0, 2.0 / (G - 1)])
+    d = O.flux_surface("rusanov", uL, uR, nh) - O.flux_lf(uL, uR, nh)
+    # the extra dissipation is along [[u]], with a positive coefficient
+    du = uR - uL
+    k = -(d @ du) / (du @ du)
+    assert np.linalg.norm(d + k * du) < 1e-13 * np.linalg.norm(d)
+    assert k > 0.1
+
+
+def test_ldroe_limits():
+    """Low-dissipation Roe: identical to Roe when a side is supersonic
+    (z = 1) and for jumps without a velocity jump; for a pure velocity jump
+    its dissipation is Roe's times z = max Mach."""
+    rng = np.random.default_rng(44)
+    nh = _unit(rng)
+
+    def state(rho, v, p):
+        v = np.asarray(v, dtype=float)
+        return np.array([rho, *(rho * v), p / (G - 1) + 0.5 * rho * v @ v])
+
+    # supersonic left side
+    uL, uR = state(1.0, [2.0, 0.3, -0.2], 1.0), state(1.2, [0.5, 0.1, 0.0], 0.9)
+    assert np.allclose(O.flux_surface("ldroe", uL, uR, nh), O.flux_roe(uL, uR, nh), rtol=1e-14, atol=1e-14)
+    # same velocity, density and pressure jumps: no velocity jump to scale
+    v = [0.05, -0.02, 0.01]
+    uL, uR = state(1.0, v, 1.0), state(1.3, v, 0.8)
+    assert np.allclose(O.flux_surface("ldroe", uL, uR, nh), O.flux_roe(uL, uR, nh), rtol=1e-14, atol=1e-14)
+    # pure velocity jump at low Mach: dissipation scales by z
+    vL, vR = np.array([0.05, 0.01, 0.0]), np.array([0.02, -0.03, 0.04])
+    uL, uR = state(1.0, vL, 1.0), state(1.0, vR, 1.0)
+    c = np.sqrt(G)
+    z = max(np.linalg.norm(vL), np.linalg.norm(vR)) / c
+    central = 0.5 * (O.flux_euler(uL, nh) + O.flux_euler(uR, nh))
+    d_ld = central - O.flux_surface("ldroe", uL, uR, nh)
+    d_roe = central - O.flux_roe(uL, uR, nh)
+    assert np.allclose(d_ld, z * d_roe, rtol=1e-12, atol=1e-15)
+    assert 0.01 < z < 0.1
+
+
+def test_matrix_dissipation_matches_roe_to_second_order():
+    """For u_R = u_L + eps d the matrix dissipation |A| (du/dw) [[w]] equals
+    Roe's |A| [[u]] to first order, which ties its scaled eigenvectors to
+    du/dw and its eigenvalues to the flux Jacobian: the difference of the two
+    fluxes shrinks like eps^2."""
+    rng = np.random.default_rng(45)
+    for _ in range(10):
+        uL = _random_state(rng)
+        d = uL * rng.standard_normal(5)
+        nh = _unit(rng)
+        diffs = []
+        for eps in (1e-2, 1e-3):
+            uR = uL + eps * d
+            diffs.append(np.linalg.norm(O.flux_surface("matrix", uL, uR, nh) - O.flux_roe(uL, uR, nh)))
+        assert 60 < diffs[0] / diffs[1] < 160, diffs
+        # and the dissipation itself is first order: it is not hidden by the EC part
+        uR = uL + 1e-3 * d
+        diss = O.flux_ec(uL, uR, nh) - O.flux_surface("matrix", uL, uR, nh)
+        assert np.linalg.norm(diss) > 10 * diffs[1]
+
+
+def test_ismail_roe_flux_tadmor_identity_and_consistency():
+    rng = np.random.default_rng(46)
+    for _ in range(50):
+        uL, uR = _random_state(rng), _random_state(rng)
+        a = rng.standard_normal(3)
+        f = O.flux_split("ir", uL, uR, a)
+        dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+        rhs = _psi(uR, a) - _psi(uL, a)
+        assert abs(dw @ f - rhs) < 1e-12 * (1 + abs(rhs))
+        assert np.allclose(O.flux_split("ir", uL, uL, a), O.flux_euler(uL, a), rtol=1e-13, atol=1e-13)
+        assert np.allclose(f, O.flux_split("ir", uR, uL, a), rtol=1e-14, atol=1e-14)
+    uL = _random_state(rng)
+    uR = uL * (1 + 1e-5 * rng.standard_normal(5))
+    a = np.array([0.3, -0.2, 0.9])
+    dw = O.entropy_vars(uR) - O.entropy_vars(uL)
+    assert abs(dw @ O.flux_split("ir", uL, uR, a) - (_psi(uR, a) - _psi(uL, a))) < 1e-15
+
+
+def test_morinishi_flux_properties():
+    """Consistent, symmetric, kinetic-energy preserving (Jameson), and its
+    flux differencing equals the product-rule split derivative with the mass
+    flux rho v kept whole."""
+    rng = np.random.default_rng(47)
+    for _ in range(20):
+        uL, uR = _random_state(rng), _random_state(rng)
+        a = rng.standard_normal(3)
+        f = O.flux_split("morinishi", uL, uR, a)
+        assert np.allclose(O.flux_split("morinishi", uL, uL, a), O.flux_euler(uL, a), rtol=1e-13, atol=1e-13)
+        assert np.allclose(f, O.flux_split("morinishi", uR, uL, a), rtol=1e-14, atol=1e-14)
+        r = f[1:4] - 0.5 * (uL[1:4] / uL[0] + uR[1:4] / uR[0]) * f[0]
+        assert np.linalg.norm(np.cross(r, a)) < 1e-12 * np.linalg.norm(r) * np.linalg.norm(a)
+    N = 5
+    D = O.dmatrix(N)
+    u = _random_state(rng, (N + 1,)).T
+    a = np.array([1.0, 0.0, 0.0])
+    lhs = np.array([2 * sum(D[i, j] * O.flux_split("morinishi", u[i], u[j], a) for j in range(N + 1))
+                    for i in range(N + 1)])
+    rho = u[:, 0]
+    v = u[:, 1:4] / rho[:, None]
+    p = (G - 1) * (u[:, 4] - 0.5 * rho * (v * v).sum(1))
+    mx = rho * v[:, 0]
+    K = 0.5 * (v * v).sum(1)
+
+    def d2(x, y):
+        return 0.5 * (D @ (x * y) + x * (D @ y) + y * (D @ x))
+
+    rhs = np.zeros_like(lhs)
+    rhs[:, 0] = D @ mx
+    for b in range(3):
+        rhs[:, 1 + b] = d2(mx, v[:, b])
+    rhs[:, 1] += D @ p
+    rhs[:, 4] = d2(mx, K) + G / (G - 1) * (D @ (p * v[:, 0]))
+    assert np.abs(lhs - rhs).max() < 1e-11 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("volume", ["morinishi", "ir"])
+def test_new_split_forms_free_stream_conservation_convergence(curved, volume):
+    m = curved
+    st = np.array([1.2, 0.36, -0.24, 0.12, 2.6])
+    u = np.broadcast_to(st[None, :, None, None, None], m.shape).copy()
+    assert np.abs(m.residual(O.Cfg("ns", "roe", volume, Re=50.0), u)).max() < 1e-12
+    rng = np.random.default_rng(48)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    r = m.residual(O.Cfg("ns", "lf", volume, Re=50.0), u)
+    tot = m.integrals(G, u, r)[:5]
+    mag = m.integrals(G, u, np.abs(r))[:5]
+    assert np.abs(tot / mag).max() < 1e-13
+    errs = []
+    for N in (2, 3, 4, 5, 6):
+        mm = O.Mesh(3, 3, 3, N, lo=(0,) * 3, hi=(10,) * 3, amp=0.05)
+        d = 1e-5
+        exact = (_wave(mm, d) - _wave(mm, -d)) / (2 * d)
+        errs.append(_rel(mm.residual(O.Cfg("euler", "roe", volume), _wave(mm, 0.0)), exact))
+    assert errs[-1] < 4e-3
+    assert all(b < 0.4 * a for a, b in zip(errs, errs[1:]))
+
+
+@pytest.mark.parametrize("surface", NEW_SURFACE)
+def test_new_surface_fluxes_in_the_residual(curved, surface):
+    m = curved
+    st = np.array([1.2, 0.36, -0.24, 0.12, 2.6])
+    u = np.broadcast_to(st[None, :, None, None, None], m.shape).copy()
+    assert np.abs(m.residual(O.Cfg("ns", surface, "ec", Re=50.0), u)).max() < 1e-12
+    rng = np.random.default_rng(49)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    res = m.integrals(G, u, m.residual(O.Cfg("euler", surface, "ec"), u))
+    mag = m.integrals(G, u, np.abs(m.residual(O.Cfg("euler", surface, "ec"), u)))
+    assert np.abs(res[:5] / mag[:5]).max() < 1e-13
+    # with the entropy-conservative volume term, the entropy-stable surface
+    # fluxes make the scheme dissipate entropy
+    if surface in ("rusanov", "matrix"):
+        assert res[5] < -1e-6 * res[6]
+
+
+def test_ismail_roe_volume_with_ec_surface_conserves_entropy(curved):
+    m = curved
+    rng = np.random.default_rng(50)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    ir = m.integrals(G, u, m.residual(O.Cfg("euler", "ec", "ir"), u))
+    assert abs(ir[5]) < 1e-13 * ir[6]
