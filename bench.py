@@ -373,9 +373,10 @@ def run_hs3d(args, world, rank, local):
         extra["tgv_64cubed_N3_standard_lf_euler"] = run_workload("sweep", 64, 3, "euler", "lf", "standard", 5, 2)
         extra["tgv_52cubed_N4_standard_lf_euler"] = run_workload("sweep", 52, 4, "euler", "lf", "standard", 5, 2)
         extra["tgv_64cubed_N3_standard_roe_br1"] = run_workload("sweep", 64, 3, "ns", "roe", "standard", 5, 2)
-        for vol, tm in (("kg", "rk4"), ("pirozzoli", "rk3"), ("ducros", "rk3")):
-            extra[f"tgv_32cubed_N3_{vol}_roe_br1_{tm}"] = run_workload("split", 32, 3, "ns", "roe", vol, 5, 2,
-                                                                       time=tm)
+        for vol, surf, tm in (("kg", "roe", "rk4"), ("pirozzoli", "roe", "rk3"), ("ducros", "roe", "rk3"),
+                              ("morinishi", "ldroe", "rk3"), ("ir", "matrix", "rk3")):
+            extra[f"tgv_32cubed_N3_{vol}_{surf}_br1_{tm}"] = run_workload("split", 32, 3, "ns", surf, vol, 5, 2,
+                                                                          time=tm)
 
     if args.stress > 0:
         extra["admission_stress"] = run_stress(args.stress, args.stress_budget_gb, args.stress_emax, "mixed32")

@@ -55,15 +55,35 @@ typedef enum {
 
 /* physics */
 enum { HS3D_EULER = 0, HS3D_NS = 1 };
-/* surface (Riemann) flux, Sec. 3.3: Lax-Friedrichs, Roe, central
- * (entropy-conservative Chandrashekar flux, no dissipation) */
-enum { HS3D_FLUX_LF = 0, HS3D_FLUX_ROE = 1, HS3D_FLUX_EC = 2 };
+/* surface (Riemann) flux, Sec. 3.3, each times the face scale |Ja^d|:
+ *   LF        (F_L+F_R).n/2 - lambda [[u]]/2, lambda = max(|v_L.n| + c_L, |v_R.n| + c_R)
+ *   ROE       Roe's flux (sqrt(rho) averages, no entropy fix); the wave strengths are
+ *             formed from the jumps of rho, v, p with the averaged state, which is also
+ *             Roe and Pike's construction (the two name the same flux)
+ *   EC        central: Chandrashekar's entropy-conservative flux, no dissipation
+ *   RUSANOV   as LF with lambda = max(|v_L.n|, |v_R.n|) + max(c_L, c_R)
+ *   LDROE     low-dissipation Roe (L2Roe): the velocity jump in Roe's dissipation
+ *             scaled by min(1, max(M_L, M_R)), M = |v|/c
+ *   MATRIX    entropy-stable: Chandrashekar's flux minus matrix dissipation
+ *             R|Lambda|T R^T [[w]] (scaled eigenvectors at the Chandrashekar averages,
+ *             w the entropy variables) */
+enum {
+    HS3D_FLUX_LF = 0,
+    HS3D_FLUX_ROE = 1,
+    HS3D_FLUX_EC = 2,
+    HS3D_FLUX_RUSANOV = 3,
+    HS3D_FLUX_LDROE = 4,
+    HS3D_FLUX_MATRIX = 5
+};
 /* volume term (Sec. 3.5): standard DGSEM, or a split form written as flux
  * differencing with a symmetric two-point flux F#(u_i, u_m).(Ja_i + Ja_m):
  *   EC         Chandrashekar's entropy-conservative, kinetic-energy-preserving flux
  *   KG         Kennedy-Gruber:  {rho}{v_a}, {rho}{v_a}{v} + {p}a, {rho}{v_a}{e} + {p}{v_a}
  *   PIROZZOLI  Pirozzoli:       as KG for mass and momentum, energy {rho}{v_a}{h}
  *   DUCROS     Ducros et al.:   {rho}{v_a}, {rho v}{v_a} + {p}a, {rho e + p}{v_a}
+ *   MORINISHI  Morinishi:       {rho v_a}, {rho v_a}{v} + {p}a, {rho v_a}{|v|^2/2} + gamma/(gamma-1){p v_a}
+ *   IR         entropy conserving (Ismail-Roe), from z = sqrt(rho/p)(1, v, p) and
+ *              logarithmic means of z1 and z5
  * ({.} arithmetic mean of the two nodes, v_a = v.a, e = (rho e)/rho,
  * h = (rho e + p)/rho) */
 enum {
@@ -71,7 +91,9 @@ enum {
     HS3D_VOL_EC = 1,
     HS3D_VOL_KG = 2,
     HS3D_VOL_PIROZZOLI = 3,
-    HS3D_VOL_DUCROS = 4
+    HS3D_VOL_DUCROS = 4,
+    HS3D_VOL_MORINISHI = 5,
+    HS3D_VOL_IR = 6
 };
 /* explicit low-storage time integrator (Sec. 3.7): Williamson's three-stage
  * third-order scheme, or Carpenter and Kennedy's five-stage fourth-order

@@ -21,15 +21,17 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONPHYSICAL, ERR_UNSUPPORTED 
 STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT",
                 -5: "NONPHYSICAL", -6: "UNSUPPORTED"}
 EULER, NS = 0, 1
-FLUX_LF, FLUX_ROE, FLUX_EC = 0, 1, 2
-VOL_STANDARD, VOL_EC, VOL_KG, VOL_PIROZZOLI, VOL_DUCROS = 0, 1, 2, 3, 4
+FLUX_LF, FLUX_ROE, FLUX_EC, FLUX_RUSANOV, FLUX_LDROE, FLUX_MATRIX = 0, 1, 2, 3, 4, 5
+VOL_STANDARD, VOL_EC, VOL_KG, VOL_PIROZZOLI, VOL_DUCROS, VOL_MORINISHI, VOL_IR = 0, 1, 2, 3, 4, 5, 6
 TIME_RK3, TIME_RK4 = 0, 1
 FP64, MIXED32 = 0, 1
 IC_VORTEX, IC_TGV = 0, 1
 
 PHYSICS = {"euler": EULER, "ns": NS}
-SURFACE = {"lf": FLUX_LF, "roe": FLUX_ROE, "ec": FLUX_EC}
-VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC, "kg": VOL_KG, "pirozzoli": VOL_PIROZZOLI, "ducros": VOL_DUCROS}
+SURFACE = {"lf": FLUX_LF, "roe": FLUX_ROE, "ec": FLUX_EC, "rusanov": FLUX_RUSANOV, "ldroe": FLUX_LDROE,
+           "matrix": FLUX_MATRIX}
+VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC, "kg": VOL_KG, "pirozzoli": VOL_PIROZZOLI, "ducros": VOL_DUCROS,
+          "morinishi": VOL_MORINISHI, "ir": VOL_IR}
 TIME = {"rk3": TIME_RK3, "rk4": TIME_RK4}
 PRECISION = {"fp64": FP64, "mixed32": MIXED32}
 

@@ -42,9 +42,9 @@ hs3d_status validate_cfg(const hs3d_solver_cfg *c)
 {
     if (!c) return fail(HS3D_ERR_INVALID, "cfg is NULL");
     if (c->physics != HS3D_EULER && c->physics != HS3D_NS) return fail(HS3D_ERR_INVALID, "bad physics %d", c->physics);
-    if (c->surface_flux < HS3D_FLUX_LF || c->surface_flux > HS3D_FLUX_EC)
+    if (c->surface_flux < HS3D_FLUX_LF || c->surface_flux > HS3D_FLUX_MATRIX)
         return fail(HS3D_ERR_INVALID, "bad surface_flux %d", c->surface_flux);
-    if (c->volume_form < HS3D_VOL_STANDARD || c->volume_form > HS3D_VOL_DUCROS)
+    if (c->volume_form < HS3D_VOL_STANDARD || c->volume_form > HS3D_VOL_IR)
         return fail(HS3D_ERR_INVALID, "bad volume_form %d", c->volume_form);
     if (c->time_scheme != HS3D_TIME_RK3 && c->time_scheme != HS3D_TIME_RK4)
         return fail(HS3D_ERR_INVALID, "bad time_scheme %d", c->time_scheme);

@@ -2,7 +2,8 @@
 //
 // k_face: one thread per face node.  Gathers the two traces (Gauss-Lobatto
 // nodes include the element boundary, so the trace is the boundary node
-// itself), computes the inviscid numerical flux (LF, Roe or central EC,
+// itself), computes the inviscid numerical flux (LF, Roe, central EC,
+// Rusanov, low-dissipation Roe or entropy-stable matrix dissipation,
 // Sec. 3.3) times the face scale and, for Navier-Stokes, subtracts the BR1
 // viscous flux (F_v(L) + F_v(R)).Sn/2.  Each face is solved once; both
 // elements read the result (with opposite sign on the -d side).
@@ -94,10 +95,25 @@ __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, i
 #pragma unroll
         for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
         flux_lf(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+    } else if (flux == HS3D_FLUX_RUSANOV) {
+        double uL[5], uR[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            uL[v] = it.u[iL + (size_t)v * n3];
+            uR[v] = it.u[iR + (size_t)v * n3];
+        }
+        R ul[5] = {qL.rho, narrow<R>(uL[1]), narrow<R>(uL[2]), narrow<R>(uL[3]), qL.E};
+        R ur[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
+        flux_rusanov(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+    } else if (flux == HS3D_FLUX_MATRIX) {
+        flux_matrix(qL, qR, P.gamma, P.hg, s1, s2, s3, fs);
     } else {
         const R ul[5] = {qL.rho, (R)0, (R)0, (R)0, qL.E};
         const R ur[5] = {qR.rho, (R)0, (R)0, (R)0, qR.E};
-        flux_roe(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+        if (flux == HS3D_FLUX_LDROE) flux_ldroe(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+        else flux_roe(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
     }
     if (NS) {
         const R *GL = (const R *)it.grad + (size_t)eL * 12 * n3 + pL;

@@ -188,11 +188,30 @@ __device__ __forceinline__ void flux_lf(const Prim<R> &L, const R uL[5], const P
     for (int v = 0; v < 5; ++v) f[v] = (R)0.5 * (fl[v] + fr[v]) - (R)0.5 * lam * (uR[v] - uL[v]);
 }
 
+// Rusanov flux times the face scale: as LF with the speed bound
+// lambda = max(|v_L.n|, |v_R.n|) + max(c_L, c_R).
+template <typename R>
+__device__ __forceinline__ void flux_rusanov(const Prim<R> &L, const R uL[5], const Prim<R> &Rr, const R uR[5],
+                                             R gamma, R s1, R s2, R s3, R f[5])
+{
+    R s = sqrt(s1 * s1 + s2 * s2 + s3 * s3);
+    R fl[5], fr[5];
+    euler_flux(L, uL[4], s1, s2, s3, fl);
+    euler_flux(Rr, uR[4], s1, s2, s3, fr);
+    R vn = fmax(fabs(L.v1 * s1 + L.v2 * s2 + L.v3 * s3), fabs(Rr.v1 * s1 + Rr.v2 * s2 + Rr.v3 * s3));
+    R c = fmax(sqrt(gamma * L.p / L.rho), sqrt(gamma * Rr.p / Rr.rho));
+    R lam = vn + s * c;        // = s * lambda
+#pragma unroll
+    for (int v = 0; v < 5; ++v) f[v] = (R)0.5 * (fl[v] + fr[v]) - (R)0.5 * lam * (uR[v] - uL[v]);
+}
+
 // Roe flux times the face scale (Roe 1981, sqrt(rho)-weighted averages, no
 // entropy fix): s [ (F_L + F_R).n/2 - sum_k |lambda_k| alpha_k r_k / 2 ].
+// zvel scales the velocity jump seen by the dissipation (1: Roe; the
+// low-dissipation variant passes min(1, max Mach)).
 template <typename R>
 __device__ __forceinline__ void flux_roe(const Prim<R> &L, const R uL[5], const Prim<R> &Rr, const R uR[5], R gamma,
-                                         R s1, R s2, R s3, R f[5])
+                                         R s1, R s2, R s3, R f[5], R zvel = (R)1)
 {
     R s = sqrt(s1 * s1 + s2 * s2 + s3 * s3);
     R is = (R)1 / s;
@@ -215,6 +234,11 @@ __device__ __forceinline__ void flux_roe(const Prim<R> &L, const R uL[5], const 
     R vnt = vt1 * n1 + vt2 * n2 + vt3 * n3;
     R dr = Rr.rho - L.rho, dp = Rr.p - L.p;
     R d1 = Rr.v1 - L.v1, d2 = Rr.v2 - L.v2, d3 = Rr.v3 - L.v3;
+    if (zvel != (R)1) {
+        d1 *= zvel;
+        d2 *= zvel;
+        d3 *= zvel;
+    }
     R dvn = d1 * n1 + d2 * n2 + d3 * n3;
     R a1 = (dp - rt * ct * dvn) * (R)0.5 * ic2;
     R a5 = (dp + rt * ct * dvn) * (R)0.5 * ic2;
@@ -232,6 +256,18 @@ __device__ __forceinline__ void flux_roe(const Prim<R> &L, const R uL[5], const 
     f[2] = (R)0.5 * (fl[2] + fr[2]) - hs * W2;
     f[3] = (R)0.5 * (fl[3] + fr[3]) - hs * W3;
     f[4] = (R)0.5 * (fl[4] + fr[4]) - hs * W4;
+}
+
+// Low-dissipation Roe (L2Roe, Osswald et al. 2016): Roe with the velocity
+// jump of the dissipation scaled by z = min(1, max(M_L, M_R)), M = |v|/c.
+template <typename R>
+__device__ __forceinline__ void flux_ldroe(const Prim<R> &L, const R uL[5], const Prim<R> &Rr, const R uR[5], R gamma,
+                                           R s1, R s2, R s3, R f[5])
+{
+    const R mL = (L.v1 * L.v1 + L.v2 * L.v2 + L.v3 * L.v3) * L.rho / (gamma * L.p);
+    const R mR = (Rr.v1 * Rr.v1 + Rr.v2 * Rr.v2 + Rr.v3 * Rr.v3) * Rr.rho / (gamma * Rr.p);
+    const R z = fmin((R)1, sqrt(fmax(mL, mR)));
+    flux_roe(L, uL, Rr, uR, gamma, s1, s2, s3, f, z);
 }
 
 template <typename R>
@@ -315,6 +351,84 @@ __device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr,
     f[4] = fm * (hg * ibeta_ln - (R)0.5 * v2) + m1 * f[1] + m2 * f[2] + m3 * f[3];
 }
 
+// Logarithmic mean of a, b > 0 from their logarithms, and its reciprocal:
+// the Ismail-Roe series in u = ((a-b)/(a+b))^2 below LogMeanEps (as in
+// flux_ec), (a-b)/(ln a - ln b) above.
+template <typename R>
+__device__ __forceinline__ R ln_mean(R a, R b, R la, R lb)
+{
+    const R s = a + b, d = a - b, fr = d * rcp_(s), u = fr * fr;
+    if (u < LogMeanEps<R>::v)
+        return (R)0.5 * s * ((R)1 - u * ((R)(1.0 / 3.0) + u * ((R)(4.0 / 45.0) + u * (R)(44.0 / 945.0))));
+    return d / (la - lb);
+}
+
+template <typename R>
+__device__ __forceinline__ R inv_ln_mean(R a, R b, R la, R lb)
+{
+    const R s = a + b, d = a - b, is = rcp_(s), fr = d * is, u = fr * fr;
+    if (u < LogMeanEps<R>::v) return (R)2 * is * ((R)1 + u * ((R)(1.0 / 3.0) + u * ((R)0.2 + u * (R)(1.0 / 7.0))));
+    return (la - lb) / d;
+}
+
+// Entropy-stable flux with matrix dissipation (Winters, Derigs, Gassner and
+// Walch 2017), times the face scale: Chandrashekar's flux minus
+// (s/2) sum_k |lambda_k| T_k r_k (r_k . [[w]]), w the entropy variables
+// ((gamma - s)/(gamma-1) - rho|v|^2/(2p), rho v/p, -rho/p), with the scaled
+// eigenvectors at rho^ = ln-mean rho, p^ = {rho}/(2{beta}), v^ = {v},
+// v2^ = 2|{v}|^2 - {|v|^2}, a^ = sqrt(gamma p^/rho^),
+// h^ = gamma/(2(gamma-1) beta^ln) + v2^/2:
+//   acoustic r = [1, v^ -+ a^ n, h^ -+ a^ v^.n], T = rho^/(2 gamma)
+//   entropy  r = [1, v^, v2^/2],                T = rho^ (gamma-1)/gamma
+//   shear    (I - n n^T) projection of [[w_m]] + v^ [[w_E]],  T = p^.
+// The entropy-variable jump uses ln p - gamma ln rho = (1-gamma) ln rho -
+// ln beta - ln 2 from the per-node logarithms of rho and beta.
+template <typename R>
+__device__ __forceinline__ void flux_matrix(const Prim<R> &L, const Prim<R> &Rr, R gamma, R hg, R s1, R s2, R s3,
+                                            R f[5])
+{
+    const ECNode<R> zl = ec_node(L), zr = ec_node(Rr);
+    flux_ec(zl, zr, hg, s1, s2, s3, f);
+    const R s = sqrt(s1 * s1 + s2 * s2 + s3 * s3);
+    const R is = rcp_(s);
+    const R n1 = s1 * is, n2 = s2 * is, n3 = s3 * is;
+    const R rho_h = ln_mean(zl.rho, zr.rho, zl.lrho, zr.lrho);
+    const R ib_ln = inv_ln_mean(zl.beta, zr.beta, zl.lbeta, zr.lbeta);
+    const R p_h = (R)0.5 * (zl.rho + zr.rho) * rcp_(zl.beta + zr.beta);
+    const R v1 = (R)0.5 * (L.v1 + Rr.v1), v2 = (R)0.5 * (L.v2 + Rr.v2), v3 = (R)0.5 * (L.v3 + Rr.v3);
+    const R qL = L.v1 * L.v1 + L.v2 * L.v2 + L.v3 * L.v3, qR = Rr.v1 * Rr.v1 + Rr.v2 * Rr.v2 + Rr.v3 * Rr.v3;
+    const R v2h = (R)2 * (v1 * v1 + v2 * v2 + v3 * v3) - (R)0.5 * (qL + qR);
+    const R a_h = sqrt(gamma * p_h / rho_h);
+    const R h_h = gamma * hg * ib_ln + (R)0.5 * v2h;
+    const R vn = v1 * n1 + v2 * n2 + v3 * n3;
+    // [[w]]: (gamma-1) [[ln rho]] + [[ln beta]] enters w_0 through 2 hg = 1/(gamma-1)
+    R dw[5];
+    dw[0] = (zr.lrho - zl.lrho) + (R)2 * hg * (zr.lbeta - zl.lbeta) - (zr.beta * qR - zl.beta * qL);
+    dw[1] = (R)2 * (zr.beta * Rr.v1 - zl.beta * L.v1);
+    dw[2] = (R)2 * (zr.beta * Rr.v2 - zl.beta * L.v2);
+    dw[3] = (R)2 * (zr.beta * Rr.v3 - zl.beta * L.v3);
+    dw[4] = (R)-2 * (zr.beta - zl.beta);
+    const R r1[5] = {(R)1, v1 - a_h * n1, v2 - a_h * n2, v3 - a_h * n3, h_h - a_h * vn};
+    const R r5[5] = {(R)1, v1 + a_h * n1, v2 + a_h * n2, v3 + a_h * n3, h_h + a_h * vn};
+    const R c1 = dw[0] + r1[1] * dw[1] + r1[2] * dw[2] + r1[3] * dw[3] + r1[4] * dw[4];
+    const R c5 = dw[0] + r5[1] * dw[1] + r5[2] * dw[2] + r5[3] * dw[3] + r5[4] * dw[4];
+    const R c2 = dw[0] + v1 * dw[1] + v2 * dw[2] + v3 * dw[3] + (R)0.5 * v2h * dw[4];
+    const R T15 = rho_h / ((R)2 * gamma), T2 = rho_h * (gamma - (R)1) / gamma;
+    const R k1 = fabs(vn - a_h) * T15 * c1, k5 = fabs(vn + a_h) * T15 * c5;
+    const R l2 = fabs(vn);
+    const R k2 = l2 * T2 * c2;
+    const R q1 = dw[1] + v1 * dw[4], q2 = dw[2] + v2 * dw[4], q3 = dw[3] + v3 * dw[4];
+    const R qn = q1 * n1 + q2 * n2 + q3 * n3;
+    const R ks = l2 * p_h;
+    const R P1 = ks * (q1 - qn * n1), P2 = ks * (q2 - qn * n2), P3 = ks * (q3 - qn * n3);
+    const R hs = (R)0.5 * s;
+    f[0] -= hs * (k1 + k2 + k5);
+    f[1] -= hs * (k1 * r1[1] + k2 * v1 + k5 * r5[1] + P1);
+    f[2] -= hs * (k1 * r1[2] + k2 * v2 + k5 * r5[2] + P2);
+    f[3] -= hs * (k1 * r1[3] + k2 * v3 + k5 * r5[3] + P3);
+    f[4] -= hs * (k1 * r1[4] + k2 * (R)0.5 * v2h + k5 * r5[4] + v1 * P1 + v2 * P2 + v3 * P3);
+}
+
 // ------------------------------------------------------------------ split forms
 //
 // Per-node inputs of the two-point fluxes, kSplitSlots values per node:
@@ -322,6 +436,8 @@ __device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr,
 //   KG         rho, v1, v2, v3, p, e = (rho e)/rho
 //   PIROZZOLI  rho, v1, v2, v3, p, h = (rho e + p)/rho
 //   DUCROS     rho, v1, v2, v3, p, rho e + p
+//   MORINISHI  rho, v1, v2, v3, p, |v|^2/2
+//   IR         z1 = sqrt(rho/p), z1 v1, z1 v2, z1 v3, z5 = sqrt(rho p), ln z1, ln z5
 // (the average-product forms leave the seventh slot unused).
 constexpr int kSplitSlots = 7;
 
@@ -337,6 +453,19 @@ __device__ __forceinline__ void split_node(const Prim<R> &q, R z[kSplitSlots])
         z[4] = c.beta;
         z[5] = c.lrho;
         z[6] = c.lbeta;
+    } else if constexpr (FORM == HS3D_VOL_IR) {
+        const R z1 = sqrt(q.rho / q.p), z5 = sqrt(q.rho * q.p);
+        z[0] = z1;
+        z[1] = z1 * q.v1;
+        z[2] = z1 * q.v2;
+        z[3] = z1 * q.v3;
+        z[4] = z5;
+        z[5] = log_(z1);
+        z[6] = log_(z5);
+    } else if constexpr (FORM == HS3D_VOL_MORINISHI) {
+        z[4] = q.p;
+        z[5] = (R)0.5 * (q.v1 * q.v1 + q.v2 * q.v2 + q.v3 * q.v3);
+        z[6] = (R)0;
     } else {
         z[4] = q.p;
         if constexpr (FORM == HS3D_VOL_KG) z[5] = q.E / q.rho;
@@ -376,13 +505,60 @@ __device__ __forceinline__ void flux_avg_product(const R *L, const R *Rr, R a1, 
     }
 }
 
+// Morinishi: ({rho v_a}, {rho v_a}{v} + {p}a, {rho v_a}{|v|^2/2} + gamma/(gamma-1){p v_a}).
+template <typename R>
+__device__ __forceinline__ void flux_morinishi(const R *L, const R *Rr, R hg, R a1, R a2, R a3, R f[5])
+{
+    const R h = (R)0.5;
+    const R vaL = L[1] * a1 + L[2] * a2 + L[3] * a3;
+    const R vaR = Rr[1] * a1 + Rr[2] * a2 + Rr[3] * a3;
+    const R m = h * (L[0] * vaL + Rr[0] * vaR);
+    const R pav = h * (L[4] + Rr[4]);
+    f[0] = m;
+    f[1] = m * (h * (L[1] + Rr[1])) + pav * a1;
+    f[2] = m * (h * (L[2] + Rr[2])) + pav * a2;
+    f[3] = m * (h * (L[3] + Rr[3])) + pav * a3;
+    f[4] = m * (h * (L[5] + Rr[5])) + ((R)1 + (R)2 * hg) * (h * (L[4] * vaL + Rr[4] * vaR));
+}
+
+// Ismail-Roe entropy-conservative flux from the parameter vector
+// z = sqrt(rho/p)(1, v, p): rho^ = {z1} z5^ln, v^ = {z_v}/{z1}, p1^ = {z5}/{z1},
+// p2^ = (gamma+1)/(2 gamma) z5^ln/z1^ln + (gamma-1)/(2 gamma) {z5}/{z1},
+// h^ = gamma p2^/((gamma-1) rho^) + |v^|^2/2;
+// f = (rho^ v^.a, rho^ v^.a v^ + p1^ a, rho^ v^.a h^).
+template <typename R>
+__device__ __forceinline__ void flux_ir(const R *L, const R *Rr, R gamma, R hg, R a1, R a2, R a3, R f[5])
+{
+    const R h = (R)0.5;
+    const R z1a = h * (L[0] + Rr[0]), z5a = h * (L[4] + Rr[4]);
+    const R iz1a = rcp_(z1a);
+    const R z5ln = ln_mean(L[4], Rr[4], L[6], Rr[6]);
+    const R iz1ln = inv_ln_mean(L[0], Rr[0], L[5], Rr[5]);
+    const R rho = z1a * z5ln;
+    const R v1 = h * (L[1] + Rr[1]) * iz1a, v2 = h * (L[2] + Rr[2]) * iz1a, v3 = h * (L[3] + Rr[3]) * iz1a;
+    const R p1 = z5a * iz1a;
+    const R ig = rcp_(gamma);
+    const R p2 = h * ((gamma + (R)1) * ig) * z5ln * iz1ln + h * ((gamma - (R)1) * ig) * p1;
+    const R hh = (R)2 * hg * gamma * p2 / rho + h * (v1 * v1 + v2 * v2 + v3 * v3);
+    const R m = rho * (v1 * a1 + v2 * a2 + v3 * a3);
+    f[0] = m;
+    f[1] = m * v1 + p1 * a1;
+    f[2] = m * v2 + p1 * a2;
+    f[3] = m * v3 + p1 * a3;
+    f[4] = m * hh;
+}
+
 template <int FORM, typename R>
-__device__ __forceinline__ void split_pair(const R *L, const R *Rr, R hg, R a1, R a2, R a3, R f[5])
+__device__ __forceinline__ void split_pair(const R *L, const R *Rr, R gamma, R hg, R a1, R a2, R a3, R f[5])
 {
     if constexpr (FORM == HS3D_VOL_EC) {
         const ECNode<R> zl = {L[0], L[1], L[2], L[3], L[4], L[5], L[6]};
         const ECNode<R> zr = {Rr[0], Rr[1], Rr[2], Rr[3], Rr[4], Rr[5], Rr[6]};
         flux_ec(zl, zr, hg, a1, a2, a3, f);
+    } else if constexpr (FORM == HS3D_VOL_MORINISHI) {
+        flux_morinishi(L, Rr, hg, a1, a2, a3, f);
+    } else if constexpr (FORM == HS3D_VOL_IR) {
+        flux_ir(L, Rr, gamma, hg, a1, a2, a3, f);
     } else {
         flux_avg_product<FORM>(L, Rr, a1, a2, a3, f);
     }

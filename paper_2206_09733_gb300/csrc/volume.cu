@@ -54,6 +54,8 @@ cudaError_t prepare_volume(int N)
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_KG>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_PIROZZOLI>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_DUCROS>(N);
+    if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_MORINISHI>(N);
+    if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_IR>(N);
     return e;
 }
 
@@ -74,6 +76,9 @@ cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, co
             return launch_volume_form<HS3D_VOL_PIROZZOLI>(N, prec, physics, b, stage, A, B, lam_slot, s);
         case HS3D_VOL_DUCROS:
             return launch_volume_form<HS3D_VOL_DUCROS>(N, prec, physics, b, stage, A, B, lam_slot, s);
+        case HS3D_VOL_MORINISHI:
+            return launch_volume_form<HS3D_VOL_MORINISHI>(N, prec, physics, b, stage, A, B, lam_slot, s);
+        case HS3D_VOL_IR: return launch_volume_form<HS3D_VOL_IR>(N, prec, physics, b, stage, A, B, lam_slot, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -6,7 +6,7 @@
 //   standard form   V = sum_d D_d F~^d,   F~^d = Ja^d . (F_e - F_v)
 //   split form      V = sum_d sum_m D_im F#(u_i, u_m).(Ja^d_i + Ja^d_m) - sum_d D_d (Ja^d . F_v)
 //                   with a symmetric two-point flux F# (Sec. 3.5): Chandrashekar,
-//                   Kennedy-Gruber, Pirozzoli or Ducros
+//                   Kennedy-Gruber, Pirozzoli, Ducros, Morinishi or Ismail-Roe
 //   surface         S = (1/w_end) (F^* - F~^d_in) on the +d face, (1/w_0)(-F^* + F~^d_in) on the -d face
 //                   F^* the face flux computed once per face by k_face
 // followed either by the residual store or by one low-storage RK stage
@@ -208,6 +208,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         constexpr int W = n2 * NP;
         R *PB = sface + (size_t)epb * FACEVALS + (size_t)le * 5 * W;
         const R hg = valid ? phys_of<R>(*itp).hg : (R)0;
+        const R gam = valid ? phys_of<R>(*itp).gamma : (R)0;
 #pragma unroll 1
         for (int d = 0; d < 3; ++d) {
             if (valid) {
@@ -231,7 +232,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                     const R a2 = S[(7 + d * 3 + 1) * n3 + a] + S[(7 + d * 3 + 1) * n3 + c];
                     const R a3 = S[(7 + d * 3 + 2) * n3 + a] + S[(7 + d * 3 + 2) * n3 + c];
                     R fs[5];
-                    split_pair<FORM>(za, zc, hg, a1, a2, a3, fs);
+                    split_pair<FORM>(za, zc, gam, hg, a1, a2, a3, fs);
 #pragma unroll
                     for (int v = 0; v < 5; ++v) PB[v * W + w] = fs[v];
                 }

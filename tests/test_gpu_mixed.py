@@ -35,8 +35,8 @@ def _built():
     hs.lib()
 
 
-COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec")
-          for v in ("standard", "ec", "kg", "pirozzoli", "ducros")]
+COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec", "rusanov", "ldroe", "matrix")
+          for v in ("standard", "ec", "kg", "pirozzoli", "ducros", "morinishi", "ir")]
 
 
 @pytest.mark.parametrize("combo", COMBOS)

@@ -87,8 +87,9 @@ def test_initial_conditions_match_oracle(kind):
 
 # ------------------------------------------------------------------ residual parity
 
-VOLUMES = ("standard", "ec", "kg", "pirozzoli", "ducros")
-COMBOS = [(p, s, v) for p in ("euler", "ns") for s in ("lf", "roe", "ec") for v in VOLUMES]
+VOLUMES = ("standard", "ec", "kg", "pirozzoli", "ducros", "morinishi", "ir")
+SURFACES = ("lf", "roe", "ec", "rusanov", "ldroe", "matrix")
+COMBOS = [(p, s, v) for p in ("euler", "ns") for s in SURFACES for v in VOLUMES]
 
 
 @pytest.mark.parametrize("combo", COMBOS)
@@ -109,7 +110,9 @@ def test_residual_parity_all_schemes(combo):
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("combo", [("ns", "roe", "ec"), ("euler", "lf", "standard"), ("ns", "roe", "standard"),
-                                   ("euler", "roe", "kg"), ("ns", "lf", "pirozzoli"), ("euler", "ec", "ducros")])
+                                   ("euler", "roe", "kg"), ("ns", "lf", "pirozzoli"), ("euler", "ec", "ducros"),
+                                   ("ns", "matrix", "ir"), ("euler", "ldroe", "morinishi"),
+                                   ("ns", "rusanov", "ec")])
 def test_residual_parity_every_degree(N, combo):
     om, gm = pair(2, 3, 2, N, amp=0.08)
     u0 = random_state(om.shape, seed=100 + N, smooth=True)
@@ -248,13 +251,15 @@ def test_vortex_10_steps_parity_stable_variants(E, volume):
     assert rel(host(u), uo) < TOL64
 
 
-@pytest.mark.parametrize("volume", ["ec", "kg", "pirozzoli"])
-def test_vortex_rk4_steps_parity(volume):
-    """Carpenter-Kennedy RK4 (five stages) with the kinetic-energy-preserving
-    split forms on the 4^3 vortex: 10 steps, state parity 1e-12, and the
+@pytest.mark.parametrize("volume,surface,time", [("ec", "roe", "rk4"), ("kg", "roe", "rk4"),
+                                                 ("pirozzoli", "roe", "rk4"), ("ir", "matrix", "rk3"),
+                                                 ("morinishi", "ldroe", "rk4"), ("ducros", "rusanov", "rk3")])
+def test_vortex_steps_parity_split_forms(volume, surface, time):
+    """The split forms with the further surface fluxes and both integrators
+    on the 4^3 curved vortex mesh: 10 steps, state parity 1e-12, and the
     same number of steps and simulated time on the device clock."""
     om, gm = pair(4, 4, 4, 3, lo=(0,) * 3, hi=(10,) * 3, amp=0.05)
-    oc, gc = cfgs("euler", "roe", volume, cfl=0.5, time="rk4")
+    oc, gc = cfgs("euler", surface, volume, cfl=0.5, time=time)
     uo = om.ic_vortex(G, 0.5, 5.0)
     go = np.zeros_like(uo)
     t = 0.0
