@@ -46,7 +46,9 @@ def build(force: bool = False) -> str:
 
 class _Box(C.Structure):
     _fields_ = [("ex", C.c_int), ("ey", C.c_int), ("ez", C.c_int), ("N", C.c_int),
-                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("amp", C.c_double)]
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("amp", C.c_double), ("nodes", C.c_int)]
+
+NODES = {"lobatto": 0, "gauss": 1}
 
 
 class _Cfg(C.Structure):
@@ -82,6 +84,10 @@ def lib():
             L.orc_logmean.argtypes = [C.c_double, C.c_double]
             L.orc_logmean.restype = C.c_double
             L.orc_residual.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
+            L.orc_residual_nodal.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
+            L.orc_gauss.argtypes = [C.c_int, _dp, _dp]
+            L.orc_lagrange_at.argtypes = [C.c_int, _dp, C.c_double, _dp]
+            L.orc_mesh_faces.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_gradients.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
             L.orc_dt.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp]
             L.orc_dt.restype = C.c_double
@@ -110,6 +116,19 @@ def lgl(N: int):
     return x, w
 
 
+def gauss(N: int):
+    x, w = np.zeros(N + 1), np.zeros(N + 1)
+    lib().orc_gauss(N, x, w)
+    return x, w
+
+
+def lagrange_at(x, y):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(x.size)
+    lib().orc_lagrange_at(x.size, x, float(y), out)
+    return out
+
+
 def dmatrix(N: int, x=None):
     """Nodal derivative matrix D[i, j] = l_j'(x_i) on the Gauss-Lobatto nodes (or given x)."""
     if x is None:
@@ -135,12 +154,15 @@ class Cfg:
 class Mesh:
     """Oracle mesh of an ex*ey*ez periodic box with Gauss-Lobatto nodes of degree N."""
 
-    def __init__(self, ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, X=None):
+    def __init__(self, ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, X=None, nodes="lobatto"):
+        """X, if given, holds the Gauss-Lobatto geometry nodes; `nodes` picks
+        the solution nodes ("lobatto" or "gauss")."""
         self.ex, self.ey, self.ez, self.N = ex, ey, ez, N
         self.n = N + 1
         self.E = ex * ey * ez
         self.lo, self.hi, self.amp = tuple(lo), tuple(hi), amp
-        box = _Box(ex, ey, ez, N, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), amp)
+        self.nodes = nodes
+        box = _Box(ex, ey, ez, N, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), amp, NODES[nodes])
         Xp = None
         if X is not None:
             X = np.ascontiguousarray(X, dtype=np.float64)
@@ -157,6 +179,10 @@ class Mesh:
         self.Ja = np.zeros((self.E, 3, 3, n, n, n))
         self.J = np.zeros((self.E, n, n, n))
         lib().orc_mesh_arrays(self._h, *(a.ctypes.data for a in (self.xi, self.w, self.D, self.X, self.Ja, self.J)))
+        self.Sf = np.zeros((self.E, 3, 2, 3, n, n))   # own face metrics [e][d][side -1/+1][c][tb][ta]
+        self.lb = np.zeros(n)
+        self.rb = np.zeros(n)
+        lib().orc_mesh_faces(self._h, self.Sf.ctypes.data, self.lb.ctypes.data, self.rb.ctypes.data)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -190,7 +216,16 @@ class Mesh:
     def residual(self, cfg: Cfg, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.zeros(self.shape)
-        lib().orc_residual(self._h, C.byref(cfg.c()), u, out)
+        if lib().orc_residual(self._h, C.byref(cfg.c()), u, out) != 0:
+            raise ValueError("residual: unsupported configuration for these nodes")
+        return out
+
+    def residual_nodal(self, cfg: Cfg, u):
+        """The interpolated-trace form of the residual (any nodes)."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(self.shape)
+        if lib().orc_residual_nodal(self._h, C.byref(cfg.c()), u, out) != 0:
+            raise ValueError("residual: unsupported configuration")
         return out
 
     def gradients(self, cfg: Cfg, u):

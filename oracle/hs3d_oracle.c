@@ -122,6 +122,43 @@ int orc_dmatrix(int N, const double *x, double *D)
     return 0;
 }
 
+/* Gauss-Legendre nodes (Sec. 3.3: the solver allows Gauss or Gauss-Lobatto
+ * quadrature points): the n = N+1 roots of L_n, by Newton from the estimate
+ * cos(pi (4j + 3) / (4n + 2)), weights w_j = 2 / ((1 - x_j^2) L_n'(x_j)^2).
+ * Ascending order. */
+int orc_gauss(int N, double *x, double *w)
+{
+    if (N < 0) return -1;
+    int n = N + 1;
+    for (int j = 0; j < n; ++j) {
+        double xj = cos(M_PI * (4.0 * j + 3.0) / (4.0 * n + 2.0));
+        for (int it = 0; it < 100; ++it) {
+            double L, dL;
+            legendre_and_derivative(n, xj, &L, &dL);
+            double dx = L / dL;
+            xj -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        double L, dL;
+        legendre_and_derivative(n, xj, &L, &dL);
+        x[n - 1 - j] = xj;
+        w[n - 1 - j] = 2.0 / ((1.0 - xj * xj) * dL * dL);
+    }
+    return 0;
+}
+
+/* Lagrange basis of the nodes x[0..n-1] at the point y:
+ *   l_j(y) = prod_{k != j} (y - x_k) / (x_j - x_k). */
+void orc_lagrange_at(int n, const double *x, double y, double *l)
+{
+    for (int j = 0; j < n; ++j) {
+        double p = 1.0;
+        for (int k = 0; k < n; ++k)
+            if (k != j) p *= (y - x[k]) / (x[j] - x[k]);
+        l[j] = p;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Mesh: periodic box of ex*ey*ez hexahedra, optional smooth perturbation    */
 /* ------------------------------------------------------------------------ */
@@ -130,15 +167,18 @@ typedef struct {
     int ex, ey, ez, N;
     double lo[3], hi[3];
     double amp;   /* x_c += amp*(L_c/2pi)*sin(t_x)sin(t_y)sin(t_z), t = box mapped to [-pi,pi] */
+    int nodes;    /* solution nodes: 0 Gauss-Lobatto, 1 Gauss-Legendre */
 } orc_box;
 
 typedef struct {
     orc_box box;
     int n, n3, E;
-    double xi[16], w[16], D[256];
-    double *X;    /* [E][3][n3] */
+    double xi[16], w[16], D[256];   /* solution nodes, weights, derivative matrix */
+    double lb[16], rb[16];          /* l_j(-1), l_j(+1) of the solution nodes */
+    double *X;    /* [E][3][n3] at the solution nodes */
     double *Ja;   /* [E][3][3][n3] */
     double *J;    /* [E][n3] */
+    double *Sf;   /* [E][3 d][2 side][3 c][n2]: the element's own Ja^d on its faces xi_d = -1, +1 */
 } orc_mesh;
 
 static int node_index(int n, int i, int j, int k) { return i + n * (j + n * k); }
@@ -260,33 +300,160 @@ int orc_metrics(int E, int N, const double *D, const double *X, double *Ja, doub
     return 0;
 }
 
-/* Build a mesh.  If X_in is given ([E][3][n3]) it replaces the box generator. */
+/* Tangential directions of face direction d (in increasing order) and the
+ * face node index ab = t0 + n*t1. */
+static void face_dirs(int d, int *d0, int *d1)
+{
+    *d0 = (d == 0) ? 1 : 0;
+    *d1 = (d == 2) ? 1 : 2;
+}
+
+/* Interpolate a nodal field of one element along direction d with the
+ * matrix I[t*n + s] (target node t from source node s). */
+static void interp_dir(int n, const double *I, const double *fs, double *ft, int d)
+{
+    for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+        int ijk[3] = {i, j, k};
+        double acc = 0.0;
+        for (int s = 0; s < n; ++s) {
+            int src[3] = {i, j, k};
+            src[d] = s;
+            acc += I[ijk[d] * n + s] * fs[node_index(n, src[0], src[1], src[2])];
+        }
+        ft[node_index(n, i, j, k)] = acc;
+    }
+}
+
+/* Tensor-product interpolation of an n^3 nodal field (three 1-D passes). */
+static void interp3(int n, const double *I, const double *fs, double *ft, double *tmp)
+{
+    interp_dir(n, I, fs, ft, 0);
+    interp_dir(n, I, ft, tmp, 1);
+    interp_dir(n, I, tmp, ft, 2);
+}
+
+/* Build a mesh.  If X_in is given ([E][3][n3], at the Gauss-Lobatto nodes) it
+ * replaces the box generator.
+ *
+ * Gauss-Lobatto solution nodes: the geometry, metric terms and J live on the
+ * same nodes; the face metrics Sf are the metric terms at the boundary nodes.
+ *
+ * Gauss-Legendre solution nodes: the geometry is the degree-N interpolant of
+ * the map through the Gauss-Lobatto nodes (neighbours share their face
+ * nodes, so the mesh is watertight).  The curl-form metric terms are formed
+ * on that grid; each Ja^d is then a polynomial of degree N per direction
+ * whose divergence vanishes identically, so its values at the Gauss nodes
+ * (exact Lobatto-to-Gauss interpolation) satisfy the discrete metric
+ * identity there, and its values on a face depend only on the face's
+ * Lobatto nodes, which both neighbours share.  X and J = det(dX/dxi) are the
+ * geometry polynomial and its derivatives evaluated at the Gauss nodes; the
+ * face metrics Sf are the face values interpolated to the face's Gauss
+ * points. */
 orc_mesh *orc_mesh_create(const orc_box *b, const double *X_in)
 {
     if (b->N < 1 || b->N > 15 || b->ex < 1 || b->ey < 1 || b->ez < 1) return NULL;
+    if (b->nodes != 0 && b->nodes != 1) return NULL;
     orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
     if (!m) return NULL;
     m->box = *b;
-    m->n = b->N + 1;
-    m->n3 = m->n * m->n * m->n;
+    int N = b->N, n = N + 1, n2 = n * n, n3 = n2 * n;
+    m->n = n;
+    m->n3 = n3;
     m->E = b->ex * b->ey * b->ez;
-    orc_lgl(b->N, m->xi, m->w);
-    orc_dmatrix(b->N, m->xi, m->D);
-    size_t en = (size_t)m->E * m->n3;
+    double xL[16], wL[16], DL[256];
+    orc_lgl(N, xL, wL);
+    orc_dmatrix(N, xL, DL);
+    if (b->nodes == 1) orc_gauss(N, m->xi, m->w);
+    else { memcpy(m->xi, xL, sizeof(double) * n); memcpy(m->w, wL, sizeof(double) * n); }
+    orc_dmatrix(N, m->xi, m->D);
+    orc_lagrange_at(n, m->xi, -1.0, m->lb);
+    orc_lagrange_at(n, m->xi, 1.0, m->rb);
+    size_t en = (size_t)m->E * n3;
     m->X = (double *)malloc(sizeof(double) * en * 3);
     m->Ja = (double *)malloc(sizeof(double) * en * 9);
     m->J = (double *)malloc(sizeof(double) * en);
-    if (!m->X || !m->Ja || !m->J) { free(m->X); free(m->Ja); free(m->J); free(m); return NULL; }
-    if (X_in) memcpy(m->X, X_in, sizeof(double) * en * 3);
-    else box_nodes(b, m->xi, m->X);
-    orc_metrics(m->E, b->N, m->D, m->X, m->Ja, m->J);
+    m->Sf = (double *)malloc(sizeof(double) * (size_t)m->E * 18 * n2);
+    double *XL = (double *)malloc(sizeof(double) * en * 3);
+    double *JaL = (double *)malloc(sizeof(double) * en * 9);
+    double *JL = (double *)malloc(sizeof(double) * en);
+    if (!m->X || !m->Ja || !m->J || !m->Sf || !XL || !JaL || !JL) {
+        free(m->X); free(m->Ja); free(m->J); free(m->Sf); free(XL); free(JaL); free(JL); free(m);
+        return NULL;
+    }
+    if (X_in) memcpy(XL, X_in, sizeof(double) * en * 3);
+    else box_nodes(b, xL, XL);
+    orc_metrics(m->E, N, DL, XL, JaL, JL);
+    if (b->nodes == 0) {
+        memcpy(m->X, XL, sizeof(double) * en * 3);
+        memcpy(m->Ja, JaL, sizeof(double) * en * 9);
+        memcpy(m->J, JL, sizeof(double) * en);
+    } else {
+        double I[256], tmp[4096], dX[4096];
+        for (int t = 0; t < n; ++t) orc_lagrange_at(n, xL, m->xi[t], I + t * n);
+        for (int e = 0; e < m->E; ++e) {
+            for (int c = 0; c < 3; ++c)
+                interp3(n, I, XL + ((size_t)e * 3 + c) * n3, m->X + ((size_t)e * 3 + c) * n3, tmp);
+            for (int k9 = 0; k9 < 9; ++k9)
+                interp3(n, I, JaL + ((size_t)e * 9 + k9) * n3, m->Ja + ((size_t)e * 9 + k9) * n3, tmp);
+            /* a_d = dX/dxi_d of the geometry polynomial at the Gauss nodes */
+            double *dXG = (double *)malloc(sizeof(double) * 9 * n3);
+            for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) {
+                for (int kk = 0; kk < n; ++kk) for (int jj = 0; jj < n; ++jj) for (int ii = 0; ii < n; ++ii)
+                    dX[node_index(n, ii, jj, kk)] = dir_derivative(n, DL, XL + ((size_t)e * 3 + c) * n3, d, ii, jj, kk);
+                interp3(n, I, dX, dXG + (c * 3 + d) * n3, tmp);
+            }
+            for (int p = 0; p < n3; ++p) {
+                double A[3][3];
+                for (int d = 0; d < 3; ++d) for (int c = 0; c < 3; ++c) A[d][c] = dXG[(c * 3 + d) * n3 + p];
+                double cx = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+                double cy = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+                double cz = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+                m->J[(size_t)e * n3 + p] = A[0][0] * cx + A[0][1] * cy + A[0][2] * cz;
+            }
+            free(dXG);
+        }
+    }
+    /* own face metrics: Ja^d at the Lobatto boundary nodes xi_d = -1 (side 0)
+     * and +1 (side 1), interpolated to the face points of the solution nodes */
+    double I2[256];
+    for (int t = 0; t < n; ++t) orc_lagrange_at(n, xL, m->xi[t], I2 + t * n);
+    for (int e = 0; e < m->E; ++e)
+    for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+    for (int c = 0; c < 3; ++c) {
+        int d0, d1;
+        face_dirs(d, &d0, &d1);
+        double fL[256];
+        for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+            int idx[3];
+            idx[d] = side ? N : 0;
+            idx[d0] = ta;
+            idx[d1] = tb;
+            fL[ta + n * tb] = JaL[(((size_t)e * 3 + d) * 3 + c) * n3 + node_index(n, idx[0], idx[1], idx[2])];
+        }
+        double *out = m->Sf + ((((size_t)e * 3 + d) * 2 + side) * 3 + c) * n2;
+        if (b->nodes == 0) { memcpy(out, fL, sizeof(double) * n2); continue; }
+        double t1[256];
+        for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+            double acc = 0.0;
+            for (int s = 0; s < n; ++s) acc += I2[ta * n + s] * fL[s + n * tb];
+            t1[ta + n * tb] = acc;
+        }
+        for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+            double acc = 0.0;
+            for (int s = 0; s < n; ++s) acc += I2[tb * n + s] * t1[ta + n * s];
+            out[ta + n * tb] = acc;
+        }
+    }
+    free(XL); free(JaL); free(JL);
     return m;
 }
 
 void orc_mesh_destroy(orc_mesh *m)
 {
     if (!m) return;
-    free(m->X); free(m->Ja); free(m->J); free(m);
+    free(m->X); free(m->Ja); free(m->J); free(m->Sf); free(m);
 }
 
 int orc_mesh_E(const orc_mesh *m) { return m->E; }
@@ -820,8 +987,11 @@ static void surface_flux(int kind, const double *uin, const double *uout, const 
  *   surface        S = (1/w_end) [ +-(F^*(L,R; Sn_L) - F_v^*.Sn_L) - (F_e - F_v)(in).(+-Ja^d_in) ]
  * on each face node (+ on the element's +d face, - on its -d face),
  * F_v^* = (F_v(L) + F_v(R))/2 (BR1), Sn_L = Ja^d of the face's minus-side element. */
+static int residual_general(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *dudt);
+
 int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *dudt)
 {
+    if (m->box.nodes == 1) return residual_general(m, cfg, u, dudt);
     int n = m->n, n3 = m->n3, E = m->E, N = n - 1;
     double g = cfg->gamma;
     int ns = (cfg->physics == 1);
@@ -940,10 +1110,218 @@ int orc_residual(const orc_mesh *m, const orc_cfg *cfg, const double *u, double 
 }
 
 /* BR1 gradients exposed for tests: grad[e][v][c][node]. */
+/* ------------------------------------------------------------------------ */
+/* Residual with the face interpolation written out (any nodal set; the only  */
+/* form for Gauss-Legendre nodes)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Node (i, j, k) of the line along d through face point (ta, tb), index m. */
+static int line_index(int n, int d, int m, int ta, int tb)
+{
+    int d0, d1, idx[3];
+    face_dirs(d, &d0, &d1);
+    idx[d] = m;
+    idx[d0] = ta;
+    idx[d1] = tb;
+    return node_index(n, idx[0], idx[1], idx[2]);
+}
+
+/* Value at the face xi_d = side (side -1 or +1) of the nodal field f of one
+ * element (stride n3 between variables), on the line through (ta, tb):
+ *   f(side) = sum_j l_j(side) f_j. */
+static double face_value(const orc_mesh *m, const double *f, int d, int side, int ta, int tb)
+{
+    const double *l = (side > 0) ? m->rb : m->lb;
+    double acc = 0.0;
+    for (int j = 0; j < m->n; ++j) acc += l[j] * f[line_index(m->n, d, j, ta, tb)];
+    return acc;
+}
+
+static const double *own_face_metric(const orc_mesh *m, int e, int d, int side, int c)
+{
+    return m->Sf + ((((size_t)e * 3 + d) * 2 + (side > 0 ? 1 : 0)) * 3 + c) * m->n * m->n;
+}
+
+/* BR1 gradients with interpolated traces (strong form, any nodes):
+ *   J grad q_c = sum_d D_d (Ja^d_c q)
+ *              + sum_faces (l_i(side)/w_i) side [ q* Sf_c - (Ja^d_c q)(side) ],
+ * q* = (q(u_in(side)) + q(u_out(side)))/2 from the interpolated conserved
+ * traces of the two elements, Sf the element's own face metric, and
+ * (Ja^d_c q)(side) the interpolated product.  On Gauss-Lobatto nodes
+ * l(side) is a unit vector and this is br1_gradients. */
+static void br1_gradients_general(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *grad)
+{
+    int n = m->n, n3 = m->n3, E = m->E;
+    double g = cfg->gamma;
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < E; ++e) {
+        double *q = (double *)malloc(sizeof(double) * NGRAD * n3);
+        double *f = (double *)malloc(sizeof(double) * 3 * n3);
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], qp[NGRAD];
+            for (int v = 0; v < NVAR; ++v) up[v] = u[((size_t)e * NVAR + v) * n3 + p];
+            grad_vars(up, g, qp);
+            for (int v = 0; v < NGRAD; ++v) q[v * n3 + p] = qp[v];
+        }
+        for (int v = 0; v < NGRAD; ++v)
+        for (int c = 0; c < 3; ++c) {
+            for (int d = 0; d < 3; ++d)
+                for (int p = 0; p < n3; ++p)
+                    f[d * n3 + p] = m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p] * q[v * n3 + p];
+            for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+                int p = node_index(n, i, j, k);
+                double acc = 0.0;
+                for (int d = 0; d < 3; ++d) acc += dir_derivative(n, m->D, f + d * n3, d, i, j, k);
+                grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p] = acc;
+            }
+        }
+        for (int d = 0; d < 3; ++d)
+        for (int side = -1; side <= 1; side += 2) {
+            int nb = neighbour(&m->box, e, d, side);
+            const double *l = (side > 0) ? m->rb : m->lb;
+            for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+                double uin[NVAR], uout[NVAR], qin[NGRAD], qout[NGRAD];
+                for (int v = 0; v < NVAR; ++v) {
+                    uin[v] = face_value(m, u + ((size_t)e * NVAR + v) * n3, d, side, ta, tb);
+                    uout[v] = face_value(m, u + ((size_t)nb * NVAR + v) * n3, d, -side, ta, tb);
+                }
+                grad_vars(uin, g, qin);
+                grad_vars(uout, g, qout);
+                for (int v = 0; v < NGRAD; ++v)
+                for (int c = 0; c < 3; ++c) {
+                    for (int jj = 0; jj < n; ++jj) {
+                        int pj = line_index(n, d, jj, ta, tb);
+                        f[pj] = m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + pj] * q[v * n3 + pj];
+                    }
+                    double jaq = face_value(m, f, d, side, ta, tb);
+                    double sf = own_face_metric(m, e, d, side, c)[ta + n * tb];
+                    double flux = side * (0.5 * (qin[v] + qout[v]) * sf - jaq);
+                    for (int i = 0; i < n; ++i) {
+                        int pi = line_index(n, d, i, ta, tb);
+                        grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + pi] += l[i] / m->w[i] * flux;
+                    }
+                }
+            }
+        }
+        for (int v = 0; v < NGRAD; ++v)
+            for (int c = 0; c < 3; ++c)
+                for (int p = 0; p < n3; ++p)
+                    grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p] /= m->J[(size_t)e * n3 + p];
+        free(q); free(f);
+    }
+}
+
+/* Residual with interpolated traces (strong form, standard volume term):
+ *   du/dt = -(1/J) [ sum_d D_d F~^d
+ *                    + sum_faces (l_i(side)/w_i) side (F* - F~^d(side)) ],
+ * F~^d(side) = sum_j l_j(side) F~^d_j the element's own contravariant flux
+ * (Euler minus viscous) interpolated to the face, F* the single-valued
+ * numerical flux of the face (Eq. NS4) from the interpolated conserved
+ * traces of its two elements with the scaled normal Sf of its minus-side
+ * element (BR1 viscous part (F_v(L) + F_v(R))/2 . Sf with interpolated
+ * gradient traces).  On Gauss-Lobatto nodes this is the standard-form
+ * orc_residual. */
+static int residual_general(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *dudt)
+{
+    if (cfg->volume_form != 0) return -2;   /* split forms need the Gauss-Lobatto SBP property */
+    int n = m->n, n3 = m->n3, E = m->E;
+    double g = cfg->gamma;
+    int ns = (cfg->physics == 1);
+    double mu = ns ? visc_mu(cfg) : 0.0, kappa = ns ? visc_kappa(cfg) : 0.0;
+    double *grad = NULL;
+    if (ns) {
+        grad = (double *)malloc(sizeof(double) * (size_t)E * NGRAD * 3 * n3);
+        if (!grad) return -1;
+        br1_gradients_general(m, cfg, u, grad);
+    }
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < E; ++e) {
+        double *Ft = (double *)malloc(sizeof(double) * 3 * NVAR * n3);
+        double *R = (double *)calloc(NVAR * n3, sizeof(double));
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], qp[NGRAD], G[12];
+            for (int v = 0; v < NVAR; ++v) up[v] = u[((size_t)e * NVAR + v) * n3 + p];
+            if (ns) {
+                grad_vars(up, g, qp);
+                for (int v = 0; v < NGRAD; ++v)
+                    for (int c = 0; c < 3; ++c) G[v * 3 + c] = grad[(((size_t)e * NGRAD + v) * 3 + c) * n3 + p];
+            }
+            for (int d = 0; d < 3; ++d) {
+                double a[3], fe[NVAR], fv[NVAR] = {0, 0, 0, 0, 0};
+                for (int c = 0; c < 3; ++c) a[c] = m->Ja[(((size_t)e * 3 + d) * 3 + c) * n3 + p];
+                orc_flux_euler(up, a, g, fe);
+                if (ns) orc_flux_visc(qp, G, mu, kappa, a, fv);
+                for (int v = 0; v < NVAR; ++v) Ft[(d * NVAR + v) * n3 + p] = fe[v] - fv[v];
+            }
+        }
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            int p = node_index(n, i, j, k);
+            for (int d = 0; d < 3; ++d)
+                for (int v = 0; v < NVAR; ++v)
+                    R[v * n3 + p] += dir_derivative(n, m->D, Ft + (d * NVAR + v) * n3, d, i, j, k);
+        }
+        for (int d = 0; d < 3; ++d)
+        for (int side = -1; side <= 1; side += 2) {
+            int nb = neighbour(&m->box, e, d, side);
+            int eL = (side > 0) ? e : nb, eR = (side > 0) ? nb : e;
+            const double *l = (side > 0) ? m->rb : m->lb;
+            for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+                double uL[NVAR], uR[NVAR], Sn[3], fstar[NVAR];
+                for (int v = 0; v < NVAR; ++v) {
+                    uL[v] = face_value(m, u + ((size_t)eL * NVAR + v) * n3, d, +1, ta, tb);
+                    uR[v] = face_value(m, u + ((size_t)eR * NVAR + v) * n3, d, -1, ta, tb);
+                }
+                for (int c = 0; c < 3; ++c) Sn[c] = own_face_metric(m, eL, d, +1, c)[ta + n * tb];
+                surface_flux(cfg->surface_flux, uL, uR, Sn, g, fstar);
+                if (ns) {
+                    double qL[NGRAD], qR[NGRAD], GL[12], GR[12], fvL[NVAR], fvR[NVAR];
+                    grad_vars(uL, g, qL);
+                    grad_vars(uR, g, qR);
+                    for (int v = 0; v < NGRAD; ++v)
+                        for (int c = 0; c < 3; ++c) {
+                            GL[v * 3 + c] = face_value(m, grad + (((size_t)eL * NGRAD + v) * 3 + c) * n3, d, +1, ta, tb);
+                            GR[v * 3 + c] = face_value(m, grad + (((size_t)eR * NGRAD + v) * 3 + c) * n3, d, -1, ta, tb);
+                        }
+                    orc_flux_visc(qL, GL, mu, kappa, Sn, fvL);
+                    orc_flux_visc(qR, GR, mu, kappa, Sn, fvR);
+                    for (int v = 0; v < NVAR; ++v) fstar[v] -= 0.5 * (fvL[v] + fvR[v]);
+                }
+                for (int v = 0; v < NVAR; ++v) {
+                    double own = face_value(m, Ft + (d * NVAR + v) * n3, d, side, ta, tb);
+                    double flux = side * (fstar[v] - own);
+                    for (int i = 0; i < n; ++i)
+                        R[v * n3 + line_index(n, d, i, ta, tb)] += l[i] / m->w[i] * flux;
+                }
+            }
+        }
+        for (int v = 0; v < NVAR; ++v)
+            for (int p = 0; p < n3; ++p)
+                dudt[((size_t)e * NVAR + v) * n3 + p] = -R[v * n3 + p] / m->J[(size_t)e * n3 + p];
+        free(Ft); free(R);
+    }
+    free(grad);
+    return 0;
+}
+
+/* The residual through the interpolated-trace path on any mesh (tests run it
+ * on Gauss-Lobatto meshes against orc_residual). */
+int orc_residual_nodal(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *dudt)
+{
+    return residual_general(m, cfg, u, dudt);
+}
+
 int orc_gradients(const orc_mesh *m, const orc_cfg *cfg, const double *u, double *grad)
 {
-    br1_gradients(m, cfg, u, grad);
+    if (m->box.nodes == 1) br1_gradients_general(m, cfg, u, grad);
+    else br1_gradients(m, cfg, u, grad);
     return 0;
+}
+
+void orc_mesh_faces(const orc_mesh *m, double *Sf, double *lb, double *rb)
+{
+    if (Sf) memcpy(Sf, m->Sf, sizeof(double) * (size_t)m->E * 18 * m->n * m->n);
+    if (lb) memcpy(lb, m->lb, sizeof(double) * m->n);
+    if (rb) memcpy(rb, m->rb, sizeof(double) * m->n);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1003,7 +1381,10 @@ void orc_lsrk3_stage(long long count, int k, double dt, double *u, double *g, co
  *               at n = 4 this equals cfl * 2 / (n * ...))
  *   viscous     dt_v = 12 / (n^4 * max_nodes (mu/rho) sum_d (|Ja^d|/J)^2)
  *               (= h^2/(nu n^4) on a straight box; Navier-Stokes only)
- *   dt = min(dt_c, dt_v). */
+ *   dt = min(dt_c, dt_v).
+ * On Gauss-Legendre nodes the spectral radius of the operator is about twice
+ * that on Gauss-Lobatto nodes (the boundary terms act on interpolated
+ * traces), so the constants 8 and 12 become 3 and 4. */
 double orc_dt(const orc_mesh *m, const orc_cfg *cfg, const double *u)
 {
     int n = m->n, n3 = m->n3, E = m->E;
@@ -1028,9 +1409,10 @@ double orc_dt(const orc_mesh *m, const orc_cfg *cfg, const double *u)
             if (sc > lam_c) lam_c = sc;
             if (mu * sv / rho > lam_v) lam_v = mu * sv / rho;
         }
-    double dt = cfg->cfl * 8.0 / ((double)n * n * lam_c);
+    double kc = (m->box.nodes == 1) ? 3.0 : 8.0, kv = (m->box.nodes == 1) ? 4.0 : 12.0;
+    double dt = cfg->cfl * kc / ((double)n * n * lam_c);
     if (lam_v > 0.0) {
-        double dtv = 12.0 / ((double)n * n * n * n * lam_v);
+        double dtv = kv / ((double)n * n * n * n * lam_v);
         if (dtv < dt) dt = dtv;
     }
     return dt;

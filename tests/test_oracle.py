@@ -1051,3 +1051,253 @@ def test_ismail_roe_volume_with_ec_surface_conserves_entropy(curved):
     u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
     ir = m.integrals(G, u, m.residual(O.Cfg("euler", "ec", "ir"), u))
     assert abs(ir[5]) < 1e-13 * ir[6]
+
+
+# --------------------------------------------------------------------------- Gauss-Legendre nodes (Sec. 3.3)
+
+def _golden_gauss():
+    rows = {}
+    with open(os.path.join(GOLD, "gauss_closed_forms.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            N, xs, ws = (s.strip() for s in line.split("|"))
+            ev = lambda s: float(eval(s, {"sqrt": np.sqrt}))  # noqa: E731  (closed-form expressions)
+            rows[int(N)] = ([ev(t) for t in xs.split(",")], [ev(t) for t in ws.split(",")])
+    return rows
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 3, 4])
+def test_gauss_closed_forms(N):
+    xs, ws = _golden_gauss()[N]
+    x, w = O.gauss(N)
+    assert np.allclose(x, xs, atol=1e-15, rtol=0)
+    assert np.allclose(w, ws, atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_gauss_quadrature_exactness_and_operators(N):
+    x, w = O.gauss(N)
+    for deg in range(0, 2 * N + 2):          # Gauss is exact through degree 2N+1
+        exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
+        assert abs(np.dot(w, x ** deg) - exact) < 2e-14
+    assert abs(np.dot(w, x ** (2 * N + 2)) - 2.0 / (2 * N + 3)) > 1e-8
+    assert np.abs(x).max() < 1.0             # no boundary nodes
+    D = O.dmatrix(N, x)
+    lm, lp = O.lagrange_at(x, -1.0), O.lagrange_at(x, 1.0)
+    for m in range(0, N + 1):
+        exact = m * x ** (m - 1) if m else np.zeros_like(x)
+        assert np.abs(D @ x ** m - exact).max() < 1e-11 * max(1, N ** 2)
+        assert abs(lm @ x ** m - (-1.0) ** m) < 1e-13 and abs(lp @ x ** m - 1.0) < 1e-13
+    # discrete integration by parts (the SBP property with boundary interpolation)
+    M = np.diag(w)
+    B = np.outer(lp, lp) - np.outer(lm, lm)
+    assert np.abs(M @ D + (M @ D).T - B).max() < 1e-12
+
+
+def _gauss_mesh(ex=3, ey=3, ez=3, N=3, amp=0.05, lo=(0,) * 3, hi=(10,) * 3):
+    return O.Mesh(ex, ey, ez, N, lo=lo, hi=hi, amp=amp, nodes="gauss")
+
+
+def test_gauss_mesh_straight_box_closed_form():
+    m = _gauss_mesh(2, 3, 4, 3, amp=0.0, lo=(0, 0, 0), hi=(4.0, 3.0, 2.0))
+    x, _ = O.gauss(3)
+    h = np.array([2.0, 1.0, 0.5])
+    for e in (0, 7, 23):
+        a = (e % 2, (e // 2) % 3, e // 6)
+        X0 = 0 + h[0] * (a[0] + 0.5 * (x + 1))
+        assert np.allclose(m.X[e, 0, 1, 2, :], X0, atol=1e-14)
+        for d in range(3):
+            J_d = np.prod(h) / 8 / (h[d] / 2)
+            assert np.allclose(m.Ja[e, d, d], J_d, atol=1e-14)
+            for c in range(3):
+                if c != d:
+                    assert np.abs(m.Ja[e, d, c]).max() < 1e-14
+        assert np.allclose(m.J[e], np.prod(h) / 8, atol=1e-14)
+
+
+def test_gauss_mesh_metric_identity_and_watertight_faces():
+    m = _gauss_mesh(3, 3, 3, 4, amp=0.08)
+    n = m.n
+    D = m.D
+    for e in range(m.E):
+        for c in range(3):
+            div = (np.einsum("im,kjm->kji", D, m.Ja[e, 0, c])
+                   + np.einsum("jm,kmi->kji", D, m.Ja[e, 1, c])
+                   + np.einsum("km,mji->kji", D, m.Ja[e, 2, c]))
+            assert np.abs(div).max() < 1e-12 * np.abs(m.Ja[e]).max()
+        for d in range(3):
+            nb = m.neighbour(e, d, +1)
+            # the +d face metric of e and the -d face metric of its neighbour coincide
+            # (to rounding at the periodic wrap, where the coordinates differ by the box length)
+            assert np.abs(m.Sf[e, d, 1] - m.Sf[nb, d, 0]).max() < 1e-13 * np.abs(m.Sf).max()
+    # the face metric is the element's own metric polynomial at the face
+    x, _ = O.gauss(4)
+    lp = O.lagrange_at(x, 1.0)
+    e = 5
+    face = np.einsum("i,ckji->ckj", lp, m.Ja[e, 0])     # Ja^0 at xi = +1, [c][k][j]
+    assert np.abs(face - m.Sf[e, 0, 1]).max() < 1e-12 * np.abs(face).max()
+
+
+def test_general_trace_path_equals_lobatto_residual():
+    """The interpolated-trace residual (the only one for Gauss nodes) on a
+    Gauss-Lobatto mesh, where the boundary interpolation is a unit vector,
+    equals the node-trace residual for every physics and surface flux."""
+    m = O.Mesh(3, 2, 2, 3, lo=(0,) * 3, hi=(10,) * 3, amp=0.08)
+    rng = np.random.default_rng(60)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    for physics in ("euler", "ns"):
+        for surface in ("lf", "roe", "ec", "matrix"):
+            cfg = O.Cfg(physics, surface, "standard", Re=50.0)
+            a = m.residual(cfg, u)
+            b = m.residual_nodal(cfg, u)
+            assert np.abs(a - b).max() < 1e-13 * np.abs(a).max(), (physics, surface)
+
+
+@pytest.mark.parametrize("surface", ["lf", "roe", "ec", "rusanov", "matrix"])
+def test_gauss_free_stream_and_conservation(surface):
+    m = _gauss_mesh(3, 3, 3, 3, amp=0.08)
+    st = np.array([1.2, 0.36, -0.24, 0.12, 2.6])
+    u = np.broadcast_to(st[None, :, None, None, None], m.shape).copy()
+    for physics in ("euler", "ns"):
+        assert np.abs(m.residual(O.Cfg(physics, surface, "standard", Re=50.0), u)).max() < 1e-12
+    rng = np.random.default_rng(61)
+    u = m.ic_tgv(Ma=0.3) * (1 + 0.05 * rng.standard_normal(m.shape))
+    r = m.residual(O.Cfg("ns", surface, "standard", Re=50.0), u)
+    tot = m.integrals(G, u, r)[:5]
+    mag = m.integrals(G, u, np.abs(r))[:5]
+    assert np.abs(tot / mag).max() < 1e-13
+
+
+def test_gauss_split_form_is_rejected():
+    m = _gauss_mesh(2, 2, 2, 2)
+    with pytest.raises(ValueError):
+        m.residual(O.Cfg("euler", "roe", "ec"), np.ones(m.shape))
+
+
+def test_gauss_spectral_convergence_density_wave():
+    errs_g, errs_l = [], []
+    for N in (2, 3, 4, 5, 6):
+        for nodes, errs in (("gauss", errs_g), ("lobatto", errs_l)):
+            mm = O.Mesh(3, 3, 3, N, lo=(0,) * 3, hi=(10,) * 3, amp=0.05, nodes=nodes)
+            d = 1e-5
+            exact = (_wave(mm, d) - _wave(mm, -d)) / (2 * d)
+            errs.append(_rel(mm.residual(O.Cfg("euler", "roe", "standard"), _wave(mm, 0.0)), exact))
+    assert errs_g[-1] < 2e-3
+    assert all(b < 0.4 * a for a, b in zip(errs_g, errs_g[1:]))
+
+
+def test_gauss_br1_exact_for_polynomial_fields_and_tgv_dissipation():
+    """On a straight Gauss mesh the BR1 gradient of a field whose gradient
+    variables are polynomials of degree <= N is exact; on the TGV the
+    kinetic-energy rate of one residual is -3/(4 Re)."""
+    # a single periodic element per direction with fields that are
+    # polynomials of degree <= N in each direction and periodic across the
+    # box: a constant plus a multiple of (x - lo)(x - hi) is not periodic, so
+    # use fields whose gradient variables are linear in one direction and
+    # constant across the wrap of the others: v1 = a + b y on a box that is
+    # one element thick in y has a jump at the wrap; instead take one element
+    # per direction and compare against the exact gradient where the field
+    # is continuous across the wrap (the quadratic y (L - y) vanishes at both ends)
+    L = 2.0
+    m = _gauss_mesh(1, 1, 1, 4, amp=0.0, lo=(0,) * 3, hi=(L, L, L))
+    X = m.X
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    rho = np.full_like(x, 1.3)
+    s = lambda t: t * (L - t)                     # noqa: E731  (continuous across the periodic wrap)
+    ds = lambda t: L - 2 * t                      # noqa: E731
+    v = [0.1 * s(y), 0.05 * s(z), 0.02 * s(x)]
+    T = 1.0 + 0.01 * s(x) * s(z)
+    p = rho * T
+    u = np.zeros(m.shape)
+    u[:, 0] = rho
+    for c in range(3):
+        u[:, 1 + c] = rho * v[c]
+    u[:, 4] = p / (G - 1) + 0.5 * rho * sum(vc * vc for vc in v)
+    grad = m.gradients(O.Cfg("ns", "roe", "standard", Re=100.0), u)
+    exact = np.zeros_like(grad)
+    exact[:, 0, 1] = 0.1 * ds(y)
+    exact[:, 1, 2] = 0.05 * ds(z)
+    exact[:, 2, 0] = 0.02 * ds(x)
+    exact[:, 3, 0] = 0.01 * ds(x) * s(z)
+    exact[:, 3, 2] = 0.01 * s(x) * ds(z)
+    assert np.abs(grad - exact).max() < 1e-12
+    mm = _gauss_mesh(4, 4, 4, 5, amp=0.05, lo=(-np.pi,) * 3, hi=(np.pi,) * 3)
+    u = mm.ic_tgv(G, 0.1)
+    Re = 1000.0
+    r = mm.residual(O.Cfg("ns", "ec", "standard", Re=Re), u)
+    ke_rate = mm.integrals(G, u, r)
+    # kinetic energy rate from the momentum and mass rates: d/dt (|m|^2/(2 rho))
+    rho_, mv = u[:, 0], u[:, 1:4]
+    dke = (mv * r[:, 1:4]).sum(1) / rho_ - 0.5 * (mv * mv).sum(1) / rho_ ** 2 * r[:, 0]
+    w3 = np.einsum("i,j,k->kji", mm.w, mm.w, mm.w)
+    rate = (mm.J * w3 * dke).sum() / (2 * np.pi) ** 3
+    assert abs(rate + 3 / (4 * Re)) < 0.03 * 3 / (4 * Re)
+    del ke_rate
+
+
+def _dg_advection_1d(N, nodes, K=6, h=1.0):
+    """1-D strong-form DG operator of u_t + u_x = 0 (upwind flux) on K
+    periodic elements with interpolated traces, from the oracle's nodes, D
+    and boundary interpolation (reduces to _dgsem_advection_1d on Lobatto)."""
+    x, w = O.gauss(N) if nodes == "gauss" else O.lgl(N)
+    D = O.dmatrix(N, x)
+    lb, rb = O.lagrange_at(x, -1.0), O.lagrange_at(x, 1.0)
+    n = N + 1
+    L = np.zeros((K * n, K * n))
+    for k in range(K):
+        s = slice(k * n, (k + 1) * n)
+        sm = slice(((k - 1) % K) * n, ((k - 1) % K) * n + n)
+        L[s, s] -= (2 / h) * (D + np.outer(lb / w, lb))
+        L[s, sm] += (2 / h) * np.outer(lb / w, rb)
+    return L
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_gauss_operator_and_its_dt_rule(N):
+    """The interpolated-trace operator on Lobatto nodes is the node-trace one;
+    on Gauss nodes its spectral radius is about twice as large, and the
+    Gauss dt constant 3 (instead of 8) keeps twice every dt*mu inside the RK3
+    stability region while 8 would not."""
+    assert np.abs(_dg_advection_1d(N, "lobatto") - _dgsem_advection_1d(N)).max() < 1e-12 * (N + 1) ** 2
+    mu = np.linalg.eigvals(_dg_advection_1d(N, "gauss"))
+    n = N + 1
+
+    def amp(z):
+        return abs(1 + z + z * z / 2 + z ** 3 / 6)
+
+    dt = 0.5 * 3 / (n * n * 2.0)
+    assert max(amp(2 * dt * m) for m in mu) <= 1 + 1e-9
+    assert max(amp(2 * (0.5 * 8 / (n * n * 2.0)) * m) for m in mu) > 1
+    # the Gauss dt rule as the oracle applies it on a straight box
+    m = O.Mesh(4, 4, 4, N, lo=(0,) * 3, hi=(8.0,) * 3, nodes="gauss")
+    st = np.array([1.3, 1.3 * 0.4, 1.3 * -0.2, 1.3 * 0.1, 0.0])
+    v = st[1:4] / st[0]
+    p = 0.9
+    st[4] = p / (G - 1) + 0.5 * st[0] * v @ v
+    u = np.zeros(m.shape)
+    u[:] = st[None, :, None, None, None]
+    c = np.sqrt(G * p / st[0])
+    dtc = 0.5 * 3 * (2.0 / 2) / (n * n * (np.abs(v).sum() + 3 * c))   # h = 2
+    assert abs(m.dt(O.Cfg("euler", cfl=0.5), u) - dtc) < 1e-12 * dtc
+
+
+def test_gauss_vortex_steps_converge_and_stay_bounded():
+    """RK3 on a curved Gauss mesh: the isentropic vortex advances stably with
+    the Gauss dt rule, and its error against the exact solution at t = 0.5
+    falls with N."""
+    errs = []
+    for N in (3, 5):
+        m = O.Mesh(4, 4, 1, N, lo=(0, 0, 0), hi=(10, 10, 2.5), amp=0.0, nodes="gauss")
+        cfg = O.Cfg("euler", "roe", "standard")
+        u = m.ic_vortex(G, 0.5, 5.0)
+        gg = np.zeros_like(u)
+        t = 0.0
+        while t < 0.5 - 1e-12:
+            dt = min(m.dt(cfg, u), 0.5 - t)
+            m.rk3_step(cfg, u, gg, dt=dt)
+            t += dt
+        exact = m.ic_vortex(G, 0.5, 5.0, t=0.5)
+        errs.append(_rel(u, exact))
+        assert np.isfinite(u).all()
+    assert errs[1] < 0.3 * errs[0], errs
