@@ -104,6 +104,10 @@ enum { HS3D_TIME_RK3 = 0, HS3D_TIME_RK4 = 1 };
 enum { HS3D_FP64 = 0, HS3D_MIXED32 = 1 };
 /* initial conditions */
 enum { HS3D_IC_VORTEX = 0, HS3D_IC_TGV = 1 };
+/* solution nodes (Sec. 3.3): Gauss-Lobatto, or Gauss-Legendre (standard
+ * volume term only: the split forms need the Gauss-Lobatto summation-by-parts
+ * property) */
+enum { HS3D_NODES_LOBATTO = 0, HS3D_NODES_GAUSS = 1 };
 
 /* Mesh of a periodic box [lo, hi] with ex*ey*ez hexahedra of degree N
  * (1 <= N <= 7) on Gauss-Lobatto nodes (Sec. 3.1, 3.3).  Every node is moved
@@ -113,7 +117,13 @@ enum { HS3D_IC_VORTEX = 0, HS3D_IC_TGV = 1 };
  * node_xyz, if not NULL, is a HOST FP64 array [E][3][n][n][n] of node
  * coordinates that replaces the generator (the box must still be periodic and
  * the faces of neighbouring elements must coincide).  periodic[] must be all
- * 1 (other boundaries: HS3D_ERR_UNSUPPORTED). */
+ * 1 (other boundaries: HS3D_ERR_UNSUPPORTED).
+ * nodes: HS3D_NODES_LOBATTO (zero) or HS3D_NODES_GAUSS.  The element map is
+ * always the degree-N interpolant through the Gauss-Lobatto points (generator
+ * or node_xyz); on Gauss nodes the state, X, Ja and J live at the
+ * Gauss-Legendre points: Ja^d is the curl-form metric polynomial evaluated
+ * there, J = det(dX/dxi) of the map, the face metrics its values at the face
+ * points. */
 typedef struct {
     int ex, ey, ez;
     int N;
@@ -121,6 +131,7 @@ typedef struct {
     int periodic[3];
     double perturb_amp;
     const double *node_xyz;
+    int nodes;
 } hs3d_mesh_desc;
 
 /* Solver configuration.  gamma: ratio of specific heats; Re, Pr: Reynolds and

@@ -24,6 +24,7 @@ EULER, NS = 0, 1
 FLUX_LF, FLUX_ROE, FLUX_EC, FLUX_RUSANOV, FLUX_LDROE, FLUX_MATRIX = 0, 1, 2, 3, 4, 5
 VOL_STANDARD, VOL_EC, VOL_KG, VOL_PIROZZOLI, VOL_DUCROS, VOL_MORINISHI, VOL_IR = 0, 1, 2, 3, 4, 5, 6
 TIME_RK3, TIME_RK4 = 0, 1
+NODES_LOBATTO, NODES_GAUSS = 0, 1
 FP64, MIXED32 = 0, 1
 IC_VORTEX, IC_TGV = 0, 1
 
@@ -33,6 +34,7 @@ SURFACE = {"lf": FLUX_LF, "roe": FLUX_ROE, "ec": FLUX_EC, "rusanov": FLUX_RUSANO
 VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC, "kg": VOL_KG, "pirozzoli": VOL_PIROZZOLI, "ducros": VOL_DUCROS,
           "morinishi": VOL_MORINISHI, "ir": VOL_IR}
 TIME = {"rk3": TIME_RK3, "rk4": TIME_RK4}
+NODES = {"lobatto": NODES_LOBATTO, "gauss": NODES_GAUSS}
 PRECISION = {"fp64": FP64, "mixed32": MIXED32}
 
 # every entry point declared in include/hs3d.h
@@ -52,7 +54,7 @@ class HS3DError(RuntimeError):
 class MeshDesc(C.Structure):
     _fields_ = [("ex", C.c_int), ("ey", C.c_int), ("ez", C.c_int), ("N", C.c_int),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int * 3),
-                ("perturb_amp", C.c_double), ("node_xyz", C.c_void_p)]
+                ("perturb_amp", C.c_double), ("node_xyz", C.c_void_p), ("nodes", C.c_int)]
 
 
 class SolverCfg(C.Structure):
@@ -156,16 +158,19 @@ def solver_cfg(physics="euler", surface="lf", volume="standard", precision="fp64
                      gamma, Re, Pr, Ma, cfl, TIME[time])
 
 
-def mesh_desc(ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None) -> MeshDesc:
+def mesh_desc(ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None,
+              nodes="lobatto") -> MeshDesc:
     return MeshDesc(ex, ey, ez, N, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int * 3)(1, 1, 1),
-                    amp, node_xyz)
+                    amp, node_xyz, NODES[nodes])
 
 
 class Mesh:
     """A library-owned mesh on the current CUDA device (``hs3d_mesh_create``)."""
 
-    def __init__(self, ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None):
+    def __init__(self, ex, ey, ez, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0, node_xyz=None,
+                 nodes="lobatto"):
         self.ex, self.ey, self.ez, self.N = ex, ey, ez, N
+        self.nodes = nodes
         self.n = N + 1
         self.E = ex * ey * ez
         self.lo, self.hi = tuple(lo), tuple(hi)
@@ -175,7 +180,7 @@ class Mesh:
             import numpy as np
             keep = np.ascontiguousarray(node_xyz, dtype=np.float64)
             xyz = keep.ctypes.data
-        d = mesh_desc(ex, ey, ez, N, lo, hi, amp, xyz)
+        d = mesh_desc(ex, ey, ez, N, lo, hi, amp, xyz, nodes)
         h = C.c_void_p()
         check(lib().hs3d_mesh_create(C.byref(d), C.byref(h)))
         self._h = h

@@ -35,6 +35,7 @@ cudaError_t prepare_kernels(int N)
     if (!device_ops(N)) return cudaErrorMemoryAllocation;
     cudaError_t e = prepare_volume(N);
     if (e == cudaSuccess) e = prepare_grad(N);
+    if (e == cudaSuccess) e = prepare_gauss(N);
     return e;
 }
 
@@ -70,16 +71,28 @@ hs3d_status validate_desc(const hs3d_mesh_desc *d)
     }
     if (!(d->perturb_amp >= 0.0 && d->perturb_amp <= 0.2))
         return fail(HS3D_ERR_INVALID, "perturb_amp must lie in [0, 0.2]");
+    if (d->nodes != HS3D_NODES_LOBATTO && d->nodes != HS3D_NODES_GAUSS)
+        return fail(HS3D_ERR_INVALID, "bad nodes %d", d->nodes);
     return HS3D_OK;
 }
 
-size_t mesh_bytes(int N, long long E)
+size_t mesh_bytes(int N, long long E, int nodes)
 {
     long long n = N + 1, n2 = n * n, n3 = n2 * n;
     size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) + sizeof(float) * (size_t)E * n3 * 15 +
                  (sizeof(double) + sizeof(float)) * 3 * (size_t)E * 3 * n2;
     size_t scratch = sizeof(double) * (3 * (size_t)E * 5 * n2 + (size_t)E * 12 * n3);
-    return geo + scratch + sizeof(Clock) + 4096 * 7 * sizeof(double);
+    // Gauss-Legendre meshes hold Gauss-Lobatto temporaries while they are built
+    size_t build = (nodes == HS3D_NODES_GAUSS) ? sizeof(double) * ((size_t)E * 21 * n3 + 9 * (size_t)E * n2) : 0;
+    return geo + scratch + build + sizeof(Clock) + 4096 * 7 * sizeof(double);
+}
+
+hs3d_status check_mesh_cfg(const hs3d_mesh *m, const hs3d_solver_cfg *c)
+{
+    if (m->nodes == HS3D_NODES_GAUSS && c->volume_form != HS3D_VOL_STANDARD)
+        return fail(HS3D_ERR_UNSUPPORTED,
+                    "split volume forms need Gauss-Lobatto nodes (summation-by-parts with boundary nodes)");
+    return HS3D_OK;
 }
 
 static hs3d_status mesh_alloc(hs3d_mesh *m)
@@ -145,6 +158,7 @@ hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out)
         m->hi[c] = desc->hi[c];
     }
     m->amp = desc->perturb_amp;
+    m->nodes = desc->nodes;
     cudaError_t e = cudaGetDevice(&m->device);
     if (e != cudaSuccess) {
         delete m;
@@ -176,7 +190,12 @@ hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out)
             return cuda_fail(e, "uploading node_xyz");
         }
     }
-    e = launch_geometry(m->N, xyz_dev, m->ex, m->ey, m->ez, m->lo, m->hi, m->amp, m->X, m->Ja, m->Jaf, m->J, m->invJ,
+    if (!device_ops(m->N, m->nodes)) {
+        if (xyz_dev) cudaFree(xyz_dev);
+        mesh_free(m);
+        return fail(HS3D_ERR_NOMEM, "operator tables");
+    }
+    e = launch_geometry(m->N, m->nodes, xyz_dev, m->ex, m->ey, m->ez, m->lo, m->hi, m->amp, m->X, m->Ja, m->Jaf, m->J, m->invJ,
                         m->invJf, m->fn, m->fnf, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->clk, 0, sizeof(Clock), m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
@@ -216,6 +235,9 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
     it.mu = (c && c->physics == HS3D_NS) ? 1.0 / c->Re : 0.0;
     it.kappa = (c && c->physics == HS3D_NS) ? it.mu * c->gamma / ((c->gamma - 1.0) * c->Pr) : 0.0;
     it.cfl = c ? c->cfl : 0.5;
+    it.gauss = m->nodes == HS3D_NODES_GAUSS;
+    it.kc = it.gauss ? 3.0 : 8.0;    // dt rule: cfl kc / (n^2 lambda_c), kv / (n^4 lambda_v)
+    it.kv = it.gauss ? 4.0 : 12.0;
     it.gm1 = it.gamma - 1.0;
     it.hg = 0.5 / it.gm1;
     it.gammaf = (float)it.gamma;
@@ -235,6 +257,7 @@ Batch single_batch(const Item &it)
     b.total_elems = it.E;
     b.total_faces = 3LL * it.E;
     b.dt_fixed = 0.0;
+    b.gauss = it.gauss;
     return b;
 }
 
@@ -338,6 +361,7 @@ hs3d_status hs3d_residual(const hs3d_mesh *m, const hs3d_solver_cfg *c, const do
 {
     if (!m) return fail(HS3D_ERR_INVALID, "mesh is NULL");
     hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st == HS3D_OK) st = check_ptr(u, "u");
     if (st == HS3D_OK) st = check_ptr(dudt, "dudt");
     if (st != HS3D_OK) return st;
@@ -354,6 +378,7 @@ hs3d_status hs3d_rk3_step(const hs3d_mesh *m, const hs3d_solver_cfg *c, double *
 {
     if (!m) return fail(HS3D_ERR_INVALID, "mesh is NULL");
     hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st == HS3D_OK) st = check_ptr(u, "u");
     if (st == HS3D_OK) st = check_ptr(g, "g");
     if (st != HS3D_OK) return st;
@@ -369,6 +394,7 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
     hs3d_mesh *m = const_cast<hs3d_mesh *>(mc);
     if (!m) return fail(HS3D_ERR_INVALID, "mesh is NULL");
     hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st == HS3D_OK) st = check_ptr(u, "u");
     if (st == HS3D_OK) st = check_ptr(g, "g");
     if (st != HS3D_OK) return st;
@@ -420,6 +446,7 @@ hs3d_status hs3d_dt(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *
 {
     if (!m) return fail(HS3D_ERR_INVALID, "mesh is NULL");
     hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st == HS3D_OK) st = check_ptr(u, "u");
     if (st == HS3D_OK && !dt_out) st = fail(HS3D_ERR_INVALID, "dt_out is NULL");
     if (st != HS3D_OK) return st;

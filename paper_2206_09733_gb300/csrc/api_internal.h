@@ -10,6 +10,7 @@
 struct hs3d_mesh {
     int ex = 0, ey = 0, ez = 0, N = 0, n = 0, n2 = 0, n3 = 0;
     int E = 0;
+    int nodes = HS3D_NODES_LOBATTO;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, amp = 0.0;
     int device = 0;
     double *X = nullptr, *Ja = nullptr, *J = nullptr, *invJ = nullptr, *fn = nullptr;
@@ -39,7 +40,8 @@ hs3d_status validate_cfg(const hs3d_solver_cfg *c);
 hs3d_status validate_desc(const hs3d_mesh_desc *d);
 hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out);
 void mesh_free(hs3d_mesh *m);
-size_t mesh_bytes(int N, long long E);
+size_t mesh_bytes(int N, long long E, int nodes);
+hs3d_status check_mesh_cfg(const hs3d_mesh *m, const hs3d_solver_cfg *c);
 Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, double *g, double *out);
 Batch single_batch(const Item &it);
 cudaError_t enqueue_stage(int N, const hs3d_solver_cfg *c, const Batch &b, int stage, int lam_slot, cudaStream_t s);

@@ -331,6 +331,7 @@ cudaError_t prepare_grad(int N)
 
 cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, cudaStream_t s)
 {
+    if (b.gauss) return launch_face_gauss(N, prec, physics, flux, b, s);
 #define F64(K) face_launch<K, double>(physics, flux, b, s)
 #define F32(K) face_launch<K, float>(physics, flux, b, s)
     if (prec == HS3D_FP64) {
@@ -344,6 +345,7 @@ cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, 
 
 cudaError_t launch_grad(int N, int prec, const Batch &b, cudaStream_t s)
 {
+    if (b.gauss) return launch_grad_gauss(N, prec, b, s);
 #define G64(K) grad_launch<K, double>(b, s)
 #define G32(K) grad_launch<K, float>(b, s)
     if (prec == HS3D_FP64) {

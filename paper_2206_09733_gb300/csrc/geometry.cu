@@ -83,28 +83,133 @@ static Ops make_ops(int N)
         }
     o.iw0 = 1.0 / o.w[0];
     o.iw0f = (float)o.iw0;
+    // boundary interpolation: the end nodes themselves
+    o.gauss = 0;
+    for (int j = 0; j < n; ++j) {
+        o.lb[j] = (j == 0) ? 1.0 : 0.0;
+        o.rb[j] = (j == N) ? 1.0 : 0.0;
+        for (int s = 0; s < n; ++s) o.IL[j * n + s] = (j == s) ? 1.0 : 0.0;
+    }
     return o;
 }
 
-const Ops &host_ops(int N)
+// Gauss-Legendre operators for degree N (n = N+1 points):
+//   nodes  roots of L_n by Newton (L_n' from L_n' (x^2 - 1) = n (x L_n - L_{n-1})),
+//   weights 2 / ((1 - x^2) L_n'(x)^2),
+//   D_ij = L_n'(x_i) / (L_n'(x_j) (x_i - x_j)) (i != j), D_ii = x_i / (1 - x_i^2)
+//          (Legendre's equation at a root of L_n),
+//   l_j(+1) = 1 / (L_n'(x_j) (1 - x_j)),  l_j(-1) = (-1)^n / (L_n'(x_j) (-1 - x_j)),
+// and the Gauss-Lobatto basis of degree N at the Gauss points,
+//   l^L_s(x) = (x^2 - 1) L_N'(x) / (N (N+1) L_N(x_s) (x - x_s)).
+static Ops make_ops_gauss(int N)
+{
+    const Ops lob = make_ops(N);
+    Ops o{};
+    const int n = N + 1;
+    double dL[kMaxn];
+    for (int j = 0; j < n; ++j) {
+        double x = -cos(M_PI * (j + 0.75) / (n + 0.5));
+        double Lm, L, Lp, d = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            legendre3(n, x, Lm, L, Lp);   // L = L_n, Lm = L_{n-1}
+            d = n * (x * L - Lm) / (x * x - 1.0);
+            const double dx = L / d;
+            x -= dx;
+            if (fabs(dx) <= 1e-17) break;
+        }
+        legendre3(n, x, Lm, L, Lp);
+        d = n * (x * L - Lm) / (x * x - 1.0);
+        o.xi[j] = x;
+        dL[j] = d;
+    }
+    for (int j = 0; j < n / 2; ++j) {   // symmetrise
+        const double s = 0.5 * (o.xi[N - j] - o.xi[j]);
+        o.xi[j] = -s;
+        o.xi[N - j] = s;
+    }
+    if (n % 2) o.xi[N / 2] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double Lm, L, Lp;
+        legendre3(n, o.xi[j], Lm, L, Lp);
+        dL[j] = n * (o.xi[j] * L - Lm) / (o.xi[j] * o.xi[j] - 1.0);
+        o.w[j] = 2.0 / ((1.0 - o.xi[j] * o.xi[j]) * dL[j] * dL[j]);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double v = (i != j) ? dL[i] / (dL[j] * (o.xi[i] - o.xi[j])) : o.xi[i] / (1.0 - o.xi[i] * o.xi[i]);
+            o.D[i * n + j] = v;
+            o.Df[i * n + j] = (float)v;
+        }
+    o.iw0 = 0.0;
+    o.iw0f = 0.0f;
+    o.gauss = 1;
+    const double sgn = (n % 2) ? -1.0 : 1.0;
+    for (int j = 0; j < n; ++j) {
+        o.rb[j] = 1.0 / (dL[j] * (1.0 - o.xi[j]));
+        o.lb[j] = sgn / (dL[j] * (-1.0 - o.xi[j]));
+    }
+    for (int t = 0; t < n; ++t) {
+        const double x = o.xi[t];
+        double Lm, L, Lp;
+        legendre3(N, x, Lm, L, Lp);   // L = L_N, Lm = L_{N-1}
+        const double dLN = N * (x * L - Lm) / (x * x - 1.0);
+        for (int s = 0; s < n; ++s) {
+            const double xs = lob.xi[s];
+            double v;
+            if (fabs(x - xs) < 1e-15) {
+                v = 1.0;   // a Gauss point on a Gauss-Lobatto node (x = 0 for even N)
+            } else {
+                double Lms, Ls, Lps;
+                legendre3(N, xs, Lms, Ls, Lps);
+                v = (x * x - 1.0) * dLN / (N * (N + 1.0) * Ls * (x - xs));
+            }
+            o.IL[t * n + s] = v;
+        }
+    }
+    for (int j = 0; j < n; ++j) {
+        if (fabs(o.xi[j]) < 1e-15)   // zero row except the coincident node
+            for (int s = 0; s < n; ++s)
+                if (fabs(lob.xi[s]) >= 1e-15) o.IL[j * n + s] = 0.0;
+    }
+    return o;
+}
+
+static void finish_ops(Ops &o, int n)
+{
+    for (int j = 0; j < n; ++j) {
+        o.lbw[j] = o.lb[j] / o.w[j];
+        o.rbw[j] = o.rb[j] / o.w[j];
+        o.lbf[j] = (float)o.lb[j];
+        o.rbf[j] = (float)o.rb[j];
+        o.lbwf[j] = (float)o.lbw[j];
+        o.rbwf[j] = (float)o.rbw[j];
+    }
+}
+
+const Ops &host_ops(int N, int nodes)
 {
     static std::mutex mu;
-    static std::map<int, Ops> cache;
+    static std::map<std::pair<int, int>, Ops> cache;
     std::lock_guard<std::mutex> g(mu);
-    auto it = cache.find(N);
-    if (it == cache.end()) it = cache.emplace(N, make_ops(N)).first;
+    auto key = std::make_pair(N, nodes);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        Ops o = (nodes == HS3D_NODES_GAUSS) ? make_ops_gauss(N) : make_ops(N);
+        finish_ops(o, N + 1);
+        it = cache.emplace(key, o).first;
+    }
     return it->second;
 }
 
-const Ops *device_ops(int N)
+const Ops *device_ops(int N, int nodes)
 {
     static std::mutex mu;
     static std::map<std::pair<int, int>, Ops *> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    const Ops &h = host_ops(N);
+    const Ops &h = host_ops(N, nodes);
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_pair(dev, N);
+    auto key = std::make_pair(dev, N + 16 * nodes);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     Ops *d = nullptr;
@@ -124,7 +229,7 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
 k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, double lo1, double lo2, double hi0,
            double hi1, double hi2, double amp, const Ops *__restrict__ ops, double *__restrict__ X,
            double *__restrict__ Ja, float *__restrict__ Jaf, double *__restrict__ J, double *__restrict__ invJ,
-           float *__restrict__ invJf, double *__restrict__ fn, float *__restrict__ fnf)
+           float *__restrict__ invJf, double *__restrict__ fn, float *__restrict__ fnf, double *__restrict__ dXout)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     __shared__ double sD[n * n];
@@ -174,6 +279,9 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
     invJ[(size_t)e * n3 + p] = 1.0 / Jp;
     invJf[(size_t)e * n3 + p] = (float)(1.0 / Jp);
     for (int c = 0; c < 3; ++c) X[((size_t)e * 3 + c) * n3 + p] = x[c];
+    if (dXout)   // dX_c/dxi_d, [E][c*3 + d][n3] (Gauss-Legendre meshes evaluate it at their nodes)
+        for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) dXout[((size_t)e * 9 + c * 3 + d) * n3 + p] = a[d][c];
 
     for (int i = 0; i < 3; ++i) {
         const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
@@ -197,25 +305,137 @@ k_geometry(const double *__restrict__ xyz, int ex, int ey, int ez, double lo0, d
     }
 }
 
-cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
+// Gauss-Legendre meshes: the element map, the curl-form metric polynomials
+// and dX/dxi come from the Gauss-Lobatto construction above; here they are
+// evaluated at the Gauss points by tensor-product interpolation (three 1-D
+// passes with the Gauss-Lobatto basis, exact for these degree-N
+// polynomials), and J = det(dX/dxi) is formed there.
+template <int N>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
+k_geometry_gauss(const double *__restrict__ XL, const double *__restrict__ JaL, const double *__restrict__ dXL,
+                 const Ops *__restrict__ ops, double *__restrict__ X, double *__restrict__ Ja, float *__restrict__ Jaf,
+                 double *__restrict__ J, double *__restrict__ invJ, float *__restrict__ invJf)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    __shared__ double sI[n * n];
+    __shared__ double sA[n3], sB[n3];
+    const int e = blockIdx.x;
+    const int p = threadIdx.x;
+    const int i = p % n, j = (p / n) % n, k = p / n2;
+    for (int t = p; t < n * n; t += n3) sI[t] = ops->IL[t];
+    double dx[9];
+    for (int f = 0; f < 21; ++f) {
+        const double *src = (f < 3) ? XL + ((size_t)e * 3 + f) * n3
+                          : (f < 12) ? JaL + ((size_t)e * 9 + (f - 3)) * n3
+                                     : dXL + ((size_t)e * 9 + (f - 12)) * n3;
+        __syncthreads();
+        sA[p] = src[p];
+        __syncthreads();
+        double acc = 0.0;
+        for (int s = 0; s < n; ++s) acc += sI[i * n + s] * sA[s + n * (j + n * k)];
+        sB[p] = acc;
+        __syncthreads();
+        acc = 0.0;
+        for (int s = 0; s < n; ++s) acc += sI[j * n + s] * sB[i + n * (s + n * k)];
+        sA[p] = acc;
+        __syncthreads();
+        acc = 0.0;
+        for (int s = 0; s < n; ++s) acc += sI[k * n + s] * sA[i + n * (j + n * s)];
+        if (f < 3) {
+            X[((size_t)e * 3 + f) * n3 + p] = acc;
+        } else if (f < 12) {
+            Ja[((size_t)e * 9 + (f - 3)) * n3 + p] = acc;
+            Jaf[((size_t)e * 9 + (f - 3)) * n3 + p] = (float)acc;
+        } else {
+            dx[f - 12] = acc;
+        }
+    }
+    // a[d][c] = dx[c*3 + d]
+    const double Jp = dx[0] * (dx[4] * dx[8] - dx[7] * dx[5]) + dx[3] * (dx[7] * dx[2] - dx[1] * dx[8]) +
+                      dx[6] * (dx[1] * dx[5] - dx[4] * dx[2]);
+    J[(size_t)e * n3 + p] = Jp;
+    invJ[(size_t)e * n3 + p] = 1.0 / Jp;
+    invJf[(size_t)e * n3 + p] = (float)(1.0 / Jp);
+}
+
+// Face metrics at the face Gauss points: the Gauss-Lobatto face values of
+// Ja^d (which both neighbours share) interpolated in the two tangential
+// directions.  One thread per (d, e, c, face point).
+__global__ void k_facemetric_gauss(int n, long long total, const double *__restrict__ fnL, const Ops *__restrict__ ops,
+                                   double *__restrict__ fn, float *__restrict__ fnf)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int n2 = n * n;
+    const int ab = (int)(t % n2);
+    const long long row = t / n2;   // (d*E + e)*3 + c
+    const int ta = ab % n, tb = ab / n;
+    const double *F = fnL + row * n2;
+    double acc = 0.0;
+    for (int b = 0; b < n; ++b) {
+        double r = 0.0;
+        for (int a = 0; a < n; ++a) r += ops->IL[ta * n + a] * F[a + n * b];
+        acc += ops->IL[tb * n + b] * r;
+    }
+    fn[t] = acc;
+    fnf[t] = (float)acc;
+}
+
+cudaError_t launch_geometry(int N, int nodes, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
                             const double *hi, double amp, double *X, double *Ja, float *Jaf, double *J, double *invJ,
                             float *invJf, double *fn, float *fnf, cudaStream_t s)
 {
-    const Ops *ops = device_ops(N);
+    const Ops *ops = device_ops(N, HS3D_NODES_LOBATTO);
     if (!ops) return cudaErrorMemoryAllocation;
-    int E = ex * ey * ez;
-    int n3 = (N + 1) * (N + 1) * (N + 1);
+    const int E = ex * ey * ez;
+    const int n = N + 1, n2 = n * n, n3 = n2 * n;
+    const bool gauss = nodes == HS3D_NODES_GAUSS;
+    double *XL = X, *JaL = Ja, *fnL = fn, *dXL = nullptr;
+    if (gauss) {
+        const Ops *opsg = device_ops(N, HS3D_NODES_GAUSS);
+        if (!opsg) return cudaErrorMemoryAllocation;
+        XL = JaL = fnL = dXL = nullptr;
+        cudaError_t e = cudaMalloc(&XL, sizeof(double) * (size_t)E * 3 * n3);
+        if (e == cudaSuccess) e = cudaMalloc(&JaL, sizeof(double) * (size_t)E * 9 * n3);
+        if (e == cudaSuccess) e = cudaMalloc(&dXL, sizeof(double) * (size_t)E * 9 * n3);
+        if (e == cudaSuccess) e = cudaMalloc(&fnL, sizeof(double) * (size_t)3 * E * 3 * n2);
+        if (e != cudaSuccess) {
+            cudaFree(XL);
+            cudaFree(JaL);
+            cudaFree(dXL);
+            cudaFree(fnL);
+            return e;
+        }
+    }
 #define HS3D_GEO(NN)                                                                                            \
     case NN:                                                                                                    \
         k_geometry<NN><<<E, n3, 0, s>>>(node_xyz_dev, ex, ey, ez, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], amp, \
-                                        ops, X, Ja, Jaf, J, invJ, invJf, fn, fnf);                              \
+                                        ops, XL, JaL, Jaf, J, invJ, invJf, fnL, fnf, dXL);                      \
+        if (gauss)                                                                                              \
+            k_geometry_gauss<NN><<<E, n3, 0, s>>>(XL, JaL, dXL, device_ops(N, HS3D_NODES_GAUSS), X, Ja, Jaf, J,  \
+                                                  invJ, invJf);                                                 \
         break;
+    cudaError_t e = cudaSuccess;
     switch (N) {
         HS3D_GEO(1) HS3D_GEO(2) HS3D_GEO(3) HS3D_GEO(4) HS3D_GEO(5) HS3D_GEO(6) HS3D_GEO(7)
-        default: return cudaErrorInvalidValue;
+        default: e = cudaErrorInvalidValue;
     }
 #undef HS3D_GEO
-    return cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (gauss) {
+        const long long total = 3LL * E * 3 * n2;
+        if (e == cudaSuccess)
+            k_facemetric_gauss<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+                n, total, fnL, device_ops(N, HS3D_NODES_GAUSS), fn, fnf);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(s);   // the temporaries are freed below
+        if (e == cudaSuccess) e = e2;
+        cudaFree(XL);
+        cudaFree(JaL);
+        cudaFree(dXL);
+        cudaFree(fnL);
+    }
+    return e;
 }
 
 // ---------------------------------------------------------------- initial conditions

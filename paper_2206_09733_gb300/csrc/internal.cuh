@@ -63,6 +63,8 @@ struct Item {
     long long elem_begin;   // first element of this item in the launch
     long long face_begin;   // first face of this item in the launch (3E faces per item)
     double gamma, mu, kappa, cfl;
+    double kc, kv;          // dt-rule constants of the node family (convective, viscous)
+    int gauss;              // Gauss-Legendre solution nodes
     double gm1, hg;                          // gamma - 1, 1/(2(gamma - 1))
     float gammaf, gm1f, hgf, muf, kappaf;    // the same constants rounded once for the FP32 path
 };
@@ -93,16 +95,24 @@ struct Batch {
     long long total_elems;
     long long total_faces;
     double dt_fixed;        // > 0: every item steps with this dt
+    int gauss;              // every item on Gauss-Legendre nodes (items of a batch share the node family)
 };
 
 // 1-D operators on the Gauss-Lobatto nodes for one N.
+// 1-D operators of one degree N on the solution nodes (Gauss-Lobatto, or
+// Gauss-Legendre with the boundary interpolation written out).
 struct Ops {
     double D[kMaxn * kMaxn];   // D[i*n + m] = l_m'(xi_i)
     double w[kMaxn];
     double xi[kMaxn];
     float Df[kMaxn * kMaxn];
-    double iw0;                // 1/w_0 = 1/w_N (surface lifting factor)
+    double iw0;                // 1/w_0 = 1/w_N (Gauss-Lobatto surface lifting factor)
     float iw0f;
+    int gauss;                 // 1: Gauss-Legendre nodes
+    double lb[kMaxn], rb[kMaxn];     // l_j(-1), l_j(+1)
+    double lbw[kMaxn], rbw[kMaxn];   // l_j(-1)/w_j, l_j(+1)/w_j
+    float lbf[kMaxn], rbf[kMaxn], lbwf[kMaxn], rbwf[kMaxn];
+    double IL[kMaxn * kMaxn];  // IL[t*n + s]: Gauss-Lobatto basis function s at solution node t
 };
 
 template <typename R>
@@ -118,9 +128,18 @@ __device__ __forceinline__ double ops_iw0<double>(const Ops *o) { return o->iw0;
 template <>
 __device__ __forceinline__ float ops_iw0<float>(const Ops *o) { return o->iw0f; }
 
-// Host side.
-const Ops &host_ops(int N);        // computed once per N
-const Ops *device_ops(int N);      // device copy (cudaMalloc'd once per device and N)
+template <typename R>
+__device__ __forceinline__ R ops_lb(const Ops *o, int j) { if constexpr (sizeof(R) == 8) return o->lb[j]; else return o->lbf[j]; }
+template <typename R>
+__device__ __forceinline__ R ops_rb(const Ops *o, int j) { if constexpr (sizeof(R) == 8) return o->rb[j]; else return o->rbf[j]; }
+template <typename R>
+__device__ __forceinline__ R ops_lbw(const Ops *o, int j) { if constexpr (sizeof(R) == 8) return o->lbw[j]; else return o->lbwf[j]; }
+template <typename R>
+__device__ __forceinline__ R ops_rbw(const Ops *o, int j) { if constexpr (sizeof(R) == 8) return o->rbw[j]; else return o->rbwf[j]; }
+
+// Host side.  nodes: HS3D_NODES_LOBATTO or HS3D_NODES_GAUSS.
+const Ops &host_ops(int N, int nodes = HS3D_NODES_LOBATTO);   // computed once per (N, nodes)
+const Ops *device_ops(int N, int nodes = HS3D_NODES_LOBATTO); // device copy, once per (device, N, nodes)
 
 // Locate the item holding global element ge (binary search on elem_begin).
 __device__ __forceinline__ const Item &find_item_elem(const Batch &b, long long ge)
@@ -234,7 +253,7 @@ __device__ __forceinline__ int nbr_minus(int e, int d, int ex, int ey, int ez)
 }
 
 // Launch helpers implemented in the .cu files (return cudaError_t of the launch).
-cudaError_t launch_geometry(int N, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
+cudaError_t launch_geometry(int N, int nodes, const double *node_xyz_dev, int ex, int ey, int ez, const double *lo,
                             const double *hi, double amp, double *X, double *Ja, float *Jaf, double *J, double *invJ,
                             float *invJf, double *fn, float *fnf, cudaStream_t s);
 cudaError_t launch_init_state(int N, int E, const double *X, const hs3d_ic &ic, const double *lo, const double *hi,
@@ -250,6 +269,12 @@ cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, 
 // stage only): also accumulate the dt maxima of the updated state into that clock slot
 cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, const Batch &b, int stage, int lam_slot,
                           cudaStream_t s);
+// Gauss-Legendre node kernels (gauss.cu); launch_face/grad/volume route batches with b.gauss to them.
+cudaError_t launch_face_gauss(int N, int prec, int physics, int flux, const Batch &b, cudaStream_t s);
+cudaError_t launch_grad_gauss(int N, int prec, const Batch &b, cudaStream_t s);
+cudaError_t launch_volume_gauss(int N, int prec, int physics, const Batch &b, int stage, double rkA, double rkB,
+                                int lam_slot, cudaStream_t s);
+cudaError_t prepare_gauss(int N);
 // Low-storage RK schemes (HS3D_TIME_*): stage count and the stage's (A_k, B_k).
 int rk_stages(int scheme);
 void rk_coeffs(int scheme, int k, double *A, double *B);

@@ -109,6 +109,7 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
 {
     if (!m || !ms_out) return fail(HS3D_ERR_INVALID, "mesh or ms_out is NULL");
     hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st != HS3D_OK) return st;
     if (!u || !g || u == g) return fail(HS3D_ERR_INVALID, "bad u/g");
     cudaStream_t s = (cudaStream_t)stream;

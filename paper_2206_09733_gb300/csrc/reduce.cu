@@ -111,10 +111,10 @@ __global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int slot)
     } else if (c->dt_fixed > 0.0) {
         dt = c->dt_fixed;
     } else {
-        dt = it.cfl * 8.0 / ((double)n * n * lc);
+        dt = it.cfl * it.kc / ((double)n * n * lc);
         if (lv > 0.0) {
             double n4 = (double)n * n * n * n;
-            double dtv = 12.0 / (n4 * lv);
+            double dtv = it.kv / (n4 * lv);
             dt = fmin(dt, dtv);
         }
     }
@@ -135,14 +135,14 @@ __global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int slot)
 }
 
 // dt only (no clock update): writes the rule's dt to out and resets the maxima.
-__global__ void k_dt_value(Clock *c, int n, double cfl, double *out)
+__global__ void k_dt_value(Clock *c, int n, double cfl, double kc, double kv, double *out)
 {
     double lc = __longlong_as_double((long long)c->lam[0][0]);
     double lv = __longlong_as_double((long long)c->lam[0][1]);
     c->lam[0][0] = 0ull;
     c->lam[0][1] = 0ull;
-    double dt = cfl * 8.0 / ((double)n * n * lc);
-    if (lv > 0.0) dt = fmin(dt, 12.0 / ((double)n * n * n * n * lv));
+    double dt = cfl * kc / ((double)n * n * lc);
+    if (lv > 0.0) dt = fmin(dt, kv / ((double)n * n * n * n * lv));
     *out = dt;
 }
 
@@ -191,7 +191,7 @@ cudaError_t launch_shadow(int N, const Batch &b, cudaStream_t s)
 cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, int slot, cudaStream_t s)
 {
     if (mode == 2) {   // dt value of a single item into b.single.out
-        k_dt_value<<<1, 1, 0, s>>>(b.single.clk, N + 1, b.single.cfl, b.single.out);
+        k_dt_value<<<1, 1, 0, s>>>(b.single.clk, N + 1, b.single.cfl, b.single.kc, b.single.kv, b.single.out);
         return cudaGetLastError();
     }
     unsigned blocks = (unsigned)((b.nitems + 127) / 128);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double *parti
 cudaError_t launch_diagnostics(int N, const Item &it, const double *dudt, double *partials, int nblocks, double *out,
                                cudaStream_t s)
 {
-    const Ops *ops = device_ops(N);
+    const Ops *ops = device_ops(N, it.gauss ? HS3D_NODES_GAUSS : HS3D_NODES_LOBATTO);
     if (!ops) return cudaErrorMemoryAllocation;
     k_diag_partial<<<nblocks, kDiagThreads, 0, s>>>(N + 1, it, dudt, ops, partials);
     cudaError_t err = cudaGetLastError();

@@ -67,7 +67,7 @@ static size_t request_bytes(const hs3d_request &r)
 {
     long long E = (long long)r.mesh.ex * r.mesh.ey * r.mesh.ez;
     long long n3 = (long long)(r.mesh.N + 1) * (r.mesh.N + 1) * (r.mesh.N + 1);
-    return mesh_bytes(r.mesh.N, E) + 2 * sizeof(double) * (size_t)E * 5 * n3;
+    return mesh_bytes(r.mesh.N, E, r.mesh.nodes) + 2 * sizeof(double) * (size_t)E * 5 * n3;
 }
 
 }  // namespace hs3d
@@ -180,12 +180,13 @@ static void finish(hs3d_server *S, ServerReq *r, hs3d_status st, const ClockView
     S->finished++;
 }
 
-typedef std::tuple<int, int, int, int, int, int> BucketKey;
+typedef std::tuple<int, int, int, int, int, int, int> BucketKey;
 
 static BucketKey key_of(const ServerReq *r)
 {
     const hs3d_solver_cfg &c = r->req.cfg;
-    return BucketKey(r->req.mesh.N, c.physics, c.surface_flux, c.volume_form, c.precision, c.time_scheme);
+    return BucketKey(r->req.mesh.N, c.physics, c.surface_flux, c.volume_form, c.precision, c.time_scheme,
+                     r->req.mesh.nodes);
 }
 
 static cudaError_t ensure_capacity(hs3d_server *S, int n)
@@ -268,6 +269,7 @@ static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
         bt.total_elems = 0;
         for (int k = lo; k < hi; ++k) bt.total_elems += run[k]->mesh->E;
         bt.total_faces = 3 * bt.total_elems;
+        bt.gauss = items[lo].gauss;
         e = enqueue_rk3_step(run[lo]->req.mesh.N, cfgs[b], bt, 0.0, 0, S->stream);
     }
     if (e == cudaSuccess) {
@@ -406,6 +408,8 @@ hs3d_status hs3d_submit(hs3d_server *S, const hs3d_request *req, uint64_t *ticke
     if (!S || !req || !ticket) return fail(HS3D_ERR_INVALID, "server, request or ticket is NULL");
     hs3d_status st = validate_desc(&req->mesh);
     if (st == HS3D_OK) st = validate_cfg(&req->cfg);
+    if (st == HS3D_OK && req->mesh.nodes == HS3D_NODES_GAUSS && req->cfg.volume_form != HS3D_VOL_STANDARD)
+        st = fail(HS3D_ERR_UNSUPPORTED, "split volume forms need Gauss-Lobatto nodes");
     if (st != HS3D_OK) return st;
     if (!(req->t_final > 0.0) && req->n_steps <= 0)
         return fail(HS3D_ERR_INVALID, "request needs t_final > 0 or n_steps > 0");

@@ -113,6 +113,7 @@ extern "C" hs3d_status hs3d_autotune(const hs3d_mesh *mc, const hs3d_solver_cfg 
     hs3d_mesh *m = const_cast<hs3d_mesh *>(mc);
     if (!m) return fail(HS3D_ERR_INVALID, "mesh is NULL");
     hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st != HS3D_OK) return st;
     std::lock_guard<std::mutex> g(g_tune_mu);
     load_cache_locked();

@@ -67,6 +67,10 @@ cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, co
         if (stage >= rk_stages(scheme)) return cudaErrorInvalidValue;
         rk_coeffs(scheme, stage, &A, &B);
     }
+    if (b.gauss) {
+        if (form != HS3D_VOL_STANDARD) return cudaErrorInvalidValue;
+        return launch_volume_gauss(N, prec, physics, b, stage, A, B, lam_slot, s);
+    }
     switch (form) {
         case HS3D_VOL_STANDARD:
             return launch_volume_form<HS3D_VOL_STANDARD>(N, prec, physics, b, stage, A, B, lam_slot, s);

@@ -68,6 +68,101 @@ __device__ __forceinline__ const double *metric_ptr<double>(const Item &it) { re
 template <>
 __device__ __forceinline__ const float *metric_ptr<float>(const Item &it) { return it.Jaf; }
 
+// Residual store or RK stage of one node from V (volume + surface sum), then,
+// after the last stage (lam_slot >= 0), the dt maxima of the updated state.
+// u holds the FP64 state on the FP64 path (loaded here on the mixed path).
+template <typename R, bool NS>
+__device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3, const R V[5], double u[5],
+                                            int stage, double rkA, double rkB, int lam_slot, double &lc, double &lv,
+                                            bool &lam_active)
+{
+    if constexpr (sizeof(R) == 4) {
+        // the FP64 state is needed only for the RK accumulation
+        if (stage >= 0) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = it.u[(size_t)e * 5 * n3 + p + v * n3];
+        }
+    }
+
+    float nf[5];   // mixed path: FP32 shadow of the updated state
+    if constexpr (sizeof(R) == 8) {
+        const double ij = it.invJ[(size_t)e * n3 + p];
+        if (stage < 0) {
+            double *O = it.out + (size_t)e * 5 * n3 + p;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
+        } else {
+            const double dt = it.clk->dt;
+            const double A = rkA, B = rkB;
+            double *Gp = it.g + (size_t)e * 5 * n3 + p;
+            double *Up = it.u + (size_t)e * 5 * n3 + p;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const double r = -(double)V[v] * ij;
+                const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
+                Gp[v * n3] = gv;
+                u[v] = u[v] + B * gv;
+                Up[v * n3] = u[v];
+            }
+        }
+    } else {
+        // mixed path: the increment dt R = -dt V / J is formed in FP32 and
+        // widened exactly; the register and the state accumulate in FP64
+        // (two FP64 FMAs per variable).
+        const float ijf = it.invJf[(size_t)e * n3 + p];
+        if (stage < 0) {
+            double *O = it.out + (size_t)e * 5 * n3 + p;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) O[v * n3] = f2d_exact(-(float)V[v] * ijf);
+        } else {
+            const float sdt = d2f_rn(it.clk->dt) * ijf;
+            const double A = rkA, B = rkB;
+            double *Gp = it.g + (size_t)e * 5 * n3 + p;
+            double *Up = it.u + (size_t)e * 5 * n3 + p;
+            float *Sp = it.uf + (size_t)e * 5 * n3 + p;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const double inc = f2d_exact(-(float)V[v] * sdt);
+                const double gv = (stage == 0) ? inc : fma(A, Gp[v * n3], inc);
+                Gp[v * n3] = gv;
+                u[v] = fma(B, gv, u[v]);
+                Up[v * n3] = u[v];
+                nf[v] = d2f_rn(u[v]);
+                Sp[v * n3] = nf[v];
+            }
+        }
+    }
+    if (stage >= 0) {
+        if (lam_slot >= 0) {
+            // dt maxima of the updated state (same rule as k_lambda, in R)
+            const Phys<R> P = phys_of<R>(it);
+            Prim<R> qn;
+            if constexpr (sizeof(R) == 8) qn = prim_from_u<R>(u, P.gm1);
+            else qn = prim_from_f(nf, P.gm1);
+            if (!(qn.rho > (R)0) || !(qn.p > (R)0)) {
+                it.clk->bad = 1;
+            } else {
+                const R c = sqrt(P.gamma * qn.p / qn.rho);
+                R iJ;
+                if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
+                else iJ = it.invJf[(size_t)e * n3 + p];
+                R sc = (R)0, sv = (R)0;
+                const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const R a1 = JA[(d * 3) * n3], a2 = JA[(d * 3 + 1) * n3], a3 = JA[(d * 3 + 2) * n3];
+                    const R an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
+                    sc += (fabs(a1 * qn.v1 + a2 * qn.v2 + a3 * qn.v3) + c * an) * iJ;
+                    sv += (an * iJ) * (an * iJ);
+                }
+                lc = widen<R>(sc);
+                lv = NS ? widen<R>(P.mu * sv / qn.rho) : 0.0;
+                lam_active = true;
+            }
+        }
+    }
+}
+
 template <int N, typename R, bool NS, int FORM>
 __global__ void __launch_bounds__(vol_threads<N>(), vol_min_blocks<N, R>())
 k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB, int lam_slot)
@@ -298,91 +393,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 for (int v = 0; v < 5; ++v) V[v] += iw * (own[v] - F[v * n2]);
             }
         }
-        if constexpr (sizeof(R) == 4) {
-            // the FP64 state is needed only for the RK accumulation
-            if (stage >= 0) {
-#pragma unroll
-                for (int v = 0; v < 5; ++v) u[v] = it.u[(size_t)e * 5 * n3 + p + v * n3];
-            }
-        }
-
-        float nf[5];   // mixed path: FP32 shadow of the updated state
-        if constexpr (sizeof(R) == 8) {
-            const double ij = it.invJ[(size_t)e * n3 + p];
-            if (stage < 0) {
-                double *O = it.out + (size_t)e * 5 * n3 + p;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) O[v * n3] = -(double)V[v] * ij;
-            } else {
-                const double dt = it.clk->dt;
-                const double A = rkA, B = rkB;
-                double *Gp = it.g + (size_t)e * 5 * n3 + p;
-                double *Up = it.u + (size_t)e * 5 * n3 + p;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                    const double r = -(double)V[v] * ij;
-                    const double gv = (stage == 0) ? dt * r : A * Gp[v * n3] + dt * r;
-                    Gp[v * n3] = gv;
-                    u[v] = u[v] + B * gv;
-                    Up[v * n3] = u[v];
-                }
-            }
-        } else {
-            // mixed path: the increment dt R = -dt V / J is formed in FP32 and
-            // widened exactly; the register and the state accumulate in FP64
-            // (two FP64 FMAs per variable).
-            const float ijf = it.invJf[(size_t)e * n3 + p];
-            if (stage < 0) {
-                double *O = it.out + (size_t)e * 5 * n3 + p;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) O[v * n3] = f2d_exact(-(float)V[v] * ijf);
-            } else {
-                const float sdt = d2f_rn(it.clk->dt) * ijf;
-                const double A = rkA, B = rkB;
-                double *Gp = it.g + (size_t)e * 5 * n3 + p;
-                double *Up = it.u + (size_t)e * 5 * n3 + p;
-                float *Sp = it.uf + (size_t)e * 5 * n3 + p;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                    const double inc = f2d_exact(-(float)V[v] * sdt);
-                    const double gv = (stage == 0) ? inc : fma(A, Gp[v * n3], inc);
-                    Gp[v * n3] = gv;
-                    u[v] = fma(B, gv, u[v]);
-                    Up[v * n3] = u[v];
-                    nf[v] = d2f_rn(u[v]);
-                    Sp[v * n3] = nf[v];
-                }
-            }
-        }
-        if (stage >= 0) {
-            if (lam_slot >= 0) {
-                // dt maxima of the updated state (same rule as k_lambda, in R)
-                const Phys<R> P = phys_of<R>(it);
-                Prim<R> qn;
-                if constexpr (sizeof(R) == 8) qn = prim_from_u<R>(u, P.gm1);
-                else qn = prim_from_f(nf, P.gm1);
-                if (!(qn.rho > (R)0) || !(qn.p > (R)0)) {
-                    it.clk->bad = 1;
-                } else {
-                    const R c = sqrt(P.gamma * qn.p / qn.rho);
-                    R iJ;
-                    if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
-                    else iJ = it.invJf[(size_t)e * n3 + p];
-                    R sc = (R)0, sv = (R)0;
-                    const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const R a1 = JA[(d * 3) * n3], a2 = JA[(d * 3 + 1) * n3], a3 = JA[(d * 3 + 2) * n3];
-                        const R an = sqrt(a1 * a1 + a2 * a2 + a3 * a3);
-                        sc += (fabs(a1 * qn.v1 + a2 * qn.v2 + a3 * qn.v3) + c * an) * iJ;
-                        sv += (an * iJ) * (an * iJ);
-                    }
-                    lc = widen<R>(sc);
-                    lv = NS ? widen<R>(P.mu * sv / qn.rho) : 0.0;
-                    lam_active = true;
-                }
-            }
-        }
+        node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active);
     }
     if (lam_slot >= 0 && stage >= 0) {
         unsigned long long *dc = nullptr, *dv = nullptr;
