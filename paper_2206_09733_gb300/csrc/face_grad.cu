@@ -57,9 +57,14 @@ __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, i
     const Item &it = find_item_face(b, gf);
     if (it.clk && it.clk->done) return;
     const int E = it.E;
-    const int f = (int)(gf - it.face_begin);
-    const int d = f / E;
-    const int eL = f - d * E;
+    // threads walk the faces element-major (the three +d faces of element 0,
+    // then of element 1, ...), so that the state sectors an element's faces
+    // share (every xi and eta trace sector holds nodes of both ends) are
+    // fetched from DRAM once and then hit in L2; storage stays f = d*E + eL
+    const int lf = (int)(gf - it.face_begin);
+    const int eL = lf / 3;
+    const int d = lf - 3 * eL;
+    const int f = d * E + eL;
     const int eR = nbr_plus(eL, d, it.ex, it.ey, it.ez);
     const int ta = ab % n, tb = ab / n;
     const int pL = face_node<n>(d, N, ta, tb), pR = face_node<n>(d, 0, ta, tb);
@@ -83,29 +88,46 @@ __global__ void __launch_bounds__(256) k_face(const __grid_constant__ Batch b, i
     if (flux == HS3D_FLUX_EC) {
         flux_ec(ec_node(qL), ec_node(qR), P.hg, s1, s2, s3, fs);
     } else if (flux == HS3D_FLUX_LF) {
-        // the LF dissipation uses the conserved jump, formed in FP64 before rounding
-        double uL[5], uR[5];
+        // conserved traces: the FP32 shadow on the mixed path (flux arithmetic
+        // in FP32 throughout); on the FP64 path the jump is formed from u
+        R ul[5], ur[5];
+        if constexpr (sizeof(R) == 4) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            uL[v] = it.u[iL + (size_t)v * n3];
-            uR[v] = it.u[iR + (size_t)v * n3];
+            for (int v = 0; v < 5; ++v) {
+                ul[v] = it.uf[iL + (size_t)v * n3];
+                ur[v] = it.uf[iR + (size_t)v * n3];
+            }
+        } else {
+            double uL[5], uR[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                uL[v] = it.u[iL + (size_t)v * n3];
+                uR[v] = it.u[iR + (size_t)v * n3];
+            }
+            ul[0] = qL.rho; ul[1] = narrow<R>(uL[1]); ul[2] = narrow<R>(uL[2]); ul[3] = narrow<R>(uL[3]); ul[4] = qL.E;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
         }
-        R ul[5] = {qL.rho, narrow<R>(uL[1]), narrow<R>(uL[2]), narrow<R>(uL[3]), qL.E};
-        R ur[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
         flux_lf(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
     } else if (flux == HS3D_FLUX_RUSANOV) {
-        double uL[5], uR[5];
+        R ul[5], ur[5];
+        if constexpr (sizeof(R) == 4) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            uL[v] = it.u[iL + (size_t)v * n3];
-            uR[v] = it.u[iR + (size_t)v * n3];
+            for (int v = 0; v < 5; ++v) {
+                ul[v] = it.uf[iL + (size_t)v * n3];
+                ur[v] = it.uf[iR + (size_t)v * n3];
+            }
+        } else {
+            double uL[5], uR[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                uL[v] = it.u[iL + (size_t)v * n3];
+                uR[v] = it.u[iR + (size_t)v * n3];
+            }
+            ul[0] = qL.rho; ul[1] = narrow<R>(uL[1]); ul[2] = narrow<R>(uL[2]); ul[3] = narrow<R>(uL[3]); ul[4] = qL.E;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
         }
-        R ul[5] = {qL.rho, narrow<R>(uL[1]), narrow<R>(uL[2]), narrow<R>(uL[3]), qL.E};
-        R ur[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) ur[v] = ul[v] + narrow<R>(uR[v] - uL[v]);
         flux_rusanov(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
     } else if (flux == HS3D_FLUX_MATRIX) {
         flux_matrix(qL, qR, P.gamma, P.hg, s1, s2, s3, fs);

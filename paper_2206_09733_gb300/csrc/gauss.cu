@@ -83,9 +83,11 @@ __global__ void __launch_bounds__(256) k_face_gauss(const __grid_constant__ Batc
     const Item &it = find_item_face(b, gf);
     if (it.clk && it.clk->done) return;
     const int E = it.E;
-    const int f = (int)(gf - it.face_begin);
-    const int d = f / E;
-    const int eL = f - d * E;
+    // element-major walk over the faces (as k_face), storage f = d*E + eL
+    const int lf = (int)(gf - it.face_begin);
+    const int eL = lf / 3;
+    const int d = lf - 3 * eL;
+    const int f = d * E + eL;
     const int eR = nbr_plus(eL, d, it.ex, it.ey, it.ez);
     const int ta = ab % n, tb = ab / n;
     const Phys<R> P = phys_of<R>(it);

@@ -71,16 +71,20 @@ __device__ __forceinline__ const float *metric_ptr<float>(const Item &it) { retu
 // Residual store or RK stage of one node from V (volume + surface sum), then,
 // after the last stage (lam_slot >= 0), the dt maxima of the updated state.
 // u holds the FP64 state on the FP64 path (loaded here on the mixed path).
+// Mixed path: sUG, when given, is the element's [u (5 n3), g (5 n3)] FP64
+// block and sIJ its 1/J (FP32), staged in shared memory by asynchronous
+// copies at the start of the kernel (g only for stage > 0).
 template <typename R, bool NS>
 __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3, const R V[5], double u[5],
                                             int stage, double rkA, double rkB, int lam_slot, double &lc, double &lv,
-                                            bool &lam_active)
+                                            bool &lam_active, const double *sUG = nullptr,
+                                            const float *sIJ = nullptr)
 {
     if constexpr (sizeof(R) == 4) {
         // the FP64 state is needed only for the RK accumulation
         if (stage >= 0) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = it.u[(size_t)e * 5 * n3 + p + v * n3];
+            for (int v = 0; v < 5; ++v) u[v] = sUG ? sUG[v * n3 + p] : it.u[(size_t)e * 5 * n3 + p + v * n3];
         }
     }
 
@@ -109,7 +113,7 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
         // mixed path: the increment dt R = -dt V / J is formed in FP32 and
         // widened exactly; the register and the state accumulate in FP64
         // (two FP64 FMAs per variable).
-        const float ijf = it.invJf[(size_t)e * n3 + p];
+        const float ijf = sIJ ? sIJ[p] : it.invJf[(size_t)e * n3 + p];
         if (stage < 0) {
             double *O = it.out + (size_t)e * 5 * n3 + p;
 #pragma unroll
@@ -123,7 +127,7 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 const double inc = f2d_exact(-(float)V[v] * sdt);
-                const double gv = (stage == 0) ? inc : fma(A, Gp[v * n3], inc);
+                const double gv = (stage == 0) ? inc : fma(A, sUG ? sUG[(5 + v) * n3 + p] : Gp[v * n3], inc);
                 Gp[v * n3] = gv;
                 u[v] = fma(B, gv, u[v]);
                 Up[v * n3] = u[v];
@@ -145,7 +149,7 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
                 const R c = sqrt(P.gamma * qn.p / qn.rho);
                 R iJ;
                 if constexpr (sizeof(R) == 8) iJ = it.invJ[(size_t)e * n3 + p];
-                else iJ = it.invJf[(size_t)e * n3 + p];
+                else iJ = sIJ ? sIJ[p] : it.invJf[(size_t)e * n3 + p];
                 R sc = (R)0, sv = (R)0;
                 const R *JA = metric_ptr<R>(it) + (size_t)e * 9 * n3 + p;
 #pragma unroll
@@ -163,6 +167,27 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
     }
 }
 
+// Byte offsets in the element kernel's dynamic shared memory: D, the
+// per-node staging of epb elements, their face-flux blocks, the split-form
+// pair buffers, then (mixed path) the staged RK block [epb][u, g][5 n3]
+// FP64 followed by [epb][n3] FP32 1/J, 16-byte aligned.
+template <int N, typename R, bool NS, int FORM>
+__host__ __device__ constexpr size_t rk_stage_offset(int epb)
+{
+    constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+    constexpr size_t pairs = (FORM != HS3D_VOL_STANDARD) ? (size_t)5 * n2 * (n * (n - 1) / 2) : 0;
+    const size_t b = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 +
+                                  (size_t)epb * 30 * n2 + (size_t)epb * pairs);
+    return (b + 15) & ~(size_t)15;
+}
+
+template <int N, typename R, bool NS, int FORM>
+__host__ __device__ constexpr size_t vol_smem_bytes(int epb)
+{
+    constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+    return rk_stage_offset<N, R, NS, FORM>(epb) + (sizeof(R) == 4 ? (size_t)epb * n3 * (10 * 8 + 4) : 0);
+}
+
 template <int N, typename R, bool NS, int FORM>
 __global__ void __launch_bounds__(vol_threads<N>(), vol_min_blocks<N, R>())
 k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB, int lam_slot)
@@ -175,6 +200,10 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     const int epb = blockDim.x / n3;
     R *sbuf = sD + ((n * n + 1) & ~1);
     R *sface = sbuf + (size_t)epb * PER * n3;
+    // mixed path: the FP64 state and register and 1/J of the RK update, staged
+    // at the start so that their loads overlap the volume and surface work
+    constexpr bool STAGE_RK = sizeof(R) == 4;
+    double *sRK = (double *)(smem_raw + rk_stage_offset<N, R, NS, FORM>(epb));
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
     const long long ge = blockIdx.x * (long long)epb + le;
@@ -206,6 +235,15 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 const int d = slot >> 1;
                 const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
                 cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
+            }
+        }
+        if constexpr (STAGE_RK) {
+            if (stage >= 0) {
+                double *mine = sRK + (size_t)le * 10 * n3;
+                cp_async_block<double>(mine, it.u + (size_t)e * 5 * n3, 5 * n3, p, n3);
+                if (stage > 0) cp_async_block<double>(mine + 5 * n3, it.g + (size_t)e * 5 * n3, 5 * n3, p, n3);
+                cp_async_block<float>((float *)(sRK + (size_t)epb * 10 * n3) + (size_t)le * n3,
+                                      it.invJf + (size_t)e * n3, n3, p, n3);
             }
         }
         const size_t node = (size_t)e * 5 * n3 + p;
@@ -393,7 +431,15 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 for (int v = 0; v < 5; ++v) V[v] += iw * (own[v] - F[v * n2]);
             }
         }
-        node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active);
+        if constexpr (STAGE_RK) {
+            if (stage >= 0)
+                node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active,
+                                   sRK + (size_t)le * 10 * n3, (const float *)(sRK + (size_t)epb * 10 * n3) + le * n3);
+            else
+                node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active);
+        } else {
+            node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active);
+        }
     }
     if (lam_slot >= 0 && stage >= 0) {
         unsigned long long *dc = nullptr, *dv = nullptr;
@@ -417,9 +463,7 @@ static cudaError_t vol_launch2(const Batch &b, int stage, double rkA, double rkB
         epb = vol_threads<N>() / n3;
         threads = epb * n3;
     }
-    const size_t pairs = (FORM != HS3D_VOL_STANDARD) ? (size_t)5 * n2 * (n * (n - 1) / 2) : 0;
-    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 +
-                               (size_t)epb * 30 * n2 + (size_t)epb * pairs);
+    const size_t smem = vol_smem_bytes<N, R, NS, FORM>(epb);
     unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
