@@ -212,10 +212,11 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
     if (valid) {
         const Item &it = *itp;
         const R gm1 = phys_of<R>(it).gm1;
+        const Nbrs nbs = elem_nbrs(e, it.ex, it.ey, it.ez);
         for (int t = p; t < 6 * n2; t += n3) {
             const int slot = t / n2, ab = t - slot * n2;
             const int d = slot >> 1, plus = slot & 1;
-            const int nb = plus ? nbr_plus(e, d, it.ex, it.ey, it.ez) : nbr_minus(e, d, it.ex, it.ey, it.ez);
+            const int nb = nbr_of_slot(nbs, slot);
             const int pn = face_node<n>(d, plus ? 0 : N, ab % n, ab / n);
             R g4[4];
             grad_vars(load_prim<R>(it, (size_t)nb * 5 * n3 + pn, n3, gm1), g4);

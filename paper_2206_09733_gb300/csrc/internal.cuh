@@ -233,23 +233,52 @@ __device__ __forceinline__ void cp_async_block(R *dst, const R *src, int count, 
     }
 }
 
-// Element neighbour across direction d (+1 side), periodic.
+// Element neighbour across direction d (+1 side), periodic.  Element e of
+// the ex x ey x ez box has coordinates a = e mod ex, b = (e / ex) mod ey,
+// c = e / (ex ey): two integer divisions.
 __device__ __forceinline__ int nbr_plus(int e, int d, int ex, int ey, int ez)
 {
-    int a = e % ex, b = (e / ex) % ey, c = e / (ex * ey);
-    if (d == 0) a = (a + 1 == ex) ? 0 : a + 1;
-    else if (d == 1) b = (b + 1 == ey) ? 0 : b + 1;
-    else c = (c + 1 == ez) ? 0 : c + 1;
-    return a + ex * (b + ey * c);
+    const int q = e / ex, a = e - q * ex;
+    const int c = q / ey, b = q - c * ey;
+    if (d == 0) return (a + 1 == ex) ? e - (ex - 1) : e + 1;
+    if (d == 1) return (b + 1 == ey) ? e - (ey - 1) * ex : e + ex;
+    return (c + 1 == ez) ? e - (ez - 1) * ex * ey : e + ex * ey;
 }
 
 __device__ __forceinline__ int nbr_minus(int e, int d, int ex, int ey, int ez)
 {
-    int a = e % ex, b = (e / ex) % ey, c = e / (ex * ey);
-    if (d == 0) a = (a == 0) ? ex - 1 : a - 1;
-    else if (d == 1) b = (b == 0) ? ey - 1 : b - 1;
-    else c = (c == 0) ? ez - 1 : c - 1;
-    return a + ex * (b + ey * c);
+    const int q = e / ex, a = e - q * ex;
+    const int c = q / ey, b = q - c * ey;
+    if (d == 0) return (a == 0) ? e + (ex - 1) : e - 1;
+    if (d == 1) return (b == 0) ? e + (ey - 1) * ex : e - ex;
+    return (c == 0) ? e + (ez - 1) * ex * ey : e - ex * ey;
+}
+
+// All six neighbours of element e: m[d] across its -d face, p[d] across its
+// +d face (one pair of divisions for the six).
+struct Nbrs {
+    int m[3], p[3];
+};
+__device__ __forceinline__ Nbrs elem_nbrs(int e, int ex, int ey, int ez)
+{
+    const int q = e / ex, a = e - q * ex;
+    const int c = q / ey, b = q - c * ey;
+    const int sz = ex * ey;
+    Nbrs r;
+    r.m[0] = (a == 0) ? e + (ex - 1) : e - 1;
+    r.p[0] = (a + 1 == ex) ? e - (ex - 1) : e + 1;
+    r.m[1] = (b == 0) ? e + (ey - 1) * ex : e - ex;
+    r.p[1] = (b + 1 == ey) ? e - (ey - 1) * ex : e + ex;
+    r.m[2] = (c == 0) ? e + (ez - 1) * sz : e - sz;
+    r.p[2] = (c + 1 == ez) ? e - (ez - 1) * sz : e + sz;
+    return r;
+}
+
+// Neighbour across face slot s = 2d (the -d face) or 2d + 1 (the +d face),
+// for a run-time slot (a select chain, so that Nbrs stays in registers).
+__device__ __forceinline__ int nbr_of_slot(const Nbrs &r, int s)
+{
+    return s == 0 ? r.m[0] : s == 1 ? r.p[0] : s == 2 ? r.m[1] : s == 3 ? r.p[1] : s == 4 ? r.m[2] : r.p[2];
 }
 
 // Launch helpers implemented in the .cu files (return cudaError_t of the launch).

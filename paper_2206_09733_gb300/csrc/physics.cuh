@@ -32,19 +32,20 @@ struct Prim {
 // stays NaN.
 __device__ __forceinline__ float d2f_rn(double x)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned rest = lo & 0x1fffffffu;
-    const int ef = e - 1023 + 127;
-    if (e == 0x7ff) return __int_as_float((int)(sign | 0x7f800000u | ((m | rest) ? 0x400000u : 0u)));
-    if (ef <= 0) return __int_as_float((int)sign);
-    if (ef >= 255) return __int_as_float((int)(sign | 0x7f800000u));
-    unsigned r = ((unsigned)ef << 23) | m;
-    if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) r += 1u;
-    return __int_as_float((int)(sign | r));
+    // branch-free: the normal-range result is formed unconditionally and the
+    // out-of-range cases are selected afterwards
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    // exponent and the top 23 significand bits, rebased by (1023 - 127) << 23;
+    // modulo 2^32 this is exact whenever the FP32 exponent is in range
+    unsigned r = __funnelshift_l(lo, hi, 3) - (896u << 23);
+    // round to nearest even on the 29 dropped bits: +1 above half, and at
+    // exactly half when r is odd
+    r += ((lo & 0x1fffffffu) + (r & 1u) + 0x0fffffffu) >> 29;
+    const unsigned special = 0x7f800000u | ((e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+    r = (e >= 1151u) ? special : r;   // FP32 exponent >= 255: infinity (NaN for NaN)
+    r = (e <= 896u) ? 0u : r;         // FP32 exponent <= 0: signed zero
+    return __uint_as_float((hi & 0x80000000u) | r);
 }
 
 // FP32 -> FP64 (exact) on the integer pipe; FP32 subnormals become zero.
@@ -64,16 +65,15 @@ __device__ __forceinline__ float narrow<float>(double x) { return d2f_rn(x); }
 
 __device__ __forceinline__ double f2d_exact(float x)
 {
-    const unsigned b = (unsigned)__float_as_int(x);
-    const unsigned sign = b & 0x80000000u;
+    const unsigned b = __float_as_uint(x);
     const unsigned e = (b >> 23) & 0xffu;
-    const unsigned m = b & 0x7fffffu;
-    unsigned hi;
-    if (e == 0) hi = sign;
-    else if (e == 0xff) hi = sign | 0x7ff00000u | (m >> 3);
-    else hi = sign | ((e - 127u + 1023u) << 20) | (m >> 3);
-    const unsigned lo = (e == 0) ? 0u : (m << 29);
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+    // exponent and significand shifted into the FP64 layout, exponent rebased
+    // by (1023 - 127) << 20; infinity and NaN keep the all-ones exponent
+    unsigned hi = ((b & 0x7fffffffu) >> 3) + (896u << 20);
+    hi = (e == 0xffu) ? (0x7ff00000u | ((b & 0x7fffffu) >> 3)) : hi;
+    hi = (e == 0u) ? 0u : hi;
+    const unsigned lo = (e == 0u) ? 0u : (b << 29);
+    return __hiloint2double((int)((b & 0x80000000u) | hi), (int)lo);
 }
 
 // Primitive variables from the FP64 conserved state.  FP64 path: in FP64.

@@ -3,8 +3,10 @@
 // The BR1-gradient and element (volume) kernels run one thread per node with
 // `epb` elements per CTA.  hs3d_autotune times every admissible epb (the CTA
 // must stay within the kernel's thread bound and shared-memory limit) for
-// the given mesh and configuration on scratch copies of a smooth state, in
-// residual mode, and keeps the fastest per (N, precision, kernel).  Choices
+// the given mesh and configuration on scratch copies of a smooth state (the
+// element kernel as a middle RK stage, with its own clock and a tiny dt, so
+// that the timed launches move the bytes of a real step), and keeps the
+// fastest per (N, precision, kernel).  Choices
 // persist across processes in a small JSON file when HS3D_TUNE_CACHE names
 // one: it is read on first use and rewritten after each tuning.
 #include <stdio.h>
@@ -79,7 +81,8 @@ void tune_cache_load()
     load_cache_locked();
 }
 
-// Time `reps` launches of the residual-mode kernels with a given epb.
+// Time `reps` launches of the gradient kernel, or of the element kernel as
+// RK stage 1 (reads and writes u and g), with a given epb.
 static float time_kernels(hs3d_mesh *m, const hs3d_solver_cfg *c, const Batch &b, int which, int reps, cudaStream_t s,
                           cudaError_t &err)
 {
@@ -89,11 +92,11 @@ static float time_kernels(hs3d_mesh *m, const hs3d_solver_cfg *c, const Batch &b
     err = cudaSuccess;
     // one untimed launch (also surfaces launch errors for this shape)
     if (which == 0) err = launch_grad(m->N, c->precision, b, s);
-    else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, -1, -1, s);
+    else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, 1, -1, s);
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int r = 0; r < reps && err == cudaSuccess; ++r) {
         if (which == 0) err = launch_grad(m->N, c->precision, b, s);
-        else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, -1, -1, s);
+        else err = launch_volume(m->N, c->precision, c->physics, c->volume_form, c->time_scheme, b, 1, -1, s);
     }
     if (err == cudaSuccess) err = cudaEventRecord(e1, s);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
@@ -115,23 +118,31 @@ extern "C" hs3d_status hs3d_autotune(const hs3d_mesh *mc, const hs3d_solver_cfg 
     hs3d_status st = validate_cfg(c);
     if (st == HS3D_OK) st = check_mesh_cfg(m, c);
     if (st != HS3D_OK) return st;
-    std::lock_guard<std::mutex> g(g_tune_mu);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
     load_cache_locked();
     cudaStream_t s = (cudaStream_t)stream;
     size_t sz = sizeof(double) * (size_t)m->E * 5 * m->n3;
-    double *u = nullptr, *out = nullptr;
+    double *u = nullptr, *g = nullptr;
+    Clock *clk = nullptr;
     cudaError_t e = cudaMalloc(&u, sz);
-    if (e == cudaSuccess) e = cudaMalloc(&out, sz);
+    if (e == cudaSuccess) e = cudaMalloc(&g, sz);
+    if (e == cudaSuccess) e = cudaMalloc(&clk, sizeof(Clock));
     if (e != cudaSuccess) {
         if (u) cudaFree(u);
+        if (g) cudaFree(g);
         cudaGetLastError();
         return cuda_fail(e, "autotune scratch");
     }
+    // the stages advance the scratch state by dt = 1e-12 (|A_1| < 1 keeps g bounded)
+    Clock hclk{};
+    hclk.dt = 1e-12;
+    e = cudaMemsetAsync(g, 0, sz, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(clk, &hclk, sizeof(Clock), cudaMemcpyHostToDevice, s);
     // a smooth state on this mesh: the Taylor-Green field (any positive state would do)
     hs3d_ic ic{HS3D_IC_TGV, c->gamma, 0.3, 0.0, 0.0, 0.0, 0.0};
-    e = launch_init_state(m->N, m->E, m->X, ic, m->lo, m->hi, u, s);
-    Item it = make_item(m, c, u, nullptr, out);
-    it.clk = nullptr;
+    if (e == cudaSuccess) e = launch_init_state(m->N, m->E, m->X, ic, m->lo, m->hi, u, s);
+    Item it = make_item(m, c, u, g, nullptr);
+    it.clk = clk;
     Batch b = single_batch(it);
     // the face fluxes the volume kernel reads: one face pass
     if (e == cudaSuccess && c->precision == HS3D_MIXED32) e = launch_shadow(m->N, b, s);
@@ -165,7 +176,8 @@ extern "C" hs3d_status hs3d_autotune(const hs3d_mesh *mc, const hs3d_solver_cfg 
     }
     cudaStreamSynchronize(s);
     cudaFree(u);
-    cudaFree(out);
+    cudaFree(g);
+    cudaFree(clk);
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     save_cache_locked();
     if (choice_out) {

@@ -175,7 +175,7 @@ template <int N, typename R, bool NS, int FORM>
 __host__ __device__ constexpr size_t rk_stage_offset(int epb)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-    constexpr size_t pairs = (FORM != HS3D_VOL_STANDARD) ? (size_t)5 * n2 * (n * (n - 1) / 2) : 0;
+    constexpr size_t pairs = (FORM != HS3D_VOL_STANDARD) ? (size_t)5 * (n / 2) * n3 : 0;
     const size_t b = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 +
                                   (size_t)epb * 30 * n2 + (size_t)epb * pairs);
     return (b + 15) & ~(size_t)15;
@@ -225,6 +225,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     Prim<R> q;   // kept across the barrier: the surface term recomputes the own flux from it
     if (valid) {
         const Item &it = *itp;
+        const Nbrs nb = elem_nbrs(e, it.ex, it.ey, it.ez);
         // the six face-flux blocks of this element (slot 2d+1: the +d face,
         // own index; slot 2d: the -d face, owned by the -d neighbour) go to
         // shared memory by asynchronous copies, waited for before the barrier
@@ -233,7 +234,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
 #pragma unroll
             for (int slot = 0; slot < 6; ++slot) {
                 const int d = slot >> 1;
-                const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
+                const int owner = (slot & 1) ? e : nb.m[d];
                 cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
             }
         }
@@ -274,7 +275,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
 #pragma unroll
             for (int slot = 0; slot < 6; ++slot) {
                 const int d = slot >> 1;
-                const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
+                const int owner = (slot & 1) ? e : nb.m[d];
                 cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
             }
         }
@@ -333,41 +334,41 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         }
     } else {
         // Split form.  F#(u_i,u_m).(Ja_i + Ja_m) is symmetric in (i, m), so
-        // each pair of nodes on a line is evaluated once: per direction, the
-        // element's threads share the n^2 * n(n-1)/2 pair fluxes (written to
-        // shared memory), then every node sums D_im times the fluxes of its
-        // line.
-        constexpr int NP = n * (n - 1) / 2;
-        constexpr int W = n2 * NP;
-        R *PB = sface + (size_t)epb * FACEVALS + (size_t)le * 5 * W;
+        // each pair of nodes on a line is evaluated once and shared through
+        // shared memory.  Pair thread t = x n^2 + l (x a position along the
+        // line, l = ta + n tb the line) evaluates the pairs (x, x + k mod n)
+        // for k = 1 .. n/2, the half-way pair k = n/2 of an even n only for
+        // x < n/2: every pair of the line exactly once, with no index search,
+        // and the threads with the extra pair grouped in the lower warps.
+        // Then every node sums D_im times the fluxes of its line.
+        constexpr int KP = n / 2;
+        R *PB = sface + (size_t)epb * FACEVALS + (size_t)le * 5 * KP * n3;
         const R hg = valid ? phys_of<R>(*itp).hg : (R)0;
         const R gam = valid ? phys_of<R>(*itp).gamma : (R)0;
 #pragma unroll 1
         for (int d = 0; d < 3; ++d) {
+            const int sd = (d == 0) ? 1 : (d == 1) ? n : n2;   // node stride along d
             if (valid) {
-                for (int w = p; w < W; w += n3) {
-                    const int l = w / NP;
-                    int pp = w - l * NP, ia = 0;
-                    while (pp >= n - 1 - ia) {
-                        pp -= n - 1 - ia;
-                        ++ia;
-                    }
-                    const int im = ia + 1 + pp;
-                    const int ta = l % n, tb = l / n;
-                    const int a = line_node<n>(d, ia, ta, tb), c = line_node<n>(d, im, ta, tb);
-                    R za[kSplitSlots], zc[kSplitSlots];
+                const int x = p / n2, l = p - x * n2;
+                const int ta = l % n, tb = l / n;
+                const int a = x * sd + ta * ((d == 0) ? n : 1) + tb * ((d == 2) ? n : n2);
+                R za[kSplitSlots];
 #pragma unroll
-                    for (int k = 0; k < kSplitSlots; ++k) {
-                        za[k] = S[k * n3 + a];
-                        zc[k] = S[k * n3 + c];
-                    }
-                    const R a1 = S[(7 + d * 3 + 0) * n3 + a] + S[(7 + d * 3 + 0) * n3 + c];
-                    const R a2 = S[(7 + d * 3 + 1) * n3 + a] + S[(7 + d * 3 + 1) * n3 + c];
-                    const R a3 = S[(7 + d * 3 + 2) * n3 + a] + S[(7 + d * 3 + 2) * n3 + c];
+                for (int k = 0; k < kSplitSlots; ++k) za[k] = S[k * n3 + a];
+                const R *SJ = S + (7 + d * 3) * n3;
+                const R j1 = SJ[a], j2 = SJ[n3 + a], j3 = SJ[2 * n3 + a];
+#pragma unroll
+                for (int k = 1; k <= KP; ++k) {
+                    if (2 * k == n && x >= KP) break;
+                    const int xm = (x + k < n) ? x + k : x + k - n;
+                    const int c = a + (xm - x) * sd;
+                    R zc[kSplitSlots];
+#pragma unroll
+                    for (int q = 0; q < kSplitSlots; ++q) zc[q] = S[q * n3 + c];
                     R fs[5];
-                    split_pair<FORM>(za, zc, gam, hg, a1, a2, a3, fs);
+                    split_pair<FORM>(za, zc, gam, hg, j1 + SJ[c], j2 + SJ[n3 + c], j3 + SJ[2 * n3 + c], fs);
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) PB[v * W + w] = fs[v];
+                    for (int v = 0; v < 5; ++v) PB[(v * KP + k - 1) * n3 + p] = fs[v];
                 }
             }
             __syncthreads();
@@ -376,20 +377,31 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 const int ta = (d == 0) ? ijk[1] : ijk[0];
                 const int tb = (d == 2) ? ijk[1] : ijk[2];
                 const int l = ta + n * tb;
-                const int stride = (d == 0) ? 1 : (d == 1) ? n : n2;
-                const int base = p - i * stride;
+                const int base = p - i * sd;
                 const R *Drow = sD + i * n;
 #pragma unroll
                 for (int m = 0; m < n; ++m) {
                     const R Dm = Drow[m];
                     if (m != i) {
-                        const int lo = m < i ? m : i, hi = m < i ? i : m;
-                        const int w = l * NP + lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
+                        // the pair (i, m) sits with pair thread x n^2 + l in slot k - 1
+                        const int k = (m > i) ? m - i : m - i + n;
+                        int slot, x;
+                        if (2 * k < n) {
+                            slot = k;
+                            x = i;
+                        } else if (2 * k > n) {
+                            slot = n - k;
+                            x = m;
+                        } else {
+                            slot = KP;
+                            x = (i < KP) ? i : m;
+                        }
+                        const R *F = PB + (slot - 1) * n3 + x * n2 + l;
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) V[v] += Dm * PB[v * W + w];
+                        for (int v = 0; v < 5; ++v) V[v] += Dm * F[v * KP * n3];
                     }
                     if (NS) {
-                        const int pm = base + m * stride;
+                        const int pm = base + m * sd;
 #pragma unroll
                         for (int v = 1; v < 5; ++v) V[v] -= Dm * S[(16 + d * 5 + v) * n3 + pm];
                     }
