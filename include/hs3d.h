@@ -202,8 +202,10 @@ hs3d_status hs3d_rk3_step(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, dou
                           void *stream);
 
 /* nsteps steps as hs3d_rk3_step, replayed from a CUDA graph captured on
- * the first call for this (mesh, cfg, u, g, dt) (re-captured when any of them
- * changes).  Stream-ordered. */
+ * the first call for this (mesh, cfg, u, g, dt).  The mesh keeps the graphs of
+ * the two most recently used (cfg, u, g, dt), so a caller alternating between
+ * two state buffers replays without re-capture; a third combination replaces
+ * the least recently used graph.  Stream-ordered. */
 hs3d_status hs3d_rk3_run(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
                          int nsteps, void *stream);
 

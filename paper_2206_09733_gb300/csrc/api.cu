@@ -130,7 +130,8 @@ static hs3d_status mesh_alloc(hs3d_mesh *m)
 void mesh_free(hs3d_mesh *m)
 {
     if (!m) return;
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    for (auto &gs : m->gslot)
+        if (gs.exec) cudaGraphExecDestroy(gs.exec);
     void *ptrs[] = {m->X,    m->Ja,   m->Jaf, m->J,   m->invJ,          m->invJf,
                     m->uf,   m->fn,   m->fnf, m->fstar, m->grad, m->clk, m->diag_partials};
     for (void *p : ptrs)
@@ -402,16 +403,25 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
     if (nsteps < 0) return fail(HS3D_ERR_INVALID, "nsteps < 0");
     if (nsteps == 0) return HS3D_OK;
     std::lock_guard<std::mutex> lock(m->mu);
-    const hs3d_solver_cfg &k = m->g_cfg;   // field-wise: the struct has padding
-    bool same = m->gexec && m->g_u == u && m->g_g == g && m->g_dt == dt && k.physics == c->physics &&
-                k.surface_flux == c->surface_flux && k.volume_form == c->volume_form &&
-                k.precision == c->precision && k.gamma == c->gamma && k.Re == c->Re && k.Pr == c->Pr &&
-                k.Ma == c->Ma && k.cfl == c->cfl && k.time_scheme == c->time_scheme;
+    // a cached graph for exactly these arguments (cfg compared field-wise: the struct has padding)
+    hs3d_mesh::GraphSlot *slot = nullptr;
+    for (auto &gs : m->gslot) {
+        const hs3d_solver_cfg &k = gs.cfg;
+        if (gs.exec && gs.u == u && gs.g == g && gs.dt == dt && k.physics == c->physics &&
+            k.surface_flux == c->surface_flux && k.volume_form == c->volume_form && k.precision == c->precision &&
+            k.gamma == c->gamma && k.Re == c->Re && k.Pr == c->Pr && k.Ma == c->Ma && k.cfl == c->cfl &&
+            k.time_scheme == c->time_scheme)
+            slot = &gs;
+    }
     cudaError_t e = cudaSuccess;
-    if (!same) {
-        if (m->gexec) {
-            cudaGraphExecDestroy(m->gexec);
-            m->gexec = nullptr;
+    if (!slot) {
+        // capture into the empty or least recently used slot
+        slot = &m->gslot[0];
+        for (auto &gs : m->gslot)
+            if (!gs.exec || (slot->exec && gs.used < slot->used)) slot = &gs;
+        if (slot->exec) {
+            cudaGraphExecDestroy(slot->exec);
+            slot->exec = nullptr;
         }
         Item it = make_item(m, c, u, g, nullptr);
         cudaGraph_t graph = nullptr;
@@ -421,24 +431,25 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
             e = cudaStreamEndCapture(m->stream, &graph);
             if (e2 != cudaSuccess) e = e2;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gexec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&slot->exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            m->gexec = nullptr;
+            slot->exec = nullptr;
             cudaGetLastError();
             return cuda_fail(e, "graph capture");
         }
-        m->g_u = u;
-        m->g_g = g;
-        m->g_dt = dt;
-        m->g_cfg = *c;
+        slot->u = u;
+        slot->g = g;
+        slot->dt = dt;
+        slot->cfg = *c;
     }
+    slot->used = ++m->gtick;
     {
         Item it = make_item(m, c, u, g, nullptr);
         if (!(dt > 0.0)) e = prime_lambda(m->N, c, single_batch(it), m->clk, (cudaStream_t)stream);
         else if (c->precision == HS3D_MIXED32) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
     }
-    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(m->gexec, (cudaStream_t)stream);
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(slot->exec, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");
 }
 
@@ -471,6 +482,7 @@ hs3d_status hs3d_clock(const hs3d_mesh *m, double *t, int64_t *steps, int reset,
     if (e != cudaSuccess) return cuda_fail(e, "clock read");
     if (t) *t = h.t;
     if (steps) *steps = h.step;
+    if (h.bad == 2) return fail(HS3D_ERR_TIMEOUT, "a device-side wait for a bulk copy ran out of polls");
     if (h.bad) return fail(HS3D_ERR_NONPHYSICAL, "non-physical state detected (rho <= 0, p <= 0 or NaN)");
     return HS3D_OK;
 }

@@ -23,13 +23,18 @@ struct hs3d_mesh {
     double *diag_partials = nullptr;
     size_t bytes = 0;
     cudaStream_t stream = nullptr;  // private stream for set-up and graph capture
-    // graph cache of hs3d_rk3_run
+    // graph cache of hs3d_rk3_run: the two most recently used (cfg, u, g, dt)
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const double *u = nullptr;
+        const double *g = nullptr;
+        double dt = 0.0;
+        hs3d_solver_cfg cfg{};
+        unsigned long long used = 0;
+    };
     std::mutex mu;
-    cudaGraphExec_t gexec = nullptr;
-    const double *g_u = nullptr;
-    const double *g_g = nullptr;
-    double g_dt = 0.0;
-    hs3d_solver_cfg g_cfg{};
+    GraphSlot gslot[2];
+    unsigned long long gtick = 0;
 };
 
 namespace hs3d {

@@ -38,7 +38,8 @@ struct Clock {
     long long step;             // steps taken
     long long nsteps;           // > 0: stop after this many steps
     int done;                   // no more steps for this solve
-    int bad;                    // non-physical state seen (rho <= 0, p <= 0, NaN)
+    int bad;                    // 1: non-physical state seen (rho <= 0, p <= 0, NaN);
+                                // 2: a device-side wait for a bulk copy ran out of polls
 };
 
 // One solve (mesh + state) inside a launch.
@@ -213,6 +214,51 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+
+// Bulk asynchronous copies on the TMA engine (cp.async.bulk, sm_90+): one
+// thread moves a whole contiguous block (16-byte aligned addresses, size a
+// multiple of 16 bytes); completion is counted in bytes on an mbarrier in
+// shared memory (phase 0 completes once the arrival and all announced
+// bytes have landed).
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the async (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Wait for phase `parity` of the barrier, at most `limit` polls (each poll
+// may suspend the thread for a hardware-defined interval).  Returns false
+// when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit)
+{
+    const unsigned a = smem_u32(bar);
+    for (long long i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// Poll limit of the element kernels' bulk-copy waits: far beyond any copy's
+// duration (the copies are a few kilobytes), yet bounded.
+constexpr long long kBulkWaitPolls = 1LL << 22;
 
 // Copy `count` contiguous values of type R from global to shared memory with
 // the widest cp.async both addresses allow (16 bytes when the byte count and

@@ -118,8 +118,8 @@ __global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int slot)
             dt = fmin(dt, dtv);
         }
     }
-    if (!(dt > 0.0) || c->bad) {   // NaN or non-physical state
-        c->bad = 1;
+    if (!(dt > 0.0) || c->bad) {   // NaN or non-physical state (or a failed device wait)
+        if (!c->bad) c->bad = 1;
         c->done = 1;
         c->dt = 0.0;
         return;

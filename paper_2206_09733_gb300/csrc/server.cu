@@ -340,7 +340,7 @@ static void server_loop(hs3d_server *S)
             }
             const ClockView &cv = S->h_clk[k];
             bool complete = (r->req.t_final > 0.0) ? cv.t >= r->req.t_final : cv.step >= r->req.n_steps;
-            if (cv.bad) finish(S, r, HS3D_ERR_NONPHYSICAL, &cv);
+            if (cv.bad) finish(S, r, cv.bad == 2 ? HS3D_ERR_TIMEOUT : HS3D_ERR_NONPHYSICAL, &cv);
             else if (complete || cv.done) finish(S, r, HS3D_OK, &cv);
             else keep.push_back(r);
         }

@@ -203,6 +203,11 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     // mixed path: the FP64 state and register and 1/J of the RK update, staged
     // at the start so that their loads overlap the volume and surface work
     constexpr bool STAGE_RK = sizeof(R) == 4;
+    // with an even number of nodes per direction every staged block is a
+    // multiple of 16 bytes at 16-byte aligned addresses: one thread per element
+    // moves them with bulk copies (TMA engine) counted on the element's mbarrier
+    constexpr bool BULK = STAGE_RK && (n % 2 == 0);
+    __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     double *sRK = (double *)(smem_raw + rk_stage_offset<N, R, NS, FORM>(epb));
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
@@ -229,7 +234,28 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         // the six face-flux blocks of this element (slot 2d+1: the +d face,
         // own index; slot 2d: the -d face, owned by the -d neighbour) go to
         // shared memory by asynchronous copies, waited for before the barrier
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (BULK) {
+            if (p == 0) {
+                unsigned long long *bar = bulk_bar + le;
+                constexpr unsigned fb = 5 * n2 * sizeof(R), ub = 5 * n3 * 8, jb = n3 * 4;
+                mbar_init(bar, 1);
+                mbar_arrive_expect_tx(bar, 6 * fb + (stage >= 0 ? ub + (stage > 0 ? ub : 0) + jb : 0));
+                const R *FS = (const R *)it.fstar;
+#pragma unroll
+                for (int slot = 0; slot < 6; ++slot) {
+                    const int d = slot >> 1;
+                    const int owner = (slot & 1) ? e : nb.m[d];
+                    bulk_g2s(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, fb, bar);
+                }
+                if (stage >= 0) {
+                    double *mine = sRK + (size_t)le * 10 * n3;
+                    bulk_g2s(mine, it.u + (size_t)e * 5 * n3, ub, bar);
+                    if (stage > 0) bulk_g2s(mine + 5 * n3, it.g + (size_t)e * 5 * n3, ub, bar);
+                    bulk_g2s((float *)(sRK + (size_t)epb * 10 * n3) + (size_t)le * n3, it.invJf + (size_t)e * n3, jb,
+                             bar);
+                }
+            }
+        } else if constexpr (sizeof(R) == 4) {
             const R *FS = (const R *)it.fstar;
 #pragma unroll
             for (int slot = 0; slot < 6; ++slot) {
@@ -238,7 +264,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
             }
         }
-        if constexpr (STAGE_RK) {
+        if constexpr (STAGE_RK && !BULK) {
             if (stage >= 0) {
                 double *mine = sRK + (size_t)le * 10 * n3;
                 cp_async_block<double>(mine, it.u + (size_t)e * 5 * n3, 5 * n3, p, n3);
@@ -408,6 +434,15 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 }
             }
             __syncthreads();
+        }
+    }
+    if constexpr (BULK) {
+        // the face fluxes and the RK operands staged by the bulk copies; a wait
+        // that runs out of polls poisons the result (NaN) and flags the solve
+        if (valid && !mbar_wait(bulk_bar + le, 0, kBulkWaitPolls)) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) V[v] = (R)NAN;
+            if (itp->clk) itp->clk->bad = 2;
         }
     }
     if (valid) {

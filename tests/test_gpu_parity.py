@@ -302,6 +302,25 @@ def test_rk3_run_graph_equals_stepwise():
     assert torch.equal(u1, u2)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed32"])
+def test_rk3_run_alternating_buffers_equals_stepwise(prec):
+    """Three state buffers stepped in turn through hs3d_rk3_run (two cached
+    graphs, the third buffer evicting the least recently used one) give
+    bitwise the states of stepping each buffer on its own."""
+    _, gm = pair(4, 4, 4, 3, amp=0.05)
+    gc = hs.solver_cfg("ns", "roe", "ec", prec, gamma=G, Re=400.0)
+    u0 = gm.init_state(gm.empty_state(), "tgv", G, 0.1)
+    bufs = [(u0.clone(), torch.zeros_like(u0)) for _ in range(3)]
+    order = [0, 1, 0, 1, 2, 0, 2, 1, 1, 0]
+    for b in order:
+        gm.rk3_run(gc, bufs[b][0], bufs[b][1], 1)
+    for b in range(3):
+        u, g = u0.clone(), torch.zeros_like(u0)
+        for _ in range(order.count(b)):
+            gm.rk3_step(gc, u, g)
+        assert torch.equal(u, bufs[b][0]), b
+
+
 @pytest.mark.parametrize("volume,time", [("ec", "rk3"), ("kg", "rk4"), ("ducros", "rk3")])
 def test_tgv_ns_steps_parity_16cubed(volume, time):
     om, gm = pair(16, 16, 16, 3, amp=0.05)
