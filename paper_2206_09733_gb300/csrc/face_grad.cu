@@ -185,12 +185,32 @@ __device__ __forceinline__ const float *grad_metric<float>(const Item &it) { ret
 // [6 faces][4][n2] (slot 2d: the -d face, slot 2d+1: the +d face).  The
 // neighbour traces are gathered by all threads of the element before the
 // barrier, so the lifting reads no global memory.
+// Shared-memory words per element of k_grad: q (or, on the bulk path, the
+// staged FP32 state whose first four planes then hold q), Ja, neighbour traces.
+template <int N, typename R>
+constexpr bool grad_bulk()
+{
+    return sizeof(R) == 4 && (N + 1) % 2 == 0;
+}
+template <int N, typename R>
+constexpr int grad_per_elem()
+{
+    return ((grad_bulk<N, R>() ? 5 : 4) + 9) * (N + 1) * (N + 1) * (N + 1) + 24 * (N + 1) * (N + 1);
+}
+
 template <int N, typename R>
 __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constant__ Batch b, const Ops *__restrict__ ops)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-    constexpr int PER_ELEM = 13 * n3 + 24 * n2;
+    // mixed path with an even number of nodes per direction: the element's
+    // FP32 state and metric terms arrive in shared memory by bulk copies
+    // (TMA engine, one thread per element, counted on the element's
+    // mbarrier) while its threads gather the neighbour traces
+    constexpr bool BULK = grad_bulk<N, R>();
+    constexpr int QW = BULK ? 5 : 4;
+    constexpr int PER_ELEM = grad_per_elem<N, R>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     R *sD = (R *)smem_raw;                      // n*n
     R *sE = sD + ((n * n + 1) & ~1);            // [epb][PER_ELEM]
     const int epb = blockDim.x / n3;
@@ -206,29 +226,78 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
         if (itp->clk && itp->clk->done) valid = false;
     }
     R *q = sE + (size_t)le * PER_ELEM;
-    R *ja = q + 4 * n3;
+    R *ja = q + QW * n3;
     R *qn = ja + 9 * n3;
     R qin[4];
+    if constexpr (BULK) {
+        // the element's barrier is initialised before any of its threads polls it
+        if (valid && p == 0) mbar_init(bulk_bar + le, 1);
+        __syncthreads();
+    }
     if (valid) {
         const Item &it = *itp;
         const R gm1 = phys_of<R>(it).gm1;
-        const Nbrs nbs = elem_nbrs(e, it.ex, it.ey, it.ez);
-        for (int t = p; t < 6 * n2; t += n3) {
-            const int slot = t / n2, ab = t - slot * n2;
-            const int d = slot >> 1, plus = slot & 1;
-            const int nb = nbr_of_slot(nbs, slot);
-            const int pn = face_node<n>(d, plus ? 0 : N, ab % n, ab / n);
-            R g4[4];
-            grad_vars(load_prim<R>(it, (size_t)nb * 5 * n3 + pn, n3, gm1), g4);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) qn[(slot * 4 + v) * n2 + ab] = g4[v];
+        if constexpr (BULK) {
+            if (p == 0) {
+                unsigned long long *bar = bulk_bar + le;
+                mbar_arrive_expect_tx(bar, 14 * n3 * 4);
+                bulk_g2s(q, it.uf + (size_t)e * 5 * n3, 5 * n3 * 4, bar);
+                bulk_g2s(ja, it.Jaf + (size_t)e * 9 * n3, 9 * n3 * 4, bar);
+            }
         }
-        grad_vars(load_prim<R>(it, (size_t)e * 5 * n3 + p, n3, gm1), qin);
+        // neighbour traces of q: all loads of this thread's face points first
+        // (the loop is unrolled to its fixed trip count), then the conversions
+        const Nbrs nbs = elem_nbrs(e, it.ex, it.ey, it.ez);
+        const R *st;
+        if constexpr (sizeof(R) == 4) st = it.uf;
+        else st = it.u;
+        constexpr int IT = (6 * n2 + n3 - 1) / n3;
+        R raw[IT][5];
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const int t = p + k * n3;
+            if (t < 6 * n2) {
+                const int slot = t / n2, ab = t - slot * n2;
+                const int d = slot >> 1, plus = slot & 1;
+                const int pn = face_node<n>(d, plus ? 0 : N, ab % n, ab / n);
+                const R *src = st + (size_t)nbr_of_slot(nbs, slot) * 5 * n3 + pn;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) raw[k][v] = src[v * n3];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const int t = p + k * n3;
+            if (t < 6 * n2) {
+                const int slot = t / n2, ab = t - slot * n2;
+                R g4[4];
+                if constexpr (sizeof(R) == 4) grad_vars(prim_from_f(raw[k], gm1), g4);
+                else grad_vars(prim_from_u<R>(raw[k], gm1), g4);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) qn[(slot * 4 + v) * n2 + ab] = g4[v];
+            }
+        }
+        if constexpr (BULK) {
+            float us[5];
+            if (mbar_wait(bulk_bar + le, 0, kBulkWaitPolls)) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) us[v] = q[v * n3 + p];
+            } else {
+                // a wait that ran out of polls poisons the gradients and flags the solve
+#pragma unroll
+                for (int v = 0; v < 5; ++v) us[v] = NAN;
+                if (it.clk) it.clk->bad = 2;
+            }
+            grad_vars(prim_from_f(us, gm1), qin);
+        } else {
+            grad_vars(load_prim<R>(it, (size_t)e * 5 * n3 + p, n3, gm1), qin);
+            const R *JA = grad_metric<R>(it) + (size_t)e * 9 * n3 + p;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) ja[k * n3 + p] = JA[k * n3];
+        }
+        // (on the bulk path this overwrites the staged state at this node only)
 #pragma unroll
         for (int v = 0; v < 4; ++v) q[v * n3 + p] = qin[v];
-        const R *JA = grad_metric<R>(it) + (size_t)e * 9 * n3 + p;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ja[k * n3 + p] = JA[k * n3];
     }
     __syncthreads();
     if (!valid) return;
@@ -310,7 +379,7 @@ static cudaError_t grad_launch(const Batch &b, cudaStream_t s)
     int epb = elems_per_block_p(N, sizeof(R) == 4 ? HS3D_MIXED32 : HS3D_FP64, 0);
     if (epb * n3 > grad_threads<N>()) epb = grad_threads<N>() / n3;
     int threads = epb * n3;
-    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * (13 * n3 + 24 * (N + 1) * (N + 1)));
+    size_t smem = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * grad_per_elem<N, R>());
     unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;

@@ -71,20 +71,20 @@ __device__ __forceinline__ const float *metric_ptr<float>(const Item &it) { retu
 // Residual store or RK stage of one node from V (volume + surface sum), then,
 // after the last stage (lam_slot >= 0), the dt maxima of the updated state.
 // u holds the FP64 state on the FP64 path (loaded here on the mixed path).
-// Mixed path: sUG, when given, is the element's [u (5 n3), g (5 n3)] FP64
-// block and sIJ its 1/J (FP32), staged in shared memory by asynchronous
-// copies at the start of the kernel (g only for stage > 0).
+// Mixed path: sU and sG, when given, are the element's FP64 u and g
+// blocks (5 n3 each) and sIJ its 1/J (FP32), staged in shared memory by
+// asynchronous copies at the start of the kernel (g only for stage > 0).
 template <typename R, bool NS>
 __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3, const R V[5], double u[5],
                                             int stage, double rkA, double rkB, int lam_slot, double &lc, double &lv,
-                                            bool &lam_active, const double *sUG = nullptr,
+                                            bool &lam_active, const double *sU = nullptr, const double *sG = nullptr,
                                             const float *sIJ = nullptr)
 {
     if constexpr (sizeof(R) == 4) {
         // the FP64 state is needed only for the RK accumulation
         if (stage >= 0) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = sUG ? sUG[v * n3 + p] : it.u[(size_t)e * 5 * n3 + p + v * n3];
+            for (int v = 0; v < 5; ++v) u[v] = sU ? sU[v * n3 + p] : it.u[(size_t)e * 5 * n3 + p + v * n3];
         }
     }
 
@@ -127,7 +127,7 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 const double inc = f2d_exact(-(float)V[v] * sdt);
-                const double gv = (stage == 0) ? inc : fma(A, sUG ? sUG[(5 + v) * n3 + p] : Gp[v * n3], inc);
+                const double gv = (stage == 0) ? inc : fma(A, sG ? sG[v * n3 + p] : Gp[v * n3], inc);
                 Gp[v * n3] = gv;
                 u[v] = fma(B, gv, u[v]);
                 Up[v * n3] = u[v];
@@ -181,11 +181,23 @@ __host__ __device__ constexpr size_t rk_stage_offset(int epb)
     return (b + 15) & ~(size_t)15;
 }
 
+// Whether the mixed element kernel also stages the RK register g (40 bytes
+// of shared memory per node more than u alone).  Measured: the bandwidth-
+// bound standard form gains from it (64^3 N = 3: -12%); the split forms,
+// whose resident CTAs are limited by shared memory, do not (16^3 N = 3 EC:
+// +8% with g staged, 32^3 unchanged), so they read g where it is used.
+template <int N, typename R, bool NS, int FORM>
+__host__ __device__ constexpr bool rk_stage_g()
+{
+    return FORM == HS3D_VOL_STANDARD;
+}
+
 template <int N, typename R, bool NS, int FORM>
 __host__ __device__ constexpr size_t vol_smem_bytes(int epb)
 {
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
-    return rk_stage_offset<N, R, NS, FORM>(epb) + (sizeof(R) == 4 ? (size_t)epb * n3 * (10 * 8 + 4) : 0);
+    constexpr int rkw = rk_stage_g<N, R, NS, FORM>() ? 10 : 5;
+    return rk_stage_offset<N, R, NS, FORM>(epb) + (sizeof(R) == 4 ? (size_t)epb * n3 * (rkw * 8 + 4) : 0);
 }
 
 template <int N, typename R, bool NS, int FORM>
@@ -207,6 +219,8 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     // multiple of 16 bytes at 16-byte aligned addresses: one thread per element
     // moves them with bulk copies (TMA engine) counted on the element's mbarrier
     constexpr bool BULK = STAGE_RK && (n % 2 == 0);
+    constexpr bool STAGE_G = rk_stage_g<N, R, NS, FORM>();
+    constexpr int RKW = STAGE_G ? 10 : 5;   // staged FP64 values per node: u (and g)
     __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     double *sRK = (double *)(smem_raw + rk_stage_offset<N, R, NS, FORM>(epb));
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
@@ -239,7 +253,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 unsigned long long *bar = bulk_bar + le;
                 constexpr unsigned fb = 5 * n2 * sizeof(R), ub = 5 * n3 * 8, jb = n3 * 4;
                 mbar_init(bar, 1);
-                mbar_arrive_expect_tx(bar, 6 * fb + (stage >= 0 ? ub + (stage > 0 ? ub : 0) + jb : 0));
+                mbar_arrive_expect_tx(bar, 6 * fb + (stage >= 0 ? ub + (STAGE_G && stage > 0 ? ub : 0) + jb : 0));
                 const R *FS = (const R *)it.fstar;
 #pragma unroll
                 for (int slot = 0; slot < 6; ++slot) {
@@ -248,10 +262,10 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                     bulk_g2s(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, fb, bar);
                 }
                 if (stage >= 0) {
-                    double *mine = sRK + (size_t)le * 10 * n3;
+                    double *mine = sRK + (size_t)le * RKW * n3;
                     bulk_g2s(mine, it.u + (size_t)e * 5 * n3, ub, bar);
-                    if (stage > 0) bulk_g2s(mine + 5 * n3, it.g + (size_t)e * 5 * n3, ub, bar);
-                    bulk_g2s((float *)(sRK + (size_t)epb * 10 * n3) + (size_t)le * n3, it.invJf + (size_t)e * n3, jb,
+                    if (STAGE_G && stage > 0) bulk_g2s(mine + 5 * n3, it.g + (size_t)e * 5 * n3, ub, bar);
+                    bulk_g2s((float *)(sRK + (size_t)epb * RKW * n3) + (size_t)le * n3, it.invJf + (size_t)e * n3, jb,
                              bar);
                 }
             }
@@ -266,10 +280,11 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         }
         if constexpr (STAGE_RK && !BULK) {
             if (stage >= 0) {
-                double *mine = sRK + (size_t)le * 10 * n3;
+                double *mine = sRK + (size_t)le * RKW * n3;
                 cp_async_block<double>(mine, it.u + (size_t)e * 5 * n3, 5 * n3, p, n3);
-                if (stage > 0) cp_async_block<double>(mine + 5 * n3, it.g + (size_t)e * 5 * n3, 5 * n3, p, n3);
-                cp_async_block<float>((float *)(sRK + (size_t)epb * 10 * n3) + (size_t)le * n3,
+                if (STAGE_G && stage > 0)
+                    cp_async_block<double>(mine + 5 * n3, it.g + (size_t)e * 5 * n3, 5 * n3, p, n3);
+                cp_async_block<float>((float *)(sRK + (size_t)epb * RKW * n3) + (size_t)le * n3,
                                       it.invJf + (size_t)e * n3, n3, p, n3);
             }
         }
@@ -481,7 +496,8 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         if constexpr (STAGE_RK) {
             if (stage >= 0)
                 node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active,
-                                   sRK + (size_t)le * 10 * n3, (const float *)(sRK + (size_t)epb * 10 * n3) + le * n3);
+                                   sRK + (size_t)le * RKW * n3, STAGE_G ? sRK + (size_t)le * RKW * n3 + 5 * n3 : nullptr,
+                                   (const float *)(sRK + (size_t)epb * RKW * n3) + le * n3);
             else
                 node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active);
         } else {
