@@ -31,7 +31,11 @@ def nvcc() -> str:
 
 
 def _flags(ptxas_verbose: bool):
-    f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"] + ARCH
+    # FP32 division and square root (the mixed path's flux arithmetic) use the
+    # hardware approximations (a few ulp, no IEEE fix-up sequence); FP64
+    # arithmetic is unaffected.
+    f = ["-O3", "-std=c++17", "-lineinfo", "-prec-div=false", "-prec-sqrt=false", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+         "--expt-relaxed-constexpr"] + ARCH
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]
     return f

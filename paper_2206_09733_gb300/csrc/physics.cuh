@@ -102,7 +102,7 @@ __device__ __forceinline__ Prim<double> prim_from_u<double>(const double u[5], d
 __device__ __forceinline__ Prim<float> prim_from_f(const float uf[5], float gm1)
 {
     const float r = uf[0], m1 = uf[1], m2 = uf[2], m3 = uf[3], E = uf[4];
-    const float ir = __frcp_rn(r);
+    const float ir = __fdividef(1.0f, r);
     Prim<float> q;
     q.rho = r;
     q.v1 = m1 * ir;
@@ -285,8 +285,10 @@ template <typename R>
 __device__ __forceinline__ R rcp_(R x);
 template <>
 __device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
+// FP32: the hardware approximate reciprocal (at most 2 ulp, no IEEE fix-up
+// path), well inside the rounding the FP32 flux arithmetic makes anyway.
 template <>
-__device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp_<float>(float x) { return __fdividef(1.0f, x); }
 
 // Per-node quantities the Chandrashekar flux uses.
 template <typename R>
