@@ -181,13 +181,20 @@ __host__ __device__ constexpr size_t rk_stage_offset(int epb)
     return (b + 15) & ~(size_t)15;
 }
 
-// Whether the mixed element kernel also stages the RK register g (40 bytes
-// of shared memory per node more than u alone).  Measured: the bandwidth-
-// bound standard form gains from it (64^3 N = 3: -12%); the split forms,
-// whose resident CTAs are limited by shared memory, do not (16^3 N = 3 EC:
-// +8% with g staged, 32^3 unchanged), so they read g where it is used.
+// Whether the mixed element kernel stages the RK register g and the FP64
+// state u (40 bytes of shared memory per node each).  Measured: the
+// bandwidth-bound standard form gains from them (64^3 N = 3: -12%); the
+// split forms, whose resident CTAs are limited by shared memory, do not
+// (16^3 N = 3 EC: 8% faster without g, a further 2% without u), so they
+// read u and g where the RK update uses them.
 template <int N, typename R, bool NS, int FORM>
 __host__ __device__ constexpr bool rk_stage_g()
+{
+    return FORM == HS3D_VOL_STANDARD;
+}
+
+template <int N, typename R, bool NS, int FORM>
+__host__ __device__ constexpr bool rk_stage_u()
 {
     return FORM == HS3D_VOL_STANDARD;
 }
@@ -196,7 +203,7 @@ template <int N, typename R, bool NS, int FORM>
 __host__ __device__ constexpr size_t vol_smem_bytes(int epb)
 {
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
-    constexpr int rkw = rk_stage_g<N, R, NS, FORM>() ? 10 : 5;
+    constexpr int rkw = (rk_stage_u<N, R, NS, FORM>() ? 5 : 0) + (rk_stage_g<N, R, NS, FORM>() ? 5 : 0);
     return rk_stage_offset<N, R, NS, FORM>(epb) + (sizeof(R) == 4 ? (size_t)epb * n3 * (rkw * 8 + 4) : 0);
 }
 
@@ -219,8 +226,10 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
     // multiple of 16 bytes at 16-byte aligned addresses: one thread per element
     // moves them with bulk copies (TMA engine) counted on the element's mbarrier
     constexpr bool BULK = STAGE_RK && (n % 2 == 0);
+    constexpr bool STAGE_U = rk_stage_u<N, R, NS, FORM>();
     constexpr bool STAGE_G = rk_stage_g<N, R, NS, FORM>();
-    constexpr int RKW = STAGE_G ? 10 : 5;   // staged FP64 values per node: u (and g)
+    constexpr int RKW = (STAGE_U ? 5 : 0) + (STAGE_G ? 5 : 0);   // staged FP64 values per node
+    constexpr int GOFF = STAGE_U ? 5 : 0;                          // g's plane offset in the block
     __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     double *sRK = (double *)(smem_raw + rk_stage_offset<N, R, NS, FORM>(epb));
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops_D<R>(ops, t);
@@ -253,7 +262,8 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 unsigned long long *bar = bulk_bar + le;
                 constexpr unsigned fb = 5 * n2 * sizeof(R), ub = 5 * n3 * 8, jb = n3 * 4;
                 mbar_init(bar, 1);
-                mbar_arrive_expect_tx(bar, 6 * fb + (stage >= 0 ? ub + (STAGE_G && stage > 0 ? ub : 0) + jb : 0));
+                mbar_arrive_expect_tx(bar, 6 * fb + (stage >= 0 ? (STAGE_U ? ub : 0) + (STAGE_G && stage > 0 ? ub : 0) + jb
+                                                               : 0));
                 const R *FS = (const R *)it.fstar;
 #pragma unroll
                 for (int slot = 0; slot < 6; ++slot) {
@@ -263,8 +273,8 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 }
                 if (stage >= 0) {
                     double *mine = sRK + (size_t)le * RKW * n3;
-                    bulk_g2s(mine, it.u + (size_t)e * 5 * n3, ub, bar);
-                    if (STAGE_G && stage > 0) bulk_g2s(mine + 5 * n3, it.g + (size_t)e * 5 * n3, ub, bar);
+                    if (STAGE_U) bulk_g2s(mine, it.u + (size_t)e * 5 * n3, ub, bar);
+                    if (STAGE_G && stage > 0) bulk_g2s(mine + GOFF * n3, it.g + (size_t)e * 5 * n3, ub, bar);
                     bulk_g2s((float *)(sRK + (size_t)epb * RKW * n3) + (size_t)le * n3, it.invJf + (size_t)e * n3, jb,
                              bar);
                 }
@@ -281,9 +291,9 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         if constexpr (STAGE_RK && !BULK) {
             if (stage >= 0) {
                 double *mine = sRK + (size_t)le * RKW * n3;
-                cp_async_block<double>(mine, it.u + (size_t)e * 5 * n3, 5 * n3, p, n3);
+                if (STAGE_U) cp_async_block<double>(mine, it.u + (size_t)e * 5 * n3, 5 * n3, p, n3);
                 if (STAGE_G && stage > 0)
-                    cp_async_block<double>(mine + 5 * n3, it.g + (size_t)e * 5 * n3, 5 * n3, p, n3);
+                    cp_async_block<double>(mine + GOFF * n3, it.g + (size_t)e * 5 * n3, 5 * n3, p, n3);
                 cp_async_block<float>((float *)(sRK + (size_t)epb * RKW * n3) + (size_t)le * n3,
                                       it.invJf + (size_t)e * n3, n3, p, n3);
             }
@@ -496,7 +506,8 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
         if constexpr (STAGE_RK) {
             if (stage >= 0)
                 node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active,
-                                   sRK + (size_t)le * RKW * n3, STAGE_G ? sRK + (size_t)le * RKW * n3 + 5 * n3 : nullptr,
+                                   STAGE_U ? sRK + (size_t)le * RKW * n3 : nullptr,
+                                   STAGE_G ? sRK + (size_t)le * RKW * n3 + GOFF * n3 : nullptr,
                                    (const float *)(sRK + (size_t)epb * RKW * n3) + le * n3);
             else
                 node_update<R, NS>(it, e, p, n3, V, u, stage, rkA, rkB, lam_slot, lc, lv, lam_active);
