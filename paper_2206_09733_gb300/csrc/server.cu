@@ -7,7 +7,11 @@
 //   2. group the running requests by (N, physics, surface flux, volume form,
 //      precision, time scheme) and advance every group by one RK step with shared
 //      launches: each kernel walks a table of items (one per request), so one
-//      launch covers all requests of a group;
+//      launch covers all requests of a group.  The launches of all groups
+//      (and the clock gather of step 3) are captured into one CUDA graph,
+//      replayed for as long as the set of running requests stays the same
+//      and re-captured (updated in place where the topology allows) when a
+//      request joins or leaves;
 //   3. gather the clocks of all running requests into one small array, copy
 //      it to pinned host memory and wait for it with a bounded poll;
 //   4. retire finished requests (copy the state out, free the slot, stamp the
@@ -97,6 +101,9 @@ struct hs3d_server {
     ClockView *d_clk = nullptr, *h_clk = nullptr;
     int clk_cap = 0;
     cudaEvent_t ev = nullptr;
+    // the captured step of the current set of running requests (ids in table order)
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uint64_t> gkey;
 
     double now() const
     {
@@ -217,6 +224,10 @@ static cudaError_t ensure_capacity(hs3d_server *S, int n)
     return cudaSuccess;
 }
 
+static cudaError_t capture_step(hs3d_server *S, std::vector<ServerReq *> &run, std::vector<Item> &items,
+                                const std::vector<std::pair<int, int>> &ranges,
+                                const std::vector<const hs3d_solver_cfg *> &cfgs);
+
 // One RK step for every running request, grouped into shared launches, then
 // the clocks of all running requests land in S->h_clk (in `running` order).
 static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
@@ -243,6 +254,38 @@ static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
     std::vector<ServerReq *> sorted(n);
     for (int k = 0; k < n; ++k) sorted[k] = run[order[k]];
     run.swap(sorted);
+    std::vector<uint64_t> key(n);
+    for (int k = 0; k < n; ++k) key[k] = run[k]->id;
+    if (!(S->gexec && key == S->gkey)) {
+        e = capture_step(S, run, items, ranges, cfgs);
+        if (e != cudaSuccess) return e;
+        S->gkey.swap(key);
+    }
+    e = cudaGraphLaunch(S->gexec, S->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ev, S->stream);
+    if (e != cudaSuccess) return e;
+    // bounded wait for the step
+    double t_start = S->now();
+    while (true) {
+        cudaError_t q = cudaEventQuery(S->ev);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return q;
+        if (S->now() - t_start > S->wait_limit_s) return cudaErrorTimeout;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return cudaSuccess;
+}
+
+// Upload the item table of a new set of running requests (sorted into
+// groups), capture one step of all groups plus the clock gather into a graph
+// and make S->gexec execute it (updating the previous executable graph in
+// place when the topology allows, else instantiating a new one).
+static cudaError_t capture_step(hs3d_server *S, std::vector<ServerReq *> &run, std::vector<Item> &items,
+                                const std::vector<std::pair<int, int>> &ranges,
+                                const std::vector<const hs3d_solver_cfg *> &cfgs)
+{
+    const int n = (int)run.size();
+    cudaError_t e = cudaSuccess;
     for (size_t b = 0; b < ranges.size(); ++b) {
         long long eb = 0, fb = 0;
         for (int k = ranges[b].first; k < ranges[b].second; ++k) {
@@ -256,6 +299,10 @@ static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
         }
     }
     e = cudaMemcpyAsync(S->d_items, items.data(), sizeof(Item) * n, cudaMemcpyHostToDevice, S->stream);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
     for (size_t b = 0; b < ranges.size() && e == cudaSuccess; ++b) {
         int lo = ranges[b].first, hi = ranges[b].second;
         Batch bt{};
@@ -278,18 +325,24 @@ static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->h_clk, S->d_clk, sizeof(ClockView) * n, cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(S->ev, S->stream);
-    if (e != cudaSuccess) return e;
-    // bounded wait for the step
-    double t_start = S->now();
-    while (true) {
-        cudaError_t q = cudaEventQuery(S->ev);
-        if (q == cudaSuccess) break;
-        if (q != cudaErrorNotReady) return q;
-        if (S->now() - t_start > S->wait_limit_s) return cudaErrorTimeout;
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    cudaError_t e2 = cudaStreamEndCapture(S->stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && S->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(S->gexec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(S->gexec);
+            S->gexec = nullptr;
+        }
     }
-    return cudaSuccess;
+    if (e == cudaSuccess && !S->gexec) e = cudaGraphInstantiate(&S->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        if (S->gexec) cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+        S->gkey.clear();
+    }
+    return e;
 }
 
 static void server_loop(hs3d_server *S)
@@ -395,6 +448,7 @@ void hs3d_server_destroy(hs3d_server *S)
         if (r->state == Q_RUNNING) release(S, r);
         delete r;
     }
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
     if (S->d_items) cudaFree(S->d_items);
     if (S->d_clk) cudaFree(S->d_clk);
     if (S->h_clk) cudaFreeHost(S->h_clk);
