@@ -401,8 +401,10 @@ def run_hs3d(args, world, rank, local):
 
     extra = {}
     if args.workloads and args.mesh == 16:
-        extra["tgv_32cubed_N7_standard_roe_br1"] = run_workload("cfg3", 32, 7, "ns", "roe", "standard", 5, 2)
-        extra["tgv_64cubed_N3_standard_lf_euler"] = run_workload("sweep", 64, 3, "euler", "lf", "standard", 5, 2)
+        extra["tgv_32cubed_N7_standard_roe_br1"] = run_workload("cfg3", 32, 7, "ns", "roe", "standard", 5, 2,
+                                                                precisions=("mixed32", "mixed_tc", "fp64"))
+        extra["tgv_64cubed_N3_standard_lf_euler"] = run_workload("sweep", 64, 3, "euler", "lf", "standard", 5, 2,
+                                                                 precisions=("mixed32", "mixed_tc", "fp64"))
         extra["tgv_52cubed_N4_standard_lf_euler"] = run_workload("sweep", 52, 4, "euler", "lf", "standard", 5, 2)
         extra["tgv_64cubed_N3_standard_roe_br1"] = run_workload("sweep", 64, 3, "ns", "roe", "standard", 5, 2)
         for vol, surf, tm in (("kg", "roe", "rk4"), ("pirozzoli", "roe", "rk3"), ("ducros", "roe", "rk3"),
@@ -499,6 +501,7 @@ def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisio
     out = {"E": Ed ** 3, "N": Nd, "nodes": npts,
            "scheme": f"{physics} {surface} surface, {volume} volume, {time} ({stages} stages), {nodes} nodes"}
     stream = torch.cuda.current_stream()
+    finals = {}
     for prec in precisions:
         cfg = hs.solver_cfg(physics, surface, volume, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL, time=time)
         mesh.autotune(cfg)
@@ -516,8 +519,15 @@ def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisio
         if nodes == "lobatto":   # the byte model counts Gauss-Lobatto traces (one node per face point)
             gbs = step_bytes(prec, physics, Ed ** 3, n, stages) / (ms * 1e-3) / 1e9
             out[prec].update({"hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac": round(gbs / measured_hbm_peak()[0], 4)})
-        del u, g
-    del mesh
+        finals[prec] = u
+        del g
+    # every precision ran warmup + steps steps from the same initial state
+    if "fp64" in finals:
+        ref = finals["fp64"]
+        for prec, u in finals.items():
+            if prec != "fp64":
+                out[prec]["l2_rel_vs_fp64_gpu"] = float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))
+    del finals, mesh
     torch.cuda.empty_cache()
     return out
 

@@ -25,7 +25,7 @@ FLUX_LF, FLUX_ROE, FLUX_EC, FLUX_RUSANOV, FLUX_LDROE, FLUX_MATRIX = 0, 1, 2, 3, 
 VOL_STANDARD, VOL_EC, VOL_KG, VOL_PIROZZOLI, VOL_DUCROS, VOL_MORINISHI, VOL_IR = 0, 1, 2, 3, 4, 5, 6
 TIME_RK3, TIME_RK4 = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
-FP64, MIXED32 = 0, 1
+FP64, MIXED32, MIXED_TC = 0, 1, 2
 IC_VORTEX, IC_TGV = 0, 1
 
 PHYSICS = {"euler": EULER, "ns": NS}
@@ -35,7 +35,7 @@ VOLUME = {"standard": VOL_STANDARD, "ec": VOL_EC, "kg": VOL_KG, "pirozzoli": VOL
           "morinishi": VOL_MORINISHI, "ir": VOL_IR}
 TIME = {"rk3": TIME_RK3, "rk4": TIME_RK4}
 NODES = {"lobatto": NODES_LOBATTO, "gauss": NODES_GAUSS}
-PRECISION = {"fp64": FP64, "mixed32": MIXED32}
+PRECISION = {"fp64": FP64, "mixed32": MIXED32, "mixed_tc": MIXED_TC}
 
 # every entry point declared in include/hs3d.h
 EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh_geometry", "hs3d_init_state",

@@ -49,7 +49,7 @@ hs3d_status validate_cfg(const hs3d_solver_cfg *c)
         return fail(HS3D_ERR_INVALID, "bad volume_form %d", c->volume_form);
     if (c->time_scheme != HS3D_TIME_RK3 && c->time_scheme != HS3D_TIME_RK4)
         return fail(HS3D_ERR_INVALID, "bad time_scheme %d", c->time_scheme);
-    if (c->precision != HS3D_FP64 && c->precision != HS3D_MIXED32)
+    if (c->precision != HS3D_FP64 && c->precision != HS3D_MIXED32 && c->precision != HS3D_MIXED_TC)
         return fail(HS3D_ERR_UNSUPPORTED, "unsupported precision %d", c->precision);
     if (!(c->gamma > 1.0)) return fail(HS3D_ERR_INVALID, "gamma must be > 1");
     if (c->physics == HS3D_NS && (!(c->Re > 0.0) || !(c->Pr > 0.0)))
@@ -283,7 +283,7 @@ cudaError_t enqueue_rk3_step(int N, const hs3d_solver_cfg *c, Batch b, double dt
     b.dt_fixed = dt > 0.0 ? dt : 0.0;
     int slot = fresh_lambda ? 0 : 1;
     if (fresh_lambda && !(dt > 0.0)) e = launch_lambda(N, c->precision, c->physics, b, 0, s);
-    else if (fresh_lambda && c->precision == HS3D_MIXED32) e = launch_shadow(N, b, s);
+    else if (fresh_lambda && c->precision != HS3D_FP64) e = launch_shadow(N, b, s);
     if (e == cudaSuccess) e = launch_dt_finalize(N, b, 0, slot, s);
     const int ns = rk_stages(c->time_scheme);
     for (int k = 0; k < ns && e == cudaSuccess; ++k) e = enqueue_stage(N, c, b, k, k == ns - 1 ? 1 : -1, s);
@@ -370,7 +370,7 @@ hs3d_status hs3d_residual(const hs3d_mesh *m, const hs3d_solver_cfg *c, const do
     Item it = make_item(m, c, u, nullptr, dudt);
     it.clk = nullptr;
     cudaError_t e = cudaSuccess;
-    if (c->precision == HS3D_MIXED32) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
+    if (c->precision != HS3D_FP64) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
     if (e == cudaSuccess) e = enqueue_stage(m->N, c, single_batch(it), -1, -1, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
 }
@@ -447,7 +447,7 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
     {
         Item it = make_item(m, c, u, g, nullptr);
         if (!(dt > 0.0)) e = prime_lambda(m->N, c, single_batch(it), m->clk, (cudaStream_t)stream);
-        else if (c->precision == HS3D_MIXED32) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
+        else if (c->precision != HS3D_FP64) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
     }
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(slot->exec, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");

@@ -121,7 +121,7 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
     b.dt_fixed = dt > 0.0 ? dt : 0.0;
     cudaError_t e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess && !(dt > 0.0)) e = launch_lambda(m->N, c->precision, c->physics, b, 0, s);
-    else if (e == cudaSuccess && c->precision == HS3D_MIXED32) e = launch_shadow(m->N, b, s);
+    else if (e == cudaSuccess && c->precision != HS3D_FP64) e = launch_shadow(m->N, b, s);
     if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 0, 0, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     int k = 2;

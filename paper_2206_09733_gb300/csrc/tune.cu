@@ -46,7 +46,7 @@ static void load_cache_locked()
     while ((s = strchr(s, '"')) != nullptr) {
         int N = 0, prec = 0, which = 0, epb = 0;
         if (sscanf(s, "\"N%d_p%d_k%d\": %d", &N, &prec, &which, &epb) == 4 && N >= 1 && N <= kMaxN && epb >= 1 &&
-            epb <= 64 && (prec == 0 || prec == 1) && (which == 0 || which == 1))
+            epb <= 64 && prec >= 0 && prec <= 2 && (which == 0 || which == 1))
             set_elems_per_block_p(N, prec, which, epb);
         s = strchr(s + 1, '"');
         if (s) ++s;
@@ -63,7 +63,7 @@ static void save_cache_locked()
     fprintf(f, "{");
     bool first = true;
     for (int N = 1; N <= kMaxN; ++N)
-        for (int prec = 0; prec < 2; ++prec)
+        for (int prec = 0; prec < 3; ++prec)
             for (int which = 0; which < 2; ++which) {
                 int v = tuned_elems_per_block(N, prec, which);
                 if (v <= 0) continue;
@@ -145,7 +145,7 @@ extern "C" hs3d_status hs3d_autotune(const hs3d_mesh *mc, const hs3d_solver_cfg 
     it.clk = clk;
     Batch b = single_batch(it);
     // the face fluxes the volume kernel reads: one face pass
-    if (e == cudaSuccess && c->precision == HS3D_MIXED32) e = launch_shadow(m->N, b, s);
+    if (e == cudaSuccess && c->precision != HS3D_FP64) e = launch_shadow(m->N, b, s);
     if (e == cudaSuccess && c->physics == HS3D_NS) e = launch_grad(m->N, c->precision, b, s);
     if (e == cudaSuccess) e = launch_face(m->N, c->precision, c->physics, c->surface_flux, b, s);
     int best[2] = {0, 0};

@@ -32,24 +32,28 @@ void rk_coeffs(int scheme, int k, double *A, double *B)
     *B = four ? kRK4B[k] : kRK3B[k];
 }
 
-static int g_epb[kMaxn + 1][2][2] = {};
+// Tuned elements per CTA by (N, precision FP64 / MIXED32 / MIXED_TC, kernel).
+static int g_epb[kMaxn + 1][3][2] = {};
 
-int tuned_elems_per_block(int N, int prec, int which) { return g_epb[N][prec ? 1 : 0][which]; }
+static int prec_slot(int prec) { return prec == HS3D_FP64 ? 0 : prec == HS3D_MIXED_TC ? 2 : 1; }
+
+int tuned_elems_per_block(int N, int prec, int which) { return g_epb[N][prec_slot(prec)][which]; }
 
 int elems_per_block_p(int N, int prec, int which)
 {
-    int v = g_epb[N][prec ? 1 : 0][which];
+    int v = g_epb[N][prec_slot(prec)][which];
     if (v > 0) return v;
     int n3 = (N + 1) * (N + 1) * (N + 1);
     int e = 256 / n3;
     return e < 1 ? 1 : e;
 }
 
-void set_elems_per_block_p(int N, int prec, int which, int epb) { g_epb[N][prec ? 1 : 0][which] = epb; }
+void set_elems_per_block_p(int N, int prec, int which, int epb) { g_epb[N][prec_slot(prec)][which] = epb; }
 
 cudaError_t prepare_volume(int N)
 {
     cudaError_t e = prepare_volume_form<HS3D_VOL_STANDARD>(N);
+    if (e == cudaSuccess) e = prepare_volume_form<kVolStdTC>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_EC>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_KG>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_PIROZZOLI>(N);
@@ -73,6 +77,7 @@ cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, co
     }
     switch (form) {
         case HS3D_VOL_STANDARD:
+            if (prec == HS3D_MIXED_TC) return launch_volume_form<kVolStdTC>(N, prec, physics, b, stage, A, B, lam_slot, s);
             return launch_volume_form<HS3D_VOL_STANDARD>(N, prec, physics, b, stage, A, B, lam_slot, s);
         case HS3D_VOL_EC: return launch_volume_form<HS3D_VOL_EC>(N, prec, physics, b, stage, A, B, lam_slot, s);
         case HS3D_VOL_KG: return launch_volume_form<HS3D_VOL_KG>(N, prec, physics, b, stage, A, B, lam_slot, s);

@@ -394,6 +394,8 @@ def test_tgv_32cubed_N7_residual_on_a_seeded_subsample():
     r64 = host(r)[sub]
     gm.residual(gc32, u, r)
     r32 = host(r)[sub]
+    gm.residual(cfgs("ns", "roe", "standard", precision="mixed_tc", Re=1600.0)[1], u, r)
+    rtc = host(r)[sub]
     kappa = conditioning(om, oc, u0, ref_full)
     assert rel(r64, ref) < max(TOL64, 32 * kappa)
     print(f"32^3 N=7 subsample: FP64 rel {rel(r64, ref):.3e} (bar {max(TOL64, 32 * kappa):.1e}), "
@@ -403,3 +405,7 @@ def test_tgv_32cubed_N7_residual_on_a_seeded_subsample():
     # per-residual error of the mixed path is ~1e-2 here (states integrated
     # in FP64 stay within ~1e-7, test_gpu_mixed.py)
     assert rel(r32, ref) < 5e-2
+    # the tensor-core contraction (TF32 split operands) is as accurate as the FP32 one
+    print(f"32^3 N=7 subsample: tensor-core rel {rel(rtc, ref):.3e}")
+    assert rel(rtc, ref) < 5e-2
+    assert rel(rtc, ref) < 2 * rel(r32, ref)
