@@ -44,6 +44,7 @@ N = 3
 AMP = 0.05
 MA, RE, PR, GAMMA, CFL = 0.1, 1600.0, 0.72, 1.4, 0.5
 NODES = EX * EY * EZ * (N + 1) ** 3
+VOLUME_FORM = "ec"
 METRIC = "DOF-stage-updates/s"
 WORKLOAD = ("NS Taylor-Green vortex Ma 0.1 Re 1600, [-pi,pi]^3, 16^3 curved hex (amp 0.05), N=3 (64^3 DOF), "
             "EC split form + Roe + BR1, Williamson RK3 CFL 0.5")
@@ -64,11 +65,19 @@ def parse():
     ap.add_argument("--stress-emax", type=int, default=40)
     ap.add_argument("--no-workloads", dest="workloads", action="store_false",
                     help="skip the larger configurations reported beside the line")
-    ap.add_argument("--only", choices=["mixed32", "fp64"], default=None,
+    ap.add_argument("--only", choices=["mixed32", "mixed_tc", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
+    ap.add_argument("--order", type=int, default=None, help="profiling runs: polynomial order N (default 3)")
+    ap.add_argument("--volume", default=None, help="profiling runs: volume form (default ec)")
     args = ap.parse_args()
-    global EX, EY, EZ, NODES
+    if (args.order is not None or args.volume is not None) and not args.only:
+        ap.error("--order and --volume select a profiling case: give --only too")
+    global EX, EY, EZ, NODES, N, VOLUME_FORM
     EX = EY = EZ = args.mesh
+    if args.order is not None:
+        N = args.order
+    if args.volume is not None:
+        VOLUME_FORM = args.volume
     NODES = EX * EY * EZ * (N + 1) ** 3
     return args
 
@@ -263,7 +272,7 @@ def run_hs3d(args, world, rank, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def cfg(prec):
-        return hs.solver_cfg("ns", "roe", "ec", prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+        return hs.solver_cfg("ns", "roe", VOLUME_FORM, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
 
     def fresh():
         u = mesh.init_state(mesh.empty_state(), "tgv", GAMMA, MA)
