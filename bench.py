@@ -429,6 +429,8 @@ def run_hs3d(args, world, rank, local):
     serving = None
     if args.serving > 0:
         serving = run_serving(args.serving, max(4, args.serving // 16))
+        # below saturation: a quarter of the requests at a twentieth of the rate
+        serving["below_saturation"] = run_serving(max(4, args.serving // 4), 0, rate_scale=20.0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -587,13 +589,15 @@ def run_serving(count, seq_count, rate_scale=1.0):
     while srv.poll(t)[0] == hs.PENDING:
         time.sleep(0.001)
     tickets = []
+    # the final states of the requests also solved sequentially in FP64 below
+    finals = [np.empty(r["E"] ** 3 * 5 * (r["N"] + 1) ** 3) for r in reqs[:seq_count]]
     t0 = time.perf_counter()
-    for r in reqs:
+    for k, r in enumerate(reqs):
         target = r["arrival"] * rate_scale
         while time.perf_counter() - t0 < target:
             time.sleep(0.0002)
         m, c, i = descs(r, "mixed32")
-        tickets.append(srv.submit(m, c, i, t_final=1.0))
+        tickets.append(srv.submit(m, c, i, t_final=1.0, result=finals[k] if k < seq_count else None))
     done = {}
     while len(done) < len(tickets):
         for tk in tickets:
@@ -613,7 +617,8 @@ def run_serving(count, seq_count, rate_scale=1.0):
     srv.close()
     # sequential FP64 per-solve through the single-mesh API
     seq_t = 0.0
-    for r in reqs[:seq_count]:
+    l2 = []
+    for k, r in enumerate(reqs[:seq_count]):
         mesh = hs.Mesh(r["E"], r["E"], r["E"], r["N"], lo=(0, 0, 0), hi=(10, 10, 10))
         u = mesh.init_state(mesh.empty_state(), "vortex", GAMMA, r["Ma"], r["beta"], r["xc"], r["yc"])
         g = torch.zeros_like(u)
@@ -629,15 +634,20 @@ def run_serving(count, seq_count, rate_scale=1.0):
             tsim += dt
         torch.cuda.synchronize()
         seq_t += time.perf_counter() - a
+        ref = u.cpu().numpy().ravel()
+        l2.append(float(np.linalg.norm(finals[k] - ref) / np.linalg.norm(ref)))
         del mesh
-    return {"requests": count, "completed": len(ok), "failed": failed, "solves_per_s": round(len(ok) / span, 2),
-            "dof_stage_per_s": round(dof_stage / span, 1),
-            "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
-            "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
-            "arrivals": f"Poisson 200 req/s x {1 / rate_scale:g}",
-            "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5",
-            "sequential_fp64_solves_per_s": round(seq_count / seq_t, 2),
-            "sequential_sample": f"first {seq_count} requests, one at a time, FP64, hs3d_rk3_step + host dt read"}
+    out = {"requests": count, "completed": len(ok), "failed": failed, "solves_per_s": round(len(ok) / span, 2),
+           "dof_stage_per_s": round(dof_stage / span, 1),
+           "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
+           "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
+           "arrivals": f"Poisson {200 / rate_scale:g} req/s",
+           "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5"}
+    if seq_count:
+        out.update({"sequential_fp64_solves_per_s": round(seq_count / seq_t, 2),
+                    "sequential_sample": f"first {seq_count} requests, one at a time, FP64, hs3d_rk3_step + host dt read",
+                    "l2_rel_server_mixed_vs_sequential_fp64_max": max(l2)})
+    return out
 
 
 def stress_requests(count, seed=1, emax=64):
