@@ -326,7 +326,16 @@ template <typename R>
 __device__ __forceinline__ void flux_ec(const ECNode<R> &L, const ECNode<R> &Rr, R hg, R a1, R a2, R a3, R f[5])
 {
     const R srho = L.rho + Rr.rho, sbeta = L.beta + Rr.beta;
-    const R irho = rcp_(srho), ibeta = rcp_(sbeta);
+    R irho, ibeta;
+    if constexpr (sizeof(R) == 8) {
+        // FP64: one division for both reciprocals (the FP64 pipe bounds this path)
+        const R inv = (R)1 / (srho * sbeta);
+        irho = sbeta * inv;
+        ibeta = srho * inv;
+    } else {
+        irho = rcp_(srho);
+        ibeta = rcp_(sbeta);
+    }
     const R dr = L.rho - Rr.rho;
     const R fr = dr * irho, ur = fr * fr;
     R rho_ln;
