@@ -403,6 +403,12 @@ def run_hs3d(args, world, rank, local):
             "kernel": "k_volume<3,float,NS,EC>" if dom == "volume" else dom, "peak_source": hbm_peak[1]}
     p64 = prof["fp64"]
     fp64_ach = volume_flops() / (p64["volume"] / 3.0 * 1e-3) / 1e12
+    # the same element kernel of the mixed path against the FP32 pipe (algorithmic flops)
+    fp32_ach = volume_flops() / (per_launch_ms * 1e-3) / 1e12 if dom == "volume" else None
+    if fp32_ach is not None:
+        roof["fp32_alu"] = {"achieved": round(fp32_ach, 3), "peak": round(peaks["fp32_tflops"], 3), "unit": "TFLOP/s",
+                            "frac": round(fp32_ach / peaks["fp32_tflops"], 4),
+                            "peak_source": "measured FP32 FMA-chain kernel (hs3d_alu_peaks)"}
     fp64_roof = {"bound": "alu", "kernel": "k_volume<3,double,NS,EC>", "achieved": round(fp64_ach, 3),
                  "peak": round(peaks["fp64_tflops"], 3), "unit": "TFLOP/s",
                  "frac": round(fp64_ach / peaks["fp64_tflops"], 4),
