@@ -119,6 +119,32 @@ def test_mixed_schemes_share_the_server_and_match_the_oracle():
     srv.close()
 
 
+def test_mixed_and_tensor_core_requests_equal_single_solves():
+    """Mixed-precision requests (CUDA-core and tensor-core contraction) in one
+    server give bitwise the states of the same solves stepped alone through
+    hs3d_rk3_run (the server's captured step graph replayed across steps)."""
+    specs = [(4, 3, "mixed_tc", "standard"), (3, 4, "mixed_tc", "standard"), (4, 3, "mixed32", "ec"),
+             (5, 2, "mixed32", "standard")]
+    n_steps = 5
+    srv = hs.Server()
+    tickets, outs = [], []
+    for E, N, prec, volume in specs:
+        mesh, cfg, ic = vortex_request(E, N, 4.0, 6.0, 2.0, 0.4, precision=prec, volume=volume)
+        out = np.zeros((E * E, 5, N + 1, N + 1, N + 1))
+        tickets.append(srv.submit(mesh, cfg, ic, n_steps=n_steps, result=out))
+        outs.append(out)
+    res = wait_all(srv, tickets)
+    srv.close()
+    for (E, N, prec, volume), t, a in zip(specs, tickets, outs):
+        assert res[t][0] == hs.OK and res[t][1].steps == n_steps
+        gm = hs.Mesh(E, E, 1, N, lo=(0, 0, 0), hi=(10, 10, 10.0 / E))
+        u = gm.init_state(gm.empty_state(), "vortex", G, 0.4, 2.0, 4.0, 6.0)
+        g = torch.zeros_like(u)
+        gm.rk3_run(hs.solver_cfg("euler", "lf", volume, prec, cfl=0.5), u, g, n_steps)
+        torch.cuda.synchronize()
+        assert np.array_equal(a, u.cpu().numpy()), (E, N, prec, volume)
+
+
 def test_t_final_is_hit_exactly():
     srv = hs.Server()
     mesh, cfg, ic = vortex_request(4, 3, 5.0, 5.0, 2.0, 0.4)
