@@ -240,6 +240,16 @@ __device__ __forceinline__ void mma_tf32_m16n8k8(float acc[4], const unsigned a[
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Ask L2 to fetch the cache lines of [p, p + bytes) ahead of their use; each
+// of `nthreads` threads (index tid) prefetches every nthreads-th line.
+__device__ __forceinline__ void prefetch_l2_block(const void *p, size_t bytes, int tid, int nthreads)
+{
+    const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)127, a1 = ((uintptr_t)p + bytes - 1) & ~(uintptr_t)127;
+    const int lines = (int)((a1 - a0) >> 7) + 1;
+    for (int t = tid; t < lines; t += nthreads)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"((const void *)(a0 + ((uintptr_t)t << 7))));
+}
+
 // Bulk asynchronous copies on the TMA engine (cp.async.bulk, sm_90+): one
 // thread moves a whole contiguous block (16-byte aligned addresses, size a
 // multiple of 16 bytes); completion is counted in bytes on an mbarrier in

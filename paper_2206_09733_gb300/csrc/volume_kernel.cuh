@@ -294,6 +294,14 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
             }
         }
+        if constexpr (STAGE_RK && !(STAGE_U && STAGE_G)) {
+            // the RK operands read where they are used: their lines are
+            // requested into L2 now, so the late loads do not wait on DRAM
+            if (stage >= 0) {
+                if (!STAGE_U) prefetch_l2_block(it.u + (size_t)e * 5 * n3, sizeof(double) * 5 * n3, p, n3);
+                if (!STAGE_G && stage > 0) prefetch_l2_block(it.g + (size_t)e * 5 * n3, sizeof(double) * 5 * n3, p, n3);
+            }
+        }
         if constexpr (STAGE_RK && !BULK) {
             if (stage >= 0) {
                 double *mine = sRK + (size_t)le * RKW * n3;
