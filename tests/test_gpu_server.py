@@ -123,8 +123,9 @@ def test_mixed_and_tensor_core_requests_equal_single_solves():
     """Mixed-precision requests (CUDA-core and tensor-core contraction) in one
     server give bitwise the states of the same solves stepped alone through
     hs3d_rk3_run (the server's captured step graph replayed across steps)."""
-    specs = [(4, 3, "mixed_tc", "standard"), (3, 4, "mixed_tc", "standard"), (4, 3, "mixed32", "ec"),
-             (5, 2, "mixed32", "standard")]
+    # pairs of requests with the same order and scheme share their launches (item tables)
+    specs = [(4, 3, "mixed_tc", "standard"), (3, 3, "mixed_tc", "standard"), (3, 4, "mixed_tc", "standard"),
+             (4, 3, "mixed32", "ec"), (5, 3, "mixed32", "ec"), (5, 2, "mixed32", "standard")]
     n_steps = 5
     srv = hs.Server()
     tickets, outs = [], []
