@@ -730,9 +730,24 @@ def cpu_baseline(u64_final_check=None, budget_s=15.0):
         if el > budget_s or steps >= 200:
             break
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(NODES * 3 * steps / el, 1), "unit": "DOF-stage-updates/s", "cores": cores,
-            "kind": "oracle", "sample": f"{steps} RK3 steps of the full 16^3 N=3 workload from t=0 "
-                                        f"({el:.1f} s, OpenMP over elements)"}
+    out = {"value": round(NODES * 3 * steps / el, 1), "unit": "DOF-stage-updates/s", "cores": cores,
+           "kind": "oracle", "sample": f"{steps} RK3 steps of the full 16^3 N=3 workload from t=0 "
+                                       f"({el:.1f} s, OpenMP over elements)"}
+    # the same oracle on one thread (a fresh process, so that OpenMP starts with one thread)
+    code = ("import os, sys, time, numpy as np; sys.path.insert(0, %r); import oracle as O; "
+            "om = O.Mesh(%d, %d, %d, %d, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=%r); "
+            "oc = O.Cfg('ns', 'roe', 'ec', gamma=%r, Re=%r, Pr=%r, cfl=%r); u = om.ic_tgv(%r, %r); g = np.zeros_like(u); "
+            "t0 = time.perf_counter(); om.rk3_step(oc, u, g); om.rk3_step(oc, u, g); "
+            "print(time.perf_counter() - t0)" % (ROOT, EX, EY, EZ, N, AMP, GAMMA, RE, PR, CFL, GAMMA, MA))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                           env=dict(os.environ, OMP_NUM_THREADS="1"))
+        el1 = float(r.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": round(NODES * 3 * 2 / el1, 1), "cores": 1,
+                                "sample": f"2 RK3 steps of the same workload ({el1:.1f} s)"}
+    except (subprocess.SubprocessError, ValueError, IndexError) as exc:
+        out["single_thread"] = {"unavailable": str(exc)[:200]}
+    return out
 
 
 def run_reference(args, world, rank):
