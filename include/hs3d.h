@@ -209,7 +209,16 @@ hs3d_status hs3d_rk3_step(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, dou
  * the first call for this (mesh, cfg, u, g, dt).  The mesh keeps the graphs of
  * the two most recently used (cfg, u, g, dt), so a caller alternating between
  * two state buffers replays without re-capture; a third combination replaces
- * the least recently used graph.  Stream-ordered. */
+ * the least recently used graph.  dt > 0: fixed; dt == 0: from the rule above,
+ * with one pass over u before the first step for its dt maxima; dt < 0:
+ * continue — when the previous hs3d_rk3_step / hs3d_rk3_run on this mesh
+ * advanced this same u with the same cfg and nothing rewrote u, the mesh's
+ * dt maxima or its FP32 shadow since (hs3d_init_state of u, hs3d_residual or
+ * hs3d_dt of another state, hs3d_clock with reset, hs3d_autotune), the
+ * maxima the last step left are used and that pass is skipped (the steps are
+ * then exactly the steps of one longer run); otherwise as dt == 0.  The
+ * library cannot see writes to u by the caller: a caller that changes u
+ * between calls passes dt = 0.  Stream-ordered. */
 hs3d_status hs3d_rk3_run(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
                          int nsteps, void *stream);
 

@@ -299,6 +299,31 @@ cudaError_t prime_lambda(int N, const hs3d_solver_cfg *c, const Batch &b, Clock 
     return e;
 }
 
+bool same_cfg(const hs3d_solver_cfg &k, const hs3d_solver_cfg &c)
+{
+    // field-wise: the struct has padding
+    return k.physics == c.physics && k.surface_flux == c.surface_flux && k.volume_form == c.volume_form &&
+           k.precision == c.precision && k.gamma == c.gamma && k.Re == c.Re && k.Pr == c.Pr && k.Ma == c.Ma &&
+           k.cfl == c.cfl && k.time_scheme == c.time_scheme;
+}
+
+void cont_set(const hs3d_mesh *mc, const double *u, const hs3d_solver_cfg *c)
+{
+    hs3d_mesh *m = const_cast<hs3d_mesh *>(mc);
+    std::lock_guard<std::mutex> lock(m->mu);
+    m->cont_u = u;
+    m->cont_cfg = *c;
+}
+
+// A call rewrote the FP32 shadow or the clock for state u_written: the
+// continuation record survives only if it is the same state.
+void cont_forget(const hs3d_mesh *mc, const double *u_written)
+{
+    hs3d_mesh *m = const_cast<hs3d_mesh *>(mc);
+    std::lock_guard<std::mutex> lock(m->mu);
+    if (!u_written || u_written != m->cont_u) m->cont_u = nullptr;
+}
+
 hs3d_status check_ptr(const void *p, const char *name)
 {
     if (!p) return fail(HS3D_ERR_INVALID, "%s is NULL", name);
@@ -354,6 +379,11 @@ hs3d_status hs3d_init_state(const hs3d_mesh *m, const hs3d_ic *ic, double *u, vo
     if (ic->kind != HS3D_IC_VORTEX && ic->kind != HS3D_IC_TGV) return fail(HS3D_ERR_INVALID, "bad ic kind");
     if (!(ic->gamma > 1.0)) return fail(HS3D_ERR_INVALID, "ic gamma must be > 1");
     if (ic->kind == HS3D_IC_TGV && !(ic->Ma > 0.0)) return fail(HS3D_ERR_INVALID, "TGV needs Ma > 0");
+    {   // the state itself is rewritten
+        hs3d_mesh *mm = const_cast<hs3d_mesh *>(m);
+        std::lock_guard<std::mutex> lock(mm->mu);
+        if (mm->cont_u == u) mm->cont_u = nullptr;
+    }
     cudaError_t e = launch_init_state(m->N, m->E, m->X, *ic, m->lo, m->hi, u, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "init_state");
 }
@@ -370,7 +400,10 @@ hs3d_status hs3d_residual(const hs3d_mesh *m, const hs3d_solver_cfg *c, const do
     Item it = make_item(m, c, u, nullptr, dudt);
     it.clk = nullptr;
     cudaError_t e = cudaSuccess;
-    if (c->precision != HS3D_FP64) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
+    if (c->precision != HS3D_FP64) {
+        cont_forget(m, u);
+        e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
+    }
     if (e == cudaSuccess) e = enqueue_stage(m->N, c, single_batch(it), -1, -1, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
 }
@@ -385,8 +418,13 @@ hs3d_status hs3d_rk3_step(const hs3d_mesh *m, const hs3d_solver_cfg *c, double *
     if (st != HS3D_OK) return st;
     if (u == g) return fail(HS3D_ERR_INVALID, "u and g must differ");
     Item it = make_item(m, c, u, g, nullptr);
-    cudaError_t e = enqueue_rk3_step(m->N, c, single_batch(it), dt, 1, (cudaStream_t)stream);
-    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "rk3 step launch");
+    cudaError_t e = enqueue_rk3_step(m->N, c, single_batch(it), dt > 0.0 ? dt : 0.0, 1, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cont_forget(m, nullptr);
+        return cuda_fail(e, "rk3 step launch");
+    }
+    cont_set(m, u, c);
+    return HS3D_OK;
 }
 
 hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *u, double *g, double dt, int nsteps,
@@ -403,16 +441,14 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
     if (nsteps < 0) return fail(HS3D_ERR_INVALID, "nsteps < 0");
     if (nsteps == 0) return HS3D_OK;
     std::lock_guard<std::mutex> lock(m->mu);
-    // a cached graph for exactly these arguments (cfg compared field-wise: the struct has padding)
+    // dt < 0: continue from the previous step on this mesh when it advanced this
+    // same state and configuration (the graph is the one of dt = 0)
+    const bool cont = dt < 0.0 && m->cont_u == u && same_cfg(m->cont_cfg, *c);
+    if (dt < 0.0) dt = 0.0;
+    // a cached graph for exactly these arguments
     hs3d_mesh::GraphSlot *slot = nullptr;
-    for (auto &gs : m->gslot) {
-        const hs3d_solver_cfg &k = gs.cfg;
-        if (gs.exec && gs.u == u && gs.g == g && gs.dt == dt && k.physics == c->physics &&
-            k.surface_flux == c->surface_flux && k.volume_form == c->volume_form && k.precision == c->precision &&
-            k.gamma == c->gamma && k.Re == c->Re && k.Pr == c->Pr && k.Ma == c->Ma && k.cfl == c->cfl &&
-            k.time_scheme == c->time_scheme)
-            slot = &gs;
-    }
+    for (auto &gs : m->gslot)
+        if (gs.exec && gs.u == u && gs.g == g && gs.dt == dt && same_cfg(gs.cfg, *c)) slot = &gs;
     cudaError_t e = cudaSuccess;
     if (!slot) {
         // capture into the empty or least recently used slot
@@ -444,13 +480,19 @@ hs3d_status hs3d_rk3_run(const hs3d_mesh *mc, const hs3d_solver_cfg *c, double *
         slot->cfg = *c;
     }
     slot->used = ++m->gtick;
-    {
+    if (!cont) {
         Item it = make_item(m, c, u, g, nullptr);
         if (!(dt > 0.0)) e = prime_lambda(m->N, c, single_batch(it), m->clk, (cudaStream_t)stream);
         else if (c->precision != HS3D_FP64) e = launch_shadow(m->N, single_batch(it), (cudaStream_t)stream);
     }
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(slot->exec, (cudaStream_t)stream);
-    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");
+    if (e != cudaSuccess) {
+        m->cont_u = nullptr;
+        return cuda_fail(e, "graph launch");
+    }
+    m->cont_u = u;
+    m->cont_cfg = *c;
+    return HS3D_OK;
 }
 
 hs3d_status hs3d_dt(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, double *dt_out, void *stream)
@@ -463,6 +505,7 @@ hs3d_status hs3d_dt(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *
     if (st != HS3D_OK) return st;
     Item it = make_item(m, c, u, nullptr, dt_out);
     Batch b = single_batch(it);
+    cont_forget(m, u);   // (the pass rewrites the FP32 shadow for u)
     cudaError_t e = launch_lambda(m->N, c->precision, c->physics, b, 0, (cudaStream_t)stream);
     if (e == cudaSuccess) e = launch_dt_finalize(m->N, b, 2, 0, (cudaStream_t)stream);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "dt launch");
@@ -476,6 +519,7 @@ hs3d_status hs3d_clock(const hs3d_mesh *m, double *t, int64_t *steps, int reset,
     cudaError_t e = cudaMemcpyAsync(&h, m->clk, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && reset) {
+        cont_forget(m, nullptr);
         e = cudaMemsetAsync(m->clk, 0, sizeof(Clock), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }

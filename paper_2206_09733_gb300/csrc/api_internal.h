@@ -35,9 +35,19 @@ struct hs3d_mesh {
     std::mutex mu;
     GraphSlot gslot[2];
     unsigned long long gtick = 0;
+    // continuation record (under mu): the state and configuration the last
+    // hs3d_rk3_step / hs3d_rk3_run advanced; clock slot 1 then holds that
+    // state's dt maxima and uf its FP32 shadow, so hs3d_rk3_run with dt < 0
+    // may skip the priming pass.  Cleared by anything that rewrites either.
+    const double *cont_u = nullptr;
+    hs3d_solver_cfg cont_cfg{};
 };
 
 namespace hs3d {
+
+bool same_cfg(const hs3d_solver_cfg &a, const hs3d_solver_cfg &b);
+void cont_set(const hs3d_mesh *m, const double *u, const hs3d_solver_cfg *c);
+void cont_forget(const hs3d_mesh *m, const double *u_written);   // nullptr: forget unconditionally
 
 hs3d_status fail(hs3d_status st, const char *fmt, ...);
 hs3d_status cuda_fail(cudaError_t e, const char *what);

@@ -151,7 +151,12 @@ hs3d_status hs3d_rk3_step_profiled(const hs3d_mesh *m, const hs3d_solver_cfg *c,
         ms_out[4] = t;
     }
     for (int j = 0; j < NEV; ++j) cudaEventDestroy(ev[j]);
-    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "profiled step");
+    if (e != cudaSuccess) {
+        cont_forget(m, nullptr);
+        return cuda_fail(e, "profiled step");
+    }
+    cont_set(m, u, c);
+    return HS3D_OK;
 }
 
 }  // extern "C"

@@ -145,6 +145,7 @@ extern "C" hs3d_status hs3d_autotune(const hs3d_mesh *mc, const hs3d_solver_cfg 
     it.clk = clk;
     Batch b = single_batch(it);
     // the face fluxes the volume kernel reads: one face pass
+    cont_forget(m, nullptr);   // the trial launches rewrite the mesh's FP32 shadow
     if (e == cudaSuccess && c->precision != HS3D_FP64) e = launch_shadow(m->N, b, s);
     if (e == cudaSuccess && c->physics == HS3D_NS) e = launch_grad(m->N, c->precision, b, s);
     if (e == cudaSuccess) e = launch_face(m->N, c->precision, c->physics, c->surface_flux, b, s);

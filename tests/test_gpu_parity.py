@@ -303,6 +303,37 @@ def test_rk3_run_graph_equals_stepwise():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed32"])
+def test_rk3_run_continuation(prec):
+    """dt < 0 continues a run: one call of 5 steps equals a first call and four
+    continuing calls of one step (bitwise); after the state is rewritten
+    (init_state) or the mesh's shadow is rewritten for another state
+    (residual), a continuing call falls back to the full dt pass."""
+    _, gm = pair(4, 4, 4, 3, amp=0.05)
+    gc = hs.solver_cfg("ns", "roe", "ec", prec, gamma=G, Re=400.0)
+    u0 = gm.init_state(gm.empty_state(), "tgv", G, 0.1)
+    a, ga = u0.clone(), torch.zeros_like(u0)
+    gm.rk3_run(gc, a, ga, 5)
+    b, gb = u0.clone(), torch.zeros_like(u0)
+    gm.rk3_run(gc, b, gb, 1)
+    for _ in range(4):
+        gm.rk3_run(gc, b, gb, 1, dt=-1.0)
+    assert torch.equal(a, b)
+    # rewritten state: continuing equals a fresh run from the new state
+    gm.init_state(b, "tgv", G, 0.1)
+    gm.rk3_run(gc, b, gb, 2, dt=-1.0)
+    c, gcc = u0.clone(), torch.zeros_like(u0)
+    gm.rk3_run(gc, c, gcc, 2)
+    assert torch.equal(b, c)
+    # the shadow rewritten for another state in between
+    other = torch.from_numpy(random_state(gm.shape, seed=11, smooth=True)).cuda()
+    gm.residual(gc, other, torch.empty_like(other))
+    gm.rk3_run(gc, c, gcc, 1, dt=-1.0)
+    d, gd = u0.clone(), torch.zeros_like(u0)
+    gm.rk3_run(gc, d, gd, 3)
+    assert torch.equal(c, d)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed32"])
 def test_rk3_run_alternating_buffers_equals_stepwise(prec):
     """Three state buffers stepped in turn through hs3d_rk3_run (two cached
     graphs, the third buffer evicting the least recently used one) give
