@@ -45,6 +45,8 @@ AMP = 0.05
 MA, RE, PR, GAMMA, CFL = 0.1, 1600.0, 0.72, 1.4, 0.5
 NODES = EX * EY * EZ * (N + 1) ** 3
 VOLUME_FORM = "ec"
+PHYSICS = "ns"
+SURFACE_FLUX = "roe"
 METRIC = "DOF-stage-updates/s"
 WORKLOAD = ("NS Taylor-Green vortex Ma 0.1 Re 1600, [-pi,pi]^3, 16^3 curved hex (amp 0.05), N=3 (64^3 DOF), "
             "EC split form + Roe + BR1, Williamson RK3 CFL 0.5")
@@ -69,15 +71,21 @@ def parse():
                     help="time one precision only (profiling runs)")
     ap.add_argument("--order", type=int, default=None, help="profiling runs: polynomial order N (default 3)")
     ap.add_argument("--volume", default=None, help="profiling runs: volume form (default ec)")
+    ap.add_argument("--physics", default=None, choices=["euler", "ns"], help="profiling runs: equations (default ns)")
+    ap.add_argument("--surface", default=None, help="profiling runs: surface flux (default roe)")
     args = ap.parse_args()
-    if (args.order is not None or args.volume is not None) and not args.only:
-        ap.error("--order and --volume select a profiling case: give --only too")
-    global EX, EY, EZ, NODES, N, VOLUME_FORM
+    if any(x is not None for x in (args.order, args.volume, args.physics, args.surface)) and not args.only:
+        ap.error("--order, --volume, --physics and --surface select a profiling case: give --only too")
+    global EX, EY, EZ, NODES, N, VOLUME_FORM, PHYSICS, SURFACE_FLUX
     EX = EY = EZ = args.mesh
     if args.order is not None:
         N = args.order
     if args.volume is not None:
         VOLUME_FORM = args.volume
+    if args.physics is not None:
+        PHYSICS = args.physics
+    if args.surface is not None:
+        SURFACE_FLUX = args.surface
     NODES = EX * EY * EZ * (N + 1) ** 3
     return args
 
@@ -272,7 +280,7 @@ def run_hs3d(args, world, rank, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def cfg(prec):
-        return hs.solver_cfg("ns", "roe", VOLUME_FORM, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+        return hs.solver_cfg(PHYSICS, SURFACE_FLUX, VOLUME_FORM, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
 
     def fresh():
         u = mesh.init_state(mesh.empty_state(), "tgv", GAMMA, MA)
