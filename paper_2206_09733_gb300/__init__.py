@@ -235,6 +235,8 @@ class Mesh:
         check(lib().hs3d_rk3_step(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), _stream(stream)))
 
     def rk3_run(self, cfg: SolverCfg, u, g, nsteps, dt=0.0, stream=None):
+        """nsteps RK steps (hs3d_rk3_run): dt > 0 fixed, dt == 0 from the
+        CFL rule, dt < 0 continue the previous run of this same state."""
         check(lib().hs3d_rk3_run(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), int(nsteps),
                                  _stream(stream)))
 
