@@ -150,6 +150,23 @@ def test_gauss_free_stream_and_mixed_precision():
         assert rel(host(r), ref) < 2e-5, surface
 
 
+def test_gauss_tensor_core_precision_computes_as_mixed32():
+    """On Gauss-Legendre meshes the tensor-core precision selects the same
+    kernels as MIXED32 (its contraction exists for Gauss-Lobatto nodes only):
+    bitwise equal residuals and steps."""
+    _, gm = pair(3, 3, 2, 3, amp=0.05)
+    u0 = gm.init_state(gm.empty_state(), "tgv", G, 0.3)
+    out = []
+    for prec in ("mixed_tc", "mixed32"):
+        gc = hs.solver_cfg("ns", "roe", "standard", prec, gamma=G, Re=200.0)
+        r = torch.empty_like(u0)
+        gm.residual(gc, u0, r)
+        u, g = u0.clone(), torch.zeros_like(u0)
+        gm.rk3_run(gc, u, g, 2)
+        out.append((r, u))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
 def test_gauss_rejects_split_forms():
     _, gm = pair(2, 2, 2, 2)
     u = gm.init_state(gm.empty_state(), "tgv", G, 0.1)
