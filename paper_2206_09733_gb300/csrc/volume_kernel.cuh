@@ -16,12 +16,16 @@
 // step rule's input for the next step) so that no separate pass over the
 // state is needed between steps.
 //
-// One thread per node, `epb` elements per CTA.  The element's contravariant
-// fluxes (standard form) or its per-node two-point-flux inputs (split form)
-// are staged in shared memory; the six face-flux blocks of the element are
-// loaded into shared memory by all of its threads at the start (contiguous
-// 5n^2 chunks), so the surface term reads no global memory after the
-// contraction.
+// One thread per node, `epb` elements per CTA (a kernel argument; the
+// tensor-core variant pads the CTA to whole warps).  The element's
+// contravariant fluxes (standard form) or its per-node two-point-flux inputs
+// (split form) are staged in shared memory.  The six face-flux blocks of the
+// element (contiguous 5n^2 chunks) and, on the mixed path, its 1/J (standard
+// form also u and g) are copied into shared memory at the start — by
+// cp.async.bulk copies on the TMA engine counted on a per-element mbarrier
+// when every block is a multiple of 16 bytes (an even number of nodes per
+// direction), else by per-thread cp.async — so the surface term and the RK
+// update read no global memory they could have waited for.
 #pragma once
 
 #include "internal.cuh"
