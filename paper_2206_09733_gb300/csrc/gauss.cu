@@ -231,11 +231,12 @@ k_grad_gauss(const __grid_constant__ Batch b, const Ops *__restrict__ ops)
         // interpolated products Ja^d_c q, times the face metric
         const Item &it = *itp;
         const R gm1 = phys_of<R>(it).gm1;
+        const Nbrs nbs = elem_nbrs(e, it.ex, it.ey, it.ez);
         for (int t = p; t < 6 * n2; t += n3) {
             const int slot = t / n2, ab = t - slot * n2;
             const int d = slot >> 1, plus = slot & 1;
             const int ta = ab % n, tb = ab / n;
-            const int nb = plus ? nbr_plus(e, d, it.ex, it.ey, it.ez) : nbr_minus(e, d, it.ex, it.ey, it.ez);
+            const int nb = nbr_of_slot(nbs, slot);
             R uo[5], un[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) uo[v] = (R)0;
@@ -255,19 +256,30 @@ k_grad_gauss(const __grid_constant__ Batch b, const Ops *__restrict__ ops)
             const R *Sf = gnormal<R>(it) + ((size_t)d * it.E + owner) * 3 * n2 + ab;
             const R sf[3] = {Sf[0], Sf[n2], Sf[2 * n2]};
             const R sg = plus ? (R)1 : (R)-1;
+            // interpolated products (Ja^d_c q_v)(+-1): line node by line node,
+            // each node's 3 metric terms and 4 variables read once
+            R jq[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) jq[k] = (R)0;
+#pragma unroll
+            for (int j = 0; j < n; ++j) {
+                const R l = plus ? ops_rb<R>(ops, j) : ops_lb<R>(ops, j);
+                const int pj = gline<n>(d, j, ta, tb);
+                R jac[3], qv[4];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) jac[c] = sja[(d * 3 + c) * n3 + pj];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) qv[v] = sq[v * n3 + pj];
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) jq[v * 3 + c] += l * (jac[c] * qv[v]);
+            }
 #pragma unroll
             for (int v = 0; v < 4; ++v)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    R jq = (R)0;
-#pragma unroll
-                    for (int j = 0; j < n; ++j) {
-                        const R l = plus ? ops_rb<R>(ops, j) : ops_lb<R>(ops, j);
-                        const int pj = gline<n>(d, j, ta, tb);
-                        jq += l * (sja[(d * 3 + c) * n3 + pj] * sq[v * n3 + pj]);
-                    }
-                    slift[(slot * 12 + v * 3 + c) * n2 + ab] = sg * (qs[v] * sf[c] - jq);
-                }
+                for (int c = 0; c < 3; ++c)
+                    slift[(slot * 12 + v * 3 + c) * n2 + ab] = sg * (qs[v] * sf[c] - jq[v * 3 + c]);
         }
     }
     __syncthreads();
@@ -350,10 +362,11 @@ k_volume_gauss(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int
     if (valid) {
         const Item &it = *itp;
         const R *FS = (const R *)it.fstar;
+        const Nbrs nb = elem_nbrs(e, it.ex, it.ey, it.ez);
 #pragma unroll
         for (int slot = 0; slot < 6; ++slot) {
             const int d = slot >> 1;
-            const int owner = (slot & 1) ? e : nbr_minus(e, d, it.ex, it.ey, it.ez);
+            const int owner = (slot & 1) ? e : nb.m[d];
             cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
         }
         const size_t node = (size_t)e * 5 * n3 + p;
