@@ -101,6 +101,19 @@ def lib():
                                         C.c_double, C.c_double, _dp]
             L.orc_ic_tgv.argtypes = [C.c_void_p, C.c_double, C.c_double, _dp]
             L.orc_integrals.argtypes = [C.c_void_p, C.c_double, _dp, C.c_void_p, _dp]
+            L.orc_mortar_matrices.argtypes = [C.c_int, C.c_int, _dp, _dp]
+            L.orc_pmesh_create.argtypes = [C.POINTER(_Box), C.c_void_p]
+            L.orc_pmesh_create.restype = C.c_void_p
+            L.orc_pmesh_destroy.argtypes = [C.c_void_p]
+            L.orc_pmesh_Ngeo.argtypes = [C.c_void_p]
+            L.orc_pmesh_arrays.argtypes = [C.c_void_p] + [C.c_void_p] * 5
+            L.orc_presidual.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
+            L.orc_pgradients.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp]
+            L.orc_pdt.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp]
+            L.orc_pdt.restype = C.c_double
+            L.orc_prk_step.argtypes = [C.c_void_p, C.POINTER(_Cfg), _dp, _dp, C.c_double, C.POINTER(C.c_double)]
+            L.orc_pic.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+            L.orc_pintegrals.argtypes = [C.c_void_p, C.c_double, _dp, C.c_void_p, _dp]
             _lib = L
     return _lib
 
@@ -354,3 +367,121 @@ def rk3_coefficients():
 def lsrk3_stage(k, dt, u, g, R):
     u = np.ascontiguousarray(u, dtype=np.float64)
     lib().orc_lsrk3_stage(u.size, k, dt, u, g, np.ascontiguousarray(R, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------- per-element degree (Sec. 3.6)
+
+def mortar_matrices(Ns: int, Nm: int):
+    """(Pi, P): interpolation from degree Ns to the mortar degree Nm >= Ns
+    ([Nm+1, Ns+1]) and the L2 projection back ([Ns+1, Nm+1])."""
+    Pi = np.zeros((Nm + 1, Ns + 1))
+    P = np.zeros((Ns + 1, Nm + 1))
+    if lib().orc_mortar_matrices(Ns, Nm, Pi, P) != 0:
+        raise ValueError("need 1 <= Ns <= Nm")
+    return Pi, P
+
+
+class PMesh:
+    """Oracle mesh of an ex*ey*ez periodic box whose elements carry their own
+    degree (Gauss-Lobatto nodes), coupled by mortars.
+
+    The state is one flat float64 vector of element blocks [5, n_e, n_e, n_e]
+    in element order; `block(u, e)` views element e's block."""
+
+    def __init__(self, ex, ey, ez, degrees, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0):
+        self.ex, self.ey, self.ez = ex, ey, ez
+        self.E = ex * ey * ez
+        deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32).reshape(-1))
+        assert deg.size == self.E
+        self.degrees = deg.copy()
+        self.lo, self.hi, self.amp = tuple(lo), tuple(hi), amp
+        box = _Box(ex, ey, ez, 0, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), amp, 0)
+        self._h = lib().orc_pmesh_create(C.byref(box), deg.ctypes.data)
+        if not self._h:
+            raise ValueError("bad p-mesh description")
+        self.Ngeo = lib().orc_pmesh_Ngeo(self._h)
+        self.off = np.zeros(self.E + 1, dtype=np.int64)
+        self.noff = np.zeros(self.E + 1, dtype=np.int64)
+        lib().orc_pmesh_arrays(self._h, self.off.ctypes.data, self.noff.ctypes.data, None, None, None)
+        nodes = int(self.noff[-1])
+        self._X = np.zeros(3 * nodes)
+        self._Ja = np.zeros(9 * nodes)
+        self._J = np.zeros(nodes)
+        lib().orc_pmesh_arrays(self._h, None, None, self._X.ctypes.data, self._Ja.ctypes.data, self._J.ctypes.data)
+        self.size = int(self.off[-1])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_pmesh_destroy(h)
+            self._h = None
+
+    def n(self, e):
+        return int(self.degrees[e]) + 1
+
+    def block(self, u, e):
+        n = self.n(e)
+        return u[self.off[e]:self.off[e + 1]].reshape(5, n, n, n)
+
+    def X(self, e):
+        n = self.n(e)
+        return self._X[3 * self.noff[e]:3 * self.noff[e + 1]].reshape(3, n, n, n)
+
+    def Ja(self, e):
+        n = self.n(e)
+        return self._Ja[9 * self.noff[e]:9 * self.noff[e + 1]].reshape(3, 3, n, n, n)
+
+    def J(self, e):
+        n = self.n(e)
+        return self._J[self.noff[e]:self.noff[e + 1]].reshape(n, n, n)
+
+    def neighbour(self, e, d, side):
+        ab = [e % self.ex, (e // self.ex) % self.ey, e // (self.ex * self.ey)]
+        ab[d] = (ab[d] + side) % (self.ex, self.ey, self.ez)[d]
+        return ab[0] + self.ex * (ab[1] + self.ey * ab[2])
+
+    def empty(self):
+        return np.zeros(self.size)
+
+    def ic_tgv(self, gamma=1.4, Ma=0.1):
+        u = self.empty()
+        lib().orc_pic(self._h, 0, np.array([gamma, Ma, 0.0, 0.0, 0.0]), u)
+        return u
+
+    def ic_vortex(self, gamma=1.4, Ma=0.5, beta=5.0, xc=None, yc=None):
+        xc = 0.5 * (self.lo[0] + self.hi[0]) if xc is None else xc
+        yc = 0.5 * (self.lo[1] + self.hi[1]) if yc is None else yc
+        u = self.empty()
+        lib().orc_pic(self._h, 1, np.array([gamma, Ma, beta, xc, yc]), u)
+        return u
+
+    def residual(self, cfg: Cfg, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = self.empty()
+        if lib().orc_presidual(self._h, C.byref(cfg.c()), u, out) != 0:
+            raise MemoryError("residual")
+        return out
+
+    def gradients(self, cfg: Cfg, u):
+        """BR1 gradients, flat: element e's [4, 3, n, n, n] block at 12 noff[e]."""
+        out = np.zeros(12 * int(self.noff[-1]))
+        lib().orc_pgradients(self._h, C.byref(cfg.c()), np.ascontiguousarray(u, dtype=np.float64), out)
+        return out
+
+    def dt(self, cfg: Cfg, u):
+        return lib().orc_pdt(self._h, C.byref(cfg.c()), np.ascontiguousarray(u, dtype=np.float64))
+
+    def rk_step(self, cfg: Cfg, u, g, dt=0.0):
+        """One low-storage RK step in place on u and g; returns the dt used."""
+        used = C.c_double(0.0)
+        lib().orc_prk_step(self._h, C.byref(cfg.c()), u, g, dt, C.byref(used))
+        return used.value
+
+    def integrals(self, gamma, u, dudt=None):
+        out = np.zeros(7)
+        dp = None
+        if dudt is not None:
+            dudt = np.ascontiguousarray(dudt, dtype=np.float64)
+            dp = dudt.ctypes.data
+        lib().orc_pintegrals(self._h, gamma, np.ascontiguousarray(u, dtype=np.float64), dp, out)
+        return out

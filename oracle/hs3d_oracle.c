@@ -1532,3 +1532,589 @@ void orc_integrals(const orc_mesh *m, double g, const double *u, const double *d
             }
         }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Per-element polynomial degree with mortar coupling (Sec. 3.6)             */
+/* ------------------------------------------------------------------------ */
+/*
+ * Element e of the ex*ey*ez periodic box carries its own degree N_e in 1..7
+ * (Gauss-Lobatto nodes, isotropic).  Sec. 3.6 names the two ingredients:
+ *
+ * Geometry (the rules of Kopriva et al. 2019 for p-non-conforming faces).
+ *   Every element's map is the polynomial of degree Ngeo = max(1, floor(Nmin/2))
+ *   (Nmin = smallest degree of the mesh) that interpolates the box map (with
+ *   its perturbation) at the element's Gauss-Lobatto points of degree Ngeo; X is
+ *   that polynomial at the element's own nodes and the metric terms are the
+ *   curl form at the element's own degree.  The products X_l dX_m of a
+ *   degree-Ngeo map have degree 2 Ngeo <= Nmin per direction, so every
+ *   element interpolates them exactly: the face metric terms are the same
+ *   polynomial seen from both sides of a face, whatever the two degrees.
+ *   With Nmin = 1 that holds only for an affine map, so amp must be 0.
+ *
+ * Coupling (the mortar method of Kopriva et al. 2002, which Sec. 3.6 notes
+ * does not keep entropy stability).  A face between degrees N_L and N_R
+ * carries a mortar of degree N_M = max(N_L, N_R) on its Gauss-Lobatto points:
+ *   - the conservative traces of both sides (and, for Navier-Stokes, their
+ *     gradients) are interpolated to the mortar points (tensor-product
+ *     Lagrange interpolation in the two face directions);
+ *   - the numerical flux s F*(u_L, u_R; n) - (F_v(L) + F_v(R)).Sn/2 is
+ *     evaluated at the mortar points, with Sn the face metric Ja^d of the
+ *     side of degree N_M (of the minus side L when the degrees agree);
+ *   - the BR1 interface value q* = (q(u_L) + q(u_R))/2 likewise;
+ *   - each side receives the L2 projection of the mortar function onto its
+ *     own degree, P = M_s^{-1} S with M_s[i][k] = int l_i l_k and
+ *     S[i][j] = int l_i^s l_j^M integrated exactly (Gauss quadrature with
+ *     N_M + 1 points), applied in both face directions; the side of degree
+ *     N_M receives the mortar values themselves.
+ * With equal degrees on every face this is the conforming method (the
+ * mortar is the face itself).
+ *
+ * State layout: element blocks [5][n_e^3] in element order, block e at
+ * off[e] doubles.
+ */
+#define PM_MAXN 7
+
+typedef struct {
+    orc_box box;       /* ex, ey, ez, lo, hi, amp (N and nodes unused) */
+    int E, Nmin, Nmax, Ngeo;
+    int *N;            /* [E] degree of each element */
+    long long *off;    /* [E+1] state offsets: element e at off[e], 5 n_e^3 values */
+    long long *noff;   /* [E+1] node offsets: element e's nodes at noff[e], n_e^3 of them */
+    double *X;         /* [3][n_e^3] per element at 3 noff[e] */
+    double *Ja;        /* [3 d][3 c][n_e^3] per element at 9 noff[e] */
+    double *J;         /* [n_e^3] per element at noff[e] */
+    double xi[PM_MAXN + 1][16], w[PM_MAXN + 1][16], D[PM_MAXN + 1][256];
+    double Pi[PM_MAXN + 1][PM_MAXN + 1][64];  /* Pi[s][m][a*ns + i] = l_i^{(s)}(xi_a^{(m)}), s <= m */
+    double Pr[PM_MAXN + 1][PM_MAXN + 1][64];  /* Pr[s][m][i*nm + j]: L2 projection, degree m -> s, s <= m */
+} orc_pmesh;
+
+/* Interpolation from degree Ns to degree Nm >= Ns (Gauss-Lobatto points) and
+ * the L2 projection back, as nm x ns and ns x nm row-major matrices.  Equal
+ * degrees give identities. */
+int orc_mortar_matrices(int Ns, int Nm, double *Pi, double *P)
+{
+    if (Ns < 1 || Nm < Ns || Nm > 15) return -1;
+    int ns = Ns + 1, nm = Nm + 1;
+    double xs[16], ws[16], xm[16], wm[16];
+    orc_lgl(Ns, xs, ws);
+    orc_lgl(Nm, xm, wm);
+    if (Ns == Nm) {
+        for (int a = 0; a < nm; ++a)
+            for (int i = 0; i < ns; ++i) Pi[a * ns + i] = P[a * ns + i] = (a == i) ? 1.0 : 0.0;
+        return 0;
+    }
+    for (int a = 0; a < nm; ++a) orc_lagrange_at(ns, xs, xm[a], Pi + a * ns);
+    /* exact integrals of products of degree <= 2 Nm with Nm + 1 Gauss points */
+    double xg[16], wg[16];
+    orc_gauss(Nm, xg, wg);
+    double M[16 * 16], S[16 * 16];
+    for (int i = 0; i < ns; ++i) {
+        for (int k = 0; k < ns; ++k) M[i * ns + k] = 0.0;
+        for (int j = 0; j < nm; ++j) S[i * nm + j] = 0.0;
+    }
+    for (int q = 0; q < Nm + 1; ++q) {
+        double ls[16], lm[16];
+        orc_lagrange_at(ns, xs, xg[q], ls);
+        orc_lagrange_at(nm, xm, xg[q], lm);
+        for (int i = 0; i < ns; ++i) {
+            for (int k = 0; k < ns; ++k) M[i * ns + k] += wg[q] * ls[i] * ls[k];
+            for (int j = 0; j < nm; ++j) S[i * nm + j] += wg[q] * ls[i] * lm[j];
+        }
+    }
+    /* solve M P = S by Gaussian elimination with partial pivoting */
+    for (int c = 0; c < ns; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < ns; ++r)
+            if (fabs(M[r * ns + c]) > fabs(M[piv * ns + c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < ns; ++k) { double t = M[c * ns + k]; M[c * ns + k] = M[piv * ns + k]; M[piv * ns + k] = t; }
+            for (int j = 0; j < nm; ++j) { double t = S[c * nm + j]; S[c * nm + j] = S[piv * nm + j]; S[piv * nm + j] = t; }
+        }
+        for (int r = c + 1; r < ns; ++r) {
+            double f = M[r * ns + c] / M[c * ns + c];
+            for (int k = c; k < ns; ++k) M[r * ns + k] -= f * M[c * ns + k];
+            for (int j = 0; j < nm; ++j) S[r * nm + j] -= f * S[c * nm + j];
+        }
+    }
+    for (int c = ns - 1; c >= 0; --c)
+        for (int j = 0; j < nm; ++j) {
+            double acc = S[c * nm + j];
+            for (int k = c + 1; k < ns; ++k) acc -= M[c * ns + k] * P[k * nm + j];
+            P[c * nm + j] = acc / M[c * ns + c];
+        }
+    return 0;
+}
+
+/* The box map at reference point r (in [-1,1]^3) of element e: the affine
+ * box position plus the perturbation amp (L_c/2pi) sin(t_x) sin(t_y) sin(t_z)
+ * of the unperturbed position, t the position mapped to [-pi, pi]. */
+static void box_map_point(const orc_box *b, int e, const double r[3], double X[3])
+{
+    int E3[3] = {b->ex, b->ey, b->ez};
+    int ab[3] = {e % b->ex, (e / b->ex) % b->ey, e / (b->ex * b->ey)};
+    double x0[3], th[3];
+    for (int c = 0; c < 3; ++c) {
+        double L = b->hi[c] - b->lo[c];
+        x0[c] = b->lo[c] + (L / E3[c]) * (ab[c] + 0.5 * (r[c] + 1.0));
+        th[c] = -M_PI + 2.0 * M_PI * (x0[c] - b->lo[c]) / L;
+    }
+    double s = sin(th[0]) * sin(th[1]) * sin(th[2]);
+    for (int c = 0; c < 3; ++c) X[c] = x0[c] + b->amp * ((b->hi[c] - b->lo[c]) / (2.0 * M_PI)) * s;
+}
+
+void orc_pmesh_destroy(orc_pmesh *m)
+{
+    if (!m) return;
+    free(m->N); free(m->off); free(m->noff); free(m->X); free(m->Ja); free(m->J); free(m);
+}
+
+orc_pmesh *orc_pmesh_create(const orc_box *b, const int *deg)
+{
+    if (b->ex < 1 || b->ey < 1 || b->ez < 1 || !deg) return NULL;
+    int E = b->ex * b->ey * b->ez;
+    int Nmin = 99, Nmax = 0;
+    for (int e = 0; e < E; ++e) {
+        if (deg[e] < 1 || deg[e] > PM_MAXN) return NULL;
+        if (deg[e] < Nmin) Nmin = deg[e];
+        if (deg[e] > Nmax) Nmax = deg[e];
+    }
+    if (Nmin == 1 && b->amp != 0.0) return NULL;
+    orc_pmesh *m = (orc_pmesh *)calloc(1, sizeof(orc_pmesh));
+    if (!m) return NULL;
+    m->box = *b;
+    m->E = E;
+    m->Nmin = Nmin;
+    m->Nmax = Nmax;
+    m->Ngeo = Nmin / 2 >= 1 ? Nmin / 2 : 1;
+    m->N = (int *)malloc(sizeof(int) * E);
+    m->off = (long long *)malloc(sizeof(long long) * (E + 1));
+    m->noff = (long long *)malloc(sizeof(long long) * (E + 1));
+    if (!m->N || !m->off || !m->noff) { orc_pmesh_destroy(m); return NULL; }
+    m->off[0] = m->noff[0] = 0;
+    for (int e = 0; e < E; ++e) {
+        int n = deg[e] + 1;
+        m->N[e] = deg[e];
+        m->noff[e + 1] = m->noff[e] + (long long)n * n * n;
+        m->off[e + 1] = m->off[e] + 5LL * n * n * n;
+    }
+    for (int N = 1; N <= PM_MAXN; ++N) {
+        orc_lgl(N, m->xi[N], m->w[N]);
+        orc_dmatrix(N, m->xi[N], m->D[N]);
+    }
+    for (int s = 1; s <= PM_MAXN; ++s)
+        for (int t = s; t <= PM_MAXN; ++t) orc_mortar_matrices(s, t, m->Pi[s][t], m->Pr[s][t]);
+    long long nodes = m->noff[E];
+    m->X = (double *)malloc(sizeof(double) * 3 * nodes);
+    m->Ja = (double *)malloc(sizeof(double) * 9 * nodes);
+    m->J = (double *)malloc(sizeof(double) * nodes);
+    if (!m->X || !m->Ja || !m->J) { orc_pmesh_destroy(m); return NULL; }
+    int G = m->Ngeo, ng = G + 1;
+    for (int e = 0; e < E; ++e) {
+        int N = m->N[e], n = N + 1, n3 = n * n * n;
+        /* the map at the degree-Ngeo points, then its interpolant at the own nodes */
+        double Xg[3][512];
+        for (int k = 0; k < ng; ++k) for (int j = 0; j < ng; ++j) for (int i = 0; i < ng; ++i) {
+            double r[3] = {m->xi[G][i], m->xi[G][j], m->xi[G][k]}, x[3];
+            box_map_point(b, e, r, x);
+            for (int c = 0; c < 3; ++c) Xg[c][node_index(ng, i, j, k)] = x[c];
+        }
+        double L[16][16];   /* L[t][s] = l_s^{(Ngeo)}(xi_t^{(N)}) */
+        for (int t = 0; t < n; ++t) orc_lagrange_at(ng, m->xi[G], m->xi[N][t], L[t]);
+        double *Xe = m->X + 3 * m->noff[e];
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int kk = 0; kk < ng; ++kk) for (int jj = 0; jj < ng; ++jj) for (int ii = 0; ii < ng; ++ii)
+                    acc += L[i][ii] * L[j][jj] * L[k][kk] * Xg[c][node_index(ng, ii, jj, kk)];
+                Xe[c * n3 + node_index(n, i, j, k)] = acc;
+            }
+        orc_metrics(1, N, m->D[N], Xe, m->Ja + 9 * m->noff[e], m->J + m->noff[e]);
+    }
+    return m;
+}
+
+int orc_pmesh_E(const orc_pmesh *m) { return m->E; }
+int orc_pmesh_Ngeo(const orc_pmesh *m) { return m->Ngeo; }
+
+/* Copies of the mesh arrays: off [E+1], noff [E+1], X [3 nodes], Ja [9 nodes], J [nodes]
+ * (each element's blocks at 3 noff[e], 9 noff[e], noff[e]). */
+void orc_pmesh_arrays(const orc_pmesh *m, long long *off, long long *noff, double *X, double *Ja, double *J)
+{
+    long long nodes = m->noff[m->E];
+    if (off) memcpy(off, m->off, sizeof(long long) * (m->E + 1));
+    if (noff) memcpy(noff, m->noff, sizeof(long long) * (m->E + 1));
+    if (X) memcpy(X, m->X, sizeof(double) * 3 * nodes);
+    if (Ja) memcpy(Ja, m->Ja, sizeof(double) * 9 * nodes);
+    if (J) memcpy(J, m->J, sizeof(double) * nodes);
+}
+
+/* nf fields of one element ([nf][n^3] from base) on its face xi_d = end:
+ * out[v][ta + n tb], (ta, tb) the face's tangential indices in increasing
+ * direction order. */
+static void pm_face_values(const double *base, int nf, int n, int d, int end, double *out)
+{
+    int n3 = n * n * n, d0, d1;
+    face_dirs(d, &d0, &d1);
+    for (int v = 0; v < nf; ++v)
+        for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+            int idx[3];
+            idx[d] = end;
+            idx[d0] = ta;
+            idx[d1] = tb;
+            out[v * n * n + ta + n * tb] = base[(size_t)v * n3 + node_index(n, idx[0], idx[1], idx[2])];
+        }
+}
+
+/* Face field of degree Ns -> mortar of degree Nm (tensor-product interpolation). */
+static void pm_to_mortar(const orc_pmesh *m, int Ns, int Nm, const double *fs, double *fm)
+{
+    int ns = Ns + 1, nm = Nm + 1;
+    const double *I = m->Pi[Ns][Nm];
+    for (int b = 0; b < nm; ++b) for (int a = 0; a < nm; ++a) {
+        double acc = 0.0;
+        for (int j = 0; j < ns; ++j)
+            for (int i = 0; i < ns; ++i) acc += I[a * ns + i] * I[b * ns + j] * fs[i + ns * j];
+        fm[a + nm * b] = acc;
+    }
+}
+
+/* Mortar field of degree Nm -> face of degree Ns (tensor-product L2 projection). */
+static void pm_from_mortar(const orc_pmesh *m, int Nm, int Ns, const double *fm, double *fs)
+{
+    int ns = Ns + 1, nm = Nm + 1;
+    const double *P = m->Pr[Ns][Nm];
+    for (int b = 0; b < ns; ++b) for (int a = 0; a < ns; ++a) {
+        double acc = 0.0;
+        for (int j = 0; j < nm; ++j)
+            for (int i = 0; i < nm; ++i) acc += P[a * nm + i] * P[b * nm + j] * fm[i + nm * j];
+        fs[a + ns * b] = acc;
+    }
+}
+
+/* The mortar computation for face (d, side) of element e, returned on e's own
+ * face nodes (out[v][ta + n_e tb]):
+ *   mode 0: the BR1 interface value q* (4 values);
+ *   mode 1: the face flux s F* - (F_v(L) + F_v(R)).Sn/2 oriented along +d (5 values).
+ * L is the element on the face's minus side, R on its plus side. */
+static void pm_mortar(const orc_pmesh *m, const orc_cfg *cfg, const double *u, const double *grad, int e, int d,
+                      int side, int mode, double *out)
+{
+    int nb = neighbour(&m->box, e, d, side);
+    int eL = side > 0 ? e : nb, eR = side > 0 ? nb : e;
+    int NL = m->N[eL], NR = m->N[eR], NM = NL > NR ? NL : NR;
+    int nL = NL + 1, nR = NR + 1, nM = NM + 1, nM2 = nM * nM;
+    double g = cfg->gamma;
+    double tL[NVAR * 64], tR[NVAR * 64], mL[NVAR * 64], mR[NVAR * 64];
+    pm_face_values(u + m->off[eL], NVAR, nL, d, NL, tL);
+    pm_face_values(u + m->off[eR], NVAR, nR, d, 0, tR);
+    for (int v = 0; v < NVAR; ++v) {
+        pm_to_mortar(m, NL, NM, tL + v * nL * nL, mL + v * nM2);
+        pm_to_mortar(m, NR, NM, tR + v * nR * nR, mR + v * nM2);
+    }
+    int nv = mode == 0 ? NGRAD : NVAR;
+    double fM[NVAR * 64];
+    if (mode == 0) {
+        for (int p = 0; p < nM2; ++p) {
+            double uL[NVAR], uR[NVAR], qL[NGRAD], qR[NGRAD];
+            for (int v = 0; v < NVAR; ++v) { uL[v] = mL[v * nM2 + p]; uR[v] = mR[v * nM2 + p]; }
+            grad_vars(uL, g, qL);
+            grad_vars(uR, g, qR);
+            for (int v = 0; v < NGRAD; ++v) fM[v * nM2 + p] = 0.5 * (qL[v] + qR[v]);
+        }
+    } else {
+        /* the face metric of the side of degree NM (L on a tie) */
+        double Sn[3 * 64];
+        if (NL >= NR) pm_face_values(m->Ja + 9 * m->noff[eL] + (size_t)d * 3 * (nL * nL * nL), 3, nL, d, NL, Sn);
+        else pm_face_values(m->Ja + 9 * m->noff[eR] + (size_t)d * 3 * (nR * nR * nR), 3, nR, d, 0, Sn);
+        double gL[12 * 64], gR[12 * 64], gmL[12 * 64], gmR[12 * 64];
+        int ns = cfg->physics == 1;
+        if (ns) {
+            pm_face_values(grad + 12 * m->noff[eL], 12, nL, d, NL, gL);
+            pm_face_values(grad + 12 * m->noff[eR], 12, nR, d, 0, gR);
+            for (int k = 0; k < 12; ++k) {
+                pm_to_mortar(m, NL, NM, gL + k * nL * nL, gmL + k * nM2);
+                pm_to_mortar(m, NR, NM, gR + k * nR * nR, gmR + k * nM2);
+            }
+        }
+        double mu = ns ? visc_mu(cfg) : 0.0, kappa = ns ? visc_kappa(cfg) : 0.0;
+        for (int p = 0; p < nM2; ++p) {
+            double uL[NVAR], uR[NVAR], s[3] = {Sn[p], Sn[nM2 + p], Sn[2 * nM2 + p]}, f[NVAR];
+            for (int v = 0; v < NVAR; ++v) { uL[v] = mL[v * nM2 + p]; uR[v] = mR[v * nM2 + p]; }
+            surface_flux(cfg->surface_flux, uL, uR, s, g, f);
+            if (ns) {
+                double qL[NGRAD], qR[NGRAD], GL[12], GR[12], fvL[NVAR], fvR[NVAR];
+                grad_vars(uL, g, qL);
+                grad_vars(uR, g, qR);
+                for (int k = 0; k < 12; ++k) { GL[k] = gmL[k * nM2 + p]; GR[k] = gmR[k * nM2 + p]; }
+                orc_flux_visc(qL, GL, mu, kappa, s, fvL);
+                orc_flux_visc(qR, GR, mu, kappa, s, fvR);
+                for (int v = 0; v < NVAR; ++v) f[v] -= 0.5 * (fvL[v] + fvR[v]);
+            }
+            for (int v = 0; v < NVAR; ++v) fM[v * nM2 + p] = f[v];
+        }
+    }
+    int Ne = m->N[e], ne = Ne + 1;
+    for (int v = 0; v < nv; ++v) pm_from_mortar(m, NM, Ne, fM + v * nM2, out + v * ne * ne);
+}
+
+/* BR1 gradients on the p-non-conforming mesh, grad per element [4][3][n_e^3]
+ * at 12 noff[e]:
+ *   J grad q_c = sum_d D_d (Ja^d_c q) + sum_faces (1/w_end) (q*_e - q_in) (+-Ja^d_c),
+ * q*_e the mortar interface value projected onto the element's face. */
+static void pm_br1(const orc_pmesh *m, const orc_cfg *cfg, const double *u, double *grad)
+{
+    double g = cfg->gamma;
+#pragma omp parallel for schedule(dynamic)
+    for (int e = 0; e < m->E; ++e) {
+        int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+        const double *D = m->D[N], *w = m->w[N];
+        const double *Ja = m->Ja + 9 * m->noff[e], *J = m->J + m->noff[e];
+        const double *ue = u + m->off[e];
+        double *G = grad + 12 * m->noff[e];
+        double q[NGRAD * 512], f[3 * 512];
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], qp[NGRAD];
+            for (int v = 0; v < NVAR; ++v) up[v] = ue[v * n3 + p];
+            grad_vars(up, g, qp);
+            for (int v = 0; v < NGRAD; ++v) q[v * n3 + p] = qp[v];
+        }
+        for (int v = 0; v < NGRAD; ++v)
+        for (int c = 0; c < 3; ++c) {
+            for (int d = 0; d < 3; ++d)
+                for (int p = 0; p < n3; ++p) f[d * n3 + p] = Ja[(d * 3 + c) * n3 + p] * q[v * n3 + p];
+            for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int d = 0; d < 3; ++d) acc += dir_derivative(n, D, f + d * n3, d, i, j, k);
+                G[(v * 3 + c) * n3 + node_index(n, i, j, k)] = acc;
+            }
+        }
+        for (int d = 0; d < 3; ++d)
+        for (int side = -1; side <= 1; side += 2) {
+            double qs[NGRAD * 64];
+            pm_mortar(m, cfg, u, NULL, e, d, side, 0, qs);
+            int at = side > 0 ? N : 0, d0, d1;
+            face_dirs(d, &d0, &d1);
+            for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+                int idx[3];
+                idx[d] = at;
+                idx[d0] = ta;
+                idx[d1] = tb;
+                int p = node_index(n, idx[0], idx[1], idx[2]);
+                for (int v = 0; v < NGRAD; ++v) {
+                    double jump = qs[v * n2 + ta + n * tb] - q[v * n3 + p];
+                    for (int c = 0; c < 3; ++c)
+                        G[(v * 3 + c) * n3 + p] += jump * side * Ja[(d * 3 + c) * n3 + p] / w[at];
+                }
+            }
+        }
+        for (int k = 0; k < 12; ++k)
+            for (int p = 0; p < n3; ++p) G[k * n3 + p] /= J[p];
+    }
+}
+
+int orc_pgradients(const orc_pmesh *m, const orc_cfg *cfg, const double *u, double *grad)
+{
+    pm_br1(m, cfg, u, grad);
+    return 0;
+}
+
+/* du/dt = -(V + S)/J per element of the p-non-conforming mesh: the volume
+ * term exactly as on a conforming mesh (standard or split form, at the
+ * element's own degree) and the surface term
+ *   S = (1/w_end) [ +-F*_e - (F_e - F_v)(in).(+-Ja^d_in) ]
+ * with F*_e the mortar flux projected onto the element's face. */
+int orc_presidual(const orc_pmesh *m, const orc_cfg *cfg, const double *u, double *dudt)
+{
+    double g = cfg->gamma;
+    int ns = cfg->physics == 1;
+    double mu = ns ? visc_mu(cfg) : 0.0, kappa = ns ? visc_kappa(cfg) : 0.0;
+    double *grad = NULL;
+    if (ns) {
+        grad = (double *)malloc(sizeof(double) * 12 * m->noff[m->E]);
+        if (!grad) return -1;
+        pm_br1(m, cfg, u, grad);
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int e = 0; e < m->E; ++e) {
+        int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
+        const double *D = m->D[N], *w = m->w[N];
+        const double *Ja = m->Ja + 9 * m->noff[e], *J = m->J + m->noff[e];
+        const double *ue = u + m->off[e];
+        double *Ft = (double *)malloc(sizeof(double) * 3 * NVAR * n3);
+        double *Fv = (double *)malloc(sizeof(double) * 3 * NVAR * n3);
+        double *R = (double *)calloc(NVAR * n3, sizeof(double));
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], qp[NGRAD], G[12];
+            for (int v = 0; v < NVAR; ++v) up[v] = ue[v * n3 + p];
+            if (ns) {
+                grad_vars(up, g, qp);
+                for (int k = 0; k < 12; ++k) G[k] = grad[12 * m->noff[e] + (size_t)k * n3 + p];
+            }
+            for (int d = 0; d < 3; ++d) {
+                double a[3] = {Ja[(d * 3) * n3 + p], Ja[(d * 3 + 1) * n3 + p], Ja[(d * 3 + 2) * n3 + p]};
+                double fe[NVAR], fv[NVAR] = {0, 0, 0, 0, 0};
+                orc_flux_euler(up, a, g, fe);
+                if (ns) orc_flux_visc(qp, G, mu, kappa, a, fv);
+                for (int v = 0; v < NVAR; ++v) {
+                    Ft[(d * NVAR + v) * n3 + p] = fe[v] - fv[v];
+                    Fv[(d * NVAR + v) * n3 + p] = fv[v];
+                }
+            }
+        }
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            int p = node_index(n, i, j, k), ijk[3] = {i, j, k};
+            for (int d = 0; d < 3; ++d) {
+                if (cfg->volume_form == 0) {
+                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += dir_derivative(n, D, Ft + (d * NVAR + v) * n3, d, i, j, k);
+                    continue;
+                }
+                double ui[NVAR];
+                for (int v = 0; v < NVAR; ++v) ui[v] = ue[v * n3 + p];
+                for (int mm = 0; mm < n; ++mm) {
+                    int pm = node_along(n, d, mm, i, j, k);
+                    double um[NVAR], a[3], fs[NVAR];
+                    for (int v = 0; v < NVAR; ++v) um[v] = ue[v * n3 + pm];
+                    for (int c = 0; c < 3; ++c) a[c] = 0.5 * (Ja[(d * 3 + c) * n3 + p] + Ja[(d * 3 + c) * n3 + pm]);
+                    split_flux(cfg->volume_form, ui, um, a, g, fs);
+                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += 2.0 * D[ijk[d] * n + mm] * fs[v];
+                }
+                if (ns)
+                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] -= dir_derivative(n, D, Fv + (d * NVAR + v) * n3, d, i, j, k);
+            }
+        }
+        for (int d = 0; d < 3; ++d)
+        for (int side = -1; side <= 1; side += 2) {
+            double fs[NVAR * 64];
+            pm_mortar(m, cfg, u, grad, e, d, side, 1, fs);
+            int at = side > 0 ? N : 0, d0, d1;
+            face_dirs(d, &d0, &d1);
+            for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+                int idx[3];
+                idx[d] = at;
+                idx[d0] = ta;
+                idx[d1] = tb;
+                int p = node_index(n, idx[0], idx[1], idx[2]);
+                for (int v = 0; v < NVAR; ++v)
+                    R[v * n3 + p] += (side * fs[v * n2 + ta + n * tb] - side * Ft[(d * NVAR + v) * n3 + p]) / w[at];
+            }
+        }
+        for (int v = 0; v < NVAR; ++v)
+            for (int p = 0; p < n3; ++p) dudt[m->off[e] + (size_t)v * n3 + p] = -R[v * n3 + p] / J[p];
+        free(Ft); free(Fv); free(R);
+    }
+    free(grad);
+    return 0;
+}
+
+/* Time step on the p-non-conforming mesh: the conforming rule per element,
+ * with the element's own n, minimised over the elements:
+ *   dt = min_e min( cfl 8/(n_e^2 lam_c,e), 12/(n_e^4 lam_v,e) ). */
+double orc_pdt(const orc_pmesh *m, const orc_cfg *cfg, const double *u)
+{
+    double g = cfg->gamma, mu = cfg->physics == 1 ? visc_mu(cfg) : 0.0, dt = INFINITY;
+    for (int e = 0; e < m->E; ++e) {
+        int n = m->N[e] + 1, n3 = n * n * n;
+        const double *Ja = m->Ja + 9 * m->noff[e], *J = m->J + m->noff[e];
+        double lam_c = 0.0, lam_v = 0.0;
+        for (int p = 0; p < n3; ++p) {
+            double up[NVAR], rho, v[3], pr;
+            for (int vv = 0; vv < NVAR; ++vv) up[vv] = u[m->off[e] + (size_t)vv * n3 + p];
+            primitives(up, g, &rho, v, &pr);
+            double c = sqrt(g * pr / rho), sc = 0.0, sv = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double a[3] = {Ja[(d * 3) * n3 + p], Ja[(d * 3 + 1) * n3 + p], Ja[(d * 3 + 2) * n3 + p]};
+                double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                sc += (fabs(a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) + c * an) / J[p];
+                sv += (an / J[p]) * (an / J[p]);
+            }
+            if (sc > lam_c) lam_c = sc;
+            if (mu * sv / rho > lam_v) lam_v = mu * sv / rho;
+        }
+        double dte = cfg->cfl * 8.0 / ((double)n * n * lam_c);
+        if (lam_v > 0.0) {
+            double dtv = 12.0 / ((double)n * n * n * n * lam_v);
+            if (dtv < dte) dte = dtv;
+        }
+        if (dte < dt) dt = dte;
+    }
+    return dt;
+}
+
+int orc_prk_step(const orc_pmesh *m, const orc_cfg *cfg, double *u, double *g, double dt_in, double *dt_used)
+{
+    long long count = m->off[m->E];
+    double dt = dt_in > 0.0 ? dt_in : orc_pdt(m, cfg, u);
+    double *R = (double *)malloc(sizeof(double) * count);
+    if (!R) return -1;
+    for (int k = 0; k < lsrk_stages(cfg->time_scheme); ++k) {
+        orc_presidual(m, cfg, u, R);
+        orc_lsrk_stage(cfg->time_scheme, count, k, dt, u, g, R);
+    }
+    free(R);
+    if (dt_used) *dt_used = dt;
+    return 0;
+}
+
+/* Taylor-Green vortex (kind 0: gamma, Ma) or isentropic vortex (kind 1:
+ * gamma, Ma, beta, xc, yc) at the nodes of the p-non-conforming mesh, the
+ * same point formulas as orc_ic_tgv / orc_ic_vortex (t = 0). */
+void orc_pic(const orc_pmesh *m, int kind, const double *par, double *u)
+{
+    double g = par[0], Ma = par[1];
+    double p0 = 1.0 / (g * Ma * Ma);
+    double Lx = m->box.hi[0] - m->box.lo[0], Ly = m->box.hi[1] - m->box.lo[1];
+    for (int e = 0; e < m->E; ++e) {
+        int n = m->N[e] + 1, n3 = n * n * n;
+        const double *X = m->X + 3 * m->noff[e];
+        for (int p = 0; p < n3; ++p) {
+            double x = X[p], y = X[n3 + p], z = X[2 * n3 + p], v[3], pr, rho, up[NVAR];
+            if (kind == 0) {
+                v[0] = sin(x) * cos(y) * cos(z);
+                v[1] = -cos(x) * sin(y) * cos(z);
+                v[2] = 0.0;
+                pr = p0 + (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0) / 16.0;
+                rho = pr / p0;
+            } else {
+                double beta = par[2], dx = x - par[3], dy = y - par[4], uinf = Ma * sqrt(g);
+                dx -= Lx * floor(dx / Lx + 0.5);
+                dy -= Ly * floor(dy / Ly + 0.5);
+                double ex = exp(0.5 * (1.0 - dx * dx - dy * dy));
+                v[0] = uinf - beta / (2.0 * M_PI) * ex * dy;
+                v[1] = beta / (2.0 * M_PI) * ex * dx;
+                v[2] = 0.0;
+                double T = 1.0 - (g - 1.0) * beta * beta / (8.0 * g * M_PI * M_PI) * ex * ex;
+                rho = pow(T, 1.0 / (g - 1.0));
+                pr = pow(rho, g);
+            }
+            conservative(rho, v, pr, g, up);
+            for (int vv = 0; vv < NVAR; ++vv) u[m->off[e] + (size_t)vv * n3 + p] = up[vv];
+        }
+    }
+}
+
+/* Quadrature integrals on the p-non-conforming mesh (each element with its
+ * own weights), as orc_integrals. */
+void orc_pintegrals(const orc_pmesh *m, double g, const double *u, const double *dudt, double *out)
+{
+    for (int v = 0; v < 7; ++v) out[v] = 0.0;
+    for (int e = 0; e < m->E; ++e) {
+        int N = m->N[e], n = N + 1, n3 = n * n * n;
+        const double *w = m->w[N], *J = m->J + m->noff[e];
+        const double *f = (dudt ? dudt : u) + m->off[e];
+        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            int p = node_index(n, i, j, k);
+            double wq = J[p] * w[i] * w[j] * w[k];
+            for (int v = 0; v < NVAR; ++v) out[v] += wq * f[(size_t)v * n3 + p];
+            if (dudt) {
+                double up[NVAR], wv[NVAR];
+                for (int v = 0; v < NVAR; ++v) up[v] = u[m->off[e] + (size_t)v * n3 + p];
+                orc_entropy_vars(up, g, wv);
+                for (int v = 0; v < NVAR; ++v) {
+                    double t = wq * wv[v] * f[(size_t)v * n3 + p];
+                    out[5] += t;
+                    out[6] += fabs(t);
+                }
+            }
+        }
+    }
+}

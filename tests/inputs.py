@@ -45,3 +45,19 @@ def random_state(shape, seed, rho=(0.8, 1.2), vmax=0.5, eps=(1.8, 2.7), smooth=F
 def cube(ex, ey, ez, lo=-np.pi, hi=np.pi):
     """Box extents (lo, hi) for an ex*ey*ez mesh of a cube."""
     return (lo, lo, lo), (hi, hi, hi)
+
+
+def random_degrees(E, seed, lo=1, hi=7):
+    """Seeded per-element polynomial degrees, uniform in [lo, hi]."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, size=E).astype(np.int32)
+
+
+def random_state_blocks(degrees, seed, **kw):
+    """Flat state of element blocks [5, n_e, n_e, n_e] in element order (the
+    layout of a mesh whose elements carry their own degree), each block drawn
+    by random_state with a seed derived from `seed` and the element index."""
+    out = []
+    for e, N in enumerate(degrees):
+        n = int(N) + 1
+        out.append(random_state((1, 5, n, n, n), seed * 100003 + e, **kw).reshape(-1))
+    return np.concatenate(out)
