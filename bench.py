@@ -438,6 +438,7 @@ def run_hs3d(args, world, rank, local):
                                                                           time=tm)
         extra["tgv_32cubed_N3_gauss_standard_roe_br1"] = run_workload("gauss", 32, 3, "ns", "roe", "standard", 5, 2,
                                                                        nodes="gauss")
+        extra["tgv_32cubed_degrees2to5_ec_roe_br1_mortar"] = run_pworkload(32, 2, 5, "ns", "roe", "ec", 5, 2)
 
     if args.stress > 0:
         extra["admission_stress"] = run_stress(args.stress, args.stress_budget_gb, args.stress_emax, "mixed32")
@@ -555,6 +556,88 @@ def run_workload(name, Ed, Nd, physics, surface, volume, steps, warmup, precisio
             if prec != "fp64":
                 out[prec]["l2_rel_vs_fp64_gpu"] = float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))
     del finals, mesh
+    torch.cuda.empty_cache()
+    return out
+
+
+def pstep_bytes(prec, physics, deg, ex, ey, ez, stages=3):
+    """Compulsory DRAM bytes of one RK step on a mesh with per-element
+    degrees: per degree bucket the element (and BR1 gradient) kernel bytes of
+    the conforming model, the gradient kernel reading the mortar's interface
+    values (4 n^2 per face) instead of neighbour traces; per face the mortar
+    kernels read both sides' traces at their own degree (+ gradients for the
+    viscous flux, + the face metric of the side of the larger degree) and
+    write each side's projected block."""
+    import numpy as np
+    s, st = (8, 40) if prec == "fp64" else (4, 20)
+    ns = physics == "ns"
+    deg = np.asarray(deg)
+    n = deg + 1
+    per_stage = 0
+    for N in np.unique(deg):
+        E = int((deg == N).sum())
+        per_stage += kernel_bytes("volume", prec, E, int(N) + 1)
+        if ns:
+            nn = int(N) + 1
+            per_stage += kernel_bytes("grad", prec, E, nn) - E * 6 * st * nn * nn + E * 6 * 4 * nn * nn * s
+    if not ns:
+        per_stage -= int(((12 * n ** 3 * s) * 1).sum())
+    e = np.arange(deg.size)
+    a, b, c = e % ex, (e // ex) % ey, e // (ex * ey)
+    for d in range(3):
+        ab = [a.copy(), b.copy(), c.copy()]
+        ab[d] = (ab[d] + 1) % (ex, ey, ez)[d]
+        r = ab[0] + ex * (ab[1] + ey * ab[2])
+        nL2, nR2 = n ** 2, n[r] ** 2
+        nH2 = np.maximum(nL2, nR2)
+        flux = (nL2 + nR2) * (st + 5 * s + (12 * s if ns else 0)) + 3 * nH2 * s
+        per_stage += int(flux.sum())
+        if ns:
+            per_stage += int(((nL2 + nR2) * (st + 4 * s)).sum())
+    return stages * per_stage
+
+
+def run_pworkload(Ed, dlo, dhi, physics, surface, volume, steps, warmup, precisions=("mixed32", "fp64"), seed=7):
+    """DOF-stage-updates/s of the curved TGV (Ma 0.1, Re 1600, amp 0.05,
+    CFL 0.5) on an Ed^3 mesh whose elements carry seeded degrees uniform in
+    [dlo, dhi], coupled by mortars (hs3d_pmesh_run), CUDA-event timed; the
+    state exceeds L2."""
+    import numpy as np
+    import torch
+
+    import paper_2206_09733_gb300 as hs
+    deg = np.random.default_rng(seed).integers(dlo, dhi + 1, size=Ed ** 3).astype(np.int32)
+    pm = hs.PMesh(Ed, Ed, Ed, deg, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=AMP)
+    npts = int(((deg + 1) ** 3).sum())
+    out = {"E": Ed ** 3, "degrees": f"uniform in {dlo}..{dhi} (numpy default_rng({seed}))", "nodes": npts,
+           "geometry_degree": pm.Ngeo,
+           "scheme": f"{physics} {surface} surface, {volume} volume, rk3, mortars of degree max(N_L, N_R)",
+           "counts": {int(k): int((deg == k).sum()) for k in range(dlo, dhi + 1)}}
+    stream = torch.cuda.current_stream()
+    finals = {}
+    for prec in precisions:
+        cfg = hs.solver_cfg(physics, surface, volume, prec, gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+        u = pm.init_state(pm.empty_state(), "tgv", GAMMA, MA)
+        g = torch.zeros_like(u)
+        pm.run(cfg, u, g, warmup)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pm.run(cfg, u, g, steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        gbs = pstep_bytes(prec, physics, deg, Ed, Ed, Ed) / (ms * 1e-3) / 1e9
+        out[prec] = {"value": round(npts * 3 / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
+                     "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac": round(gbs / measured_hbm_peak()[0], 4)}
+        finals[prec] = u
+        del g
+    if "fp64" in finals:
+        ref = finals["fp64"]
+        for prec, u in finals.items():
+            if prec != "fp64":
+                out[prec]["l2_rel_vs_fp64_gpu"] = float(torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref))
+    del finals, pm
     torch.cuda.empty_cache()
     return out
 

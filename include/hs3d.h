@@ -272,6 +272,69 @@ hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, const doubl
  * Call it outside any stream capture. */
 hs3d_status hs3d_autotune(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, int *choice_out, void *stream);
 
+/* ---------------------------------------------------------------- per-element degree (Sec. 3.6) */
+
+/* A periodic box as for hs3d_mesh_create whose elements carry their own
+ * polynomial degree (Sec. 3.6, isotropic per element): degree is a HOST
+ * array of E = ex*ey*ez ints in 1..7 in element order e = a + ex*(b + ey*c);
+ * desc->N is ignored, desc->node_xyz must be NULL and desc->nodes
+ * Gauss-Lobatto.  Faces between elements of degrees N_L and N_R are coupled
+ * by a mortar of degree max(N_L, N_R) (the mortar method Sec. 3.6 names):
+ * traces interpolated to its Gauss-Lobatto points, the numerical flux and
+ * the BR1 interface value formed there, and each side given the L2
+ * projection onto its degree (exact integrals).  Like the paper's, this
+ * coupling does not keep entropy conservation across faces of different
+ * degree.  Geometry (the rules for p-non-conforming faces Sec. 3.6 follows):
+ * every element's map is the degree-Ngeo polynomial, Ngeo = max(1,
+ * floor(Nmin/2)), interpolating the box map (with its perturbation) at the
+ * element's degree-Ngeo Gauss-Lobatto points; its metric terms are the curl
+ * form at the element's own degree, so the two sides of every face see the
+ * same face metric and a uniform flow stays uniform.  Nmin = 1 requires
+ * perturb_amp = 0 (HS3D_ERR_INVALID otherwise).  Synchronous. */
+typedef struct hs3d_pmesh hs3d_pmesh;
+hs3d_status hs3d_pmesh_create(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmesh **out);
+void hs3d_pmesh_destroy(hs3d_pmesh *pmesh);
+
+/* State layout of the mesh: element e's block [5][n_e][n_e][n_e] (n_e its
+ * degree + 1, v and i as in the conforming layout) starts offset[e] doubles
+ * into the state array; offset (HOST, E+1 int64) also receives offset[E] =
+ * the doubles a state array must hold.  Elements are stored grouped by
+ * degree (ascending), in element order within a degree; each group starts at
+ * a multiple of 160 doubles, and the gaps between groups are never read or
+ * written.  Ngeo (may be NULL) receives the geometry degree. */
+hs3d_status hs3d_pmesh_layout(const hs3d_pmesh *pmesh, int64_t *offset, int *Ngeo);
+
+/* Node coordinates and Jacobians into caller-owned DEVICE arrays (either may
+ * be NULL): element e's X block [3][n_e^3] at 3*offset[e]/5, its J block
+ * [n_e^3] at offset[e]/5 (arrays of 3*offset[E]/5 and offset[E]/5 doubles).
+ * Stream-ordered. */
+hs3d_status hs3d_pmesh_geometry(const hs3d_pmesh *pmesh, double *X, double *J, void *stream);
+
+/* Initial condition at every element's nodes into u (device, the layout above). */
+hs3d_status hs3d_pmesh_init_state(const hs3d_pmesh *pmesh, const hs3d_ic *ic, double *u, void *stream);
+
+/* Residual du/dt = -(V + S)/J of every element (volume term at its own
+ * degree, surface term from the mortar fluxes projected onto its faces), as
+ * hs3d_residual.  u, dudt: device, the layout above, distinct.  Any
+ * precision; Gauss-Lobatto nodes.  Stream-ordered. */
+hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *cfg, const double *u, double *dudt,
+                                void *stream);
+
+/* nsteps low-storage RK steps of cfg->time_scheme on u and g (device, the
+ * layout above; g need not be initialised).  dt > 0: fixed; otherwise dt
+ * of every step is the conforming rule per element with the element's own
+ * n, minimised over the elements:
+ *   dt = min_e min( cfl*8/(n_e^2 lam_c,e), 12/(n_e^4 lam_v,e) ),
+ * the first step from a pass over u, the later ones from the maxima the
+ * previous step's last stage reduced.  Steps after the first replay one
+ * captured CUDA graph (kept for the last (cfg, u, g, dt)).  Stream-ordered. */
+hs3d_status hs3d_pmesh_run(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
+                           int nsteps, void *stream);
+
+/* Simulated time and steps of hs3d_pmesh_run since creation or the last
+ * reset, as hs3d_clock. */
+hs3d_status hs3d_pmesh_clock(const hs3d_pmesh *pmesh, double *t, int64_t *steps, int reset, void *stream);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* One RK3 step exactly as hs3d_rk3_step, launched eagerly with CUDA events

@@ -42,7 +42,9 @@ EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh
            "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
            "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
            "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
-           "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding"]
+           "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding", "hs3d_pmesh_create",
+           "hs3d_pmesh_destroy", "hs3d_pmesh_layout", "hs3d_pmesh_geometry", "hs3d_pmesh_init_state",
+           "hs3d_pmesh_residual", "hs3d_pmesh_run", "hs3d_pmesh_clock"]
 
 
 class HS3DError(RuntimeError):
@@ -115,6 +117,14 @@ def lib():
                 "hs3d_diagnostics_noalloc": [i, C.c_int64, d, vp, vp, vp, vp, vp],
                 "hs3d_autotune": [vp, C.POINTER(SolverCfg), C.POINTER(i), vp],
                 "hs3d_check_rounding": [vp, C.c_int64, vp, vp],
+                "hs3d_pmesh_create": [C.POINTER(MeshDesc), vp, C.POINTER(vp)],
+                "hs3d_pmesh_destroy": [vp],
+                "hs3d_pmesh_layout": [vp, vp, C.POINTER(i)],
+                "hs3d_pmesh_geometry": [vp, vp, vp, vp],
+                "hs3d_pmesh_init_state": [vp, C.POINTER(IC), vp, vp],
+                "hs3d_pmesh_residual": [vp, C.POINTER(SolverCfg), vp, vp, vp],
+                "hs3d_pmesh_run": [vp, C.POINTER(SolverCfg), vp, vp, d, i, vp],
+                "hs3d_pmesh_clock": [vp, C.POINTER(d), C.POINTER(C.c_int64), i, vp],
                 "hs3d_last_error": [],
                 "hs3d_version": [],
             }
@@ -123,6 +133,7 @@ def lib():
                 f.argtypes = args
                 f.restype = C.c_int
             L.hs3d_mesh_destroy.restype = None
+            L.hs3d_pmesh_destroy.restype = None
             L.hs3d_server_destroy.restype = None
             L.hs3d_last_error.restype = C.c_char_p
             L.hs3d_version.restype = C.c_char_p
@@ -274,6 +285,85 @@ class Mesh:
         check(lib().hs3d_diagnostics(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(dudt, "dudt"), _ptr(out, "out"),
                                      _stream(stream)))
         return out
+
+
+class PMesh:
+    """A mesh whose elements carry their own polynomial degree, coupled by
+    mortars (``hs3d_pmesh_create``, Sec. 3.6).
+
+    States are flat float64 CUDA tensors of ``size`` doubles; element e's
+    block [5, n_e, n_e, n_e] starts at ``offset[e]`` (elements grouped by
+    degree, see ``hs3d_pmesh_layout``)."""
+
+    def __init__(self, ex, ey, ez, degrees, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0):
+        import numpy as np
+        self.ex, self.ey, self.ez = ex, ey, ez
+        self.E = ex * ey * ez
+        deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32).reshape(-1))
+        if deg.size != self.E:
+            raise HS3DError(ERR_INVALID, "one degree per element")
+        self.degrees = deg.copy()
+        self.lo, self.hi = tuple(lo), tuple(hi)
+        d = mesh_desc(ex, ey, ez, 1, lo, hi, amp)
+        h = C.c_void_p()
+        check(lib().hs3d_pmesh_create(C.byref(d), C.c_void_p(deg.ctypes.data), C.byref(h)))
+        self._h = h
+        off = np.zeros(self.E + 1, dtype=np.int64)
+        ng = C.c_int()
+        check(lib().hs3d_pmesh_layout(h, C.c_void_p(off.ctypes.data), C.byref(ng)))
+        self.offset = off
+        self.size = int(off[-1])
+        self.Ngeo = ng.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().hs3d_pmesh_destroy(h)
+            self._h = None
+
+    def n(self, e):
+        return int(self.degrees[e]) + 1
+
+    def empty_state(self):
+        import torch
+        return torch.zeros(self.size, dtype=torch.float64, device="cuda")
+
+    def block(self, u, e):
+        """View of element e's block [5, n, n, n] of a flat state (tensor or array)."""
+        n = self.n(e)
+        o = int(self.offset[e])
+        return u[o:o + 5 * n ** 3].reshape(5, n, n, n)
+
+    def geometry(self, stream=None):
+        """(X, J) as flat tensors: element e's X [3, n^3] at 3 offset[e]/5, J [n^3] at offset[e]/5."""
+        import torch
+        X = torch.zeros(3 * self.size // 5, dtype=torch.float64, device="cuda")
+        J = torch.zeros(self.size // 5, dtype=torch.float64, device="cuda")
+        check(lib().hs3d_pmesh_geometry(self._h, _ptr(X), _ptr(J), _stream(stream)))
+        return X, J
+
+    def init_state(self, u, kind="tgv", gamma=1.4, Ma=0.1, beta=5.0, xc=None, yc=None, t=0.0, stream=None):
+        if xc is None:
+            xc = 0.5 * (self.lo[0] + self.hi[0])
+        if yc is None:
+            yc = 0.5 * (self.lo[1] + self.hi[1])
+        ic = IC({"vortex": IC_VORTEX, "tgv": IC_TGV}[kind], gamma, Ma, beta, xc, yc, t)
+        check(lib().hs3d_pmesh_init_state(self._h, C.byref(ic), _ptr(u, "u"), _stream(stream)))
+        return u
+
+    def residual(self, cfg: SolverCfg, u, dudt, stream=None):
+        check(lib().hs3d_pmesh_residual(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(dudt, "dudt"), _stream(stream)))
+        return dudt
+
+    def run(self, cfg: SolverCfg, u, g, nsteps, dt=0.0, stream=None):
+        """nsteps RK steps (hs3d_pmesh_run): dt > 0 fixed, else the CFL rule."""
+        check(lib().hs3d_pmesh_run(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), int(nsteps),
+                                   _stream(stream)))
+
+    def clock(self, reset=False, stream=None):
+        t, s = C.c_double(), C.c_int64()
+        check(lib().hs3d_pmesh_clock(self._h, C.byref(t), C.byref(s), int(reset), _stream(stream)))
+        return t.value, s.value
 
 
 class Server:

@@ -52,6 +52,7 @@ void cont_forget(const hs3d_mesh *m, const double *u_written);   // nullptr: for
 hs3d_status fail(hs3d_status st, const char *fmt, ...);
 hs3d_status cuda_fail(cudaError_t e, const char *what);
 hs3d_status validate_cfg(const hs3d_solver_cfg *c);
+hs3d_status check_ptr(const void *p, const char *name);   // non-NULL and 16-byte aligned
 hs3d_status validate_desc(const hs3d_mesh_desc *d);
 hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out);
 void mesh_free(hs3d_mesh *m);

@@ -247,14 +247,28 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
         }
         // neighbour traces of q: all loads of this thread's face points first
         // (the loop is unrolled to its fixed trip count), then the conversions
+        constexpr int IT = (6 * n2 + n3 - 1) / n3;
+        if (it.face6) {
+            // mesh with per-element degrees: the mortar kernel left 2 q*_e - q_in
+#pragma unroll
+            for (int k = 0; k < IT; ++k) {
+                const int t = p + k * n3;
+                if (t < 6 * n2) {
+                    const int slot = t / n2, ab = t - slot * n2;
+                    const R *src = (const R *)it.qhat6 + ((size_t)slot * it.E + e) * 4 * n2 + ab;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) qn[(slot * 4 + v) * n2 + ab] = src[v * n2];
+                }
+            }
+        }
         const Nbrs nbs = elem_nbrs(e, it.ex, it.ey, it.ez);
         const R *st;
         if constexpr (sizeof(R) == 4) st = it.uf;
         else st = it.u;
-        constexpr int IT = (6 * n2 + n3 - 1) / n3;
         R raw[IT][5];
 #pragma unroll
         for (int k = 0; k < IT; ++k) {
+            if (it.face6) break;
             const int t = p + k * n3;
             if (t < 6 * n2) {
                 const int slot = t / n2, ab = t - slot * n2;
@@ -267,6 +281,7 @@ __global__ void __launch_bounds__(grad_threads<N>()) k_grad(const __grid_constan
         }
 #pragma unroll
         for (int k = 0; k < IT; ++k) {
+            if (it.face6) break;
             const int t = p + k * n3;
             if (t < 6 * n2) {
                 const int slot = t / n2, ab = t - slot * n2;

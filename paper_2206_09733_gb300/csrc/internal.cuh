@@ -61,8 +61,17 @@ struct Item {
                             // kernel that writes u, or by a shadow/priming pass)
     double *g;
     double *out;            // residual output (residual mode)
-    void *fstar;            // R [3][E][5][n2]
+    void *fstar;            // R [3][E][5][n2] (face6: [6][E][5][n2], see below)
     void *grad;             // R [E][12][n3]
+    // face6 != 0 (one degree bucket of a mesh with per-element degrees): the
+    // element's six face fluxes are its own blocks fstar[slot][e], slot 2d
+    // the -d face and 2d+1 the +d face, each already projected onto this
+    // element's face; the BR1 gradient kernel reads, instead of the
+    // neighbour's trace, qhat6[slot][e][4][n2] = 2 q*_e - q_in (q*_e the
+    // mortar interface value projected onto this face), so that its lifting
+    // (q_out - q_in)/2 = q*_e - q_in is unchanged
+    const void *qhat6;
+    int face6;
     Clock *clk;
     int ex, ey, ez;
     int E;

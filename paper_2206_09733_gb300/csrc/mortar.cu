@@ -1,0 +1,428 @@
+// Mortar coupling of elements of different polynomial degree (Sec. 3.6).
+//
+// A mesh whose elements carry their own degree runs the element kernels once
+// per degree (one bucket of elements per degree, Item::face6 set); what
+// couples the buckets are the faces.  Every face between an element L (its
+// +d face, degree N_L) and its +d neighbour R (its -d face, degree N_R)
+// carries a mortar of degree N_M = max(N_L, N_R) on the Gauss-Lobatto points
+// of that degree (the mortar method of Kopriva et al. 2002 that Sec. 3.6
+// names; it does not keep entropy stability, as the section notes):
+//   1. the conservative traces of both sides (and for the viscous flux their
+//      BR1 gradients) are interpolated to the mortar points,
+//        f_M(a, b) = sum_j I_b,j sum_i I_a,i f(i, j),  I = l_i^(N_s)(xi_a^(N_M));
+//   2. at every mortar point either the BR1 interface value
+//      q* = (q(u_L) + q(u_R))/2 (k_mortar<MODE 0>) or the face flux
+//      s F*(u_L, u_R; n) - (F_v(L) + F_v(R)).Sn/2 (MODE 1) is formed, with the
+//      face metric Sn = Ja^d of the side of degree N_M (of L on a tie);
+//   3. each side receives the L2 projection of the mortar function onto its
+//      degree, P = M_s^-1 S (M_s[i][k] = int l_i l_k, S[i][j] = int l_i^s l_j^M,
+//      exact integrals), in both face directions; the side of degree N_M
+//      receives the mortar values.
+// Equal degrees make every matrix the identity: the conforming face.
+//
+// One CTA of 64 threads per face, one thread per mortar point (N_M <= 7).
+// The per-bucket pointers live in a small device table (MortarSide); the
+// operators of every degree pair in MortarOps.
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+#include "mortar.cuh"
+#include "physics.cuh"
+
+namespace hs3d {
+
+// ------------------------------------------------------------------ operators (host)
+
+// Lagrange basis of the nodes x[0..n) at y.
+static void lagrange_basis(int n, const double *x, double y, double *l)
+{
+    for (int j = 0; j < n; ++j) {
+        double v = 1.0;
+        for (int k = 0; k < n; ++k)
+            if (k != j) v *= (y - x[k]) / (x[j] - x[k]);
+        l[j] = v;
+    }
+}
+
+// Interpolation Ns -> Nm (nm x ns) and the exact L2 projection Nm -> Ns
+// (ns x nm) on the Gauss-Lobatto points.  The projection solves
+// M_s P = S with the symmetric positive definite mass matrix M_s factored by
+// Cholesky; both integrals use Nm + 1 Gauss-Legendre points (exact for the
+// degree Ns + Nm <= 2 Nm products).
+static void build_pair(int Ns, int Nm, double *Pi, double *P)
+{
+    const int ns = Ns + 1, nm = Nm + 1;
+    const Ops &os = host_ops(Ns), &om = host_ops(Nm);
+    if (Ns == Nm) {
+        for (int a = 0; a < ns; ++a)
+            for (int i = 0; i < ns; ++i) Pi[a * ns + i] = P[a * ns + i] = (a == i) ? 1.0 : 0.0;
+        return;
+    }
+    for (int a = 0; a < nm; ++a) lagrange_basis(ns, os.xi, om.xi[a], Pi + a * ns);
+    const Ops &og = host_ops(Nm, HS3D_NODES_GAUSS);
+    double M[kMaxn * kMaxn] = {0}, S[kMaxn * kMaxn] = {0};
+    for (int q = 0; q < nm; ++q) {
+        double ls[kMaxn], lm[kMaxn];
+        lagrange_basis(ns, os.xi, og.xi[q], ls);
+        lagrange_basis(nm, om.xi, og.xi[q], lm);
+        for (int i = 0; i < ns; ++i) {
+            for (int k = 0; k < ns; ++k) M[i * ns + k] += og.w[q] * ls[i] * ls[k];
+            for (int j = 0; j < nm; ++j) S[i * nm + j] += og.w[q] * ls[i] * lm[j];
+        }
+    }
+    // M = C C^T (C lower triangular), then C y = S, C^T P = y, column by column
+    double Cl[kMaxn * kMaxn] = {0};
+    for (int i = 0; i < ns; ++i)
+        for (int k = 0; k <= i; ++k) {
+            double s = M[i * ns + k];
+            for (int r = 0; r < k; ++r) s -= Cl[i * ns + r] * Cl[k * ns + r];
+            Cl[i * ns + k] = (i == k) ? sqrt(s) : s / Cl[k * ns + k];
+        }
+    for (int j = 0; j < nm; ++j) {
+        double y[kMaxn];
+        for (int i = 0; i < ns; ++i) {
+            double s = S[i * nm + j];
+            for (int r = 0; r < i; ++r) s -= Cl[i * ns + r] * y[r];
+            y[i] = s / Cl[i * ns + i];
+        }
+        for (int i = ns - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int r = i + 1; r < ns; ++r) s -= Cl[r * ns + i] * P[r * nm + j];
+            P[i * nm + j] = s / Cl[i * ns + i];
+        }
+    }
+}
+
+const MortarOps &host_mortar_ops()
+{
+    static MortarOps mo;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int s = 1; s <= kMaxN; ++s)
+            for (int m = s; m <= kMaxN; ++m) {
+                build_pair(s, m, mo.Pi[s][m], mo.P[s][m]);
+                for (int k = 0; k < kMaxn * kMaxn; ++k) {
+                    mo.Pif[s][m][k] = (float)mo.Pi[s][m][k];
+                    mo.Pf[s][m][k] = (float)mo.P[s][m][k];
+                }
+            }
+    });
+    return mo;
+}
+
+const MortarOps *device_mortar_ops()
+{
+    static std::mutex mu;
+    static std::vector<MortarOps *> per_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
+    if (!per_dev[dev]) {
+        MortarOps *d = nullptr;
+        if (cudaMalloc(&d, sizeof(MortarOps)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaMemcpy(d, &host_mortar_ops(), sizeof(MortarOps), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(d);
+            cudaGetLastError();
+            return nullptr;
+        }
+        per_dev[dev] = d;
+    }
+    return per_dev[dev];
+}
+
+// ------------------------------------------------------------------ device helpers
+
+template <typename R>
+__device__ __forceinline__ const R *mo_interp(const MortarOps *mo, int Ns, int Nm);
+template <>
+__device__ __forceinline__ const double *mo_interp<double>(const MortarOps *mo, int Ns, int Nm) { return mo->Pi[Ns][Nm]; }
+template <>
+__device__ __forceinline__ const float *mo_interp<float>(const MortarOps *mo, int Ns, int Nm) { return mo->Pif[Ns][Nm]; }
+template <typename R>
+__device__ __forceinline__ const R *mo_proj(const MortarOps *mo, int Ns, int Nm);
+template <>
+__device__ __forceinline__ const double *mo_proj<double>(const MortarOps *mo, int Ns, int Nm) { return mo->P[Ns][Nm]; }
+template <>
+__device__ __forceinline__ const float *mo_proj<float>(const MortarOps *mo, int Ns, int Nm) { return mo->Pf[Ns][Nm]; }
+
+template <typename R>
+__device__ __forceinline__ Prim<R> mortar_prim(const R u[5], R gm1)
+{
+    if constexpr (sizeof(R) == 8) return prim_from_u<double>((const double *)u, gm1);
+    else return prim_from_f((const float *)u, gm1);
+}
+
+// BR1 gradient variables q = (v1, v2, v3, T), T = p/rho.
+template <typename R>
+__device__ __forceinline__ void mortar_q(const R u[5], R gm1, R q[4])
+{
+    const Prim<R> w = mortar_prim(u, gm1);
+    q[0] = w.v1;
+    q[1] = w.v2;
+    q[2] = w.v3;
+    q[3] = w.p / w.rho;
+}
+
+// Inviscid numerical flux times the face scale, from the two conservative
+// states at a mortar point (the same flux functions as the conforming face
+// kernel).
+template <typename R>
+__device__ __forceinline__ void mortar_riemann(int flux, const R ul[5], const R ur[5], const MortarPhys<R> &P, R s1,
+                                               R s2, R s3, R fs[5])
+{
+    const Prim<R> qL = mortar_prim(ul, P.gm1), qR = mortar_prim(ur, P.gm1);
+    if (flux == HS3D_FLUX_EC) {
+        flux_ec(ec_node(qL), ec_node(qR), P.hg, s1, s2, s3, fs);
+    } else if (flux == HS3D_FLUX_LF) {
+        flux_lf(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+    } else if (flux == HS3D_FLUX_RUSANOV) {
+        flux_rusanov(qL, ul, qR, ur, P.gamma, s1, s2, s3, fs);
+    } else if (flux == HS3D_FLUX_MATRIX) {
+        flux_matrix(qL, qR, P.gamma, P.hg, s1, s2, s3, fs);
+    } else {
+        const R a[5] = {qL.rho, (R)0, (R)0, (R)0, qL.E};
+        const R c[5] = {qR.rho, (R)0, (R)0, (R)0, qR.E};
+        if (flux == HS3D_FLUX_LDROE) flux_ldroe(qL, a, qR, c, P.gamma, s1, s2, s3, fs);
+        else flux_roe(qL, a, qR, c, P.gamma, s1, s2, s3, fs);
+    }
+}
+
+// Node of an element of n nodes per direction with index `end` along d and
+// tangential indices (ta, tb) (increasing direction order).
+__device__ __forceinline__ int mortar_face_node(int n, int d, int end, int ta, int tb)
+{
+    if (d == 0) return end + n * (ta + n * tb);
+    if (d == 1) return ta + n * (end + n * tb);
+    return ta + n * (tb + n * end);
+}
+
+// ------------------------------------------------------------------ the face kernel
+
+// MODE 0: BR1 interface values, written as qhat = 2 q*_s - q_s (4 values) to
+//         each side's qhat6 block; MODE 1: face fluxes (5 values) to each
+//         side's fstar block (both oriented along +d).
+template <typename R, bool NS, int MODE>
+__global__ void __launch_bounds__(64) k_mortar(const MortarFace *__restrict__ faces, int nfaces,
+                                               const MortarSide *__restrict__ sides, const double *__restrict__ u,
+                                               const MortarOps *__restrict__ mo, int flux, MortarPhys<R> P)
+{
+    constexpr int NV = (MODE == 1 && NS) ? 17 : 5;   // traces per point: state (+ 12 gradients)
+    __shared__ R tr[2][NV][64];   // each side's traces on its own face points
+    __shared__ R mt[2][NV][64];   // the same at the mortar points
+    __shared__ R fm[5][64];       // the mortar result
+    const int f = blockIdx.x;
+    if (f >= nfaces) return;
+    const MortarFace F = faces[f];
+    const int d = f % 3;
+    const MortarSide &SL = sides[F.bL], &SR = sides[F.bR];
+    const int NL = SL.N, NR = SR.N, NM = NL > NR ? NL : NR;
+    const int nM = NM + 1;
+    const int t = threadIdx.x;
+
+    // 1. traces of both sides: L's +d face (index N_L along d), R's -d face (index 0)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const MortarSide &S = s ? SR : SL;
+        const int ns = S.N + 1, n3 = ns * ns * ns;
+        const int le = s ? F.lR : F.lL;
+        if (t < ns * ns) {
+            const int node = mortar_face_node(ns, d, s ? 0 : S.N, t % ns, t / ns);
+            if constexpr (sizeof(R) == 8) {
+                const double *src = u + S.base + (size_t)le * 5 * n3 + node;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) tr[s][v][t] = src[(size_t)v * n3];
+            } else {
+                const float *src = S.uf + (size_t)le * 5 * n3 + node;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) tr[s][v][t] = src[(size_t)v * n3];
+            }
+            if constexpr (MODE == 1 && NS) {
+                const R *G = (const R *)S.grad + (size_t)le * 12 * n3 + node;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) tr[s][5 + k][t] = G[(size_t)k * n3];
+            }
+        }
+    }
+    __syncthreads();
+
+    // 2. interpolation to the mortar points
+    if (t < nM * nM) {
+        const int a = t % nM, b = t / nM;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int Ns = s ? NR : NL, ns = Ns + 1;
+            if (Ns == NM) {
+                for (int v = 0; v < NV; ++v) mt[s][v][t] = tr[s][v][t];
+            } else {
+                const R *I = mo_interp<R>(mo, Ns, NM);
+                for (int v = 0; v < NV; ++v) {
+                    R acc = (R)0;
+                    for (int j = 0; j < ns; ++j) {
+                        R row = (R)0;
+                        for (int i = 0; i < ns; ++i) row += I[a * ns + i] * tr[s][v][i + ns * j];
+                        acc += I[b * ns + j] * row;
+                    }
+                    mt[s][v][t] = acc;
+                }
+            }
+        }
+        // 3. the mortar function
+        R ul[5], ur[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            ul[v] = mt[0][v][t];
+            ur[v] = mt[1][v][t];
+        }
+        if constexpr (MODE == 0) {
+            R qL[4], qR[4];
+            mortar_q(ul, P.gm1, qL);
+            mortar_q(ur, P.gm1, qR);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) fm[v][t] = (R)0.5 * (qL[v] + qR[v]);
+        } else {
+            // face metric of the side of degree N_M (L on a tie): its own face point t
+            const bool useL = NL >= NR;
+            const MortarSide &H = useL ? SL : SR;
+            const int nh = H.N + 1, n3h = nh * nh * nh;
+            const int node = mortar_face_node(nh, d, useL ? H.N : 0, a, b);
+            const R *JA = (const R *)(sizeof(R) == 8 ? (const void *)H.Ja : (const void *)H.Jaf) +
+                          ((size_t)(useL ? F.lL : F.lR) * 9 + d * 3) * n3h + node;
+            const R s1 = JA[0], s2 = JA[n3h], s3 = JA[2 * (size_t)n3h];
+            R fs[5];
+            mortar_riemann<R>(flux, ul, ur, P, s1, s2, s3, fs);
+            if constexpr (NS) {
+                R gl[12], gr[12], fl[5], fr[5];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    gl[k] = mt[0][5 + k][t];
+                    gr[k] = mt[1][5 + k][t];
+                }
+                const Prim<R> pL = mortar_prim(ul, P.gm1), pR = mortar_prim(ur, P.gm1);
+                visc_flux(pL, gl, P.mu, P.kappa, s1, s2, s3, fl);
+                visc_flux(pR, gr, P.mu, P.kappa, s1, s2, s3, fr);
+#pragma unroll
+                for (int v = 1; v < 5; ++v) fs[v] -= (R)0.5 * (fl[v] + fr[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < 5; ++v) fm[v][t] = fs[v];
+        }
+    }
+    __syncthreads();
+
+    // 4. projection onto each side and the write to its own face block
+    constexpr int NOUT = MODE == 0 ? 4 : 5;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const MortarSide &S = s ? SR : SL;
+        const int Ns = S.N, ns = Ns + 1, n2 = ns * ns;
+        if (t >= n2) continue;
+        const int a = t % ns, b = t / ns;
+        R val[5];
+        if (Ns == NM) {
+#pragma unroll
+            for (int v = 0; v < NOUT; ++v) val[v] = fm[v][t];
+        } else {
+            const R *Pr = mo_proj<R>(mo, Ns, NM);
+#pragma unroll
+            for (int v = 0; v < NOUT; ++v) {
+                R acc = (R)0;
+                for (int j = 0; j < nM; ++j) {
+                    R row = (R)0;
+                    for (int i = 0; i < nM; ++i) row += Pr[a * nM + i] * fm[v][i + nM * j];
+                    acc += Pr[b * nM + j] * row;
+                }
+                val[v] = acc;
+            }
+        }
+        const int slot = s ? 2 * d : 2 * d + 1;
+        const int le = s ? F.lR : F.lL;
+        if constexpr (MODE == 0) {
+            R uin[5], qin[4];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) uin[v] = tr[s][v][t];
+            mortar_q(uin, P.gm1, qin);
+            R *dst = (R *)S.qhat6 + ((size_t)slot * S.E + le) * 4 * n2 + t;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) dst[v * n2] = (R)2 * val[v] - qin[v];
+        } else {
+            R *dst = (R *)S.fstar6 + ((size_t)slot * S.E + le) * 5 * n2 + t;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) dst[v * n2] = val[v];
+        }
+    }
+}
+
+cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, int nfaces,
+                          const MortarSide *sides, const double *u, const MortarPhys<double> &P, cudaStream_t s)
+{
+    if (nfaces == 0) return cudaSuccess;
+    const MortarOps *mo = device_mortar_ops();
+    if (!mo) return cudaErrorMemoryAllocation;
+    const bool ns = physics == HS3D_NS;
+    if (prec == HS3D_FP64) {
+        if (mode == 0) k_mortar<double, true, 0><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, P);
+        else if (ns) k_mortar<double, true, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, P);
+        else k_mortar<double, false, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, P);
+    } else {
+        const MortarPhys<float> Pf{(float)P.gamma, (float)P.gm1, (float)P.hg, (float)P.mu, (float)P.kappa};
+        if (mode == 0) k_mortar<float, true, 0><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, Pf);
+        else if (ns) k_mortar<float, true, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, Pf);
+        else k_mortar<float, false, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, Pf);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ time step
+
+// dt of a mesh with per-element degrees: the conforming rule per degree
+// bucket (its own n, its maxima in clock slot `slot`), minimised over the
+// buckets; every bucket's clock then carries the same dt, t and step count,
+// and its maxima are reset.  One thread.
+__global__ void k_pdt_finalize(Clock *const *clks, const int *nb_n, int nb, double cfl, double kc, double kv, int slot,
+                               double dt_fixed)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double dt = dt_fixed > 0.0 ? dt_fixed : INFINITY;
+    int bad = 0;
+    for (int i = 0; i < nb; ++i) {
+        Clock *c = clks[i];
+        const double lc = __longlong_as_double((long long)c->lam[slot][0]);
+        const double lv = __longlong_as_double((long long)c->lam[slot][1]);
+        if (c->bad) bad = c->bad;
+        if (dt_fixed > 0.0) continue;
+        const double n = nb_n[i];
+        double dti = cfl * kc / (n * n * lc);
+        if (lv > 0.0) dti = fmin(dti, kv / (n * n * n * n * lv));
+        dt = fmin(dt, dti);
+    }
+    if (!(dt > 0.0) || !(dt < INFINITY)) bad = bad ? bad : 1;
+    for (int i = 0; i < nb; ++i) {
+        Clock *c = clks[i];
+        c->lam[0][0] = c->lam[0][1] = c->lam[1][0] = c->lam[1][1] = 0ull;
+        if (bad) {
+            c->bad = bad;
+            c->done = 1;
+            c->dt = 0.0;
+            continue;
+        }
+        c->dt = dt;
+        c->t += dt;
+        c->step += 1;
+    }
+}
+
+cudaError_t launch_pdt_finalize(Clock *const *clks, const int *nb_n, int nb, double cfl, double kc, double kv,
+                                int slot, double dt_fixed, cudaStream_t s)
+{
+    k_pdt_finalize<<<1, 1, 0, s>>>(clks, nb_n, nb, cfl, kc, kv, slot, dt_fixed);
+    return cudaGetLastError();
+}
+
+}  // namespace hs3d

@@ -1,0 +1,458 @@
+// Meshes whose elements carry their own polynomial degree (Sec. 3.6: the
+// degree of every element may differ; neighbours of different degree are
+// coupled by mortars).
+//
+// The elements are grouped by degree into buckets.  Each bucket is a
+// conforming-path mesh object of its own degree (geometry, FP32 shadow,
+// gradient scratch, clock) whose element kernels run with Item::face6: they
+// take their six face fluxes (and BR1 interface values) from per-element
+// blocks that the mortar face kernel (mortar.cu) writes for every face of
+// the whole mesh.  A stage is
+//   [k_mortar interface values -> k_grad per bucket]  (Navier-Stokes)
+//   k_mortar face fluxes -> k_volume per bucket (volume + lift + 1/J + RK stage)
+// and a step starts with the dt rule over all buckets (k_pdt_finalize).
+//
+// Geometry (the free-stream rules for p-non-conforming faces that Sec. 3.6
+// follows): every element's map is the polynomial of degree
+// Ngeo = max(1, floor(Nmin/2)) that interpolates the box map at the
+// element's Gauss-Lobatto points of degree Ngeo, evaluated at its own nodes;
+// the metric terms are the curl form at the element's own degree.  The
+// products X_l dX_m then have degree 2 Ngeo <= Nmin per direction, every
+// element represents them exactly, and the face metric terms are one
+// polynomial seen from both sides.  Nmin = 1 allows only an affine map
+// (perturb_amp = 0).
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "api_internal.h"
+#include "mortar.cuh"
+
+using namespace hs3d;
+
+struct hs3d_pmesh {
+    int ex = 0, ey = 0, ez = 0, E = 0, Nmin = 0, Nmax = 0, Ngeo = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, amp = 0.0;
+    std::vector<int> deg;
+    std::vector<int64_t> off;   // [E+1] state offsets (doubles)
+    struct Bucket {
+        int N = 0, E = 0;
+        int64_t base = 0;
+        hs3d_mesh *m = nullptr;
+        void *fstar6 = nullptr, *qhat6 = nullptr;
+    };
+    std::vector<Bucket> b;
+    MortarFace *faces = nullptr;   // device [3E]
+    MortarSide *sides = nullptr;   // device [nb]
+    Clock **clks = nullptr;        // device [nb]
+    int *nb_n = nullptr;           // device [nb]
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    cudaGraphExec_t gexec = nullptr;   // one step of hs3d_pmesh_run for (gcfg, gu, gg, gdt)
+    hs3d_solver_cfg gcfg{};
+    const double *gu = nullptr, *gg = nullptr;
+    double gdt = 0.0;
+};
+
+namespace {
+
+void pmesh_free(hs3d_pmesh *pm)
+{
+    if (!pm) return;
+    if (pm->gexec) cudaGraphExecDestroy(pm->gexec);
+    for (auto &bk : pm->b) {
+        if (bk.m) mesh_free(bk.m);
+        if (bk.fstar6) cudaFree(bk.fstar6);
+        if (bk.qhat6) cudaFree(bk.qhat6);
+    }
+    void *ptrs[] = {pm->faces, pm->sides, pm->clks, pm->nb_n};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (pm->stream) cudaStreamDestroy(pm->stream);
+    delete pm;
+}
+
+// The box map (with its perturbation) at reference point r of element e.
+void box_point(const hs3d_pmesh *pm, int e, const double r[3], double x[3])
+{
+    const int Ed[3] = {pm->ex, pm->ey, pm->ez};
+    const int ab[3] = {e % pm->ex, (e / pm->ex) % pm->ey, e / (pm->ex * pm->ey)};
+    double th[3];
+    for (int c = 0; c < 3; ++c) {
+        const double L = pm->hi[c] - pm->lo[c];
+        x[c] = pm->lo[c] + (L / Ed[c]) * (ab[c] + 0.5 * (r[c] + 1.0));
+        th[c] = -M_PI + 2.0 * M_PI * (x[c] - pm->lo[c]) / L;
+    }
+    const double s = sin(th[0]) * sin(th[1]) * sin(th[2]);
+    for (int c = 0; c < 3; ++c) x[c] += pm->amp * ((pm->hi[c] - pm->lo[c]) / (2.0 * M_PI)) * s;
+}
+
+void lagrange_row(int n, const double *x, double y, double *l)
+{
+    for (int j = 0; j < n; ++j) {
+        double v = 1.0;
+        for (int k = 0; k < n; ++k)
+            if (k != j) v *= (y - x[k]) / (x[j] - x[k]);
+        l[j] = v;
+    }
+}
+
+// Node coordinates [3][n3] of element e at degree N: the degree-Ngeo
+// interpolant of the box map evaluated at the degree-N Gauss-Lobatto nodes.
+void element_nodes(const hs3d_pmesh *pm, int e, int N, double *X)
+{
+    const int G = pm->Ngeo, ng = G + 1, n = N + 1, n3 = n * n * n;
+    const Ops &og = host_ops(G), &on = host_ops(N);
+    std::vector<double> Xg(3 * ng * ng * ng);
+    for (int k = 0; k < ng; ++k)
+        for (int j = 0; j < ng; ++j)
+            for (int i = 0; i < ng; ++i) {
+                const double r[3] = {og.xi[i], og.xi[j], og.xi[k]};
+                double x[3];
+                box_point(pm, e, r, x);
+                for (int c = 0; c < 3; ++c) Xg[(size_t)c * ng * ng * ng + i + ng * (j + ng * k)] = x[c];
+            }
+    double L[kMaxn][kMaxn];
+    for (int t = 0; t < n; ++t) lagrange_row(ng, og.xi, on.xi[t], L[t]);
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    double acc = 0.0;
+                    for (int kk = 0; kk < ng; ++kk)
+                        for (int jj = 0; jj < ng; ++jj)
+                            for (int ii = 0; ii < ng; ++ii)
+                                acc += L[k][kk] * L[j][jj] * L[i][ii] *
+                                       Xg[(size_t)c * ng * ng * ng + ii + ng * (jj + ng * kk)];
+                    X[(size_t)c * n3 + i + n * (j + n * k)] = acc;
+                }
+}
+
+hs3d_status pmesh_build(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmesh **out)
+{
+    if (!desc || !degree) return fail(HS3D_ERR_INVALID, "desc or degree is NULL");
+    if (desc->node_xyz) return fail(HS3D_ERR_UNSUPPORTED, "per-element degrees take no node_xyz");
+    if (desc->nodes != HS3D_NODES_LOBATTO)
+        return fail(HS3D_ERR_UNSUPPORTED, "per-element degrees need Gauss-Lobatto nodes");
+    if (desc->ex < 1 || desc->ey < 1 || desc->ez < 1) return fail(HS3D_ERR_INVALID, "element counts must be >= 1");
+    const long long E = (long long)desc->ex * desc->ey * desc->ez;
+    if (E > (1 << 26)) return fail(HS3D_ERR_UNSUPPORTED, "too many elements");
+    int Nmin = 99, Nmax = 0;
+    for (long long e = 0; e < E; ++e) {
+        if (degree[e] < 1 || degree[e] > kMaxN)
+            return fail(HS3D_ERR_UNSUPPORTED, "degree %d of element %lld outside 1..%d", degree[e], e, kMaxN);
+        Nmin = degree[e] < Nmin ? degree[e] : Nmin;
+        Nmax = degree[e] > Nmax ? degree[e] : Nmax;
+    }
+    hs3d_mesh_desc chk = *desc;
+    chk.N = Nmax;
+    hs3d_status st = validate_desc(&chk);
+    if (st != HS3D_OK) return st;
+    if (Nmin == 1 && desc->perturb_amp != 0.0)
+        return fail(HS3D_ERR_INVALID, "a degree-1 element allows only an affine map (perturb_amp = 0)");
+    hs3d_pmesh *pm = new (std::nothrow) hs3d_pmesh();
+    if (!pm) return fail(HS3D_ERR_NOMEM, "host allocation failed");
+    pm->ex = desc->ex;
+    pm->ey = desc->ey;
+    pm->ez = desc->ez;
+    pm->E = (int)E;
+    pm->Nmin = Nmin;
+    pm->Nmax = Nmax;
+    pm->Ngeo = Nmin / 2 >= 1 ? Nmin / 2 : 1;
+    for (int c = 0; c < 3; ++c) {
+        pm->lo[c] = desc->lo[c];
+        pm->hi[c] = desc->hi[c];
+    }
+    pm->amp = desc->perturb_amp;
+    pm->deg.assign(degree, degree + E);
+    pm->off.assign(E + 1, 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&pm->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        pmesh_free(pm);
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    // buckets in increasing degree
+    std::vector<int> bucket_of(E), local_of(E);
+    int64_t base = 0;
+    for (int N = 1; N <= kMaxN; ++N) {
+        std::vector<int> els;
+        for (int i = 0; i < pm->E; ++i)
+            if (pm->deg[i] == N) els.push_back(i);
+        if (els.empty()) continue;
+        const int n = N + 1, n2 = n * n, n3 = n2 * n;
+        hs3d_pmesh::Bucket bk;
+        bk.N = N;
+        bk.E = (int)els.size();
+        bk.base = base;
+        std::vector<double> X((size_t)bk.E * 3 * n3);
+        for (int l = 0; l < bk.E; ++l) {
+            element_nodes(pm, els[l], N, X.data() + (size_t)l * 3 * n3);
+            bucket_of[els[l]] = (int)pm->b.size();
+            local_of[els[l]] = l;
+            pm->off[els[l]] = base + (int64_t)l * 5 * n3;
+        }
+        hs3d_mesh_desc bd = *desc;
+        bd.ex = bk.E;
+        bd.ey = bd.ez = 1;
+        bd.N = N;
+        bd.node_xyz = X.data();
+        st = mesh_build(&bd, &bk.m);
+        if (st == HS3D_OK) {
+            e = cudaMalloc(&bk.fstar6, sizeof(double) * 6 * (size_t)bk.E * 5 * n2);
+            if (e == cudaSuccess) e = cudaMalloc(&bk.qhat6, sizeof(double) * 6 * (size_t)bk.E * 4 * n2);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                st = cuda_fail(e, "cudaMalloc of face blocks");
+            }
+        }
+        pm->b.push_back(bk);
+        if (st != HS3D_OK) {
+            pmesh_free(pm);
+            return st;
+        }
+        // the next bucket starts at a multiple of 160 doubles: 16-byte aligned
+        // for the bulk copies, and a multiple of 5 so that node offsets
+        // (state offset / 5) are whole
+        base += (int64_t)bk.E * 5 * n3;
+        base = (base + 159) / 160 * 160;
+    }
+    pm->off[E] = base;
+    // face and bucket tables
+    const int nb = (int)pm->b.size();
+    std::vector<MortarFace> faces(3 * (size_t)E);
+    for (int i = 0; i < pm->E; ++i) {
+        const int ab[3] = {i % pm->ex, (i / pm->ex) % pm->ey, i / (pm->ex * pm->ey)};
+        const int Ed[3] = {pm->ex, pm->ey, pm->ez};
+        for (int d = 0; d < 3; ++d) {
+            int c[3] = {ab[0], ab[1], ab[2]};
+            c[d] = (c[d] + 1) % Ed[d];
+            const int r = c[0] + pm->ex * (c[1] + pm->ey * c[2]);
+            faces[3 * (size_t)i + d] = MortarFace{bucket_of[i], local_of[i], bucket_of[r], local_of[r]};
+        }
+    }
+    std::vector<MortarSide> sides(nb);
+    std::vector<Clock *> clks(nb);
+    std::vector<int> nbn(nb);
+    for (int k = 0; k < nb; ++k) {
+        const auto &bk = pm->b[k];
+        sides[k] = MortarSide{bk.N, bk.E, (long long)bk.base, bk.m->uf, bk.m->grad, bk.m->Ja, bk.m->Jaf,
+                              bk.fstar6, bk.qhat6};
+        clks[k] = bk.m->clk;
+        nbn[k] = bk.N + 1;
+    }
+    e = cudaMalloc(&pm->faces, sizeof(MortarFace) * faces.size());
+    if (e == cudaSuccess) e = cudaMalloc(&pm->sides, sizeof(MortarSide) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&pm->clks, sizeof(Clock *) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&pm->nb_n, sizeof(int) * nb);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pm->faces, faces.data(), sizeof(MortarFace) * faces.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pm->sides, sides.data(), sizeof(MortarSide) * nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pm->clks, clks.data(), sizeof(Clock *) * nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pm->nb_n, nbn.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !device_mortar_ops()) e = cudaErrorMemoryAllocation;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        pmesh_free(pm);
+        return cuda_fail(e, "mortar tables");
+    }
+    *out = pm;
+    return HS3D_OK;
+}
+
+// Items of every bucket for state u (and g / dudt), on the face6 path.
+std::vector<Batch> bucket_batches(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const double *u, double *g,
+                                  double *out, bool with_clock)
+{
+    std::vector<Batch> v;
+    for (const auto &bk : pm->b) {
+        Item it = make_item(bk.m, c, u + bk.base, g ? g + bk.base : nullptr, out ? out + bk.base : nullptr);
+        it.face6 = 1;
+        it.fstar = bk.fstar6;
+        it.qhat6 = bk.qhat6;
+        if (!with_clock) it.clk = nullptr;
+        v.push_back(single_batch(it));
+    }
+    return v;
+}
+
+MortarPhys<double> mortar_phys(const hs3d_pmesh *pm, const hs3d_solver_cfg *c)
+{
+    const Item it = make_item(pm->b[0].m, c, nullptr, nullptr, nullptr);
+    return MortarPhys<double>{it.gamma, it.gm1, it.hg, it.mu, it.kappa};
+}
+
+// One residual evaluation or RK stage over all buckets.
+cudaError_t p_stage(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const std::vector<Batch> &bb, const double *u,
+                    int stage, int lam_slot, cudaStream_t s)
+{
+    const MortarPhys<double> P = mortar_phys(pm, c);
+    const int nf = 3 * pm->E;
+    cudaError_t e = cudaSuccess;
+    if (c->physics == HS3D_NS) {
+        e = launch_mortar(c->precision, c->physics, 0, c->surface_flux, pm->faces, nf, pm->sides, u, P, s);
+        for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) e = launch_grad(pm->b[k].N, c->precision, bb[k], s);
+    }
+    if (e == cudaSuccess) e = launch_mortar(c->precision, c->physics, 1, c->surface_flux, pm->faces, nf, pm->sides, u, P, s);
+    for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k)
+        e = launch_volume(pm->b[k].N, c->precision, c->physics, c->volume_form, c->time_scheme, bb[k], stage, lam_slot, s);
+    return e;
+}
+
+// One step: dt from clock slot `slot` (filled by a fresh pass over u when
+// fresh != 0), then the stages; the last stage refills slot 1.
+cudaError_t p_step(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, double *u, double *g, double dt, bool fresh,
+                   cudaStream_t s)
+{
+    std::vector<Batch> bb = bucket_batches(pm, c, u, g, nullptr, true);
+    cudaError_t e = cudaSuccess;
+    if (fresh) {
+        for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) {
+            if (!(dt > 0.0)) e = launch_lambda(pm->b[k].N, c->precision, c->physics, bb[k], 0, s);
+            else if (c->precision != HS3D_FP64) e = launch_shadow(pm->b[k].N, bb[k], s);
+        }
+    }
+    if (e == cudaSuccess)
+        e = launch_pdt_finalize(pm->clks, pm->nb_n, (int)pm->b.size(), c->cfl, 8.0, 12.0, fresh ? 0 : 1,
+                                dt > 0.0 ? dt : 0.0, s);
+    const int ns = rk_stages(c->time_scheme);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) e = p_stage(pm, c, bb, u, k, k == ns - 1 ? 1 : -1, s);
+    return e;
+}
+
+hs3d_status p_check(const hs3d_pmesh *pm, const hs3d_solver_cfg *c)
+{
+    if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
+    return validate_cfg(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+hs3d_status hs3d_pmesh_create(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmesh **out)
+{
+    if (!out) return fail(HS3D_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    return pmesh_build(desc, degree, out);
+}
+
+void hs3d_pmesh_destroy(hs3d_pmesh *pm) { pmesh_free(pm); }
+
+hs3d_status hs3d_pmesh_layout(const hs3d_pmesh *pm, int64_t *offset, int *Ngeo)
+{
+    if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
+    if (offset) memcpy(offset, pm->off.data(), sizeof(int64_t) * (pm->E + 1));
+    if (Ngeo) *Ngeo = pm->Ngeo;
+    return HS3D_OK;
+}
+
+hs3d_status hs3d_pmesh_geometry(const hs3d_pmesh *pm, double *X, double *J, void *stream)
+{
+    if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (const auto &bk : pm->b) {
+        const size_t en = (size_t)bk.E * bk.m->n3;
+        const size_t nb = (size_t)bk.base / 5;   // node offset of the bucket (bases are multiples of 5)
+        if (X && e == cudaSuccess)
+            e = cudaMemcpyAsync(X + 3 * nb, bk.m->X, sizeof(double) * 3 * en, cudaMemcpyDeviceToDevice, s);
+        if (J && e == cudaSuccess) e = cudaMemcpyAsync(J + nb, bk.m->J, sizeof(double) * en, cudaMemcpyDeviceToDevice, s);
+    }
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "geometry copy");
+}
+
+hs3d_status hs3d_pmesh_init_state(const hs3d_pmesh *pm, const hs3d_ic *ic, double *u, void *stream)
+{
+    if (!pm || !ic) return fail(HS3D_ERR_INVALID, "pmesh or ic is NULL");
+    hs3d_status st = check_ptr(u, "u");
+    for (size_t k = 0; k < pm->b.size() && st == HS3D_OK; ++k)
+        st = hs3d_init_state(pm->b[k].m, ic, u + pm->b[k].base, stream);
+    return st;
+}
+
+hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const double *u, double *dudt,
+                                void *stream)
+{
+    hs3d_status st = p_check(pm, c);
+    if (st == HS3D_OK) st = check_ptr(u, "u");
+    if (st == HS3D_OK) st = check_ptr(dudt, "dudt");
+    if (st != HS3D_OK) return st;
+    if ((const void *)u == (const void *)dudt) return fail(HS3D_ERR_INVALID, "u and dudt must differ");
+    hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
+    std::lock_guard<std::mutex> lock(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Batch> bb = bucket_batches(pm, c, u, nullptr, dudt, false);
+    cudaError_t e = cudaSuccess;
+    if (c->precision != HS3D_FP64)
+        for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) e = launch_shadow(pm->b[k].N, bb[k], s);
+    if (e == cudaSuccess) e = p_stage(pm, c, bb, u, -1, -1, s);
+    m->gu = nullptr;   // the shadow no longer holds the state a run left
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
+}
+
+hs3d_status hs3d_pmesh_run(const hs3d_pmesh *pmc, const hs3d_solver_cfg *c, double *u, double *g, double dt,
+                           int nsteps, void *stream)
+{
+    hs3d_status st = p_check(pmc, c);
+    if (st == HS3D_OK) st = check_ptr(u, "u");
+    if (st == HS3D_OK) st = check_ptr(g, "g");
+    if (st != HS3D_OK) return st;
+    if (u == g) return fail(HS3D_ERR_INVALID, "u and g must differ");
+    if (nsteps < 0) return fail(HS3D_ERR_INVALID, "nsteps < 0");
+    if (nsteps == 0) return HS3D_OK;
+    hs3d_pmesh *pm = const_cast<hs3d_pmesh *>(pmc);
+    std::lock_guard<std::mutex> lock(pm->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dt < 0.0) dt = 0.0;
+    cudaError_t e = cudaSuccess;
+    // the first step reads a fresh dt pass (or writes the FP32 shadow for a fixed dt)
+    e = p_step(pm, c, u, g, dt, true, s);
+    if (e != cudaSuccess || nsteps == 1) return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "step launch");
+    // the remaining steps replay one captured step that continues from clock slot 1
+    if (!(pm->gexec && pm->gu == u && pm->gg == g && pm->gdt == dt && same_cfg(pm->gcfg, *c))) {
+        if (pm->gexec) cudaGraphExecDestroy(pm->gexec);
+        pm->gexec = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(pm->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = p_step(pm, c, u, g, dt, false, pm->stream);
+            e = cudaStreamEndCapture(pm->stream, &graph);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&pm->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            pm->gexec = nullptr;
+            cudaGetLastError();
+            return cuda_fail(e, "graph capture");
+        }
+        pm->gu = u;
+        pm->gg = g;
+        pm->gdt = dt;
+        pm->gcfg = *c;
+    }
+    for (int k = 1; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(pm->gexec, s);
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");
+}
+
+hs3d_status hs3d_pmesh_clock(const hs3d_pmesh *pm, double *t, int64_t *steps, int reset, void *stream)
+{
+    if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
+    hs3d_status worst = HS3D_OK;
+    for (size_t k = 0; k < pm->b.size(); ++k) {
+        double tk = 0.0;
+        int64_t sk = 0;
+        hs3d_status st = hs3d_clock(pm->b[k].m, &tk, &sk, reset, stream);
+        if (st == HS3D_ERR_CUDA) return st;
+        if (st != HS3D_OK && worst == HS3D_OK) worst = st;
+        if (k == 0) {
+            if (t) *t = tk;
+            if (steps) *steps = sk;
+        }
+    }
+    return worst;   // (its message set by hs3d_clock)
+}
+
+}  // extern "C"

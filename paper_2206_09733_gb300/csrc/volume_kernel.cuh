@@ -60,6 +60,14 @@ constexpr int vol_smem_per_node()
     return is_standard(FORM) ? 15 : (16 + (NS ? 15 : 0));
 }
 
+// Index of the 5 n^2 face-flux block of face `slot` of element e: the +d
+// face's own block d E + e or the -d neighbour's d E + owner (conforming
+// mesh), or the element's own per-face block slot E + e (face6).
+__device__ __forceinline__ size_t face_block(const Item &it, int slot, int d, int owner, int e)
+{
+    return it.face6 ? (size_t)slot * it.E + e : (size_t)d * it.E + owner;
+}
+
 // Node with index `idx` along direction d on the line with tangential indices (ta, tb).
 template <int n>
 __device__ __forceinline__ int line_node(int d, int idx, int ta, int tb)
@@ -279,7 +287,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
                 for (int slot = 0; slot < 6; ++slot) {
                     const int d = slot >> 1;
                     const int owner = (slot & 1) ? e : nb.m[d];
-                    bulk_g2s(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, fb, bar);
+                    bulk_g2s(F6 + slot * 5 * n2, FS + face_block(it, slot, d, owner, e) * 5 * n2, fb, bar);
                 }
                 if (stage >= 0) {
                     double *mine = sRK + (size_t)le * RKW * n3;
@@ -295,7 +303,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
             for (int slot = 0; slot < 6; ++slot) {
                 const int d = slot >> 1;
                 const int owner = (slot & 1) ? e : nb.m[d];
-                cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
+                cp_async_block<R>(F6 + slot * 5 * n2, FS + face_block(it, slot, d, owner, e) * 5 * n2, 5 * n2, p, n3);
             }
         }
         if constexpr (STAGE_RK && !(STAGE_U && STAGE_G)) {
@@ -345,7 +353,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
             for (int slot = 0; slot < 6; ++slot) {
                 const int d = slot >> 1;
                 const int owner = (slot & 1) ? e : nb.m[d];
-                cp_async_block<R>(F6 + slot * 5 * n2, FS + ((size_t)d * it.E + owner) * 5 * n2, 5 * n2, p, n3);
+                cp_async_block<R>(F6 + slot * 5 * n2, FS + face_block(it, slot, d, owner, e) * 5 * n2, 5 * n2, p, n3);
             }
         }
         // contravariant fluxes at this node; for the split form the diagonal
