@@ -20,9 +20,10 @@
 //      receives the mortar values.
 // Equal degrees make every matrix the identity: the conforming face.
 //
-// One CTA of 64 threads per face, one thread per mortar point (N_M <= 7).
-// The per-bucket pointers live in a small device table (MortarSide); the
-// operators of every degree pair in MortarOps.
+// Faces are grouped by mortar degree; a CTA holds several faces of one
+// degree, one thread per mortar point.  The per-bucket pointers live in a
+// small device table (MortarSide); the operators of every degree pair in
+// MortarOps.
 #include <math.h>
 
 #include <mutex>
@@ -159,11 +160,15 @@ __device__ __forceinline__ Prim<R> mortar_prim(const R u[5], R gm1)
     else return prim_from_f((const float *)u, gm1);
 }
 
-// BR1 gradient variables q = (v1, v2, v3, T), T = p/rho.
+// BR1 gradient variables q = (v1, v2, v3, T), T = p/rho, of the state
+// u[0], u[stride], ..., u[4 stride].
 template <typename R>
-__device__ __forceinline__ void mortar_q(const R u[5], R gm1, R q[4])
+__device__ __forceinline__ void mortar_q(const R *u, R gm1, R q[4], int stride = 1)
 {
-    const Prim<R> w = mortar_prim(u, gm1);
+    R c[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) c[v] = u[v * stride];
+    const Prim<R> w = mortar_prim(c, gm1);
     q[0] = w.v1;
     q[1] = w.v2;
     q[2] = w.v3;
@@ -205,113 +210,153 @@ __device__ __forceinline__ int mortar_face_node(int n, int d, int end, int ta, i
 
 // ------------------------------------------------------------------ the face kernel
 
-// MODE 0: BR1 interface values, written as qhat = 2 q*_s - q_s (4 values) to
-//         each side's qhat6 block; MODE 1: face fluxes (5 values) to each
-//         side's fstar block (both oriented along +d).
-template <typename R, bool NS, int MODE>
-__global__ void __launch_bounds__(64) k_mortar(const MortarFace *__restrict__ faces, int nfaces,
-                                               const MortarSide *__restrict__ sides, const double *__restrict__ u,
-                                               const MortarOps *__restrict__ mo, int flux, MortarPhys<R> P)
-{
-    constexpr int NV = (MODE == 1 && NS) ? 17 : 5;   // traces per point: state (+ 12 gradients)
-    __shared__ R tr[2][NV][64];   // each side's traces on its own face points
-    __shared__ R mt[2][NV][64];   // the same at the mortar points
-    __shared__ R fm[5][64];       // the mortar result
-    const int f = blockIdx.x;
-    if (f >= nfaces) return;
-    const MortarFace F = faces[f];
-    const int d = f % 3;
-    const MortarSide &SL = sides[F.bL], &SR = sides[F.bR];
-    const int NL = SL.N, NR = SR.N, NM = NL > NR ? NL : NR;
-    const int nM = NM + 1;
-    const int t = threadIdx.x;
+// Faces are grouped by mortar degree NM (a template parameter): a CTA holds
+// FPC faces of P = (NM+1)^2 threads each, thread p of a face owning mortar
+// point (a, b) = (p mod (NM+1), p div (NM+1)).  Interpolation and projection
+// are separable: a first pass along the face's first direction, shared by
+// the face's threads through shared memory, then the second pass per point.
+//   MODE 0: BR1 interface values, written as qhat = 2 q*_s - q_s (4 values)
+//           to each side's qhat6 block;
+//   MODE 1: face fluxes (5 values) to each side's fstar block (both oriented
+//           along +d).
+template <typename R, bool NS, int MODE, int NM>
+struct MortarShape {
+    static constexpr int nM = NM + 1, P = nM * nM;
+    static constexpr int NV = (MODE == 1 && NS) ? 17 : 5;         // values per trace point
+    static constexpr int TARGET = sizeof(R) == 8 ? 64 : 128;      // threads per CTA aimed at
+    static constexpr int FPC = TARGET / P >= 1 ? TARGET / P : 1;  // faces per CTA
+    static constexpr int THREADS = FPC * P;
+    // shared values per face: two sides' traces, the first-pass buffer, the mortar result
+    static constexpr int PER_FACE = 2 * NV * P + NV * P + 5 * P;
+};
 
-    // 1. traces of both sides: L's +d face (index N_L along d), R's -d face (index 0)
+template <typename R, bool NS, int MODE, int NM>
+__global__ void __launch_bounds__(MortarShape<R, NS, MODE, NM>::THREADS)
+k_mortar(const MortarFace *__restrict__ faces, int nfaces, const MortarSide *__restrict__ sides,
+         const double *__restrict__ u, const MortarOps *__restrict__ mo, int flux, MortarPhys<R> Ph)
+{
+    using S = MortarShape<R, NS, MODE, NM>;
+    constexpr int nM = S::nM, P = S::P, NV = S::NV;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int q = threadIdx.x / P, p = threadIdx.x - q * P;
+    const int f = blockIdx.x * S::FPC + q;
+    const bool live = f < nfaces;
+    R *tr = (R *)smem_raw + (size_t)q * S::PER_FACE;   // [2][NV][P]
+    R *T = tr + 2 * NV * P;                            // [NV][P]
+    R *fm = T + NV * P;                                // [5][P]
+    const int a = p % nM, b = p / nM;
+    MortarFace F{};
+    int Nside[2] = {NM, NM};
+    if (live) {
+        F = faces[f];
+        Nside[0] = sides[F.bL].N;
+        Nside[1] = sides[F.bR].N;
+    }
+    const int d = F.d;
+
+    // 1. traces of both sides on their own face points: L's +d face, R's -d face
+    if (live) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const MortarSide &S = s ? SR : SL;
-        const int ns = S.N + 1, n3 = ns * ns * ns;
-        const int le = s ? F.lR : F.lL;
-        if (t < ns * ns) {
-            const int node = mortar_face_node(ns, d, s ? 0 : S.N, t % ns, t / ns);
-            if constexpr (sizeof(R) == 8) {
-                const double *src = u + S.base + (size_t)le * 5 * n3 + node;
+        for (int s = 0; s < 2; ++s) {
+            const MortarSide &SD = sides[s ? F.bR : F.bL];
+            const int ns = SD.N + 1, n3 = ns * ns * ns;
+            const int le = s ? F.lR : F.lL;
+            if (p < ns * ns) {
+                const int node = mortar_face_node(ns, d, s ? 0 : SD.N, p % ns, p / ns);
+                R *dst = tr + s * NV * P + p;
+                if constexpr (sizeof(R) == 8) {
+                    const double *src = u + SD.base + (size_t)le * 5 * n3 + node;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) tr[s][v][t] = src[(size_t)v * n3];
-            } else {
-                const float *src = S.uf + (size_t)le * 5 * n3 + node;
+                    for (int v = 0; v < 5; ++v) dst[v * P] = src[(size_t)v * n3];
+                } else {
+                    const float *src = SD.uf + (size_t)le * 5 * n3 + node;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) tr[s][v][t] = src[(size_t)v * n3];
-            }
-            if constexpr (MODE == 1 && NS) {
-                const R *G = (const R *)S.grad + (size_t)le * 12 * n3 + node;
+                    for (int v = 0; v < 5; ++v) dst[v * P] = src[(size_t)v * n3];
+                }
+                if constexpr (MODE == 1 && NS) {
+                    const R *G = (const R *)SD.grad + (size_t)le * 12 * n3 + node;
 #pragma unroll
-                for (int k = 0; k < 12; ++k) tr[s][5 + k][t] = G[(size_t)k * n3];
+                    for (int k = 0; k < 12; ++k) dst[(5 + k) * P] = G[(size_t)k * n3];
+                }
             }
         }
     }
     __syncthreads();
 
-    // 2. interpolation to the mortar points
-    if (t < nM * nM) {
-        const int a = t % nM, b = t / nM;
+    // 2. both sides at this thread's mortar point (registers)
+    R w[2][NV];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int Ns = s ? NR : NL, ns = Ns + 1;
-            if (Ns == NM) {
-                for (int v = 0; v < NV; ++v) mt[s][v][t] = tr[s][v][t];
-            } else {
-                const R *I = mo_interp<R>(mo, Ns, NM);
-                for (int v = 0; v < NV; ++v) {
-                    R acc = (R)0;
-                    for (int j = 0; j < ns; ++j) {
-                        R row = (R)0;
-                        for (int i = 0; i < ns; ++i) row += I[a * ns + i] * tr[s][v][i + ns * j];
-                        acc += I[b * ns + j] * row;
-                    }
-                    mt[s][v][t] = acc;
-                }
+    for (int s = 0; s < 2; ++s) {
+        const int Ns = Nside[s], ns = Ns + 1;
+        const R *src = tr + s * NV * P;
+        // (nM ns <= P entries: at most one per thread; loops unrolled to nM with
+        // the side's ns as a predicate)
+        if (Ns < NM && p < nM * ns) {
+            const R *I = mo_interp<R>(mo, Ns, NM);   // [nM][ns]
+            // first pass: T[v][a' + nM j] = sum_i I[a'][i] f[v][i + ns j]
+            const int ap = p % nM, j = p / nM;
+            R row[nM];
+#pragma unroll
+            for (int i = 0; i < nM; ++i) row[i] = i < ns ? I[ap * ns + i] : (R)0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R acc = (R)0;
+#pragma unroll
+                for (int i = 0; i < nM; ++i)
+                    if (i < ns) acc += row[i] * src[v * P + i + ns * j];
+                T[v * P + p] = acc;
             }
         }
-        // 3. the mortar function
-        R ul[5], ur[5];
+        __syncthreads();   // (uniform: every thread of the CTA reaches it for both sides)
+        if (Ns < NM) {
+            const R *I = mo_interp<R>(mo, Ns, NM);
+            R col[nM];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            ul[v] = mt[0][v][t];
-            ur[v] = mt[1][v][t];
+            for (int j = 0; j < nM; ++j) col[j] = j < ns ? I[b * ns + j] : (R)0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R acc = (R)0;
+#pragma unroll
+                for (int j = 0; j < nM; ++j)
+                    if (j < ns) acc += col[j] * T[v * P + a + nM * j];
+                w[s][v] = acc;
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) w[s][v] = src[v * P + p];
         }
+        __syncthreads();   // T is reused by the other side
+    }
+
+    // 3. the mortar function at this point
+    if (live) {
         if constexpr (MODE == 0) {
             R qL[4], qR[4];
-            mortar_q(ul, P.gm1, qL);
-            mortar_q(ur, P.gm1, qR);
+            mortar_q(w[0], Ph.gm1, qL);
+            mortar_q(w[1], Ph.gm1, qR);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) fm[v][t] = (R)0.5 * (qL[v] + qR[v]);
+            for (int v = 0; v < 4; ++v) fm[v * P + p] = (R)0.5 * (qL[v] + qR[v]);
         } else {
-            // face metric of the side of degree N_M (L on a tie): its own face point t
-            const bool useL = NL >= NR;
-            const MortarSide &H = useL ? SL : SR;
-            const int nh = H.N + 1, n3h = nh * nh * nh;
-            const int node = mortar_face_node(nh, d, useL ? H.N : 0, a, b);
+            // face metric of the side of degree NM (L on a tie), at its own face point (a, b)
+            const bool useL = Nside[0] >= Nside[1];
+            const MortarSide &H = sides[useL ? F.bL : F.bR];
+            const int n3h = nM * nM * nM;
+            const int node = mortar_face_node(nM, d, useL ? NM : 0, a, b);
             const R *JA = (const R *)(sizeof(R) == 8 ? (const void *)H.Ja : (const void *)H.Jaf) +
                           ((size_t)(useL ? F.lL : F.lR) * 9 + d * 3) * n3h + node;
             const R s1 = JA[0], s2 = JA[n3h], s3 = JA[2 * (size_t)n3h];
             R fs[5];
-            mortar_riemann<R>(flux, ul, ur, P, s1, s2, s3, fs);
+            mortar_riemann<R>(flux, w[0], w[1], Ph, s1, s2, s3, fs);
             if constexpr (NS) {
-                R gl[12], gr[12], fl[5], fr[5];
-#pragma unroll
-                for (int k = 0; k < 12; ++k) {
-                    gl[k] = mt[0][5 + k][t];
-                    gr[k] = mt[1][5 + k][t];
-                }
-                const Prim<R> pL = mortar_prim(ul, P.gm1), pR = mortar_prim(ur, P.gm1);
-                visc_flux(pL, gl, P.mu, P.kappa, s1, s2, s3, fl);
-                visc_flux(pR, gr, P.mu, P.kappa, s1, s2, s3, fr);
+                R fl[5], fr[5];
+                const Prim<R> pL = mortar_prim(w[0], Ph.gm1), pR = mortar_prim(w[1], Ph.gm1);
+                visc_flux(pL, &w[0][5], Ph.mu, Ph.kappa, s1, s2, s3, fl);
+                visc_flux(pR, &w[1][5], Ph.mu, Ph.kappa, s1, s2, s3, fr);
 #pragma unroll
                 for (int v = 1; v < 5; ++v) fs[v] -= (R)0.5 * (fl[v] + fr[v]);
             }
 #pragma unroll
-            for (int v = 0; v < 5; ++v) fm[v][t] = fs[v];
+            for (int v = 0; v < 5; ++v) fm[v * P + p] = fs[v];
         }
     }
     __syncthreads();
@@ -320,63 +365,108 @@ __global__ void __launch_bounds__(64) k_mortar(const MortarFace *__restrict__ fa
     constexpr int NOUT = MODE == 0 ? 4 : 5;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const MortarSide &S = s ? SR : SL;
-        const int Ns = S.N, ns = Ns + 1, n2 = ns * ns;
-        if (t >= n2) continue;
-        const int a = t % ns, b = t / ns;
-        R val[5];
-        if (Ns == NM) {
+        const int Ns = Nside[s], ns = Ns + 1, n2 = ns * ns;
+        if (Ns < NM && p < ns * nM) {
+            const R *Pr = mo_proj<R>(mo, Ns, NM);   // [ns][nM]
+            // first pass: T[v][a' + ns j] = sum_i Pr[a'][i] fm[v][i + nM j]
+            const int ap = p % ns, j = p / ns;
+            R row[nM];
 #pragma unroll
-            for (int v = 0; v < NOUT; ++v) val[v] = fm[v][t];
-        } else {
-            const R *Pr = mo_proj<R>(mo, Ns, NM);
+            for (int i = 0; i < nM; ++i) row[i] = Pr[ap * nM + i];
 #pragma unroll
             for (int v = 0; v < NOUT; ++v) {
                 R acc = (R)0;
-                for (int j = 0; j < nM; ++j) {
-                    R row = (R)0;
-                    for (int i = 0; i < nM; ++i) row += Pr[a * nM + i] * fm[v][i + nM * j];
-                    acc += Pr[b * nM + j] * row;
-                }
-                val[v] = acc;
+#pragma unroll
+                for (int i = 0; i < nM; ++i) acc += row[i] * fm[v * P + i + nM * j];
+                T[v * P + p] = acc;
             }
         }
-        const int slot = s ? 2 * d : 2 * d + 1;
-        const int le = s ? F.lR : F.lL;
-        if constexpr (MODE == 0) {
-            R uin[5], qin[4];
+        __syncthreads();
+        if (live && p < n2) {
+            const int ap = p % ns, bp = p / ns;
+            R val[5];
+            if (Ns < NM) {
+                const R *Pr = mo_proj<R>(mo, Ns, NM);
+                R col[nM];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) uin[v] = tr[s][v][t];
-            mortar_q(uin, P.gm1, qin);
-            R *dst = (R *)S.qhat6 + ((size_t)slot * S.E + le) * 4 * n2 + t;
+                for (int j = 0; j < nM; ++j) col[j] = Pr[bp * nM + j];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) dst[v * n2] = (R)2 * val[v] - qin[v];
-        } else {
-            R *dst = (R *)S.fstar6 + ((size_t)slot * S.E + le) * 5 * n2 + t;
+                for (int v = 0; v < NOUT; ++v) {
+                    R acc = (R)0;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) dst[v * n2] = val[v];
+                    for (int j = 0; j < nM; ++j) acc += col[j] * T[v * P + ap + ns * j];
+                    val[v] = acc;
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NOUT; ++v) val[v] = fm[v * P + p];
+            }
+            const MortarSide &SD = sides[s ? F.bR : F.bL];
+            const int slot = s ? 2 * d : 2 * d + 1;
+            const int le = s ? F.lR : F.lL;
+            if constexpr (MODE == 0) {
+                R qin[4];
+                mortar_q(tr + s * NV * P + p, Ph.gm1, qin, P);
+                R *dst = (R *)SD.qhat6 + ((size_t)slot * SD.E + le) * 4 * n2 + p;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) dst[v * n2] = (R)2 * val[v] - qin[v];
+            } else {
+                R *dst = (R *)SD.fstar6 + ((size_t)slot * SD.E + le) * 5 * n2 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) dst[v * n2] = val[v];
+            }
         }
+        __syncthreads();   // T is reused by the other side
     }
 }
 
-cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, int nfaces,
+template <typename R, bool NS, int MODE, int NM>
+static cudaError_t mortar_group(const MortarFace *faces, int nfaces, const MortarSide *sides, const double *u,
+                                const MortarOps *mo, int flux, const MortarPhys<R> &P, cudaStream_t s)
+{
+    using S = MortarShape<R, NS, MODE, NM>;
+    const size_t smem = sizeof(R) * (size_t)S::FPC * S::PER_FACE;
+    static bool attr = false;   // (idempotent; raced writes store the same value)
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mortar<R, NS, MODE, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const unsigned blocks = (unsigned)((nfaces + S::FPC - 1) / S::FPC);
+    k_mortar<R, NS, MODE, NM><<<blocks, S::THREADS, smem, s>>>(faces, nfaces, sides, u, mo, flux, P);
+    return cudaGetLastError();
+}
+
+template <typename R, bool NS, int MODE>
+static cudaError_t mortar_mode(const MortarFace *faces, const int *group_begin, const MortarSide *sides,
+                               const double *u, const MortarOps *mo, int flux, const MortarPhys<R> &P, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+#define HS3D_MG(K)                                                                                                \
+    if (e == cudaSuccess && group_begin[K + 1] > group_begin[K])                                                  \
+        e = mortar_group<R, NS, MODE, K>(faces + group_begin[K], group_begin[K + 1] - group_begin[K], sides, u, mo, \
+                                         flux, P, s);
+    HS3D_MG(1) HS3D_MG(2) HS3D_MG(3) HS3D_MG(4) HS3D_MG(5) HS3D_MG(6) HS3D_MG(7)
+#undef HS3D_MG
+    return e;
+}
+
+cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, const int *group_begin,
                           const MortarSide *sides, const double *u, const MortarPhys<double> &P, cudaStream_t s)
 {
-    if (nfaces == 0) return cudaSuccess;
     const MortarOps *mo = device_mortar_ops();
     if (!mo) return cudaErrorMemoryAllocation;
     const bool ns = physics == HS3D_NS;
     if (prec == HS3D_FP64) {
-        if (mode == 0) k_mortar<double, true, 0><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, P);
-        else if (ns) k_mortar<double, true, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, P);
-        else k_mortar<double, false, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, P);
-    } else {
-        const MortarPhys<float> Pf{(float)P.gamma, (float)P.gm1, (float)P.hg, (float)P.mu, (float)P.kappa};
-        if (mode == 0) k_mortar<float, true, 0><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, Pf);
-        else if (ns) k_mortar<float, true, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, Pf);
-        else k_mortar<float, false, 1><<<nfaces, 64, 0, s>>>(faces, nfaces, sides, u, mo, flux, Pf);
+        if (mode == 0) return mortar_mode<double, true, 0>(faces, group_begin, sides, u, mo, flux, P, s);
+        if (ns) return mortar_mode<double, true, 1>(faces, group_begin, sides, u, mo, flux, P, s);
+        return mortar_mode<double, false, 1>(faces, group_begin, sides, u, mo, flux, P, s);
     }
-    return cudaGetLastError();
+    const MortarPhys<float> Pf{(float)P.gamma, (float)P.gm1, (float)P.hg, (float)P.mu, (float)P.kappa};
+    if (mode == 0) return mortar_mode<float, true, 0>(faces, group_begin, sides, u, mo, flux, Pf, s);
+    if (ns) return mortar_mode<float, true, 1>(faces, group_begin, sides, u, mo, flux, Pf, s);
+    return mortar_mode<float, false, 1>(faces, group_begin, sides, u, mo, flux, Pf, s);
 }
 
 // ------------------------------------------------------------------ time step

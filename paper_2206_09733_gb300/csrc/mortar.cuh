@@ -21,11 +21,11 @@ struct MortarOps {
 const MortarOps &host_mortar_ops();
 const MortarOps *device_mortar_ops();
 
-// One face of a mesh with per-element degrees: face f = 3 e + d is the +d
-// face of element e (bucket bL, index lL within it) shared with its +d
-// neighbour (bucket bR, index lR).
+// One face of a mesh with per-element degrees: the +d face of an element
+// (bucket bL, index lL within it) shared with its +d neighbour (bucket bR,
+// index lR).  The face table is sorted by mortar degree max(N_L, N_R).
 struct MortarFace {
-    int bL, lL, bR, lR;
+    int bL, lL, bR, lR, d;
 };
 
 // One degree bucket as the face kernel sees it.
@@ -45,8 +45,10 @@ struct MortarPhys {
     R gamma, gm1, hg, mu, kappa;
 };
 
-// mode 0: BR1 interface values; mode 1: face fluxes.
-cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, int nfaces,
+// mode 0: BR1 interface values; mode 1: face fluxes.  group_begin (HOST,
+// kMaxn + 1 ints): faces of mortar degree NM are faces[group_begin[NM] ..
+// group_begin[NM + 1]).
+cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, const int *group_begin,
                           const MortarSide *sides, const double *u, const MortarPhys<double> &P, cudaStream_t s);
 cudaError_t launch_pdt_finalize(Clock *const *clks, const int *nb_n, int nb, double cfl, double kc, double kv,
                                 int slot, double dt_fixed, cudaStream_t s);

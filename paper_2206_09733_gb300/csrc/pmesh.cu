@@ -44,7 +44,8 @@ struct hs3d_pmesh {
         void *fstar6 = nullptr, *qhat6 = nullptr;
     };
     std::vector<Bucket> b;
-    MortarFace *faces = nullptr;   // device [3E]
+    MortarFace *faces = nullptr;   // device [3E], sorted by mortar degree
+    int group_begin[kMaxn + 1] = {0};   // faces of mortar degree NM: [group_begin[NM], group_begin[NM + 1])
     MortarSide *sides = nullptr;   // device [nb]
     Clock **clks = nullptr;        // device [nb]
     int *nb_n = nullptr;           // device [nb]
@@ -221,7 +222,8 @@ hs3d_status pmesh_build(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmes
     pm->off[E] = base;
     // face and bucket tables
     const int nb = (int)pm->b.size();
-    std::vector<MortarFace> faces(3 * (size_t)E);
+    // faces grouped by mortar degree (element-major within a group)
+    std::vector<MortarFace> by_deg[kMaxn];
     for (int i = 0; i < pm->E; ++i) {
         const int ab[3] = {i % pm->ex, (i / pm->ex) % pm->ey, i / (pm->ex * pm->ey)};
         const int Ed[3] = {pm->ex, pm->ey, pm->ez};
@@ -229,9 +231,16 @@ hs3d_status pmesh_build(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmes
             int c[3] = {ab[0], ab[1], ab[2]};
             c[d] = (c[d] + 1) % Ed[d];
             const int r = c[0] + pm->ex * (c[1] + pm->ey * c[2]);
-            faces[3 * (size_t)i + d] = MortarFace{bucket_of[i], local_of[i], bucket_of[r], local_of[r]};
+            const int NM = pm->deg[i] > pm->deg[r] ? pm->deg[i] : pm->deg[r];
+            by_deg[NM].push_back(MortarFace{bucket_of[i], local_of[i], bucket_of[r], local_of[r], d});
         }
     }
+    std::vector<MortarFace> faces;
+    for (int NM = 0; NM < kMaxn; ++NM) {
+        pm->group_begin[NM] = (int)faces.size();
+        faces.insert(faces.end(), by_deg[NM].begin(), by_deg[NM].end());
+    }
+    pm->group_begin[kMaxn] = (int)faces.size();
     std::vector<MortarSide> sides(nb);
     std::vector<Clock *> clks(nb);
     std::vector<int> nbn(nb);
@@ -288,13 +297,13 @@ cudaError_t p_stage(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const std::v
                     int stage, int lam_slot, cudaStream_t s)
 {
     const MortarPhys<double> P = mortar_phys(pm, c);
-    const int nf = 3 * pm->E;
+    const int *gb = pm->group_begin;
     cudaError_t e = cudaSuccess;
     if (c->physics == HS3D_NS) {
-        e = launch_mortar(c->precision, c->physics, 0, c->surface_flux, pm->faces, nf, pm->sides, u, P, s);
+        e = launch_mortar(c->precision, c->physics, 0, c->surface_flux, pm->faces, gb, pm->sides, u, P, s);
         for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) e = launch_grad(pm->b[k].N, c->precision, bb[k], s);
     }
-    if (e == cudaSuccess) e = launch_mortar(c->precision, c->physics, 1, c->surface_flux, pm->faces, nf, pm->sides, u, P, s);
+    if (e == cudaSuccess) e = launch_mortar(c->precision, c->physics, 1, c->surface_flux, pm->faces, gb, pm->sides, u, P, s);
     for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k)
         e = launch_volume(pm->b[k].N, c->precision, c->physics, c->volume_form, c->time_scheme, bb[k], stage, lam_slot, s);
     return e;
