@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--volume", default=None, help="profiling runs: volume form (default ec)")
     ap.add_argument("--physics", default=None, choices=["euler", "ns"], help="profiling runs: equations (default ns)")
     ap.add_argument("--surface", default=None, help="profiling runs: surface flux (default roe)")
+    ap.add_argument("--pmesh-profile", type=int, default=0, metavar="E",
+                    help="profiling run only: 3 mixed RK3 steps of the E^3 TGV with per-element degrees 2..5 "
+                         "(NS, EC + Roe), then exit")
     args = ap.parse_args()
     if any(x is not None for x in (args.order, args.volume, args.physics, args.surface)) and not args.only:
         ap.error("--order, --volume, --physics and --surface select a profiling case: give --only too")
@@ -880,8 +883,29 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def pmesh_profile(E):
+    """The p-mesh kernels alone, for an ncu launch list or capture: mesh set-up,
+    one initial condition and 3 mixed RK3 steps (per stage 4 + 4 mortar
+    launches, one gradient and one element kernel per degree)."""
+    import numpy as np
+    import torch
+
+    import paper_2206_09733_gb300 as hs
+    deg = np.random.default_rng(7).integers(2, 6, size=E ** 3).astype(np.int32)
+    pm = hs.PMesh(E, E, E, deg, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=AMP)
+    cfg = hs.solver_cfg("ns", "roe", "ec", "mixed32", gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+    u = pm.init_state(pm.empty_state(), "tgv", GAMMA, MA)
+    g = torch.zeros_like(u)
+    pm.run(cfg, u, g, 3)
+    torch.cuda.synchronize()
+    print(json.dumps({"pmesh_profile": E, "clock": pm.clock()}))
+
+
 def main():
     args = parse()
+    if args.pmesh_profile:
+        pmesh_profile(args.pmesh_profile)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
