@@ -228,10 +228,17 @@ struct MortarShape {
     static constexpr int THREADS = FPC * P;
     // shared values per face: two sides' traces, the first-pass buffer, the mortar result
     static constexpr int PER_FACE = 2 * NV * P + NV * P + 5 * P;
+    // resident CTAs per SM asked of the register allocator (FP32): 8 (64
+    // registers) where that spills nothing, 6 for the viscous flux, whose
+    // two sides' state and gradients (34 values) are live at once
+    // (measured at 32^3, degrees 2..5: 0.6% faster than no cap; asking for
+    // the maximum shared-memory carveout as well made the step 6% slower --
+    // the trace gathers go through L1)
+    static constexpr int MIN_BLOCKS = sizeof(R) == 8 ? 1 : ((MODE == 1 && NS) ? 6 : 8);
 };
 
 template <typename R, bool NS, int MODE, int NM>
-__global__ void __launch_bounds__(MortarShape<R, NS, MODE, NM>::THREADS)
+__global__ void __launch_bounds__(MortarShape<R, NS, MODE, NM>::THREADS, MortarShape<R, NS, MODE, NM>::MIN_BLOCKS)
 k_mortar(const MortarFace *__restrict__ faces, int nfaces, const MortarSide *__restrict__ sides,
          const double *__restrict__ u, const MortarOps *__restrict__ mo, int flux, MortarPhys<R> Ph)
 {
