@@ -321,3 +321,62 @@ def test_16cubed_mixed_degrees_fp64():
     r = torch.zeros_like(ud)
     gm.residual(gc, ud, r)
     assert rel(to_host(om, gm, r), ref) <= TOL64
+
+
+# ------------------------------------------------------------------ the benchmark's own configuration
+
+@pytest.fixture(scope="module")
+def bench_pmesh():
+    """The 32^3 mesh of degrees 2..5 (numpy default_rng(7)) and curvature bench.py times."""
+    deg = np.random.default_rng(7).integers(2, 6, size=32 ** 3).astype(np.int32)
+    return deg, hs.PMesh(32, 32, 32, deg, *PI3, amp=0.05)
+
+
+def _weights(N):
+    _, w = O.lgl(N)
+    return w[None, None, :] * w[None, :, None] * w[:, None, None]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed32"])
+def test_bench_configuration_free_stream(bench_pmesh, precision):
+    deg, gm = bench_pmesh
+    gc = hs.solver_cfg("ns", "roe", "ec", precision, gamma=G, Re=1600.0)
+    u = torch.zeros(gm.size, dtype=torch.float64, device="cuda")
+    st = torch.tensor([1.1, 0.33, -0.22, 0.11, 0.9 / (G - 1) + 0.5 * 1.1 * 0.14], dtype=torch.float64, device="cuda")
+    for N in range(2, 6):
+        els = np.nonzero(deg == N)[0]
+        n3 = (N + 1) ** 3
+        o0 = int(gm.offset[els[0]])
+        u[o0:o0 + len(els) * 5 * n3].view(len(els), 5, n3)[:] = st[None, :, None]
+    r = torch.zeros_like(u)
+    gm.residual(gc, u, r)
+    _, J = gm.geometry()
+    torch.cuda.synchronize()
+    worst = float(r.abs().max())
+    # du/dt = -(V + S)/J: the rounding of V + S (the small meshes' 2e-14 n^4 at J ~ 1) is
+    # amplified by 1/J (~1/0.0009 here); the oracle itself leaves 6.8e-9 on this mesh (the
+    # conforming N = 3 oracle 3.7e-10), a face-metric mismatch would leave O(0.1)
+    inv_j = 1.0 / float(J[J != 0].min())
+    assert worst < (2e-14 * 6 ** 4 * inv_j if precision == "fp64" else 2e-5 * 36), worst
+
+
+def test_bench_configuration_conservation(bench_pmesh):
+    deg, gm = bench_pmesh
+    gc = hs.solver_cfg("ns", "roe", "ec", "fp64", gamma=G, Re=1600.0)
+    u = gm.init_state(torch.zeros(gm.size, dtype=torch.float64, device="cuda"), "tgv", G, 0.3)
+    r = torch.zeros_like(u)
+    gm.residual(gc, u, r)
+    _, J = gm.geometry()
+    torch.cuda.synchronize()
+    tot = np.zeros(5)
+    mag = np.zeros(5)
+    for N in range(2, 6):
+        els = np.nonzero(deg == N)[0]
+        n = N + 1
+        o0 = int(gm.offset[els[0]])
+        R = r[o0:o0 + len(els) * 5 * n ** 3].view(len(els), 5, n, n, n).cpu().numpy()
+        Jb = J[o0 // 5:o0 // 5 + len(els) * n ** 3].view(len(els), 1, n, n, n).cpu().numpy()
+        W = Jb * _weights(N)[None, None]
+        tot += (R * W).sum(axis=(0, 2, 3, 4))
+        mag += np.abs(R * W).sum(axis=(0, 2, 3, 4))
+    assert np.all(np.abs(tot) <= 1e-12 * mag.max()), (tot, mag)
