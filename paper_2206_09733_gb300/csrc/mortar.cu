@@ -223,7 +223,7 @@ template <typename R, bool NS, int MODE, int NM>
 struct MortarShape {
     static constexpr int nM = NM + 1, P = nM * nM;
     static constexpr int NV = (MODE == 1 && NS) ? 17 : 5;         // values per trace point
-    static constexpr int TARGET = sizeof(R) == 8 ? 64 : 128;      // threads per CTA aimed at
+    static constexpr int TARGET = 128;                             // threads per CTA aimed at
     static constexpr int FPC = TARGET / P >= 1 ? TARGET / P : 1;  // faces per CTA
     static constexpr int THREADS = FPC * P;
     // shared values per face: two sides' traces, the first-pass buffer, the mortar result

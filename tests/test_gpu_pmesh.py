@@ -172,6 +172,19 @@ def test_two_elements_of_different_degree_neighbouring_twice():
         assert rel(to_host(om, gm, r), ref) <= TOL64
 
 
+@pytest.mark.parametrize("N", [1, 4, 7])
+def test_single_element_is_its_own_neighbour(N):
+    om, gm = pair(1, 1, 1, [N], lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0)
+    for phys, surf, vol in [("euler", "rusanov", "standard"), ("ns", "roe", "ec")]:
+        oc, gc = cfgs(phys, surf, vol)
+        u = I.random_state_blocks([N], seed=59, smooth=True)
+        ref = om.residual(oc, u)
+        ud = to_dev(om, gm, u)
+        r = torch.zeros_like(ud)
+        gm.residual(gc, ud, r)
+        assert rel(to_host(om, gm, r), ref) <= TOL64
+
+
 def test_equal_degrees_match_the_conforming_gpu_path():
     """All degrees equal and an affine box: the p-mesh is the conforming mesh
     (same geometry), so both GPU paths must agree."""
