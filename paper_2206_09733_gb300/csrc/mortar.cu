@@ -446,12 +446,12 @@ static cudaError_t mortar_group(const MortarFace *faces, int nfaces, const Morta
 }
 
 template <typename R, bool NS, int MODE>
-static cudaError_t mortar_mode(const MortarFace *faces, const int *group_begin, const MortarSide *sides,
+static cudaError_t mortar_mode(const MortarFace *faces, const int *group_begin, int only, const MortarSide *sides,
                                const double *u, const MortarOps *mo, int flux, const MortarPhys<R> &P, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
 #define HS3D_MG(K)                                                                                                \
-    if (e == cudaSuccess && group_begin[K + 1] > group_begin[K])                                                  \
+    if (e == cudaSuccess && (only < 0 || only == K) && group_begin[K + 1] > group_begin[K])                       \
         e = mortar_group<R, NS, MODE, K>(faces + group_begin[K], group_begin[K + 1] - group_begin[K], sides, u, mo, \
                                          flux, P, s);
     HS3D_MG(1) HS3D_MG(2) HS3D_MG(3) HS3D_MG(4) HS3D_MG(5) HS3D_MG(6) HS3D_MG(7)
@@ -460,20 +460,21 @@ static cudaError_t mortar_mode(const MortarFace *faces, const int *group_begin, 
 }
 
 cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, const int *group_begin,
-                          const MortarSide *sides, const double *u, const MortarPhys<double> &P, cudaStream_t s)
+                          int only, const MortarSide *sides, const double *u, const MortarPhys<double> &P,
+                          cudaStream_t s)
 {
     const MortarOps *mo = device_mortar_ops();
     if (!mo) return cudaErrorMemoryAllocation;
     const bool ns = physics == HS3D_NS;
     if (prec == HS3D_FP64) {
-        if (mode == 0) return mortar_mode<double, true, 0>(faces, group_begin, sides, u, mo, flux, P, s);
-        if (ns) return mortar_mode<double, true, 1>(faces, group_begin, sides, u, mo, flux, P, s);
-        return mortar_mode<double, false, 1>(faces, group_begin, sides, u, mo, flux, P, s);
+        if (mode == 0) return mortar_mode<double, true, 0>(faces, group_begin, only, sides, u, mo, flux, P, s);
+        if (ns) return mortar_mode<double, true, 1>(faces, group_begin, only, sides, u, mo, flux, P, s);
+        return mortar_mode<double, false, 1>(faces, group_begin, only, sides, u, mo, flux, P, s);
     }
     const MortarPhys<float> Pf{(float)P.gamma, (float)P.gm1, (float)P.hg, (float)P.mu, (float)P.kappa};
-    if (mode == 0) return mortar_mode<float, true, 0>(faces, group_begin, sides, u, mo, flux, Pf, s);
-    if (ns) return mortar_mode<float, true, 1>(faces, group_begin, sides, u, mo, flux, Pf, s);
-    return mortar_mode<float, false, 1>(faces, group_begin, sides, u, mo, flux, Pf, s);
+    if (mode == 0) return mortar_mode<float, true, 0>(faces, group_begin, only, sides, u, mo, flux, Pf, s);
+    if (ns) return mortar_mode<float, true, 1>(faces, group_begin, only, sides, u, mo, flux, Pf, s);
+    return mortar_mode<float, false, 1>(faces, group_begin, only, sides, u, mo, flux, Pf, s);
 }
 
 // ------------------------------------------------------------------ time step

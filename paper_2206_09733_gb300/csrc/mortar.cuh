@@ -47,9 +47,11 @@ struct MortarPhys {
 
 // mode 0: BR1 interface values; mode 1: face fluxes.  group_begin (HOST,
 // kMaxn + 1 ints): faces of mortar degree NM are faces[group_begin[NM] ..
-// group_begin[NM + 1]).
+// group_begin[NM + 1]).  only >= 0: launch the group of that mortar degree
+// alone (else every non-empty group, in order).
 cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, const int *group_begin,
-                          const MortarSide *sides, const double *u, const MortarPhys<double> &P, cudaStream_t s);
+                          int only, const MortarSide *sides, const double *u, const MortarPhys<double> &P,
+                          cudaStream_t s);
 cudaError_t launch_pdt_finalize(Clock *const *clks, const int *nb_n, int nb, double cfl, double kc, double kv,
                                 int slot, double dt_fixed, cudaStream_t s);
 

@@ -50,6 +50,12 @@ struct hs3d_pmesh {
     Clock **clks = nullptr;        // device [nb]
     int *nb_n = nullptr;           // device [nb]
     cudaStream_t stream = nullptr;
+    // the degree buckets (and the mortar-degree groups) of one phase are independent: they run on
+    // these streams, forked from and joined back to the caller's stream (parallel graph branches
+    // when captured)
+    cudaStream_t aux[kMaxn] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kMaxn] = {};
     std::mutex mu;
     cudaGraphExec_t gexec = nullptr;   // one step of hs3d_pmesh_run for (gcfg, gu, gg, gdt)
     hs3d_solver_cfg gcfg{};
@@ -71,6 +77,11 @@ void pmesh_free(hs3d_pmesh *pm)
     void *ptrs[] = {pm->faces, pm->sides, pm->clks, pm->nb_n};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int k = 0; k < kMaxn; ++k) {
+        if (pm->aux[k]) cudaStreamDestroy(pm->aux[k]);
+        if (pm->ev_join[k]) cudaEventDestroy(pm->ev_join[k]);
+    }
+    if (pm->ev_fork) cudaEventDestroy(pm->ev_fork);
     if (pm->stream) cudaStreamDestroy(pm->stream);
     delete pm;
 }
@@ -170,6 +181,11 @@ hs3d_status pmesh_build(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmes
     pm->deg.assign(degree, degree + E);
     pm->off.assign(E + 1, 0);
     cudaError_t e = cudaStreamCreateWithFlags(&pm->stream, cudaStreamNonBlocking);
+    for (int k = 0; k < kMaxn && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&pm->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pm->ev_join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pm->ev_fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         pmesh_free(pm);
         return cuda_fail(e, "cudaStreamCreate");
@@ -292,20 +308,51 @@ MortarPhys<double> mortar_phys(const hs3d_pmesh *pm, const hs3d_solver_cfg *c)
     return MortarPhys<double>{it.gamma, it.gm1, it.hg, it.mu, it.kappa};
 }
 
+// fn(k, stream) for every k of ks, each on its own auxiliary stream ordered
+// after the work already on s; s then waits for all of them.
+template <class F>
+cudaError_t fork_join(const hs3d_pmesh *pm, cudaStream_t s, const std::vector<int> &ks, F fn)
+{
+    if (ks.size() <= 1) return ks.empty() ? cudaSuccess : fn(ks[0], s);
+    cudaError_t e = cudaEventRecord(pm->ev_fork, s);
+    for (size_t i = 0; i < ks.size() && e == cudaSuccess; ++i) {
+        e = cudaStreamWaitEvent(pm->aux[i], pm->ev_fork, 0);
+        if (e == cudaSuccess) e = fn(ks[i], pm->aux[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(pm->ev_join[i], pm->aux[i]);
+    }
+    for (size_t i = 0; i < ks.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s, pm->ev_join[i], 0);
+    return e;
+}
+
 // One residual evaluation or RK stage over all buckets.
 cudaError_t p_stage(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const std::vector<Batch> &bb, const double *u,
                     int stage, int lam_slot, cudaStream_t s)
 {
     const MortarPhys<double> P = mortar_phys(pm, c);
     const int *gb = pm->group_begin;
+    std::vector<int> groups, buckets;
+    for (int NM = 1; NM <= kMaxN; ++NM)
+        if (gb[NM + 1] > gb[NM]) groups.push_back(NM);
+    for (size_t k = 0; k < bb.size(); ++k) buckets.push_back((int)k);
+    auto mortar = [&](int mode) {
+        return [&, mode](int NM, cudaStream_t st) {
+            return launch_mortar(c->precision, c->physics, mode, c->surface_flux, pm->faces, gb, NM, pm->sides, u, P,
+                                 st);
+        };
+    };
     cudaError_t e = cudaSuccess;
     if (c->physics == HS3D_NS) {
-        e = launch_mortar(c->precision, c->physics, 0, c->surface_flux, pm->faces, gb, pm->sides, u, P, s);
-        for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) e = launch_grad(pm->b[k].N, c->precision, bb[k], s);
+        e = fork_join(pm, s, groups, mortar(0));
+        if (e == cudaSuccess)
+            e = fork_join(pm, s, buckets,
+                          [&](int k, cudaStream_t st) { return launch_grad(pm->b[k].N, c->precision, bb[k], st); });
     }
-    if (e == cudaSuccess) e = launch_mortar(c->precision, c->physics, 1, c->surface_flux, pm->faces, gb, pm->sides, u, P, s);
-    for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k)
-        e = launch_volume(pm->b[k].N, c->precision, c->physics, c->volume_form, c->time_scheme, bb[k], stage, lam_slot, s);
+    if (e == cudaSuccess) e = fork_join(pm, s, groups, mortar(1));
+    if (e == cudaSuccess)
+        e = fork_join(pm, s, buckets, [&](int k, cudaStream_t st) {
+            return launch_volume(pm->b[k].N, c->precision, c->physics, c->volume_form, c->time_scheme, bb[k], stage,
+                                 lam_slot, st);
+        });
     return e;
 }
 
