@@ -444,7 +444,6 @@ hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, 
     if (c->precision != HS3D_FP64)
         for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) e = launch_shadow(pm->b[k].N, bb[k], s);
     if (e == cudaSuccess) e = p_stage(pm, c, bb, u, -1, -1, s);
-    m->gu = nullptr;   // the shadow no longer holds the state a run left
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
 }
 
