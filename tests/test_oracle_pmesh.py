@@ -223,3 +223,39 @@ def test_linear_pressure_field_is_exact(phys, vol, surf):
         checked += 1
     assert checked == 8
     assert len(set(deg.tolist())) >= 4
+
+
+def _density_wave_error(lo, hi, surf, vol):
+    """Max-norm residual error (relative) on the density wave
+    rho = 1 + 0.2 sin(2 pi x/L), v and p constant -- an exact Euler solution
+    with du/dt = -(v.grad rho)(1, v, |v|^2/2) -- on a 3^3 mesh whose elements
+    draw their degrees from [lo, hi]."""
+    v, p, L = np.array([0.4, -0.3, 0.2]), 1.0, 2.0
+    deg = I.random_degrees(27, seed=61, lo=lo, hi=hi)
+    pm = O.PMesh(3, 3, 3, deg, lo=(0.0, 0.0, 0.0), hi=(L, L, L), amp=0.0)
+    u, exact = pm.empty(), pm.empty()
+    for e in range(pm.E):
+        ph = 2 * np.pi * pm.X(e)[0] / L
+        rho = 1 + 0.2 * np.sin(ph)
+        vgr = 0.2 * np.cos(ph) * 2 * np.pi / L * v[0]
+        b, x = pm.block(u, e), pm.block(exact, e)
+        b[0] = rho
+        x[0] = -vgr
+        for c in range(3):
+            b[1 + c] = rho * v[c]
+            x[1 + c] = -vgr * v[c]
+        b[4] = p / (G - 1) + 0.5 * rho * (v @ v)
+        x[4] = -vgr * 0.5 * (v @ v)
+    r = pm.residual(O.Cfg("euler", surf, vol), u)
+    return np.abs(r - exact).max() / np.abs(exact).max()
+
+
+@pytest.mark.parametrize("surf,vol", [("roe", "standard"), ("lf", "kg"), ("ec", "ec")])
+def test_spectral_convergence_across_mortars(surf, vol):
+    """The error of mixed-degree meshes falls spectrally as their degree range
+    rises, and stays at the level of their lowest degree's uniform mesh: the
+    mortars keep the method's accuracy (measured: within 1.5x)."""
+    e24, e46, e57 = (_density_wave_error(lo, hi, surf, vol) for lo, hi in ((2, 4), (4, 6), (5, 7)))
+    assert e46 < e24 / 10 and e57 < e46 / 3, (e24, e46, e57)
+    assert e57 < 1e-2
+    assert e46 <= 2 * _density_wave_error(4, 4, surf, vol)
