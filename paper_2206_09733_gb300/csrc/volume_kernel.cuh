@@ -622,7 +622,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
 template <int N, typename R, bool NS, int FORM>
 static cudaError_t vol_launch2(const Batch &b, int stage, double rkA, double rkB, int lam_slot, cudaStream_t s)
 {
-    constexpr int n = N + 1, n2 = n * n, n3 = n * n * n;
+    constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
     int epb = elems_per_block_p(N, sizeof(R) == 4 ? (FORM == kVolStdTC ? HS3D_MIXED_TC : HS3D_MIXED32) : HS3D_FP64, 1);
     int threads = epb * n3;
     if (threads > vol_threads<N>()) {
