@@ -393,3 +393,45 @@ def test_bench_configuration_conservation(bench_pmesh):
         tot += (R * W).sum(axis=(0, 2, 3, 4))
         mag += np.abs(R * W).sum(axis=(0, 2, 3, 4))
     assert np.all(np.abs(tot) <= 1e-12 * mag.max()), (tot, mag)
+
+
+def test_64cubed_mixed_degrees_free_stream_and_conservation():
+    """262,144 elements of degrees 2..4 (~1.9e7 nodes, 786,432 mortar faces):
+    the large-size index paths of the face table, the buckets and the mortar
+    grid, checked by what holds at any size (free stream, conservation)."""
+    E = 64
+    deg = np.random.default_rng(11).integers(2, 5, size=E ** 3).astype(np.int32)
+    gm = hs.PMesh(E, E, E, deg, *PI3, amp=0.05)
+    _, J = gm.geometry()
+    inv_j = 1.0 / float(J[J != 0].min())
+    for precision in ("fp64", "mixed32"):
+        gc = hs.solver_cfg("euler", "roe", "standard", precision, gamma=G)
+        u = torch.zeros(gm.size, dtype=torch.float64, device="cuda")
+        st = torch.tensor([1.1, 0.33, -0.22, 0.11, 0.9 / (G - 1) + 0.5 * 1.1 * 0.14], dtype=torch.float64,
+                          device="cuda")
+        for N in range(2, 5):
+            els = np.nonzero(deg == N)[0]
+            o0 = int(gm.offset[els[0]])
+            u[o0:o0 + len(els) * 5 * (N + 1) ** 3].view(len(els), 5, -1)[:] = st[None, :, None]
+        r = torch.zeros_like(u)
+        gm.residual(gc, u, r)
+        torch.cuda.synchronize()
+        bound = 2e-14 * 5 ** 4 * inv_j if precision == "fp64" else 2e-5 * 25 * inv_j / 1e3
+        assert float(r.abs().max()) < bound, (precision, float(r.abs().max()), bound)
+    gc = hs.solver_cfg("euler", "roe", "standard", "fp64", gamma=G)
+    u = gm.init_state(torch.zeros(gm.size, dtype=torch.float64, device="cuda"), "tgv", G, 0.3)
+    r = torch.zeros_like(u)
+    gm.residual(gc, u, r)
+    torch.cuda.synchronize()
+    tot = torch.zeros(5, dtype=torch.float64, device="cuda")
+    mag = torch.zeros(5, dtype=torch.float64, device="cuda")
+    for N in range(2, 5):
+        els = np.nonzero(deg == N)[0]
+        n = N + 1
+        o0 = int(gm.offset[els[0]])
+        R = r[o0:o0 + len(els) * 5 * n ** 3].view(len(els), 5, n ** 3)
+        W = J[o0 // 5:o0 // 5 + len(els) * n ** 3].view(len(els), 1, n ** 3) * torch.from_numpy(
+            _weights(N).reshape(1, 1, -1)).cuda()
+        tot += (R * W).sum(dim=(0, 2))
+        mag += (R * W).abs().sum(dim=(0, 2))
+    assert bool(torch.all(tot.abs() <= 1e-12 * mag.max())), (tot, mag)
