@@ -21,7 +21,8 @@
 // Equal degrees make every matrix the identity: the conforming face.
 //
 // Faces are grouped by mortar degree; a CTA holds several faces of one
-// degree, one thread per mortar point.  The per-bucket pointers live in a
+// degree, one thread per mortar point.  Faces of two equal degrees take a
+// barrier-free variant (k_mortar_conf) with the same arithmetic.  The per-bucket pointers live in a
 // small device table (MortarSide); the operators of every degree pair in
 // MortarOps.
 #include <math.h>
@@ -427,6 +428,95 @@ k_mortar(const MortarFace *__restrict__ faces, int nfaces, const MortarSide *__r
     }
 }
 
+// Faces whose two sides have the same degree N: the mortar is the face
+// itself and interpolation and projection are identities, so each thread
+// takes one face point, gathers both traces into registers, forms the same
+// interface value or flux as k_mortar and writes it to both sides' blocks --
+// no shared memory, no barriers.  Several faces per CTA.
+template <typename R, bool NS, int MODE, int N>
+__global__ void __launch_bounds__(128) k_mortar_conf(const MortarFace *__restrict__ faces, int nfaces,
+                                                     const MortarSide *__restrict__ sides, const double *__restrict__ u,
+                                                     int flux, MortarPhys<R> Ph)
+{
+    constexpr int n = N + 1, P = n * n, n3 = P * n;
+    constexpr int FPC = 128 / P >= 1 ? 128 / P : 1;
+    constexpr int NV = (MODE == 1 && NS) ? 17 : 5;
+    const int q = threadIdx.x / P, p = threadIdx.x - q * P;
+    const int f = blockIdx.x * FPC + q;
+    if (q >= FPC || f >= nfaces) return;
+    const MortarFace F = faces[f];
+    const int d = F.d;
+    const MortarSide &SL = sides[F.bL], &SR = sides[F.bR];
+    R w[2][NV];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const MortarSide &SD = s ? SR : SL;
+        const int le = s ? F.lR : F.lL;
+        const int node = mortar_face_node(n, d, s ? 0 : N, p % n, p / n);
+        if constexpr (sizeof(R) == 8) {
+            const double *src = u + SD.base + (size_t)le * 5 * n3 + node;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) w[s][v] = src[(size_t)v * n3];
+        } else {
+            const float *src = SD.uf + (size_t)le * 5 * n3 + node;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) w[s][v] = src[(size_t)v * n3];
+        }
+        if constexpr (MODE == 1 && NS) {
+            const R *G = (const R *)SD.grad + (size_t)le * 12 * n3 + node;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[s][5 + k] = G[(size_t)k * n3];
+        }
+    }
+    if constexpr (MODE == 0) {
+        R qL[4], qR[4], qs[4];
+        mortar_q(w[0], Ph.gm1, qL);
+        mortar_q(w[1], Ph.gm1, qR);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qs[v] = (R)0.5 * (qL[v] + qR[v]);
+        R *dL = (R *)SL.qhat6 + ((size_t)(2 * d + 1) * SL.E + F.lL) * 4 * P + p;
+        R *dR = (R *)SR.qhat6 + ((size_t)(2 * d) * SR.E + F.lR) * 4 * P + p;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            dL[v * P] = (R)2 * qs[v] - qL[v];
+            dR[v * P] = (R)2 * qs[v] - qR[v];
+        }
+    } else {
+        const int node = mortar_face_node(n, d, N, p % n, p / n);
+        const R *JA = (const R *)(sizeof(R) == 8 ? (const void *)SL.Ja : (const void *)SL.Jaf) +
+                      ((size_t)F.lL * 9 + d * 3) * n3 + node;
+        const R s1 = JA[0], s2 = JA[n3], s3 = JA[2 * (size_t)n3];
+        R fs[5];
+        mortar_riemann<R>(flux, w[0], w[1], Ph, s1, s2, s3, fs);
+        if constexpr (NS) {
+            R fl[5], fr[5];
+            const Prim<R> pL = mortar_prim(w[0], Ph.gm1), pR = mortar_prim(w[1], Ph.gm1);
+            visc_flux(pL, &w[0][5], Ph.mu, Ph.kappa, s1, s2, s3, fl);
+            visc_flux(pR, &w[1][5], Ph.mu, Ph.kappa, s1, s2, s3, fr);
+#pragma unroll
+            for (int v = 1; v < 5; ++v) fs[v] -= (R)0.5 * (fl[v] + fr[v]);
+        }
+        R *dL = (R *)SL.fstar6 + ((size_t)(2 * d + 1) * SL.E + F.lL) * 5 * P + p;
+        R *dR = (R *)SR.fstar6 + ((size_t)(2 * d) * SR.E + F.lR) * 5 * P + p;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            dL[v * P] = fs[v];
+            dR[v * P] = fs[v];
+        }
+    }
+}
+
+template <typename R, bool NS, int MODE, int N>
+static cudaError_t conf_group(const MortarFace *faces, int nfaces, const MortarSide *sides, const double *u, int flux,
+                              const MortarPhys<R> &P, cudaStream_t s)
+{
+    constexpr int n2 = (N + 1) * (N + 1);
+    constexpr int FPC = 128 / n2 >= 1 ? 128 / n2 : 1;
+    const unsigned blocks = (unsigned)((nfaces + FPC - 1) / FPC);
+    k_mortar_conf<R, NS, MODE, N><<<blocks, FPC * n2, 0, s>>>(faces, nfaces, sides, u, flux, P);
+    return cudaGetLastError();
+}
+
 template <typename R, bool NS, int MODE, int NM>
 static cudaError_t mortar_group(const MortarFace *faces, int nfaces, const MortarSide *sides, const double *u,
                                 const MortarOps *mo, int flux, const MortarPhys<R> &P, cudaStream_t s)
@@ -456,6 +546,12 @@ static cudaError_t mortar_mode(const MortarFace *faces, const int *group_begin, 
                                          flux, P, s);
     HS3D_MG(1) HS3D_MG(2) HS3D_MG(3) HS3D_MG(4) HS3D_MG(5) HS3D_MG(6) HS3D_MG(7)
 #undef HS3D_MG
+#define HS3D_CG(K)                                                                                                 \
+    if (e == cudaSuccess && (only < 0 || only == kMaxn + K) && group_begin[kMaxn + K + 1] > group_begin[kMaxn + K]) \
+        e = conf_group<R, NS, MODE, K>(faces + group_begin[kMaxn + K],                                             \
+                                       group_begin[kMaxn + K + 1] - group_begin[kMaxn + K], sides, u, flux, P, s);
+    HS3D_CG(1) HS3D_CG(2) HS3D_CG(3) HS3D_CG(4) HS3D_CG(5) HS3D_CG(6) HS3D_CG(7)
+#undef HS3D_CG
     return e;
 }
 

@@ -23,7 +23,9 @@ const MortarOps *device_mortar_ops();
 
 // One face of a mesh with per-element degrees: the +d face of an element
 // (bucket bL, index lL within it) shared with its +d neighbour (bucket bR,
-// index lR).  The face table is sorted by mortar degree max(N_L, N_R).
+// index lR).  The face table is sorted into groups by mortar degree
+// max(N_L, N_R) (on a mesh of one degree: the conforming groups, see
+// launch_mortar).
 struct MortarFace {
     int bL, lL, bR, lR, d;
 };
@@ -46,9 +48,11 @@ struct MortarPhys {
 };
 
 // mode 0: BR1 interface values; mode 1: face fluxes.  group_begin (HOST,
-// kMaxn + 1 ints): faces of mortar degree NM are faces[group_begin[NM] ..
-// group_begin[NM + 1]).  only >= 0: launch the group of that mortar degree
-// alone (else every non-empty group, in order).
+// 2 kMaxn + 1 ints): faces of mortar degree NM taken by k_mortar are
+// faces[group_begin[NM] .. group_begin[NM + 1]); faces between two elements
+// of degree N taken by the barrier-free conforming kernel are
+// faces[group_begin[kMaxn + N] .. group_begin[kMaxn + N + 1]).  only >= 0:
+// launch that group alone (else every non-empty group, in order).
 cudaError_t launch_mortar(int prec, int physics, int mode, int flux, const MortarFace *faces, const int *group_begin,
                           int only, const MortarSide *sides, const double *u, const MortarPhys<double> &P,
                           cudaStream_t s);
