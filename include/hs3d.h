@@ -331,6 +331,16 @@ hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *
 hs3d_status hs3d_pmesh_run(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
                            int nsteps, void *stream);
 
+/* Quadrature diagnostics of hs3d_diagnostics on the mesh with per-element
+ * degrees (each element with its own Gauss-Lobatto weights): out[0..4] =
+ * sum_e sum_ijk J w_i w_j w_k f_v (f = dudt if given, else u), out[5] the
+ * entropy rate and out[6] its magnitude scale.  Each degree group reduces in
+ * a fixed order and the groups are summed in a fixed order, so the result
+ * is bitwise reproducible.  u, dudt: device, the layout above; out: DEVICE,
+ * 7 doubles.  Stream-ordered. */
+hs3d_status hs3d_pmesh_diagnostics(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *cfg, const double *u,
+                                   const double *dudt, double *out, void *stream);
+
 /* Simulated time and steps of hs3d_pmesh_run since creation or the last
  * reset, as hs3d_clock. */
 hs3d_status hs3d_pmesh_clock(const hs3d_pmesh *pmesh, double *t, int64_t *steps, int reset, void *stream);

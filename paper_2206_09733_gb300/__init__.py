@@ -44,7 +44,7 @@ EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh
            "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
            "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding", "hs3d_pmesh_create",
            "hs3d_pmesh_destroy", "hs3d_pmesh_layout", "hs3d_pmesh_geometry", "hs3d_pmesh_init_state",
-           "hs3d_pmesh_residual", "hs3d_pmesh_run", "hs3d_pmesh_clock"]
+           "hs3d_pmesh_residual", "hs3d_pmesh_run", "hs3d_pmesh_clock", "hs3d_pmesh_diagnostics"]
 
 
 class HS3DError(RuntimeError):
@@ -125,6 +125,7 @@ def lib():
                 "hs3d_pmesh_residual": [vp, C.POINTER(SolverCfg), vp, vp, vp],
                 "hs3d_pmesh_run": [vp, C.POINTER(SolverCfg), vp, vp, d, i, vp],
                 "hs3d_pmesh_clock": [vp, C.POINTER(d), C.POINTER(C.c_int64), i, vp],
+                "hs3d_pmesh_diagnostics": [vp, C.POINTER(SolverCfg), vp, vp, vp, vp],
                 "hs3d_last_error": [],
                 "hs3d_version": [],
             }
@@ -359,6 +360,12 @@ class PMesh:
         """nsteps RK steps (hs3d_pmesh_run): dt > 0 fixed, else the CFL rule."""
         check(lib().hs3d_pmesh_run(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), int(nsteps),
                                    _stream(stream)))
+
+    def diagnostics(self, cfg: SolverCfg, u, out, dudt=None, stream=None):
+        """hs3d_pmesh_diagnostics into out (7 float64 on the device)."""
+        check(lib().hs3d_pmesh_diagnostics(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(dudt, "dudt"),
+                                           _ptr(out, "out"), _stream(stream)))
+        return out
 
     def clock(self, reset=False, stream=None):
         t, s = C.c_double(), C.c_int64()

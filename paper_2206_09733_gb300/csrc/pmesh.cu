@@ -44,6 +44,7 @@ struct hs3d_pmesh {
         void *fstar6 = nullptr, *qhat6 = nullptr;
     };
     std::vector<Bucket> b;
+    double *diag_tmp = nullptr;    // device [nb][7]: per-bucket diagnostics before their fixed-order sum
     MortarFace *faces = nullptr;   // device [3E], sorted into groups (see launch_mortar)
     int group_begin[2 * kMaxn + 1] = {0};   // group g: faces [group_begin[g], group_begin[g + 1])
     MortarSide *sides = nullptr;   // device [nb]
@@ -75,7 +76,7 @@ void pmesh_free(hs3d_pmesh *pm)
         if (bk.fstar6) cudaFree(bk.fstar6);
         if (bk.qhat6) cudaFree(bk.qhat6);
     }
-    void *ptrs[] = {pm->faces, pm->sides, pm->clks, pm->nb_n};
+    void *ptrs[] = {pm->faces, pm->sides, pm->clks, pm->nb_n, pm->diag_tmp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < hs3d_pmesh::kAux; ++k) {
@@ -278,6 +279,7 @@ hs3d_status pmesh_build(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmes
     if (e == cudaSuccess) e = cudaMalloc(&pm->sides, sizeof(MortarSide) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&pm->clks, sizeof(Clock *) * nb);
     if (e == cudaSuccess) e = cudaMalloc(&pm->nb_n, sizeof(int) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&pm->diag_tmp, sizeof(double) * 7 * nb);
     if (e == cudaSuccess)
         e = cudaMemcpy(pm->faces, faces.data(), sizeof(MortarFace) * faces.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pm->sides, sides.data(), sizeof(MortarSide) * nb, cudaMemcpyHostToDevice);
@@ -434,6 +436,43 @@ hs3d_status hs3d_pmesh_init_state(const hs3d_pmesh *pm, const hs3d_ic *ic, doubl
     for (size_t k = 0; k < pm->b.size() && st == HS3D_OK; ++k)
         st = hs3d_init_state(pm->b[k].m, ic, u + pm->b[k].base, stream);
     return st;
+}
+
+// out[k] = sum over the buckets b, in bucket order, of tmp[b][k] (one thread:
+// a fixed order, so the result is reproducible bit for bit).
+__global__ void k_pdiag_sum(const double *tmp, int nb, double *out)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int k = 0; k < 7; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += tmp[b * 7 + k];
+        out[k] = acc;
+    }
+}
+
+hs3d_status hs3d_pmesh_diagnostics(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const double *u, const double *dudt,
+                                   double *out, void *stream)
+{
+    hs3d_status st = p_check(pm, c);
+    if (st == HS3D_OK) st = check_ptr(u, "u");
+    if (st == HS3D_OK && dudt) st = check_ptr(dudt, "dudt");
+    if (st == HS3D_OK && !out) st = fail(HS3D_ERR_INVALID, "out is NULL");
+    if (st != HS3D_OK) return st;
+    hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
+    std::lock_guard<std::mutex> lock(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < pm->b.size() && e == cudaSuccess; ++k) {
+        const auto &bk = pm->b[k];
+        const Item it = make_item(bk.m, c, u + bk.base, nullptr, nullptr);
+        e = launch_diagnostics(bk.N, it, dudt ? dudt + bk.base : nullptr, bk.m->diag_partials,
+                               diagnostics_blocks(bk.N, bk.E), pm->diag_tmp + 7 * k, s);
+    }
+    if (e == cudaSuccess) {
+        k_pdiag_sum<<<1, 1, 0, s>>>(pm->diag_tmp, (int)pm->b.size(), out);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "diagnostics launch");
 }
 
 hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const double *u, double *dudt,

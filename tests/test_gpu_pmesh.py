@@ -435,3 +435,28 @@ def test_64cubed_mixed_degrees_free_stream_and_conservation():
         tot += (R * W).sum(dim=(0, 2))
         mag += (R * W).abs().sum(dim=(0, 2))
     assert bool(torch.all(tot.abs() <= 1e-12 * mag.max())), (tot, mag)
+
+
+@pytest.mark.parametrize("with_dudt", [False, True])
+def test_diagnostics_match_oracle_and_reproduce(with_dudt):
+    deg, (om, gm) = _mesh("curved_2to7")
+    oc, gc = cfgs("euler", "ec", "ec")
+    u = om.ic_tgv(G, 0.3)
+    ud = to_dev(om, gm, u)
+    r = torch.zeros_like(ud)
+    gm.residual(gc, ud, r)
+    ref = om.integrals(G, u, om.residual(oc, u) if with_dudt else None)
+    out = torch.zeros(7, dtype=torch.float64, device="cuda")
+    out2 = torch.zeros_like(out)
+    gm.diagnostics(gc, ud, out, r if with_dudt else None)
+    gm.diagnostics(gc, ud, out2, r if with_dudt else None)
+    got = out.cpu().numpy()
+    assert torch.equal(out, out2)
+    if with_dudt:
+        # conservation sums of the residual are round-off: compare against the magnitude scale
+        assert np.all(np.abs(got[:5] - ref[:5]) <= 1e-12 * ref[6])
+        assert abs(got[5] - ref[5]) <= 1e-12 * ref[6]
+        assert got[6] == pytest.approx(ref[6], rel=1e-12)
+    else:
+        # (the momentum integrals nearly cancel: bound every sum by the largest)
+        assert np.all(np.abs(got[:5] - ref[:5]) <= 1e-13 * np.abs(ref[:5]).max())
