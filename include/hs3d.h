@@ -327,7 +327,14 @@ hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *
  *   dt = min_e min( cfl*8/(n_e^2 lam_c,e), 12/(n_e^4 lam_v,e) ),
  * the first step from a pass over u, the later ones from the maxima the
  * previous step's last stage reduced.  Steps after the first replay one
- * captured CUDA graph (kept for the last (cfg, u, g, dt)).  Stream-ordered. */
+ * captured CUDA graph (kept for the last (cfg, u, g, dt)).  dt < 0:
+ * continue -- when the previous hs3d_pmesh_run on this mesh advanced this
+ * same u with the same cfg and neither hs3d_pmesh_init_state of u, a
+ * mixed-precision hs3d_pmesh_residual of another state nor a clock reset
+ * came between, every
+ * step is a replay (the steps are exactly those of one longer run);
+ * otherwise as dt = 0.  Writes to u by the caller are not seen: a caller
+ * that changes u passes dt = 0.  Stream-ordered. */
 hs3d_status hs3d_pmesh_run(const hs3d_pmesh *pmesh, const hs3d_solver_cfg *cfg, double *u, double *g, double dt,
                            int nsteps, void *stream);
 

@@ -357,7 +357,8 @@ class PMesh:
         return dudt
 
     def run(self, cfg: SolverCfg, u, g, nsteps, dt=0.0, stream=None):
-        """nsteps RK steps (hs3d_pmesh_run): dt > 0 fixed, else the CFL rule."""
+        """nsteps RK steps (hs3d_pmesh_run): dt > 0 fixed, dt == 0 the CFL rule,
+        dt < 0 continue the previous run of this same state."""
         check(lib().hs3d_pmesh_run(self._h, C.byref(cfg), _ptr(u, "u"), _ptr(g, "g"), float(dt), int(nsteps),
                                    _stream(stream)))
 

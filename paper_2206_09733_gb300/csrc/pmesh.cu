@@ -59,6 +59,10 @@ struct hs3d_pmesh {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kAux] = {};
     std::mutex mu;
+    // continuation record: the state and configuration the last hs3d_pmesh_run advanced (its last
+    // stage left the dt maxima in clock slot 1 and the FP32 shadow of that state)
+    const double *cont_u = nullptr;
+    hs3d_solver_cfg cont_cfg{};
     cudaGraphExec_t gexec = nullptr;   // one step of hs3d_pmesh_run for (gcfg, gu, gg, gdt)
     hs3d_solver_cfg gcfg{};
     const double *gu = nullptr, *gg = nullptr;
@@ -433,6 +437,12 @@ hs3d_status hs3d_pmesh_init_state(const hs3d_pmesh *pm, const hs3d_ic *ic, doubl
 {
     if (!pm || !ic) return fail(HS3D_ERR_INVALID, "pmesh or ic is NULL");
     hs3d_status st = check_ptr(u, "u");
+    if (st != HS3D_OK) return st;
+    {
+        hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
+        std::lock_guard<std::mutex> lock(m->mu);
+        if (m->cont_u == u) m->cont_u = nullptr;   // the state itself is rewritten
+    }
     for (size_t k = 0; k < pm->b.size() && st == HS3D_OK; ++k)
         st = hs3d_init_state(pm->b[k].m, ic, u + pm->b[k].base, stream);
     return st;
@@ -488,8 +498,10 @@ hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, 
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<Batch> bb = bucket_batches(pm, c, u, nullptr, dudt, false);
     cudaError_t e = cudaSuccess;
-    if (c->precision != HS3D_FP64)
+    if (c->precision != HS3D_FP64) {
+        if (m->cont_u != u) m->cont_u = nullptr;   // the FP32 shadow now holds another state
         for (size_t k = 0; k < bb.size() && e == cudaSuccess; ++k) e = launch_shadow(pm->b[k].N, bb[k], s);
+    }
     if (e == cudaSuccess) e = p_stage(pm, c, bb, u, -1, -1, s);
     return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
 }
@@ -507,11 +519,23 @@ hs3d_status hs3d_pmesh_run(const hs3d_pmesh *pmc, const hs3d_solver_cfg *c, doub
     hs3d_pmesh *pm = const_cast<hs3d_pmesh *>(pmc);
     std::lock_guard<std::mutex> lock(pm->mu);
     cudaStream_t s = (cudaStream_t)stream;
+    // dt < 0: continue the state the previous run on this mesh advanced with this cfg
+    const bool cont = dt < 0.0 && pm->cont_u == u && same_cfg(pm->cont_cfg, *c);
     if (dt < 0.0) dt = 0.0;
+    pm->cont_u = nullptr;
     cudaError_t e = cudaSuccess;
-    // the first step reads a fresh dt pass (or writes the FP32 shadow for a fixed dt)
-    e = p_step(pm, c, u, g, dt, true, s);
-    if (e != cudaSuccess || nsteps == 1) return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "step launch");
+    int replays = nsteps;
+    if (!cont) {
+        // the first step reads a fresh dt pass (or writes the FP32 shadow for a fixed dt)
+        e = p_step(pm, c, u, g, dt, true, s);
+        replays = nsteps - 1;
+        if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    }
+    if (replays == 0) {
+        pm->cont_u = u;
+        pm->cont_cfg = *c;
+        return HS3D_OK;
+    }
     // the remaining steps replay one captured step that continues from clock slot 1
     if (!(pm->gexec && pm->gu == u && pm->gg == g && pm->gdt == dt && same_cfg(pm->gcfg, *c))) {
         if (pm->gexec) cudaGraphExecDestroy(pm->gexec);
@@ -535,13 +559,21 @@ hs3d_status hs3d_pmesh_run(const hs3d_pmesh *pmc, const hs3d_solver_cfg *c, doub
         pm->gdt = dt;
         pm->gcfg = *c;
     }
-    for (int k = 1; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(pm->gexec, s);
-    return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "graph launch");
+    for (int k = 0; k < replays && e == cudaSuccess; ++k) e = cudaGraphLaunch(pm->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    pm->cont_u = u;
+    pm->cont_cfg = *c;
+    return HS3D_OK;
 }
 
 hs3d_status hs3d_pmesh_clock(const hs3d_pmesh *pm, double *t, int64_t *steps, int reset, void *stream)
 {
     if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
+    if (reset) {   // the reset clears the dt maxima a continuing run would read
+        hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
+        std::lock_guard<std::mutex> lock(m->mu);
+        m->cont_u = nullptr;
+    }
     hs3d_status worst = HS3D_OK;
     for (size_t k = 0; k < pm->b.size(); ++k) {
         double tk = 0.0;

@@ -460,3 +460,23 @@ def test_diagnostics_match_oracle_and_reproduce(with_dudt):
     else:
         # (the momentum integrals nearly cancel: bound every sum by the largest)
         assert np.all(np.abs(got[:5] - ref[:5]) <= 1e-13 * np.abs(ref[:5]).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed32"])
+def test_run_continuation_equals_one_run(precision):
+    deg, (om, gm) = _mesh("curved_2to7")
+    gc = hs.solver_cfg("ns", "roe", "ec", precision, gamma=G, Re=400.0)
+    u1 = gm.init_state(torch.zeros(gm.size, dtype=torch.float64, device="cuda"), "tgv", G, 0.2)
+    g1 = torch.zeros_like(u1)
+    gm.clock(reset=True)
+    gm.run(gc, u1, g1, 5)
+    t1, s1 = gm.clock()
+    u2 = gm.init_state(torch.zeros_like(u1), "tgv", G, 0.2)
+    g2 = torch.zeros_like(u1)
+    gm.clock(reset=True)
+    gm.run(gc, u2, g2, 2)
+    gm.run(gc, u2, g2, 3, dt=-1.0)
+    t2, s2 = gm.clock()
+    torch.cuda.synchronize()
+    assert s1 == s2 == 5 and t1 == t2
+    assert torch.equal(u1, u2)
