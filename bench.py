@@ -202,12 +202,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ measured DRAM traffic of the dominant kernel
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of k_volume<3,float,NS,EC> on this workload,
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of k_volume_dev<3,NS,EC> on this workload,
 # from one ncu capture (profiles/k_volume_mixed_ec_ns_N3_tgv16_traffic.md), and the digest of the
 # kernel's sources at the time of the capture: the figure is reported only while they are unchanged.
 VOLUME_TRAFFIC = {"bytes_per_launch": 49779541,
                   "sources_sha256": "d6cc5af3683c6d0b55cd49699e713b84e9edc1912c784041bbec54ecd63357ee"}
-VOLUME_SOURCES = ["volume_kernel.cuh", "volume_ec.cu", "physics.cuh", "internal.cuh"]
+VOLUME_SOURCES = ["volume_dev.cuh", "lowmach.cuh", "volume_ec.cu", "physics.cuh", "internal.cuh"]
 
 
 def volume_sources_digest():
@@ -230,23 +230,23 @@ def measured_volume_traffic():
 
 def kernel_bytes(kernel, prec, E=None, n=N + 1):
     """Compulsory DRAM bytes of one launch of each kernel.  FP64 path: state,
-    metric terms, 1/J and scratch in FP64.  Mixed path: the kernels read the
-    FP32 shadow of the state and FP32 copies of Ja, 1/J and the face normals;
-    the element kernel also reads the FP64 state for the RK accumulation and
-    writes both the FP64 state and its shadow; scratch in FP32."""
+    metric terms, 1/J and scratch in FP64.  Mixed path: every kernel reads
+    the FP64 state (it forms the deviations from it) and FP32 copies of Ja,
+    1/J and the face normals; the element kernel also reads the FP32 low
+    part of Ja (the float-float mass divergence) and the RK register; the
+    face kernel writes one flux block per side of each face; scratch in FP32."""
     E = EX * EY * EZ if E is None else E
     n2, n3 = n * n, n ** 3
     if prec == "fp64":
-        s, st, geo = 8, 40, 72 + 8
+        s, geo, jal, sides = 8, 72 + 8, 0, 1
     else:
-        s, st, geo = 4, 20, 36 + 4
-    if kernel == "volume":     # state, metrics, 1/J, grads, 6 face-flux blocks in; g in/out, u out (+ shadow)
-        rk = 40 * 3 + (40 + 20 if prec != "fp64" else 0)
-        return E * (st * n3 + geo * n3 + 12 * n3 * s + 6 * 5 * n2 * s + rk * n3)
-    if kernel == "face":       # two traces, face normal, two gradient traces in; flux out
-        return 3 * E * (2 * st * n2 + 3 * n2 * s + 2 * 12 * n2 * s + 5 * n2 * s)
-    if kernel == "grad":       # own state, metrics, 1/J, 6 neighbour traces in; gradients out
-        return E * (st * n3 + geo * n3 + 6 * st * n2 + 12 * n3 * s)
+        s, geo, jal, sides = 4, 36 + 4, 36, 2
+    if kernel == "volume":     # u, metrics (+ low part), 1/J, grads, this element's 6 face blocks; g in/out, u out
+        return E * (40 * n3 + (geo + jal) * n3 + 12 * n3 * s + 6 * 5 * n2 * s + 40 * 3 * n3)
+    if kernel == "face":       # two FP64 traces, face normal, two gradient traces in; flux (per side) out
+        return 3 * E * (2 * 40 * n2 + 3 * n2 * s + 2 * 12 * n2 * s + sides * 5 * n2 * s)
+    if kernel == "grad":       # own FP64 state, metrics, 1/J, 6 neighbour FP64 traces in; gradients out
+        return E * (40 * n3 + geo * n3 + 6 * 40 * n2 + 12 * n3 * s)
     return 0
 
 
@@ -413,7 +413,7 @@ def run_hs3d(args, world, rank, local):
             "frac": round(achieved_gbs / hbm_peak[0], 4),
             "traffic": measured_volume_traffic() if dom == "volume" else None,
             "algorithmic_bytes_per_launch": kernel_bytes(dom, "mixed32"),
-            "kernel": "k_volume<3,float,NS,EC>" if dom == "volume" else dom, "peak_source": hbm_peak[1]}
+            "kernel": "k_volume_dev<3,NS,EC>" if dom == "volume" else dom, "peak_source": hbm_peak[1]}
     p64 = prof["fp64"]
     fp64_ach = volume_flops() / (p64["volume"] / 3.0 * 1e-3) / 1e12
     # the same element kernel of the mixed path against the FP32 pipe (algorithmic flops)
@@ -463,7 +463,10 @@ def run_hs3d(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (analytic Taylor-Green initial condition)",
         "config": {"workload": WORKLOAD, "E": EX * EY * EZ, "N": N, "nodes": NODES,
-                   "precision": "mixed32: FP32 flux arithmetic, FP64 state/geometry/primitive conversion/RK",
+                   "precision": "mixed32: FP32 flux arithmetic on deviations from a per-element reference state "
+                                "(deviations formed in FP64 from the FP64 state), mass divergence in float-float "
+                                "(FP32 pairs), FP32 copies of Ja (+ FP32 low part), 1/J and face normals; FP64 "
+                                "state, RK registers and accumulation",
                    "l2": "flushed between timed steps (512 MB write outside the step events)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "timing": "sum of per-step CUDA-event times on the launching stream, CUDA-graph replay"},

@@ -79,7 +79,9 @@ hs3d_status validate_desc(const hs3d_mesh_desc *d)
 size_t mesh_bytes(int N, long long E, int nodes)
 {
     long long n = N + 1, n2 = n * n, n3 = n2 * n;
-    size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) + sizeof(float) * (size_t)E * n3 * 15 +
+    // X, Ja, J, 1/J in FP64; Jaf, Jalo, 1/J in FP32 (+ the FP32 shadow on Gauss-Legendre nodes); face normals
+    size_t geo = sizeof(double) * (size_t)E * n3 * (3 + 9 + 1 + 1) +
+                 sizeof(float) * (size_t)E * n3 * (19 + (nodes == HS3D_NODES_GAUSS ? 5 : 0)) +
                  (sizeof(double) + sizeof(float)) * 3 * (size_t)E * 3 * n2;
     size_t scratch = sizeof(double) * (3 * (size_t)E * 5 * n2 + (size_t)E * 12 * n3);
     // Gauss-Legendre meshes hold Gauss-Lobatto temporaries while they are built
@@ -105,10 +107,11 @@ static hs3d_status mesh_alloc(hs3d_mesh *m)
         {(void **)&m->X, sizeof(double) * E * 3 * n3},
         {(void **)&m->Ja, sizeof(double) * E * 9 * n3},
         {(void **)&m->Jaf, sizeof(float) * E * 9 * n3},
+        {(void **)&m->Jalo, sizeof(float) * E * 9 * n3},
         {(void **)&m->J, sizeof(double) * E * n3},
         {(void **)&m->invJ, sizeof(double) * E * n3},
         {(void **)&m->invJf, sizeof(float) * E * n3},
-        {(void **)&m->uf, sizeof(float) * E * 5 * n3},
+        {(void **)&m->uf, m->nodes == HS3D_NODES_GAUSS ? sizeof(float) * E * 5 * n3 : 0},
         {(void **)&m->fn, sizeof(double) * 3 * E * 3 * n2},
         {(void **)&m->fnf, sizeof(float) * 3 * E * 3 * n2},
         {(void **)&m->fstar, sizeof(double) * 3 * E * 5 * n2},
@@ -117,6 +120,7 @@ static hs3d_status mesh_alloc(hs3d_mesh *m)
         {(void **)&m->diag_partials, sizeof(double) * 4096 * 7},
     };
     for (auto &a : allocs) {
+        if (a.bytes == 0) continue;
         cudaError_t e = cudaMalloc(a.p, a.bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -132,8 +136,8 @@ void mesh_free(hs3d_mesh *m)
     if (!m) return;
     for (auto &gs : m->gslot)
         if (gs.exec) cudaGraphExecDestroy(gs.exec);
-    void *ptrs[] = {m->X,    m->Ja,   m->Jaf, m->J,   m->invJ,          m->invJf,
-                    m->uf,   m->fn,   m->fnf, m->fstar, m->grad, m->clk, m->diag_partials};
+    void *ptrs[] = {m->X,  m->Ja,  m->Jaf,   m->Jalo, m->J,   m->invJ,          m->invJf,
+                    m->uf, m->fn,  m->fnf,   m->fstar, m->grad, m->clk, m->diag_partials};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->stream) cudaStreamDestroy(m->stream);
@@ -198,6 +202,7 @@ hs3d_status mesh_build(const hs3d_mesh_desc *desc, hs3d_mesh **out)
     }
     e = launch_geometry(m->N, m->nodes, xyz_dev, m->ex, m->ey, m->ez, m->lo, m->hi, m->amp, m->X, m->Ja, m->Jaf, m->J, m->invJ,
                         m->invJf, m->fn, m->fnf, m->stream);
+    if (e == cudaSuccess) e = launch_metric_lo(m->Ja, m->Jaf, m->Jalo, (long long)m->E * 9 * m->n3, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->clk, 0, sizeof(Clock), m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (xyz_dev) cudaFree(xyz_dev);
@@ -214,6 +219,7 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
     Item it{};
     it.Ja = m->Ja;
     it.Jaf = m->Jaf;
+    it.Jalo = m->Jalo;
     it.invJ = m->invJ;
     it.invJf = m->invJf;
     it.fn = m->fn;
@@ -244,6 +250,8 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
     it.gammaf = (float)it.gamma;
     it.gm1f = (float)it.gm1;
     it.hgf = (float)it.hg;
+    it.igm1f = 1.0 / (double)it.gm1f;
+    it.hglof = (float)(0.5 * it.igm1f - (double)it.hgf);
     it.muf = (float)it.mu;
     it.kappaf = (float)it.kappa;
     return it;

@@ -15,7 +15,9 @@ struct hs3d_mesh {
     int device = 0;
     double *X = nullptr, *Ja = nullptr, *J = nullptr, *invJ = nullptr, *fn = nullptr;
     float *Jaf = nullptr, *invJf = nullptr;
-    float *uf = nullptr;            // FP32 shadow of the state being stepped (mixed path)
+    float *Jalo = nullptr;          // Ja - Jaf in FP32 (the mixed path's float-float mass divergence)
+    float *uf = nullptr;            // FP32 shadow of the state being stepped, only where FP32 traces are
+                                    // read (Gauss-Legendre nodes; the degree buckets of a p-mesh)
     float *fnf = nullptr;
     void *fstar = nullptr;          // scratch, sized for FP64
     void *grad = nullptr;           // scratch, sized for FP64

@@ -407,13 +407,9 @@ static cudaError_t prep_grad()
 {
     cudaError_t e = cudaFuncSetAttribute(k_grad<N, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_grad<N, double>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<N, float>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = prepare_grad_dev(N);
     return e;
 }
 
@@ -439,29 +435,19 @@ cudaError_t prepare_grad(int N)
 cudaError_t launch_face(int N, int prec, int physics, int flux, const Batch &b, cudaStream_t s)
 {
     if (b.gauss) return launch_face_gauss(N, prec, physics, flux, b, s);
+    if (prec != HS3D_FP64) return launch_face_dev(N, physics, flux, b, s);
 #define F64(K) face_launch<K, double>(physics, flux, b, s)
-#define F32(K) face_launch<K, float>(physics, flux, b, s)
-    if (prec == HS3D_FP64) {
-        HS3D_SWITCH_N(F64)
-    } else {
-        HS3D_SWITCH_N(F32)
-    }
+    HS3D_SWITCH_N(F64)
 #undef F64
-#undef F32
 }
 
 cudaError_t launch_grad(int N, int prec, const Batch &b, cudaStream_t s)
 {
     if (b.gauss) return launch_grad_gauss(N, prec, b, s);
+    if (prec != HS3D_FP64) return launch_grad_dev(N, b, s);
 #define G64(K) grad_launch<K, double>(b, s)
-#define G32(K) grad_launch<K, float>(b, s)
-    if (prec == HS3D_FP64) {
-        HS3D_SWITCH_N(G64)
-    } else {
-        HS3D_SWITCH_N(G32)
-    }
+    HS3D_SWITCH_N(G64)
 #undef G64
-#undef G32
 }
 
 }  // namespace hs3d

@@ -80,6 +80,7 @@ static Ops make_ops(int N)
             else v = 0.0;
             o.D[i * n + j] = v;
             o.Df[i * n + j] = (float)v;
+            o.Dlo[i * n + j] = (float)(v - (double)o.Df[i * n + j]);
         }
     o.iw0 = 1.0 / o.w[0];
     o.iw0f = (float)o.iw0;
@@ -139,6 +140,7 @@ static Ops make_ops_gauss(int N)
             const double v = (i != j) ? dL[i] / (dL[j] * (o.xi[i] - o.xi[j])) : o.xi[i] / (1.0 - o.xi[i] * o.xi[i]);
             o.D[i * n + j] = v;
             o.Df[i * n + j] = (float)v;
+            o.Dlo[i * n + j] = (float)(v - (double)o.Df[i * n + j]);
         }
     o.iw0 = 0.0;
     o.iw0f = 0.0f;
@@ -489,6 +491,21 @@ cudaError_t launch_init_state(int N, int E, const double *X, const hs3d_ic &ic, 
     int threads = 256;
     long long blocks = (total + threads - 1) / threads;
     k_init_state<<<(unsigned)blocks, threads, 0, s>>>(n3, total, X, ic, hi[0] - lo[0], hi[1] - lo[1], u);
+    return cudaGetLastError();
+}
+
+// Low part of the FP32 metric terms: Jalo = Ja - Jaf rounded to FP32.
+__global__ void k_metric_lo(const double *__restrict__ Ja, const float *__restrict__ Jaf, float *__restrict__ Jalo,
+                            long long count)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < count) Jalo[i] = (float)(Ja[i] - (double)Jaf[i]);
+}
+
+cudaError_t launch_metric_lo(const double *Ja, const float *Jaf, float *Jalo, long long count, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_metric_lo<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(Ja, Jaf, Jalo, count);
     return cudaGetLastError();
 }
 

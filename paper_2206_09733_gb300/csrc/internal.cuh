@@ -51,14 +51,17 @@ struct Clock {
 struct Item {
     const double *Ja;
     const float *Jaf;       // FP32 copy of Ja (the mixed path rounds Ja to FP32 anyway)
+    const float *Jalo;      // Ja - Jaf rounded to FP32: Jaf + Jalo carries Ja to ~2^-48 (mixed path's
+                            // float-float mass divergence)
     const double *invJ;
     const float *invJf;     // FP32 copy of 1/J
     const double *fn;
     const float *fnf;       // FP32 copy of fn
     const double *J;       // for diagnostics
     double *u;
-    float *uf;              // FP32 shadow of u (the mixed path's kernels read it; written by the
-                            // kernel that writes u, or by a shadow/priming pass)
+    float *uf;              // FP32 shadow of u, or nullptr: read by the kernels that take FP32
+                            // traces (mortars, Gauss-Legendre nodes); written by the kernel that
+                            // writes u, or by a shadow/priming pass
     double *g;
     double *out;            // residual output (residual mode)
     void *fstar;            // R [3][E][5][n2] (face6: [6][E][5][n2], see below)
@@ -82,6 +85,8 @@ struct Item {
     int gauss;              // Gauss-Legendre solution nodes
     double gm1, hg;                          // gamma - 1, 1/(2(gamma - 1))
     float gammaf, gm1f, hgf, muf, kappaf;    // the same constants rounded once for the FP32 path
+    float hglof;            // 1/(2 gm1f) - hgf: hgf + hglof is the reciprocal of the FP32 (gamma-1) to ~2^-48
+    double igm1f;           // 1/gm1f in FP64
 };
 
 // Physical constants of an item in the arithmetic type R (no per-thread
@@ -121,6 +126,7 @@ struct Ops {
     double w[kMaxn];
     double xi[kMaxn];
     float Df[kMaxn * kMaxn];
+    float Dlo[kMaxn * kMaxn];  // D - Df rounded to FP32 (float-float contractions)
     double iw0;                // 1/w_0 = 1/w_N (Gauss-Lobatto surface lifting factor)
     float iw0f;
     int gauss;                 // 1: Gauss-Legendre nodes
@@ -394,6 +400,13 @@ cudaError_t launch_grad_gauss(int N, int prec, const Batch &b, cudaStream_t s);
 cudaError_t launch_volume_gauss(int N, int prec, int physics, const Batch &b, int stage, double rkA, double rkB,
                                 int lam_slot, cudaStream_t s);
 cudaError_t prepare_gauss(int N);
+// Mixed path on Gauss-Lobatto nodes: FP32 flux arithmetic on deviations from
+// a per-element reference state (face_dev.cu, grad_dev.cu, volume_dev.cuh).
+cudaError_t launch_face_dev(int N, int physics, int flux, const Batch &b, cudaStream_t s);
+cudaError_t launch_grad_dev(int N, const Batch &b, cudaStream_t s);
+cudaError_t prepare_grad_dev(int N);
+// Ja - Jaf rounded to FP32, one thread per value.
+cudaError_t launch_metric_lo(const double *Ja, const float *Jaf, float *Jalo, long long count, cudaStream_t s);
 // Low-storage RK schemes (HS3D_TIME_*): stage count and the stage's (A_k, B_k).
 int rk_stages(int scheme);
 void rk_coeffs(int scheme, int k, double *A, double *B);

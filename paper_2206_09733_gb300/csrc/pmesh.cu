@@ -223,7 +223,10 @@ hs3d_status pmesh_build(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmes
         bd.node_xyz = X.data();
         st = mesh_build(&bd, &bk.m);
         if (st == HS3D_OK) {
-            e = cudaMalloc(&bk.fstar6, sizeof(double) * 6 * (size_t)bk.E * 5 * n2);
+            // the mortar kernels read the bucket's FP32 shadow of the state
+            e = cudaMalloc(&bk.m->uf, sizeof(float) * (size_t)bk.E * 5 * n3);
+            if (e == cudaSuccess) bk.m->bytes += sizeof(float) * (size_t)bk.E * 5 * n3;
+            if (e == cudaSuccess) e = cudaMalloc(&bk.fstar6, sizeof(double) * 6 * (size_t)bk.E * 5 * n2);
             if (e == cudaSuccess) e = cudaMalloc(&bk.qhat6, sizeof(double) * 6 * (size_t)bk.E * 4 * n2);
             if (e != cudaSuccess) {
                 cudaGetLastError();

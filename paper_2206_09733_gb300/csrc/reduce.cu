@@ -51,11 +51,12 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b,
         } else {
             // the mixed path's dt pass also writes the FP32 shadow of the state
             float us[5];
-            float *S = it.uf + (size_t)e * 5 * n3 + p;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-                us[v] = d2f_rn(u[v]);
-                S[v * n3] = us[v];
+            for (int v = 0; v < 5; ++v) us[v] = d2f_rn(u[v]);
+            if (it.uf) {
+                float *S = it.uf + (size_t)e * 5 * n3 + p;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) S[v * n3] = us[v];
             }
             q = prim_from_f(us, P.gm1);
         }
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(256) k_shadow(const __grid_constant__ Batch b,
     const long long ge = t / n3;
     const int p = (int)(t - ge * n3);
     const Item &it = find_item_elem(b, ge);
+    if (!it.uf) return;
     const size_t idx = (size_t)(ge - it.elem_begin) * 5 * n3 + p;
 #pragma unroll
     for (int v = 0; v < 5; ++v) it.uf[idx + (size_t)v * n3] = d2f_rn(it.u[idx + (size_t)v * n3]);
@@ -184,6 +186,7 @@ cudaError_t launch_shadow(int N, const Batch &b, cudaStream_t s)
     const int n3 = (N + 1) * (N + 1) * (N + 1);
     const long long total = b.total_elems * n3;
     if (total == 0) return cudaSuccess;
+    if (b.nitems == 1 && !b.single.uf) return cudaSuccess;   // no FP32 shadow on this path
     k_shadow<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(b, n3);
     return cudaGetLastError();
 }

@@ -10,6 +10,11 @@ cudaError_t launch_volume_form(int N, int prec, int physics, const Batch &b, int
                                int lam_slot, cudaStream_t s);
 template <int FORM>
 cudaError_t prepare_volume_form(int N);
+template <int FORM>
+cudaError_t launch_volume_dev_form(int N, int physics, const Batch &b, int stage, double rkA, double rkB,
+                                   int lam_slot, cudaStream_t s);
+template <int FORM>
+cudaError_t prepare_volume_dev_form(int N);
 
 // Low-storage Runge-Kutta schemes of Sec. 3.7, stage k: g <- A_k g + dt R,
 // u <- u + B_k g.  Williamson (1980) three-stage third order; Carpenter and
@@ -60,6 +65,14 @@ cudaError_t prepare_volume(int N)
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_DUCROS>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_MORINISHI>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_IR>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_STANDARD>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<kVolStdTC>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_EC>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_KG>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_PIROZZOLI>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_DUCROS>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_MORINISHI>(N);
+    if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_IR>(N);
     return e;
 }
 
@@ -74,6 +87,23 @@ cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, co
     if (b.gauss) {
         if (form != HS3D_VOL_STANDARD) return cudaErrorInvalidValue;
         return launch_volume_gauss(N, prec, physics, b, stage, A, B, lam_slot, s);
+    }
+    if (prec != HS3D_FP64) {
+        // mixed path: FP32 flux arithmetic on deviations (volume_dev.cuh)
+        switch (form) {
+            case HS3D_VOL_STANDARD:
+                if (prec == HS3D_MIXED_TC) return launch_volume_dev_form<kVolStdTC>(N, physics, b, stage, A, B, lam_slot, s);
+                return launch_volume_dev_form<HS3D_VOL_STANDARD>(N, physics, b, stage, A, B, lam_slot, s);
+            case HS3D_VOL_EC: return launch_volume_dev_form<HS3D_VOL_EC>(N, physics, b, stage, A, B, lam_slot, s);
+            case HS3D_VOL_KG: return launch_volume_dev_form<HS3D_VOL_KG>(N, physics, b, stage, A, B, lam_slot, s);
+            case HS3D_VOL_PIROZZOLI:
+                return launch_volume_dev_form<HS3D_VOL_PIROZZOLI>(N, physics, b, stage, A, B, lam_slot, s);
+            case HS3D_VOL_DUCROS: return launch_volume_dev_form<HS3D_VOL_DUCROS>(N, physics, b, stage, A, B, lam_slot, s);
+            case HS3D_VOL_MORINISHI:
+                return launch_volume_dev_form<HS3D_VOL_MORINISHI>(N, physics, b, stage, A, B, lam_slot, s);
+            case HS3D_VOL_IR: return launch_volume_dev_form<HS3D_VOL_IR>(N, physics, b, stage, A, B, lam_slot, s);
+        }
+        return cudaErrorInvalidValue;
     }
     switch (form) {
         case HS3D_VOL_STANDARD:

@@ -645,11 +645,9 @@ cudaError_t launch_volume_form(int N, int prec, int physics, const Batch &b, int
     if (b.total_elems == 0) return cudaSuccess;
 #define HS3D_VOLN(K)                                                                                          \
     case K:                                                                                                   \
-        if (prec == HS3D_FP64)                                                                                \
-            return physics == HS3D_NS ? vol_launch2<K, double, true, FORM>(b, stage, rkA, rkB, lam_slot, s)   \
-                                      : vol_launch2<K, double, false, FORM>(b, stage, rkA, rkB, lam_slot, s); \
-        return physics == HS3D_NS ? vol_launch2<K, float, true, FORM>(b, stage, rkA, rkB, lam_slot, s)        \
-                                  : vol_launch2<K, float, false, FORM>(b, stage, rkA, rkB, lam_slot, s);
+        if (prec != HS3D_FP64) return cudaErrorInvalidValue;                                                  \
+        return physics == HS3D_NS ? vol_launch2<K, double, true, FORM>(b, stage, rkA, rkB, lam_slot, s)       \
+                                  : vol_launch2<K, double, false, FORM>(b, stage, rkA, rkB, lam_slot, s);
     switch (N) {
         HS3D_VOLN(1) HS3D_VOLN(2) HS3D_VOLN(3) HS3D_VOLN(4) HS3D_VOLN(5) HS3D_VOLN(6) HS3D_VOLN(7)
     }
@@ -670,8 +668,6 @@ static cudaError_t prep_vol_n()
                                  cudaSharedmemCarveoutMaxShared);
     HS3D_ATTR(double, false)
     HS3D_ATTR(double, true)
-    HS3D_ATTR(float, false)
-    HS3D_ATTR(float, true)
 #undef HS3D_ATTR
     return e;
 }

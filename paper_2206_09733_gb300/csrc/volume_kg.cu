@@ -1,7 +1,9 @@
 // Element kernels of the Kennedy-Gruber split form (Sec. 3.5): all degrees, both
 // precisions, Euler and Navier-Stokes.
+#include "volume_dev.cuh"
 #include "volume_kernel.cuh"
 
 namespace hs3d {
 HS3D_VOLUME_FORM_TU(HS3D_VOL_KG)
+HS3D_VOLUME_DEV_FORM_TU(HS3D_VOL_KG)
 }  // namespace hs3d

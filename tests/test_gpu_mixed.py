@@ -1,10 +1,12 @@
-"""Mixed-precision path (FP32 flux arithmetic; FP64 state, geometry,
-primitive-variable conversion and RK accumulation) against the FP64 oracle.
+"""Mixed-precision path against the FP64 oracle: FP32 flux arithmetic on
+deviations from a per-element reference state formed in FP64, the mass
+divergence in float-float, FP64 state, geometry and RK accumulation.
 
-The errors are measured and bounded.  The per-residual bound depends on the
-flow: at Mach 0.1 the residual is a small difference of O(p0 = 71) fluxes and
-FP32 rounding of those fluxes dominates; the state after time integration is
-well conditioned and is held to 1e-5 relative (the final-state bar)."""
+Every residual is held to 1e-5 relative (rel-L2 over all nodes and
+variables), on smooth random states for every scheme and on the Mach 0.1
+Taylor-Green vortex, where the residual is a small difference of fluxes
+of O(p0 = 71) and O(H = 250): rounding the state alone to FP32 moves that
+residual by ~5e-4, so only the deviation formulation meets the bar there."""
 import numpy as np
 import pytest
 
@@ -51,7 +53,7 @@ def test_mixed_residual_smooth_state(combo):
     gm.residual(hs.solver_cfg(*combo, "mixed32", Re=400.0), u, r)
     err = rel(host(r), ref)
     print(f"mixed residual rel-L2 {combo}: {err:.3e}")
-    assert err < 2e-5
+    assert err < 1e-5
 
 
 @pytest.mark.parametrize("N", range(1, 8))
@@ -71,7 +73,7 @@ def test_mixed_every_order(N, combo):
     u = torch.from_numpy(u0).cuda()
     r = torch.empty_like(u)
     gm.residual(gc, u, r)
-    assert rel(host(r), ref) < 2e-5
+    assert rel(host(r), ref) < 1e-5
     uo, go = u0.copy(), np.zeros_like(u0)
     for _ in range(3):
         om.rk3_step(oc, uo, go)
@@ -102,7 +104,7 @@ def test_tensor_core_contraction_every_order(N, physics, surface):
     gm.residual(hs.solver_cfg(*combo, "mixed32", Re=400.0), u, r_32)
     e_tc, e_32 = rel(host(r_tc), ref), rel(host(r_32), ref)
     print(f"N={N} {combo}: tensor-core residual rel-L2 {e_tc:.3e}, CUDA-core {e_32:.3e}")
-    assert e_tc < 2e-5
+    assert e_tc < 1e-5
     # the split products keep FP32 accuracy: no worse than twice the CUDA-core error
     assert e_tc < 2 * e_32 + 1e-7
     uo, go = u0.copy(), np.zeros_like(u0)
@@ -143,8 +145,10 @@ def test_mixed_tgv_residual_and_state():
     g = torch.zeros_like(u)
     gm.rk3_run(gc, u, g, 10)
     err_u = rel(host(u), uo)
-    print(f"mixed TGV 16^3: residual rel-L2 {err_r:.3e}, state after 10 steps rel-L2 {err_u:.3e}")
-    assert err_r < 1e-2
+    per_var = [float(np.linalg.norm(host(r)[:, v] - ref[:, v]) / np.linalg.norm(ref)) for v in range(5)]
+    print(f"mixed TGV 16^3: residual rel-L2 {err_r:.3e} (per variable {per_var}), "
+          f"state after 10 steps rel-L2 {err_u:.3e}")
+    assert err_r < 1e-5
     assert err_u < 1e-5
 
 
