@@ -59,12 +59,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hs3d", choices=["hs3d", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving", type=int, default=128, help="requests in the batched-serving sample (0: skip)")
+    ap.add_argument("--serving", type=int, default=512, help="requests in the batched-serving stream (0: skip)")
     ap.add_argument("--mesh", type=int, default=16,
                     help="elements per direction (16 = the metric's workload; larger sizes for profiling only)")
     ap.add_argument("--stress", type=int, default=16, help="requests in the memory-admission stress run (0: skip)")
-    ap.add_argument("--stress-budget-gb", type=float, default=8.0)
+    ap.add_argument("--stress-budget-gb", type=float, default=8.0,
+                    help="server device budget of the stress run; 0: 90%% of the device's free memory")
     ap.add_argument("--stress-emax", type=int, default=40)
+    ap.add_argument("--stress-precisions", default="mixed32,fp64",
+                    help="comma-separated precisions of the stress run, each on its own server")
     ap.add_argument("--no-workloads", dest="workloads", action="store_false",
                     help="skip the larger configurations reported beside the line")
     ap.add_argument("--only", choices=["mixed32", "mixed_tc", "fp64"], default=None,
@@ -444,17 +447,21 @@ def run_hs3d(args, world, rank, local):
         extra["tgv_32cubed_degrees2to5_ec_roe_br1_mortar"] = run_pworkload(32, 2, 5, "ns", "roe", "ec", 5, 2)
 
     if args.stress > 0:
-        extra["admission_stress"] = run_stress(args.stress, args.stress_budget_gb, args.stress_emax, "mixed32")
+        extra["admission_stress"] = {p: run_stress(args.stress, args.stress_budget_gb, args.stress_emax, p)
+                                     for p in args.stress_precisions.split(",")}
 
     serving = None
     if args.serving > 0:
-        serving = run_serving(args.serving, max(4, args.serving // 16))
-        # below saturation: a quarter of the requests at a twentieth of the rate
-        serving["below_saturation"] = run_serving(max(4, args.serving // 4), 0, rate_scale=20.0)
+        serving = run_serving(args.serving)
+        # below saturation: 32 requests at a twentieth of the rate
+        serving["below_saturation"] = run_serving(32, rate_scale=20.0, baselines=False)
 
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(u64_final_check=None)
+        # both headline paths advanced W + K steps from the initial condition
+        cpu, errors = cpu_baseline(finals={"mixed32": u32.cpu().numpy(), "fp64": u64.cpu().numpy()},
+                                   compare_steps=args.warmup + args.steps)
 
     launches_per_step = 1 + 3 * 3   # dt finalize, 3 x (grad, face, element) (continuing steps: no priming pass)
     line = {
@@ -471,6 +478,7 @@ def run_hs3d(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "timing": "sum of per-step CUDA-event times on the launching stream, CUDA-graph replay"},
         "l2_rel_vs_fp64_gpu": l2_32_vs_64,
+        "error_vs_oracle": errors,
         "fp64": {"value": round(v64, 1), "ms_per_step": round(s64 * 1e3 / args.steps, 4), "dtype": "f64",
                  "sim_time_after_all_steps": t64, "roofline": fp64_roof},
         "kernel_ms_per_step": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in prof.items()},
@@ -670,88 +678,126 @@ def serving_requests(count, seed=0):
     return reqs
 
 
-def run_serving(count, seq_count, rate_scale=1.0):
-    """Submit `count` requests at their arrival times to the batched server
-    (mixed FP32 residual, FP64 state), poll to completion; then run the first
-    `seq_count` requests one at a time through the single-solve FP64 API.
-    Returns solves/s, p50/p99 latency and the sequential comparison."""
-    import numpy as np
-    import torch
+def serving_sample(reqs, t_final):
+    """A stratified sample of the request stream: for every N in 2..7 and every
+    third of the E range (4-10, 11-17, 18-24), the first request of the
+    stream in that stratum (18 requests), each integrated to t_final."""
+    picked = {}
+    for k, r in enumerate(reqs):
+        key = (r["N"], 0 if r["E"] <= 10 else 1 if r["E"] <= 17 else 2)
+        if key not in picked:
+            picked[key] = k
+    return [dict(reqs[k], t_final=t_final) for k in sorted(picked.values())]
 
+
+def serve(reqs, precision, mode, rate_scale=1.0, finals=None):
+    """Run requests through one server.  mode "stream": submitted at their
+    arrival times (rate_scale stretches them); "batch": all at once;
+    "sequential": one at a time, each submitted when the previous finished
+    (the library's single-solve path: graph replay, device dt, last step
+    clipped at t_final, no host work per step).  Returns per-request
+    (status, latency, t_done, t_submit, dof-stage updates) and the span."""
     import paper_2206_09733_gb300 as hs
-    reqs = serving_requests(count)
 
-    def descs(r, prec):
+    def descs(r):
         mesh = hs.mesh_desc(r["E"], r["E"], r["E"], r["N"], lo=(0, 0, 0), hi=(10, 10, 10))
-        cfg = hs.solver_cfg("euler", "lf", "ec", prec, gamma=GAMMA, cfl=CFL)
+        cfg = hs.solver_cfg("euler", "lf", "ec", precision, gamma=GAMMA, cfl=CFL)
         ic = hs.ic_desc("vortex", GAMMA, r["Ma"], r["beta"], r["xc"], r["yc"])
         return mesh, cfg, ic
 
     srv = hs.Server()
-    # warm-up: one small request through the server
-    m, c, i = descs(reqs[0], "mixed32")
+    m, c, i = descs(reqs[0])                      # warm-up: one short request
     t = srv.submit(m, c, i, t_final=0.05)
     while srv.poll(t)[0] == hs.PENDING:
         time.sleep(0.001)
+    done = {}
+
+    def wait(tk):
+        while True:
+            st, res = srv.poll(tk)
+            if st != hs.PENDING:
+                done[tk] = (st, res.t_done - res.t_submit, res.t_done, res.t_submit, res.dof * res.steps * 3)
+                return
+            time.sleep(0.0005)
+
     tickets = []
-    # the final states of the requests also solved sequentially in FP64 below
-    finals = [np.empty(r["E"] ** 3 * 5 * (r["N"] + 1) ** 3) for r in reqs[:seq_count]]
     t0 = time.perf_counter()
     for k, r in enumerate(reqs):
-        target = r["arrival"] * rate_scale
-        while time.perf_counter() - t0 < target:
-            time.sleep(0.0002)
-        m, c, i = descs(r, "mixed32")
-        tickets.append(srv.submit(m, c, i, t_final=1.0, result=finals[k] if k < seq_count else None))
-    done = {}
-    while len(done) < len(tickets):
-        for tk in tickets:
-            if tk not in done:
-                st, res = srv.poll(tk)
-                if st != hs.PENDING:
-                    done[tk] = (st, res.t_done - res.t_submit, res.t_done, res.t_submit, res.dof * res.steps * 3)
-        time.sleep(0.0005)
-    ok = [v for v in done.values() if v[0] == hs.OK]
-    failed = {}
-    for v in done.values():
-        if v[0] != hs.OK:
-            failed[hs.STATUS_NAMES.get(v[0], str(v[0]))] = failed.get(hs.STATUS_NAMES.get(v[0], str(v[0])), 0) + 1
-    lat = np.array([v[1] for v in ok])
-    span = max(v[2] for v in ok) - min(v[3] for v in ok)
-    dof_stage = sum(v[4] for v in ok)
+        if mode == "stream":
+            while time.perf_counter() - t0 < r["arrival"] * rate_scale:
+                time.sleep(0.0002)
+        m, c, i = descs(r)
+        res = finals[k] if finals is not None else None
+        tickets.append(srv.submit(m, c, i, t_final=r.get("t_final", 1.0), result=res))
+        if mode == "sequential":
+            wait(tickets[-1])
+    for tk in tickets:
+        if tk not in done:
+            wait(tk)
     srv.close()
-    # sequential FP64 per-solve through the single-mesh API
-    seq_t = 0.0
-    l2 = []
-    for k, r in enumerate(reqs[:seq_count]):
-        mesh = hs.Mesh(r["E"], r["E"], r["E"], r["N"], lo=(0, 0, 0), hi=(10, 10, 10))
-        u = mesh.init_state(mesh.empty_state(), "vortex", GAMMA, r["Ma"], r["beta"], r["xc"], r["yc"])
-        g = torch.zeros_like(u)
-        cfg = hs.solver_cfg("euler", "lf", "ec", "fp64", gamma=GAMMA, cfl=CFL)
-        dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        tsim = 0.0
-        while tsim < 1.0 - 1e-12:
-            mesh.dt(cfg, u, dt_dev)
-            dt = min(float(dt_dev.item()), 1.0 - tsim)
-            mesh.rk3_step(cfg, u, g, dt=dt)
-            tsim += dt
-        torch.cuda.synchronize()
-        seq_t += time.perf_counter() - a
-        ref = u.cpu().numpy().ravel()
-        l2.append(float(np.linalg.norm(finals[k] - ref) / np.linalg.norm(ref)))
-        del mesh
-    out = {"requests": count, "completed": len(ok), "failed": failed, "solves_per_s": round(len(ok) / span, 2),
-           "dof_stage_per_s": round(dof_stage / span, 1),
+    return [done[tk] for tk in tickets]
+
+
+def serving_summary(rows, extra=None):
+    import numpy as np
+    ok = [v for v in rows if v[0] == 0]
+    lat = np.array([v[1] for v in ok]) if ok else np.array([0.0])
+    span = (max(v[2] for v in ok) - min(v[3] for v in ok)) if ok else 1.0
+    out = {"requests": len(rows), "completed": len(ok), "solves_per_s": round(len(ok) / span, 3),
+           "dof_stage_per_s": round(sum(v[4] for v in ok) / span, 1),
            "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
-           "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
-           "arrivals": f"Poisson {200 / rate_scale:g} req/s",
-           "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5"}
-    if seq_count:
-        out.update({"sequential_fp64_solves_per_s": round(seq_count / seq_t, 2),
-                    "sequential_sample": f"first {seq_count} requests, one at a time, FP64, hs3d_rk3_step + host dt read",
-                    "l2_rel_server_mixed_vs_sequential_fp64_max": max(l2)})
+           "latency_p99_s": round(float(np.percentile(lat, 99)), 4)}
+    if extra:
+        out.update(extra)
+    return out
+
+
+def run_serving(count, rate_scale=1.0, sample_t_final=0.25, baselines=True):
+    """The batched server (mixed FP32 flux arithmetic, FP64 state) on `count`
+    requests arriving as a Poisson stream, and, on a stratified sample of
+    the stream, the same engine in four arms that separate the batching and
+    precision effects: sequential FP64 per-solve, sequential mixed, batched
+    FP64 and batched mixed (sample submitted at once), with the largest
+    rel-L2 difference between the batched mixed final states and the
+    sequential FP64 ones."""
+    import numpy as np
+    import paper_2206_09733_gb300 as hs
+    reqs = serving_requests(count)
+    rows = serve(reqs, "mixed32", "stream", rate_scale)
+    failed = {}
+    for v in rows:
+        if v[0] != hs.OK:
+            nm = hs.STATUS_NAMES.get(v[0], str(v[0]))
+            failed[nm] = failed.get(nm, 0) + 1
+    out = serving_summary(rows, {"failed": failed, "arrivals": f"Poisson {200 / rate_scale:g} req/s",
+                                 "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5"})
+    if not baselines:
+        return out
+    sample = serving_sample(reqs, sample_t_final)
+    sizes = [r["E"] ** 3 * 5 * (r["N"] + 1) ** 3 for r in sample]
+    fin = {}
+    arms = {}
+    for prec in ("fp64", "mixed32"):
+        for mode in ("sequential", "batch"):
+            fin[(prec, mode)] = [np.empty(n) for n in sizes]
+            rows = serve(sample, prec, mode, finals=fin[(prec, mode)])
+            arms[f"{mode}_{prec}"] = serving_summary(rows)
+    ref = fin[("fp64", "sequential")]
+    l2 = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(fin[("mixed32", "batch")], ref)]
+    l2b = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(fin[("fp64", "batch")], ref)]
+    out["sample"] = {"requests": len(sample), "t_final": sample_t_final,
+                     "strata": "every N in 2..7 x every third of E in 4..24, the first request of each stratum",
+                     "arms": arms,
+                     "batching_gain_mixed": round(arms["batch_mixed32"]["solves_per_s"] /
+                                                  arms["sequential_mixed32"]["solves_per_s"], 3),
+                     "batching_gain_fp64": round(arms["batch_fp64"]["solves_per_s"] /
+                                                 arms["sequential_fp64"]["solves_per_s"], 3),
+                     "precision_gain_batched": round(arms["batch_mixed32"]["solves_per_s"] /
+                                                     arms["batch_fp64"]["solves_per_s"], 3),
+                     "server_mixed_vs_sequential_fp64": round(arms["batch_mixed32"]["solves_per_s"] /
+                                                              arms["sequential_fp64"]["solves_per_s"], 3),
+                     "l2_rel_batched_mixed_vs_sequential_fp64_max": max(l2),
+                     "l2_rel_batched_fp64_vs_sequential_fp64_max": max(l2b)}
     return out
 
 
@@ -774,7 +820,10 @@ def run_stress(count, budget_gb, emax, precision):
     import paper_2206_09733_gb300 as hs
     reqs = stress_requests(count, emax=emax)
     budget = int(budget_gb * 2 ** 30)
-    srv = hs.Server(hbm_budget_bytes=budget)
+    srv = hs.Server(hbm_budget_bytes=budget)        # 0: the library takes 90% of the free device memory
+    if budget == 0:
+        free, _ = __import__("torch").cuda.mem_get_info()
+        budget = int(0.9 * free)
     tickets, total_bytes = [], 0
     t0 = time.perf_counter()
     for r in reqs:
@@ -810,9 +859,22 @@ def run_stress(count, budget_gb, emax, precision):
 
 # ------------------------------------------------------------------ the oracle on the host cores
 
-def cpu_baseline(u64_final_check=None, budget_s=15.0):
+def rel_errors(a, b):
+    """rel-L2 = |a - b|_2 / |b|_2 over all nodes and variables; rel-Linf =
+    max |a - b| / max |b|."""
+    import numpy as np
+    d = np.asarray(a) - np.asarray(b)
+    return {"l2_rel": float(np.linalg.norm(d) / np.linalg.norm(b)),
+            "linf_rel": float(np.abs(d).max() / np.abs(b).max())}
+
+
+def cpu_baseline(finals=None, compare_steps=0, budget_s=15.0):
     """Time the FP64 CPU oracle (as it stands) on this workload: RK3 steps
-    from the initial condition until ~budget_s of CPU work."""
+    from the initial condition until ~budget_s of CPU work (at most 200).
+    finals: {precision: host state of the GPU path after compare_steps RK3
+    steps from the same initial condition}; each is compared with the
+    oracle's state after the same number of steps (each side with its own
+    CFL time step)."""
     import numpy as np
 
     import oracle as O
@@ -821,12 +883,20 @@ def cpu_baseline(u64_final_check=None, budget_s=15.0):
     u = om.ic_tgv(GAMMA, MA)
     g = np.zeros_like(u)
     steps = 0
+    t_sim = 0.0
+    errors = None
     t0 = time.perf_counter()
     while True:
-        om.rk3_step(oc, u, g)
+        t_sim += om.rk3_step(oc, u, g)
         steps += 1
+        if finals and steps == compare_steps:
+            errors = {"steps": steps, "oracle_sim_time": t_sim,
+                      "how": "GPU state after W+K RK3 steps vs the FP64 CPU oracle after as many steps from the "
+                             "same initial condition (each with its own CFL time step)"}
+            for prec, a in finals.items():
+                errors[prec] = rel_errors(a, u)
         el = time.perf_counter() - t0
-        if el > budget_s or steps >= 200:
+        if (el > budget_s and steps >= compare_steps) or steps >= max(200, compare_steps):
             break
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out = {"value": round(NODES * 3 * steps / el, 1), "unit": "DOF-stage-updates/s", "cores": cores,
@@ -846,7 +916,7 @@ def cpu_baseline(u64_final_check=None, budget_s=15.0):
                                 "sample": f"2 RK3 steps of the same workload ({el1:.1f} s)"}
     except (subprocess.SubprocessError, ValueError, IndexError) as exc:
         out["single_thread"] = {"unavailable": str(exc)[:200]}
-    return out
+    return out, errors
 
 
 def run_reference(args, world, rank):

@@ -246,9 +246,11 @@ hs3d_status hs3d_diagnostics(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, 
  * memory pool owns all device memory, or real-time loops that must not
  * allocate or synchronise.  The paper has no counterpart; this is a library
  * convenience.  Allocates nothing: the caller passes every input (N, E,
- * gamma, the Jacobian J [E][n3] e.g. copied out by hs3d_mesh_geometry, the
- * state u and optionally dudt, all DEVICE FP64) and the DEVICE output out[7]
- * (same meaning as hs3d_diagnostics; the two give the same result).  The
+ * gamma, the solution nodes the mesh was built on, HS3D_NODES_LOBATTO or
+ * HS3D_NODES_GAUSS, whose quadrature weights the sums use, the Jacobian J
+ * [E][n3] e.g. copied out by hs3d_mesh_geometry, the state u and optionally
+ * dudt, all DEVICE FP64) and the DEVICE output out[7] (same meaning as
+ * hs3d_diagnostics; the two give the same result on the same mesh).  The
  * per-block partial sums live in one fixed device array of 4096 slots, each
  * covering 2048 nodes, so E*(N+1)^3 may not exceed 8,388,608 nodes
  * (HS3D_ERR_INVALID beyond).  The array is compiled into the library: every
@@ -259,7 +261,7 @@ hs3d_status hs3d_diagnostics(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, 
  * call writes every slot it later reads, so nothing needs clearing, but two
  * calls that overlap on the GPU (other streams, other threads) race on the
  * array and give wrong results.  Stream-ordered. */
-hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, const double *J, const double *u,
+hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, int nodes, const double *J, const double *u,
                                      const double *dudt, double *out, void *stream);
 
 /* Autotuner: times every admissible launch shape (elements per CTA) of the

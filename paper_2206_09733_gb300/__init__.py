@@ -114,7 +114,7 @@ def lib():
                                       C.POINTER(C.c_size_t)],
                 "hs3d_rk3_step_profiled": [vp, C.POINTER(SolverCfg), vp, vp, d, C.POINTER(d), vp],
                 "hs3d_alu_peaks": [C.POINTER(d), vp],
-                "hs3d_diagnostics_noalloc": [i, C.c_int64, d, vp, vp, vp, vp, vp],
+                "hs3d_diagnostics_noalloc": [i, C.c_int64, d, i, vp, vp, vp, vp, vp],
                 "hs3d_autotune": [vp, C.POINTER(SolverCfg), C.POINTER(i), vp],
                 "hs3d_check_rounding": [vp, C.c_int64, vp, vp],
                 "hs3d_pmesh_create": [C.POINTER(MeshDesc), vp, C.POINTER(vp)],
@@ -419,10 +419,11 @@ class Server:
         return {"queued": q.value, "running": r.value, "finished": f.value, "bytes_in_use": b.value}
 
 
-def diagnostics_noalloc(N, E, gamma, J, u, out, dudt=None, stream=None):
+def diagnostics_noalloc(N, E, gamma, J, u, out, dudt=None, nodes="lobatto", stream=None):
     """hs3d_diagnostics_noalloc: the quadrature diagnostics with no device
-    allocation (for callers that cannot allocate; see include/hs3d.h)."""
-    check(lib().hs3d_diagnostics_noalloc(int(N), int(E), float(gamma), _ptr(J, "J"), _ptr(u, "u"),
+    allocation (for callers that cannot allocate; see include/hs3d.h);
+    `nodes` names the solution nodes of the mesh J and u belong to."""
+    check(lib().hs3d_diagnostics_noalloc(int(N), int(E), float(gamma), NODES[nodes], _ptr(J, "J"), _ptr(u, "u"),
                                          _ptr(dudt, "dudt"), _ptr(out, "out"), _stream(stream)))
     return out
 

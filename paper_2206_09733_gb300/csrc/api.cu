@@ -114,6 +114,7 @@ static hs3d_status mesh_alloc(hs3d_mesh *m)
         {(void **)&m->uf, m->nodes == HS3D_NODES_GAUSS ? sizeof(float) * E * 5 * n3 : 0},
         {(void **)&m->fn, sizeof(double) * 3 * E * 3 * n2},
         {(void **)&m->fnf, sizeof(float) * 3 * E * 3 * n2},
+        {(void **)&m->anc, (size_t)112 * E},
         {(void **)&m->fstar, sizeof(double) * 3 * E * 5 * n2},
         {(void **)&m->grad, sizeof(double) * E * 12 * n3},
         {(void **)&m->clk, sizeof(Clock)},
@@ -137,7 +138,7 @@ void mesh_free(hs3d_mesh *m)
     for (auto &gs : m->gslot)
         if (gs.exec) cudaGraphExecDestroy(gs.exec);
     void *ptrs[] = {m->X,  m->Ja,  m->Jaf,   m->Jalo, m->J,   m->invJ,          m->invJf,
-                    m->uf, m->fn,  m->fnf,   m->fstar, m->grad, m->clk, m->diag_partials};
+                    m->uf, m->fn,  m->fnf,   m->anc,  m->fstar, m->grad, m->clk, m->diag_partials};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->stream) cudaStreamDestroy(m->stream);
@@ -227,6 +228,7 @@ Item make_item(const hs3d_mesh *m, const hs3d_solver_cfg *c, const double *u, do
     it.J = m->J;
     it.u = const_cast<double *>(u);
     it.uf = m->uf;
+    it.anc = m->anc;
     it.g = g;
     it.out = out;
     it.fstar = m->fstar;

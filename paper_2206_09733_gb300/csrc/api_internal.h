@@ -19,6 +19,7 @@ struct hs3d_mesh {
     float *uf = nullptr;            // FP32 shadow of the state being stepped, only where FP32 traces are
                                     // read (Gauss-Legendre nodes; the degree buckets of a p-mesh)
     float *fnf = nullptr;
+    void *anc = nullptr;            // mixed path: reference state of each element (112 bytes each)
     void *fstar = nullptr;          // scratch, sized for FP64
     void *grad = nullptr;           // scratch, sized for FP64
     hs3d::Clock *clk = nullptr;

@@ -151,8 +151,24 @@ __global__ void __launch_bounds__(256) k_face_dev(const __grid_constant__ Batch 
     // the reference state whose identities hold exactly; the others only differences
     const bool two_point = (flux == HS3D_FLUX_EC || flux == HS3D_FLUX_MATRIX);
     double ad[5];
-    const Anchor A = two_point ? make_anchor(uL, gm1, hg, it.hglof, it.igm1f, ad) : make_anchor_face(uL, gm1, ad);
-    const Dev DL = make_dev(uL, ad, A, gm1), DR = make_dev(uR, ad, A, gm1);
+    Anchor A;
+    Dev DL, DR;
+    if (two_point) {
+        // the minus element's reference state, left by the pass before
+        const AnchorRec &R = ((const AnchorRec *)it.anc)[eL];
+        A = R.a;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ad[v] = R.ad[v];
+        DL = make_dev(uL, ad, A, gm1);
+        DR = make_dev(uR, ad, A, gm1);
+    } else {
+        // the reference is u_L itself (its FP32 values serve as the coefficients):
+        // u_L's deviation is zero and u_R's is the jump, one FP64 subtraction each
+        A = make_anchor_face(uL, gm1, ad);
+        DL = make_dev_f(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, A, gm1);
+        DR = make_dev_f(dev_round(uR[0] - uL[0]), dev_round(uR[1] - uL[1]), dev_round(uR[2] - uL[2]),
+                        dev_round(uR[3] - uL[3]), dev_round(uR[4] - uL[4]), A, gm1);
+    }
     const float *Fn = it.fnf + (size_t)f * 3 * n2 + ab;
     const float s1 = Fn[0], s2 = Fn[n2], s3 = Fn[2 * n2];
     const Prim<float> qL = dev_prim(DL, A), qR = dev_prim(DR, A);

@@ -86,17 +86,17 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
     float *qn = q + 4 * n3;
     Anchor *ANC = (Anchor *)((float *)AD + 10);
     float qin[4];
-    constexpr int pc = (n / 2) * (1 + n + n2);   // the element's centre node: its reference state
+    constexpr int pc = anchor_node(n);   // the element's centre node: its reference state
     double uo[5];
     if (valid) {
         const double *U = itp->u + (size_t)e * 5 * n3;
 #pragma unroll
         for (int v = 0; v < 5; ++v) uo[v] = U[v * n3 + p];
-        if (p == pc) {
-            double ad[5];
-            *ANC = make_anchor(uo, itp->gm1f, itp->hgf, itp->hglof, itp->igm1f, ad);
+        if (p == pc) {   // the element's reference state, left by the pass before
+            const AnchorRec &R = ((const AnchorRec *)itp->anc)[e];
+            *ANC = R.a;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) AD[v] = ad[v];
+            for (int v = 0; v < 5; ++v) AD[v] = R.ad[v];
         }
         // the element's barrier is initialised before any of its threads polls it
         if (BULK && p == 0) mbar_init(bulk_bar + le, 1);

@@ -75,6 +75,7 @@ struct Item {
     // (q_out - q_in)/2 = q*_e - q_in is unchanged
     const void *qhat6;
     int face6;
+    void *anc;              // mixed path: one reference-state record per element (AnchorRec), or nullptr
     Clock *clk;
     int ex, ey, ez;
     int E;

@@ -137,10 +137,10 @@ __device__ __forceinline__ Anchor make_anchor(const double uc[5], float gm1, flo
 }
 
 // Reference state of a face for fluxes of the "central + dissipation" kind,
-// which use only differences of one-point flux deviations and jumps: any
-// FP32 state serves, so the minus side's conserved values rounded to FP32
-// are taken as they are (no FP64 arithmetic); the residuals of the rounded
-// derived quantities are constant offsets that cancel in every difference.
+// which use only F(u_R) - F(u_L) and jumps: the minus side's state u_L is the
+// reference (its deviation is zero, u_R's is the jump u_R - u_L formed in
+// FP64), and its values rounded to FP32 serve as the coefficients of the
+// deviation formulas, whose results are then accurate relative to the jump.
 __device__ __forceinline__ Anchor make_anchor_face(const double uc[5], float gm1, double ad[5])
 {
     Anchor A;
@@ -165,6 +165,31 @@ __device__ __forceinline__ Anchor make_anchor_face(const double uc[5], float gm1
     ad[3] = f2d_exact(A.m3);
     ad[4] = f2d_exact(A.E);
     return A;
+}
+
+// An element's reference state as the mixed kernels keep it in HBM (one
+// record per element, Item::anc): the FP64 conserved values and the FP32
+// Anchor.  The element kernel's centre-node thread rewrites it after each RK
+// stage from the updated state (the priming passes before the first stage),
+// so the next kernels load it instead of building it: any FP32 state near
+// the element's serves, as long as every thread of one kernel launch uses
+// the same one.
+struct AnchorRec {
+    double ad[5];
+    Anchor a;
+    float pad[4];
+};
+static_assert(sizeof(AnchorRec) == 112, "AnchorRec layout");
+
+// Centre node of an element of n^3 nodes: its state becomes the reference.
+__host__ __device__ constexpr int anchor_node(int n) { return (n / 2) * (1 + n + n * n); }
+
+__device__ __forceinline__ void write_anchor(const Item &it, int e, const double u[5])
+{
+    AnchorRec r;
+    r.a = make_anchor(u, it.gm1f, it.hgf, it.hglof, it.igm1f, r.ad);
+    r.pad[0] = r.pad[1] = r.pad[2] = r.pad[3] = 0.0f;
+    ((AnchorRec *)it.anc)[e] = r;
 }
 
 // ------------------------------------------------------------------ deviations of one node

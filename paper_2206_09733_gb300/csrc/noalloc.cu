@@ -123,10 +123,11 @@ static double *static_partials_ptr(int dev, cudaError_t &err)
 
 using namespace hs3d;
 
-extern "C" hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, const double *J, const double *u,
-                                                const double *dudt, double *out, void *stream)
+extern "C" hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, int nodes, const double *J,
+                                                const double *u, const double *dudt, double *out, void *stream)
 {
     if (N < 1 || N > kMaxN) return fail(HS3D_ERR_INVALID, "N=%d outside 1..%d", N, kMaxN);
+    if (nodes != HS3D_NODES_LOBATTO && nodes != HS3D_NODES_GAUSS) return fail(HS3D_ERR_INVALID, "bad nodes %d", nodes);
     if (E < 1) return fail(HS3D_ERR_INVALID, "E must be >= 1");
     if (!(gamma > 1.0)) return fail(HS3D_ERR_INVALID, "gamma must be > 1");
     if (!J || !u || !out) return fail(HS3D_ERR_INVALID, "J, u and out must not be NULL");
@@ -146,7 +147,8 @@ extern "C" hs3d_status hs3d_diagnostics_noalloc(int N, int64_t E, double gamma, 
     long long nb = (total + kStaticNodesPerSlot - 1) / kStaticNodesPerSlot;
     int nblocks = (int)(nb < 1 ? 1 : nb);
     Weights W{};
-    const Ops &o = host_ops(N);
+    // the quadrature weights of the mesh's solution nodes (Gauss-Lobatto or Gauss-Legendre)
+    const Ops &o = host_ops(N, nodes);
     for (int k = 0; k <= N; ++k) W.w[k] = o.w[k];
     cudaStream_t s = (cudaStream_t)stream;
     k_diag_partial_static<<<nblocks, kStaticThreads, 0, s>>>(N + 1, E, gamma, J, u, dudt, W, partials);

@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "lowmach.cuh"
 #include "physics.cuh"
 
 namespace hs3d {
@@ -53,6 +54,8 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b,
             float us[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) us[v] = d2f_rn(u[v]);
+            // the pass before a run also leaves each element's reference state
+            if (it.anc && p == anchor_node(n)) write_anchor(it, e, u);
             if (it.uf) {
                 float *S = it.uf + (size_t)e * 5 * n3 + p;
 #pragma unroll
@@ -167,7 +170,11 @@ cudaError_t launch_lambda(int N, int prec, int physics, const Batch &b, int slot
     return cudaGetLastError();
 }
 
-// FP32 shadow of every item's state, one thread per node.
+// n from n^3 (n <= 8).
+__device__ __forceinline__ int cbrt_int(int n3) { return n3 <= 8 ? 2 : n3 <= 27 ? 3 : n3 <= 64 ? 4 : n3 <= 125 ? 5 : n3 <= 216 ? 6 : n3 <= 343 ? 7 : 8; }
+
+// FP32 shadow of every item's state (where it has one) and the reference
+// state of every element (mixed path), one thread per node.
 __global__ void __launch_bounds__(256) k_shadow(const __grid_constant__ Batch b, int n3)
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -175,8 +182,14 @@ __global__ void __launch_bounds__(256) k_shadow(const __grid_constant__ Batch b,
     const long long ge = t / n3;
     const int p = (int)(t - ge * n3);
     const Item &it = find_item_elem(b, ge);
-    if (!it.uf) return;
     const size_t idx = (size_t)(ge - it.elem_begin) * 5 * n3 + p;
+    if (it.anc && p == anchor_node(cbrt_int(n3))) {
+        double u[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = it.u[idx + (size_t)v * n3];
+        write_anchor(it, (int)(ge - it.elem_begin), u);
+    }
+    if (!it.uf) return;
 #pragma unroll
     for (int v = 0; v < 5; ++v) it.uf[idx + (size_t)v * n3] = d2f_rn(it.u[idx + (size_t)v * n3]);
 }
@@ -186,7 +199,7 @@ cudaError_t launch_shadow(int N, const Batch &b, cudaStream_t s)
     const int n3 = (N + 1) * (N + 1) * (N + 1);
     const long long total = b.total_elems * n3;
     if (total == 0) return cudaSuccess;
-    if (b.nitems == 1 && !b.single.uf) return cudaSuccess;   // no FP32 shadow on this path
+    if (b.nitems == 1 && !b.single.uf && !b.single.anc) return cudaSuccess;   // nothing to write on this path
     k_shadow<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(b, n3);
     return cudaGetLastError();
 }

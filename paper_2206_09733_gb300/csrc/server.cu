@@ -124,12 +124,11 @@ static void release(hs3d_server *S, ServerReq *r)
 }
 
 // Build the request's slot.  Returns HS3D_OK, HS3D_ERR_NOMEM (retry later) or another error (fail it).
+// Build a popped request's mesh, state and clock (called without the server
+// lock: it touches only r and the server's private stream, so submit and
+// poll stay responsive while a large mesh is set up).
 static hs3d_status admit(hs3d_server *S, ServerReq *r)
 {
-    if (S->fault_alloc > 0) {
-        S->fault_alloc--;
-        return fail(HS3D_ERR_NOMEM, "injected allocation failure");
-    }
     hs3d_mesh_desc d = r->req.mesh;
     d.node_xyz = r->xyz.empty() ? nullptr : r->xyz.data();
     hs3d_status st = mesh_build(&d, &r->mesh);
@@ -165,7 +164,6 @@ static hs3d_status admit(hs3d_server *S, ServerReq *r)
         return cuda_fail(e, "request set-up");
     }
     r->bytes = request_bytes(r->req);
-    S->in_use += r->bytes;
     return HS3D_OK;
 }
 
@@ -356,7 +354,13 @@ static void server_loop(hs3d_server *S)
             size_t need = request_bytes(r->req);
             if (S->in_use + need > S->budget && !S->running.empty()) break;
             S->queue.pop_front();
-            hs3d_status st = admit(S, r);
+            S->in_use += need;   // reserved while the request is set up without the lock
+            const bool inject = S->fault_alloc > 0;
+            if (inject) S->fault_alloc--;
+            lk.unlock();
+            hs3d_status st = inject ? fail(HS3D_ERR_NOMEM, "injected allocation failure") : admit(S, r);
+            lk.lock();
+            if (st != HS3D_OK) S->in_use -= need;
             if (st == HS3D_ERR_NOMEM && !S->running.empty()) {
                 S->queue.push_front(r);   // wait for memory to free
                 break;

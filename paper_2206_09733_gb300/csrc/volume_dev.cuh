@@ -158,18 +158,18 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
     Anchor *ANC = (Anchor *)(selem + (size_t)le * kDevElemBlock + 10);
     float *CEN = selem + (size_t)le * kDevElemBlock + 24;            // centre metric terms (EC)
     const int ijk[3] = {p % n, (p / n) % n, p / n2};
-    constexpr int pc = (n / 2) * (1 + n + n2);   // centre node: the element's reference state
+    constexpr int pc = anchor_node(n);   // centre node: the element's reference state
 
     double u[5];
     if (valid) {
         const double *U = itp->u + (size_t)e * 5 * n3;
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = U[v * n3 + p];
-        if (p == pc) {
-            double ad[5];
-            *ANC = make_anchor(u, itp->gm1f, itp->hgf, itp->hglof, itp->igm1f, ad);
+        if (p == pc) {   // the element's reference state, left by the pass before
+            const AnchorRec &R = ((const AnchorRec *)itp->anc)[e];
+            *ANC = R.a;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) AD[v] = ad[v];
+            for (int v = 0; v < 5; ++v) AD[v] = R.ad[v];
         }
         if (BULK && p == 0) mbar_init(bulk_bar + le, 1);
     }
@@ -548,6 +548,9 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
 #pragma unroll
             for (int v = 0; v < 5; ++v) Sp[v * n3] = nf[v];
         }
+        // the reference state of the next stage (every thread of this element
+        // has read the current one: barriers lie in between)
+        if (p == pc && it.anc) write_anchor(it, e, u);
         if (lam_slot >= 0) {
             const Prim<float> qn = prim_from_f(nf, it.gm1f);
             if (!(qn.rho > 0.0f) || !(qn.p > 0.0f)) {

@@ -6,6 +6,7 @@ library's own LGL/D construction).  Mixed path (FP32 flux arithmetic, FP64
 state/geometry/RK): the errors are reported and bounded in
 test_gpu_mixed.py.
 """
+import os
 import numpy as np
 import pytest
 
@@ -437,3 +438,38 @@ def test_tgv_32cubed_N7_residual_on_a_seeded_subsample():
     print(f"32^3 N=7 subsample: tensor-core rel {rel(rtc, ref):.3e}")
     assert rel(rtc, ref) < 1e-5
     assert rel(rtc, ref) < 2 * rel(r32, ref)
+
+
+@pytest.mark.skipif(os.environ.get("HS3D_SLOW") != "1",
+                    reason="the oracle runs 100 RK3 steps of 1.7e7 nodes (minutes of CPU): set HS3D_SLOW=1")
+def test_tgv_32cubed_N7_state_after_100_steps_on_a_seeded_subsample():
+    """The 32^3-element N=7 curved TGV (standard form, Roe, BR1) after 100
+    RK3 steps: the GPU states (FP64, mixed, mixed with the tensor-core
+    contraction) against the oracle's on the 64 elements of the seeded 4x4x4
+    sub-block (the oracle integrates the full mesh, each side with its own
+    CFL time step)."""
+    E1, N, steps = 32, 7, 100
+    om, gm = pair(E1, E1, E1, N, amp=0.05)
+    a0, b0, c0 = np.random.default_rng(3).integers(0, E1 - 4 + 1, size=3)
+    sub = np.array([(a0 + i) + E1 * ((b0 + j) + E1 * (c0 + k)) for k in range(4) for j in range(4) for i in range(4)])
+    u0 = om.ic_tgv(G, 0.1)
+    results = {}
+    for prec in ("fp64", "mixed32", "mixed_tc"):
+        gc = cfgs("ns", "roe", "standard", precision=prec, Re=1600.0)[1]
+        u = dev(u0)
+        g = torch.zeros_like(u)
+        gm.clock(reset=True)
+        gm.rk3_run(gc, u, g, steps)
+        results[prec] = host(u)[sub]
+    oc = cfgs("ns", "roe", "standard", Re=1600.0)[0]
+    uo, go = u0.copy(), np.zeros_like(u0)
+    for _ in range(steps):
+        om.rk3_step(oc, uo, go)
+    ref = uo[sub]
+    for prec, a in results.items():
+        d = a - ref
+        print(f"32^3 N=7 after {steps} steps, subsample, {prec}: rel-L2 {np.linalg.norm(d) / np.linalg.norm(ref):.3e}, "
+              f"rel-Linf {np.abs(d).max() / np.abs(ref).max():.3e}")
+    assert rel(results["fp64"], ref) < TOL64
+    assert rel(results["mixed32"], ref) < 1e-5
+    assert rel(results["mixed_tc"], ref) < 1e-5

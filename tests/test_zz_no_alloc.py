@@ -65,3 +65,48 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         hs.diagnostics_noalloc(7, 16385, 1.4, u, u, out)      # 16385 * 512 > 8,388,608 nodes
     assert ei.value.status == hs.ERR_INVALID
     assert "capacity" in str(ei.value)
+
+
+def test_noalloc_on_gauss_nodes_uses_their_weights():
+    """On a mesh with Gauss-Legendre solution nodes J and u live at the Gauss
+    points: the sums take the Gauss weights, as hs3d_diagnostics does."""
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    for N in (2, 3):
+        m = hs.Mesh(4, 3, 2, N, lo=lo, hi=hi, amp=0.06, nodes="gauss")
+        cfg = hs.solver_cfg("euler", "roe", "standard", "fp64")
+        u = torch.from_numpy(random_state(m.shape, seed=10 + N)).cuda()
+        r = torch.empty_like(u)
+        m.residual(cfg, u, r)
+        _, _, J = m.geometry()
+        for dudt in (None, r):
+            ref = torch.zeros(7, dtype=torch.float64, device="cuda")
+            got = torch.full((7,), float("nan"), dtype=torch.float64, device="cuda")
+            m.diagnostics(cfg, u, ref, dudt=dudt)
+            hs.diagnostics_noalloc(N, m.E, 1.4, J, u, got, dudt=dudt, nodes="gauss")
+            torch.cuda.synchronize()
+            a, b = got.cpu().numpy(), ref.cpu().numpy()
+            assert _rel(a[:5], b[:5]) < TOL, (N, a, b)
+            if dudt is not None:
+                assert abs(a[5] - b[5]) <= TOL * b[6] and _rel(a[6:7], b[6:7]) < TOL
+        # the Lobatto weights would not do: the sums differ at O(1)
+        wrong = torch.zeros(7, dtype=torch.float64, device="cuda")
+        hs.diagnostics_noalloc(N, m.E, 1.4, J, u, wrong)
+        torch.cuda.synchronize()
+        assert _rel(wrong.cpu().numpy()[:5], b[:5]) > 1e-3
+
+
+def test_noalloc_small_call_after_a_large_one():
+    """A call that uses fewer partial-sum slots than the previous one reads
+    only the slots it wrote (the array keeps the previous call's sums)."""
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    for shape, N in (((16, 16, 8), 3), ((1, 1, 1), 2)):
+        m = hs.Mesh(*shape, N, lo=lo, hi=hi, amp=0.05)
+        cfg = hs.solver_cfg("euler", "lf", "standard", "fp64")
+        u = torch.from_numpy(random_state(m.shape, seed=3)).cuda()
+        _, _, J = m.geometry()
+        ref = torch.zeros(7, dtype=torch.float64, device="cuda")
+        got = torch.zeros(7, dtype=torch.float64, device="cuda")
+        m.diagnostics(cfg, u, ref)
+        hs.diagnostics_noalloc(N, m.E, 1.4, J, u, got)
+        torch.cuda.synchronize()
+        assert _rel(got.cpu().numpy()[:5], ref.cpu().numpy()[:5]) < TOL, shape
