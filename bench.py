@@ -236,20 +236,24 @@ def kernel_bytes(kernel, prec, E=None, n=N + 1):
     metric terms, 1/J and scratch in FP64.  Mixed path: every kernel reads
     the FP64 state (it forms the deviations from it) and FP32 copies of Ja,
     1/J and the face normals; the element kernel also reads the FP32 low
-    part of Ja (the float-float mass divergence) and the RK register; the
-    face kernel writes one flux block per side of each face; scratch in FP32."""
+    part of Ja (the float-float mass divergence), keeps the RK register in
+    FP32 and reads and rewrites each element's 112-byte reference state,
+    which the gradient kernel reads too; the face kernel writes one flux
+    block per side of each face; scratch in FP32."""
     E = EX * EY * EZ if E is None else E
     n2, n3 = n * n, n ** 3
     if prec == "fp64":
-        s, geo, jal, sides = 8, 72 + 8, 0, 1
+        s, geo, jal, sides, reg, anc = 8, 72 + 8, 0, 1, 8, 0
     else:
-        s, geo, jal, sides = 4, 36 + 4, 36, 2
-    if kernel == "volume":     # u, metrics (+ low part), 1/J, grads, this element's 6 face blocks; g in/out, u out
-        return E * (40 * n3 + (geo + jal) * n3 + 12 * n3 * s + 6 * 5 * n2 * s + 40 * 3 * n3)
+        s, geo, jal, sides, reg, anc = 4, 36 + 4, 36, 2, 4, 112
+    if kernel == "volume":     # u, metrics (+ low part), 1/J, grads, this element's 6 face blocks, reference
+        #                        state in and out; g in/out, u out
+        return E * (40 * n3 + (geo + jal) * n3 + 12 * n3 * s + 6 * 5 * n2 * s + 2 * anc + 2 * 5 * reg * n3 + 40 * n3)
     if kernel == "face":       # two FP64 traces, face normal, two gradient traces in; flux (per side) out
         return 3 * E * (2 * 40 * n2 + 3 * n2 * s + 2 * 12 * n2 * s + sides * 5 * n2 * s)
-    if kernel == "grad":       # own FP64 state, metrics, 1/J, 6 neighbour FP64 traces in; gradients out
-        return E * (40 * n3 + geo * n3 + 6 * 40 * n2 + 12 * n3 * s)
+    if kernel == "grad":       # own FP64 state, metrics, 1/J, 6 neighbour FP64 traces, reference state in;
+        #                        gradients out
+        return E * (40 * n3 + geo * n3 + 6 * 40 * n2 + anc + 12 * n3 * s)
     return 0
 
 

@@ -196,7 +196,11 @@ hs3d_status hs3d_residual(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, con
  * Williamson RK3: A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15);
  * Carpenter-Kennedy RK4: five stages with their published A_k, B_k.
  * (The name keeps "rk3" for the default scheme.)  u and g: device
- * [E][5][n3], updated in place (g need not be initialised).  dt > 0 is used
+ * [E][5][n3] doubles, updated in place.  g is the stepper's register
+ * (caller-owned scratch, need not be initialised): the FP64 path keeps it in
+ * FP64; the mixed paths, whose increments dt R are FP32 quantities, keep it
+ * as FP32 [E][5][n3] in the first half of the buffer (the state u always
+ * accumulates in FP64).  dt > 0 is used
  * as given; dt <= 0 computes dt on the device from the state at the start of
  * the step:
  *   dt = min( cfl*8/(n^2 max_nodes sum_d (|Ja^d.v| + c|Ja^d|)/J),

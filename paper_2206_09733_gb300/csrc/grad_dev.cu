@@ -37,7 +37,6 @@ constexpr int grad_dev_per_elem()
 {
     return 13 * (N + 1) * (N + 1) * (N + 1) + 24 * (N + 1) * (N + 1);
 }
-constexpr int kGradElemBlock = 24;
 
 template <int n>
 __device__ __forceinline__ int gd_face_node(int d, int end, int ta, int tb)
@@ -79,43 +78,33 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
         e = (int)(ge - itp->elem_begin);
         if (itp->clk && itp->clk->done) valid = false;
     }
-    // per-element reference-state blocks first (8-byte aligned whatever n), then the per-element staging
-    double *AD = (double *)(sE + (size_t)le * kGradElemBlock);
-    float *ja = sE + (size_t)epb * kGradElemBlock + (size_t)le * PER;
+    float *ja = sE + (size_t)le * PER;
     float *q = ja + 9 * n3;
     float *qn = q + 4 * n3;
-    Anchor *ANC = (Anchor *)((float *)AD + 10);
     float qin[4];
-    constexpr int pc = anchor_node(n);   // the element's centre node: its reference state
-    double uo[5];
-    if (valid) {
-        const double *U = itp->u + (size_t)e * 5 * n3;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) uo[v] = U[v * n3 + p];
-        if (p == pc) {   // the element's reference state, left by the pass before
-            const AnchorRec &R = ((const AnchorRec *)itp->anc)[e];
-            *ANC = R.a;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) AD[v] = R.ad[v];
-        }
-        // the element's barrier is initialised before any of its threads polls it
-        if (BULK && p == 0) mbar_init(bulk_bar + le, 1);
-    }
-    __syncthreads();
     if (valid) {
         const Item &it = *itp;
+        double uo[5];
+        const double *U = it.u + (size_t)e * 5 * n3;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) uo[v] = U[v * n3 + p];
+        // the element's reference state, left by the pass before
+        const AnchorRec R = load_anchor(it.anc, e);
         if constexpr (BULK) {
+            // one thread initialises, arms and fills the element's barrier; the
+            // others poll it only after the block barrier below
             if (p == 0) {
                 unsigned long long *bar = bulk_bar + le;
+                mbar_init(bar, 1);
                 mbar_arrive_expect_tx(bar, 9 * n3 * 4);
                 bulk_g2s(ja, it.Jaf + (size_t)e * 9 * n3, 9 * n3 * 4, bar);
             }
         }
         const float gm1 = it.gm1f;
-        const Anchor A = *ANC;
+        const Anchor A = R.a;
         double ad[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) ad[v] = AD[v];
+        for (int v = 0; v < 5; ++v) ad[v] = R.ad[v];
         const float Tb = A.p * __fdividef(1.0f, A.rho);
         const float rT = fmaf(-Tb, A.rho, A.p);
         constexpr int IT = (6 * n2 + n3 - 1) / n3;
@@ -168,17 +157,18 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
             const float *JA = it.Jaf + (size_t)e * 9 * n3 + p;
 #pragma unroll
             for (int k = 0; k < 9; ++k) ja[k * n3 + p] = JA[k * n3];
-        } else {
-            if (!mbar_wait(bulk_bar + le, 0, kBulkWaitPolls)) {
-                // a wait that ran out of polls poisons the gradients and flags the solve
-#pragma unroll
-                for (int v = 0; v < 4; ++v) qin[v] = NAN;
-                if (it.clk) it.clk->bad = 2;
-            }
         }
     }
     __syncthreads();
     if (!valid) return;
+    if constexpr (BULK) {
+        if (!mbar_wait(bulk_bar + le, 0, kBulkWaitPolls)) {
+            // a wait that ran out of polls poisons the gradients and flags the solve
+#pragma unroll
+            for (int v = 0; v < 4; ++v) qin[v] = NAN;
+            if (itp->clk) itp->clk->bad = 2;
+        }
+    }
     const int ijk[3] = {p % n, (p / n) % n, p / n2};
     float acc[12];
 #pragma unroll
@@ -241,7 +231,7 @@ static cudaError_t grad_dev_launch(const Batch &b, cudaStream_t s)
     int epb = elems_per_block_p(N, HS3D_MIXED32, 0);
     if (epb * n3 > grad_dev_threads<N>()) epb = grad_dev_threads<N>() / n3;
     const int threads = epb * n3;
-    const size_t smem = sizeof(float) * (((n * n + 3) & ~3) + (size_t)epb * (grad_dev_per_elem<N>() + kGradElemBlock));
+    const size_t smem = sizeof(float) * (((n * n + 3) & ~3) + (size_t)epb * grad_dev_per_elem<N>());
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;

@@ -181,6 +181,18 @@ struct AnchorRec {
 };
 static_assert(sizeof(AnchorRec) == 112, "AnchorRec layout");
 
+// Every thread of an element loads its record (seven 16-byte loads, the
+// same addresses across the element: broadcast from L1).
+__device__ __forceinline__ AnchorRec load_anchor(const void *anc, int e)
+{
+    AnchorRec r;
+    const float4 *src = (const float4 *)((const AnchorRec *)anc + e);
+    float4 *dst = (float4 *)&r;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) dst[k] = __ldg(src + k);
+    return r;
+}
+
 // Centre node of an element of n^3 nodes: its state becomes the reference.
 __host__ __device__ constexpr int anchor_node(int n) { return (n / 2) * (1 + n + n * n); }
 

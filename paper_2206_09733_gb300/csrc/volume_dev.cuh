@@ -86,13 +86,13 @@ __host__ __device__ constexpr size_t dev_rk_offset(int epb)
     return (sizeof(float) * fl + 15) & ~(size_t)15;
 }
 
-// RK staging: standard form g [epb][5 n3] (FP64), then 1/J [epb][n3] (FP32).
+// RK staging: standard form g [epb][5 n3] (FP32), then 1/J [epb][n3] (FP32).
 template <int N, bool NS, int FORM>
 __host__ __device__ constexpr size_t dev_smem_bytes(int epb)
 {
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
     constexpr bool SG = (FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC);
-    return dev_rk_offset<N, NS, FORM>(epb) + (size_t)epb * n3 * ((SG ? 40 : 0) + 4);
+    return dev_rk_offset<N, NS, FORM>(epb) + (size_t)epb * n3 * ((SG ? 20 : 0) + 4);
 }
 
 template <int n>
@@ -135,7 +135,7 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
     float *sbuf = selem + (size_t)epb * kDevElemBlock;
     float *sface = sbuf + (size_t)epb * PER * n3;
     float *spair = sface + (size_t)epb * 30 * n2;
-    double *sG = (double *)(smem_raw + dev_rk_offset<N, NS, FORM>(epb));
+    float *sG = (float *)(smem_raw + dev_rk_offset<N, NS, FORM>(epb));
     float *sIJ = (float *)(sG + (STD ? (size_t)epb * 5 * n3 : 0));
     for (int t = threadIdx.x; t < n2; t += blockDim.x) {
         sD[t] = ops->Df[t];
@@ -161,19 +161,21 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
     constexpr int pc = anchor_node(n);   // centre node: the element's reference state
 
     double u[5];
+    AnchorRec R;   // the element's reference state, left by the pass before
     if (valid) {
         const double *U = itp->u + (size_t)e * 5 * n3;
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = U[v * n3 + p];
-        if (p == pc) {   // the element's reference state, left by the pass before
-            const AnchorRec &R = ((const AnchorRec *)itp->anc)[e];
+        R = load_anchor(itp->anc, e);
+        if (p == pc) {   // a copy for the pair phase and the surface term (read after later barriers)
             *ANC = R.a;
 #pragma unroll
             for (int v = 0; v < 5; ++v) AD[v] = R.ad[v];
         }
+        // the thread that initialises the element's barrier is the one that arms it
+        // and issues the copies; the others poll it only after the staging barrier
         if (BULK && p == 0) mbar_init(bulk_bar + le, 1);
     }
-    __syncthreads();
     float V[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     float Ch = 0.0f, Cl = 0.0f;   // float-float C (low-Mach forms)
     float Hb = 0.0f;
@@ -182,6 +184,7 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
         const Nbrs nb = elem_nbrs(e, it.ex, it.ey, it.ez);
         // face blocks of this element's side of its six faces, 1/J, g
         {
+            const float *gf = (const float *)it.g;   // the RK register: FP32 on this path
             const float *FS = (const float *)it.fstar;
             size_t blk[6];
 #pragma unroll
@@ -194,28 +197,28 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
             if constexpr (BULK) {
                 if (p == 0) {
                     unsigned long long *bar = bulk_bar + le;
-                    constexpr unsigned fb = 5 * n2 * 4, gb = 5 * n3 * 8, jb = n3 * 4;
+                    constexpr unsigned fb = 5 * n2 * 4, gb = 5 * n3 * 4, jb = n3 * 4;
                     mbar_arrive_expect_tx(bar, 6 * fb + jb + (STD && stage > 0 ? gb : 0));
 #pragma unroll
                     for (int slot = 0; slot < 6; ++slot) bulk_g2s(F6 + slot * 5 * n2, FS + blk[slot], fb, bar);
                     bulk_g2s(sIJ + (size_t)le * n3, it.invJf + (size_t)e * n3, jb, bar);
-                    if (STD && stage > 0) bulk_g2s(sG + (size_t)le * 5 * n3, it.g + (size_t)e * 5 * n3, gb, bar);
+                    if (STD && stage > 0) bulk_g2s(sG + (size_t)le * 5 * n3, gf + (size_t)e * 5 * n3, gb, bar);
                 }
             } else {
 #pragma unroll
                 for (int slot = 0; slot < 6; ++slot) cp_async_block<float>(F6 + slot * 5 * n2, FS + blk[slot], 5 * n2, p, n3);
                 cp_async_block<float>(sIJ + (size_t)le * n3, it.invJf + (size_t)e * n3, n3, p, n3);
-                if (STD && stage > 0) cp_async_block<double>(sG + (size_t)le * 5 * n3, it.g + (size_t)e * 5 * n3, 5 * n3, p, n3);
+                if (STD && stage > 0) cp_async_block<float>(sG + (size_t)le * 5 * n3, gf + (size_t)e * 5 * n3, 5 * n3, p, n3);
             }
             if constexpr (!STD) {
-                if (stage > 0) prefetch_l2_block(it.g + (size_t)e * 5 * n3, sizeof(double) * 5 * n3, p, n3);
+                if (stage > 0) prefetch_l2_block(gf + (size_t)e * 5 * n3, sizeof(float) * 5 * n3, p, n3);
             }
         }
         const float gm1 = it.gm1f, hg = it.hgf;
-        const Anchor A = *ANC;
+        const Anchor A = R.a;
         double ad[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) ad[v] = AD[v];
+        for (int v = 0; v < 5; ++v) ad[v] = R.ad[v];
         Hb = A.H;
         const double dm64[3] = {u[1] - ad[1], u[2] - ad[2], u[3] - ad[3]};
         const Dev dv = make_dev_f(dev_round(u[0] - ad[0]), dev_round(dm64[0]), dev_round(dm64[1]),
@@ -528,20 +531,26 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
 #pragma unroll
         for (int v = 0; v < 5; ++v) O[v * n3] = f2d_exact(-V[v] * ijf);
     } else {
+        // the register g holds FP32 increments (dt R is an FP32 quantity here);
+        // the state accumulates in FP64: u <- u + B g, one FP64 FMA a variable
         const float sdt = d2f_rn(it.clk->dt) * ijf;
-        double *Gp = it.g + (size_t)e * 5 * n3 + p;
+        const float rkAf = d2f_rn(rkA);
+        float *Gp = (float *)it.g + (size_t)e * 5 * n3 + p;
         double *Up = it.u + (size_t)e * 5 * n3 + p;
-        float nf[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-            const double inc = f2d_exact(-V[v] * sdt);
-            double gv;
+            const float inc = -V[v] * sdt;
+            float gv;
             if (stage == 0) gv = inc;
-            else gv = fma(rkA, STD ? sG[(size_t)le * 5 * n3 + v * n3 + p] : Gp[v * n3], inc);
+            else gv = fmaf(rkAf, STD ? sG[(size_t)le * 5 * n3 + v * n3 + p] : Gp[v * n3], inc);
             Gp[v * n3] = gv;
-            u[v] = fma(rkB, gv, u[v]);
+            u[v] = fma(rkB, f2d_exact(gv), u[v]);
             Up[v * n3] = u[v];
-            nf[v] = d2f_rn(u[v]);
+        }
+        float nf[5];
+        if (it.uf || lam_slot >= 0) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) nf[v] = d2f_rn(u[v]);
         }
         if (it.uf) {
             float *Sp = it.uf + (size_t)e * 5 * n3 + p;

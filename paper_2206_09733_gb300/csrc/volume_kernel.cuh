@@ -126,9 +126,10 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
             }
         }
     } else {
-        // mixed path: the increment dt R = -dt V / J is formed in FP32 and
-        // widened exactly; the register and the state accumulate in FP64
-        // (two FP64 FMAs per variable).
+        // mixed path: the increment dt R = -dt V / J is formed in FP32; the
+        // register g holds FP32 increments ([E][5][n3] floats in the first half
+        // of the caller's buffer) and the state accumulates in FP64 (one FP64
+        // FMA per variable).
         const float ijf = sIJ ? sIJ[p] : it.invJf[(size_t)e * n3 + p];
         if (stage < 0) {
             double *O = it.out + (size_t)e * 5 * n3 + p;
@@ -136,16 +137,17 @@ __device__ __forceinline__ void node_update(const Item &it, int e, int p, int n3
             for (int v = 0; v < 5; ++v) O[v * n3] = f2d_exact(-(float)V[v] * ijf);
         } else {
             const float sdt = d2f_rn(it.clk->dt) * ijf;
-            const double A = rkA, B = rkB;
-            double *Gp = it.g + (size_t)e * 5 * n3 + p;
+            const float A = d2f_rn(rkA);
+            const double B = rkB;
+            float *Gp = (float *)it.g + (size_t)e * 5 * n3 + p;
             double *Up = it.u + (size_t)e * 5 * n3 + p;
             float *Sp = it.uf + (size_t)e * 5 * n3 + p;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-                const double inc = f2d_exact(-(float)V[v] * sdt);
-                const double gv = (stage == 0) ? inc : fma(A, sG ? sG[v * n3 + p] : Gp[v * n3], inc);
+                const float inc = -(float)V[v] * sdt;
+                const float gv = (stage == 0) ? inc : fmaf(A, Gp[v * n3], inc);
                 Gp[v * n3] = gv;
-                u[v] = fma(B, gv, u[v]);
+                u[v] = fma(B, f2d_exact(gv), u[v]);
                 Up[v * n3] = u[v];
                 nf[v] = d2f_rn(u[v]);
                 Sp[v * n3] = nf[v];
