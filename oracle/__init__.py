@@ -104,6 +104,8 @@ def lib():
             L.orc_mortar_matrices.argtypes = [C.c_int, C.c_int, _dp, _dp]
             L.orc_pmesh_create.argtypes = [C.POINTER(_Box), C.c_void_p]
             L.orc_pmesh_create.restype = C.c_void_p
+            L.orc_pmesh_create3.argtypes = [C.POINTER(_Box), C.c_void_p]
+            L.orc_pmesh_create3.restype = C.c_void_p
             L.orc_pmesh_destroy.argtypes = [C.c_void_p]
             L.orc_pmesh_Ngeo.argtypes = [C.c_void_p]
             L.orc_pmesh_arrays.argtypes = [C.c_void_p] + [C.c_void_p] * 5
@@ -383,20 +385,35 @@ def mortar_matrices(Ns: int, Nm: int):
 
 class PMesh:
     """Oracle mesh of an ex*ey*ez periodic box whose elements carry their own
-    degree (Gauss-Lobatto nodes), coupled by mortars.
+    degrees (Gauss-Lobatto nodes), coupled by mortars.  `degrees` is one
+    degree per element (isotropic, shape (E,)) or one per element and
+    reference direction (anisotropic, shape (E, 3): P_x, P_y, P_z).
 
-    The state is one flat float64 vector of element blocks [5, n_e, n_e, n_e]
-    in element order; `block(u, e)` views element e's block."""
+    The state is one flat float64 vector of element blocks
+    [5, n_z, n_y, n_x] in element order; `block(u, e)` views element e's
+    block."""
 
     def __init__(self, ex, ey, ez, degrees, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0):
         self.ex, self.ey, self.ez = ex, ey, ez
         self.E = ex * ey * ez
-        deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32).reshape(-1))
-        assert deg.size == self.E
-        self.degrees = deg.copy()
+        d = np.asarray(degrees, dtype=np.int32)
+        if d.ndim == 2:
+            assert d.shape == (self.E, 3)
+            deg3 = np.ascontiguousarray(d)
+        else:
+            d = d.reshape(-1)
+            assert d.size == self.E
+            deg3 = np.ascontiguousarray(np.repeat(d[:, None], 3, axis=1))
+        self.degrees3 = deg3.copy()
+        self.isotropic = bool(np.all(deg3 == deg3[:, :1]))
+        self.degrees = deg3[:, 0].copy() if self.isotropic else None
         self.lo, self.hi, self.amp = tuple(lo), tuple(hi), amp
         box = _Box(ex, ey, ez, 0, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), amp, 0)
-        self._h = lib().orc_pmesh_create(C.byref(box), deg.ctypes.data)
+        if d.ndim == 2:
+            self._h = lib().orc_pmesh_create3(C.byref(box), deg3.ctypes.data)
+        else:
+            dd = np.ascontiguousarray(d)
+            self._h = lib().orc_pmesh_create(C.byref(box), dd.ctypes.data)
         if not self._h:
             raise ValueError("bad p-mesh description")
         self.Ngeo = lib().orc_pmesh_Ngeo(self._h)
@@ -417,23 +434,30 @@ class PMesh:
             self._h = None
 
     def n(self, e):
-        return int(self.degrees[e]) + 1
+        """Nodes per direction of an isotropic element."""
+        nx, ny, nz = self.shape3(e)
+        assert nx == ny == nz
+        return nx
+
+    def shape3(self, e):
+        """(n_x, n_y, n_z) of element e."""
+        return tuple(int(x) + 1 for x in self.degrees3[e])
+
+    def _dims(self, e):
+        nx, ny, nz = self.shape3(e)
+        return (nz, ny, nx)
 
     def block(self, u, e):
-        n = self.n(e)
-        return u[self.off[e]:self.off[e + 1]].reshape(5, n, n, n)
+        return u[self.off[e]:self.off[e + 1]].reshape(5, *self._dims(e))
 
     def X(self, e):
-        n = self.n(e)
-        return self._X[3 * self.noff[e]:3 * self.noff[e + 1]].reshape(3, n, n, n)
+        return self._X[3 * self.noff[e]:3 * self.noff[e + 1]].reshape(3, *self._dims(e))
 
     def Ja(self, e):
-        n = self.n(e)
-        return self._Ja[9 * self.noff[e]:9 * self.noff[e + 1]].reshape(3, 3, n, n, n)
+        return self._Ja[9 * self.noff[e]:9 * self.noff[e + 1]].reshape(3, 3, *self._dims(e))
 
     def J(self, e):
-        n = self.n(e)
-        return self._J[self.noff[e]:self.noff[e + 1]].reshape(n, n, n)
+        return self._J[self.noff[e]:self.noff[e + 1]].reshape(*self._dims(e))
 
     def neighbour(self, e, d, side):
         ab = [e % self.ex, (e // self.ex) % self.ey, e // (self.ex * self.ey)]

@@ -1534,42 +1534,55 @@ void orc_integrals(const orc_mesh *m, double g, const double *u, const double *d
 }
 
 /* ------------------------------------------------------------------------ */
-/* Per-element polynomial degree with mortar coupling (Sec. 3.6)             */
+/* Per-element, per-direction polynomial degree with mortar coupling         */
+/* (Sec. 3.6)                                                                */
 /* ------------------------------------------------------------------------ */
 /*
- * Element e of the ex*ey*ez periodic box carries its own degree N_e in 1..7
- * (Gauss-Lobatto nodes, isotropic).  Sec. 3.6 names the two ingredients:
+ * Element e of the ex*ey*ez periodic box carries its own degrees
+ * (P_x, P_y, P_z) in 1..7, one per reference direction (Sec. 3.6: the order
+ * may differ per element and per direction, anisotropic p-adaptation);
+ * Gauss-Lobatto nodes n_d = P_d + 1 per direction, n_x n_y n_z per element,
+ * node (i, j, k) at i + n_x (j + n_y k).  An isotropic element has
+ * P_x = P_y = P_z.  Sec. 3.6 names the two ingredients:
  *
  * Geometry (the rules of Kopriva et al. 2019 for p-non-conforming faces).
- *   Every element's map is the polynomial of degree Ngeo = max(1, floor(Nmin/2))
- *   (Nmin = smallest degree of the mesh) that interpolates the box map (with
- *   its perturbation) at the element's Gauss-Lobatto points of degree Ngeo; X is
- *   that polynomial at the element's own nodes and the metric terms are the
- *   curl form at the element's own degree.  The products X_l dX_m of a
- *   degree-Ngeo map have degree 2 Ngeo <= Nmin per direction, so every
- *   element interpolates them exactly: the face metric terms are the same
- *   polynomial seen from both sides of a face, whatever the two degrees.
- *   With Nmin = 1 that holds only for an affine map, so amp must be 0.
+ *   Every element's map is the polynomial of degree Ngeo = max(1, floor(Pmin/2))
+ *   per direction (Pmin = smallest degree of the mesh, over elements and
+ *   directions) that interpolates the box map (with its perturbation) at the
+ *   element's Gauss-Lobatto points of degree Ngeo; X is that polynomial at the
+ *   element's own nodes and the metric terms are the curl form with the
+ *   element's own derivative matrix in each direction.  The products
+ *   X_l dX_m of a degree-Ngeo map have degree 2 Ngeo <= Pmin per direction,
+ *   so every element interpolates them exactly: the face metric terms are the
+ *   same polynomial seen from both sides of a face, whatever the degrees.
+ *   With Pmin = 1 that holds only for an affine map, so amp must be 0.
  *
  * Coupling (the mortar method of Kopriva et al. 2002, which Sec. 3.6 notes
- * does not keep entropy stability).  A face between degrees N_L and N_R
- * carries a mortar of degree N_M = max(N_L, N_R) on its Gauss-Lobatto points:
+ * does not keep entropy stability).  The face normal to direction d between
+ * L (its +d face) and R (its -d face) has the tangential directions d0 < d1
+ * with degrees (P_L[d0], P_L[d1]) and (P_R[d0], P_R[d1]); it carries a
+ * mortar of degree M_k = max(P_L[dk], P_R[dk]) in tangential direction k, on
+ * the Gauss-Lobatto points of those degrees:
  *   - the conservative traces of both sides (and, for Navier-Stokes, their
  *     gradients) are interpolated to the mortar points (tensor-product
- *     Lagrange interpolation in the two face directions);
+ *     Lagrange interpolation, each tangential direction with its own pair of
+ *     degrees);
  *   - the numerical flux s F*(u_L, u_R; n) - (F_v(L) + F_v(R)).Sn/2 is
- *     evaluated at the mortar points, with Sn the face metric Ja^d of the
- *     side of degree N_M (of the minus side L when the degrees agree);
+ *     evaluated at the mortar points, with Sn the face metric Ja^d of a side
+ *     whose tangential degrees are the mortar's (L when both are; R when only
+ *     R is); when neither side's are (e.g. (3,5) against (5,3)) it is L's face
+ *     metric interpolated to the mortar points, which is exact: the face
+ *     metric has degree <= Pmin in each direction;
  *   - the BR1 interface value q* = (q(u_L) + q(u_R))/2 likewise;
  *   - each side receives the L2 projection of the mortar function onto its
- *     own degree, P = M_s^{-1} S with M_s[i][k] = int l_i l_k and
+ *     own tangential degrees, P = M_s^{-1} S with M_s[i][k] = int l_i l_k and
  *     S[i][j] = int l_i^s l_j^M integrated exactly (Gauss quadrature with
- *     N_M + 1 points), applied in both face directions; the side of degree
- *     N_M receives the mortar values themselves.
+ *     M + 1 points), applied in both face directions; a direction in which
+ *     the side's degree is the mortar's takes the identity.
  * With equal degrees on every face this is the conforming method (the
  * mortar is the face itself).
  *
- * State layout: element blocks [5][n_e^3] in element order, block e at
+ * State layout: element blocks [5][n_x n_y n_z] in element order, block e at
  * off[e] doubles.
  */
 #define PM_MAXN 7
@@ -1577,16 +1590,84 @@ void orc_integrals(const orc_mesh *m, double g, const double *u, const double *d
 typedef struct {
     orc_box box;       /* ex, ey, ez, lo, hi, amp (N and nodes unused) */
     int E, Nmin, Nmax, Ngeo;
-    int *N;            /* [E] degree of each element */
-    long long *off;    /* [E+1] state offsets: element e at off[e], 5 n_e^3 values */
-    long long *noff;   /* [E+1] node offsets: element e's nodes at noff[e], n_e^3 of them */
-    double *X;         /* [3][n_e^3] per element at 3 noff[e] */
-    double *Ja;        /* [3 d][3 c][n_e^3] per element at 9 noff[e] */
-    double *J;         /* [n_e^3] per element at noff[e] */
+    int *P;            /* [3E] degree of element e in direction d at P[3e + d] */
+    long long *off;    /* [E+1] state offsets: element e at off[e], 5 n_x n_y n_z values */
+    long long *noff;   /* [E+1] node offsets: element e's nodes at noff[e] */
+    double *X;         /* [3][nodes_e] per element at 3 noff[e] */
+    double *Ja;        /* [3 d][3 c][nodes_e] per element at 9 noff[e] */
+    double *J;         /* [nodes_e] per element at noff[e] */
     double xi[PM_MAXN + 1][16], w[PM_MAXN + 1][16], D[PM_MAXN + 1][256];
     double Pi[PM_MAXN + 1][PM_MAXN + 1][64];  /* Pi[s][m][a*ns + i] = l_i^{(s)}(xi_a^{(m)}), s <= m */
     double Pr[PM_MAXN + 1][PM_MAXN + 1][64];  /* Pr[s][m][i*nm + j]: L2 projection, degree m -> s, s <= m */
 } orc_pmesh;
+
+/* Nodes per direction of element e, and their product. */
+static void pm_shape(const orc_pmesh *m, int e, int n[3])
+{
+    for (int d = 0; d < 3; ++d) n[d] = m->P[3 * e + d] + 1;
+}
+static int pm_nodes(const int n[3]) { return n[0] * n[1] * n[2]; }
+static int aidx(const int n[3], int i, int j, int k) { return i + n[0] * (j + n[1] * k); }
+
+/* Index of the node with index mm along direction d, the other two indices
+ * taken from (i, j, k). */
+static int anode_along(const int n[3], int d, int mm, int i, int j, int k)
+{
+    if (d == 0) return aidx(n, mm, j, k);
+    if (d == 1) return aidx(n, i, mm, k);
+    return aidx(n, i, j, mm);
+}
+
+/* Derivative along reference direction d of a nodal field f of one element
+ * with n[d] nodes in that direction, D the derivative matrix of degree n[d]-1:
+ * (D_d f)_ijk = sum_m D[ind_d][m] f(node with ind_d -> m). */
+static double adir_derivative(const int n[3], const double *D, const double *f, int d, int i, int j, int k)
+{
+    int row = (d == 0) ? i : (d == 1) ? j : k;
+    double s = 0.0;
+    for (int mm = 0; mm < n[d]; ++mm) s += D[row * n[d] + mm] * f[anode_along(n, d, mm, i, j, k)];
+    return s;
+}
+
+/* The curl-form metric terms and J of one element with n[d] nodes per
+ * direction (the formulas of orc_metrics, each derivative along d with the
+ * derivative matrix Dd[d] of that direction's degree). */
+static int ametrics(const int n[3], const double *const Dd[3], const double *X, double *Ja, double *J)
+{
+    int n3 = pm_nodes(n);
+    double *tmp = (double *)malloc(sizeof(double) * n3 * 2);
+    double *dX = (double *)malloc(sizeof(double) * n3 * 9);   /* dX[c][d][node] */
+    if (!tmp || !dX) { free(tmp); free(dX); return -1; }
+    for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < n[2]; ++k) for (int j = 0; j < n[1]; ++j) for (int i = 0; i < n[0]; ++i)
+        dX[(c * 3 + d) * n3 + aidx(n, i, j, k)] = adir_derivative(n, Dd[d], X + c * n3, d, i, j, k);
+    for (int p = 0; p < n3; ++p) {
+        double a[3][3];
+        for (int d = 0; d < 3; ++d) for (int c = 0; c < 3; ++c) a[d][c] = dX[(c * 3 + d) * n3 + p];
+        double cx = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+        double cy = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+        double cz = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+        J[p] = a[0][0] * cx + a[0][1] * cy + a[0][2] * cz;
+    }
+    for (int i = 0; i < 3; ++i) {
+        int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        for (int c = 0; c < 3; ++c) {
+            int mc = (c + 1) % 3, l = (c + 2) % 3;
+            for (int p = 0; p < n3; ++p) {
+                tmp[p] = X[l * n3 + p] * dX[(mc * 3 + i1) * n3 + p];
+                tmp[n3 + p] = X[l * n3 + p] * dX[(mc * 3 + i2) * n3 + p];
+            }
+            for (int k = 0; k < n[2]; ++k) for (int j = 0; j < n[1]; ++j) for (int ii = 0; ii < n[0]; ++ii) {
+                int p = aidx(n, ii, j, k);
+                Ja[(i * 3 + c) * n3 + p] = adir_derivative(n, Dd[i2], tmp, i2, ii, j, k)
+                                         - adir_derivative(n, Dd[i1], tmp + n3, i1, ii, j, k);
+            }
+        }
+    }
+    free(tmp); free(dX);
+    return 0;
+}
 
 /* Interpolation from degree Ns to degree Nm >= Ns (Gauss-Lobatto points) and
  * the L2 projection back, as nm x ns and ns x nm row-major matrices.  Equal
@@ -1665,18 +1746,19 @@ static void box_map_point(const orc_box *b, int e, const double r[3], double X[3
 void orc_pmesh_destroy(orc_pmesh *m)
 {
     if (!m) return;
-    free(m->N); free(m->off); free(m->noff); free(m->X); free(m->Ja); free(m->J); free(m);
+    free(m->P); free(m->off); free(m->noff); free(m->X); free(m->Ja); free(m->J); free(m);
 }
 
-orc_pmesh *orc_pmesh_create(const orc_box *b, const int *deg)
+/* Degrees deg3[3e + d] (element e, direction d), each in 1..PM_MAXN. */
+orc_pmesh *orc_pmesh_create3(const orc_box *b, const int *deg3)
 {
-    if (b->ex < 1 || b->ey < 1 || b->ez < 1 || !deg) return NULL;
+    if (b->ex < 1 || b->ey < 1 || b->ez < 1 || !deg3) return NULL;
     int E = b->ex * b->ey * b->ez;
     int Nmin = 99, Nmax = 0;
-    for (int e = 0; e < E; ++e) {
-        if (deg[e] < 1 || deg[e] > PM_MAXN) return NULL;
-        if (deg[e] < Nmin) Nmin = deg[e];
-        if (deg[e] > Nmax) Nmax = deg[e];
+    for (int t = 0; t < 3 * E; ++t) {
+        if (deg3[t] < 1 || deg3[t] > PM_MAXN) return NULL;
+        if (deg3[t] < Nmin) Nmin = deg3[t];
+        if (deg3[t] > Nmax) Nmax = deg3[t];
     }
     if (Nmin == 1 && b->amp != 0.0) return NULL;
     orc_pmesh *m = (orc_pmesh *)calloc(1, sizeof(orc_pmesh));
@@ -1686,16 +1768,17 @@ orc_pmesh *orc_pmesh_create(const orc_box *b, const int *deg)
     m->Nmin = Nmin;
     m->Nmax = Nmax;
     m->Ngeo = Nmin / 2 >= 1 ? Nmin / 2 : 1;
-    m->N = (int *)malloc(sizeof(int) * E);
+    m->P = (int *)malloc(sizeof(int) * 3 * E);
     m->off = (long long *)malloc(sizeof(long long) * (E + 1));
     m->noff = (long long *)malloc(sizeof(long long) * (E + 1));
-    if (!m->N || !m->off || !m->noff) { orc_pmesh_destroy(m); return NULL; }
+    if (!m->P || !m->off || !m->noff) { orc_pmesh_destroy(m); return NULL; }
+    memcpy(m->P, deg3, sizeof(int) * 3 * E);
     m->off[0] = m->noff[0] = 0;
     for (int e = 0; e < E; ++e) {
-        int n = deg[e] + 1;
-        m->N[e] = deg[e];
-        m->noff[e + 1] = m->noff[e] + (long long)n * n * n;
-        m->off[e + 1] = m->off[e] + 5LL * n * n * n;
+        int n[3];
+        pm_shape(m, e, n);
+        m->noff[e + 1] = m->noff[e] + pm_nodes(n);
+        m->off[e + 1] = m->off[e] + 5LL * pm_nodes(n);
     }
     for (int N = 1; N <= PM_MAXN; ++N) {
         orc_lgl(N, m->xi[N], m->w[N]);
@@ -1710,7 +1793,9 @@ orc_pmesh *orc_pmesh_create(const orc_box *b, const int *deg)
     if (!m->X || !m->Ja || !m->J) { orc_pmesh_destroy(m); return NULL; }
     int G = m->Ngeo, ng = G + 1;
     for (int e = 0; e < E; ++e) {
-        int N = m->N[e], n = N + 1, n3 = n * n * n;
+        int n[3];
+        pm_shape(m, e, n);
+        int n3 = pm_nodes(n);
         /* the map at the degree-Ngeo points, then its interpolant at the own nodes */
         double Xg[3][512];
         for (int k = 0; k < ng; ++k) for (int j = 0; j < ng; ++j) for (int i = 0; i < ng; ++i) {
@@ -1718,18 +1803,36 @@ orc_pmesh *orc_pmesh_create(const orc_box *b, const int *deg)
             box_map_point(b, e, r, x);
             for (int c = 0; c < 3; ++c) Xg[c][node_index(ng, i, j, k)] = x[c];
         }
-        double L[16][16];   /* L[t][s] = l_s^{(Ngeo)}(xi_t^{(N)}) */
-        for (int t = 0; t < n; ++t) orc_lagrange_at(ng, m->xi[G], m->xi[N][t], L[t]);
+        double L[3][16][16];   /* L[d][t][s] = l_s^{(Ngeo)}(xi_t^{(P_d)}) */
+        for (int d = 0; d < 3; ++d)
+            for (int t = 0; t < n[d]; ++t) orc_lagrange_at(ng, m->xi[G], m->xi[n[d] - 1][t], L[d][t]);
         double *Xe = m->X + 3 * m->noff[e];
         for (int c = 0; c < 3; ++c)
-            for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < n[2]; ++k) for (int j = 0; j < n[1]; ++j) for (int i = 0; i < n[0]; ++i) {
                 double acc = 0.0;
                 for (int kk = 0; kk < ng; ++kk) for (int jj = 0; jj < ng; ++jj) for (int ii = 0; ii < ng; ++ii)
-                    acc += L[i][ii] * L[j][jj] * L[k][kk] * Xg[c][node_index(ng, ii, jj, kk)];
-                Xe[c * n3 + node_index(n, i, j, k)] = acc;
+                    acc += L[0][i][ii] * L[1][j][jj] * L[2][k][kk] * Xg[c][node_index(ng, ii, jj, kk)];
+                Xe[c * n3 + aidx(n, i, j, k)] = acc;
             }
-        orc_metrics(1, N, m->D[N], Xe, m->Ja + 9 * m->noff[e], m->J + m->noff[e]);
+        const double *Dd[3] = {m->D[n[0] - 1], m->D[n[1] - 1], m->D[n[2] - 1]};
+        if (ametrics(n, Dd, Xe, m->Ja + 9 * m->noff[e], m->J + m->noff[e]) != 0) {
+            orc_pmesh_destroy(m);
+            return NULL;
+        }
     }
+    return m;
+}
+
+/* Isotropic degrees: deg[e] in every direction. */
+orc_pmesh *orc_pmesh_create(const orc_box *b, const int *deg)
+{
+    if (b->ex < 1 || b->ey < 1 || b->ez < 1 || !deg) return NULL;
+    int E = b->ex * b->ey * b->ez;
+    int *deg3 = (int *)malloc(sizeof(int) * 3 * E);
+    if (!deg3) return NULL;
+    for (int e = 0; e < E; ++e) deg3[3 * e] = deg3[3 * e + 1] = deg3[3 * e + 2] = deg[e];
+    orc_pmesh *m = orc_pmesh_create3(b, deg3);
+    free(deg3);
     return m;
 }
 
@@ -1748,68 +1851,77 @@ void orc_pmesh_arrays(const orc_pmesh *m, long long *off, long long *noff, doubl
     if (J) memcpy(J, m->J, sizeof(double) * nodes);
 }
 
-/* nf fields of one element ([nf][n^3] from base) on its face xi_d = end:
- * out[v][ta + n tb], (ta, tb) the face's tangential indices in increasing
- * direction order. */
-static void pm_face_values(const double *base, int nf, int n, int d, int end, double *out)
+/* nf fields of one element ([nf][nodes] from base, n[d] nodes per direction)
+ * on its face xi_d = end: out[v][ta + n[d0] tb], (ta, tb) the face's
+ * tangential indices in increasing direction order. */
+static void pm_face_values(const double *base, int nf, const int n[3], int d, int end, double *out)
 {
-    int n3 = n * n * n, d0, d1;
+    int n3 = pm_nodes(n), d0, d1;
     face_dirs(d, &d0, &d1);
+    int f2 = n[d0] * n[d1];
     for (int v = 0; v < nf; ++v)
-        for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+        for (int tb = 0; tb < n[d1]; ++tb) for (int ta = 0; ta < n[d0]; ++ta) {
             int idx[3];
             idx[d] = end;
             idx[d0] = ta;
             idx[d1] = tb;
-            out[v * n * n + ta + n * tb] = base[(size_t)v * n3 + node_index(n, idx[0], idx[1], idx[2])];
+            out[v * f2 + ta + n[d0] * tb] = base[(size_t)v * n3 + aidx(n, idx[0], idx[1], idx[2])];
         }
 }
 
-/* Face field of degree Ns -> mortar of degree Nm (tensor-product interpolation). */
-static void pm_to_mortar(const orc_pmesh *m, int Ns, int Nm, const double *fs, double *fm)
+/* Face field of degrees (S0, S1) -> mortar of degrees (M0, M1), Sk <= Mk
+ * (tensor-product interpolation, fm[a + (M0+1) b]). */
+static void pm_to_mortar(const orc_pmesh *m, int S0, int S1, int M0, int M1, const double *fs, double *fm)
 {
-    int ns = Ns + 1, nm = Nm + 1;
-    const double *I = m->Pi[Ns][Nm];
-    for (int b = 0; b < nm; ++b) for (int a = 0; a < nm; ++a) {
+    int ns0 = S0 + 1, ns1 = S1 + 1, nm0 = M0 + 1, nm1 = M1 + 1;
+    const double *I0 = m->Pi[S0][M0], *I1 = m->Pi[S1][M1];
+    for (int b = 0; b < nm1; ++b) for (int a = 0; a < nm0; ++a) {
         double acc = 0.0;
-        for (int j = 0; j < ns; ++j)
-            for (int i = 0; i < ns; ++i) acc += I[a * ns + i] * I[b * ns + j] * fs[i + ns * j];
-        fm[a + nm * b] = acc;
+        for (int j = 0; j < ns1; ++j)
+            for (int i = 0; i < ns0; ++i) acc += I0[a * ns0 + i] * I1[b * ns1 + j] * fs[i + ns0 * j];
+        fm[a + nm0 * b] = acc;
     }
 }
 
-/* Mortar field of degree Nm -> face of degree Ns (tensor-product L2 projection). */
-static void pm_from_mortar(const orc_pmesh *m, int Nm, int Ns, const double *fm, double *fs)
+/* Mortar field of degrees (M0, M1) -> face of degrees (S0, S1) (tensor-product
+ * L2 projection). */
+static void pm_from_mortar(const orc_pmesh *m, int M0, int M1, int S0, int S1, const double *fm, double *fs)
 {
-    int ns = Ns + 1, nm = Nm + 1;
-    const double *P = m->Pr[Ns][Nm];
-    for (int b = 0; b < ns; ++b) for (int a = 0; a < ns; ++a) {
+    int ns0 = S0 + 1, ns1 = S1 + 1, nm0 = M0 + 1, nm1 = M1 + 1;
+    const double *P0 = m->Pr[S0][M0], *P1 = m->Pr[S1][M1];
+    for (int b = 0; b < ns1; ++b) for (int a = 0; a < ns0; ++a) {
         double acc = 0.0;
-        for (int j = 0; j < nm; ++j)
-            for (int i = 0; i < nm; ++i) acc += P[a * nm + i] * P[b * nm + j] * fm[i + nm * j];
-        fs[a + ns * b] = acc;
+        for (int j = 0; j < nm1; ++j)
+            for (int i = 0; i < nm0; ++i) acc += P0[a * nm0 + i] * P1[b * nm1 + j] * fm[i + nm0 * j];
+        fs[a + ns0 * b] = acc;
     }
 }
 
 /* The mortar computation for face (d, side) of element e, returned on e's own
- * face nodes (out[v][ta + n_e tb]):
+ * face nodes (out[v][ta + n_e[d0] tb]):
  *   mode 0: the BR1 interface value q* (4 values);
- *   mode 1: the face flux s F* - (F_v(L) + F_v(R)).Sn/2 oriented along +d (5 values).
+ *   mode 1: the face flux s F*(u_L, u_R; n) - (F_v(L) + F_v(R)).Sn/2 oriented along +d (5 values).
  * L is the element on the face's minus side, R on its plus side. */
 static void pm_mortar(const orc_pmesh *m, const orc_cfg *cfg, const double *u, const double *grad, int e, int d,
                       int side, int mode, double *out)
 {
     int nb = neighbour(&m->box, e, d, side);
     int eL = side > 0 ? e : nb, eR = side > 0 ? nb : e;
-    int NL = m->N[eL], NR = m->N[eR], NM = NL > NR ? NL : NR;
-    int nL = NL + 1, nR = NR + 1, nM = NM + 1, nM2 = nM * nM;
+    int d0, d1;
+    face_dirs(d, &d0, &d1);
+    int nLs[3], nRs[3];
+    pm_shape(m, eL, nLs);
+    pm_shape(m, eR, nRs);
+    int L0 = nLs[d0] - 1, L1 = nLs[d1] - 1, R0 = nRs[d0] - 1, R1 = nRs[d1] - 1;
+    int M0 = L0 > R0 ? L0 : R0, M1 = L1 > R1 ? L1 : R1;
+    int fL = (L0 + 1) * (L1 + 1), fR = (R0 + 1) * (R1 + 1), nM2 = (M0 + 1) * (M1 + 1);
     double g = cfg->gamma;
     double tL[NVAR * 64], tR[NVAR * 64], mL[NVAR * 64], mR[NVAR * 64];
-    pm_face_values(u + m->off[eL], NVAR, nL, d, NL, tL);
-    pm_face_values(u + m->off[eR], NVAR, nR, d, 0, tR);
+    pm_face_values(u + m->off[eL], NVAR, nLs, d, nLs[d] - 1, tL);
+    pm_face_values(u + m->off[eR], NVAR, nRs, d, 0, tR);
     for (int v = 0; v < NVAR; ++v) {
-        pm_to_mortar(m, NL, NM, tL + v * nL * nL, mL + v * nM2);
-        pm_to_mortar(m, NR, NM, tR + v * nR * nR, mR + v * nM2);
+        pm_to_mortar(m, L0, L1, M0, M1, tL + v * fL, mL + v * nM2);
+        pm_to_mortar(m, R0, R1, M0, M1, tR + v * fR, mR + v * nM2);
     }
     int nv = mode == 0 ? NGRAD : NVAR;
     double fM[NVAR * 64];
@@ -1822,18 +1934,26 @@ static void pm_mortar(const orc_pmesh *m, const orc_cfg *cfg, const double *u, c
             for (int v = 0; v < NGRAD; ++v) fM[v * nM2 + p] = 0.5 * (qL[v] + qR[v]);
         }
     } else {
-        /* the face metric of the side of degree NM (L on a tie) */
+        /* the face metric at the mortar points */
         double Sn[3 * 64];
-        if (NL >= NR) pm_face_values(m->Ja + 9 * m->noff[eL] + (size_t)d * 3 * (nL * nL * nL), 3, nL, d, NL, Sn);
-        else pm_face_values(m->Ja + 9 * m->noff[eR] + (size_t)d * 3 * (nR * nR * nR), 3, nR, d, 0, Sn);
+        int nL3 = pm_nodes(nLs), nR3 = pm_nodes(nRs);
+        if (L0 == M0 && L1 == M1) {
+            pm_face_values(m->Ja + 9 * m->noff[eL] + (size_t)d * 3 * nL3, 3, nLs, d, nLs[d] - 1, Sn);
+        } else if (R0 == M0 && R1 == M1) {
+            pm_face_values(m->Ja + 9 * m->noff[eR] + (size_t)d * 3 * nR3, 3, nRs, d, 0, Sn);
+        } else {
+            double SL[3 * 64];
+            pm_face_values(m->Ja + 9 * m->noff[eL] + (size_t)d * 3 * nL3, 3, nLs, d, nLs[d] - 1, SL);
+            for (int c = 0; c < 3; ++c) pm_to_mortar(m, L0, L1, M0, M1, SL + c * fL, Sn + c * nM2);
+        }
         double gL[12 * 64], gR[12 * 64], gmL[12 * 64], gmR[12 * 64];
         int ns = cfg->physics == 1;
         if (ns) {
-            pm_face_values(grad + 12 * m->noff[eL], 12, nL, d, NL, gL);
-            pm_face_values(grad + 12 * m->noff[eR], 12, nR, d, 0, gR);
+            pm_face_values(grad + 12 * m->noff[eL], 12, nLs, d, nLs[d] - 1, gL);
+            pm_face_values(grad + 12 * m->noff[eR], 12, nRs, d, 0, gR);
             for (int k = 0; k < 12; ++k) {
-                pm_to_mortar(m, NL, NM, gL + k * nL * nL, gmL + k * nM2);
-                pm_to_mortar(m, NR, NM, gR + k * nR * nR, gmR + k * nM2);
+                pm_to_mortar(m, L0, L1, M0, M1, gL + k * fL, gmL + k * nM2);
+                pm_to_mortar(m, R0, R1, M0, M1, gR + k * fR, gmR + k * nM2);
             }
         }
         double mu = ns ? visc_mu(cfg) : 0.0, kappa = ns ? visc_kappa(cfg) : 0.0;
@@ -1853,21 +1973,26 @@ static void pm_mortar(const orc_pmesh *m, const orc_cfg *cfg, const double *u, c
             for (int v = 0; v < NVAR; ++v) fM[v * nM2 + p] = f[v];
         }
     }
-    int Ne = m->N[e], ne = Ne + 1;
-    for (int v = 0; v < nv; ++v) pm_from_mortar(m, NM, Ne, fM + v * nM2, out + v * ne * ne);
+    int ne[3];
+    pm_shape(m, e, ne);
+    int E0 = ne[d0] - 1, E1 = ne[d1] - 1;
+    for (int v = 0; v < nv; ++v) pm_from_mortar(m, M0, M1, E0, E1, fM + v * nM2, out + v * (E0 + 1) * (E1 + 1));
 }
 
-/* BR1 gradients on the p-non-conforming mesh, grad per element [4][3][n_e^3]
+/* BR1 gradients on the p-non-conforming mesh, grad per element [4][3][nodes_e]
  * at 12 noff[e]:
  *   J grad q_c = sum_d D_d (Ja^d_c q) + sum_faces (1/w_end) (q*_e - q_in) (+-Ja^d_c),
- * q*_e the mortar interface value projected onto the element's face. */
+ * D_d and w of the element's degree in direction d, q*_e the mortar interface
+ * value projected onto the element's face. */
 static void pm_br1(const orc_pmesh *m, const orc_cfg *cfg, const double *u, double *grad)
 {
     double g = cfg->gamma;
 #pragma omp parallel for schedule(dynamic)
     for (int e = 0; e < m->E; ++e) {
-        int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
-        const double *D = m->D[N], *w = m->w[N];
+        int n[3];
+        pm_shape(m, e, n);
+        int n3 = pm_nodes(n);
+        const double *Dd[3] = {m->D[n[0] - 1], m->D[n[1] - 1], m->D[n[2] - 1]};
         const double *Ja = m->Ja + 9 * m->noff[e], *J = m->J + m->noff[e];
         const double *ue = u + m->off[e];
         double *G = grad + 12 * m->noff[e];
@@ -1882,26 +2007,28 @@ static void pm_br1(const orc_pmesh *m, const orc_cfg *cfg, const double *u, doub
         for (int c = 0; c < 3; ++c) {
             for (int d = 0; d < 3; ++d)
                 for (int p = 0; p < n3; ++p) f[d * n3 + p] = Ja[(d * 3 + c) * n3 + p] * q[v * n3 + p];
-            for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < n[2]; ++k) for (int j = 0; j < n[1]; ++j) for (int i = 0; i < n[0]; ++i) {
                 double acc = 0.0;
-                for (int d = 0; d < 3; ++d) acc += dir_derivative(n, D, f + d * n3, d, i, j, k);
-                G[(v * 3 + c) * n3 + node_index(n, i, j, k)] = acc;
+                for (int d = 0; d < 3; ++d) acc += adir_derivative(n, Dd[d], f + d * n3, d, i, j, k);
+                G[(v * 3 + c) * n3 + aidx(n, i, j, k)] = acc;
             }
         }
         for (int d = 0; d < 3; ++d)
         for (int side = -1; side <= 1; side += 2) {
             double qs[NGRAD * 64];
             pm_mortar(m, cfg, u, NULL, e, d, side, 0, qs);
-            int at = side > 0 ? N : 0, d0, d1;
+            int at = side > 0 ? n[d] - 1 : 0, d0, d1;
             face_dirs(d, &d0, &d1);
-            for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+            int f2 = n[d0] * n[d1];
+            const double *w = m->w[n[d] - 1];
+            for (int tb = 0; tb < n[d1]; ++tb) for (int ta = 0; ta < n[d0]; ++ta) {
                 int idx[3];
                 idx[d] = at;
                 idx[d0] = ta;
                 idx[d1] = tb;
-                int p = node_index(n, idx[0], idx[1], idx[2]);
+                int p = aidx(n, idx[0], idx[1], idx[2]);
                 for (int v = 0; v < NGRAD; ++v) {
-                    double jump = qs[v * n2 + ta + n * tb] - q[v * n3 + p];
+                    double jump = qs[v * f2 + ta + n[d0] * tb] - q[v * n3 + p];
                     for (int c = 0; c < 3; ++c)
                         G[(v * 3 + c) * n3 + p] += jump * side * Ja[(d * 3 + c) * n3 + p] / w[at];
                 }
@@ -1919,10 +2046,12 @@ int orc_pgradients(const orc_pmesh *m, const orc_cfg *cfg, const double *u, doub
 }
 
 /* du/dt = -(V + S)/J per element of the p-non-conforming mesh: the volume
- * term exactly as on a conforming mesh (standard or split form, at the
- * element's own degree) and the surface term
+ * term exactly as on a conforming mesh (standard or split form), each
+ * direction d with the derivative matrix of the element's degree in d, and
+ * the surface term
  *   S = (1/w_end) [ +-F*_e - (F_e - F_v)(in).(+-Ja^d_in) ]
- * with F*_e the mortar flux projected onto the element's face. */
+ * with F*_e the mortar flux projected onto the element's face and w_end the
+ * end weight of the element's degree in d. */
 int orc_presidual(const orc_pmesh *m, const orc_cfg *cfg, const double *u, double *dudt)
 {
     double g = cfg->gamma;
@@ -1936,8 +2065,10 @@ int orc_presidual(const orc_pmesh *m, const orc_cfg *cfg, const double *u, doubl
     }
 #pragma omp parallel for schedule(dynamic)
     for (int e = 0; e < m->E; ++e) {
-        int N = m->N[e], n = N + 1, n2 = n * n, n3 = n2 * n;
-        const double *D = m->D[N], *w = m->w[N];
+        int n[3];
+        pm_shape(m, e, n);
+        int n3 = pm_nodes(n);
+        const double *Dd[3] = {m->D[n[0] - 1], m->D[n[1] - 1], m->D[n[2] - 1]};
         const double *Ja = m->Ja + 9 * m->noff[e], *J = m->J + m->noff[e];
         const double *ue = u + m->off[e];
         double *Ft = (double *)malloc(sizeof(double) * 3 * NVAR * n3);
@@ -1961,41 +2092,45 @@ int orc_presidual(const orc_pmesh *m, const orc_cfg *cfg, const double *u, doubl
                 }
             }
         }
-        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
-            int p = node_index(n, i, j, k), ijk[3] = {i, j, k};
+        for (int k = 0; k < n[2]; ++k) for (int j = 0; j < n[1]; ++j) for (int i = 0; i < n[0]; ++i) {
+            int p = aidx(n, i, j, k), ijk[3] = {i, j, k};
             for (int d = 0; d < 3; ++d) {
                 if (cfg->volume_form == 0) {
-                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += dir_derivative(n, D, Ft + (d * NVAR + v) * n3, d, i, j, k);
+                    for (int v = 0; v < NVAR; ++v)
+                        R[v * n3 + p] += adir_derivative(n, Dd[d], Ft + (d * NVAR + v) * n3, d, i, j, k);
                     continue;
                 }
                 double ui[NVAR];
                 for (int v = 0; v < NVAR; ++v) ui[v] = ue[v * n3 + p];
-                for (int mm = 0; mm < n; ++mm) {
-                    int pm = node_along(n, d, mm, i, j, k);
+                for (int mm = 0; mm < n[d]; ++mm) {
+                    int pm = anode_along(n, d, mm, i, j, k);
                     double um[NVAR], a[3], fs[NVAR];
                     for (int v = 0; v < NVAR; ++v) um[v] = ue[v * n3 + pm];
                     for (int c = 0; c < 3; ++c) a[c] = 0.5 * (Ja[(d * 3 + c) * n3 + p] + Ja[(d * 3 + c) * n3 + pm]);
                     split_flux(cfg->volume_form, ui, um, a, g, fs);
-                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += 2.0 * D[ijk[d] * n + mm] * fs[v];
+                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] += 2.0 * Dd[d][ijk[d] * n[d] + mm] * fs[v];
                 }
                 if (ns)
-                    for (int v = 0; v < NVAR; ++v) R[v * n3 + p] -= dir_derivative(n, D, Fv + (d * NVAR + v) * n3, d, i, j, k);
+                    for (int v = 0; v < NVAR; ++v)
+                        R[v * n3 + p] -= adir_derivative(n, Dd[d], Fv + (d * NVAR + v) * n3, d, i, j, k);
             }
         }
         for (int d = 0; d < 3; ++d)
         for (int side = -1; side <= 1; side += 2) {
             double fs[NVAR * 64];
             pm_mortar(m, cfg, u, grad, e, d, side, 1, fs);
-            int at = side > 0 ? N : 0, d0, d1;
+            int at = side > 0 ? n[d] - 1 : 0, d0, d1;
             face_dirs(d, &d0, &d1);
-            for (int tb = 0; tb < n; ++tb) for (int ta = 0; ta < n; ++ta) {
+            int f2 = n[d0] * n[d1];
+            const double *w = m->w[n[d] - 1];
+            for (int tb = 0; tb < n[d1]; ++tb) for (int ta = 0; ta < n[d0]; ++ta) {
                 int idx[3];
                 idx[d] = at;
                 idx[d0] = ta;
                 idx[d1] = tb;
-                int p = node_index(n, idx[0], idx[1], idx[2]);
+                int p = aidx(n, idx[0], idx[1], idx[2]);
                 for (int v = 0; v < NVAR; ++v)
-                    R[v * n3 + p] += (side * fs[v * n2 + ta + n * tb] - side * Ft[(d * NVAR + v) * n3 + p]) / w[at];
+                    R[v * n3 + p] += (side * fs[v * f2 + ta + n[d0] * tb] - side * Ft[(d * NVAR + v) * n3 + p]) / w[at];
             }
         }
         for (int v = 0; v < NVAR; ++v)
@@ -2006,14 +2141,20 @@ int orc_presidual(const orc_pmesh *m, const orc_cfg *cfg, const double *u, doubl
     return 0;
 }
 
-/* Time step on the p-non-conforming mesh: the conforming rule per element,
- * with the element's own n, minimised over the elements:
- *   dt = min_e min( cfl 8/(n_e^2 lam_c,e), 12/(n_e^4 lam_v,e) ). */
+/* Time step on the p-non-conforming mesh: the conforming rule per element
+ * with each direction's resolution n_d^2 inside the sum (the reference grid
+ * spacing of degree P_d scales like 1/n_d^2; an isotropic element gives the
+ * conforming rule with n^2 taken outside, the same value up to rounding),
+ * minimised over the elements:
+ *   dt = min_e min( cfl 8 / max_nodes sum_d n_d^2 (|Ja^d.v| + c|Ja^d|)/J,
+ *                   12 / max_nodes (mu/rho) sum_d n_d^4 (|Ja^d|/J)^2 ). */
 double orc_pdt(const orc_pmesh *m, const orc_cfg *cfg, const double *u)
 {
     double g = cfg->gamma, mu = cfg->physics == 1 ? visc_mu(cfg) : 0.0, dt = INFINITY;
     for (int e = 0; e < m->E; ++e) {
-        int n = m->N[e] + 1, n3 = n * n * n;
+        int n[3];
+        pm_shape(m, e, n);
+        int n3 = pm_nodes(n);
         const double *Ja = m->Ja + 9 * m->noff[e], *J = m->J + m->noff[e];
         double lam_c = 0.0, lam_v = 0.0;
         for (int p = 0; p < n3; ++p) {
@@ -2024,15 +2165,16 @@ double orc_pdt(const orc_pmesh *m, const orc_cfg *cfg, const double *u)
             for (int d = 0; d < 3; ++d) {
                 double a[3] = {Ja[(d * 3) * n3 + p], Ja[(d * 3 + 1) * n3 + p], Ja[(d * 3 + 2) * n3 + p]};
                 double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-                sc += (fabs(a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) + c * an) / J[p];
-                sv += (an / J[p]) * (an / J[p]);
+                double n2 = (double)n[d] * n[d];
+                sc += n2 * (fabs(a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) + c * an) / J[p];
+                sv += n2 * n2 * (an / J[p]) * (an / J[p]);
             }
             if (sc > lam_c) lam_c = sc;
             if (mu * sv / rho > lam_v) lam_v = mu * sv / rho;
         }
-        double dte = cfg->cfl * 8.0 / ((double)n * n * lam_c);
+        double dte = cfg->cfl * 8.0 / lam_c;
         if (lam_v > 0.0) {
-            double dtv = 12.0 / ((double)n * n * n * n * lam_v);
+            double dtv = 12.0 / lam_v;
             if (dtv < dte) dte = dtv;
         }
         if (dte < dt) dt = dte;
@@ -2064,7 +2206,9 @@ void orc_pic(const orc_pmesh *m, int kind, const double *par, double *u)
     double p0 = 1.0 / (g * Ma * Ma);
     double Lx = m->box.hi[0] - m->box.lo[0], Ly = m->box.hi[1] - m->box.lo[1];
     for (int e = 0; e < m->E; ++e) {
-        int n = m->N[e] + 1, n3 = n * n * n;
+        int n[3];
+        pm_shape(m, e, n);
+        int n3 = pm_nodes(n);
         const double *X = m->X + 3 * m->noff[e];
         for (int p = 0; p < n3; ++p) {
             double x = X[p], y = X[n3 + p], z = X[2 * n3 + p], v[3], pr, rho, up[NVAR];
@@ -2093,17 +2237,19 @@ void orc_pic(const orc_pmesh *m, int kind, const double *par, double *u)
 }
 
 /* Quadrature integrals on the p-non-conforming mesh (each element with its
- * own weights), as orc_integrals. */
+ * own weights per direction), as orc_integrals. */
 void orc_pintegrals(const orc_pmesh *m, double g, const double *u, const double *dudt, double *out)
 {
     for (int v = 0; v < 7; ++v) out[v] = 0.0;
     for (int e = 0; e < m->E; ++e) {
-        int N = m->N[e], n = N + 1, n3 = n * n * n;
-        const double *w = m->w[N], *J = m->J + m->noff[e];
+        int n[3];
+        pm_shape(m, e, n);
+        int n3 = pm_nodes(n);
+        const double *wx = m->w[n[0] - 1], *wy = m->w[n[1] - 1], *wz = m->w[n[2] - 1], *J = m->J + m->noff[e];
         const double *f = (dudt ? dudt : u) + m->off[e];
-        for (int k = 0; k < n; ++k) for (int j = 0; j < n; ++j) for (int i = 0; i < n; ++i) {
-            int p = node_index(n, i, j, k);
-            double wq = J[p] * w[i] * w[j] * w[k];
+        for (int k = 0; k < n[2]; ++k) for (int j = 0; j < n[1]; ++j) for (int i = 0; i < n[0]; ++i) {
+            int p = aidx(n, i, j, k);
+            double wq = J[p] * wx[i] * wy[j] * wz[k];
             for (int v = 0; v < NVAR; ++v) out[v] += wq * f[(size_t)v * n3 + p];
             if (dudt) {
                 double up[NVAR], wv[NVAR];
