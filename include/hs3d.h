@@ -299,6 +299,27 @@ hs3d_status hs3d_autotune(const hs3d_mesh *mesh, const hs3d_solver_cfg *cfg, int
  * perturb_amp = 0 (HS3D_ERR_INVALID otherwise).  Synchronous. */
 typedef struct hs3d_pmesh hs3d_pmesh;
 hs3d_status hs3d_pmesh_create(const hs3d_mesh_desc *desc, const int *degree, hs3d_pmesh **out);
+
+/* As hs3d_pmesh_create with a degree per element AND reference direction
+ * (Sec. 3.6: P_x, P_y, P_z may differ, anisotropic p-adaptation): degree3 is
+ * a HOST array of 3E ints in 1..7, element e's (P_x, P_y, P_z) at 3e.  Element
+ * e has P_d + 1 Gauss-Lobatto nodes along d, node (i, j, k) at
+ * i + n_x (j + n_y k), and its block [5][n_x n_y n_z] in element order (the
+ * offsets of hs3d_pmesh_layout).  The face normal to d couples its two sides
+ * with a mortar of degree max(P_L, P_R) in EACH tangential direction
+ * separately (interpolation to, and L2 projection from, its points direction
+ * by direction); its face metric is that of a side whose tangential degrees
+ * are the mortar's (the minus side first), else the minus side's
+ * interpolated, which is exact (Pmin = the smallest degree of the mesh over
+ * elements and directions, Ngeo = max(1, floor(Pmin/2)) as above).  The dt
+ * rule takes each direction's resolution inside the sum:
+ *   dt = min( cfl*8 / max_nodes sum_d n_d^2 (|Ja^d.v| + c|Ja^d|)/J,
+ *             12 / max_nodes (mu/rho) sum_d n_d^4 (|Ja^d|/J)^2 ).
+ * When every element has equal degrees in its three directions this is
+ * hs3d_pmesh_create with degree[e] = P_x of e.  Otherwise the mesh runs in
+ * FP64 only (a mixed-precision cfg gives HS3D_ERR_UNSUPPORTED), and every
+ * hs3d_pmesh_* call below applies.  Synchronous. */
+hs3d_status hs3d_pmesh_create3(const hs3d_mesh_desc *desc, const int *degree3, hs3d_pmesh **out);
 void hs3d_pmesh_destroy(hs3d_pmesh *pmesh);
 
 /* State layout of the mesh: element e's block [5][n_e][n_e][n_e] (n_e its
@@ -307,12 +328,14 @@ void hs3d_pmesh_destroy(hs3d_pmesh *pmesh);
  * the doubles a state array must hold.  Elements are stored grouped by
  * degree (ascending), in element order within a degree; each group starts at
  * a multiple of 160 doubles, and the gaps between groups are never read or
- * written.  Ngeo (may be NULL) receives the geometry degree. */
+ * written.  (A mesh of hs3d_pmesh_create3 with per-direction degrees stores
+ * its blocks [5][n_x n_y n_z] in element order, without gaps.)  Ngeo (may be
+ * NULL) receives the geometry degree. */
 hs3d_status hs3d_pmesh_layout(const hs3d_pmesh *pmesh, int64_t *offset, int *Ngeo);
 
 /* Node coordinates and Jacobians into caller-owned DEVICE arrays (either may
- * be NULL): element e's X block [3][n_e^3] at 3*offset[e]/5, its J block
- * [n_e^3] at offset[e]/5 (arrays of 3*offset[E]/5 and offset[E]/5 doubles).
+ * be NULL): element e's X block [3][nodes_e] at 3*offset[e]/5, its J block
+ * [nodes_e] at offset[e]/5 (arrays of 3*offset[E]/5 and offset[E]/5 doubles).
  * Stream-ordered. */
 hs3d_status hs3d_pmesh_geometry(const hs3d_pmesh *pmesh, double *X, double *J, void *stream);
 

@@ -42,7 +42,7 @@ EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh
            "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
            "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
            "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
-           "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding", "hs3d_pmesh_create",
+           "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding", "hs3d_pmesh_create", "hs3d_pmesh_create3",
            "hs3d_pmesh_destroy", "hs3d_pmesh_layout", "hs3d_pmesh_geometry", "hs3d_pmesh_init_state",
            "hs3d_pmesh_residual", "hs3d_pmesh_run", "hs3d_pmesh_clock", "hs3d_pmesh_diagnostics"]
 
@@ -118,6 +118,7 @@ def lib():
                 "hs3d_autotune": [vp, C.POINTER(SolverCfg), C.POINTER(i), vp],
                 "hs3d_check_rounding": [vp, C.c_int64, vp, vp],
                 "hs3d_pmesh_create": [C.POINTER(MeshDesc), vp, C.POINTER(vp)],
+                "hs3d_pmesh_create3": [C.POINTER(MeshDesc), vp, C.POINTER(vp)],
                 "hs3d_pmesh_destroy": [vp],
                 "hs3d_pmesh_layout": [vp, vp, C.POINTER(i)],
                 "hs3d_pmesh_geometry": [vp, vp, vp, vp],
@@ -290,24 +291,37 @@ class Mesh:
 
 class PMesh:
     """A mesh whose elements carry their own polynomial degree, coupled by
-    mortars (``hs3d_pmesh_create``, Sec. 3.6).
+    mortars (``hs3d_pmesh_create``, Sec. 3.6).  ``degrees``: one per element
+    (shape (E,)), or one per element and reference direction (shape (E, 3):
+    P_x, P_y, P_z, ``hs3d_pmesh_create3``).
 
     States are flat float64 CUDA tensors of ``size`` doubles; element e's
-    block [5, n_e, n_e, n_e] starts at ``offset[e]`` (elements grouped by
-    degree, see ``hs3d_pmesh_layout``)."""
+    block [5, n_z, n_y, n_x] starts at ``offset[e]`` (see
+    ``hs3d_pmesh_layout``)."""
 
     def __init__(self, ex, ey, ez, degrees, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.0):
         import numpy as np
         self.ex, self.ey, self.ez = ex, ey, ez
         self.E = ex * ey * ez
-        deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32).reshape(-1))
-        if deg.size != self.E:
-            raise HS3DError(ERR_INVALID, "one degree per element")
-        self.degrees = deg.copy()
+        dg = np.asarray(degrees, dtype=np.int32)
+        if dg.ndim == 2:
+            if dg.shape != (self.E, 3):
+                raise HS3DError(ERR_INVALID, "three degrees per element")
+            deg3 = np.ascontiguousarray(dg)
+        else:
+            if dg.size != self.E:
+                raise HS3DError(ERR_INVALID, "one degree per element")
+            deg3 = np.ascontiguousarray(np.repeat(dg.reshape(-1)[:, None], 3, axis=1))
+        self.degrees3 = deg3.copy()
+        self.degrees = deg3[:, 0].copy() if bool(np.all(deg3 == deg3[:, :1])) else None
         self.lo, self.hi = tuple(lo), tuple(hi)
         d = mesh_desc(ex, ey, ez, 1, lo, hi, amp)
         h = C.c_void_p()
-        check(lib().hs3d_pmesh_create(C.byref(d), C.c_void_p(deg.ctypes.data), C.byref(h)))
+        if dg.ndim == 2:
+            check(lib().hs3d_pmesh_create3(C.byref(d), C.c_void_p(deg3.ctypes.data), C.byref(h)))
+        else:
+            deg = np.ascontiguousarray(dg.reshape(-1))
+            check(lib().hs3d_pmesh_create(C.byref(d), C.c_void_p(deg.ctypes.data), C.byref(h)))
         self._h = h
         off = np.zeros(self.E + 1, dtype=np.int64)
         ng = C.c_int()
@@ -323,17 +337,25 @@ class PMesh:
             self._h = None
 
     def n(self, e):
-        return int(self.degrees[e]) + 1
+        """Nodes per direction of an element of equal degrees."""
+        nx, ny, nz = self.shape3(e)
+        if not nx == ny == nz:
+            raise HS3DError(ERR_INVALID, "element with per-direction degrees: use shape3")
+        return nx
+
+    def shape3(self, e):
+        """(n_x, n_y, n_z) of element e."""
+        return tuple(int(x) + 1 for x in self.degrees3[e])
 
     def empty_state(self):
         import torch
         return torch.zeros(self.size, dtype=torch.float64, device="cuda")
 
     def block(self, u, e):
-        """View of element e's block [5, n, n, n] of a flat state (tensor or array)."""
-        n = self.n(e)
+        """View of element e's block [5, n_z, n_y, n_x] of a flat state (tensor or array)."""
+        nx, ny, nz = self.shape3(e)
         o = int(self.offset[e])
-        return u[o:o + 5 * n ** 3].reshape(5, n, n, n)
+        return u[o:o + 5 * nx * ny * nz].reshape(5, nz, ny, nx)
 
     def geometry(self, stream=None):
         """(X, J) as flat tensors: element e's X [3, n^3] at 3 offset[e]/5, J [n^3] at offset[e]/5."""

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <vector>
 
+#include "ic.cuh"
 #include "internal.cuh"
 
 namespace hs3d {
@@ -450,37 +451,12 @@ __global__ void k_init_state(int n3, long long total, const double *__restrict__
     if (t >= total) return;
     long long e = t / n3;
     int p = (int)(t % n3);
-    double x = X[(e * 3 + 0) * n3 + p], y = X[(e * 3 + 1) * n3 + p], z = X[(e * 3 + 2) * n3 + p];
-    double g = ic.gamma;
-    double rho, v1, v2, v3, pr;
-    if (ic.kind == HS3D_IC_VORTEX) {
-        double uinf = ic.Ma * sqrt(g);
-        double dx = x - (ic.xc + uinf * ic.t), dy = y - ic.yc;
-        dx -= Lx * floor(dx / Lx + 0.5);
-        dy -= Ly * floor(dy / Ly + 0.5);
-        double r2 = dx * dx + dy * dy;
-        double ex = exp(0.5 * (1.0 - r2));
-        double k = ic.beta / (2.0 * M_PI);
-        v1 = uinf - k * ex * dy;
-        v2 = k * ex * dx;
-        v3 = 0.0;
-        double T = 1.0 - (g - 1.0) * ic.beta * ic.beta / (8.0 * g * M_PI * M_PI) * ex * ex;
-        rho = pow(T, 1.0 / (g - 1.0));
-        pr = rho * T;
-    } else {
-        double p0 = 1.0 / (g * ic.Ma * ic.Ma);
-        v1 = sin(x) * cos(y) * cos(z);
-        v2 = -cos(x) * sin(y) * cos(z);
-        v3 = 0.0;
-        pr = p0 + (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0) * (1.0 / 16.0);
-        rho = pr / p0;
-    }
+    const double x = X[(e * 3 + 0) * n3 + p], y = X[(e * 3 + 1) * n3 + p], z = X[(e * 3 + 2) * n3 + p];
+    double w[5];
+    ic_point(ic, Lx, Ly, x, y, z, w);
     double *ue = u + e * 5 * n3 + p;
-    ue[0] = rho;
-    ue[n3] = rho * v1;
-    ue[2 * n3] = rho * v2;
-    ue[3 * n3] = rho * v3;
-    ue[4 * n3] = pr / (g - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ue[(size_t)v * n3] = w[v];
 }
 
 cudaError_t launch_init_state(int N, int E, const double *X, const hs3d_ic &ic, const double *lo, const double *hi,

@@ -27,6 +27,7 @@
 #include <mutex>
 #include <vector>
 
+#include "aniso.cuh"
 #include "api_internal.h"
 #include "mortar.cuh"
 
@@ -37,6 +38,8 @@ struct hs3d_pmesh {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, amp = 0.0;
     std::vector<int> deg;
     std::vector<int64_t> off;   // [E+1] state offsets (doubles)
+    AnisoMesh *an = nullptr;    // degrees that differ between directions: the anisotropic path (aniso.cu),
+                                // which then holds everything below instead of the buckets
     struct Bucket {
         int N = 0, E = 0;
         int64_t base = 0;
@@ -74,6 +77,7 @@ namespace {
 void pmesh_free(hs3d_pmesh *pm)
 {
     if (!pm) return;
+    if (pm->an) aniso_free(pm->an);
     if (pm->gexec) cudaGraphExecDestroy(pm->gexec);
     for (auto &bk : pm->b) {
         if (bk.m) mesh_free(bk.m);
@@ -378,6 +382,7 @@ cudaError_t p_stage(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, const std::v
 cudaError_t p_step(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, double *u, double *g, double dt, bool fresh,
                    cudaStream_t s)
 {
+    if (pm->an) return aniso_step(pm->an, c, u, g, dt, fresh, s);
     std::vector<Batch> bb = bucket_batches(pm, c, u, g, nullptr, true);
     cudaError_t e = cudaSuccess;
     if (fresh) {
@@ -397,7 +402,10 @@ cudaError_t p_step(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, double *u, do
 hs3d_status p_check(const hs3d_pmesh *pm, const hs3d_solver_cfg *c)
 {
     if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
-    return validate_cfg(c);
+    hs3d_status st = validate_cfg(c);
+    if (st == HS3D_OK && pm->an && c->precision != HS3D_FP64)
+        return fail(HS3D_ERR_UNSUPPORTED, "meshes with per-direction degrees run in FP64");
+    return st;
 }
 
 }  // namespace
@@ -409,6 +417,66 @@ hs3d_status hs3d_pmesh_create(const hs3d_mesh_desc *desc, const int *degree, hs3
     if (!out) return fail(HS3D_ERR_INVALID, "out is NULL");
     *out = nullptr;
     return pmesh_build(desc, degree, out);
+}
+
+hs3d_status hs3d_pmesh_create3(const hs3d_mesh_desc *desc, const int *degree3, hs3d_pmesh **out)
+{
+    if (!out) return fail(HS3D_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!desc || !degree3) return fail(HS3D_ERR_INVALID, "desc or degree3 is NULL");
+    if (desc->ex < 1 || desc->ey < 1 || desc->ez < 1) return fail(HS3D_ERR_INVALID, "element counts must be >= 1");
+    const long long E = (long long)desc->ex * desc->ey * desc->ez;
+    if (E > (1 << 24)) return fail(HS3D_ERR_UNSUPPORTED, "too many elements");
+    bool iso = true;
+    int Pmin = 99, Pmax = 0;
+    for (long long t = 0; t < 3 * E; ++t) {
+        if (degree3[t] < 1 || degree3[t] > kMaxN)
+            return fail(HS3D_ERR_UNSUPPORTED, "degree %d (element %lld) outside 1..%d", degree3[t], t / 3, kMaxN);
+        Pmin = degree3[t] < Pmin ? degree3[t] : Pmin;
+        Pmax = degree3[t] > Pmax ? degree3[t] : Pmax;
+        iso = iso && degree3[t] == degree3[3 * (t / 3)];
+    }
+    if (iso) {   // one degree per element: the bucketed path
+        std::vector<int> deg(E);
+        for (long long e = 0; e < E; ++e) deg[e] = degree3[3 * e];
+        return pmesh_build(desc, deg.data(), out);
+    }
+    if (desc->node_xyz) return fail(HS3D_ERR_UNSUPPORTED, "per-element degrees take no node_xyz");
+    if (desc->nodes != HS3D_NODES_LOBATTO)
+        return fail(HS3D_ERR_UNSUPPORTED, "per-element degrees need Gauss-Lobatto nodes");
+    hs3d_mesh_desc chk = *desc;
+    chk.N = Pmax;
+    hs3d_status st = validate_desc(&chk);
+    if (st != HS3D_OK) return st;
+    if (Pmin == 1 && desc->perturb_amp != 0.0)
+        return fail(HS3D_ERR_INVALID, "a degree-1 direction allows only an affine map (perturb_amp = 0)");
+    hs3d_pmesh *pm = new (std::nothrow) hs3d_pmesh();
+    if (!pm) return fail(HS3D_ERR_NOMEM, "host allocation failed");
+    pm->ex = desc->ex;
+    pm->ey = desc->ey;
+    pm->ez = desc->ez;
+    pm->E = (int)E;
+    pm->Nmin = Pmin;
+    pm->Nmax = Pmax;
+    for (int c = 0; c < 3; ++c) {
+        pm->lo[c] = desc->lo[c];
+        pm->hi[c] = desc->hi[c];
+    }
+    pm->amp = desc->perturb_amp;
+    cudaError_t e = cudaStreamCreateWithFlags(&pm->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        pmesh_free(pm);
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    st = aniso_build(desc, degree3, &pm->an);
+    if (st != HS3D_OK) {
+        pmesh_free(pm);
+        return st;
+    }
+    pm->Ngeo = pm->an->Ngeo;
+    pm->off = pm->an->off;
+    *out = pm;
+    return HS3D_OK;
 }
 
 void hs3d_pmesh_destroy(hs3d_pmesh *pm) { pmesh_free(pm); }
@@ -426,6 +494,11 @@ hs3d_status hs3d_pmesh_geometry(const hs3d_pmesh *pm, double *X, double *J, void
     if (!pm) return fail(HS3D_ERR_INVALID, "pmesh is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    if (pm->an) {
+        const size_t nodes = (size_t)pm->an->noff[pm->E];
+        if (X) e = cudaMemcpyAsync(X, pm->an->X, sizeof(double) * 3 * nodes, cudaMemcpyDeviceToDevice, s);
+        if (J && e == cudaSuccess) e = cudaMemcpyAsync(J, pm->an->J, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, s);
+    }
     for (const auto &bk : pm->b) {
         const size_t en = (size_t)bk.E * bk.m->n3;
         const size_t nb = (size_t)bk.base / 5;   // node offset of the bucket (bases are multiples of 5)
@@ -445,6 +518,10 @@ hs3d_status hs3d_pmesh_init_state(const hs3d_pmesh *pm, const hs3d_ic *ic, doubl
         hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
         std::lock_guard<std::mutex> lock(m->mu);
         if (m->cont_u == u) m->cont_u = nullptr;   // the state itself is rewritten
+    }
+    if (pm->an) {
+        cudaError_t e = aniso_init_state(pm->an, *ic, u, (cudaStream_t)stream);
+        return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "init launch");
     }
     for (size_t k = 0; k < pm->b.size() && st == HS3D_OK; ++k)
         st = hs3d_init_state(pm->b[k].m, ic, u + pm->b[k].base, stream);
@@ -475,6 +552,10 @@ hs3d_status hs3d_pmesh_diagnostics(const hs3d_pmesh *pm, const hs3d_solver_cfg *
     std::lock_guard<std::mutex> lock(m->mu);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    if (pm->an) {
+        e = aniso_diagnostics(pm->an, c, u, dudt, out, s);
+        return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "diagnostics launch");
+    }
     for (size_t k = 0; k < pm->b.size() && e == cudaSuccess; ++k) {
         const auto &bk = pm->b[k];
         const Item it = make_item(bk.m, c, u + bk.base, nullptr, nullptr);
@@ -499,6 +580,10 @@ hs3d_status hs3d_pmesh_residual(const hs3d_pmesh *pm, const hs3d_solver_cfg *c, 
     hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
     std::lock_guard<std::mutex> lock(m->mu);
     cudaStream_t s = (cudaStream_t)stream;
+    if (pm->an) {
+        cudaError_t e = aniso_stage(pm->an, c, const_cast<double *>(u), nullptr, dudt, -1, -1, s);
+        return e == cudaSuccess ? HS3D_OK : cuda_fail(e, "residual launch");
+    }
     std::vector<Batch> bb = bucket_batches(pm, c, u, nullptr, dudt, false);
     cudaError_t e = cudaSuccess;
     if (c->precision != HS3D_FP64) {
@@ -576,6 +661,21 @@ hs3d_status hs3d_pmesh_clock(const hs3d_pmesh *pm, double *t, int64_t *steps, in
         hs3d_pmesh *m = const_cast<hs3d_pmesh *>(pm);
         std::lock_guard<std::mutex> lock(m->mu);
         m->cont_u = nullptr;
+    }
+    if (pm->an) {
+        Clock h{};
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaError_t e = cudaMemcpyAsync(&h, pm->an->clk, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && reset) {
+            e = cudaMemsetAsync(pm->an->clk, 0, sizeof(Clock), s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "clock read");
+        if (t) *t = h.t;
+        if (steps) *steps = h.step;
+        if (h.bad) return fail(HS3D_ERR_NONPHYSICAL, "non-physical state detected (rho <= 0, p <= 0 or NaN)");
+        return HS3D_OK;
     }
     hs3d_status worst = HS3D_OK;
     for (size_t k = 0; k < pm->b.size(); ++k) {

@@ -183,7 +183,7 @@ def test_residual_parity_tgv_16cubed_full_size():
     same node coordinates (the oracle's, through node_xyz); their metric
     terms still differ by the rounding of each side's own curl-form
     arithmetic, which moves this residual by ~1e-9 (a one-ulp change of the
-    coordinates moves it by ~2e-9).  The bar is max(1e-12, 32x the larger
+    coordinates moves it by ~2e-9).  The bar is max(1e-12, 4x the larger
     sensitivity); the metric terms themselves are held to 1e-12 in
     test_geometry_from_node_coordinates, and the state after several steps
     is well conditioned and held to 1e-12 in test_tgv_ns_steps_parity_16cubed."""
@@ -197,7 +197,7 @@ def test_residual_parity_tgv_16cubed_full_size():
     r = torch.empty_like(u)
     gm.residual(gc, u, r)
     k_state, k_geo = conditioning(om, oc, u0, ref)
-    tol = max(TOL64, 32 * max(k_state, k_geo))
+    tol = max(TOL64, 4 * max(k_state, k_geo))
     err = rel(host(r), ref)
     print(f"16^3 N=3 TGV residual, FP64, same node coordinates: rel-L2 {err:.3e} "
           f"(sensitivity: state {k_state:.2e}, geometry {k_geo:.2e}; bar {tol:.2e})")
@@ -445,11 +445,13 @@ def test_tgv_32cubed_N7_residual_on_a_seeded_subsample():
     r32 = host(r)[sub]
     gm.residual(cfgs("ns", "roe", "standard", precision="mixed_tc", Re=1600.0)[1], u, r)
     rtc = host(r)[sub]
+    # (N = 7: a one-ulp change of the coordinates moves this residual by ~8e-7;
+    # measured with the same coordinates on both sides: 3.5e-8)
     k_state, k_geo = conditioning(om, oc, u0, ref_full)
-    tol = max(TOL64, 32 * max(k_state, k_geo))
+    tol = max(TOL64, 4 * max(k_state, k_geo))
     print(f"32^3 N=7 subsample: FP64 rel {rel(r64, ref):.3e} (sensitivity: state {k_state:.2e}, "
           f"geometry {k_geo:.2e}; bar {tol:.1e}), mixed rel {rel(r32, ref):.3e}")
-    assert tol < 1e-6
+    assert tol < 1e-5
     assert rel(r64, ref) < tol
     # the mixed path (FP32 flux arithmetic on FP64-formed deviations, float-float
     # mass divergence) meets the per-residual bar at Mach 0.1 and N = 7
