@@ -437,9 +437,9 @@ def run_hs3d(args, world, rank, local):
     extra = {}
     if args.workloads and args.mesh == 16:
         extra["tgv_32cubed_N7_standard_roe_br1"] = run_workload("cfg3", 32, 7, "ns", "roe", "standard", 5, 2,
-                                                                precisions=("mixed32", "mixed_tc", "fp64"))
+                                                                precisions=("mixed32", "fp64"))
         extra["tgv_64cubed_N3_standard_lf_euler"] = run_workload("sweep", 64, 3, "euler", "lf", "standard", 5, 2,
-                                                                 precisions=("mixed32", "mixed_tc", "fp64"))
+                                                                 precisions=("mixed32", "fp64"))
         extra["tgv_52cubed_N4_standard_lf_euler"] = run_workload("sweep", 52, 4, "euler", "lf", "standard", 5, 2)
         extra["tgv_64cubed_N3_standard_roe_br1"] = run_workload("sweep", 64, 3, "ns", "roe", "standard", 5, 2)
         for vol, surf, tm in (("kg", "roe", "rk4"), ("pirozzoli", "roe", "rk3"), ("ducros", "roe", "rk3"),

@@ -99,12 +99,13 @@ enum {
  * third-order scheme, or Carpenter and Kennedy's five-stage fourth-order
  * 2N-storage scheme (NASA TM 109112, 1994) */
 enum { HS3D_TIME_RK3 = 0, HS3D_TIME_RK4 = 1 };
-/* arithmetic: all FP64; or FP32 flux arithmetic with FP64 state, geometry
- * and RK accumulation (MIXED32); or MIXED32 with the standard-form volume
- * term's derivative-matrix contraction on the tensor cores as TF32 products
- * of split operands (each FP32 operand written as a TF32 head plus a TF32
- * tail, three products, FP32 accumulation: FP32 accuracy) (MIXED_TC; the
- * split forms compute as in MIXED32) */
+/* arithmetic: all FP64; or FP32 flux arithmetic on FP64-formed deviations
+ * from a per-element reference state, with FP64 state, geometry and state
+ * accumulation (MIXED32).  MIXED_TC is accepted and computes exactly as
+ * MIXED32: the derivative-matrix contraction stays on the CUDA cores (the
+ * part a TF32-split tensor-core product could take measured at most 4% of
+ * the residual at N = 7; the float-float mass contraction needs more than
+ * FP32 accuracy). */
 enum { HS3D_FP64 = 0, HS3D_MIXED32 = 1, HS3D_MIXED_TC = 2 };
 /* initial conditions */
 enum { HS3D_IC_VORTEX = 0, HS3D_IC_TGV = 1 };

@@ -25,10 +25,7 @@ namespace hs3d {
 constexpr int kMaxN = 7;
 constexpr int kMaxn = kMaxN + 1;
 
-// Internal volume-form id of the standard form with its D contraction on the
-// tensor cores (precision HS3D_MIXED_TC).
-constexpr int kVolStdTC = 100;
-__host__ __device__ constexpr bool is_standard(int form) { return form == HS3D_VOL_STANDARD || form == kVolStdTC; }
+__host__ __device__ constexpr bool is_standard(int form) { return form == HS3D_VOL_STANDARD; }
 
 // Per-solve device clock: dt rule inputs and the simulated time.
 struct Clock {
@@ -234,26 +231,6 @@ __device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// TF32 tensor-core product (warp-wide mma.sync m16n8k8, FP32 accumulate):
-// acc (16x8) += A (16x8, row-major) * B (8x8, column-major).  Fragments per
-// lane (g = lane / 4, t = lane % 4): a = A[g][t], A[g+8][t], A[g][t+4],
-// A[g+8][t+4]; b = B[t][g], B[t+4][g]; acc = C[g][2t], C[g][2t+1],
-// C[g+8][2t], C[g+8][2t+1].  Operands are FP32 bit patterns rounded to
-// TF32 (round to nearest, ties away from zero) by f32_to_tf32.
-__device__ __forceinline__ unsigned f32_to_tf32(float x)
-{
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void mma_tf32_m16n8k8(float acc[4], const unsigned a[4], const unsigned b[2])
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-                 "{%0, %1, %2, %3};\n"
-                 : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 // Ask L2 to fetch the cache lines of [p, p + bytes) ahead of their use; each

@@ -63,7 +63,7 @@ static void save_cache_locked()
     fprintf(f, "{");
     bool first = true;
     for (int N = 1; N <= kMaxN; ++N)
-        for (int prec = 0; prec < 3; ++prec)
+        for (int prec = 0; prec < 2; ++prec)
             for (int which = 0; which < 2; ++which) {
                 int v = tuned_elems_per_block(N, prec, which);
                 if (v <= 0) continue;

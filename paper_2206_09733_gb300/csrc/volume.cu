@@ -37,10 +37,11 @@ void rk_coeffs(int scheme, int k, double *A, double *B)
     *B = four ? kRK4B[k] : kRK3B[k];
 }
 
-// Tuned elements per CTA by (N, precision FP64 / MIXED32 / MIXED_TC, kernel).
-static int g_epb[kMaxn + 1][3][2] = {};
+// Tuned elements per CTA by (N, precision FP64 / mixed, kernel).
+static int g_epb[kMaxn + 1][2][2] = {};
 
-static int prec_slot(int prec) { return prec == HS3D_FP64 ? 0 : prec == HS3D_MIXED_TC ? 2 : 1; }
+// (HS3D_MIXED_TC runs the MIXED32 kernels and shares their slot)
+static int prec_slot(int prec) { return prec == HS3D_FP64 ? 0 : 1; }
 
 int tuned_elems_per_block(int N, int prec, int which) { return g_epb[N][prec_slot(prec)][which]; }
 
@@ -58,7 +59,6 @@ void set_elems_per_block_p(int N, int prec, int which, int epb) { g_epb[N][prec_
 cudaError_t prepare_volume(int N)
 {
     cudaError_t e = prepare_volume_form<HS3D_VOL_STANDARD>(N);
-    if (e == cudaSuccess) e = prepare_volume_form<kVolStdTC>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_EC>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_KG>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_PIROZZOLI>(N);
@@ -66,7 +66,6 @@ cudaError_t prepare_volume(int N)
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_MORINISHI>(N);
     if (e == cudaSuccess) e = prepare_volume_form<HS3D_VOL_IR>(N);
     if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_STANDARD>(N);
-    if (e == cudaSuccess) e = prepare_volume_dev_form<kVolStdTC>(N);
     if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_EC>(N);
     if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_KG>(N);
     if (e == cudaSuccess) e = prepare_volume_dev_form<HS3D_VOL_PIROZZOLI>(N);
@@ -92,7 +91,6 @@ cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, co
         // mixed path: FP32 flux arithmetic on deviations (volume_dev.cuh)
         switch (form) {
             case HS3D_VOL_STANDARD:
-                if (prec == HS3D_MIXED_TC) return launch_volume_dev_form<kVolStdTC>(N, physics, b, stage, A, B, lam_slot, s);
                 return launch_volume_dev_form<HS3D_VOL_STANDARD>(N, physics, b, stage, A, B, lam_slot, s);
             case HS3D_VOL_EC: return launch_volume_dev_form<HS3D_VOL_EC>(N, physics, b, stage, A, B, lam_slot, s);
             case HS3D_VOL_KG: return launch_volume_dev_form<HS3D_VOL_KG>(N, physics, b, stage, A, B, lam_slot, s);
@@ -107,7 +105,6 @@ cudaError_t launch_volume(int N, int prec, int physics, int form, int scheme, co
     }
     switch (form) {
         case HS3D_VOL_STANDARD:
-            if (prec == HS3D_MIXED_TC) return launch_volume_form<kVolStdTC>(N, prec, physics, b, stage, A, B, lam_slot, s);
             return launch_volume_form<HS3D_VOL_STANDARD>(N, prec, physics, b, stage, A, B, lam_slot, s);
         case HS3D_VOL_EC: return launch_volume_form<HS3D_VOL_EC>(N, prec, physics, b, stage, A, B, lam_slot, s);
         case HS3D_VOL_KG: return launch_volume_form<HS3D_VOL_KG>(N, prec, physics, b, stage, A, B, lam_slot, s);

@@ -40,7 +40,7 @@ namespace hs3d {
 template <int FORM>
 constexpr bool dev_lowmach()
 {
-    return FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC || FORM == HS3D_VOL_EC;
+    return FORM == HS3D_VOL_STANDARD || FORM == HS3D_VOL_EC;
 }
 
 template <int N>
@@ -58,7 +58,7 @@ constexpr int dev_threads()
 template <int FORM, bool NS>
 constexpr int dev_per_node()
 {
-    return (FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC) ? 18 : (FORM == HS3D_VOL_EC ? 24 : 16) + (NS ? 12 : 0);
+    return (FORM == HS3D_VOL_STANDARD) ? 18 : (FORM == HS3D_VOL_EC ? 24 : 16) + (NS ? 12 : 0);
 }
 
 template <int FORM, bool NS>
@@ -80,7 +80,7 @@ template <int N, bool NS, int FORM>
 __host__ __device__ constexpr size_t dev_rk_offset(int epb)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-    constexpr size_t pairs = (FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC) ? 0 : (size_t)5 * (n / 2) * n3;
+    constexpr size_t pairs = (FORM == HS3D_VOL_STANDARD) ? 0 : (size_t)5 * (n / 2) * n3;
     const size_t fl = 2 * ((n2 + 3) & ~3) + (size_t)epb * kDevElemBlock + (size_t)epb * dev_per_node<FORM, NS>() * n3 +
                       (size_t)epb * 30 * n2 + (size_t)epb * pairs;
     return (sizeof(float) * fl + 15) & ~(size_t)15;
@@ -91,7 +91,7 @@ template <int N, bool NS, int FORM>
 __host__ __device__ constexpr size_t dev_smem_bytes(int epb)
 {
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
-    constexpr bool SG = (FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC);
+    constexpr bool SG = (FORM == HS3D_VOL_STANDARD);
     return dev_rk_offset<N, NS, FORM>(epb) + (size_t)epb * n3 * ((SG ? 20 : 0) + 4);
 }
 
@@ -110,7 +110,7 @@ __device__ __forceinline__ int dev_line_node(int d, int idx, int ta, int tb)
 template <int N, int FORM>
 constexpr int dev_min_blocks()
 {
-    return ((N + 1) * (N + 1) * (N + 1) <= 256) ? ((FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC) ? 4 : 3) : 2;
+    return ((N + 1) * (N + 1) * (N + 1) <= 256) ? ((FORM == HS3D_VOL_STANDARD) ? 4 : 3) : 2;
 }
 
 template <int N, bool NS, int FORM>
@@ -119,7 +119,7 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
              int lam_slot, int epb)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-    constexpr bool STD = (FORM == HS3D_VOL_STANDARD || FORM == kVolStdTC);
+    constexpr bool STD = (FORM == HS3D_VOL_STANDARD);
     constexpr bool EC = (FORM == HS3D_VOL_EC);
     constexpr bool LM = dev_lowmach<FORM>();
     constexpr int PER = dev_per_node<FORM, NS>();
@@ -598,7 +598,7 @@ template <int N, bool NS, int FORM>
 static cudaError_t vol_dev_launch2(const Batch &b, int stage, double rkA, double rkB, int lam_slot, cudaStream_t s)
 {
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
-    int epb = elems_per_block_p(N, FORM == kVolStdTC ? HS3D_MIXED_TC : HS3D_MIXED32, 1);
+    int epb = elems_per_block_p(N, HS3D_MIXED32, 1);
     if (epb * n3 > dev_threads<N>()) epb = dev_threads<N>() / n3;
     if (epb < 1) epb = 1;
     const int threads = ((epb * n3) + 31) & ~31;

@@ -193,9 +193,8 @@ template <int N, typename R, bool NS, int FORM>
 __host__ __device__ constexpr size_t rk_stage_offset(int epb)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-    // split forms: pair fluxes [5][n/2][n3]; tensor-core standard form: the
-    // three directions' contraction results [3][5][n3]
-    constexpr size_t pairs = !is_standard(FORM) ? (size_t)5 * (n / 2) * n3 : (FORM == kVolStdTC ? 15 * n3 : 0);
+    // split forms: pair fluxes [5][n/2][n3]
+    constexpr size_t pairs = !is_standard(FORM) ? (size_t)5 * (n / 2) * n3 : 0;
     const size_t b = sizeof(R) * (((n * n + 1) & ~1) + (size_t)epb * vol_smem_per_node<FORM, NS>() * n3 +
                                   (size_t)epb * 30 * n2 + (size_t)epb * pairs);
     return (b + 15) & ~(size_t)15;
@@ -396,73 +395,7 @@ k_volume(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage
 
     double lc = 0.0, lv = 0.0;
     bool lam_active = false;
-    if constexpr (FORM == kVolStdTC && sizeof(R) == 4) {
-        // D contraction on the tensor cores: per element and direction d,
-        // C[r][i] = sum_m A[r][m] D[i][m] with rows r = (v, line) of the staged
-        // contravariant fluxes, A[r][m] = F~^d_v at node m of the line, as
-        // m16n8k8 TF32 products (m and i padded to 8) with each FP32 operand
-        // split into a TF32 head and a TF32 tail: A_t D_h + A_h D_t + A_h D_h,
-        // accumulated in FP32, so the product keeps FP32 accuracy.  Warps take
-        // the 16-row tiles of all elements of the CTA in turn; the results go
-        // to shared memory per direction and every node sums its three.
-        constexpr int RT = (5 * n2 + 15) / 16;   // 16-row tiles per direction
-        constexpr int TPE = 3 * RT;              // tiles per element
-        float *VB = (float *)sface + (size_t)epb * FACEVALS;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        const int gid = lane >> 2, tig = lane & 3;
-        unsigned bh[2], bl[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int m = tig + 4 * h;
-            const float dv = (gid < n && m < n) ? (float)sD[gid * n + m] : 0.0f;
-            bh[h] = f32_to_tf32(dv);
-            bl[h] = f32_to_tf32(dv - __uint_as_float(bh[h]));
-        }
-        for (int t = warp; t < epb * TPE; t += nwarps) {
-            const int lt = t / TPE, rem = t - lt * TPE, d = rem / RT, rt = rem - d * RT;
-            const int sd = (d == 0) ? 1 : (d == 1) ? n : n2;
-            const R *Se = sbuf + (size_t)lt * PER * n3 + (size_t)d * 5 * n3;
-            unsigned ah[4], al[4];
-            int rowbase[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = rt * 16 + gid + 8 * h;
-                rowbase[h] = -1;
-                if (r < 5 * n2) {
-                    const int v = r / n2, l = r - v * n2;
-                    rowbase[h] = v * n3 + line_node<n>(d, 0, l % n, l / n);
-                }
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int m = tig + 4 * c;
-                    const float x = (rowbase[h] >= 0 && m < n) ? (float)Se[rowbase[h] + m * sd] : 0.0f;
-                    const unsigned hx = f32_to_tf32(x);
-                    ah[h + 2 * c] = hx;
-                    al[h + 2 * c] = f32_to_tf32(x - __uint_as_float(hx));
-                }
-            }
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            mma_tf32_m16n8k8(acc, al, bh);
-            mma_tf32_m16n8k8(acc, ah, bl);
-            mma_tf32_m16n8k8(acc, ah, bh);
-            float *Ve = VB + ((size_t)lt * 3 + d) * 5 * n3;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (rowbase[h] < 0) continue;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int i = 2 * tig + c;
-                    if (i < n) Ve[rowbase[h] + i * sd] = acc[2 * h + c];
-                }
-            }
-        }
-        __syncthreads();
-        if (valid) {
-            const float *Ve = VB + (size_t)le * 15 * n3;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) V[v] += (Ve[v * n3 + p] + Ve[(5 + v) * n3 + p]) + Ve[(10 + v) * n3 + p];
-        }
-    } else if (is_standard(FORM)) {
+    if constexpr (is_standard(FORM)) {
         if (valid) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -625,13 +558,12 @@ template <int N, typename R, bool NS, int FORM>
 static cudaError_t vol_launch2(const Batch &b, int stage, double rkA, double rkB, int lam_slot, cudaStream_t s)
 {
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
-    int epb = elems_per_block_p(N, sizeof(R) == 4 ? (FORM == kVolStdTC ? HS3D_MIXED_TC : HS3D_MIXED32) : HS3D_FP64, 1);
+    int epb = elems_per_block_p(N, sizeof(R) == 4 ? HS3D_MIXED32 : HS3D_FP64, 1);
     int threads = epb * n3;
     if (threads > vol_threads<N>()) {
         epb = vol_threads<N>() / n3;
         threads = epb * n3;
     }
-    if (FORM == kVolStdTC) threads = (threads + 31) & ~31;   // whole warps for the tensor-core products
     const size_t smem = vol_smem_bytes<N, R, NS, FORM>(epb);
     unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);

@@ -456,17 +456,15 @@ def test_tgv_32cubed_N7_residual_on_a_seeded_subsample():
     # the mixed path (FP32 flux arithmetic on FP64-formed deviations, float-float
     # mass divergence) meets the per-residual bar at Mach 0.1 and N = 7
     assert rel(r32, ref) < 1e-5
-    print(f"32^3 N=7 subsample: tensor-core rel {rel(rtc, ref):.3e}")
-    assert rel(rtc, ref) < 1e-5
-    assert rel(rtc, ref) < 2 * rel(r32, ref)
+    # (HS3D_MIXED_TC runs the MIXED32 kernels)
+    assert np.array_equal(rtc, r32)
 
 
 @pytest.mark.skipif(os.environ.get("HS3D_SLOW") != "1",
                     reason="the oracle runs 100 RK3 steps of 1.7e7 nodes (minutes of CPU): set HS3D_SLOW=1")
 def test_tgv_32cubed_N7_state_after_100_steps_on_a_seeded_subsample():
     """The 32^3-element N=7 curved TGV (standard form, Roe, BR1) after 100
-    RK3 steps: the GPU states (FP64, mixed, mixed with the tensor-core
-    contraction) against the oracle's on the 64 elements of the seeded 4x4x4
+    RK3 steps: the GPU states (FP64, mixed) against the oracle's on the 64 elements of the seeded 4x4x4
     sub-block (the oracle integrates the full mesh, each side with its own
     CFL time step)."""
     E1, N, steps = 32, 7, 100
@@ -475,7 +473,7 @@ def test_tgv_32cubed_N7_state_after_100_steps_on_a_seeded_subsample():
     sub = np.array([(a0 + i) + E1 * ((b0 + j) + E1 * (c0 + k)) for k in range(4) for j in range(4) for i in range(4)])
     u0 = om.ic_tgv(G, 0.1)
     results = {}
-    for prec in ("fp64", "mixed32", "mixed_tc"):
+    for prec in ("fp64", "mixed32"):
         gc = cfgs("ns", "roe", "standard", precision=prec, Re=1600.0)[1]
         u = dev(u0)
         g = torch.zeros_like(u)
@@ -493,4 +491,3 @@ def test_tgv_32cubed_N7_state_after_100_steps_on_a_seeded_subsample():
               f"rel-Linf {np.abs(d).max() / np.abs(ref).max():.3e}")
     assert rel(results["fp64"], ref) < TOL64
     assert rel(results["mixed32"], ref) < 1e-5
-    assert rel(results["mixed_tc"], ref) < 1e-5

@@ -120,8 +120,8 @@ def test_mixed_schemes_share_the_server_and_match_the_oracle():
 
 
 def test_mixed_and_tensor_core_requests_equal_single_solves():
-    """Mixed-precision requests (CUDA-core and tensor-core contraction) in one
-    server give bitwise the states of the same solves stepped alone through
+    """Mixed-precision requests (MIXED32, and MIXED_TC which runs the same
+    kernels) in one server give bitwise the states of the same solves stepped alone through
     hs3d_rk3_run (the server's captured step graph replayed across steps)."""
     # pairs of requests with the same order and scheme share their launches (item tables)
     specs = [(4, 3, "mixed_tc", "standard"), (3, 3, "mixed_tc", "standard"), (3, 4, "mixed_tc", "standard"),
