@@ -401,11 +401,13 @@ hs3d_status hs3d_alu_peaks(double *tflops_out, void *stream);
 
 /* Self-check of the library's integer-pipe FP64->FP32 rounding (used by the
  * mixed path instead of the FP64-pipe conversion): over n DEVICE doubles,
- * counts (DEVICE, 3 x uint64) receives [0] results that differ bitwise from
+ * counts (DEVICE, 4 x uint64) receives [0] results that differ bitwise from
  * the hardware round-to-nearest conversion (inputs in the FP32 normal range,
  * infinities, NaN), [1] FP32->FP64 widenings that differ from the hardware
- * one, [2] inputs below the FP32 normal range (flushed to zero by design).
- * Stream-ordered. */
+ * one, [2] inputs below the FP32 normal range (flushed to zero by design),
+ * [3] finite inputs of magnitude 2^-74 .. 2^127 whose integer-pipe low part
+ * (x - hi rounded to FP32, the float-float split) differs bitwise from the
+ * hardware rounding of the FP64 difference.  Stream-ordered. */
 hs3d_status hs3d_check_rounding(const double *in, int64_t n, unsigned long long *counts, void *stream);
 
 /* ---------------------------------------------------------------- serving */

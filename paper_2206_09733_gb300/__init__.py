@@ -452,9 +452,10 @@ def diagnostics_noalloc(N, E, gamma, J, u, out, dudt=None, nodes="lobatto", stre
 
 def check_rounding(x, stream=None):
     """Counts from hs3d_check_rounding for a float64 CUDA tensor x:
-    (d2f mismatches, widening mismatches, inputs below the FP32 normal range)."""
+    (d2f mismatches, widening mismatches, inputs below the FP32 normal range,
+    float-float split low-part mismatches)."""
     import torch
-    counts = torch.zeros(3, dtype=torch.int64, device=x.device)
+    counts = torch.zeros(4, dtype=torch.int64, device=x.device)
     check(lib().hs3d_check_rounding(_ptr(x, "x"), x.numel(), C.c_void_p(counts.data_ptr()), _stream(stream)))
     torch.cuda.synchronize()
     return tuple(int(v) for v in counts.cpu())

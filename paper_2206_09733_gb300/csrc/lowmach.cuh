@@ -71,11 +71,26 @@ __host__ __device__ __forceinline__ void ff_fma(float &sh, float &sl, float ah, 
 // measured 3-20% slower in all three deviation kernels).
 __device__ __forceinline__ float dev_round(double x) { return d2f_rn(x); }
 
-// FP64 -> (hi, lo) with hi + lo = x to ~2^-48 relative.
+// FP64 -> (hi, lo) with hi = x rounded to FP32 (d2f_rn) and lo = x - hi
+// rounded to FP32, with no FP64 instruction: x - hi is exactly the integer
+// R = (the 29 significand bits the rounding drops) - (2^29 if it rounded
+// up), |R| <= 2^28, times 2^(e - 1075) (e the biased FP64 exponent of x), so
+// lo is the integer-to-float conversion of R (round to nearest) scaled by that
+// power of two, with the sign of x.  Equal to d2f_rn(x - (double)hi) for
+// |x| >= 2^-74 (below, lo is flushed to zero; hi is already zero below the
+// FP32 normal range).
 __device__ __forceinline__ void ff_split(double x, float &hi, float &lo)
 {
     hi = d2f_rn(x);
-    lo = d2f_rn(x - f2d_exact(hi));
+    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+    const unsigned e = (h >> 20) & 0x7ffu;
+    const unsigned t = __funnelshift_l(l, h, 3);   // the kept bits, as d2f_rn truncates them
+    const unsigned dropped = l & 0x1fffffffu;
+    const unsigned up = (dropped + (t & 1u) + 0x0fffffffu) >> 29;   // d2f_rn's rounding increment
+    const int R = (int)dropped - (int)(up << 29);
+    const float scale = (e >= 949u && e <= 1202u) ? __int_as_float((int)(e - 948u) << 23) : 0.0f;
+    const float mag = __int2float_rn(R) * scale;
+    lo = (h & 0x80000000u) ? -mag : mag;
 }
 
 // ------------------------------------------------------------------ anchor

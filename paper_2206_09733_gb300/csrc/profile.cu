@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include "api_internal.h"
+#include "lowmach.cuh"
 #include "physics.cuh"
 
 namespace hs3d {
@@ -71,6 +72,13 @@ __global__ void k_check_rounding(const double *in, long long n, unsigned long lo
         const double a = f2d_exact(hw), b = (double)hw;
         if (__double_as_longlong(a) != __double_as_longlong(b)) atomicAdd(&counts[1], 1ull);
     }
+    const double ax = fabs(x);
+    if (ax >= 5.293955920339377e-23 && ax < 1.7014118346046923e38) {   // 2^-74 .. 2^127
+        float hi, lo;
+        ff_split(x, hi, lo);
+        const float ref = __double2float_rn(x - (double)hi);
+        if (__float_as_int(lo) != __float_as_int(ref) && !(lo == 0.0f && ref == 0.0f)) atomicAdd(&counts[3], 1ull);
+    }
 }
 
 }  // namespace hs3d
@@ -81,7 +89,7 @@ extern "C" hs3d_status hs3d_check_rounding(const double *in, int64_t n, unsigned
 {
     if (!in || !counts || n < 0) return fail(HS3D_ERR_INVALID, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
     if (e == cudaSuccess && n > 0) {
         k_check_rounding<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, counts);
         e = cudaGetLastError();

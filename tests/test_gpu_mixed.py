@@ -128,7 +128,9 @@ def test_mixed_tgv_residual_and_state():
 def test_integer_pipe_rounding_matches_hardware():
     """The mixed path's FP64->FP32 rounding (bit operations) equals the
     hardware round-to-nearest conversion on random and edge-case inputs;
-    the exact widening equals the hardware FP32->FP64 conversion."""
+    the exact widening equals the hardware FP32->FP64 conversion; the
+    float-float split's low part (integer arithmetic and one int->float
+    conversion) equals the hardware rounding of x - hi."""
     rng = np.random.default_rng(0)
     parts = [rng.standard_normal(1 << 20) * 10.0 ** rng.uniform(-30, 30, 1 << 20),
              rng.uniform(-1e3, 1e3, 1 << 20),
@@ -139,6 +141,6 @@ def test_integer_pipe_rounding_matches_hardware():
     parts.append(f + 2.0 ** -24)
     parts.append(f - 2.0 ** -24)
     x = torch.from_numpy(np.concatenate(parts)).cuda()
-    bad, bad_widen, tiny = hs.check_rounding(x)
-    assert bad == 0 and bad_widen == 0
+    bad, bad_widen, tiny, bad_split = hs.check_rounding(x)
+    assert bad == 0 and bad_widen == 0 and bad_split == 0
     assert tiny >= 3
