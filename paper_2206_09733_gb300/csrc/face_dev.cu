@@ -124,6 +124,7 @@ __device__ __forceinline__ void matrix_diss(const Prim<float> &L, const Prim<flo
 template <int N, bool NS>
 __global__ void __launch_bounds__(256) k_face_dev(const __grid_constant__ Batch b, int flux)
 {
+    pdl_wait();
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= b.total_faces * n2) return;
@@ -258,9 +259,8 @@ static cudaError_t face_dev_launch(int physics, int flux, const Batch &b, cudaSt
     const long long total = b.total_faces * n2;
     if (total == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    if (physics == HS3D_NS) k_face_dev<N, true><<<blocks, 256, 0, s>>>(b, flux);
-    else k_face_dev<N, false><<<blocks, 256, 0, s>>>(b, flux);
-    return cudaGetLastError();
+    if (physics == HS3D_NS) return launch_pdl(k_face_dev<N, true>, blocks, 256, 0, s, b, flux);
+    return launch_pdl(k_face_dev<N, false>, blocks, 256, 0, s, b, flux);
 }
 
 cudaError_t launch_face_dev(int N, int physics, int flux, const Batch &b, cudaStream_t s)

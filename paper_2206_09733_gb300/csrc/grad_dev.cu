@@ -59,6 +59,7 @@ template <int N>
 __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid_constant__ Batch b,
                                                                     const Ops *__restrict__ ops)
 {
+    pdl_wait();
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr bool BULK = (n % 2 == 0);
     constexpr int PER = grad_dev_per_elem<N>();
@@ -235,7 +236,8 @@ static cudaError_t grad_dev_launch(const Batch &b, cudaStream_t s)
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    k_grad_dev<N><<<blocks, threads, smem, s>>>(b, ops);
+    cudaError_t e = launch_pdl(k_grad_dev<N>, blocks, threads, smem, s, b, ops);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -211,6 +211,31 @@ __device__ __forceinline__ void warp_max_to_clock(unsigned long long *dst_c, uns
     }
 }
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be
+// scheduled while the kernel before it in the stream drains (its CTAs take
+// the SMs that the other's last CTAs free); it calls pdl_wait() before it
+// reads or writes anything, which returns once that kernel has completed
+// and its memory is visible.  (A no-op for a kernel launched without the
+// attribute.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Asynchronous global->shared copies (cp.async, sm_80+): the copies are
 // issued without staging through registers and waited for once.
 __device__ __forceinline__ void cp_async_16(void *smem, const void *gmem)

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ Batch b,
 // dt), clipped at t_final; advances the clock and resets both maxima slots.
 __global__ void k_dt_finalize(const __grid_constant__ Batch b, int n, int slot)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.nitems) return;
     const Item &it = (b.nitems == 1) ? b.single : b.items[i];
@@ -211,7 +212,8 @@ cudaError_t launch_dt_finalize(int N, const Batch &b, int mode, int slot, cudaSt
         return cudaGetLastError();
     }
     unsigned blocks = (unsigned)((b.nitems + 127) / 128);
-    k_dt_finalize<<<blocks, 128, 0, s>>>(b, N + 1, slot);
+    cudaError_t e = launch_pdl(k_dt_finalize, blocks, 128, 0, s, b, N + 1, slot);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

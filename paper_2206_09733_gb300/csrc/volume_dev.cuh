@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(dev_threads<N>(), dev_min_blocks<N, FORM>())
 k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB,
              int lam_slot, int epb)
 {
+    pdl_wait();
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr bool STD = (FORM == HS3D_VOL_STANDARD);
     constexpr bool EC = (FORM == HS3D_VOL_EC);
@@ -604,8 +605,8 @@ static cudaError_t vol_dev_launch2(const Batch &b, int stage, double rkA, double
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    k_volume_dev<N, NS, FORM><<<blocks, threads, smem, s>>>(b, ops, stage, rkA, rkB, stage >= 0 ? lam_slot : -1, epb);
-    return cudaGetLastError();
+    return launch_pdl(k_volume_dev<N, NS, FORM>, blocks, threads, smem, s, b, ops, stage, rkA, rkB,
+                      stage >= 0 ? lam_slot : -1, epb);
 }
 
 template <int FORM>
