@@ -731,7 +731,7 @@ def serving_sample(reqs, t_final):
     return [dict(reqs[k], t_final=t_final) for k in sorted(picked.values())]
 
 
-def serve(reqs, precision, mode, rate_scale=1.0, finals=None):
+def serve(reqs, precision, mode, rate_scale=1.0, finals=None, launch_mode="grid"):
     """Run requests through one server.  mode "stream": submitted at their
     arrival times (rate_scale stretches them); "batch": all at once;
     "sequential": one at a time, each submitted when the previous finished
@@ -746,7 +746,7 @@ def serve(reqs, precision, mode, rate_scale=1.0, finals=None):
         ic = hs.ic_desc("vortex", GAMMA, r["Ma"], r["beta"], r["xc"], r["yc"])
         return mesh, cfg, ic
 
-    srv = hs.Server()
+    srv = hs.Server(launch_mode=launch_mode)
     m, c, i = descs(reqs[0])                      # warm-up: one short request
     t = srv.submit(m, c, i, t_final=0.05)
     while srv.poll(t)[0] == hs.PENDING:
@@ -804,14 +804,23 @@ def run_serving(count, rate_scale=1.0, sample_t_final=0.25, baselines=True):
     import numpy as np
     import paper_2206_09733_gb300 as hs
     reqs = serving_requests(count)
-    rows = serve(reqs, "mixed32", "stream", rate_scale)
-    failed = {}
-    for v in rows:
-        if v[0] != hs.OK:
-            nm = hs.STATUS_NAMES.get(v[0], str(v[0]))
-            failed[nm] = failed.get(nm, 0) + 1
-    out = serving_summary(rows, {"failed": failed, "arrivals": f"Poisson {200 / rate_scale:g} req/s",
-                                 "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5"})
+    designs = {}
+    for launch_mode in ("grid", "persistent"):
+        rows = serve(reqs, "mixed32", "stream", rate_scale, launch_mode=launch_mode)
+        failed = {}
+        for v in rows:
+            if v[0] != hs.OK:
+                nm = hs.STATUS_NAMES.get(v[0], str(v[0]))
+                failed[nm] = failed.get(nm, 0) + 1
+        designs[launch_mode] = serving_summary(
+            rows, {"failed": failed, "arrivals": f"Poisson {200 / rate_scale:g} req/s",
+                   "scheme": "Euler, LF + EC split form, mixed32, to t=1.0 at CFL 0.5",
+                   "launch_design": launch_mode})
+    out = dict(designs["grid"])
+    out["launch_designs"] = {
+        "grid": "a CTA per tile, binary search over the group's item table",
+        "persistent": "work table (request of every element) + persistent grids walking the tiles",
+        "persistent_run": designs["persistent"]}
     if not baselines:
         return out
     sample = serving_sample(reqs, sample_t_final)

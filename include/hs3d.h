@@ -446,6 +446,16 @@ typedef struct {
 hs3d_status hs3d_server_create(size_t hbm_budget_bytes, int max_batch, hs3d_server **out);
 /* Stops the thread after the running step; unfinished requests are dropped. */
 void hs3d_server_destroy(hs3d_server *server);
+/* Launch design of the shared launches (takes effect at the next step):
+ *   HS3D_LAUNCH_GRID (default): one CTA per tile of elements (faces), each
+ *     finding its request by a binary search over the group's item table;
+ *   HS3D_LAUNCH_PERSISTENT: a work table (the request of every element of a
+ *     group, uploaded when the set of running requests changes) and a
+ *     persistent grid per kernel (as many CTAs as are resident at once), whose
+ *     CTAs walk the tiles with a stride of the grid size.
+ * Both compute the same results bit for bit. */
+enum { HS3D_LAUNCH_GRID = 0, HS3D_LAUNCH_PERSISTENT = 1 };
+hs3d_status hs3d_server_set_launch_mode(hs3d_server *server, int mode);
 /* Copies the request and queues it; never blocks on the GPU.  HS3D_ERR_NOMEM
  * if the request alone exceeds the budget, HS3D_ERR_INVALID for a bad
  * descriptor. */

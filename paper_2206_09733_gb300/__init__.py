@@ -40,7 +40,8 @@ PRECISION = {"fp64": FP64, "mixed32": MIXED32, "mixed_tc": MIXED_TC}
 # every entry point declared in include/hs3d.h
 EXPORTS = ["hs3d_mesh_create", "hs3d_mesh_destroy", "hs3d_mesh_info", "hs3d_mesh_geometry", "hs3d_init_state",
            "hs3d_residual", "hs3d_rk3_step", "hs3d_rk3_run", "hs3d_dt", "hs3d_clock", "hs3d_diagnostics",
-           "hs3d_server_create", "hs3d_server_destroy", "hs3d_submit", "hs3d_poll", "hs3d_server_stats",
+           "hs3d_server_create", "hs3d_server_destroy", "hs3d_server_set_launch_mode", "hs3d_submit", "hs3d_poll",
+           "hs3d_server_stats",
            "hs3d_last_error", "hs3d_version", "hs3d_rk3_step_profiled", "hs3d_alu_peaks",
            "hs3d_diagnostics_noalloc", "hs3d_autotune", "hs3d_check_rounding", "hs3d_pmesh_create", "hs3d_pmesh_create3",
            "hs3d_pmesh_destroy", "hs3d_pmesh_layout", "hs3d_pmesh_geometry", "hs3d_pmesh_init_state",
@@ -108,6 +109,7 @@ def lib():
                 "hs3d_diagnostics": [vp, C.POINTER(SolverCfg), vp, vp, vp, vp],
                 "hs3d_server_create": [C.c_size_t, i, C.POINTER(vp)],
                 "hs3d_server_destroy": [vp],
+                "hs3d_server_set_launch_mode": [vp, i],
                 "hs3d_submit": [vp, C.POINTER(Request), C.POINTER(C.c_uint64)],
                 "hs3d_poll": [vp, C.c_uint64, C.POINTER(Result)],
                 "hs3d_server_stats": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -399,11 +401,18 @@ class PMesh:
 class Server:
     """Continuous-batching solve server (hs3d_server_create / hs3d_submit / hs3d_poll)."""
 
-    def __init__(self, hbm_budget_bytes=0, max_batch=0):
+    def __init__(self, hbm_budget_bytes=0, max_batch=0, launch_mode="grid"):
         h = C.c_void_p()
         check(lib().hs3d_server_create(int(hbm_budget_bytes), int(max_batch), C.byref(h)))
         self._h = h
         self._keep = {}
+        if launch_mode != "grid":
+            self.set_launch_mode(launch_mode)
+
+    def set_launch_mode(self, mode):
+        """"grid" (a CTA per tile, binary search for the request) or
+        "persistent" (work table + persistent grids); hs3d_server_set_launch_mode."""
+        check(lib().hs3d_server_set_launch_mode(self._h, {"grid": 0, "persistent": 1}[mode]))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

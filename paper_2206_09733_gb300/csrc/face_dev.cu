@@ -121,13 +121,11 @@ __device__ __forceinline__ void matrix_diss(const Prim<float> &L, const Prim<flo
     D[4] = hs * (k1 * r1[4] + k2 * 0.5f * v2h + k5 * r5[4] + v1 * P1 + v2 * P2 + v3 * P3);
 }
 
+// Face point t (face gf = t / n^2, point ab = t mod n^2) of the batch.
 template <int N, bool NS>
-__global__ void __launch_bounds__(256) k_face_dev(const __grid_constant__ Batch b, int flux)
+__device__ __forceinline__ void face_dev_point(const Batch &b, int flux, long long t)
 {
-    pdl_wait();
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= b.total_faces * n2) return;
     const long long gf = t / n2;
     const int ab = (int)(t - gf * n2);
     const Item &it = find_item_face(b, gf);
@@ -252,6 +250,19 @@ __global__ void __launch_bounds__(256) k_face_dev(const __grid_constant__ Batch 
     }
 }
 
+// The face kernel: one thread per face point, or (Batch::persistent) a
+// persistent grid striding over the face points.
+template <int N, bool NS>
+__global__ void __launch_bounds__(256) k_face_dev(const __grid_constant__ Batch b, int flux)
+{
+    pdl_wait();
+    constexpr int n2 = (N + 1) * (N + 1);
+    const long long total = b.total_faces * n2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        face_dev_point<N, NS>(b, flux, t);
+}
+
 template <int N>
 static cudaError_t face_dev_launch(int physics, int flux, const Batch &b, cudaStream_t s)
 {
@@ -259,8 +270,12 @@ static cudaError_t face_dev_launch(int physics, int flux, const Batch &b, cudaSt
     const long long total = b.total_faces * n2;
     if (total == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    if (physics == HS3D_NS) return launch_pdl(k_face_dev<N, true>, blocks, 256, 0, s, b, flux);
-    return launch_pdl(k_face_dev<N, false>, blocks, 256, 0, s, b, flux);
+    if (physics == HS3D_NS) {
+        const unsigned grid = b.persistent ? persistent_grid(k_face_dev<N, true>, 256, 0, blocks) : blocks;
+        return launch_pdl(k_face_dev<N, true>, grid, 256, 0, s, b, flux);
+    }
+    const unsigned grid = b.persistent ? persistent_grid(k_face_dev<N, false>, 256, 0, blocks) : blocks;
+    return launch_pdl(k_face_dev<N, false>, grid, 256, 0, s, b, flux);
 }
 
 cudaError_t launch_face_dev(int N, int physics, int flux, const Batch &b, cudaStream_t s)

@@ -55,22 +55,22 @@ __device__ __forceinline__ void grad_dev_vars(const Dev &d, const Anchor &A, flo
     q[3] = (d.dp - Tb * d.dr + rT) * __fdividef(1.0f, d.rho);
 }
 
+// One tile (epb elements) of the gradient kernel; returns true on the thread
+// that initialised its element's bulk-copy barrier.
 template <int N>
-__global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid_constant__ Batch b,
-                                                                    const Ops *__restrict__ ops)
+__device__ __forceinline__ bool grad_dev_tile(const Batch &b, const Ops *__restrict__ ops, long long tile,
+                                              unsigned long long *bulk_bar)
 {
-    pdl_wait();
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr bool BULK = (n % 2 == 0);
     constexpr int PER = grad_dev_per_elem<N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     float *sD = (float *)smem_raw;
     float *sE = sD + ((n * n + 3) & ~3);
     const int epb = blockDim.x / n3;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops->Df[t];
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
-    const long long ge = blockIdx.x * (long long)epb + le;
+    const long long ge = tile * epb + le;
     bool valid = ge < b.total_elems;
     const Item *itp = nullptr;
     int e = 0;
@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
         e = (int)(ge - itp->elem_begin);
         if (itp->clk && itp->clk->done) valid = false;
     }
+    const bool armed = BULK && valid && p == 0;
     float *ja = sE + (size_t)le * PER;
     float *q = ja + 9 * n3;
     float *qn = q + 4 * n3;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
         }
     }
     __syncthreads();
-    if (!valid) return;
+    if (!valid) return armed;
     if constexpr (BULK) {
         if (!mbar_wait(bulk_bar + le, 0, kBulkWaitPolls)) {
             // a wait that ran out of polls poisons the gradients and flags the solve
@@ -222,6 +223,25 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
     float *G = (float *)it.grad + (size_t)e * 12 * n3 + p;
 #pragma unroll
     for (int k = 0; k < 12; ++k) G[k * n3] = acc[k] * ij;
+    return armed;
+}
+
+// The gradient kernel: a CTA per tile, or (Batch::persistent) a persistent
+// grid walking the tiles (as k_volume_dev).
+template <int N>
+__global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid_constant__ Batch b,
+                                                                    const Ops *__restrict__ ops, long long ntiles)
+{
+    pdl_wait();
+    constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+    constexpr bool BULK = ((N + 1) % 2 == 0);
+    __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool armed = grad_dev_tile<N>(b, ops, tile, bulk_bar);
+        if (tile + gridDim.x >= ntiles) break;   // (uniform across the CTA)
+        __syncthreads();
+        if (armed) mbar_inval(bulk_bar + threadIdx.x / n3);
+    }
 }
 
 template <int N>
@@ -236,7 +256,8 @@ static cudaError_t grad_dev_launch(const Batch &b, cudaStream_t s)
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    cudaError_t e = launch_pdl(k_grad_dev<N>, blocks, threads, smem, s, b, ops);
+    const unsigned grid = b.persistent ? persistent_grid(k_grad_dev<N>, threads, smem, blocks) : blocks;
+    cudaError_t e = launch_pdl(k_grad_dev<N>, grid, threads, smem, s, b, ops, (long long)blocks);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

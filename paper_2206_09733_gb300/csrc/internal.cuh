@@ -114,6 +114,12 @@ struct Batch {
     long long total_faces;
     double dt_fixed;        // > 0: every item steps with this dt
     int gauss;              // every item on Gauss-Legendre nodes (items of a batch share the node family)
+    // work table (nitems > 1, optional): item of every element of the batch, items[elem_item[ge]],
+    // instead of a binary search over the items' first elements
+    const int *elem_item;
+    // 1: the element, gradient and face kernels run a persistent grid (as many CTAs as fit at
+    // once) whose CTAs walk the tiles with a stride of the grid size
+    int persistent;
 };
 
 // 1-D operators on the Gauss-Lobatto nodes for one N.
@@ -164,6 +170,7 @@ const Ops *device_ops(int N, int nodes = HS3D_NODES_LOBATTO); // device copy, on
 __device__ __forceinline__ const Item &find_item_elem(const Batch &b, long long ge)
 {
     if (b.nitems == 1) return b.single;
+    if (b.elem_item) return b.items[b.elem_item[ge]];
     int lo = 0, hi = b.nitems - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -175,6 +182,7 @@ __device__ __forceinline__ const Item &find_item_elem(const Batch &b, long long 
 __device__ __forceinline__ const Item &find_item_face(const Batch &b, long long gf)
 {
     if (b.nitems == 1) return b.single;
+    if (b.elem_item) return b.items[b.elem_item[gf / 3]];   // (face_begin = 3 elem_begin)
     int lo = 0, hi = b.nitems - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -236,6 +244,21 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// CTAs of a persistent grid: as many as are resident at once (occupancy x
+// SMs), at most `tiles`.
+template <typename K>
+inline unsigned persistent_grid(K kernel, int threads, size_t smem, unsigned tiles)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return tiles;
+    }
+    const unsigned long long cap = (unsigned long long)per * sms;
+    return tiles < cap ? tiles : (unsigned)cap;
+}
+
 // Asynchronous global->shared copies (cp.async, sm_80+): the copies are
 // issued without staging through registers and waited for once.
 __device__ __forceinline__ void cp_async_16(void *smem, const void *gmem)
@@ -295,6 +318,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 // Wait for phase `parity` of the barrier, at most `limit` polls (each poll
 // may suspend the thread for a hardware-defined interval).  Returns false
 // when the limit ran out.
+// Invalidate a barrier whose copies have all completed, so that the same
+// shared-memory word can be initialised again (the next tile of a
+// persistent CTA).
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit)
 {
     const unsigned a = smem_u32(bar);

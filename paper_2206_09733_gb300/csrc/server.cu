@@ -104,6 +104,13 @@ struct hs3d_server {
     // the captured step of the current set of running requests (ids in table order)
     cudaGraphExec_t gexec = nullptr;
     std::vector<uint64_t> gkey;
+    // launch design (HS3D_LAUNCH_GRID / HS3D_LAUNCH_PERSISTENT), set from any thread; the step
+    // thread re-captures when it differs from the design of the current graph (gmode)
+    std::atomic<int> launch_mode{HS3D_LAUNCH_GRID};
+    int gmode = HS3D_LAUNCH_GRID;
+    // persistent design: the work table, item of every element of every group
+    int *d_elem_item = nullptr;
+    long long elem_cap = 0;
 
     double now() const
     {
@@ -254,7 +261,9 @@ static cudaError_t step_all(hs3d_server *S, std::vector<ServerReq *> &run)
     run.swap(sorted);
     std::vector<uint64_t> key(n);
     for (int k = 0; k < n; ++k) key[k] = run[k]->id;
-    if (!(S->gexec && key == S->gkey)) {
+    const int mode = S->launch_mode.load();
+    if (!(S->gexec && key == S->gkey && mode == S->gmode)) {
+        S->gmode = mode;
         e = capture_step(S, run, items, ranges, cfgs);
         if (e != cudaSuccess) return e;
         S->gkey.swap(key);
@@ -298,6 +307,31 @@ static cudaError_t capture_step(hs3d_server *S, std::vector<ServerReq *> &run, s
     }
     e = cudaMemcpyAsync(S->d_items, items.data(), sizeof(Item) * n, cudaMemcpyHostToDevice, S->stream);
     if (e != cudaSuccess) return e;
+    // persistent design: the work table (item of every element, group by group)
+    const bool persistent = S->gmode == HS3D_LAUNCH_PERSISTENT;
+    std::vector<long long> table_off(ranges.size(), 0);
+    std::vector<int> table;
+    if (persistent) {
+        for (size_t b = 0; b < ranges.size(); ++b) {
+            table_off[b] = (long long)table.size();
+            for (int k = ranges[b].first; k < ranges[b].second; ++k)
+                table.insert(table.end(), (size_t)run[k]->mesh->E, k - ranges[b].first);
+        }
+        if ((long long)table.size() > S->elem_cap) {
+            const long long cap = std::max((long long)table.size(), 2 * S->elem_cap);
+            if (S->d_elem_item) cudaFree(S->d_elem_item);
+            S->d_elem_item = nullptr;
+            S->elem_cap = 0;
+            e = cudaMalloc(&S->d_elem_item, sizeof(int) * cap);
+            if (e != cudaSuccess) return e;
+            S->elem_cap = cap;
+        }
+        if (!table.empty())
+            e = cudaMemcpyAsync(S->d_elem_item, table.data(), sizeof(int) * table.size(), cudaMemcpyHostToDevice,
+                                S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);   // (the host table is freed on return)
+        if (e != cudaSuccess) return e;
+    }
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -315,6 +349,10 @@ static cudaError_t capture_step(hs3d_server *S, std::vector<ServerReq *> &run, s
         for (int k = lo; k < hi; ++k) bt.total_elems += run[k]->mesh->E;
         bt.total_faces = 3 * bt.total_elems;
         bt.gauss = items[lo].gauss;
+        if (persistent) {
+            bt.persistent = 1;
+            if (bt.nitems > 1) bt.elem_item = S->d_elem_item + table_off[b];
+        }
         e = enqueue_rk3_step(run[lo]->req.mesh.N, cfgs[b], bt, 0.0, 0, S->stream);
     }
     if (e == cudaSuccess) {
@@ -454,11 +492,20 @@ void hs3d_server_destroy(hs3d_server *S)
     }
     if (S->gexec) cudaGraphExecDestroy(S->gexec);
     if (S->d_items) cudaFree(S->d_items);
+    if (S->d_elem_item) cudaFree(S->d_elem_item);
     if (S->d_clk) cudaFree(S->d_clk);
     if (S->h_clk) cudaFreeHost(S->h_clk);
     if (S->ev) cudaEventDestroy(S->ev);
     if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
+}
+
+hs3d_status hs3d_server_set_launch_mode(hs3d_server *S, int mode)
+{
+    if (!S) return fail(HS3D_ERR_INVALID, "server is NULL");
+    if (mode != HS3D_LAUNCH_GRID && mode != HS3D_LAUNCH_PERSISTENT) return fail(HS3D_ERR_INVALID, "bad launch mode");
+    S->launch_mode.store(mode);
+    return HS3D_OK;
 }
 
 hs3d_status hs3d_submit(hs3d_server *S, const hs3d_request *req, uint64_t *ticket)

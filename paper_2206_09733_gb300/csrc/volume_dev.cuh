@@ -113,12 +113,13 @@ constexpr int dev_min_blocks()
     return ((N + 1) * (N + 1) * (N + 1) <= 256) ? ((FORM == HS3D_VOL_STANDARD) ? 4 : 3) : 2;
 }
 
+// One tile (epb elements) of the element kernel; returns true on the
+// thread that initialised its element's bulk-copy barrier.
 template <int N, bool NS, int FORM>
-__global__ void __launch_bounds__(dev_threads<N>(), dev_min_blocks<N, FORM>())
-k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB,
-             int lam_slot, int epb)
+__device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__restrict__ ops, int stage, double rkA,
+                                                double rkB, int lam_slot, int epb, long long tile,
+                                                unsigned long long *bulk_bar)
 {
-    pdl_wait();
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
     constexpr bool STD = (FORM == HS3D_VOL_STANDARD);
     constexpr bool EC = (FORM == HS3D_VOL_EC);
@@ -129,7 +130,6 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
     constexpr bool BULK = (n % 2 == 0);
     constexpr int D2 = (n2 + 3) & ~3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     float *sD = (float *)smem_raw;
     float *sDl = sD + D2;
     float *selem = sDl + D2;
@@ -143,7 +143,7 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
         sDl[t] = ops->Dlo[t];
     }
     const int le = threadIdx.x / n3, p = threadIdx.x - le * n3;
-    const long long ge = blockIdx.x * (long long)epb + le;
+    const long long ge = tile * epb + le;
     bool valid = le < epb && ge < b.total_elems;
     const Item *itp = nullptr;
     int e = 0;
@@ -152,6 +152,7 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
         e = (int)(ge - itp->elem_begin);
         if (itp->clk && itp->clk->done) valid = false;
     }
+    const bool armed = BULK && valid && p == 0;
     float *S = sbuf + (size_t)le * PER * n3;
     float *F6 = sface + (size_t)le * 30 * n2;
     float *PB = spair + (size_t)le * 5 * KP * n3;
@@ -589,6 +590,28 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
         }
         warp_max_to_clock(dc, dvp, lc, lv, lam_active);
     }
+    return armed;
+}
+
+// The element kernel: a CTA per tile, or (Batch::persistent) a persistent
+// grid whose CTAs walk the tiles with a stride of the grid size, reusing
+// their shared memory; a tile's element barriers are invalidated before the
+// next tile initialises them again.
+template <int N, bool NS, int FORM>
+__global__ void __launch_bounds__(dev_threads<N>(), dev_min_blocks<N, FORM>())
+k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB,
+             int lam_slot, int epb, long long ntiles)
+{
+    pdl_wait();
+    constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+    constexpr bool BULK = ((N + 1) % 2 == 0);
+    __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool armed = volume_dev_tile<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, tile, bulk_bar);
+        if (tile + gridDim.x >= ntiles) break;   // (uniform across the CTA)
+        __syncthreads();
+        if (armed) mbar_inval(bulk_bar + threadIdx.x / n3);
+    }
 }
 
 // ------------------------------------------------------------------ launch (one volume form)
@@ -605,8 +628,9 @@ static cudaError_t vol_dev_launch2(const Batch &b, int stage, double rkA, double
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    return launch_pdl(k_volume_dev<N, NS, FORM>, blocks, threads, smem, s, b, ops, stage, rkA, rkB,
-                      stage >= 0 ? lam_slot : -1, epb);
+    const unsigned grid = b.persistent ? persistent_grid(k_volume_dev<N, NS, FORM>, threads, smem, blocks) : blocks;
+    return launch_pdl(k_volume_dev<N, NS, FORM>, grid, threads, smem, s, b, ops, stage, rkA, rkB,
+                      stage >= 0 ? lam_slot : -1, epb, (long long)blocks);
 }
 
 template <int FORM>

@@ -256,3 +256,49 @@ srv.close()
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert int(r.stdout.split()[-1]) == hs.ERR_TIMEOUT
+
+
+def _tgv_request(E, N, precision, physics, surface, volume, amp):
+    mesh = hs.mesh_desc(E, E, E, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=amp)
+    cfg = hs.solver_cfg(physics, surface, volume, precision, gamma=G, Re=800.0, Pr=0.72, Ma=0.1, cfl=0.5)
+    ic = hs.ic_desc("tgv", G, 0.1)
+    return mesh, cfg, ic
+
+
+def test_persistent_launches_equal_grid_launches_and_single_solves():
+    """The persistent design (work table + persistent grids whose CTAs walk
+    several tiles: groups here hold more tiles than fit on the GPU at once)
+    gives bitwise the states of the grid design and of the same solves
+    stepped alone -- Navier-Stokes on the bulk-copy (N = 3) and per-thread
+    copy (N = 2, 4) staging paths, the split and standard forms, FP64 and
+    mixed precision."""
+    specs = [(14, 3, "mixed32", "ns", "roe", "ec", 0.05), (12, 3, "mixed32", "ns", "roe", "ec", 0.03),
+             (13, 3, "mixed32", "ns", "roe", "ec", 0.0),
+             (16, 2, "mixed32", "euler", "lf", "standard", 0.04), (15, 2, "mixed32", "euler", "lf", "standard", 0.0),
+             (8, 4, "mixed32", "ns", "roe", "standard", 0.05), (9, 4, "mixed32", "ns", "roe", "standard", 0.02),
+             (6, 3, "fp64", "ns", "roe", "ec", 0.05), (5, 3, "fp64", "ns", "roe", "ec", 0.0)]
+    n_steps = 3
+    finals = {}
+    for mode in ("grid", "persistent"):
+        srv = hs.Server(launch_mode=mode)
+        tickets, outs = [], []
+        for E, N, prec, phys, surf, vol, amp in specs:
+            mesh, cfg, ic = _tgv_request(E, N, prec, phys, surf, vol, amp)
+            out = np.zeros((E ** 3, 5, N + 1, N + 1, N + 1))
+            tickets.append(srv.submit(mesh, cfg, ic, n_steps=n_steps, result=out))
+            outs.append(out)
+        res = wait_all(srv, tickets)
+        srv.close()
+        for t in tickets:
+            assert res[t][0] == hs.OK and res[t][1].steps == n_steps
+        finals[mode] = outs
+    for a, b in zip(finals["grid"], finals["persistent"]):
+        assert np.array_equal(a, b)
+    for k in (0, 3, 5):
+        E, N, prec, phys, surf, vol, amp = specs[k]
+        gm = hs.Mesh(E, E, E, N, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=amp)
+        u = gm.init_state(gm.empty_state(), "tgv", G, 0.1)
+        g = torch.zeros_like(u)
+        gm.rk3_run(hs.solver_cfg(phys, surf, vol, prec, gamma=G, Re=800.0, Pr=0.72, Ma=0.1, cfl=0.5), u, g, n_steps)
+        torch.cuda.synchronize()
+        assert np.array_equal(finals["persistent"][k], u.cpu().numpy()), specs[k]
