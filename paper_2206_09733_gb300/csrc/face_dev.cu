@@ -253,7 +253,7 @@ __device__ __forceinline__ void face_dev_point(const Batch &b, int flux, long lo
 // The face kernel: one thread per face point, or (Batch::persistent) a
 // persistent grid striding over the face points.
 template <int N, bool NS>
-__global__ void __launch_bounds__(256) k_face_dev(const __grid_constant__ Batch b, int flux)
+__global__ void __launch_bounds__(256, 4) k_face_dev(const __grid_constant__ Batch b, int flux)
 {
     pdl_wait();
     constexpr int n2 = (N + 1) * (N + 1);

@@ -226,9 +226,16 @@ __device__ __forceinline__ bool grad_dev_tile(const Batch &b, const Ops *__restr
     return armed;
 }
 
-// The gradient kernel: a CTA per tile, or (Batch::persistent) a persistent
-// grid walking the tiles (as k_volume_dev).
 template <int N>
+__device__ __noinline__ bool grad_dev_tile_call(const Batch &b, const Ops *__restrict__ ops, long long tile,
+                                                unsigned long long *bulk_bar)
+{
+    return grad_dev_tile<N>(b, ops, tile, bulk_bar);
+}
+
+// The gradient kernel: a CTA per tile, or (PERSIST, Batch::persistent) a
+// persistent grid walking the tiles (as k_volume_dev).
+template <int N, bool PERSIST>
 __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid_constant__ Batch b,
                                                                     const Ops *__restrict__ ops, long long ntiles)
 {
@@ -236,11 +243,15 @@ __global__ void __launch_bounds__(grad_dev_threads<N>()) k_grad_dev(const __grid
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
     constexpr bool BULK = ((N + 1) % 2 == 0);
     __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const bool armed = grad_dev_tile<N>(b, ops, tile, bulk_bar);
-        if (tile + gridDim.x >= ntiles) break;   // (uniform across the CTA)
-        __syncthreads();
-        if (armed) mbar_inval(bulk_bar + threadIdx.x / n3);
+    if constexpr (!PERSIST) {
+        grad_dev_tile<N>(b, ops, blockIdx.x, bulk_bar);
+    } else {
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const bool armed = grad_dev_tile_call<N>(b, ops, tile, bulk_bar);
+            if (tile + gridDim.x >= ntiles) break;   // (uniform across the CTA)
+            __syncthreads();
+            if (armed) mbar_inval(bulk_bar + threadIdx.x / n3);
+        }
     }
 }
 
@@ -256,19 +267,33 @@ static cudaError_t grad_dev_launch(const Batch &b, cudaStream_t s)
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    const unsigned grid = b.persistent ? persistent_grid(k_grad_dev<N>, threads, smem, blocks) : blocks;
-    cudaError_t e = launch_pdl(k_grad_dev<N>, grid, threads, smem, s, b, ops, (long long)blocks);
+    cudaError_t e;
+    if (b.persistent) {
+        const unsigned grid = persistent_grid(k_grad_dev<N, true>, threads, smem, blocks);
+        e = launch_pdl(k_grad_dev<N, true>, grid, threads, smem, s, b, ops, (long long)blocks);
+    } else {
+        e = launch_pdl(k_grad_dev<N, false>, blocks, threads, smem, s, b, ops, (long long)blocks);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+template <int N, bool PERSIST>
+static cudaError_t grad_dev_prep_one()
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_grad_dev<N, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_grad_dev<N, PERSIST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 template <int N>
 static cudaError_t grad_dev_prep()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_grad_dev<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad_dev<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = grad_dev_prep_one<N, false>();
+    if (e == cudaSuccess) e = grad_dev_prep_one<N, true>();
     return e;
 }
 

@@ -593,11 +593,21 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
     return armed;
 }
 
-// The element kernel: a CTA per tile, or (Batch::persistent) a persistent
-// grid whose CTAs walk the tiles with a stride of the grid size, reusing
-// their shared memory; a tile's element barriers are invalidated before the
-// next tile initialises them again.
+// The tile as a separate function for the persistent loop (inlined into a
+// loop, its values were hoisted across iterations and spilled).
 template <int N, bool NS, int FORM>
+__device__ __noinline__ bool volume_dev_tile_call(const Batch &b, const Ops *__restrict__ ops, int stage, double rkA,
+                                                  double rkB, int lam_slot, int epb, long long tile,
+                                                  unsigned long long *bulk_bar)
+{
+    return volume_dev_tile<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, tile, bulk_bar);
+}
+
+// The element kernel: a CTA per tile, or (PERSIST, Batch::persistent) a
+// persistent grid whose CTAs walk the tiles with a stride of the grid size,
+// reusing their shared memory; a tile's element barriers are invalidated
+// before the next tile initialises them again.
+template <int N, bool NS, int FORM, bool PERSIST>
 __global__ void __launch_bounds__(dev_threads<N>(), dev_min_blocks<N, FORM>())
 k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB,
              int lam_slot, int epb, long long ntiles)
@@ -606,11 +616,16 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
     constexpr bool BULK = ((N + 1) % 2 == 0);
     __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const bool armed = volume_dev_tile<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, tile, bulk_bar);
-        if (tile + gridDim.x >= ntiles) break;   // (uniform across the CTA)
-        __syncthreads();
-        if (armed) mbar_inval(bulk_bar + threadIdx.x / n3);
+    if constexpr (!PERSIST) {
+        volume_dev_tile<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, blockIdx.x, bulk_bar);
+    } else {
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const bool armed =
+                volume_dev_tile_call<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, tile, bulk_bar);
+            if (tile + gridDim.x >= ntiles) break;   // (uniform across the CTA)
+            __syncthreads();
+            if (armed) mbar_inval(bulk_bar + threadIdx.x / n3);
+        }
     }
 }
 
@@ -628,8 +643,12 @@ static cudaError_t vol_dev_launch2(const Batch &b, int stage, double rkA, double
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    const unsigned grid = b.persistent ? persistent_grid(k_volume_dev<N, NS, FORM>, threads, smem, blocks) : blocks;
-    return launch_pdl(k_volume_dev<N, NS, FORM>, grid, threads, smem, s, b, ops, stage, rkA, rkB,
+    if (b.persistent) {
+        const unsigned grid = persistent_grid(k_volume_dev<N, NS, FORM, true>, threads, smem, blocks);
+        return launch_pdl(k_volume_dev<N, NS, FORM, true>, grid, threads, smem, s, b, ops, stage, rkA, rkB,
+                          stage >= 0 ? lam_slot : -1, epb, (long long)blocks);
+    }
+    return launch_pdl(k_volume_dev<N, NS, FORM, false>, blocks, threads, smem, s, b, ops, stage, rkA, rkB,
                       stage >= 0 ? lam_slot : -1, epb, (long long)blocks);
 }
 
@@ -649,19 +668,22 @@ cudaError_t launch_volume_dev_form(int N, int physics, const Batch &b, int stage
     return cudaErrorInvalidValue;
 }
 
+template <typename K>
+static cudaError_t prep_vol_dev_kernel(K kernel)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <int N, int FORM>
 static cudaError_t prep_vol_dev_n()
 {
-    const int big = 220 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_volume_dev<N, false, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_volume_dev<N, true, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_volume_dev<N, false, FORM>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_volume_dev<N, true, FORM>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = prep_vol_dev_kernel(k_volume_dev<N, false, FORM, false>);
+    if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, true, FORM, false>);
+    if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, false, FORM, true>);
+    if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, true, FORM, true>);
     return e;
 }
 
