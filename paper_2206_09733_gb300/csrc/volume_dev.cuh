@@ -103,14 +103,19 @@ __device__ __forceinline__ int dev_line_node(int d, int idx, int ta, int tb)
     return ta + n * (tb + n * idx);
 }
 
-// Minimum resident CTAs asked of the compiler (its register budget): the
-// standard form keeps 4 (64 registers, no spills); the split forms hold
-// about 55 KB of shared memory per 256-thread CTA, so at most 3 are resident
-// anyway, and 3 leave them 85 registers (64 spilled 100-200 bytes per thread).
+// Minimum resident CTAs asked of the compiler (its register budget), for
+// CTAs of up to 256 threads: the split forms 4 (64 registers; with about
+// 55 KB of shared memory per CTA, 4 are resident; ~56 bytes of spills per
+// thread, and still 8-12% faster than 3 CTAs at 80 registers, 16^3 and 32^3
+// N = 3, EC and KG); the standard form 5 up to N = 3 (48 registers, ~50
+// bytes of spills: -4% at 64^3 N = 3) and 4 above (no spills; 5 measured
+// +3% at N = 4).
 template <int N, int FORM>
 constexpr int dev_min_blocks()
 {
-    return ((N + 1) * (N + 1) * (N + 1) <= 256) ? ((FORM == HS3D_VOL_STANDARD) ? 4 : 3) : 2;
+    constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
+    if (n3 > 256) return 2;
+    return (FORM == HS3D_VOL_STANDARD && n3 <= 64) ? 5 : 4;
 }
 
 // One tile (epb elements) of the element kernel; returns true on the
