@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--volume", default=None, help="profiling runs: volume form (default ec)")
     ap.add_argument("--physics", default=None, choices=["euler", "ns"], help="profiling runs: equations (default ns)")
     ap.add_argument("--surface", default=None, help="profiling runs: surface flux (default roe)")
+    ap.add_argument("--aniso-profile", type=int, default=0, metavar="E",
+                    help="profiling run only: 2 FP64 RK3 steps of the E^3 TGV with per-direction degrees 2..5 "
+                         "(NS, EC + Roe), then exit")
     ap.add_argument("--pmesh-profile", type=int, default=0, metavar="E",
                     help="profiling run only: 3 mixed RK3 steps of the E^3 TGV with per-element degrees 2..5 "
                          "(NS, EC + Roe), then exit")
@@ -208,8 +211,8 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of k_volume_dev<3,NS,EC> on this workload,
 # from one ncu capture (profiles/k_volume_mixed_ec_ns_N3_tgv16_traffic.md), and the digest of the
 # kernel's sources at the time of the capture: the figure is reported only while they are unchanged.
-VOLUME_TRAFFIC = {"bytes_per_launch": 49779541,
-                  "sources_sha256": "d6cc5af3683c6d0b55cd49699e713b84e9edc1912c784041bbec54ecd63357ee"}
+VOLUME_TRAFFIC = {"bytes_per_launch": 57363371,
+                  "sources_sha256": "6c1315c365a2b548ed0225ac8980edb1bd5f7e11cb2b186ab9fe2aa1c428f907"}
 VOLUME_SOURCES = ["volume_dev.cuh", "lowmach.cuh", "volume_ec.cu", "physics.cuh", "internal.cuh"]
 
 
@@ -1024,10 +1027,32 @@ def pmesh_profile(E):
     print(json.dumps({"pmesh_profile": E, "clock": pm.clock()}))
 
 
+def aniso_profile(E):
+    """The anisotropic-degree kernels alone, for an ncu launch list or
+    capture: mesh set-up, one initial condition and 2 FP64 RK3 steps (per
+    stage two mortar launches, then the gradient and element kernels of
+    every node-count class)."""
+    import numpy as np
+    import torch
+
+    import paper_2206_09733_gb300 as hs
+    deg = np.random.default_rng(7).integers(2, 6, size=(E ** 3, 3)).astype(np.int32)
+    pm = hs.PMesh(E, E, E, deg, lo=(-np.pi,) * 3, hi=(np.pi,) * 3, amp=AMP)
+    cfg = hs.solver_cfg("ns", "roe", "ec", "fp64", gamma=GAMMA, Re=RE, Pr=PR, Ma=MA, cfl=CFL)
+    u = pm.init_state(pm.empty_state(), "tgv", GAMMA, MA)
+    g = torch.zeros_like(u)
+    pm.run(cfg, u, g, 2)
+    torch.cuda.synchronize()
+    print(json.dumps({"aniso_profile": E, "clock": pm.clock()}))
+
+
 def main():
     args = parse()
     if args.pmesh_profile:
         pmesh_profile(args.pmesh_profile)
+        return
+    if args.aniso_profile:
+        aniso_profile(args.aniso_profile)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":
