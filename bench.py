@@ -481,7 +481,7 @@ def run_hs3d(args, world, rank, local):
                    "precision": "mixed32: FP32 flux arithmetic on deviations from a per-element reference state "
                                 "(deviations formed in FP64 from the FP64 state), mass divergence in float-float "
                                 "(FP32 pairs), FP32 copies of Ja (+ FP32 low part), 1/J and face normals; FP64 "
-                                "state, RK registers and accumulation",
+                                "state and RK accumulation, FP32 RK register",
                    "l2": "flushed between timed steps (512 MB write outside the step events)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "timing": "sum of per-step CUDA-event times on the launching stream, CUDA-graph replay"},
