@@ -30,8 +30,7 @@ constexpr int grad_dev_threads()
 }
 
 // Shared-memory floats per element: metric terms [9][n3], q' [4][n3],
-// neighbour-trace deviations [6][4][n2]; before them, one block per element
-// with its reference state (5 doubles and the FP32 Anchor, 24 floats).
+// neighbour-trace deviations [6][4][n2].
 template <int N>
 constexpr int grad_dev_per_elem()
 {

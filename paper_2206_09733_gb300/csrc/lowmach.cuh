@@ -109,6 +109,7 @@ struct Anchor {
     float rho, m1, m2, m3, E;
     float v1, v2, v3, p, beta, H;
     float rbeta, rH, cK;
+    float ib, pr;   // 1/beta and p/rho, factors of the flux formulas
 };
 
 // uc: the FP64 state at the anchor node; ad receives the FP64 conserved anchor.
@@ -136,6 +137,8 @@ __device__ __forceinline__ Anchor make_anchor(const double uc[5], float gm1, flo
     A.E = d2f_rn(ad[4]);
     A.beta = A.rho / (2.0f * A.p);
     A.rbeta = fmaf(-2.0f * A.p, A.beta, A.rho);
+    A.ib = __fdividef(1.0f, A.beta);
+    A.pr = A.p * __fdividef(1.0f, A.rho);
     // H = hg/beta + |v|^2/2 + p/rho in FP32, every rounding residual into cK
     const float x = hg / A.beta;
     const float e1 = (fmaf(-x, A.beta, hg) + hglo) / A.beta;
@@ -171,6 +174,8 @@ __device__ __forceinline__ Anchor make_anchor_face(const double uc[5], float gm1
     A.p = gm1 * (A.E - 0.5f * (A.m1 * A.v1 + A.m2 * A.v2 + A.m3 * A.v3));
     A.beta = 0.5f * A.rho * __fdividef(1.0f, A.p);
     A.H = (A.E + A.p) * ir;
+    A.ib = __fdividef(1.0f, A.beta);
+    A.pr = A.p * __fdividef(1.0f, A.rho);
     A.rbeta = 0.0f;
     A.rH = 0.0f;
     A.cK = 0.0f;
@@ -192,7 +197,7 @@ __device__ __forceinline__ Anchor make_anchor_face(const double uc[5], float gm1
 struct AnchorRec {
     double ad[5];
     Anchor a;
-    float pad[4];
+    float pad[2];
 };
 static_assert(sizeof(AnchorRec) == 112, "AnchorRec layout");
 
@@ -215,7 +220,7 @@ __device__ __forceinline__ void write_anchor(const Item &it, int e, const double
 {
     AnchorRec r;
     r.a = make_anchor(u, it.gm1f, it.hgf, it.hglof, it.igm1f, r.ad);
-    r.pad[0] = r.pad[1] = r.pad[2] = r.pad[3] = 0.0f;
+    r.pad[0] = r.pad[1] = 0.0f;
     ((AnchorRec *)it.anc)[e] = r;
 }
 
@@ -379,18 +384,18 @@ __device__ __forceinline__ void dflux_ec(const ECDev &L, const ECDev &Rr, const 
     const float dr = L.dr - Rr.dr, db = L.db - Rr.db;
     const float fr = dr * isr, ur = fr * fr;
     const float rbar_m = 0.5f * (L.dr + Rr.dr);   // {rho'}
-    float rh_m;                                    // rho^ - {rho}
-    if (ur < LogMeanEps<float>::v)
-        rh_m = -0.5f * sr * ur * ((1.0f / 3.0f) + ur * ((4.0f / 45.0f) + ur * (44.0f / 945.0f)));
-    else
-        rh_m = __fdividef(dr, logf(rL) - logf(rR)) - 0.5f * sr;
     const float fb = db * isb, ub = fb * fb;
-    float ibd;                                     // 1/beta^ - 1/betabar
-    if (ub < LogMeanEps<float>::v)
-        ibd = -(L.db + Rr.db) * isb * __fdividef(1.0f, A.beta) +
-              2.0f * isb * ub * ((1.0f / 3.0f) + ub * (0.2f + ub * (1.0f / 7.0f)));
-    else
-        ibd = __fdividef(logf(bL) - logf(bR), db) - __fdividef(1.0f, A.beta);
+    // rho^ - {rho} and 1/beta^ - 1/betabar on the series branch, replaced by the
+    // logarithmic form where the jump is large; the common case is the series,
+    // and a warp vote keeps the logarithms off the warps that need none
+    float rh_m = -0.5f * sr * ur * ((1.0f / 3.0f) + ur * ((4.0f / 45.0f) + ur * (44.0f / 945.0f)));
+    float ibd = -(L.db + Rr.db) * isb * A.ib +
+                2.0f * isb * ub * ((1.0f / 3.0f) + ub * (0.2f + ub * (1.0f / 7.0f)));
+    const bool log_r = !(ur < LogMeanEps<float>::v), log_b = !(ub < LogMeanEps<float>::v);
+    if (__any_sync(__activemask(), log_r || log_b)) {
+        if (log_r) rh_m = __fdividef(dr, logf(rL) - logf(rR)) - 0.5f * sr;
+        if (log_b) ibd = __fdividef(logf(bL) - logf(bR), db) - A.ib;
+    }
     const float rhd = rbar_m + rh_m;               // rho^ - rhobar
     const float dv1 = 0.5f * (L.dv1 + Rr.dv1), dv2 = 0.5f * (L.dv2 + Rr.dv2), dv3 = 0.5f * (L.dv3 + Rr.dv3);
     const float mv1 = A.v1 + dv1, mv2 = A.v2 + dv2, mv3 = A.v3 + dv3;
@@ -410,7 +415,7 @@ __device__ __forceinline__ void dflux_ec(const ECDev &L, const ECDev &Rr, const 
     const float q2d = 0.5f * (L.q + Rr.q);
     const float m2d = dv1 * (mv1 + A.v1) + dv2 * (mv2 + A.v2) + dv3 * (mv3 + A.v3);
     const float Kd = hg * ibd - 0.5f * q2d + m2d + A.cK;
-    rest = (ptd - A.p * __fdividef(1.0f, A.rho) * rhd) * va + (Fbr + frho) * Kd;
+    rest = (ptd - A.pr * rhd) * va + (Fbr + frho) * Kd;
 }
 
 // dflux_ec at u_i = u_m (the diagonal pair of the volume term): the
@@ -423,7 +428,7 @@ __device__ __forceinline__ void dflux_ec_diag(const ECDev &z, const Anchor &A, f
 {
     const float b = A.beta + z.db;
     const float ib = __fdividef(1.0f, b);
-    const float ibd = -z.db * ib * __fdividef(1.0f, A.beta);
+    const float ibd = -z.db * ib * A.ib;
     const float v1 = A.v1 + z.dv1, v2 = A.v2 + z.dv2, v3 = A.v3 + z.dv3;
     const float va = v1 * a1 + v2 * a2 + v3 * a3;
     const float vda = z.dv1 * a1 + z.dv2 * a2 + z.dv3 * a3;
@@ -434,7 +439,7 @@ __device__ __forceinline__ void dflux_ec_diag(const ECDev &z, const Anchor &A, f
     fm[1] = frho * v2 + Fbr * z.dv2 + ptd * a2;
     fm[2] = frho * v3 + Fbr * z.dv3 + ptd * a3;
     const float Kd = hg * ibd + 0.5f * z.q + A.cK;
-    rest = (ptd - A.p * __fdividef(1.0f, A.rho) * z.dr) * va + (Fbr + frho) * Kd;
+    rest = (ptd - A.pr * z.dr) * va + (Fbr + frho) * Kd;
 }
 
 }  // namespace hs3d

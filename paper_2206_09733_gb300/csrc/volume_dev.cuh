@@ -31,6 +31,8 @@
 // cp.async, issued at the start and awaited before the surface term.
 #pragma once
 
+#include <stddef.h>
+
 #include "internal.cuh"
 #include "lowmach.cuh"
 #include "physics.cuh"
@@ -68,11 +70,14 @@ constexpr int dev_visc_off()
 }
 
 // Per-element block of shared memory, 36 floats: the element's reference
-// state, computed once by its centre-node thread before the first barrier
-// (FP64 conserved values [0, 10), the FP32 Anchor [10, 24)), and the centre
-// node's metric terms (EC, [24, 33)).
+// state record, copied in by the element's first seven threads before a
+// barrier at the start (FP64 conserved values [0, 10), the FP32 Anchor
+// [10, 26)), and the centre node's metric terms (EC, [26, 35)).  Read from
+// shared memory, the record holds no registers while the node's inputs are
+// in flight.
 constexpr int kDevElemBlock = 36;
-static_assert(sizeof(Anchor) == 14 * sizeof(float), "Anchor layout");
+static_assert(sizeof(Anchor) == 16 * sizeof(float) && offsetof(AnchorRec, a) == 10 * sizeof(float),
+              "reference-state record layout");
 
 // Byte offset of the RK staging block (16-byte aligned): D, Dlo, per-element
 // blocks, per-node staging, face blocks, pair buffers (split forms).
@@ -93,6 +98,16 @@ __host__ __device__ constexpr size_t dev_smem_bytes(int epb)
     constexpr int n3 = (N + 1) * (N + 1) * (N + 1);
     constexpr bool SG = (FORM == HS3D_VOL_STANDARD);
     return dev_rk_offset<N, NS, FORM>(epb) + (size_t)epb * n3 * ((SG ? 20 : 0) + 4);
+}
+
+// The node's FP64 state read again after the pair phase instead of being
+// kept in registers across it (an L2 hit; registers are the kernel's
+// limit): a load the compiler does not merge with the first one.
+__device__ __forceinline__ double reload_state(const double *ptr)
+{
+    double x;
+    asm volatile("ld.global.f64 %0, [%1];" : "=d"(x) : "l"(ptr));
+    return x;
 }
 
 template <int n>
@@ -163,26 +178,28 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
     float *PB = spair + (size_t)le * 5 * KP * n3;
     double *AD = (double *)(selem + (size_t)le * kDevElemBlock);     // reference state, FP64 conserved
     Anchor *ANC = (Anchor *)(selem + (size_t)le * kDevElemBlock + 10);
-    float *CEN = selem + (size_t)le * kDevElemBlock + 24;            // centre metric terms (EC)
+    float *CEN = selem + (size_t)le * kDevElemBlock + 26;            // centre metric terms (EC)
     const int ijk[3] = {p % n, (p / n) % n, p / n2};
     constexpr int pc = anchor_node(n);   // centre node: the element's reference state
 
     double u[5];
-    AnchorRec R;   // the element's reference state, left by the pass before
     if (valid) {
         const double *U = itp->u + (size_t)e * 5 * n3;
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = U[v * n3 + p];
-        R = load_anchor(itp->anc, e);
-        if (p == pc) {   // a copy for the pair phase and the surface term (read after later barriers)
-            *ANC = R.a;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) AD[v] = R.ad[v];
+        // the element's reference state, left by the pass before, into its shared
+        // block (its first 26 floats: the record's padding would overwrite CEN)
+        if (p < 7) {
+            const float4 x = __ldg((const float4 *)((const AnchorRec *)itp->anc + e) + p);
+            float *blk = selem + (size_t)le * kDevElemBlock;
+            if (p < 6) ((float4 *)blk)[p] = x;
+            else ((float2 *)blk)[12] = make_float2(x.x, x.y);
         }
         // the thread that initialises the element's barrier is the one that arms it
         // and issues the copies; the others poll it only after the staging barrier
         if (BULK && p == 0) mbar_init(bulk_bar + le, 1);
     }
+    __syncthreads();
     float V[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     float Ch = 0.0f, Cl = 0.0f;   // float-float C (low-Mach forms)
     float Hb = 0.0f;
@@ -222,10 +239,10 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
             }
         }
         const float gm1 = it.gm1f, hg = it.hgf;
-        const Anchor A = R.a;
+        const Anchor A = *ANC;
         double ad[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) ad[v] = R.ad[v];
+        for (int v = 0; v < 5; ++v) ad[v] = AD[v];
         Hb = A.H;
         // momentum deviations as FP32 pairs (hi: the deviation rounded once; lo: the rest)
         float mh[3], ml[3];
@@ -365,7 +382,7 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
         const float gam = valid ? itp->gammaf : 0.0f;
         Anchor A{};
         if (EC && valid) A = *ANC;
-#pragma unroll 1
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int sd = (d == 0) ? 1 : (d == 1) ? n : n2;
             if (valid) {
@@ -471,6 +488,8 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
     bool lam_active = false;
     if (valid) {
     const Item &it = *itp;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = reload_state(it.u + (size_t)e * 5 * n3 + v * n3 + p);
     const float iw = ops->iw0f;
     // volume rows: mass = C (+ the split form's remainder), energy = Hbar mass + rest
     float Vr = V[0];
