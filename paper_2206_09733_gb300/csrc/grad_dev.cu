@@ -103,9 +103,6 @@ __device__ __forceinline__ bool grad_dev_tile(const Batch &b, const Ops *__restr
         }
         const float gm1 = it.gm1f;
         const Anchor A = R.a;
-        double ad[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) ad[v] = R.ad[v];
         const float Tb = A.p * __fdividef(1.0f, A.rho);
         const float rT = fmaf(-Tb, A.rho, A.p);
         constexpr int IT = (6 * n2 + n3 - 1) / n3;
@@ -145,13 +142,13 @@ __device__ __forceinline__ bool grad_dev_tile(const Batch &b, const Ops *__restr
                 if (t < 6 * n2) {
                     const int slot = t / n2, ab = t - slot * n2;
                     float g4[4];
-                    grad_dev_vars(make_dev(raw[k], ad, A, gm1), A, Tb, rT, g4);
+                    grad_dev_vars(make_dev_rec(raw[k], A, R.Elo, gm1), A, Tb, rT, g4);
 #pragma unroll
                     for (int v = 0; v < 4; ++v) qn[(slot * 4 + v) * n2 + ab] = g4[v];
                 }
             }
         }
-        grad_dev_vars(make_dev(uo, ad, A, gm1), A, Tb, rT, qin);
+        grad_dev_vars(make_dev_rec(uo, A, R.Elo, gm1), A, Tb, rT, qin);
 #pragma unroll
         for (int v = 0; v < 4; ++v) q[v * n3 + p] = qin[v];
         if constexpr (!BULK) {

@@ -197,7 +197,8 @@ __device__ __forceinline__ Anchor make_anchor_face(const double uc[5], float gm1
 struct AnchorRec {
     double ad[5];
     Anchor a;
-    float pad[2];
+    float Elo;   // ad[4] - a.E rounded to FP32 (a.E is ad[4] rounded)
+    float pad;
 };
 static_assert(sizeof(AnchorRec) == 112, "AnchorRec layout");
 
@@ -220,8 +221,20 @@ __device__ __forceinline__ void write_anchor(const Item &it, int e, const double
 {
     AnchorRec r;
     r.a = make_anchor(u, it.gm1f, it.hgf, it.hglof, it.igm1f, r.ad);
-    r.pad[0] = r.pad[1] = 0.0f;
+    r.Elo = d2f_rn(r.ad[4] - f2d_exact(r.a.E));
+    r.pad = 0.0f;
     ((AnchorRec *)it.anc)[e] = r;
+}
+
+// u - ad for an FP64 value u and a reference value given as an FP32 pair
+// (h, l), with no FP64 instruction: u = uh + ul + r by ff_split (|r| <=
+// 2^-48 |u|), then (uh - h) + (ul - l) in FP32: the deviation within ~1.5 ulp
+// of its FP32 rounding, plus 2^-48 |u|.
+__device__ __forceinline__ float dev_one(double u, float h, float l)
+{
+    float uh, ul;
+    ff_split(u, uh, ul);
+    return (uh - h) + (ul - l);
 }
 
 // ------------------------------------------------------------------ deviations of one node
@@ -260,6 +273,16 @@ __device__ __forceinline__ Dev make_dev_f(float dr, float dm1, float dm2, float 
     d.dp = gm1 * (dE - 0.5f * mv);
     d.p = A.p + d.dp;
     return d;
+}
+
+// make_dev from the record's FP32 values alone: the conserved reference values
+// as FP32 pairs, rho (exact), m = rho v (a product of two FP32 numbers: its
+// rounding a.m and the FMA residual) and E (a.E and Elo).
+__device__ __forceinline__ Dev make_dev_rec(const double u[5], const Anchor &A, float Elo, float gm1)
+{
+    return make_dev_f(dev_one(u[0], A.rho, 0.0f), dev_one(u[1], A.m1, fmaf(A.rho, A.v1, -A.m1)),
+                      dev_one(u[2], A.m2, fmaf(A.rho, A.v2, -A.m2)), dev_one(u[3], A.m3, fmaf(A.rho, A.v3, -A.m3)),
+                      dev_one(u[4], A.E, Elo), A, gm1);
 }
 
 __device__ __forceinline__ Dev make_dev(const double u[5], const double ad[5], const Anchor &A, float gm1)
