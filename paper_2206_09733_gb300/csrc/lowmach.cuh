@@ -66,22 +66,30 @@ __host__ __device__ __forceinline__ void ff_fma(float &sh, float &sl, float ah, 
     sl += e + pe;
 }
 
+// (sh, sl) = (ah + al) * (bh + bl): ff_fma into a zero pair (the first term
+// of a sum), bitwise the same, without the two-sum.
+__host__ __device__ __forceinline__ void ff_mul(float &sh, float &sl, float ah, float al, float bh, float bl)
+{
+    sh = ah * bh;
+    const float pe = fmaf(ah, bh, -sh);
+    sl = fmaf(ah, bl, fmaf(al, bh, pe));
+}
+
 // FP64 -> FP32 (round to nearest even) of the deviations: the integer-pipe
 // rounding d2f_rn (the hardware conversion, one FP64-pipe instruction each,
 // measured 3-20% slower in all three deviation kernels).
 __device__ __forceinline__ float dev_round(double x) { return d2f_rn(x); }
 
 // FP64 -> (hi, lo) with hi = x rounded to FP32 (d2f_rn) and lo = x - hi
-// rounded to FP32, with no FP64 instruction: x - hi is exactly the integer
+// rounded to FP32 (ff_lo), with no FP64 instruction: x - hi is exactly the integer
 // R = (the 29 significand bits the rounding drops) - (2^29 if it rounded
 // up), |R| <= 2^28, times 2^(e - 1075) (e the biased FP64 exponent of x), so
 // lo is the integer-to-float conversion of R (round to nearest) scaled by that
 // power of two, with the sign of x.  Equal to d2f_rn(x - (double)hi) for
 // |x| >= 2^-74 (below, lo is flushed to zero; hi is already zero below the
 // FP32 normal range).
-__device__ __forceinline__ void ff_split(double x, float &hi, float &lo)
+__device__ __forceinline__ float ff_lo(double x)
 {
-    hi = d2f_rn(x);
     const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
     const unsigned e = (h >> 20) & 0x7ffu;
     const unsigned t = __funnelshift_l(l, h, 3);   // the kept bits, as d2f_rn truncates them
@@ -90,7 +98,13 @@ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo)
     const int R = (int)dropped - (int)(up << 29);
     const float scale = (e >= 949u && e <= 1202u) ? __int_as_float((int)(e - 948u) << 23) : 0.0f;
     const float mag = __int2float_rn(R) * scale;
-    lo = (h & 0x80000000u) ? -mag : mag;
+    return (h & 0x80000000u) ? -mag : mag;
+}
+
+__device__ __forceinline__ void ff_split(double x, float &hi, float &lo)
+{
+    hi = d2f_rn(x);
+    lo = ff_lo(x);
 }
 
 // ------------------------------------------------------------------ anchor
@@ -227,14 +241,14 @@ __device__ __forceinline__ void write_anchor(const Item &it, int e, const double
 }
 
 // u - ad for an FP64 value u and a reference value given as an FP32 pair
-// (h, l), with no FP64 instruction: u = uh + ul + r by ff_split (|r| <=
-// 2^-48 |u|), then (uh - h) + (ul - l) in FP32: the deviation within ~1.5 ulp
-// of its FP32 rounding, plus 2^-48 |u|.
+// (h, l), with no FP64 arithmetic: u = uh + ul + r (uh = u rounded to FP32,
+// ul = ff_lo(u), |r| <= 2^-48 |u|), then (uh - h) + (ul - l) in FP32: the
+// deviation within ~1.5 ulp of its FP32 rounding, plus 2^-48 |u|.  uh is the
+// hardware conversion (one FP64-pipe instruction, where the integer-pipe
+// d2f_rn measured slower: the gradient kernel that uses this is ALU-bound).
 __device__ __forceinline__ float dev_one(double u, float h, float l)
 {
-    float uh, ul;
-    ff_split(u, uh, ul);
-    return (uh - h) + (ul - l);
+    return (__double2float_rn(u) - h) + (ff_lo(u) - l);
 }
 
 // ------------------------------------------------------------------ deviations of one node
@@ -424,7 +438,7 @@ __device__ __forceinline__ void dflux_ec(const ECDev &L, const ECDev &Rr, const 
     const float mv1 = A.v1 + dv1, mv2 = A.v2 + dv2, mv3 = A.v3 + dv3;
     const float va = mv1 * a1 + mv2 * a2 + mv3 * a3;
     const float vda = dv1 * a1 + dv2 * a2 + dv3 * a3;
-    const float Fbr = A.rho * (A.v1 * a1 + A.v2 * a2 + A.v3 * a3);
+    const float Fbr = A.m1 * a1 + A.m2 * a2 + A.m3 * a3;   // rhobar vbar.A
     frho = rhd * va + A.rho * vda;
     // rho^{v} - {m} = (rho^ - {rho}){v} - (rho_i - rho_m)(v_i - v_m)/4
     {
@@ -455,7 +469,7 @@ __device__ __forceinline__ void dflux_ec_diag(const ECDev &z, const Anchor &A, f
     const float v1 = A.v1 + z.dv1, v2 = A.v2 + z.dv2, v3 = A.v3 + z.dv3;
     const float va = v1 * a1 + v2 * a2 + v3 * a3;
     const float vda = z.dv1 * a1 + z.dv2 * a2 + z.dv3 * a3;
-    const float Fbr = A.rho * (A.v1 * a1 + A.v2 * a2 + A.v3 * a3);
+    const float Fbr = A.m1 * a1 + A.m2 * a2 + A.m3 * a3;
     const float frho = z.dr * va + A.rho * vda;
     const float ptd = (z.dr - 2.0f * A.p * z.db + A.rbeta) * 0.5f * ib;
     fm[0] = frho * v1 + Fbr * z.dv1 + ptd * a1;

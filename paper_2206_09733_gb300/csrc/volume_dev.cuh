@@ -276,7 +276,10 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
             for (int d = 0; d < 3; ++d) {
                 float wh = 0.0f, wl = 0.0f;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ff_fma(wh, wl, ja[d * 3 + c], JL[(d * 3 + c) * n3 + p], mh[c], ml[c]);
+                for (int c = 0; c < 3; ++c) {
+                    if (c == 0) ff_mul(wh, wl, ja[d * 3], JL[(d * 3) * n3 + p], mh[0], ml[0]);
+                    else ff_fma(wh, wl, ja[d * 3 + c], JL[(d * 3 + c) * n3 + p], mh[c], ml[c]);
+                }
                 S[(WOFF + 2 * d) * n3 + p] = wh;
                 S[(WOFF + 2 * d + 1) * n3 + p] = wl;
             }
@@ -380,7 +383,8 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
                     const int pm = base + m * stride;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) V[v + 1] += Dm * S[(d * 4 + v) * n3 + pm];
-                    ff_fma(Ch, Cl, Dm, Dlrow[m], S[(12 + 2 * d) * n3 + pm], S[(13 + 2 * d) * n3 + pm]);
+                    if (d == 0 && m == 0) ff_mul(Ch, Cl, Dm, Dlrow[m], S[(12 + 2 * d) * n3 + pm], S[(13 + 2 * d) * n3 + pm]);
+                    else ff_fma(Ch, Cl, Dm, Dlrow[m], S[(12 + 2 * d) * n3 + pm], S[(13 + 2 * d) * n3 + pm]);
                 }
             }
         }
@@ -478,7 +482,10 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
 #pragma unroll
                         for (int v = 0; v < 4; ++v) V[v + 1] -= Dm * S[(VOFF + d * 4 + v) * n3 + pm];
                     }
-                    if constexpr (EC) ff_fma(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                    if constexpr (EC) {
+                        if (d == 0 && m == 0) ff_mul(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                        else ff_fma(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                    }
                 }
             }
             __syncthreads();
