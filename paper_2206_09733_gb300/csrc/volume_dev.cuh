@@ -396,6 +396,84 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int sd = (d == 0) ? 1 : (d == 1) ? n : n2;
+            // N = 3, Chandrashekar form: the x- and y-lines of a 64-thread element lie
+            // inside one warp, so their pair fluxes go to the partner node by warp
+            // shuffles (no pair buffer, no barrier); z-lines span two warps and take
+            // the shared-memory pair buffer below
+            const bool shfl = EC && n == 4 && d < 2;
+            if (shfl) {
+                const int x = ijk[d];
+                const int lane = threadIdx.x & 31;
+                const float *Drow = sD + x * n;
+                const float *DA = S + (9 + d * 3) * n3;
+                ECDev za{};
+                float dma[3] = {0.0f, 0.0f, 0.0f}, da[3] = {0.0f, 0.0f, 0.0f};
+                float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
+                if (valid) {
+                    za = {S[p], S[n3 + p], S[2 * n3 + p], S[3 * n3 + p], S[4 * n3 + p], S[5 * n3 + p]};
+                    dma[0] = S[6 * n3 + p];
+                    dma[1] = S[7 * n3 + p];
+                    dma[2] = S[8 * n3 + p];
+                    da[0] = DA[p];
+                    da[1] = DA[n3 + p];
+                    da[2] = DA[2 * n3 + p];
+                    c1 = 2.0f * CEN[d * 3];
+                    c2 = 2.0f * CEN[d * 3 + 1];
+                    c3 = 2.0f * CEN[d * 3 + 2];
+                }
+#pragma unroll
+                for (int k = 1; k <= KP; ++k) {
+                    // this node's thread evaluates the pair (x, x + k mod n) (for k = n/2 the
+                    // lower half of the line only) and receives the pair (x - k mod n, x)
+                    const bool own = !(2 * k == n && x >= KP);
+                    const bool recv = !(2 * k == n && x < KP);
+                    float fp[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                    if (valid && own) {
+                        const int xm = (x + k < n) ? x + k : x + k - n;
+                        const int c = p + (xm - x) * sd;
+                        const ECDev zc = {S[c], S[n3 + c], S[2 * n3 + c], S[3 * n3 + c], S[4 * n3 + c], S[5 * n3 + c]};
+                        const float dc[3] = {DA[c], DA[n3 + c], DA[2 * n3 + c]};
+                        float frho, rmass, fm[3], rest;
+                        dflux_ec(za, zc, A, hg, c1 + da[0] + dc[0], c2 + da[1] + dc[1], c3 + da[2] + dc[2], frho, rmass,
+                                 fm, rest);
+                        const float dm1 = dma[0] - S[6 * n3 + c], dm2 = dma[1] - S[7 * n3 + c], dm3 = dma[2] - S[8 * n3 + c];
+                        fp[0] = rmass - 0.5f * (dm1 * (da[0] - dc[0]) + dm2 * (da[1] - dc[1]) + dm3 * (da[2] - dc[2]));
+                        fp[1] = fm[0];
+                        fp[2] = fm[1];
+                        fp[3] = fm[2];
+                        fp[4] = rest;
+                        const float Dm = Drow[xm];
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) V[v] += Dm * fp[v];
+                    }
+                    const int xs = (x >= k) ? x - k : x - k + n;
+                    const int src = lane + (xs - x) * sd;
+                    float fr[5];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) fr[v] = __shfl_sync(0xffffffffu, fp[v], src);
+                    if (valid && recv) {
+                        const float Dm = Drow[xs];
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) V[v] += Dm * fr[v];
+                    }
+                }
+                if (valid) {
+                    const int base = p - x * sd;
+                    const float *Dlrow = sDl + x * n;
+#pragma unroll
+                    for (int m = 0; m < n; ++m) {
+                        const float Dm = Drow[m];
+                        const int pm = base + m * sd;
+                        if (NS) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) V[v + 1] -= Dm * S[(VOFF + d * 4 + v) * n3 + pm];
+                        }
+                        if (d == 0 && m == 0) ff_mul(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                        else ff_fma(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                    }
+                }
+                continue;
+            }
             if (valid) {
                 // the thread of node a (index x along d) evaluates the pairs (x, x + k mod n)
                 // of its line: consecutive threads read consecutive nodes, without the
@@ -488,7 +566,8 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
                     }
                 }
             }
-            __syncthreads();
+            // (after the last direction the pair buffer is not written again)
+            if (d < 2) __syncthreads();
         }
     }
     if constexpr (BULK) {
