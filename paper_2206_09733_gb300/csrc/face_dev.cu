@@ -121,8 +121,11 @@ __device__ __forceinline__ void matrix_diss(const Prim<float> &L, const Prim<flo
     D[4] = hs * (k1 * r1[4] + k2 * 0.5f * v2h + k5 * r5[4] + v1 * P1 + v2 * P2 + v3 * P3);
 }
 
-// Face point t (face gf = t / n^2, point ab = t mod n^2) of the batch.
-template <int N, bool NS>
+// Face point t (face gf = t / n^2, point ab = t mod n^2) of the batch.  TWO:
+// the flux is one of the two-point family (EC, matrix dissipation), else of
+// the central + dissipation family (LF, Rusanov, Roe, low-dissipation Roe);
+// a kernel per family keeps the other family's registers out of it.
+template <int N, bool NS, bool TWO>
 __device__ __forceinline__ void face_dev_point(const Batch &b, int flux, long long t)
 {
     constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -148,11 +151,10 @@ __device__ __forceinline__ void face_dev_point(const Batch &b, int flux, long lo
     const float gm1 = it.gm1f, hg = it.hgf, gamma = it.gammaf;
     // the entropy-conservative fluxes mix one- and two-point deviations and need
     // the reference state whose identities hold exactly; the others only differences
-    const bool two_point = (flux == HS3D_FLUX_EC || flux == HS3D_FLUX_MATRIX);
     double ad[5];
     Anchor A;
     Dev DL, DR;
-    if (two_point) {
+    if constexpr (TWO) {
         // the minus element's reference state, left by the pass before
         const AnchorRec &R = ((const AnchorRec *)it.anc)[eL];
         A = R.a;
@@ -173,7 +175,7 @@ __device__ __forceinline__ void face_dev_point(const Batch &b, int flux, long lo
     const Prim<float> qL = dev_prim(DL, A), qR = dev_prim(DR, A);
     float fL[5], fR[5], GL[5], GR[5];
     dflux_euler(DL, A, s1, s2, s3, fL);
-    if (flux == HS3D_FLUX_EC || flux == HS3D_FLUX_MATRIX) {
+    if constexpr (TWO) {
         const ECDev zL = ec_dev(DL, A), zR = ec_dev(DR, A);
         float frho, rmass, fm[3], rest;
         dflux_ec(zL, zR, A, hg, s1, s2, s3, frho, rmass, fm, rest);
@@ -252,7 +254,7 @@ __device__ __forceinline__ void face_dev_point(const Batch &b, int flux, long lo
 
 // The face kernel: one thread per face point, or (Batch::persistent) a
 // persistent grid striding over the face points.
-template <int N, bool NS>
+template <int N, bool NS, bool TWO>
 __global__ void __launch_bounds__(256, 4) k_face_dev(const __grid_constant__ Batch b, int flux)
 {
     pdl_wait();
@@ -260,7 +262,14 @@ __global__ void __launch_bounds__(256, 4) k_face_dev(const __grid_constant__ Bat
     const long long total = b.total_faces * n2;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x)
-        face_dev_point<N, NS>(b, flux, t);
+        face_dev_point<N, NS, TWO>(b, flux, t);
+}
+
+template <int N, bool NS, bool TWO>
+static cudaError_t face_dev_launch3(int flux, const Batch &b, unsigned blocks, cudaStream_t s)
+{
+    const unsigned grid = b.persistent ? persistent_grid(k_face_dev<N, NS, TWO>, 256, 0, blocks) : blocks;
+    return launch_pdl(k_face_dev<N, NS, TWO>, grid, 256, 0, s, b, flux);
 }
 
 template <int N>
@@ -270,12 +279,10 @@ static cudaError_t face_dev_launch(int physics, int flux, const Batch &b, cudaSt
     const long long total = b.total_faces * n2;
     if (total == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    if (physics == HS3D_NS) {
-        const unsigned grid = b.persistent ? persistent_grid(k_face_dev<N, true>, 256, 0, blocks) : blocks;
-        return launch_pdl(k_face_dev<N, true>, grid, 256, 0, s, b, flux);
-    }
-    const unsigned grid = b.persistent ? persistent_grid(k_face_dev<N, false>, 256, 0, blocks) : blocks;
-    return launch_pdl(k_face_dev<N, false>, grid, 256, 0, s, b, flux);
+    const bool two = (flux == HS3D_FLUX_EC || flux == HS3D_FLUX_MATRIX);
+    if (physics == HS3D_NS)
+        return two ? face_dev_launch3<N, true, true>(flux, b, blocks, s) : face_dev_launch3<N, true, false>(flux, b, blocks, s);
+    return two ? face_dev_launch3<N, false, true>(flux, b, blocks, s) : face_dev_launch3<N, false, false>(flux, b, blocks, s);
 }
 
 cudaError_t launch_face_dev(int N, int physics, int flux, const Batch &b, cudaStream_t s)
