@@ -269,6 +269,7 @@ Batch single_batch(const Item &it)
     b.total_faces = 3LL * it.E;
     b.dt_fixed = 0.0;
     b.gauss = it.gauss;
+    b.mortar = it.face6 ? 1 : 0;
     return b;
 }
 

@@ -120,6 +120,9 @@ struct Batch {
     // 1: the element, gradient and face kernels run a persistent grid (as many CTAs as fit at
     // once) whose CTAs walk the tiles with a stride of the grid size
     int persistent;
+    // 1: every item takes its face fluxes from the mortar kernels (Item::face6, meshes with
+    // per-element degrees), 0: none does; the element kernel has an instantiation for each
+    int mortar;
 };
 
 // 1-D operators on the Gauss-Lobatto nodes for one N.

@@ -134,8 +134,9 @@ constexpr int dev_min_blocks()
 }
 
 // One tile (epb elements) of the element kernel; returns true on the
-// thread that initialised its element's bulk-copy barrier.
-template <int N, bool NS, int FORM>
+// thread that initialised its element's bulk-copy barrier.  MORT: the items
+// take their face fluxes from the mortar kernels (Item::face6).
+template <int N, bool NS, int FORM, bool MORT>
 __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__restrict__ ops, int stage, double rkA,
                                                 double rkB, int lam_slot, int epb, long long tile,
                                                 unsigned long long *bulk_bar)
@@ -221,7 +222,7 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
 #pragma unroll
             for (int slot = 0; slot < 6; ++slot) {
                 const int d = slot >> 1;
-                if (it.face6) blk[slot] = ((size_t)slot * it.E + e) * 5 * n2;
+                if (MORT) blk[slot] = ((size_t)slot * it.E + e) * 5 * n2;
                 else if (slot & 1) blk[slot] = (((size_t)d * it.E + e) * 2 + 0) * 5 * n2;
                 else blk[slot] = (((size_t)d * it.E + nb.m[d]) * 2 + 1) * 5 * n2;
             }
@@ -608,7 +609,7 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
     // surface term
     float own[3][5];
     bool need_own = false;
-    if (it.face6) {
+    if constexpr (MORT) {
         // mortar flux minus the own FP32 flux (full values)
 #pragma unroll
         for (int d = 0; d < 3; ++d) need_own |= (ijk[d] == 0 || ijk[d] == N);
@@ -647,7 +648,7 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
         const int ab = ta + n * tb;
         const bool plus = ijk[d] == N;
         const float *F = F6 + (2 * d + (plus ? 1 : 0)) * 5 * n2 + ab;
-        if (it.face6) {
+        if constexpr (MORT) {
 #pragma unroll
             for (int v = 0; v < 5; ++v) V[v] += plus ? iw * (F[v * n2] - own[d][v]) : iw * (own[d][v] - F[v * n2]);
         } else {
@@ -730,14 +731,14 @@ __device__ __noinline__ bool volume_dev_tile_call(const Batch &b, const Ops *__r
                                                   double rkB, int lam_slot, int epb, long long tile,
                                                   unsigned long long *bulk_bar)
 {
-    return volume_dev_tile<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, tile, bulk_bar);
+    return volume_dev_tile<N, NS, FORM, false>(b, ops, stage, rkA, rkB, lam_slot, epb, tile, bulk_bar);
 }
 
 // The element kernel: a CTA per tile, or (PERSIST, Batch::persistent) a
 // persistent grid whose CTAs walk the tiles with a stride of the grid size,
 // reusing their shared memory; a tile's element barriers are invalidated
 // before the next tile initialises them again.
-template <int N, bool NS, int FORM, bool PERSIST>
+template <int N, bool NS, int FORM, bool PERSIST, bool MORT = false>
 __global__ void __launch_bounds__(dev_threads<N>(), dev_min_blocks<N, FORM>())
 k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int stage, double rkA, double rkB,
              int lam_slot, int epb, long long ntiles)
@@ -747,7 +748,7 @@ k_volume_dev(const __grid_constant__ Batch b, const Ops *__restrict__ ops, int s
     constexpr bool BULK = ((N + 1) % 2 == 0);
     __shared__ unsigned long long bulk_bar[BULK ? 256 / (n3 < 256 ? n3 : 256) : 1];
     if constexpr (!PERSIST) {
-        volume_dev_tile<N, NS, FORM>(b, ops, stage, rkA, rkB, lam_slot, epb, blockIdx.x, bulk_bar);
+        volume_dev_tile<N, NS, FORM, MORT>(b, ops, stage, rkA, rkB, lam_slot, epb, blockIdx.x, bulk_bar);
     } else {
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const bool armed =
@@ -773,11 +774,14 @@ static cudaError_t vol_dev_launch2(const Batch &b, int stage, double rkA, double
     const unsigned blocks = (unsigned)((b.total_elems + epb - 1) / epb);
     const Ops *ops = device_ops(N);
     if (!ops) return cudaErrorMemoryAllocation;
-    if (b.persistent) {
+    if (b.persistent && !b.mortar) {
         const unsigned grid = persistent_grid(k_volume_dev<N, NS, FORM, true>, threads, smem, blocks);
         return launch_pdl(k_volume_dev<N, NS, FORM, true>, grid, threads, smem, s, b, ops, stage, rkA, rkB,
                           stage >= 0 ? lam_slot : -1, epb, (long long)blocks);
     }
+    if (b.mortar)
+        return launch_pdl(k_volume_dev<N, NS, FORM, false, true>, blocks, threads, smem, s, b, ops, stage, rkA, rkB,
+                          stage >= 0 ? lam_slot : -1, epb, (long long)blocks);
     return launch_pdl(k_volume_dev<N, NS, FORM, false>, blocks, threads, smem, s, b, ops, stage, rkA, rkB,
                       stage >= 0 ? lam_slot : -1, epb, (long long)blocks);
 }
@@ -814,6 +818,8 @@ static cudaError_t prep_vol_dev_n()
     if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, true, FORM, false>);
     if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, false, FORM, true>);
     if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, true, FORM, true>);
+    if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, false, FORM, false, true>);
+    if (e == cudaSuccess) e = prep_vol_dev_kernel(k_volume_dev<N, true, FORM, false, true>);
     return e;
 }
 
