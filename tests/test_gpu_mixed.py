@@ -83,6 +83,30 @@ def test_mixed_every_order(N, combo):
     assert gm.clock()[1] >= 3
 
 
+def test_mixed_ec_n3_partial_tile():
+    """The Chandrashekar element kernel at N = 3, whose x- and y-line pair
+    fluxes travel by warp shuffles: 27 elements in the default tiles of 4
+    elements, so that the last tile holds an element past the end of the mesh
+    (its lanes take part in the shuffles with no work), against the oracle."""
+    lo, hi = (-np.pi,) * 3, (np.pi,) * 3
+    om = O.Mesh(3, 3, 3, 3, lo=lo, hi=hi, amp=0.07)
+    gm = hs.Mesh(3, 3, 3, 3, lo=lo, hi=hi, amp=0.07)
+    u0 = random_state(om.shape, seed=77, smooth=True)
+    oc = O.Cfg("ns", "roe", "ec", Re=400.0)
+    gc = hs.solver_cfg("ns", "roe", "ec", "mixed32", Re=400.0)
+    ref = om.residual(oc, u0)
+    u = torch.from_numpy(u0).cuda()
+    r = torch.empty_like(u)
+    gm.residual(gc, u, r)
+    assert rel(host(r), ref) < 1e-5
+    uo, go = u0.copy(), np.zeros_like(u0)
+    for _ in range(2):
+        om.rk3_step(oc, uo, go)
+    g = torch.zeros_like(u)
+    gm.rk3_run(gc, u, g, 2)
+    assert rel(host(u), uo) < 1e-5
+
+
 @pytest.mark.parametrize("vol", ["standard", "ec", "kg"])
 def test_tensor_core_precision_computes_as_mixed32(vol):
     """HS3D_MIXED_TC is accepted and runs the MIXED32 kernels (the
