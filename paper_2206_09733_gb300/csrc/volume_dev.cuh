@@ -397,30 +397,42 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int sd = (d == 0) ? 1 : (d == 1) ? n : n2;
-            // N = 3, Chandrashekar form: the x- and y-lines of a 64-thread element lie
-            // inside one warp, so their pair fluxes go to the partner node by warp
-            // shuffles (no pair buffer, no barrier); z-lines span two warps and take
-            // the shared-memory pair buffer below
-            const bool shfl = EC && n == 4 && d < 2;
+            // N = 3: the x- and y-lines of a 64-thread element lie inside one warp,
+            // so their pair fluxes go to the partner node by warp shuffles (no pair
+            // buffer, no barrier); z-lines span two warps and take the shared-memory
+            // pair buffer below
+            const bool shfl = n == 4 && d < 2;
             if (shfl) {
                 const int x = ijk[d];
                 const int lane = threadIdx.x & 31;
                 const float *Drow = sD + x * n;
-                const float *DA = S + (9 + d * 3) * n3;
+                const float *DA = S + (9 + d * 3) * n3;   // Chandrashekar form: metric deviations
+                const float *SJ = S + (7 + d * 3) * n3;   // other split forms: metric terms
                 ECDev za{};
                 float dma[3] = {0.0f, 0.0f, 0.0f}, da[3] = {0.0f, 0.0f, 0.0f};
                 float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
+                float zo[kSplitSlots];
+#pragma unroll
+                for (int q = 0; q < kSplitSlots; ++q) zo[q] = 0.0f;
                 if (valid) {
-                    za = {S[p], S[n3 + p], S[2 * n3 + p], S[3 * n3 + p], S[4 * n3 + p], S[5 * n3 + p]};
-                    dma[0] = S[6 * n3 + p];
-                    dma[1] = S[7 * n3 + p];
-                    dma[2] = S[8 * n3 + p];
-                    da[0] = DA[p];
-                    da[1] = DA[n3 + p];
-                    da[2] = DA[2 * n3 + p];
-                    c1 = 2.0f * CEN[d * 3];
-                    c2 = 2.0f * CEN[d * 3 + 1];
-                    c3 = 2.0f * CEN[d * 3 + 2];
+                    if constexpr (EC) {
+                        za = {S[p], S[n3 + p], S[2 * n3 + p], S[3 * n3 + p], S[4 * n3 + p], S[5 * n3 + p]};
+                        dma[0] = S[6 * n3 + p];
+                        dma[1] = S[7 * n3 + p];
+                        dma[2] = S[8 * n3 + p];
+                        da[0] = DA[p];
+                        da[1] = DA[n3 + p];
+                        da[2] = DA[2 * n3 + p];
+                        c1 = 2.0f * CEN[d * 3];
+                        c2 = 2.0f * CEN[d * 3 + 1];
+                        c3 = 2.0f * CEN[d * 3 + 2];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < kSplitSlots; ++q) zo[q] = S[q * n3 + p];
+                        c1 = SJ[p];
+                        c2 = SJ[n3 + p];
+                        c3 = SJ[2 * n3 + p];
+                    }
                 }
 #pragma unroll
                 for (int k = 1; k <= KP; ++k) {
@@ -432,17 +444,25 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
                     if (valid && own) {
                         const int xm = (x + k < n) ? x + k : x + k - n;
                         const int c = p + (xm - x) * sd;
-                        const ECDev zc = {S[c], S[n3 + c], S[2 * n3 + c], S[3 * n3 + c], S[4 * n3 + c], S[5 * n3 + c]};
-                        const float dc[3] = {DA[c], DA[n3 + c], DA[2 * n3 + c]};
-                        float frho, rmass, fm[3], rest;
-                        dflux_ec(za, zc, A, hg, c1 + da[0] + dc[0], c2 + da[1] + dc[1], c3 + da[2] + dc[2], frho, rmass,
-                                 fm, rest);
-                        const float dm1 = dma[0] - S[6 * n3 + c], dm2 = dma[1] - S[7 * n3 + c], dm3 = dma[2] - S[8 * n3 + c];
-                        fp[0] = rmass - 0.5f * (dm1 * (da[0] - dc[0]) + dm2 * (da[1] - dc[1]) + dm3 * (da[2] - dc[2]));
-                        fp[1] = fm[0];
-                        fp[2] = fm[1];
-                        fp[3] = fm[2];
-                        fp[4] = rest;
+                        if constexpr (EC) {
+                            const ECDev zc = {S[c], S[n3 + c], S[2 * n3 + c], S[3 * n3 + c], S[4 * n3 + c], S[5 * n3 + c]};
+                            const float dc[3] = {DA[c], DA[n3 + c], DA[2 * n3 + c]};
+                            float frho, rmass, fm[3], rest;
+                            dflux_ec(za, zc, A, hg, c1 + da[0] + dc[0], c2 + da[1] + dc[1], c3 + da[2] + dc[2], frho,
+                                     rmass, fm, rest);
+                            const float dm1 = dma[0] - S[6 * n3 + c], dm2 = dma[1] - S[7 * n3 + c],
+                                        dm3 = dma[2] - S[8 * n3 + c];
+                            fp[0] = rmass - 0.5f * (dm1 * (da[0] - dc[0]) + dm2 * (da[1] - dc[1]) + dm3 * (da[2] - dc[2]));
+                            fp[1] = fm[0];
+                            fp[2] = fm[1];
+                            fp[3] = fm[2];
+                            fp[4] = rest;
+                        } else {
+                            float zc[kSplitSlots];
+#pragma unroll
+                            for (int q = 0; q < kSplitSlots; ++q) zc[q] = S[q * n3 + c];
+                            split_pair<FORM>(zo, zc, gam, hg, c1 + SJ[c], c2 + SJ[n3 + c], c3 + SJ[2 * n3 + c], fp);
+                        }
                         const float Dm = Drow[xm];
 #pragma unroll
                         for (int v = 0; v < 5; ++v) V[v] += Dm * fp[v];
@@ -469,8 +489,10 @@ __device__ __forceinline__ bool volume_dev_tile(const Batch &b, const Ops *__res
 #pragma unroll
                             for (int v = 0; v < 4; ++v) V[v + 1] -= Dm * S[(VOFF + d * 4 + v) * n3 + pm];
                         }
-                        if (d == 0 && m == 0) ff_mul(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
-                        else ff_fma(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                        if constexpr (EC) {
+                            if (d == 0 && m == 0) ff_mul(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                            else ff_fma(Ch, Cl, Dm, Dlrow[m], S[(18 + 2 * d) * n3 + pm], S[(19 + 2 * d) * n3 + pm]);
+                        }
                     }
                 }
                 continue;
